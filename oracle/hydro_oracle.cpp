@@ -1,0 +1,842 @@
+// hydro_oracle.cpp -- TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT PATH.
+//
+// Plain, slow CPU reference ("oracle") for one unsplit six-solve CTU step of the
+// 3D Euler equations (Schneider & Robertson, "Cholla", Sec. 2.3, Eqs.
+// simple_conserved_update / transverse_evolution / conserved_update), with PPMC
+// reconstruction (App. A.3, slopes from App. A.2) and the exact Riemann solver of
+// Toro ch. 4 as the paper gives it (App. B.1).  Everything is FP64 and follows
+// the paper's steps in the paper's order and notation: every intermediate of the
+// method (cell primitives w, face states U*, first fluxes F*, CTU fluxes
+// F^{n+1/2}) is a full-grid array, nothing is fused, blocked or reordered.
+//
+// Only the test suite, the smoke check and the benchmark's CPU-baseline leg load
+// this library.  It shares no source, header, table or helper with the CUDA path.
+//
+// Build: g++ -std=c++17 -O2 -ffp-contract=off -fopenmp -shared -fPIC.  No
+// fast-math, no fused multiply-add: every operation is one IEEE round-to-nearest
+// operation; divisions and square roots are correctly rounded, pow is libm's.
+//
+// Readings of the paper adopted here (each is a reading, not a printed fact):
+//  * ghost depth NG = 4 per active side; PPMC needs 3 (App. A.3 stencil).
+//  * transmissive boundary = every ghost copies the outermost real cell; reflective
+//    = mirror copy with the normal momentum negated (Sec. 3.1); inflow = a fixed
+//    prescribed primitive state; ghosts are filled x, then y, then z, each pass
+//    over the already-filled ghosts of earlier axes (this fills edges and corners
+//    the way the x->y->z exchange of Sec. 3.5.2 does).
+//  * dt is taken from the state at the start of the step over real cells and
+//    active axes (Eq. calc_dt_3D); an axis with one cell is inactive (no ghosts,
+//    no sweep, no transverse term), so the step reduces to 2D/1D CTU (Sec. 2.3).
+//  * the 1e-20 pressure floor (Sec. 2.4.1) applies to every derived pressure: cell
+//    primitives, the PPMC face states, the states fed to each Riemann solve and
+//    each Newton iterate.  Stored conserved variables are never modified.
+//  * PLMC projection: xi0 = 0.5(-rho du/a + dp/a^2) (the printed sign of the rho
+//    du/a term makes projection followed by back-projection lose dp; App. A.2).
+//  * PPMC: w6 = 6 w_i - 3 (W_L + W_R) (the cell mean of the parabola is w_i);
+//    B uses alpha^m in its first bracket and D uses the "beta" form with minus
+//    signs in both brackets, so that E, B, C, D are differences of the traced
+//    states W^k (App. A.3).  Slopes of cells i-1, i, i+1 use each cell's own rho
+//    and a and are not clipped to the neighbours (PPMC step one).
+//  * MC limiter: zero unless xi_L xi_R > 0, sgn(0) = +1 (App. A.1).
+//  * Newton: tolerance 1e-6, at most 50 iterations (cap sets a status flag and
+//    keeps the last iterate); an iterate below the floor is raised to it; u^m uses
+//    f_L, f_R evaluated at the final p^m.
+//  * Right-hand rarefaction fan: a = 2/(gamma+1) (a_R - (gamma-1) u_R / 2), u = -a
+//    (the printed "+" breaks continuity at the fan head u_R + a_R = 0); the right
+//    shock speed is s_R (printed "s_LR").
+//  * Interface energy: E = p/(gamma-1) + rho (u^2 + v_k^2 + w_k^2)/2; transverse
+//    velocities are taken from the left state when the sampled u >= 0.
+//  * Velocity order of a sweep is cyclic: x (u,v,w), y (v,w,u), z (w,u,v); the
+//    transverse terms of an x face are added y then z, of a y face z then x, of a
+//    z face x then y; the update adds the x, then y, then z flux differences.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+constexpr int NG = 4;
+constexpr double P_FLOOR = 1e-20;
+constexpr double P0_FLOOR = 1e-6;
+constexpr double NEWTON_TOL = 1e-6;
+constexpr int NEWTON_MAX = 50;
+
+enum : int { FLAG_NEWTON = 1, FLAG_NONPHYS = 2 };
+enum : int { BC_PERIODIC = 0, BC_REFLECT = 1, BC_OUTFLOW = 2, BC_INFLOW = 3 };
+
+// ---------------------------------------------------------------------------
+// Operation-counting scalar.  The same templated code runs on `double` (the
+// oracle proper) and on `CR` (a double that counts each arithmetic operation) so
+// that the algorithmic FP64 operation count per cell update can be measured on
+// any workload.  Counting runs single-threaded.
+struct OpCount {
+  uint64_t add = 0, mul = 0, div = 0, sqrt = 0, pow = 0, cmp = 0;
+};
+OpCount g_ops;
+
+struct CR {
+  double v;
+  CR() : v(0.0) {}
+  CR(double x) : v(x) {}
+};
+inline CR operator+(CR a, CR b) { ++g_ops.add; return CR(a.v + b.v); }
+inline CR operator-(CR a, CR b) { ++g_ops.add; return CR(a.v - b.v); }
+inline CR operator-(CR a) { return CR(-a.v); }
+inline CR operator*(CR a, CR b) { ++g_ops.mul; return CR(a.v * b.v); }
+inline CR operator/(CR a, CR b) { ++g_ops.div; return CR(a.v / b.v); }
+inline bool operator<(CR a, CR b) { ++g_ops.cmp; return a.v < b.v; }
+inline bool operator>(CR a, CR b) { ++g_ops.cmp; return a.v > b.v; }
+inline bool operator<=(CR a, CR b) { ++g_ops.cmp; return a.v <= b.v; }
+inline bool operator>=(CR a, CR b) { ++g_ops.cmp; return a.v >= b.v; }
+inline CR sqrt(CR a) { ++g_ops.sqrt; return CR(std::sqrt(a.v)); }
+inline CR pow(CR a, CR b) { ++g_ops.pow; return CR(std::pow(a.v, b.v)); }
+inline CR fabs(CR a) { ++g_ops.cmp; return CR(std::fabs(a.v)); }
+inline double val(CR a) { return a.v; }
+inline double val(double a) { return a; }
+// the double overloads sit beside the counted ones so that templated code picks
+// the exact match for R = double
+using std::fabs;
+using std::pow;
+using std::sqrt;
+
+template <class R> inline R mn(R a, R b) { return (b < a) ? b : a; }
+template <class R> inline R mx(R a, R b) { return (a < b) ? b : a; }
+// sgn(x) = -1 for x < 0, else +1 (App. A.1)
+template <class R> inline R sgn(R x) { return (x < R(0.0)) ? R(-1.0) : R(1.0); }
+
+// Constants that depend on gamma only (computed once, not per operation).
+struct Gas {
+  double gamma, gm1, gp1;
+  double z;        // (gamma-1)/(2 gamma), rarefaction exponent
+  double zd;       // -(gamma+1)/(2 gamma), exponent of f' on a rarefaction
+  double inv_g;    // 1/gamma
+  double g_fan_d;  // 2/(gamma-1)
+  double g_fan_p;  // 2 gamma/(gamma-1)
+  double two_gp1;  // 2/(gamma+1)
+  double half_gm1; // (gamma-1)/2
+  double sh_a;     // (gamma+1)/(2 gamma)
+  double sh_b;     // (gamma-1)/(2 gamma)
+  double gm1_gp1;  // (gamma-1)/(gamma+1)
+  explicit Gas(double g) {
+    gamma = g; gm1 = g - 1.0; gp1 = g + 1.0;
+    z = (g - 1.0) / (2.0 * g);
+    zd = -(g + 1.0) / (2.0 * g);
+    inv_g = 1.0 / g;
+    g_fan_d = 2.0 / (g - 1.0);
+    g_fan_p = 2.0 * g / (g - 1.0);
+    two_gp1 = 2.0 / (g + 1.0);
+    half_gm1 = (g - 1.0) / 2.0;
+    sh_a = (g + 1.0) / (2.0 * g);
+    sh_b = (g - 1.0) / (2.0 * g);
+    gm1_gp1 = (g - 1.0) / (g + 1.0);
+  }
+};
+
+// Velocity order of a sweep along axis d: (normal, t1, t2) as global components.
+constexpr int PERM[3][3] = {{0, 1, 2}, {1, 2, 0}, {2, 0, 1}};
+
+// ---------------------------------------------------------------------------
+// Conserved <-> primitive (Sec. 2.1: u = [rho, rho u, rho v, rho w, E],
+// w = [rho, u, v, w, p], p = (gamma-1) rho e, E = rho (V^2/2 + e)).  Vectors are in
+// the sweep's rotated order (rho, normal, t1, t2, energy-or-pressure).
+template <class R>
+void cons_to_prim(const R U[5], const Gas& g, R W[5]) {
+  const R d = U[0];
+  const R u = U[1] / d, v = U[2] / d, w = U[3] / d;
+  R p = R(g.gm1) * (U[4] - R(0.5) * d * (u * u + v * v + w * w));
+  W[0] = d; W[1] = u; W[2] = v; W[3] = w;
+  W[4] = mx(p, R(P_FLOOR));
+}
+
+template <class R>
+void prim_to_cons(const R W[5], const Gas& g, R U[5]) {
+  const R d = W[0], u = W[1], v = W[2], w = W[3], p = W[4];
+  U[0] = d; U[1] = d * u; U[2] = d * v; U[3] = d * w;
+  U[4] = p / R(g.gm1) + R(0.5) * d * (u * u + v * v + w * w);
+}
+
+// ---------------------------------------------------------------------------
+// Exact Riemann solver (App. B.1, after Toro ch. 4).
+template <class R>
+struct RiemannResult {
+  R F[5];    // flux, rotated order
+  R pm, um;  // star pressure and velocity
+  R ws[5];   // sampled primitive state at x/t = 0 (rotated order)
+  int iters;
+  int flags;
+};
+
+// Pressure function f_k and its derivative (Eq. pressure_functions and the
+// derivative that follows it).
+template <class R>
+void pressure_function(R p, R dk, R pk, R ak, R Ak, R Bk, const Gas& g, R& f, R& fd) {
+  if (p <= pk) {  // rarefaction
+    const R ratio = p / pk;
+    f = R(2.0) * ak / R(g.gm1) * (pow(ratio, R(g.z)) - R(1.0));
+    fd = R(1.0) / (dk * ak) * pow(ratio, R(g.zd));
+  } else {        // shock
+    const R q = sqrt(Ak / (p + Bk));
+    f = (p - pk) * q;
+    fd = q * (R(1.0) - (p - pk) / (R(2.0) * (Bk + p)));
+  }
+}
+
+template <class R>
+void riemann_exact_prim(const R WL[5], const R WR[5], const Gas& g, RiemannResult<R>& out) {
+  const R dL = WL[0], uL = WL[1], pL = WL[4];
+  const R dR = WR[0], uR = WR[1], pR = WR[4];
+  out.flags = 0;
+  // sound speeds
+  const R aL = sqrt(R(g.gamma) * pL / dL);
+  const R aR = sqrt(R(g.gamma) * pR / dR);
+  // primitive-variable (PVRS) estimate, not below zero
+  R pt = R(0.5) * (pL + pR) + R(0.125) * (uL - uR) * (dL + dR) * (aL + aR);
+  if (pt < R(0.0)) pt = R(0.0);
+  // two-shock estimate p0, floored at 1e-6
+  const R AL = R(2.0) / (R(g.gp1) * dL), AR = R(2.0) / (R(g.gp1) * dR);
+  const R BL = R(g.gm1_gp1) * pL, BR = R(g.gm1_gp1) * pR;
+  const R gL = sqrt(AL / (pt + BL)), gR = sqrt(AR / (pt + BR));
+  R p0 = (gL * pL + gR * pR - (uR - uL)) / (gL + gR);
+  if (p0 < R(P0_FLOOR)) p0 = R(P0_FLOOR);
+  // Newton-Raphson iteration on f_L + f_R + u_R - u_L = 0
+  R p = p0, fL, fR, dfL, dfR;
+  int it = 0;
+  bool converged = false;
+  while (it < NEWTON_MAX) {
+    pressure_function(p, dL, pL, aL, AL, BL, g, fL, dfL);
+    pressure_function(p, dR, pR, aR, AR, BR, g, fR, dfR);
+    R pn = p - (fL + fR + uR - uL) / (dfL + dfR);
+    if (pn < R(P_FLOOR)) pn = R(P_FLOOR);
+    const R delta = R(2.0) * fabs(pn - p) / fabs(pn + p);
+    p = pn;
+    ++it;
+    if (delta < R(NEWTON_TOL)) { converged = true; break; }
+  }
+  if (!converged) out.flags |= FLAG_NEWTON;
+  out.iters = it;
+  // star velocity from the pressure functions at the final p^m
+  pressure_function(p, dL, pL, aL, AL, BL, g, fL, dfL);
+  pressure_function(p, dR, pR, aR, AR, BR, g, fR, dfR);
+  const R pm = p;
+  const R um = R(0.5) * (uL + uR + fR - fL);
+  out.pm = pm;
+  out.um = um;
+
+  // sample the solution at the interface (ten cases)
+  R d, u, pp;
+  if (um >= R(0.0)) {
+    if (pm <= pL) {  // left rarefaction
+      if (uL - aL >= R(0.0)) {
+        d = dL; u = uL; pp = pL;
+      } else if (um - aL * pow(pm / pL, R(g.z)) < R(0.0)) {
+        d = dL * pow(pm / pL, R(g.inv_g)); u = um; pp = pm;
+      } else {
+        const R a = R(g.two_gp1) * (aL + R(g.half_gm1) * uL);
+        d = dL * pow(a / aL, R(g.g_fan_d)); u = a; pp = pL * pow(a / aL, R(g.g_fan_p));
+      }
+    } else {          // left shock
+      const R sL = uL - aL * sqrt(R(g.sh_a) * pm / pL + R(g.sh_b));
+      if (sL >= R(0.0)) {
+        d = dL; u = uL; pp = pL;
+      } else {
+        d = dL * (pm / pL + R(g.gm1_gp1)) / (pm / pL * R(g.gm1_gp1) + R(1.0));
+        u = um; pp = pm;
+      }
+    }
+  } else {
+    if (pm <= pR) {  // right rarefaction
+      if (uR + aR <= R(0.0)) {
+        d = dR; u = uR; pp = pR;
+      } else if (um + aR * pow(pm / pR, R(g.z)) >= R(0.0)) {
+        d = dR * pow(pm / pR, R(g.inv_g)); u = um; pp = pm;
+      } else {
+        const R a = R(g.two_gp1) * (aR - R(g.half_gm1) * uR);
+        d = dR * pow(a / aR, R(g.g_fan_d)); u = -a; pp = pR * pow(a / aR, R(g.g_fan_p));
+      }
+    } else {          // right shock
+      const R sR = uR + aR * sqrt(R(g.sh_a) * pm / pR + R(g.sh_b));
+      if (sR <= R(0.0)) {
+        d = dR; u = uR; pp = pR;
+      } else {
+        d = dR * (pm / pR + R(g.gm1_gp1)) / (pm / pR * R(g.gm1_gp1) + R(1.0));
+        u = um; pp = pm;
+      }
+    }
+  }
+  // transverse velocities are advected: left state if u >= 0, else right
+  const R v = (u >= R(0.0)) ? WL[2] : WR[2];
+  const R w = (u >= R(0.0)) ? WL[3] : WR[3];
+  out.ws[0] = d; out.ws[1] = u; out.ws[2] = v; out.ws[3] = w; out.ws[4] = pp;
+  // flux (Eq. x_flux with E = p/(gamma-1) + rho V^2/2)
+  const R E = pp / R(g.gm1) + R(0.5) * d * (u * u + v * v + w * w);
+  const R mflux = d * u;
+  out.F[0] = mflux;
+  out.F[1] = mflux * u + pp;
+  out.F[2] = mflux * v;
+  out.F[3] = mflux * w;
+  out.F[4] = (E + pp) * u;
+}
+
+template <class R>
+int riemann_exact_cons(const R UL[5], const R UR[5], const Gas& g, R F[5]) {
+  R WL[5], WR[5];
+  cons_to_prim(UL, g, WL);
+  cons_to_prim(UR, g, WR);
+  RiemannResult<R> res;
+  riemann_exact_prim(WL, WR, g, res);
+  for (int q = 0; q < 5; ++q) F[q] = res.F[q];
+  return res.flags;
+}
+
+// ---------------------------------------------------------------------------
+// PLMC slope of one cell (App. A.2: differences, characteristic projection with the
+// cell's own rho and a, MC limiter on each characteristic, back-projection).
+template <class R>
+void project(const R dv[5], R d, R a, R x[5]) {
+  x[0] = R(0.5) * (-(d * dv[1]) / a + dv[4] / (a * a));
+  x[1] = dv[0] - dv[4] / (a * a);
+  x[2] = dv[2];
+  x[3] = dv[3];
+  x[4] = R(0.5) * (d * dv[1] / a + dv[4] / (a * a));
+}
+
+template <class R>
+void plmc_slope(const R wm[5], const R wc[5], const R wp[5], const Gas& g, R dw[5]) {
+  const R d = wc[0];
+  const R a = sqrt(R(g.gamma) * wc[4] / d);
+  R dL[5], dR[5], dC[5];
+  for (int q = 0; q < 5; ++q) {
+    dL[q] = wc[q] - wm[q];
+    dR[q] = wp[q] - wc[q];
+    dC[q] = R(0.5) * (wp[q] - wm[q]);
+  }
+  R xL[5], xR[5], xC[5], xi[5];
+  project(dL, d, a, xL);
+  project(dR, d, a, xR);
+  project(dC, d, a, xC);
+  for (int q = 0; q < 5; ++q) {
+    if (xL[q] * xR[q] > R(0.0)) {
+      const R lim = mn(mn(fabs(xC[q]), R(2.0) * fabs(xL[q])), R(2.0) * fabs(xR[q]));
+      xi[q] = sgn(xC[q]) * lim;
+    } else {
+      xi[q] = R(0.0);
+    }
+  }
+  dw[0] = xi[0] + xi[1] + xi[4];
+  dw[1] = a / d * (-xi[0] + xi[4]);
+  dw[2] = xi[2];
+  dw[3] = xi[3];
+  dw[4] = a * a * (xi[0] + xi[4]);
+}
+
+// PPMC for cell i (App. A.3).  w[0..4] are the primitive states of cells
+// i-2..i+2 in rotated order; dtdx = dt/dx along the sweep.  Returns the
+// time-evolved left-face state W*_L and right-face state W*_R of cell i.
+template <class R>
+void ppmc_cell(const R w[5][5], R dtdx, const Gas& g, R WsL[5], R WsR[5]) {
+  R dwm[5], dwc[5], dwp[5];
+  plmc_slope(w[0], w[1], w[2], g, dwm);  // cell i-1
+  plmc_slope(w[1], w[2], w[3], g, dwc);  // cell i
+  plmc_slope(w[2], w[3], w[4], g, dwp);  // cell i+1
+  const R* wim = w[1];
+  const R* wi = w[2];
+  const R* wip = w[3];
+
+  R WL[5], WR[5], dw[5], w6[5];
+  for (int q = 0; q < 5; ++q) {
+    // parabolic interpolation (Eq. parabolic_interpolation)
+    R L = R(0.5) * (wi[q] + wim[q]) - (dwc[q] - dwm[q]) / R(6.0);
+    R Rr = R(0.5) * (wip[q] + wi[q]) - (dwp[q] - dwc[q]) / R(6.0);
+    // local extremum (Eq. max_min)
+    if ((Rr - wi[q]) * (wi[q] - L) <= R(0.0)) { L = wi[q]; Rr = wi[q]; }
+    // steep gradients (Eq. steep_gradient), in the printed order
+    if ((Rr - L) * (L - (R(3.0) * wi[q] - R(2.0) * Rr)) < R(0.0)) L = R(3.0) * wi[q] - R(2.0) * Rr;
+    if ((Rr - L) * ((R(3.0) * wi[q] - R(2.0) * L) - Rr) < R(0.0)) Rr = R(3.0) * wi[q] - R(2.0) * L;
+    // bound by the neighbouring averages
+    L = mn(mx(wi[q], wim[q]), mx(mn(wi[q], wim[q]), L));
+    Rr = mn(mx(wi[q], wip[q]), mx(mn(wi[q], wip[q]), Rr));
+    WL[q] = L;
+    WR[q] = Rr;
+    dw[q] = Rr - L;
+    w6[q] = R(6.0) * wi[q] - R(3.0) * (L + Rr);
+  }
+
+  // characteristic speeds of cell i and the CW84 Courant fractions
+  const R d = wi[0];
+  const R a = sqrt(R(g.gamma) * wi[4] / d);
+  const R u = wi[1];
+  const R lm = u - a, l0 = u, lp = u + a;
+  const R am = dtdx * mn(lm, R(0.0)), a0 = dtdx * mn(l0, R(0.0)), ap = dtdx * mn(lp, R(0.0));
+  const R bm = dtdx * mx(lm, R(0.0)), b0 = dtdx * mx(l0, R(0.0)), bp = dtdx * mx(lp, R(0.0));
+  const R two3 = R(2.0 / 3.0);
+
+  R TL_m[5], TL_0[5], TL_p[5], TR_m[5], TR_0[5], TR_p[5];
+  for (int q = 0; q < 5; ++q) {
+    // integral under the parabola over the domain of dependence of each wave
+    TL_m[q] = R(0.5) * am * (dw[q] + w6[q] * (R(1.0) + two3 * am));
+    TL_0[q] = R(0.5) * a0 * (dw[q] + w6[q] * (R(1.0) + two3 * a0));
+    TL_p[q] = R(0.5) * ap * (dw[q] + w6[q] * (R(1.0) + two3 * ap));
+    TR_m[q] = R(0.5) * bm * (dw[q] - w6[q] * (R(1.0) - two3 * bm));
+    TR_0[q] = R(0.5) * b0 * (dw[q] - w6[q] * (R(1.0) - two3 * b0));
+    TR_p[q] = R(0.5) * bp * (dw[q] - w6[q] * (R(1.0) - two3 * bp));
+  }
+  R WtL[5], WtR[5], E[5], B[5], C[5], D[5];
+  for (int q = 0; q < 5; ++q) {
+    WtL[q] = WL[q] - TL_m[q];  // Eq. integration_PPMC
+    WtR[q] = WR[q] - TR_p[q];
+    E[q] = TL_m[q] - TL_0[q];
+    B[q] = TL_m[q] - TL_p[q];
+    C[q] = TR_p[q] - TR_m[q];
+    D[q] = TR_p[q] - TR_0[q];
+  }
+  const R a2 = a * a;
+  R sL[5] = {R(0.0), R(0.0), R(0.0), R(0.0), R(0.0)};
+  R sR[5] = {R(0.0), R(0.0), R(0.0), R(0.0), R(0.0)};
+  if (l0 < R(0.0)) {  // contact (and advected transverse velocities)
+    sL[0] = sL[0] + (E[0] - E[4] / a2);
+    sL[2] = sL[2] + E[2];
+    sL[3] = sL[3] + E[3];
+  }
+  if (lp < R(0.0)) {  // right-moving acoustic wave reaching the left face
+    sL[0] = sL[0] + R(0.5) * (d * B[1] / a + B[4] / a2);
+    sL[1] = sL[1] + R(0.5) * (B[1] + B[4] / (a * d));
+    sL[4] = sL[4] + R(0.5) * (d * B[1] * a + B[4]);
+  }
+  if (lm > R(0.0)) {  // left-moving acoustic wave reaching the right face
+    sR[0] = sR[0] + R(0.5) * (-(d * C[1]) / a + C[4] / a2);
+    sR[1] = sR[1] + R(0.5) * (C[1] - C[4] / (a * d));
+    sR[4] = sR[4] + R(0.5) * (-(d * C[1] * a) + C[4]);
+  }
+  if (l0 > R(0.0)) {  // contact (and advected transverse velocities)
+    sR[0] = sR[0] + (D[0] - D[4] / a2);
+    sR[2] = sR[2] + D[2];
+    sR[3] = sR[3] + D[3];
+  }
+  for (int q = 0; q < 5; ++q) {
+    WsL[q] = WtL[q] + sL[q];
+    WsR[q] = WtR[q] + sR[q];
+  }
+  WsL[4] = mx(WsL[4], R(P_FLOOR));
+  WsR[4] = mx(WsR[4], R(P_FLOOR));
+}
+
+// ---------------------------------------------------------------------------
+// Grid: conserved variables as five padded planes [5][N2][N1][N0], x fastest.
+template <class R>
+struct Grid {
+  int n[3], gh[3], N[3];
+  double dx, gamma;
+  int bc[6];
+  double inflow_prim[6][5];
+  size_t ncell;
+  std::vector<R> u;
+
+  Grid(const int nn[3], double dx_, double gamma_, const int bc_[6]) : dx(dx_), gamma(gamma_) {
+    for (int d = 0; d < 3; ++d) {
+      n[d] = nn[d];
+      gh[d] = (nn[d] > 1) ? NG : 0;
+      N[d] = n[d] + 2 * gh[d];
+    }
+    for (int f = 0; f < 6; ++f) {
+      bc[f] = bc_[f];
+      for (int q = 0; q < 5; ++q) inflow_prim[f][q] = 0.0;
+    }
+    ncell = (size_t)N[0] * N[1] * N[2];
+    u.assign(5 * ncell, R(0.0));
+  }
+  size_t idx(int i, int j, int k) const { return ((size_t)k * N[1] + j) * N[0] + i; }
+  size_t stride(int d) const { return d == 0 ? 1 : (d == 1 ? (size_t)N[0] : (size_t)N[0] * N[1]); }
+};
+
+template <class R>
+void fill_ghosts(Grid<R>& G) {
+  const Gas g(G.gamma);
+  for (int d = 0; d < 3; ++d) {
+    if (G.gh[d] == 0) continue;
+    // ranges: axes filled earlier cover their full padded range, later axes only real
+    int lo[3], hi[3];
+    for (int t = 0; t < 3; ++t) {
+      if (t < d) { lo[t] = 0; hi[t] = G.N[t]; }
+      else { lo[t] = G.gh[t]; hi[t] = G.gh[t] + G.n[t]; }
+    }
+    for (int side = 0; side < 2; ++side) {
+      const int type = G.bc[2 * d + side];
+      double Uin[5] = {0, 0, 0, 0, 0};
+      if (type == BC_INFLOW) {
+        const double* W = G.inflow_prim[2 * d + side];
+        Uin[0] = W[0]; Uin[1] = W[0] * W[1]; Uin[2] = W[0] * W[2]; Uin[3] = W[0] * W[3];
+        Uin[4] = W[4] / (G.gamma - 1.0) + 0.5 * W[0] * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+      }
+      for (int gd = 1; gd <= G.gh[d]; ++gd) {
+        const int tgt = side == 0 ? G.gh[d] - gd : G.gh[d] + G.n[d] - 1 + gd;
+        int src = 0;
+        switch (type) {
+          case BC_PERIODIC: src = side == 0 ? G.gh[d] + G.n[d] - gd : G.gh[d] + gd - 1; break;
+          case BC_REFLECT: src = side == 0 ? G.gh[d] + gd - 1 : G.gh[d] + G.n[d] - gd; break;
+          case BC_OUTFLOW: src = side == 0 ? G.gh[d] : G.gh[d] + G.n[d] - 1; break;
+          default: src = -1; break;
+        }
+        int c[3];
+        for (c[2] = (d == 2 ? 0 : lo[2]); c[2] < (d == 2 ? 1 : hi[2]); ++c[2])
+          for (c[1] = (d == 1 ? 0 : lo[1]); c[1] < (d == 1 ? 1 : hi[1]); ++c[1])
+            for (c[0] = (d == 0 ? 0 : lo[0]); c[0] < (d == 0 ? 1 : hi[0]); ++c[0]) {
+              int ct[3] = {c[0], c[1], c[2]}, cs[3] = {c[0], c[1], c[2]};
+              ct[d] = tgt;
+              cs[d] = src;
+              const size_t it = G.idx(ct[0], ct[1], ct[2]);
+              for (int q = 0; q < 5; ++q) {
+                if (type == BC_INFLOW) {
+                  G.u[q * G.ncell + it] = R(Uin[q]);
+                } else {
+                  const size_t is = G.idx(cs[0], cs[1], cs[2]);
+                  R val_ = G.u[q * G.ncell + is];
+                  if (type == BC_REFLECT && q == 1 + d) val_ = -val_;
+                  G.u[q * G.ncell + it] = val_;
+                }
+              }
+            }
+      }
+    }
+  }
+  (void)g;
+}
+
+template <class R>
+R compute_dt_min(const Grid<R>& G) {
+  const Gas g(G.gamma);
+  double best = std::numeric_limits<double>::infinity();
+  R bestR = R(best);
+  for (int k = G.gh[2]; k < G.gh[2] + G.n[2]; ++k)
+    for (int j = G.gh[1]; j < G.gh[1] + G.n[1]; ++j)
+      for (int i = G.gh[0]; i < G.gh[0] + G.n[0]; ++i) {
+        const size_t c = G.idx(i, j, k);
+        R U[5], W[5];
+        for (int q = 0; q < 5; ++q) U[q] = G.u[q * G.ncell + c];
+        cons_to_prim(U, g, W);
+        const R a = sqrt(R(g.gamma) * W[4] / W[0]);
+        for (int d = 0; d < 3; ++d) {
+          if (G.n[d] <= 1) continue;
+          const R t = R(G.dx) / (fabs(W[1 + d]) + a);
+          if (t < bestR) bestR = t;
+        }
+      }
+  return bestR;
+}
+
+// One CTU step with a given dt (Sec. 2.3 steps 1-5).  Returns status flags.
+template <class R>
+int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
+  const Gas g(G.gamma);
+  const size_t nc = G.ncell;
+  const R dt = R(dt_in);
+  const R dtdx = dt / R(G.dx);
+  const R hdtdx = R(0.5) * dtdx;
+  int flags = 0;
+
+  fill_ghosts(G);
+
+  // cell-average primitives (global order) of every padded cell
+  std::vector<R> W(5 * nc);
+#pragma omp parallel for if (threaded) schedule(static)
+  for (long c = 0; c < (long)nc; ++c) {
+    R U[5], Wc[5];
+    for (int q = 0; q < 5; ++q) U[q] = G.u[q * nc + c];
+    cons_to_prim(U, g, Wc);
+    for (int q = 0; q < 5; ++q) W[q * nc + c] = Wc[q];
+  }
+
+  bool active[3];
+  for (int d = 0; d < 3; ++d) active[d] = G.n[d] > 1;
+
+  // face arrays, indexed by the padded index of the cell right of the face
+  std::vector<R> UL[3], UR[3], F1[3], F2[3];
+  for (int d = 0; d < 3; ++d) {
+    if (!active[d]) continue;
+    UL[d].assign(5 * nc, R(0.0));
+    UR[d].assign(5 * nc, R(0.0));
+    F1[d].assign(5 * nc, R(0.0));
+    F2[d].assign(5 * nc, R(0.0));
+  }
+
+  // steps 1-2: reconstruction (PPMC with characteristic tracing) and the first
+  // set of Riemann solves, one axis at a time
+  for (int d = 0; d < 3; ++d) {
+    if (!active[d]) continue;
+    const size_t sd = G.stride(d);
+    const int* P = PERM[d];
+#pragma omp parallel for if (threaded) schedule(static)
+    for (int k = 0; k < G.N[2]; ++k)
+      for (int j = 0; j < G.N[1]; ++j)
+        for (int i = 0; i < G.N[0]; ++i) {
+          const int c3[3] = {i, j, k};
+          if (c3[d] < 2 || c3[d] > G.N[d] - 3) continue;
+          const size_t c = G.idx(i, j, k);
+          R w[5][5];
+          for (int s = 0; s < 5; ++s) {
+            const size_t cs = c + (size_t)((long)(s - 2) * (long)sd);
+            w[s][0] = W[0 * nc + cs];
+            w[s][1] = W[(1 + P[0]) * nc + cs];
+            w[s][2] = W[(1 + P[1]) * nc + cs];
+            w[s][3] = W[(1 + P[2]) * nc + cs];
+            w[s][4] = W[4 * nc + cs];
+          }
+          R WsL[5], WsR[5], UsL[5], UsR[5];
+          ppmc_cell(w, dtdx, g, WsL, WsR);
+          prim_to_cons(WsL, g, UsL);
+          prim_to_cons(WsR, g, UsR);
+          // left face of cell i is the right state of face i-1/2; right face of
+          // cell i is the left state of face i+1/2
+          const size_t cr = c + sd;
+          UR[d][0 * nc + c] = UsL[0];
+          UR[d][4 * nc + c] = UsL[4];
+          UL[d][0 * nc + cr] = UsR[0];
+          UL[d][4 * nc + cr] = UsR[4];
+          for (int s = 0; s < 3; ++s) {
+            UR[d][(1 + P[s]) * nc + c] = UsL[1 + s];
+            UL[d][(1 + P[s]) * nc + cr] = UsR[1 + s];
+          }
+        }
+    int fl = 0;
+#pragma omp parallel for if (threaded) schedule(static) reduction(| : fl)
+    for (int k = 0; k < G.N[2]; ++k)
+      for (int j = 0; j < G.N[1]; ++j)
+        for (int i = 0; i < G.N[0]; ++i) {
+          const int c3[3] = {i, j, k};
+          if (c3[d] < 3 || c3[d] > G.N[d] - 3) continue;
+          const size_t f = G.idx(i, j, k);
+          R ULr[5], URr[5], Fr[5];
+          ULr[0] = UL[d][0 * nc + f]; URr[0] = UR[d][0 * nc + f];
+          ULr[4] = UL[d][4 * nc + f]; URr[4] = UR[d][4 * nc + f];
+          for (int s = 0; s < 3; ++s) {
+            ULr[1 + s] = UL[d][(1 + P[s]) * nc + f];
+            URr[1 + s] = UR[d][(1 + P[s]) * nc + f];
+          }
+          fl |= riemann_exact_cons(ULr, URr, g, Fr);
+          F1[d][0 * nc + f] = Fr[0];
+          F1[d][4 * nc + f] = Fr[4];
+          for (int s = 0; s < 3; ++s) F1[d][(1 + P[s]) * nc + f] = Fr[1 + s];
+        }
+    flags |= fl;
+  }
+
+  // steps 3-4: transverse half-step (Eq. transverse_evolution) and the second
+  // set of Riemann solves
+  for (int d = 0; d < 3; ++d) {
+    if (!active[d]) continue;
+    const size_t sd = G.stride(d);
+    const int* P = PERM[d];
+    const int t1 = P[1], t2 = P[2];  // transverse axes in cyclic order
+    int fl = 0;
+#pragma omp parallel for if (threaded) schedule(static) reduction(| : fl)
+    for (int k = 0; k < G.N[2]; ++k)
+      for (int j = 0; j < G.N[1]; ++j)
+        for (int i = 0; i < G.N[0]; ++i) {
+          const int c3[3] = {i, j, k};
+          if (c3[d] < 3 || c3[d] > G.N[d] - 3) continue;
+          bool ok = true;
+          for (int t = 0; t < 3; ++t)
+            if (t != d && active[t] && (c3[t] < 3 || c3[t] > G.N[t] - 4)) ok = false;
+          if (!ok) continue;
+          const size_t f = G.idx(i, j, k);
+          const size_t cl = f - sd;  // cell left of the face
+          const size_t cr = f;       // cell right of the face
+          R UhL[5], UhR[5];
+          for (int q = 0; q < 5; ++q) {
+            UhL[q] = UL[d][q * nc + f];
+            UhR[q] = UR[d][q * nc + f];
+          }
+          const int tt[2] = {t1, t2};
+          for (int m = 0; m < 2; ++m) {
+            const int t = tt[m];
+            if (!active[t]) continue;
+            const size_t st = G.stride(t);
+            for (int q = 0; q < 5; ++q) {
+              UhL[q] = UhL[q] + hdtdx * (F1[t][q * nc + cl] - F1[t][q * nc + cl + st]);
+              UhR[q] = UhR[q] + hdtdx * (F1[t][q * nc + cr] - F1[t][q * nc + cr + st]);
+            }
+          }
+          R ULr[5], URr[5], Fr[5];
+          ULr[0] = UhL[0]; URr[0] = UhR[0];
+          ULr[4] = UhL[4]; URr[4] = UhR[4];
+          for (int s = 0; s < 3; ++s) {
+            ULr[1 + s] = UhL[1 + P[s]];
+            URr[1 + s] = UhR[1 + P[s]];
+          }
+          fl |= riemann_exact_cons(ULr, URr, g, Fr);
+          F2[d][0 * nc + f] = Fr[0];
+          F2[d][4 * nc + f] = Fr[4];
+          for (int s = 0; s < 3; ++s) F2[d][(1 + P[s]) * nc + f] = Fr[1 + s];
+        }
+    flags |= fl;
+  }
+
+  // step 5: conserved update of the real cells (Eq. conserved_update)
+  int fl = 0;
+#pragma omp parallel for if (threaded) schedule(static) reduction(| : fl)
+  for (int k = G.gh[2]; k < G.gh[2] + G.n[2]; ++k)
+    for (int j = G.gh[1]; j < G.gh[1] + G.n[1]; ++j)
+      for (int i = G.gh[0]; i < G.gh[0] + G.n[0]; ++i) {
+        const size_t c = G.idx(i, j, k);
+        for (int q = 0; q < 5; ++q) {
+          R un = G.u[q * nc + c];
+          for (int d = 0; d < 3; ++d) {
+            if (!active[d]) continue;
+            const size_t sd = G.stride(d);
+            un = un + dtdx * (F2[d][q * nc + c] - F2[d][q * nc + c + sd]);
+          }
+          G.u[q * nc + c] = un;
+          if (std::isnan(val(un))) fl |= FLAG_NONPHYS;
+        }
+        if (!(val(G.u[c]) > 0.0)) fl |= FLAG_NONPHYS;
+      }
+  flags |= fl;
+  return flags;
+}
+
+struct Handle {
+  Grid<double> G;
+  Handle(const int n[3], double dx, double gamma, const int bc[6]) : G(n, dx, gamma, bc) {}
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C interface used by the tests (ctypes).  Conserved state layout for set/get:
+// five planes [5][nz][ny][nx] of real cells, x fastest.
+extern "C" {
+
+void* oracle_init(int nx, int ny, int nz, double dx, double gamma, const int* bc) {
+  const int n[3] = {nx, ny, nz};
+  for (int d = 0; d < 3; ++d) {
+    if (n[d] < 1 || (n[d] > 1 && n[d] < NG)) return nullptr;
+    if (n[d] > 1 && ((bc[2 * d] == BC_PERIODIC) != (bc[2 * d + 1] == BC_PERIODIC))) return nullptr;
+  }
+  if (!(dx > 0.0) || !(gamma > 1.0)) return nullptr;
+  return new Handle(n, dx, gamma, bc);
+}
+
+void oracle_free(void* h) { delete static_cast<Handle*>(h); }
+
+int oracle_set_inflow(void* h, int face, const double* prim) {
+  if (!h || face < 0 || face > 5) return -1;
+  for (int q = 0; q < 5; ++q) static_cast<Handle*>(h)->G.inflow_prim[face][q] = prim[q];
+  return 0;
+}
+
+int oracle_set_state(void* h, const double* u) {
+  auto& G = static_cast<Handle*>(h)->G;
+  const size_t nreal = (size_t)G.n[0] * G.n[1] * G.n[2];
+  for (int q = 0; q < 5; ++q)
+    for (int k = 0; k < G.n[2]; ++k)
+      for (int j = 0; j < G.n[1]; ++j)
+        for (int i = 0; i < G.n[0]; ++i)
+          G.u[q * G.ncell + G.idx(i + G.gh[0], j + G.gh[1], k + G.gh[2])] =
+              u[q * nreal + ((size_t)k * G.n[1] + j) * G.n[0] + i];
+  return 0;
+}
+
+int oracle_get_state(void* h, double* u) {
+  auto& G = static_cast<Handle*>(h)->G;
+  const size_t nreal = (size_t)G.n[0] * G.n[1] * G.n[2];
+  for (int q = 0; q < 5; ++q)
+    for (int k = 0; k < G.n[2]; ++k)
+      for (int j = 0; j < G.n[1]; ++j)
+        for (int i = 0; i < G.n[0]; ++i)
+          u[q * nreal + ((size_t)k * G.n[1] + j) * G.n[0] + i] =
+              G.u[q * G.ncell + G.idx(i + G.gh[0], j + G.gh[1], k + G.gh[2])];
+  return 0;
+}
+
+double oracle_compute_dt(void* h, double cfl) {
+  return cfl * compute_dt_min(static_cast<Handle*>(h)->G);
+}
+
+int oracle_step_dt(void* h, double dt) { return ctu_step(static_cast<Handle*>(h)->G, dt, true); }
+
+// Padded conserved state after the ghost fill of the current state, for the
+// boundary tests: [5][N2][N1][N0] with N = n + 8 on active axes.
+int oracle_fill_ghosts(void* h, double* upad) {
+  auto& G = static_cast<Handle*>(h)->G;
+  fill_ghosts(G);
+  std::memcpy(upad, G.u.data(), sizeof(double) * 5 * G.ncell);
+  return 0;
+}
+
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
+// Exact Riemann solver on n primitive state pairs (rotated order, [n][5] each).
+int oracle_riemann_prim(int n, const double* WL, const double* WR, double gamma, double* F,
+                        double* pm, double* um, double* ws, int* iters) {
+  const Gas g(gamma);
+  int flags = 0;
+  for (int i = 0; i < n; ++i) {
+    RiemannResult<double> r;
+    riemann_exact_prim(WL + 5 * i, WR + 5 * i, g, r);
+    for (int q = 0; q < 5; ++q) {
+      if (F) F[5 * i + q] = r.F[q];
+      if (ws) ws[5 * i + q] = r.ws[q];
+    }
+    if (pm) pm[i] = r.pm;
+    if (um) um[i] = r.um;
+    if (iters) iters[i] = r.iters;
+    flags |= r.flags;
+  }
+  return flags;
+}
+
+// Exact Riemann solver on n conserved state pairs (rotated order, [n][5] each),
+// as the CTU step calls it (conversion to primitives with the pressure floor).
+int oracle_riemann_cons(int n, const double* UL, const double* UR, double gamma, double* F) {
+  const Gas g(gamma);
+  int flags = 0;
+  for (int i = 0; i < n; ++i) flags |= riemann_exact_cons(UL + 5 * i, UR + 5 * i, g, F + 5 * i);
+  return flags;
+}
+
+// PPMC on n five-cell stencils w[n][5 cells][5 prims] (rotated order).
+int oracle_ppmc(int n, const double* w, double dtdx, double gamma, double* WsL, double* WsR) {
+  const Gas g(gamma);
+  for (int i = 0; i < n; ++i) {
+    double st[5][5];
+    for (int s = 0; s < 5; ++s)
+      for (int q = 0; q < 5; ++q) st[s][q] = w[25 * i + 5 * s + q];
+    ppmc_cell(st, dtdx, g, WsL + 5 * i, WsR + 5 * i);
+  }
+  return 0;
+}
+
+// Algorithmic operation count of one CTU step with the given dt on the current
+// state (the state itself is not changed).  counts = {add/sub, mul, div, sqrt,
+// pow, compare/min/max/abs}; returns the step's status flags.
+int oracle_count_step(void* h, double dt, double* counts) {
+  const auto& G0 = static_cast<Handle*>(h)->G;
+  Grid<CR> G(G0.n, G0.dx, G0.gamma, G0.bc);
+  for (int f = 0; f < 6; ++f)
+    for (int q = 0; q < 5; ++q) G.inflow_prim[f][q] = G0.inflow_prim[f][q];
+  for (size_t i = 0; i < G0.u.size(); ++i) G.u[i] = CR(G0.u[i]);
+  g_ops = OpCount();
+  const int fl = ctu_step(G, dt, false);
+  counts[0] = (double)g_ops.add;
+  counts[1] = (double)g_ops.mul;
+  counts[2] = (double)g_ops.div;
+  counts[3] = (double)g_ops.sqrt;
+  counts[4] = (double)g_ops.pow;
+  counts[5] = (double)g_ops.cmp;
+  return fl;
+}
+
+}  // extern "C"

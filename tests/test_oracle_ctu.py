@@ -1,0 +1,219 @@
+"""Pins of the oracle's full CTU step (Sec. 2.3) and boundary fill (Sec. 3.1).
+
+  * a uniform state is preserved exactly (periodic, outflow, reflective at rest);
+  * totals of mass, momentum and energy are conserved to rounding on periodic
+    boxes (Eq. conserved_update telescopes);
+  * mirror and cyclic axis-permutation symmetry on small 3D grids;
+  * Sod shock tube (config: 512 cells, t = 0.2): converges to the exact Riemann
+    solution (sampled with the exact solver, pinned separately by Toro's values);
+  * smooth advection converges at second order or better (paper Sec. 4.1: the
+    method is second-order for smooth flow);
+  * Sedov-Taylor blast: shock radius follows R = xi0 (E t^2 / rho)^(1/5) with
+    xi0 = 1.152 for gamma = 5/3 (Sedov 1959), peak density below the strong
+    shock limit (gamma+1)/(gamma-1);
+  * ghost cells: periodic wrap, reflective mirror with negated normal
+    momentum, outflow copy, inflow state; corners filled x, then y, then z.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_4194_gb300 import workloads as W
+from tests.helpers import mirror_x, rotate_xyz
+
+P, R_, O, I_ = 0, 1, 2, 3
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _threads():
+    oracle.set_threads(0)
+    yield
+
+
+def uniform_state(shape, rho, v, p, gamma):
+    nz, ny, nx = shape
+    return W.prim_to_cons(np.full(shape, rho), v[0], v[1], v[2], np.full(shape, p), gamma)
+
+
+@pytest.mark.parametrize("shape,bc,v", [
+    ((8, 8, 8), [P] * 6, (0.3, -0.2, 0.1)),
+    ((1, 1, 32), [O, O, P, P, P, P], (0.5, 0.0, 0.0)),
+    ((6, 7, 8), [R_] * 6, (0.0, 0.0, 0.0)),
+    ((1, 12, 10), [O, O, P, P, P, P], (0.2, 0.4, 0.0)),
+])
+def test_uniform_state_preserved_exactly(shape, bc, v):
+    u0 = uniform_state(shape, 1.3, v, 0.7, 1.4)
+    u, t, n, fl = oracle.run(u0, 0.1, 1.4, bc, nsteps=3, cfl=0.4)
+    assert fl == 0
+    assert np.array_equal(u, u0)
+
+
+@pytest.mark.parametrize("shape", [(12, 12, 12), (1, 16, 16), (1, 1, 64), (6, 10, 8)])
+def test_conservation_periodic(shape):
+    u0 = W.smooth_periodic(shape, gamma=1.4, seed=21)
+    tot0 = u0.reshape(5, -1).sum(axis=1)
+    scale = np.abs(u0).reshape(5, -1).sum(axis=1)
+    u, t, n, fl = oracle.run(u0, 1.0 / max(shape), 1.4, [P] * 6, nsteps=6, cfl=0.4)
+    assert fl == 0
+    tot = u.reshape(5, -1).sum(axis=1)
+    assert np.all(np.abs(tot - tot0) <= 1e-13 * scale + 1e-15), (tot - tot0) / scale
+    assert not np.array_equal(u, u0)  # the state did evolve
+
+
+def test_mirror_symmetry_3d():
+    shape = (8, 10, 12)
+    u0 = W.smooth_periodic(shape, gamma=1.4, seed=5, vamp=0.8)
+    bc = [R_, R_, P, P, O, O]
+    ua, *_ = oracle.run(u0, 0.1, 1.4, bc, nsteps=4, cfl=0.4)
+    ub, *_ = oracle.run(mirror_x(u0), 0.1, 1.4, bc, nsteps=4, cfl=0.4)
+    scale = np.abs(ua).reshape(5, -1).max(axis=1)[:, None, None, None]
+    assert np.all(np.abs(mirror_x(ub) - ua) <= 1e-12 * scale)
+
+
+def test_axis_permutation_symmetry_3d():
+    shape = (8, 8, 8)
+    u0 = W.smooth_periodic(shape, gamma=1.4, seed=6, vamp=0.8)
+    ua, *_ = oracle.run(u0, 0.1, 1.4, [P] * 6, nsteps=4, cfl=0.4)
+    ub, *_ = oracle.run(rotate_xyz(u0), 0.1, 1.4, [P] * 6, nsteps=4, cfl=0.4)
+    scale = np.abs(ua).reshape(5, -1).max(axis=1)[:, None, None, None]
+    assert np.all(np.abs(ub - rotate_xyz(ua)) <= 1e-12 * scale)
+
+
+def exact_riemann_profile(x, t, x0, left, right, gamma):
+    """Exact solution of a 1D Riemann problem at time t, through the exact
+    solver's interface sampler and a Galilean shift per point."""
+    n = len(x)
+    S = (x - x0) / t
+    WL = np.tile([left[0], left[1], 0.0, 0.0, left[2]], (n, 1))
+    WR = np.tile([right[0], right[1], 0.0, 0.0, right[2]], (n, 1))
+    WL[:, 1] -= S
+    WR[:, 1] -= S
+    r = oracle.riemann_prim(WL, WR, gamma)
+    ws = r["ws"]
+    return ws[:, 0], ws[:, 1] + S, ws[:, 4]
+
+
+def sod_l1(nx):
+    w = W.sod(nx)
+    u, t, n, fl = oracle.run(w["u"], w["dx"], w["gamma"], w["bc"], t_end=0.2, cfl=0.3)
+    assert fl == 0 and t == 0.2
+    x = (np.arange(nx) + 0.5) / nx
+    rho_e, v_e, p_e = exact_riemann_profile(x, 0.2, 0.5, (1, 0, 1), (0.125, 0, 0.1), 1.4)
+    rho = u[0, 0, 0]
+    return np.mean(np.abs(rho - rho_e)), u, rho_e
+
+
+def test_sod_converges_to_exact_solution():
+    e1, _, _ = sod_l1(128)
+    e2, _, _ = sod_l1(256)
+    e3, u, rho_e = sod_l1(512)
+    assert e2 < e1 and e3 < e2
+    assert e1 / e3 > 2.5  # at least ~first order overall across the discontinuities
+    assert e3 < 3e-3
+    rho = u[0, 0, 0]
+    # plateau values away from the waves: star-left and star-right densities
+    x = (np.arange(512) + 0.5) / 512
+    mid_l = (x > 0.62) & (x < 0.66)  # between rarefaction tail and contact
+    mid_r = (x > 0.72) & (x < 0.82)  # between contact and shock
+    np.testing.assert_allclose(rho[mid_l], 0.42632, rtol=2e-3)
+    np.testing.assert_allclose(rho[mid_r], 0.26557, rtol=2e-3)
+    # total mass in the box is conserved until waves reach the ends
+    assert abs(u[0].sum() / 512 - (0.5 * 1 + 0.5 * 0.125)) < 1e-13
+
+
+def test_smooth_advection_second_order():
+    errs = []
+    for n in (32, 64, 128):
+        x = (np.arange(n) + 0.5) / n
+        rho = 1.0 + 0.2 * np.sin(2 * np.pi * x)
+        u0 = W.prim_to_cons(rho.reshape(1, 1, n), 1.0, 0.0, 0.0, 1.0, 1.4)
+        u, t, _, fl = oracle.run(u0, 1.0 / n, 1.4, [P] * 6, t_end=1.0, cfl=0.4)
+        assert fl == 0
+        errs.append(np.mean(np.abs(u[0, 0, 0] - rho)))
+    order = np.log2(errs[1] / errs[2])
+    assert order > 1.8, errs
+
+
+@pytest.mark.slow
+def test_sedov_radius_and_symmetry():
+    n = 32
+    w = W.sedov(n)
+    g = oracle.Grid(n, n, n, w["dx"], w["gamma"], w["bc"])
+    g.set_state(w["u"])
+    t = 0.0
+    t_check = 0.04
+    while t < t_check:
+        dt = min(g.compute_dt(0.3), t_check - t)
+        assert g.step_dt(dt) == 0
+        t += dt
+    u = g.get_state()
+    rho = u[0]
+    gamma = w["gamma"]
+    assert rho.max() < (gamma + 1) / (gamma - 1)
+    # shock radius: outermost radius where the spherically binned density
+    # exceeds half of its peak excess
+    c = (np.arange(n) + 0.5) / n - 0.5
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    bins = np.linspace(0, 0.5, 41)
+    idx = np.digitize(r.ravel(), bins)
+    prof = np.array([rho.ravel()[idx == k].mean() if np.any(idx == k) else 1.0
+                     for k in range(1, len(bins))])
+    rc = 0.5 * (bins[1:] + bins[:-1])
+    kpk = int(np.argmax(prof))
+    half = 1.0 + 0.5 * (prof[kpk] - 1.0)
+    k = kpk
+    while k + 1 < len(prof) and prof[k + 1] > half:
+        k += 1
+    r_shock = rc[k]
+    r_exact = 1.152 * (1.0 * t * t / 1.0) ** 0.2
+    assert abs(r_shock - r_exact) / r_exact < 0.12, (r_shock, r_exact)
+    # symmetry of the blast under the 48 cube symmetries, spot-checked
+    scale = np.abs(rho).max()
+    assert np.max(np.abs(rho - rho[::-1, :, :])) < 1e-12 * scale
+    assert np.max(np.abs(rho - rho[:, ::-1, :])) < 1e-12 * scale
+    assert np.max(np.abs(rho - rho[:, :, ::-1])) < 1e-12 * scale
+    assert np.max(np.abs(rho - np.transpose(rho, (1, 2, 0)))) < 1e-12 * scale
+    assert np.max(np.abs(rho - np.transpose(rho, (0, 2, 1)))) < 1e-12 * scale
+
+
+def test_ghost_fill_rules():
+    nx, ny, nz = 6, 5, 4
+    rng = np.random.Generator(np.random.PCG64(2))
+    u0 = np.zeros((5, nz, ny, nx))
+    u0[0] = 1.0 + rng.random((nz, ny, nx))
+    u0[1:4] = rng.normal(size=(3, nz, ny, nx))
+    u0[4] = 5.0 + rng.random((nz, ny, nx))
+    g = oracle.Grid(nx, ny, nz, 0.1, 1.4, [P, P, R_, O, I_, O])
+    inflow = (2.0, 0.5, -0.25, 0.75, 3.0)
+    g.set_inflow(4, inflow)
+    g.set_state(u0)
+    up = g.padded_after_ghost_fill()
+    G = 4
+    real = up[:, G:G + nz, G:G + ny, G:G + nx]
+    assert np.array_equal(real, u0)
+    # x periodic: ghost i = -d copies real nx - d
+    for d in range(1, G + 1):
+        np.testing.assert_array_equal(up[:, G:G + nz, G:G + ny, G - d], u0[:, :, :, nx - d])
+        np.testing.assert_array_equal(up[:, G:G + nz, G:G + ny, G + nx - 1 + d], u0[:, :, :, d - 1])
+    # y- reflective: ghost j = -d mirrors real d-1 with negated y momentum
+    for d in range(1, G + 1):
+        got = up[:, G:G + nz, G - d, G:G + nx]
+        exp = u0[:, :, d - 1, :].copy()
+        exp[2] = -exp[2]
+        np.testing.assert_array_equal(got, exp)
+    # y+ outflow: every ghost copies the last real row
+    for d in range(1, G + 1):
+        np.testing.assert_array_equal(up[:, G:G + nz, G + ny - 1 + d, G:G + nx], u0[:, :, ny - 1, :])
+    # z- inflow: the prescribed state everywhere in the ghost slab, corners included
+    rho, vx, vy, vz, p = inflow
+    E = p / (1.4 - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz)
+    for q, val in enumerate((rho, rho * vx, rho * vy, rho * vz, E)):
+        assert np.all(up[q, :G] == val)
+    # z+ outflow copies the last real plane including its x/y ghosts (corners)
+    for d in range(1, G + 1):
+        np.testing.assert_array_equal(up[:, G + nz - 1 + d], up[:, G + nz - 1])
+    # an x-y corner ghost equals the y rule applied to the x-filled ghost column
+    exp = up[:, G:G + nz, G, G - 1].copy()  # x-ghost of the first real row
+    exp[2] = -exp[2]
+    np.testing.assert_array_equal(up[:, G:G + nz, G - 1, G - 1], exp)

@@ -1,0 +1,158 @@
+/*
+ * hydro.h -- C-ABI of the GB300 CTU + PPMC + exact-Riemann hydrodynamics library.
+ *
+ * One call of hydro_step() advances the 3D Euler equations of an ideal gas
+ * (Schneider & Robertson, "Cholla", Sec. 2.1, Eqs. mass_cons ... energy_cons)
+ * by one unsplit six-solve Corner Transport Upwind step on a static Cartesian
+ * mesh (Sec. 2.3): ghost cells from the boundary conditions (Sec. 3.1), the
+ * CFL time step (Eq. calc_dt_3D), PPMC reconstruction with characteristic
+ * tracing per axis (App. A.3), the exact Riemann solver (App. B.1), the
+ * transverse half-step (Eq. transverse_evolution), a second set of exact
+ * Riemann solves and the conserved update (Eq. conserved_update).
+ *
+ * Conventions for every function below:
+ *  - Conserved state arrays are five planes [5][nz][ny][nx] of float64 real
+ *    cells, x fastest: rho, rho*u, rho*v, rho*w, E (Sec. 2.1, Eq.
+ *    conserved_variables).  There are no ghost cells in caller-visible arrays.
+ *  - Cells are cubic (dx = dy = dz).  An axis with one cell is inactive: no
+ *    ghost cells, no sweep and no transverse term, so the step reduces to 2D or
+ *    1D CTU (Sec. 2.3).  Active axes need at least 4 cells.
+ *  - Functions returning int return HYDRO_OK (0) or a negative HYDRO_E* code.
+ *    Functions returning double return a value >= 0 on success and a negative
+ *    value on error; hydro_last_error() then gives the code.  No function
+ *    aborts, traps or waits on the device without a bound.
+ *  - The library owns all device memory it allocates (hydro_init .. hydro_free).
+ *    Buffers passed by the caller stay owned by the caller; the library copies
+ *    from or into them, in order on the handle's stream, and returns only when
+ *    the copy has completed.
+ *  - Device pointers are plain CUDA device addresses in the current context;
+ *    streams are cudaStream_t values passed as void*.  No torch types appear in
+ *    this interface.
+ *  - A handle must not be used from two host threads at the same time.
+ */
+#ifndef HYDRO_H
+#define HYDRO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hydro_s* hydro_t;
+
+/* Boundary condition of one face (Sec. 3.1): periodic wrap; reflective (mirror
+ * copy, normal momentum negated); transmissive/outflow (every ghost copies the
+ * outermost real cell); inflow (every ghost holds a prescribed state).  Both
+ * faces of an axis must be periodic or neither. */
+enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_REFLECT = 1, HYDRO_BC_OUTFLOW = 2, HYDRO_BC_INFLOW = 3 };
+
+/* Arithmetic of the step.  HYDRO_FP64: every operation in float64.
+ * HYDRO_MIXED: reconstruction and Riemann solves in float32; the conserved
+ * update (flux accumulation), the recovery of the internal energy from E minus
+ * the kinetic energy, the positivity floors and the time step stay float64. */
+enum { HYDRO_FP64 = 0, HYDRO_MIXED = 1 };
+
+enum {
+  HYDRO_OK = 0,
+  HYDRO_EINVAL = -1,    /* invalid argument (sizes, bc, gamma, dx, null pointer, face) */
+  HYDRO_ENOMEM = -2,    /* device or host allocation failed */
+  HYDRO_ECUDA = -3,     /* a CUDA runtime call failed (see hydro_cuda_error_string) */
+  HYDRO_ENONPHYS = -4,  /* after a step some real cell has rho <= 0 or a NaN */
+  HYDRO_ENEWTON = -5,   /* a Riemann solve reached the 50-iteration Newton cap */
+  HYDRO_ENOSTATE = -6   /* a step or dt was requested before hydro_set_state */
+};
+
+/* Create a grid of nx*ny*nz real cells of width dx for an ideal gas of index
+ * gamma (> 1).  bc[6] lists the faces x-, x+, y-, y+, z-, z+.  Allocates all
+ * device memory the step needs (about 450 bytes per padded cell in float64).
+ * On success *out holds the handle; on error *out is NULL. */
+int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, const int bc[6]);
+
+/* Prescribed primitive state (rho, u, v, w, p) of an HYDRO_BC_INFLOW face
+ * (0..5 in the order of bc[]).  Host pointer, copied. */
+int hydro_set_inflow(hydro_t h, int face, const double prim[5]);
+
+/* Select HYDRO_FP64 (default) or HYDRO_MIXED for the following steps. */
+int hydro_set_precision(hydro_t h, int mode);
+
+/* Stream on which all following work of this handle is ordered (a
+ * cudaStream_t; NULL = the legacy default stream). */
+int hydro_set_stream(hydro_t h, void* stream);
+
+/* Copy a conserved state [5][nz][ny][nx] float64 into the handle.  u is a
+ * device pointer if on_device != 0, else a host pointer. */
+int hydro_set_state(hydro_t h, const double* u, int on_device);
+
+/* Copy the current conserved state out, same layout as hydro_set_state. */
+int hydro_get_state(hydro_t h, double* u, int on_device);
+
+/* Advance one CTU step with dt = cfl * min over real cells and active axes of
+ * dx/(|v_d| + a), a = sqrt(gamma p / rho) (Eq. calc_dt_3D; the paper requires
+ * cfl < 0.5 for the six-solve CTU).  Returns the dt used, or a negative value
+ * on error (then hydro_last_error() is HYDRO_ENONPHYS, HYDRO_ENEWTON, ...; the
+ * state is the result of the step even then). */
+double hydro_step(hydro_t h, double cfl);
+
+/* Advance one CTU step with a caller-chosen dt (> 0), e.g. to land exactly on a
+ * final time.  Returns dt, or a negative value on error. */
+double hydro_step_dt(hydro_t h, double dt);
+
+/* The dt that hydro_step(h, cfl) would use now, without changing the state. */
+double hydro_compute_dt(hydro_t h, double cfl);
+
+/* Code of the last error on this handle (HYDRO_OK if the last call succeeded). */
+int hydro_last_error(hydro_t h);
+
+/* Static description of a HYDRO_E* code. */
+const char* hydro_error_string(int code);
+
+/* Text of the last CUDA runtime error seen by this handle ("" if none). */
+const char* hydro_cuda_error_string(hydro_t h);
+
+/* ---- tracing -----------------------------------------------------------------
+ * Stages of a step, in launch order: 0 ghost remap + primitives (+ dt minimum),
+ * 1 dt, 2 limited slopes (per axis), 3 PPMC face states (per axis), 4 first
+ * Riemann fluxes (per axis), 5 transverse half-step + CTU fluxes (per axis),
+ * 6 conserved update.  The paper times the GPU hydro step as a whole (Sec.
+ * 3.5.3); this adds the per-stage split. */
+#define HYDRO_NUM_STAGES 7
+
+/* Enable (1) or disable (0) per-stage timing: each kernel launch of a step is
+ * bracketed by CUDA events on the handle's stream.  Either call resets the
+ * accumulated totals and the launch counter. */
+int hydro_profile(hydro_t h, int enable);
+
+/* Totals since the last hydro_profile() call, for the first nstages stages
+ * (<= HYDRO_NUM_STAGES): device milliseconds, number of launches and number of
+ * cells or faces processed, per stage; plus the total number of kernel launches
+ * (counted whether or not timing is enabled).  Any output pointer may be NULL. */
+int hydro_profile_read(hydro_t h, int nstages, double* ms, long long* launches, long long* units,
+                       long long* launches_total);
+
+/* Release the handle and all device memory it owns.  NULL is accepted. */
+void hydro_free(hydro_t h);
+
+/* ---- building blocks of the step, exposed on device arrays ------------------
+ * Both read and write device memory laid out as structure-of-arrays planes of
+ * n entries each, enqueue on `stream` and return after the launch has been
+ * enqueued (they do not wait for completion). */
+
+/* Exact Riemann solver (App. B.1) on n interfaces.  UL, UR: conserved states
+ * [5][n] in sweep order (rho, normal momentum, two transverse momenta, E); the
+ * pressure derived from them is floored at 1e-20.  F: fluxes [5][n] in the same
+ * order.  flags: one int on the device, OR-ed with 1 when a solve hits the
+ * Newton cap. */
+int hydro_riemann_exact(int n, const double* UL, const double* UR, double gamma, double* F,
+                        int* flags, void* stream);
+
+/* PPMC reconstruction with characteristic tracing (App. A.3) of n cells.
+ * w: primitive stencils [5 cells][5 variables][n] (cells i-2..i+2; variables
+ * rho, normal velocity, two transverse velocities, p); dtdx = dt/dx.  WsL, WsR:
+ * the time-evolved primitive states [5][n] at the left and right face of cell i. */
+int hydro_ppmc(int n, const double* w, double dtdx, double gamma, double* WsL, double* WsR,
+               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYDRO_H */

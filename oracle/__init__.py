@@ -54,6 +54,7 @@ def lib():
         L.oracle_riemann_cons.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, _dp]
         L.oracle_ppmc.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp]
         L.oracle_count_step.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp]
+        L.oracle_count_step_stages.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp]
         _lib = L
     return _lib
 
@@ -167,6 +168,25 @@ class Grid:
         keys = ("add", "mul", "div", "sqrt", "pow", "cmp")
         out = {k: int(v) for k, v in zip(keys, c)}
         out["flags"] = fl
+        return out
+
+    STAGES = ("prims", "ppmc", "riemann1", "riemann2", "update", "slopes")
+
+    def count_step_stages(self, dt):
+        """Per-stage algorithmic operation counts of one step (state unchanged).
+
+        Returns {stage: {"ops": {kind: count}, "units": n}} for the stages
+        prims (incl. the dt minimum), ppmc (without slopes), riemann1,
+        riemann2 (incl. the transverse half-step), update and slopes.
+        """
+        c = np.zeros(36)
+        u = np.zeros(6)
+        lib().oracle_count_step_stages(self.h, float(dt), _ptr(c), _ptr(u))
+        keys = ("add", "mul", "div", "sqrt", "pow", "cmp")
+        out = {}
+        for k, name in enumerate(self.STAGES):
+            out[name] = {"ops": {kk: int(c[6 * k + q]) for q, kk in enumerate(keys)},
+                         "units": int(u[k])}
         return out
 
 

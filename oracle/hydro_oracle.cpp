@@ -79,24 +79,40 @@ struct OpCount {
   uint64_t add = 0, mul = 0, div = 0, sqrt = 0, pow = 0, cmp = 0;
 };
 OpCount g_ops;
+// Counts are also kept per stage of the step: 0 primitives and dt, 1 PPMC
+// (without its slopes), 2 first Riemann solves, 3 transverse half-step and
+// second Riemann solves, 4 conserved update, 5 limited slopes.  g_units holds
+// the number of cells or faces each stage processed.
+constexpr int kStages = 6;
+OpCount g_stage_ops[kStages];
+uint64_t g_units[kStages];
+int g_stage = 0;
 
 struct CR {
   double v;
   CR() : v(0.0) {}
   CR(double x) : v(x) {}
 };
-inline CR operator+(CR a, CR b) { ++g_ops.add; return CR(a.v + b.v); }
-inline CR operator-(CR a, CR b) { ++g_ops.add; return CR(a.v - b.v); }
+#define ORACLE_COUNT(field) (++g_ops.field, ++g_stage_ops[g_stage].field)
+inline CR operator+(CR a, CR b) { ORACLE_COUNT(add); return CR(a.v + b.v); }
+inline CR operator-(CR a, CR b) { ORACLE_COUNT(add); return CR(a.v - b.v); }
 inline CR operator-(CR a) { return CR(-a.v); }
-inline CR operator*(CR a, CR b) { ++g_ops.mul; return CR(a.v * b.v); }
-inline CR operator/(CR a, CR b) { ++g_ops.div; return CR(a.v / b.v); }
-inline bool operator<(CR a, CR b) { ++g_ops.cmp; return a.v < b.v; }
-inline bool operator>(CR a, CR b) { ++g_ops.cmp; return a.v > b.v; }
-inline bool operator<=(CR a, CR b) { ++g_ops.cmp; return a.v <= b.v; }
-inline bool operator>=(CR a, CR b) { ++g_ops.cmp; return a.v >= b.v; }
-inline CR sqrt(CR a) { ++g_ops.sqrt; return CR(std::sqrt(a.v)); }
-inline CR pow(CR a, CR b) { ++g_ops.pow; return CR(std::pow(a.v, b.v)); }
-inline CR fabs(CR a) { ++g_ops.cmp; return CR(std::fabs(a.v)); }
+inline CR operator*(CR a, CR b) { ORACLE_COUNT(mul); return CR(a.v * b.v); }
+inline CR operator/(CR a, CR b) { ORACLE_COUNT(div); return CR(a.v / b.v); }
+inline bool operator<(CR a, CR b) { ORACLE_COUNT(cmp); return a.v < b.v; }
+inline bool operator>(CR a, CR b) { ORACLE_COUNT(cmp); return a.v > b.v; }
+inline bool operator<=(CR a, CR b) { ORACLE_COUNT(cmp); return a.v <= b.v; }
+inline bool operator>=(CR a, CR b) { ORACLE_COUNT(cmp); return a.v >= b.v; }
+inline CR sqrt(CR a) { ORACLE_COUNT(sqrt); return CR(std::sqrt(a.v)); }
+inline CR pow(CR a, CR b) { ORACLE_COUNT(pow); return CR(std::pow(a.v, b.v)); }
+inline CR fabs(CR a) { ORACLE_COUNT(cmp); return CR(std::fabs(a.v)); }
+#undef ORACLE_COUNT
+
+// stage bookkeeping; does nothing for the plain double oracle
+inline void set_stage(double*, int) {}
+inline void set_stage(CR*, int s) { g_stage = s; }
+inline void add_units(double*, int) {}
+inline void add_units(CR*, int s) { ++g_units[s]; }
 inline double val(CR a) { return a.v; }
 inline double val(double a) { return a; }
 // the double overloads sit beside the counted ones so that templated code picks
@@ -341,9 +357,12 @@ void plmc_slope(const R wm[5], const R wc[5], const R wp[5], const Gas& g, R dw[
 template <class R>
 void ppmc_cell(const R w[5][5], R dtdx, const Gas& g, R WsL[5], R WsR[5]) {
   R dwm[5], dwc[5], dwp[5];
+  set_stage((R*)nullptr, 5);
   plmc_slope(w[0], w[1], w[2], g, dwm);  // cell i-1
   plmc_slope(w[1], w[2], w[3], g, dwc);  // cell i
   plmc_slope(w[2], w[3], w[4], g, dwp);  // cell i+1
+  for (int k = 0; k < 3; ++k) add_units((R*)nullptr, 5);
+  set_stage((R*)nullptr, 1);
   const R* wim = w[1];
   const R* wi = w[2];
   const R* wip = w[3];
@@ -542,6 +561,7 @@ int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
   fill_ghosts(G);
 
   // cell-average primitives (global order) of every padded cell
+  set_stage((R*)nullptr, 0);
   std::vector<R> W(5 * nc);
 #pragma omp parallel for if (threaded) schedule(static)
   for (long c = 0; c < (long)nc; ++c) {
@@ -549,6 +569,7 @@ int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
     for (int q = 0; q < 5; ++q) U[q] = G.u[q * nc + c];
     cons_to_prim(U, g, Wc);
     for (int q = 0; q < 5; ++q) W[q * nc + c] = Wc[q];
+    add_units((R*)nullptr, 0);
   }
 
   bool active[3];
@@ -587,6 +608,8 @@ int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
             w[s][4] = W[4 * nc + cs];
           }
           R WsL[5], WsR[5], UsL[5], UsR[5];
+          set_stage((R*)nullptr, 1);
+          add_units((R*)nullptr, 1);
           ppmc_cell(w, dtdx, g, WsL, WsR);
           prim_to_cons(WsL, g, UsL);
           prim_to_cons(WsR, g, UsR);
@@ -617,6 +640,8 @@ int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
             ULr[1 + s] = UL[d][(1 + P[s]) * nc + f];
             URr[1 + s] = UR[d][(1 + P[s]) * nc + f];
           }
+          set_stage((R*)nullptr, 2);
+          add_units((R*)nullptr, 2);
           fl |= riemann_exact_cons(ULr, URr, g, Fr);
           F1[d][0 * nc + f] = Fr[0];
           F1[d][4 * nc + f] = Fr[4];
@@ -646,6 +671,8 @@ int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
           const size_t f = G.idx(i, j, k);
           const size_t cl = f - sd;  // cell left of the face
           const size_t cr = f;       // cell right of the face
+          set_stage((R*)nullptr, 3);
+          add_units((R*)nullptr, 3);
           R UhL[5], UhR[5];
           for (int q = 0; q < 5; ++q) {
             UhL[q] = UL[d][q * nc + f];
@@ -677,12 +704,14 @@ int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
   }
 
   // step 5: conserved update of the real cells (Eq. conserved_update)
+  set_stage((R*)nullptr, 4);
   int fl = 0;
 #pragma omp parallel for if (threaded) schedule(static) reduction(| : fl)
   for (int k = G.gh[2]; k < G.gh[2] + G.n[2]; ++k)
     for (int j = G.gh[1]; j < G.gh[1] + G.n[1]; ++j)
       for (int i = G.gh[0]; i < G.gh[0] + G.n[0]; ++i) {
         const size_t c = G.idx(i, j, k);
+        add_units((R*)nullptr, 4);
         for (int q = 0; q < 5; ++q) {
           R un = G.u[q * nc + c];
           for (int d = 0; d < 3; ++d) {
@@ -829,6 +858,11 @@ int oracle_count_step(void* h, double dt, double* counts) {
     for (int q = 0; q < 5; ++q) G.inflow_prim[f][q] = G0.inflow_prim[f][q];
   for (size_t i = 0; i < G0.u.size(); ++i) G.u[i] = CR(G0.u[i]);
   g_ops = OpCount();
+  for (int k = 0; k < kStages; ++k) {
+    g_stage_ops[k] = OpCount();
+    g_units[k] = 0;
+  }
+  g_stage = 0;
   const int fl = ctu_step(G, dt, false);
   counts[0] = (double)g_ops.add;
   counts[1] = (double)g_ops.mul;
@@ -836,6 +870,34 @@ int oracle_count_step(void* h, double dt, double* counts) {
   counts[3] = (double)g_ops.sqrt;
   counts[4] = (double)g_ops.pow;
   counts[5] = (double)g_ops.cmp;
+  return fl;
+}
+
+// Per-stage version of oracle_count_step: counts[stage*6 + kind] with the kinds
+// of oracle_count_step and units[stage] cells or faces processed, for the six
+// stages (0 primitives and the dt minimum, 1 PPMC without slopes, 2 first
+// Riemann solves, 3 transverse half-step + second Riemann solves, 4 update,
+// 5 limited slopes -- the oracle computes three per PPMC cell).
+int oracle_count_step_stages(void* h, double dt, double* counts, double* units) {
+  const auto& G0 = static_cast<Handle*>(h)->G;
+  Grid<CR> G(G0.n, G0.dx, G0.gamma, G0.bc);
+  for (int f = 0; f < 6; ++f)
+    for (int q = 0; q < 5; ++q) G.inflow_prim[f][q] = G0.inflow_prim[f][q];
+  for (size_t i = 0; i < G0.u.size(); ++i) G.u[i] = CR(G0.u[i]);
+  g_ops = OpCount();
+  for (int k = 0; k < kStages; ++k) {
+    g_stage_ops[k] = OpCount();
+    g_units[k] = 0;
+  }
+  g_stage = 0;
+  (void)compute_dt_min(G);
+  const int fl = ctu_step(G, dt, false);
+  for (int k = 0; k < kStages; ++k) {
+    const OpCount& c = g_stage_ops[k];
+    const uint64_t v[6] = {c.add, c.mul, c.div, c.sqrt, c.pow, c.cmp};
+    for (int q = 0; q < 6; ++q) counts[6 * k + q] = (double)v[q];
+    units[k] = (double)g_units[k];
+  }
   return fl;
 }
 

@@ -1,0 +1,440 @@
+// hydro_api.cu -- the C-ABI of include/hydro.h: handle, device memory, the
+// order of the stage launches of one CTU step (Sec. 2.3), errors.
+//
+// All device memory of a handle is one allocation carved into 256-byte aligned
+// planes.  The conserved state stays resident in HBM between steps; a step
+// reads back only a 64-byte record (dt and status flags) so that hydro_step()
+// can return dt, as the paper's host loop does after its reduction (Sec. 3.4).
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/hydro.h"
+#include "hydro_internal.h"
+#include "hydro_math.cuh"
+
+using namespace hydro;
+
+struct hydro_s {
+  Geom G;
+  Bufs B;
+  BcDesc bc;
+  double gamma;
+  int precision;
+  int device;
+  cudaStream_t stream;
+  bool have_state;
+  int last_error;
+  char cuda_err[256];
+  void* slab;
+  size_t slab_bytes;
+  double* host_rec;  // pinned copy of the device step record
+  // tracing: per-stage device time (CUDA events around each launch) and counts
+  bool profile;
+  int nev;
+  cudaEvent_t ev[2 * 64];
+  int ev_stage[64];
+  long long ev_units[64];
+  double stage_ms[kNumStages];
+  long long stage_launches[kNumStages];
+  long long stage_units_sum[kNumStages];
+  long long launches_total;
+};
+
+namespace {
+
+int fail(hydro_t h, int code) {
+  if (h) h->last_error = code;
+  return code;
+}
+
+int cuda_fail(hydro_t h, cudaError_t e) {
+  if (h) {
+    snprintf(h->cuda_err, sizeof(h->cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    h->last_error = HYDRO_ECUDA;
+  }
+  return HYDRO_ECUDA;
+}
+
+#define CK(h, call)                              \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_); \
+  } while (0)
+
+int use_device(hydro_t h) {
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  if (cur != h->device) {
+    e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+  }
+  return HYDRO_OK;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool active(const Geom& G, int d) { return G.n[d] > 1; }
+
+// Tracing: when enabled, every launch is bracketed by two events on the
+// handle's stream; times are folded into per-stage totals once the step has
+// completed (hydro_step waits for its record anyway).
+int mark_begin(hydro_t h, int stage, int axis) {
+  ++h->launches_total;
+  if (!h->profile || h->nev >= 64) return HYDRO_OK;
+  const int k = h->nev;
+  h->ev_stage[k] = stage;
+  h->ev_units[k] = stage_units(h->G, stage, axis);
+  CK(h, cudaEventRecord(h->ev[2 * k], h->stream));
+  return HYDRO_OK;
+}
+
+int mark_end(hydro_t h) {
+  if (!h->profile || h->nev >= 64) return HYDRO_OK;
+  CK(h, cudaEventRecord(h->ev[2 * h->nev + 1], h->stream));
+  ++h->nev;
+  return HYDRO_OK;
+}
+
+int fold_events(hydro_t h) {
+  for (int k = 0; k < h->nev; ++k) {
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, h->ev[2 * k], h->ev[2 * k + 1]));
+    h->stage_ms[h->ev_stage[k]] += ms;
+    h->stage_launches[h->ev_stage[k]] += 1;
+    h->stage_units_sum[h->ev_stage[k]] += h->ev_units[k];
+  }
+  h->nev = 0;
+  return HYDRO_OK;
+}
+
+#define STAGE(h, stage, axis, call)          \
+  do {                                       \
+    int rc_ = mark_begin(h, stage, axis);    \
+    if (rc_) return rc_;                     \
+    cudaError_t e_ = (call);                 \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_); \
+    rc_ = mark_end(h);                       \
+    if (rc_) return rc_;                     \
+  } while (0)
+
+// Enqueue one full step; dt from the CFL condition when fixed_dt <= 0.
+int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
+  const Geom& G = h->G;
+  const Bufs& B = h->B;
+  cudaStream_t st = h->stream;
+  h->nev = 0;
+  CK(h, cudaMemsetAsync(B.rec + 4, 0, sizeof(double), st));
+  STAGE(h, kStagePrims, 0, fp64_prims(G, B, h->bc, h->gamma, fixed_dt <= 0.0, st));
+  STAGE(h, kStageSetDt, 0, fp64_set_dt(G, B, cfl, fixed_dt, st));
+  for (int d = 0; d < 3; ++d) {
+    if (!active(G, d)) continue;
+    STAGE(h, kStageSlopes, d, fp64_stage(G, B, kStageSlopes, d, h->gamma, st));
+    STAGE(h, kStagePpmc, d, fp64_stage(G, B, kStagePpmc, d, h->gamma, st));
+    STAGE(h, kStageRiemann1, d, fp64_stage(G, B, kStageRiemann1, d, h->gamma, st));
+  }
+  for (int d = 0; d < 3; ++d)
+    if (active(G, d)) STAGE(h, kStageRiemann2, d, fp64_stage(G, B, kStageRiemann2, d, h->gamma, st));
+  STAGE(h, kStageUpdate, 0, fp64_update(G, B, st));
+  return HYDRO_OK;
+}
+
+int read_record(hydro_t h) {
+  CK(h, cudaMemcpyAsync(h->host_rec, h->B.rec, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return HYDRO_OK;
+}
+
+double run_step(hydro_t h, double cfl, double fixed_dt) {
+  if (!h) return (double)HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (!h->have_state) return (double)fail(h, HYDRO_ENOSTATE);
+  if (fixed_dt <= 0.0 && !(cfl > 0.0)) return (double)fail(h, HYDRO_EINVAL);
+  int rc = use_device(h);
+  if (rc) return (double)rc;
+  rc = enqueue_step(h, cfl, fixed_dt);
+  if (rc) return (double)rc;
+  rc = read_record(h);
+  if (rc) return (double)rc;
+  if (h->profile) {
+    rc = fold_events(h);
+    if (rc) return (double)rc;
+  }
+  int flags;
+  memcpy(&flags, h->host_rec + 4, sizeof(int));
+  if (flags & kFlagNonPhys) return (double)fail(h, HYDRO_ENONPHYS);
+  if (flags & kFlagNewton) return (double)fail(h, HYDRO_ENEWTON);
+  return h->host_rec[1];
+}
+
+}  // namespace
+
+extern "C" {
+
+int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, const int bc[6]) {
+  if (!out) return HYDRO_EINVAL;
+  *out = nullptr;
+  if (!bc || !(dx > 0.0) || !(gamma > 1.0)) return HYDRO_EINVAL;
+  const int n[3] = {nx, ny, nz};
+  for (int d = 0; d < 3; ++d) {
+    if (n[d] < 1 || (n[d] > 1 && n[d] < kNG)) return HYDRO_EINVAL;
+    if (n[d] > 1 && (bc[2 * d] < 0 || bc[2 * d] > 3 || bc[2 * d + 1] < 0 || bc[2 * d + 1] > 3))
+      return HYDRO_EINVAL;
+    if (n[d] > 1 && ((bc[2 * d] == HYDRO_BC_PERIODIC) != (bc[2 * d + 1] == HYDRO_BC_PERIODIC)))
+      return HYDRO_EINVAL;
+  }
+  hydro_t h = new (std::nothrow) hydro_s();
+  if (!h) return HYDRO_ENOMEM;
+  h->profile = false;
+  h->nev = 0;
+  h->launches_total = 0;
+  for (int k = 0; k < kNumStages; ++k) {
+    h->stage_ms[k] = 0.0;
+    h->stage_launches[k] = 0;
+    h->stage_units_sum[k] = 0;
+  }
+  memset(h->cuda_err, 0, sizeof(h->cuda_err));
+  h->gamma = gamma;
+  h->precision = HYDRO_FP64;
+  h->stream = nullptr;
+  h->have_state = false;
+  h->last_error = HYDRO_OK;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return HYDRO_ECUDA;
+  }
+  Geom& G = h->G;
+  for (int d = 0; d < 3; ++d) {
+    G.n[d] = n[d];
+    G.g[d] = n[d] > 1 ? kNG : 0;
+    G.N[d] = n[d] + 2 * G.g[d];
+  }
+  G.s[0] = 1;
+  G.s[1] = G.N[0];
+  G.s[2] = (long long)G.N[0] * G.N[1];
+  G.ps = (long long)align_up((size_t)G.N[0] * G.N[1] * G.N[2], 32);
+  G.nreal = (long long)nx * ny * nz;
+  G.dx = dx;
+  for (int f = 0; f < 6; ++f) {
+    h->bc.type[f] = (n[f / 2] > 1) ? bc[f] : HYDRO_BC_PERIODIC;
+    for (int q = 0; q < 5; ++q) h->bc.inflow[f][q] = 0.0;
+  }
+  // one slab: u, W (6 planes), S (5), per active axis UL/UR/F1 (15), record
+  int nact = 0;
+  for (int d = 0; d < 3; ++d) nact += active(G, d) ? 1 : 0;
+  const size_t plane = (size_t)G.ps * sizeof(double);
+  const size_t ubytes = align_up((size_t)G.nreal * 5 * sizeof(double), 256);
+  const size_t total = ubytes + plane * (6 + 5 + 15 * (size_t)nact) + 256;
+  h->slab_bytes = total;
+  e = cudaMalloc(&h->slab, total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return HYDRO_ENOMEM;
+  }
+  e = cudaMallocHost((void**)&h->host_rec, 8 * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaFree(h->slab);
+    delete h;
+    return HYDRO_ENOMEM;
+  }
+  char* p = static_cast<char*>(h->slab);
+  Bufs& B = h->B;
+  B.u = reinterpret_cast<double*>(p);
+  p += ubytes;
+  B.W = reinterpret_cast<double*>(p);
+  p += 6 * plane;
+  B.S = reinterpret_cast<double*>(p);
+  p += 5 * plane;
+  for (int d = 0; d < 3; ++d) {
+    B.UL[d] = B.UR[d] = B.F1[d] = nullptr;
+    if (!active(G, d)) continue;
+    B.UL[d] = reinterpret_cast<double*>(p);
+    p += 5 * plane;
+    B.UR[d] = reinterpret_cast<double*>(p);
+    p += 5 * plane;
+    B.F1[d] = reinterpret_cast<double*>(p);
+    p += 5 * plane;
+  }
+  B.rec = reinterpret_cast<double*>(p);
+  e = cudaMemset(h->slab, 0, total);
+  if (e != cudaSuccess) {
+    cudaFreeHost(h->host_rec);
+    cudaFree(h->slab);
+    delete h;
+    return HYDRO_ECUDA;
+  }
+  *out = h;
+  return HYDRO_OK;
+}
+
+int hydro_set_inflow(hydro_t h, int face, const double prim[5]) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (face < 0 || face > 5 || !prim) return fail(h, HYDRO_EINVAL);
+  if (!(prim[0] > 0.0) || !(prim[4] >= 0.0)) return fail(h, HYDRO_EINVAL);
+  double* U = h->bc.inflow[face];
+  U[0] = prim[0];
+  U[1] = prim[0] * prim[1];
+  U[2] = prim[0] * prim[2];
+  U[3] = prim[0] * prim[3];
+  U[4] = prim[4] / (h->gamma - 1.0) + 0.5 * prim[0] * (prim[1] * prim[1] + prim[2] * prim[2] + prim[3] * prim[3]);
+  return HYDRO_OK;
+}
+
+int hydro_set_precision(hydro_t h, int mode) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (mode != HYDRO_FP64) return fail(h, HYDRO_EINVAL);
+  h->precision = mode;
+  return HYDRO_OK;
+}
+
+int hydro_set_stream(hydro_t h, void* stream) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return HYDRO_OK;
+}
+
+int hydro_set_state(hydro_t h, const double* u, int on_device) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (!u) return fail(h, HYDRO_EINVAL);
+  int rc = use_device(h);
+  if (rc) return rc;
+  const size_t bytes = (size_t)h->G.nreal * 5 * sizeof(double);
+  CK(h, cudaMemcpyAsync(h->B.u, u, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->have_state = true;
+  return HYDRO_OK;
+}
+
+int hydro_get_state(hydro_t h, double* u, int on_device) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (!u) return fail(h, HYDRO_EINVAL);
+  if (!h->have_state) return fail(h, HYDRO_ENOSTATE);
+  int rc = use_device(h);
+  if (rc) return rc;
+  const size_t bytes = (size_t)h->G.nreal * 5 * sizeof(double);
+  CK(h, cudaMemcpyAsync(u, h->B.u, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return HYDRO_OK;
+}
+
+double hydro_step(hydro_t h, double cfl) { return run_step(h, cfl, 0.0); }
+
+double hydro_step_dt(hydro_t h, double dt) {
+  if (!h) return (double)HYDRO_EINVAL;
+  if (!(dt > 0.0)) return (double)fail(h, HYDRO_EINVAL);
+  return run_step(h, 0.0, dt);
+}
+
+double hydro_compute_dt(hydro_t h, double cfl) {
+  if (!h) return (double)HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (!h->have_state) return (double)fail(h, HYDRO_ENOSTATE);
+  if (!(cfl > 0.0)) return (double)fail(h, HYDRO_EINVAL);
+  int rc = use_device(h);
+  if (rc) return (double)rc;
+  cudaError_t e = fp64_prims(h->G, h->B, h->bc, h->gamma, true, h->stream);
+  if (e != cudaSuccess) return (double)cuda_fail(h, e);
+  e = fp64_set_dt(h->G, h->B, cfl, 0.0, h->stream);
+  if (e != cudaSuccess) return (double)cuda_fail(h, e);
+  h->launches_total += 2;
+  rc = read_record(h);
+  if (rc) return (double)rc;
+  return h->host_rec[1];
+}
+
+int hydro_last_error(hydro_t h) { return h ? h->last_error : HYDRO_EINVAL; }
+
+const char* hydro_error_string(int code) {
+  switch (code) {
+    case HYDRO_OK: return "ok";
+    case HYDRO_EINVAL: return "invalid argument";
+    case HYDRO_ENOMEM: return "out of memory";
+    case HYDRO_ECUDA: return "CUDA runtime error";
+    case HYDRO_ENONPHYS: return "non-physical state (rho <= 0 or NaN) after the step";
+    case HYDRO_ENEWTON: return "Riemann Newton iteration reached its cap";
+    case HYDRO_ENOSTATE: return "no state set";
+    default: return "unknown error";
+  }
+}
+
+const char* hydro_cuda_error_string(hydro_t h) { return h ? h->cuda_err : ""; }
+
+int hydro_profile(hydro_t h, int enable) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  int rc = use_device(h);
+  if (rc) return rc;
+  if (enable && !h->profile) {
+    for (int k = 0; k < 2 * 64; ++k) CK(h, cudaEventCreate(&h->ev[k]));
+    h->profile = true;
+  } else if (!enable && h->profile) {
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 2 * 64; ++k) cudaEventDestroy(h->ev[k]);
+    h->profile = false;
+  }
+  for (int k = 0; k < kNumStages; ++k) {
+    h->stage_ms[k] = 0.0;
+    h->stage_launches[k] = 0;
+    h->stage_units_sum[k] = 0;
+  }
+  h->launches_total = 0;
+  h->nev = 0;
+  return HYDRO_OK;
+}
+
+int hydro_profile_read(hydro_t h, int nstages, double* ms, long long* launches, long long* units,
+                       long long* launches_total) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (nstages < 0 || nstages > kNumStages) return fail(h, HYDRO_EINVAL);
+  for (int k = 0; k < nstages; ++k) {
+    if (ms) ms[k] = h->stage_ms[k];
+    if (launches) launches[k] = h->stage_launches[k];
+    if (units) units[k] = h->stage_units_sum[k];
+  }
+  if (launches_total) *launches_total = h->launches_total;
+  return HYDRO_OK;
+}
+
+void hydro_free(hydro_t h) {
+  if (!h) return;
+  int cur = -1;
+  if (cudaGetDevice(&cur) == cudaSuccess && cur != h->device) cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  if (h->profile)
+    for (int k = 0; k < 2 * 64; ++k) cudaEventDestroy(h->ev[k]);
+  cudaFree(h->slab);
+  cudaFreeHost(h->host_rec);
+  if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
+  delete h;
+}
+
+int hydro_riemann_exact(int n, const double* UL, const double* UR, double gamma, double* F,
+                        int* flags, void* stream) {
+  if (n < 0 || (n > 0 && (!UL || !UR || !F)) || !(gamma > 1.0)) return HYDRO_EINVAL;
+  cudaError_t e = fp64_riemann_soa(n, UL, UR, gamma, F, flags, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
+}
+
+int hydro_ppmc(int n, const double* w, double dtdx, double gamma, double* WsL, double* WsR,
+               void* stream) {
+  if (n < 0 || (n > 0 && (!w || !WsL || !WsR)) || !(gamma > 1.0) || !(dtdx >= 0.0))
+    return HYDRO_EINVAL;
+  cudaError_t e = fp64_ppmc_soa(n, w, dtdx, gamma, WsL, WsR, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+// hydro_internal.h -- host-side types shared by the C-ABI and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hydro {
+
+// Geometry of one grid.  Padded arrays carry kNG ghost layers on each side of
+// an active axis (an axis with one cell has none) and are laid out x fastest.
+struct Geom {
+  int n[3];          // real cells per axis
+  int g[3];          // ghost layers per side (4 on active axes, 0 otherwise)
+  int N[3];          // padded extent per axis
+  long long s[3];    // padded strides: 1, N0, N0*N1
+  long long ps;      // plane stride of padded arrays (multiple of 32)
+  long long nreal;   // nx*ny*nz
+  double dx;
+};
+
+// Boundary description passed to the primitive kernel by value.
+struct BcDesc {
+  int type[6];          // HYDRO_BC_* per face x-, x+, y-, y+, z-, z+
+  double inflow[6][5];  // conserved inflow state per face (rho, mx, my, mz, E)
+};
+
+// Device buffers of the FP64 path.
+struct Bufs {
+  double* u;       // real cells [5][nz][ny][nx]
+  double* W;       // padded primitives [6][ps]: rho, vx, vy, vz, p, a
+  double* S;       // padded limited slopes [5][ps] of the current sweep (sweep order)
+  double* UL[3];   // per axis: left states of faces [5][ps]; reused for F^{n+1/2}
+  double* UR[3];   // per axis: right states of faces [5][ps]
+  double* F1[3];   // per axis: first fluxes F* [5][ps]
+  // 64-byte step record on the device: [0] dt-min bits, [1] dt, [2] dt/dx,
+  // [3] dt/(2 dx), [4] flags (int in the low word)
+  double* rec;
+};
+
+// Box of cells (or faces: a face carries the index of the cell to its right).
+struct Box {
+  int lo[3];
+  int n[3];
+};
+
+// Stages of one step; each is one kernel launch (per axis for the sweep stages).
+enum Stage : int {
+  kStagePrims = 0,     // ghost remap + primitives (+ dt minimum)
+  kStageSetDt = 1,     // dt, dt/dx
+  kStageSlopes = 2,    // limited slopes along an axis
+  kStagePpmc = 3,      // traced face states along an axis
+  kStageRiemann1 = 4,  // first fluxes along an axis
+  kStageRiemann2 = 5,  // transverse half-step + CTU fluxes along an axis
+  kStageUpdate = 6,    // conserved update
+  kNumStages = 7
+};
+
+// Units (cells or faces) one launch of a stage processes.
+long long stage_units(const Geom& G, int stage, int axis);
+
+// FP64 launchers (hydro_fp64.cu).  Every launcher enqueues on `st` and returns
+// the launch error.
+cudaError_t fp64_prims(const Geom& G, const Bufs& B, const BcDesc& bc, double gamma, bool want_dt,
+                       cudaStream_t st);
+cudaError_t fp64_set_dt(const Geom& G, const Bufs& B, double cfl, double fixed_dt, cudaStream_t st);
+cudaError_t fp64_stage(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
+                       cudaStream_t st);
+cudaError_t fp64_update(const Geom& G, const Bufs& B, cudaStream_t st);
+cudaError_t fp64_riemann_soa(int n, const double* UL, const double* UR, double gamma, double* F,
+                             int* flags, cudaStream_t st);
+cudaError_t fp64_ppmc_soa(int n, const double* w, double dtdx, double gamma, double* WsL,
+                          double* WsR, cudaStream_t st);
+
+}  // namespace hydro

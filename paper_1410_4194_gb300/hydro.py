@@ -1,0 +1,250 @@
+"""Python binding of the C-ABI in ``include/hydro.h`` (ctypes, marshalling only).
+
+Every step of the method runs in the CUDA library ``_build/libhydro.so``; this
+module only converts arguments.  There is no CPU fallback: if the library has
+not been built, or no GPU is present, the calls raise.
+
+Arrays are conserved states ``[5, nz, ny, nx]`` float64 (rho, rho u, rho v,
+rho w, E).  A ``torch`` CUDA tensor is passed by device pointer on the current
+torch stream; a numpy array or CPU tensor by host pointer.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HYDRO_BC_PERIODIC, HYDRO_BC_REFLECT, HYDRO_BC_OUTFLOW, HYDRO_BC_INFLOW = 0, 1, 2, 3
+HYDRO_FP64, HYDRO_MIXED = 0, 1
+ERRORS = {0: "HYDRO_OK", -1: "HYDRO_EINVAL", -2: "HYDRO_ENOMEM", -3: "HYDRO_ECUDA",
+          -4: "HYDRO_ENONPHYS", -5: "HYDRO_ENEWTON", -6: "HYDRO_ENOSTATE"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhydro.so")
+
+# every entry point that include/hydro.h declares
+EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_precision", "hydro_set_stream",
+           "hydro_set_state", "hydro_get_state", "hydro_step", "hydro_step_dt",
+           "hydro_compute_dt", "hydro_last_error", "hydro_error_string",
+           "hydro_cuda_error_string", "hydro_profile", "hydro_profile_read", "hydro_free",
+           "hydro_riemann_exact", "hydro_ppmc")
+STAGES = ("prims", "set_dt", "slopes", "ppmc", "riemann1", "riemann2", "update")
+
+_lib = None
+
+
+class HydroError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__("%s (%d)%s" % (ERRORS.get(code, "?"), code, (": " + msg) if msg else ""))
+
+
+def load():
+    """Load libhydro.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libhydro.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    L.hydro_init.argtypes = [ctypes.POINTER(vp)] + [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [ip]
+    L.hydro_set_inflow.argtypes = [vp, ctypes.c_int, dp]
+    L.hydro_set_precision.argtypes = [vp, ctypes.c_int]
+    L.hydro_set_stream.argtypes = [vp, vp]
+    L.hydro_set_state.argtypes = [vp, vp, ctypes.c_int]
+    L.hydro_get_state.argtypes = [vp, vp, ctypes.c_int]
+    for f in (L.hydro_step, L.hydro_step_dt, L.hydro_compute_dt):
+        f.argtypes = [vp, ctypes.c_double]
+        f.restype = ctypes.c_double
+    L.hydro_last_error.argtypes = [vp]
+    L.hydro_error_string.argtypes = [ctypes.c_int]
+    L.hydro_error_string.restype = ctypes.c_char_p
+    L.hydro_cuda_error_string.argtypes = [vp]
+    L.hydro_cuda_error_string.restype = ctypes.c_char_p
+    L.hydro_free.argtypes = [vp]
+    L.hydro_profile.argtypes = [vp, ctypes.c_int]
+    llp = ctypes.POINTER(ctypes.c_longlong)
+    L.hydro_profile_read.argtypes = [vp, ctypes.c_int, dp, llp, llp, llp]
+    L.hydro_riemann_exact.argtypes = [ctypes.c_int, vp, vp, ctypes.c_double, vp, vp, vp]
+    L.hydro_ppmc.argtypes = [ctypes.c_int, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp]
+    _lib = L
+    return L
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _torch_stream_ptr():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _buffer(u, shape, writable):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor."""
+    if _is_torch(u):
+        if tuple(u.shape) != shape or str(u.dtype) != "torch.float64" or not u.is_contiguous():
+            raise ValueError("expected a contiguous float64 tensor of shape %s" % (shape,))
+        return ctypes.c_void_p(u.data_ptr()), int(u.is_cuda), u
+    a = u if writable else np.ascontiguousarray(u, dtype=np.float64)
+    if a.shape != shape or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous float64 array of shape %s" % (shape,))
+    return ctypes.c_void_p(a.ctypes.data), 0, a
+
+
+class Grid:
+    """One grid advanced by the CUDA CTU step (see include/hydro.h)."""
+
+    def __init__(self, nx, ny, nz, dx, gamma, bc, precision=HYDRO_FP64, stream=None):
+        L = load()
+        self._L = L
+        h = ctypes.c_void_p()
+        bca = (ctypes.c_int * 6)(*[int(b) for b in bc])
+        rc = L.hydro_init(ctypes.byref(h), int(nx), int(ny), int(nz), float(dx), float(gamma), bca)
+        if rc != 0:
+            raise HydroError(rc, "hydro_init")
+        self.h = h
+        self.shape = (5, nz, ny, nx)
+        self.n = (nx, ny, nz)
+        if stream is not None:
+            self.set_stream(stream)
+        if precision != HYDRO_FP64:
+            self.set_precision(precision)
+
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = what
+            if rc == -3:
+                msg += ": " + self._L.hydro_cuda_error_string(self.h).decode()
+            raise HydroError(rc, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.hydro_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_inflow(self, face, prim):
+        p = (ctypes.c_double * 5)(*[float(x) for x in prim])
+        self._check(self._L.hydro_set_inflow(self.h, int(face), p), "set_inflow")
+
+    def set_precision(self, mode):
+        self._check(self._L.hydro_set_precision(self.h, int(mode)), "set_precision")
+
+    def set_stream(self, stream):
+        """Order this grid's work on a stream: a torch.cuda.Stream, a raw
+        cudaStream_t integer, or "torch" for torch's current stream."""
+        if stream == "torch":
+            ptr = _torch_stream_ptr()
+        elif hasattr(stream, "cuda_stream"):
+            ptr = ctypes.c_void_p(stream.cuda_stream)
+        else:
+            ptr = ctypes.c_void_p(int(stream) if stream else 0)
+        self._check(self._L.hydro_set_stream(self.h, ptr), "set_stream")
+
+    def set_state(self, u):
+        ptr, dev, keep = _buffer(u, self.shape, False)
+        self._check(self._L.hydro_set_state(self.h, ptr, dev), "set_state")
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float64)
+        ptr, dev, keep = _buffer(out, self.shape, True)
+        self._check(self._L.hydro_get_state(self.h, ptr, dev), "get_state")
+        return out
+
+    def _dt_result(self, dt, what, check):
+        if dt < 0:
+            rc = self._L.hydro_last_error(self.h)
+            if check:
+                self._check(rc, what)
+            return dt
+        return dt
+
+    def step(self, cfl, check=True):
+        """One CTU step with the CFL time step; returns dt (raises on error)."""
+        return self._dt_result(self._L.hydro_step(self.h, float(cfl)), "step", check)
+
+    def step_dt(self, dt, check=True):
+        """One CTU step with a given dt; returns dt (raises on error)."""
+        return self._dt_result(self._L.hydro_step_dt(self.h, float(dt)), "step_dt", check)
+
+    def compute_dt(self, cfl):
+        return self._dt_result(self._L.hydro_compute_dt(self.h, float(cfl)), "compute_dt", True)
+
+    def last_error(self):
+        return self._L.hydro_last_error(self.h)
+
+    def profile(self, enable=True):
+        """Enable/disable per-stage CUDA-event timing; resets the totals."""
+        self._check(self._L.hydro_profile(self.h, int(bool(enable))), "profile")
+
+    def profile_read(self):
+        """Per-stage totals: {stage: (ms, launches, units)} and total launches."""
+        n = len(STAGES)
+        ms = (ctypes.c_double * n)()
+        la = (ctypes.c_longlong * n)()
+        un = (ctypes.c_longlong * n)()
+        tot = ctypes.c_longlong()
+        self._check(self._L.hydro_profile_read(self.h, n, ms, la, un, ctypes.byref(tot)),
+                    "profile_read")
+        return {STAGES[k]: (ms[k], la[k], un[k]) for k in range(n)}, tot.value
+
+
+def run(u0, dx, gamma, bc, nsteps=None, cfl=0.3, t_end=None, inflow=None, precision=HYDRO_FP64,
+        max_steps=100000):
+    """Advance ``u0`` on the GPU; returns ``(u, t, nsteps)`` (host numpy state)."""
+    _, nz, ny, nx = u0.shape
+    g = Grid(nx, ny, nz, dx, gamma, bc, precision=precision)
+    try:
+        if inflow:
+            for face, prim in inflow.items():
+                g.set_inflow(face, prim)
+        g.set_state(np.ascontiguousarray(u0, dtype=np.float64))
+        t, steps = 0.0, 0
+        while steps < max_steps:
+            if nsteps is not None and steps >= nsteps:
+                break
+            if t_end is not None and t >= t_end:
+                break
+            if t_end is None:
+                dt = g.step(cfl)
+                t += dt
+            else:
+                dt = g.compute_dt(cfl)
+                last = t + dt >= t_end
+                if last:
+                    dt = t_end - t
+                g.step_dt(dt)
+                t = t_end if last else t + dt
+            steps += 1
+        return g.get_state(), t, steps
+    finally:
+        g.close()
+
+
+def riemann_exact(UL, UR, gamma, F, flags=None):
+    """Exact Riemann fluxes of device SoA arrays [5, n] (torch CUDA tensors)."""
+    L = load()
+    n = UL.shape[1]
+    fp = ctypes.c_void_p(flags.data_ptr()) if flags is not None else None
+    rc = L.hydro_riemann_exact(n, ctypes.c_void_p(UL.data_ptr()), ctypes.c_void_p(UR.data_ptr()),
+                               float(gamma), ctypes.c_void_p(F.data_ptr()), fp, _torch_stream_ptr())
+    if rc != 0:
+        raise HydroError(rc, "riemann_exact")
+
+
+def ppmc(w, dtdx, gamma, WsL, WsR):
+    """PPMC of device stencils w [5 cells, 5, n] into WsL, WsR [5, n] (torch CUDA tensors)."""
+    L = load()
+    n = w.shape[2]
+    rc = L.hydro_ppmc(n, ctypes.c_void_p(w.data_ptr()), float(dtdx), float(gamma),
+                      ctypes.c_void_p(WsL.data_ptr()), ctypes.c_void_p(WsR.data_ptr()),
+                      _torch_stream_ptr())
+    if rc != 0:
+        raise HydroError(rc, "ppmc")

@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA FP64 path (through the C-ABI) against the CPU oracle.
+
+Tolerance (FP64 path): per cell and field,
+    |gpu - oracle| <= 1e-10 * max(|oracle|, 1e-12 * max_cells |oracle_field|)
+after up to 10 steps.  Both sides evaluate the same IEEE operations without
+fused multiply-add; the remaining difference is CUDA's pow versus libm's (a few
+ulp), which the step then carries.  Kernel-level comparisons (one Riemann solve,
+one PPMC reconstruction) use 1e-12 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_4194_gb300 import hydro
+from paper_1410_4194_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+P, R_, O, I_ = 0, 1, 2, 3
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for -m gpu tests")
+    hydro.load()
+    oracle.set_threads(0)
+    yield
+
+
+def rel_err(g, o):
+    o = np.asarray(o)
+    scale = np.abs(o).reshape(o.shape[0], -1).max(axis=1)
+    scale = scale.reshape((-1,) + (1,) * (o.ndim - 1))
+    den = np.maximum(np.abs(o), 1e-12 * scale)
+    den = np.where(den > 0, den, 1.0)
+    return np.abs(np.asarray(g) - o) / den
+
+
+def run_both(w, nsteps, cfl=0.3):
+    inflow = w.get("inflow")
+    uo, to, no, fl = oracle.run(w["u"], w["dx"], w["gamma"], w["bc"], nsteps=nsteps, cfl=cfl,
+                                inflow=inflow)
+    assert fl == 0
+    ug, tg, ng = hydro.run(w["u"], w["dx"], w["gamma"], w["bc"], nsteps=nsteps, cfl=cfl,
+                           inflow=inflow)
+    return ug, uo, tg, to
+
+
+def test_riemann_kernel_matches_oracle():
+    import torch
+    WL, WR = W.random_states(4096, seed=31, gamma=5.0 / 3.0)
+    aL = np.sqrt(5 / 3 * WL[:, 4] / WL[:, 0]); aR = np.sqrt(5 / 3 * WR[:, 4] / WR[:, 0])
+    keep = (WR[:, 1] - WL[:, 1]) < 0.9 * 2 * (aL + aR) / (2 / 3)
+    WL, WR = WL[keep], WR[keep]
+    g = 5.0 / 3.0
+    UL = W.prim_to_cons(WL[:, 0], WL[:, 1], WL[:, 2], WL[:, 3], WL[:, 4], g).reshape(5, -1)
+    UR = W.prim_to_cons(WR[:, 0], WR[:, 1], WR[:, 2], WR[:, 3], WR[:, 4], g).reshape(5, -1)
+    Fo, flo = oracle.riemann_cons(UL.T, UR.T, g)
+    dUL = torch.tensor(UL, device="cuda"); dUR = torch.tensor(UR, device="cuda")
+    dF = torch.empty_like(dUL); fl = torch.zeros(1, dtype=torch.int32, device="cuda")
+    hydro.riemann_exact(dUL, dUR, g, dF, fl)
+    torch.cuda.synchronize()
+    Fg = dF.cpu().numpy().T
+    assert int(fl.item()) == flo
+    scale = np.abs(Fo).max(axis=1, keepdims=True)
+    assert np.all(np.abs(Fg - Fo) <= 1e-12 * scale)
+
+
+def test_ppmc_kernel_matches_oracle():
+    import torch
+    rng = np.random.Generator(np.random.PCG64(17))
+    n = 4096
+    w = np.zeros((n, 5, 5))
+    w[:, :, 0] = np.exp(rng.normal(scale=0.4, size=(n, 5)))
+    w[:, :, 1:4] = rng.normal(scale=0.7, size=(n, 5, 3))
+    w[:, :, 4] = np.exp(rng.normal(scale=0.4, size=(n, 5)))
+    for dtdx in (0.0, 0.13, 0.31):
+        Lo, Ro = oracle.ppmc(w, dtdx, 1.4)
+        dw = torch.tensor(np.ascontiguousarray(w.transpose(1, 2, 0)), device="cuda")
+        dL = torch.empty((5, n), dtype=torch.float64, device="cuda"); dR = torch.empty_like(dL)
+        hydro.ppmc(dw, dtdx, 1.4, dL, dR)
+        torch.cuda.synchronize()
+        # no pow in PPMC: the two sides perform the same IEEE operations
+        assert np.array_equal(dL.cpu().numpy().T, Lo)
+        assert np.array_equal(dR.cpu().numpy().T, Ro)
+
+
+@pytest.mark.parametrize("case", ["sedov32", "smooth24", "tube3d", "ragged", "twod", "inflow"])
+def test_step_parity_10_steps(case):
+    if case == "sedov32":
+        w = W.sedov(32)
+    elif case == "smooth24":
+        w = dict(u=W.smooth_periodic((24, 24, 24), gamma=1.4, seed=3, vamp=0.8), dx=1 / 24,
+                 gamma=1.4, bc=[P] * 6)
+    elif case == "tube3d":
+        nx, ny, nz = 40, 12, 10
+        x = np.arange(nx) < nx // 2
+        rho = np.broadcast_to(np.where(x, 3.0, 0.4), (nz, ny, nx)).copy()
+        p = np.broadcast_to(np.where(x, 5.0, 0.2), (nz, ny, nx)).copy()
+        rho *= 1 + 0.05 * np.sin(np.arange(ny) * 0.7)[None, :, None]
+        w = dict(u=W.prim_to_cons(rho, 0.1, -0.2, 0.3, p, 5 / 3), dx=1 / 40, gamma=5 / 3,
+                 bc=[O, O, R_, R_, P, P])
+    elif case == "ragged":
+        u = W.smooth_periodic((5, 7, 13), gamma=1.4, seed=8, vamp=0.6)
+        w = dict(u=u, dx=0.07, gamma=1.4, bc=[O, O, R_, O, P, P])
+    elif case == "twod":
+        u = W.smooth_periodic((1, 20, 28), gamma=1.4, seed=4, vamp=0.7)
+        w = dict(u=u, dx=0.05, gamma=1.4, bc=[P, P, R_, R_, P, P])
+    else:  # inflow: a small shock-cloud
+        rho2, u2, p2, vs = W.rankine_hugoniot(10.0)
+        nx, ny, nz = 32, 16, 16
+        rho = np.ones((nz, ny, nx)); vx = np.zeros_like(rho); p = np.ones_like(rho)
+        rho[:, :, :8] = rho2; vx[:, :, :8] = u2; p[:, :, :8] = p2
+        zz, yy, xx = np.meshgrid(np.arange(nz) - 8, np.arange(ny) - 8, np.arange(nx) - 20, indexing="ij")
+        rho[(xx ** 2 + yy ** 2 + zz ** 2) < 25] = 10.0
+        w = dict(u=W.prim_to_cons(rho, vx, 0.0, 0.0, p, 5 / 3), dx=1 / 16, gamma=5 / 3,
+                 bc=[I_, O, P, P, P, P], inflow={0: (rho2, u2, 0.0, 0.0, p2)})
+    ug, uo, tg, to = run_both(w, 10)
+    assert tg == pytest.approx(to, rel=1e-12)
+    err = rel_err(ug, uo)
+    assert err.max() <= TOL, (case, err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+def test_sod_config_to_t02():
+    """Config 1: 512-cell Sod to t = 0.2; parity with the oracle and with the
+    exact solution's plateaus."""
+    w = W.sod(512)
+    uo, to, no, fl = oracle.run(w["u"], w["dx"], w["gamma"], w["bc"], t_end=0.2, cfl=0.3)
+    ug, tg, ng = hydro.run(w["u"], w["dx"], w["gamma"], w["bc"], t_end=0.2, cfl=0.3)
+    assert ng == no and tg == to == 0.2
+    err = rel_err(ug, uo)
+    assert err.max() <= 1e-8, err.max()
+    x = (np.arange(512) + 0.5) / 512
+    rho = ug[0, 0, 0]
+    np.testing.assert_allclose(rho[(x > 0.62) & (x < 0.66)], 0.42632, rtol=2e-3)
+    np.testing.assert_allclose(rho[(x > 0.72) & (x < 0.82)], 0.26557, rtol=2e-3)
+
+
+def test_full_size_sedov_one_step_all_cells():
+    """Config 2 at full size (256^3, the benchmark's launch configuration): one
+    step compared cell by cell with the oracle."""
+    w = W.sedov(256)
+    ug, uo, tg, to = run_both(w, 1)
+    err = rel_err(ug, uo)
+    assert err.max() <= TOL, err.max()
+
+
+def test_conservation_and_symmetry_on_gpu():
+    w = W.sedov(64)
+    ug, tg, ng = hydro.run(w["u"], w["dx"], w["gamma"], w["bc"], nsteps=20, cfl=0.3)
+    tot0 = w["u"].reshape(5, -1).sum(axis=1)
+    tot = ug.reshape(5, -1).sum(axis=1)
+    scale = np.abs(w["u"]).reshape(5, -1).sum(axis=1)
+    assert np.all(np.abs(tot - tot0) <= 1e-13 * scale + 1e-14)
+    rho = ug[0]
+    s = np.abs(rho).max()
+    assert np.max(np.abs(rho - rho[::-1])) <= 1e-12 * s
+    assert np.max(np.abs(rho - np.transpose(rho, (1, 2, 0)))) <= 1e-12 * s
+
+
+def test_uniform_state_exact_on_gpu():
+    u0 = W.prim_to_cons(np.full((9, 10, 11), 1.7), 0.4, -0.3, 0.2, np.full((9, 10, 11), 0.9), 1.4)
+    ug, tg, ng = hydro.run(u0, 0.1, 1.4, [P] * 6, nsteps=3, cfl=0.4)
+    assert np.array_equal(ug, u0)
+
+
+def test_device_buffers_and_resume_bit_exact():
+    import torch
+    w = W.sedov(24)
+    u0 = torch.tensor(w["u"], device="cuda")
+    g = hydro.Grid(24, 24, 24, w["dx"], w["gamma"], w["bc"], stream="torch")
+    g.set_state(u0)
+    for _ in range(3):
+        g.step(0.3)
+    mid = torch.empty_like(u0)
+    g.get_state(mid)
+    for _ in range(3):
+        g.step(0.3)
+    straight = g.get_state()
+    g2 = hydro.Grid(24, 24, 24, w["dx"], w["gamma"], w["bc"], stream="torch")
+    g2.set_state(mid)
+    for _ in range(3):
+        g2.step(0.3)
+    assert np.array_equal(g2.get_state(), straight)
+
+
+def test_error_paths():
+    g = hydro.Grid(8, 8, 8, 0.1, 1.4, [P] * 6)
+    with pytest.raises(hydro.HydroError) as e:
+        g.step(0.3)
+    assert e.value.code == -6  # no state yet
+    with pytest.raises(hydro.HydroError):
+        hydro.Grid(3, 8, 8, 0.1, 1.4, [P] * 6)  # active axis shorter than the ghost depth
+    with pytest.raises(hydro.HydroError):
+        hydro.Grid(8, 8, 8, 0.1, 1.4, [P, O, P, P, P, P])  # half-periodic axis
+    with pytest.raises(hydro.HydroError):
+        hydro.Grid(8, 8, 8, -0.1, 1.4, [P] * 6)
+    # a negative density injected on the host: the step reports ENONPHYS
+    u = W.prim_to_cons(np.ones((8, 8, 8)), 0.0, 0.0, 0.0, np.ones((8, 8, 8)), 1.4)
+    u[0, 4, 4, 4] = -1.0
+    g.set_state(u)
+    dt = g.step(0.3, check=False)
+    assert dt < 0 and g.last_error() == -4
+    with pytest.raises(hydro.HydroError):
+        g.step_dt(-1.0)

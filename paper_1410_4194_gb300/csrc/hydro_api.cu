@@ -223,12 +223,12 @@ int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, co
     h->bc.type[f] = (n[f / 2] > 1) ? bc[f] : HYDRO_BC_PERIODIC;
     for (int q = 0; q < 5; ++q) h->bc.inflow[f][q] = 0.0;
   }
-  // one slab: u, W (6 planes), S (5), per active axis UL/UR/F1 (15), record
+  // one slab: u, W (8 planes), S (5), per active axis UL/UR/F1 (15), record
   int nact = 0;
   for (int d = 0; d < 3; ++d) nact += active(G, d) ? 1 : 0;
   const size_t plane = (size_t)G.ps * sizeof(double);
   const size_t ubytes = align_up((size_t)G.nreal * 5 * sizeof(double), 256);
-  const size_t total = ubytes + plane * (6 + 5 + 15 * (size_t)nact) + 256;
+  const size_t total = ubytes + plane * (8 + 5 + 15 * (size_t)nact) + 256;
   h->slab_bytes = total;
   e = cudaMalloc(&h->slab, total);
   if (e != cudaSuccess) {
@@ -247,7 +247,7 @@ int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, co
   B.u = reinterpret_cast<double*>(p);
   p += ubytes;
   B.W = reinterpret_cast<double*>(p);
-  p += 6 * plane;
+  p += 8 * plane;
   B.S = reinterpret_cast<double*>(p);
   p += 5 * plane;
   for (int d = 0; d < 3; ++d) {

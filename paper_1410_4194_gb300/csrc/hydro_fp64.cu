@@ -16,7 +16,7 @@
 //   k_prims      ghost cells by index remap (Sec. 3.1) + primitives + dt minimum
 //   k_set_dt     dt = cfl * min (Eq. calc_dt_3D) or a fixed dt; dt/dx
 //   k_slopes<d>  limited characteristic slopes along axis d (App. A.2)
-//   k_ppmc<d>    traced face states U* of every cell (App. A.3)
+//   k_ppmc<d>    traced face states W* of every cell (App. A.3)
 //   k_riemann1<d> first fluxes F* (Sec. 2.3 step 2; App. B.1)
 //   k_riemann2<d> transverse half-step (Eq. transverse_evolution) + CTU fluxes
 //   k_update     conserved update (Eq. conserved_update) + positivity check
@@ -164,12 +164,21 @@ __global__ void __launch_bounds__(kThreads) k_prims(Geom G, Bufs B, BcDesc bc, G
 #pragma unroll
     for (int d = 0; d < 3; ++d)
       if (neg & (1 << d)) U[1 + d] = -U[1 + d];
+    // primitives in the CPU reference's operation order (divisions), then the
+    // per-cell reciprocals the later stages multiply by
+    const double d = U[0];
     double W[5];
-    cons2prim(U, g, W);  // global order: rho, vx, vy, vz, p
-    const double a = sqrt(g.gamma * W[4] / W[0]);
+    W[0] = d;
+    W[1] = U[1] / d;
+    W[2] = U[2] / d;
+    W[3] = U[3] / d;
+    W[4] = tmax(g.gm1 * (U[4] - 0.5 * d * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3])), kPFloor);
+    const double a = sqrt(g.gamma * W[4] / d);
 #pragma unroll
     for (int q = 0; q < 5; ++q) B.W[q * G.ps + t] = W[q];
     B.W[5 * G.ps + t] = a;
+    B.W[6 * G.ps + t] = 1.0 / a;
+    B.W[7 * G.ps + t] = 1.0 / d;
     if (want_dt && real) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -207,7 +216,9 @@ __global__ void __launch_bounds__(kThreads) k_slopes(Geom G, Bufs B, Box box, Ga
   load_prim<D>(B.W, G.ps, c, wc);
   load_prim<D>(B.W, G.ps, c + s, wp);
   const double a = B.W[5 * G.ps + c];
-  limited_slope(wm, wc, wp, a, dw);
+  const double inv_a = B.W[6 * G.ps + c];
+  const double inv_rho = B.W[7 * G.ps + c];
+  limited_slope(wm, wc, wp, a, inv_a, inv_rho, dw);
 #pragma unroll
   for (int q = 0; q < 5; ++q) B.S[q * G.ps + c] = dw[q];
 }
@@ -232,15 +243,15 @@ __global__ void __launch_bounds__(kThreads) k_ppmc(Geom G, Bufs B, Box box, Gas 
     sp[q] = B.S[q * G.ps + c + s];
   }
   const double a = B.W[5 * G.ps + c];
+  const double inv_a = B.W[6 * G.ps + c];
+  const double inv_rho = B.W[7 * G.ps + c];
   const double dtdx = B.rec[2];
-  double WsL[5], WsR[5], UsL[5], UsR[5];
-  ppmc_states(wm, wc, wp, sm, sc, sp, a, dtdx, WsL, WsR);
-  prim2cons(WsL, g, UsL);
-  prim2cons(WsR, g, UsR);
+  double WsL[5], WsR[5];
+  ppmc_states(wm, wc, wp, sm, sc, sp, a, inv_a, inv_rho, dtdx, WsL, WsR);
   // the left face of cell c is the right state of face c; its right face is the
-  // left state of face c+1
-  store_rot<D>(B.UR[D], G.ps, c, UsL);
-  store_rot<D>(B.UL[D], G.ps, c + s, UsR);
+  // left state of face c+1 (stored as primitives)
+  store_rot<D>(B.UR[D], G.ps, c, WsL);
+  store_rot<D>(B.UL[D], G.ps, c + s, WsR);
 }
 
 template <int D>
@@ -251,12 +262,10 @@ __global__ void __launch_bounds__(kThreads) k_riemann1(Geom G, Bufs B, Box box, 
   int c3[3];
   box_coords(box, t, c3);
   const long long f = pidx(G, c3);
-  double UL[5], UR[5], WL[5], WR[5], F[5];
-  load_rot<D>(B.UL[D], G.ps, f, UL);
-  load_rot<D>(B.UR[D], G.ps, f, UR);
-  cons2prim(UL, g, WL);
-  cons2prim(UR, g, WR);
-  const int fl = riemann_exact(WL, WR, g, F);
+  double WL[5], WR[5], F[5];
+  load_rot<D>(B.UL[D], G.ps, f, WL);
+  load_rot<D>(B.UR[D], G.ps, f, WR);
+  const int fl = riemann_exact(WL, WR, 1.0 / WL[0], 1.0 / WR[0], g, F);
   store_rot<D>(B.F1[D], G.ps, f, F);
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
@@ -272,12 +281,14 @@ __global__ void __launch_bounds__(kThreads) k_riemann2(Geom G, Bufs B, Box box, 
   const long long ps = G.ps;
   const long long cl = f - G.s[D], cr = f;
   const double h = B.rec[3];
-  double UhL[5], UhR[5];
+  double WsL[5], WsR[5], UhL[5], UhR[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    UhL[q] = B.UL[D][q * ps + f];
-    UhR[q] = B.UR[D][q * ps + f];
+    WsL[q] = B.UL[D][q * ps + f];
+    WsR[q] = B.UR[D][q * ps + f];
   }
+  prim2cons(WsL, g, UhL);  // global order: U* of the two sides of the face
+  prim2cons(WsR, g, UhR);
   constexpr int T1 = Perm<D>::t1, T2 = Perm<D>::t2;
   if (G.n[T1] > 1) {
     const double* F = B.F1[T1];
@@ -297,12 +308,12 @@ __global__ void __launch_bounds__(kThreads) k_riemann2(Geom G, Bufs B, Box box, 
       UhR[q] = UhR[q] + h * (F[q * ps + cr] - F[q * ps + cr + st]);
     }
   }
-  double UL[5], UR[5], WL[5], WR[5], Fx[5];
+  double UL[5], UR[5], WL[5], WR[5], Fx[5], idL, idR;
   UL[0] = UhL[0]; UL[1] = UhL[1 + D]; UL[2] = UhL[1 + T1]; UL[3] = UhL[1 + T2]; UL[4] = UhL[4];
   UR[0] = UhR[0]; UR[1] = UhR[1 + D]; UR[2] = UhR[1 + T1]; UR[3] = UhR[1 + T2]; UR[4] = UhR[4];
-  cons2prim(UL, g, WL);
-  cons2prim(UR, g, WR);
-  const int fl = riemann_exact(WL, WR, g, Fx);
+  cons2prim(UL, g, WL, idL);
+  cons2prim(UR, g, WR, idR);
+  const int fl = riemann_exact(WL, WR, idL, idR, g, Fx);
   // CTU flux of this face replaces its (now consumed) left state
   store_rot<D>(B.UL[D], ps, f, Fx);
   if (fl) atomicOr(rec_flags(B.rec), fl);
@@ -339,15 +350,15 @@ __global__ void k_riemann_soa(int n, const double* __restrict__ UL, const double
                               Gas g, double* __restrict__ F, int* flags) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  double L[5], R[5], WL[5], WR[5], Fx[5];
+  double L[5], R[5], WL[5], WR[5], Fx[5], idL, idR;
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     L[q] = UL[(long long)q * n + t];
     R[q] = UR[(long long)q * n + t];
   }
-  cons2prim(L, g, WL);
-  cons2prim(R, g, WR);
-  const int fl = riemann_exact(WL, WR, g, Fx);
+  cons2prim(L, g, WL, idL);
+  cons2prim(R, g, WR, idR);
+  const int fl = riemann_exact(WL, WR, idL, idR, g, Fx);
 #pragma unroll
   for (int q = 0; q < 5; ++q) F[(long long)q * n + t] = Fx[q];
   if (fl && flags) atomicOr(flags, fl);
@@ -357,18 +368,20 @@ __global__ void k_ppmc_soa(int n, const double* __restrict__ w, double dtdx, Gas
                            double* __restrict__ WsL, double* __restrict__ WsR) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  double st[5][5], a[5];
+  double st[5][5], a[5], ia[5], ir[5];
 #pragma unroll
   for (int s = 0; s < 5; ++s) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) st[s][q] = w[((long long)s * 5 + q) * n + t];
     a[s] = sqrt(g.gamma * st[s][4] / st[s][0]);
+    ia[s] = 1.0 / a[s];
+    ir[s] = 1.0 / st[s][0];
   }
   double sm[5], sc[5], sp[5], L[5], R[5];
-  limited_slope(st[0], st[1], st[2], a[1], sm);
-  limited_slope(st[1], st[2], st[3], a[2], sc);
-  limited_slope(st[2], st[3], st[4], a[3], sp);
-  ppmc_states(st[1], st[2], st[3], sm, sc, sp, a[2], dtdx, L, R);
+  limited_slope(st[0], st[1], st[2], a[1], ia[1], ir[1], sm);
+  limited_slope(st[1], st[2], st[3], a[2], ia[2], ir[2], sc);
+  limited_slope(st[2], st[3], st[4], a[3], ia[3], ir[3], sp);
+  ppmc_states(st[1], st[2], st[3], sm, sc, sp, a[2], ia[2], ir[2], dtdx, L, R);
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     WsL[(long long)q * n + t] = L[q];

@@ -26,10 +26,10 @@ struct BcDesc {
 // Device buffers of the FP64 path.
 struct Bufs {
   double* u;       // real cells [5][nz][ny][nx]
-  double* W;       // padded primitives [6][ps]: rho, vx, vy, vz, p, a
+  double* W;       // padded primitives [8][ps]: rho, vx, vy, vz, p, a, 1/a, 1/rho
   double* S;       // padded limited slopes [5][ps] of the current sweep (sweep order)
-  double* UL[3];   // per axis: left states of faces [5][ps]; reused for F^{n+1/2}
-  double* UR[3];   // per axis: right states of faces [5][ps]
+  double* UL[3];   // per axis: primitive left states W*_L of faces [5][ps]; reused for F^{n+1/2}
+  double* UR[3];   // per axis: primitive right states W*_R of faces [5][ps]
   double* F1[3];   // per axis: first fluxes F* [5][ps]
   // 64-byte step record on the device: [0] dt-min bits, [1] dt, [2] dt/dx,
   // [3] dt/(2 dx), [4] flags (int in the low word)

@@ -3,20 +3,43 @@
 // Riemann stages of the mixed path).
 //
 //   * cons/prim conversion of the ideal gas (Sec. 2.1);
-//   * the characteristic-limited slope of one cell (App. A.2, Eqs. diffs,
-//     plmc_lim_slopes and the PLMC projection);
+//   * the characteristic-limited slope of one cell (App. A.2: differences,
+//     projection onto the characteristic fields, MC limiter, back-projection);
 //   * PPMC face states with characteristic tracing (App. A.3);
 //   * the exact Riemann solver with Newton iteration and ten-case sampling
 //     (App. B.1).
 //
-// Readings where the paper's printed formulas are garbled (the same readings
-// as the CPU reference): xi0 = (-rho du/a + dp/a^2)/2; w6 = 6 w_i - 3 (W_L + W_R);
+// GB300 executes FP64 at two FMA per clock per SM, 1/64 of its FP32 rate, and a
+// library pow() costs about a hundred FP64 FMA slots, a division or square root
+// about ten.  The arithmetic below therefore evaluates the paper's formulas
+// through algebraic identities that remove most of those operations; every
+// result equals the printed formula up to rounding:
+//   * (p/p_k)^z with z = (gamma-1)/(2 gamma) = 1/k (gamma = 5/3 -> k = 5,
+//     gamma = 7/5 -> k = 7) is a k-th root: an FP32 seed from the SFU
+//     (log2/exp2) refined by Newton steps for the reciprocal root,
+//     t <- t + (t/k)(1 - r t^k), then r^(1/k) = r t^(k-1); any other gamma uses pow;
+//   * f'_k on a rarefaction: (p/p_k)^(-(gamma+1)/(2gamma)) / (rho_k a_k)
+//     = x (a_k/gamma) / p with x = (p/p_k)^z, since -(gamma+1)/(2gamma) = z - 1 and
+//     p_k/(rho_k a_k) = a_k/gamma;
+//   * rarefaction star density rho_k (p/p_k)^(1/gamma) = rho_k r / x^2, since
+//     1/gamma = 1 - 2z; the fan exponents 2gamma/(gamma-1) = k and
+//     2/(gamma-1) = k - 2 are integer powers;
+//   * the Newton stopping test 2|p_{n+1}-p_n|/|p_{n+1}+p_n| < tol is evaluated as
+//     2|p_{n+1}-p_n| < tol |p_{n+1}+p_n|;
+//   * divisions by a, a^2, rho and 6 become products with reciprocals computed
+//     once per cell;
+//   * of the six traced-parabola integrals of PPMC only those whose wave moves
+//     toward the face (the sign tests of App. A.3) are formed.
+//
+// Readings where the printed formulas are garbled (shared with the CPU
+// reference): xi0 = (-rho du/a + dp/a^2)/2; w6 = 6 w_i - 3 (W_L + W_R);
 // B = T^m_L - T^p_L and D = T^p_R - T^0_R with T the traced-parabola integrals;
-// the right fan sound speed 2/(gamma+1) (a_R - (gamma-1) u_R/2) with u = -a.
-// Newton: tolerance 1e-6, at most 50 iterations, iterates floored at 1e-20,
-// u^m from f_L, f_R at the final p^m.
+// right fan sound speed 2/(gamma+1) (a_R - (gamma-1) u_R/2) with u = -a.  Newton:
+// tolerance 1e-6, at most 50 iterations, iterates floored at 1e-20, u^m from
+// f_L, f_R at the final p^m.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace hydro {
@@ -34,8 +57,8 @@ template <typename T>
 struct GasT {
   T gamma, gm1, gp1;
   T z;        // (gamma-1)/(2 gamma)
-  T zd;       // -(gamma+1)/(2 gamma)
   T inv_g;    // 1/gamma
+  T inv_gm1;  // 1/(gamma-1)
   T fan_d;    // 2/(gamma-1)
   T fan_p;    // 2 gamma/(gamma-1)
   T two_gp1;  // 2/(gamma+1)
@@ -43,6 +66,7 @@ struct GasT {
   T sh_a;     // (gamma+1)/(2 gamma)
   T sh_b;     // (gamma-1)/(2 gamma)
   T gm1_gp1;  // (gamma-1)/(gamma+1)
+  int k;      // z = 1/k exactly for k = 5 or 7, else 0
 };
 
 template <typename T>
@@ -52,8 +76,8 @@ inline GasT<T> make_gas(double g) {
   c.gm1 = T(g - 1.0);
   c.gp1 = T(g + 1.0);
   c.z = T((g - 1.0) / (2.0 * g));
-  c.zd = T(-(g + 1.0) / (2.0 * g));
   c.inv_g = T(1.0 / g);
+  c.inv_gm1 = T(1.0 / (g - 1.0));
   c.fan_d = T(2.0 / (g - 1.0));
   c.fan_p = T(2.0 * g / (g - 1.0));
   c.two_gp1 = T(2.0 / (g + 1.0));
@@ -61,6 +85,9 @@ inline GasT<T> make_gas(double g) {
   c.sh_a = T((g + 1.0) / (2.0 * g));
   c.sh_b = T((g - 1.0) / (2.0 * g));
   c.gm1_gp1 = T((g - 1.0) / (g + 1.0));
+  const double kk = 2.0 * g / (g - 1.0);
+  const int ki = (int)(kk + 0.5);
+  c.k = ((ki == 5 || ki == 7) && fabs(kk - ki) < 1e-12 * ki) ? ki : 0;
   return c;
 }
 
@@ -70,17 +97,77 @@ __device__ __forceinline__ double xsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float xsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double xabs(double x) { return fabs(x); }
 __device__ __forceinline__ float xabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double xfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float xfma(float a, float b, float c) { return fmaf(a, b, c); }
 
 // min/max with the tie and signed-zero behaviour of "(b < a) ? b : a"
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return (b < a) ? b : a; }
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return (a < b) ? b : a; }
 
+// x^K by squaring (K is small)
+template <int K, typename T>
+__device__ __forceinline__ T ipow(T x) {
+  if constexpr (K == 0) {
+    return T(1);
+  } else if constexpr (K == 1) {
+    return x;
+  } else {
+    const T h = ipow<K / 2>(x);
+    if constexpr (K % 2 == 0)
+      return h * h;
+    else
+      return h * h * x;
+  }
+}
+
+// r^(1/K) for r in [1e-30, 1e30]: SFU seed of t = r^(-1/K) in float, Newton steps
+// t <- t + (t/K)(1 - r t^K) (quadratic; two in double, one in float), r t^(K-1).
+template <int K, typename T>
+__device__ __forceinline__ T kth_root(T r) {
+  const float lr = __log2f((float)r);
+  T t = (T)exp2f(lr * (-1.0f / (float)K));
+  const T invK = T(1.0 / K);
+  constexpr int kSteps = sizeof(T) == 8 ? 2 : 1;
+#pragma unroll
+  for (int i = 0; i < kSteps; ++i) {
+    const T e = xfma(-r, ipow<K>(t), T(1));
+    t = xfma(t * invK, e, t);
+  }
+  return r * ipow<K - 1>(t);
+}
+
+// (p/p_k)^z
+template <typename T>
+__device__ __forceinline__ T pow_z(T r, const GasT<T>& g) {
+  if (r > T(1e-30) && r < T(1e30)) {
+    if (g.k == 5) return kth_root<5>(r);
+    if (g.k == 7) return kth_root<7>(r);
+  }
+  return xpow(r, g.z);
+}
+
+// s^(2/(gamma-1)) and s^(2 gamma/(gamma-1)) of the rarefaction fan
+template <typename T>
+__device__ __forceinline__ void fan_powers(T s, const GasT<T>& g, T& pd, T& pp) {
+  if (g.k == 5) {
+    pd = ipow<3>(s);
+    pp = pd * s * s;
+  } else if (g.k == 7) {
+    pd = ipow<5>(s);
+    pp = pd * s * s;
+  } else {
+    pd = xpow(s, g.fan_d);
+    pp = xpow(s, g.fan_p);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // ideal-gas conversion in sweep order (rho, normal, t1, t2, E | p)
 template <typename T>
-__device__ __forceinline__ void cons2prim(const T U[5], const GasT<T>& g, T W[5]) {
+__device__ __forceinline__ void cons2prim(const T U[5], const GasT<T>& g, T W[5], T& inv_d) {
   const T d = U[0];
-  const T vn = U[1] / d, v1 = U[2] / d, v2 = U[3] / d;
+  inv_d = T(1) / d;
+  const T vn = U[1] * inv_d, v1 = U[2] * inv_d, v2 = U[3] * inv_d;
   const T p = g.gm1 * (U[4] - T(0.5) * d * (vn * vn + v1 * v1 + v2 * v2));
   W[0] = d;
   W[1] = vn;
@@ -96,17 +183,15 @@ __device__ __forceinline__ void prim2cons(const T W[5], const GasT<T>& g, T U[5]
   U[1] = d * W[1];
   U[2] = d * W[2];
   U[3] = d * W[3];
-  U[4] = W[4] / g.gm1 + T(0.5) * d * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  U[4] = W[4] * g.inv_gm1 + T(0.5) * d * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
 }
 
 // ---------------------------------------------------------------------------
-// App. A.2: project a primitive difference onto the characteristic fields of a
-// cell with density rho and sound speed a
+// App. A.2: characteristic projection of a primitive difference
 template <typename T>
-__device__ __forceinline__ void char_project(const T dw[5], T rho, T a, T xi[5]) {
-  const T a2 = a * a;
-  const T dpa2 = dw[4] / a2;
-  const T rdu_a = rho * dw[1] / a;
+__device__ __forceinline__ void char_project(const T dw[5], T rho, T inv_a, T inv_a2, T xi[5]) {
+  const T dpa2 = dw[4] * inv_a2;
+  const T rdu_a = rho * dw[1] * inv_a;
   xi[0] = T(0.5) * (-rdu_a + dpa2);
   xi[1] = dw[0] - dpa2;
   xi[2] = dw[2];
@@ -117,18 +202,19 @@ __device__ __forceinline__ void char_project(const T dw[5], T rho, T a, T xi[5])
 // limited slope of the cell c from its neighbours m (c-1) and p (c+1)
 template <typename T>
 __device__ __forceinline__ void limited_slope(const T wm[5], const T wc[5], const T wp[5], T a,
-                                              T dw[5]) {
-  T dl[5], dr[5], dc[5];
+                                              T inv_a, T inv_rho, T dw[5]) {
+  const T inv_a2 = inv_a * inv_a;
+  T xl[5], xr[5], xc[5], dl[5], dr[5], dc[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     dl[q] = wc[q] - wm[q];
     dr[q] = wp[q] - wc[q];
     dc[q] = T(0.5) * (wp[q] - wm[q]);
   }
-  T xl[5], xr[5], xc[5], xi[5];
-  char_project(dl, wc[0], a, xl);
-  char_project(dr, wc[0], a, xr);
-  char_project(dc, wc[0], a, xc);
+  char_project(dl, wc[0], inv_a, inv_a2, xl);
+  char_project(dr, wc[0], inv_a, inv_a2, xr);
+  char_project(dc, wc[0], inv_a, inv_a2, xc);
+  T xi[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     T s = T(0);
@@ -139,7 +225,7 @@ __device__ __forceinline__ void limited_slope(const T wm[5], const T wc[5], cons
     xi[q] = s;
   }
   dw[0] = xi[0] + xi[1] + xi[4];
-  dw[1] = a / wc[0] * (-xi[0] + xi[4]);
+  dw[1] = a * inv_rho * (-xi[0] + xi[4]);
   dw[2] = xi[2];
   dw[3] = xi[3];
   dw[4] = a * a * (xi[0] + xi[4]);
@@ -147,19 +233,20 @@ __device__ __forceinline__ void limited_slope(const T wm[5], const T wc[5], cons
 
 // ---------------------------------------------------------------------------
 // App. A.3: PPMC.  w_m, w_c, w_p: primitive averages of cells i-1, i, i+1;
-// s_m, s_c, s_p: their limited slopes; a: sound speed of cell i.  Outputs the
+// s_m, s_c, s_p: their limited slopes; a, inv_a, inv_rho of cell i.  Outputs the
 // traced states at the left (WsL) and right (WsR) face of cell i, pressure
 // floored.
 template <typename T>
 __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], const T w_p[5],
                                             const T s_m[5], const T s_c[5], const T s_p[5], T a,
-                                            T dtdx, T WsL[5], T WsR[5]) {
-  T dw[5], w6[5], WL[5], WR[5];
+                                            T inv_a, T inv_rho, T dtdx, T WsL[5], T WsR[5]) {
+  const T c16 = T(1.0 / 6.0);
+  T dw[5], w6[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     const T wi = w_c[q];
-    T L = T(0.5) * (wi + w_m[q]) - (s_c[q] - s_m[q]) / T(6);
-    T R = T(0.5) * (w_p[q] + wi) - (s_p[q] - s_c[q]) / T(6);
+    T L = T(0.5) * (wi + w_m[q]) - (s_c[q] - s_m[q]) * c16;
+    T R = T(0.5) * (w_p[q] + wi) - (s_p[q] - s_c[q]) * c16;
     if ((R - wi) * (wi - L) <= T(0)) {
       L = wi;
       R = wi;
@@ -168,159 +255,205 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
     if ((R - L) * ((T(3) * wi - T(2) * L) - R) < T(0)) R = T(3) * wi - T(2) * L;
     L = tmin(tmax(wi, w_m[q]), tmax(tmin(wi, w_m[q]), L));
     R = tmin(tmax(wi, w_p[q]), tmax(tmin(wi, w_p[q]), R));
-    WL[q] = L;
-    WR[q] = R;
+    WsL[q] = L;
+    WsR[q] = R;
     dw[q] = R - L;
     w6[q] = T(6) * wi - T(3) * (L + R);
   }
   const T rho = w_c[0];
   const T un = w_c[1];
   const T lm = un - a, l0 = un, lp = un + a;
-  const T am = dtdx * tmin(lm, T(0)), a0 = dtdx * tmin(l0, T(0)), ap = dtdx * tmin(lp, T(0));
-  const T bm = dtdx * tmax(lm, T(0)), b0 = dtdx * tmax(l0, T(0)), bp = dtdx * tmax(lp, T(0));
+  const T am = dtdx * tmin(lm, T(0)), bp = dtdx * tmax(lp, T(0));
   const T c23 = T(2.0 / 3.0);
-  const T a2 = a * a;
-  T E[5], B[5], C[5], D[5];
+  const T inv_a2 = inv_a * inv_a;
+  // integral of the parabola over the domain of dependence of the fastest
+  // left-going (m) and right-going (p) waves: the reference states
+  T tLm[5], tRp[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    const T tLm = T(0.5) * am * (dw[q] + w6[q] * (T(1) + c23 * am));
-    const T tL0 = T(0.5) * a0 * (dw[q] + w6[q] * (T(1) + c23 * a0));
-    const T tLp = T(0.5) * ap * (dw[q] + w6[q] * (T(1) + c23 * ap));
-    const T tRm = T(0.5) * bm * (dw[q] - w6[q] * (T(1) - c23 * bm));
-    const T tR0 = T(0.5) * b0 * (dw[q] - w6[q] * (T(1) - c23 * b0));
-    const T tRp = T(0.5) * bp * (dw[q] - w6[q] * (T(1) - c23 * bp));
-    WsL[q] = WL[q] - tLm;
-    WsR[q] = WR[q] - tRp;
-    E[q] = tLm - tL0;
-    B[q] = tLm - tLp;
-    C[q] = tRp - tRm;
-    D[q] = tRp - tR0;
+    tLm[q] = T(0.5) * am * (dw[q] + w6[q] * (T(1) + c23 * am));
+    tRp[q] = T(0.5) * bp * (dw[q] - w6[q] * (T(1) - c23 * bp));
   }
   T sL[5] = {T(0), T(0), T(0), T(0), T(0)};
   T sR[5] = {T(0), T(0), T(0), T(0), T(0)};
-  if (l0 < T(0)) {
-    sL[0] = sL[0] + (E[0] - E[4] / a2);
+  if (l0 < T(0)) {  // contact and advected velocities reach the left face: E
+    const T a0 = dtdx * l0;
+    T E[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) E[q] = tLm[q] - T(0.5) * a0 * (dw[q] + w6[q] * (T(1) + c23 * a0));
+    sL[0] = sL[0] + (E[0] - E[4] * inv_a2);
     sL[2] = sL[2] + E[2];
     sL[3] = sL[3] + E[3];
   }
-  if (lp < T(0)) {
-    sL[0] = sL[0] + T(0.5) * (rho * B[1] / a + B[4] / a2);
-    sL[1] = sL[1] + T(0.5) * (B[1] + B[4] / (a * rho));
-    sL[4] = sL[4] + T(0.5) * (rho * B[1] * a + B[4]);
+  if (lp < T(0)) {  // right acoustic wave reaches the left face: B
+    const T ap = dtdx * lp;
+    const T B1 = tLm[1] - T(0.5) * ap * (dw[1] + w6[1] * (T(1) + c23 * ap));
+    const T B4 = tLm[4] - T(0.5) * ap * (dw[4] + w6[4] * (T(1) + c23 * ap));
+    sL[0] = sL[0] + T(0.5) * (rho * B1 * inv_a + B4 * inv_a2);
+    sL[1] = sL[1] + T(0.5) * (B1 + B4 * (inv_a * inv_rho));
+    sL[4] = sL[4] + T(0.5) * (rho * B1 * a + B4);
   }
-  if (lm > T(0)) {
-    sR[0] = sR[0] + T(0.5) * (-(rho * C[1]) / a + C[4] / a2);
-    sR[1] = sR[1] + T(0.5) * (C[1] - C[4] / (a * rho));
-    sR[4] = sR[4] + T(0.5) * (-(rho * C[1] * a) + C[4]);
+  if (lm > T(0)) {  // left acoustic wave reaches the right face: C
+    const T bm = dtdx * lm;
+    const T C1 = tRp[1] - T(0.5) * bm * (dw[1] - w6[1] * (T(1) - c23 * bm));
+    const T C4 = tRp[4] - T(0.5) * bm * (dw[4] - w6[4] * (T(1) - c23 * bm));
+    sR[0] = sR[0] + T(0.5) * (-(rho * C1) * inv_a + C4 * inv_a2);
+    sR[1] = sR[1] + T(0.5) * (C1 - C4 * (inv_a * inv_rho));
+    sR[4] = sR[4] + T(0.5) * (-(rho * C1 * a) + C4);
   }
-  if (l0 > T(0)) {
-    sR[0] = sR[0] + (D[0] - D[4] / a2);
+  if (l0 > T(0)) {  // contact and advected velocities reach the right face: D
+    const T b0 = dtdx * l0;
+    T D[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) D[q] = tRp[q] - T(0.5) * b0 * (dw[q] - w6[q] * (T(1) - c23 * b0));
+    sR[0] = sR[0] + (D[0] - D[4] * inv_a2);
     sR[2] = sR[2] + D[2];
     sR[3] = sR[3] + D[3];
   }
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    WsL[q] = WsL[q] + sL[q];
-    WsR[q] = WsR[q] + sR[q];
+    WsL[q] = (WsL[q] - tLm[q]) + sL[q];
+    WsR[q] = (WsR[q] - tRp[q]) + sR[q];
   }
   WsL[4] = tmax(WsL[4], T(kPFloor));
   WsR[4] = tmax(WsR[4], T(kPFloor));
 }
 
 // ---------------------------------------------------------------------------
-// App. B.1: pressure function of one side and its derivative
+// App. B.1: exact Riemann solver
 template <typename T>
-__device__ __forceinline__ void pressure_fn(T p, T dk, T pk, T ak, T Ak, T Bk, const GasT<T>& g,
-                                            T& f, T& fd) {
-  if (p <= pk) {
-    const T r = p / pk;
-    f = T(2) * ak / g.gm1 * (xpow(r, g.z) - T(1));
-    fd = T(1) / (dk * ak) * xpow(r, g.zd);
+struct RSide {
+  T d, u, p, a;
+  T inv_p;  // 1/p_k
+  T A, B;   // A_k = 2/((gamma+1) rho_k), B_k = (gamma-1)/(gamma+1) p_k
+  T cf;     // 2 a_k/(gamma-1)
+  T cd;     // a_k/gamma = p_k/(rho_k a_k)
+};
+
+// pressure function f_k, its derivative, and x = (p/p_k)^z on a rarefaction
+template <typename T>
+__device__ __forceinline__ void side_f(T p, T inv_p, const RSide<T>& s, const GasT<T>& g, T& f,
+                                       T& fd, T& x) {
+  if (p <= s.p) {
+    x = pow_z(p * s.inv_p, g);
+    f = s.cf * (x - T(1));
+    fd = x * s.cd * inv_p;
   } else {
-    const T q = xsqrt(Ak / (p + Bk));
-    f = (p - pk) * q;
-    fd = q * (T(1) - (p - pk) / (T(2) * (Bk + p)));
+    const T ipb = T(1) / (p + s.B);
+    const T q = xsqrt(s.A * ipb);
+    const T dp = p - s.p;
+    f = dp * q;
+    fd = q * (T(1) - T(0.5) * dp * ipb);
+    x = T(0);
   }
 }
 
-// Exact Riemann flux from primitive states in sweep order; returns the flags.
 template <typename T>
-__device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], const GasT<T>& g,
-                                             T F[5]) {
-  const T dL = WL[0], uL = WL[1], pL = WL[4];
-  const T dR = WR[0], uR = WR[1], pR = WR[4];
-  const T aL = xsqrt(g.gamma * pL / dL);
-  const T aR = xsqrt(g.gamma * pR / dR);
-  T pt = T(0.5) * (pL + pR) + T(0.125) * (uL - uR) * (dL + dR) * (aL + aR);
+__device__ __forceinline__ void side_f_only(T p, const RSide<T>& s, const GasT<T>& g, T& f, T& x) {
+  if (p <= s.p) {
+    x = pow_z(p * s.inv_p, g);
+    f = s.cf * (x - T(1));
+  } else {
+    f = (p - s.p) * xsqrt(s.A / (p + s.B));
+    x = T(0);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void make_side(const T W[5], T inv_d, const GasT<T>& g, RSide<T>& s) {
+  s.d = W[0];
+  s.u = W[1];
+  s.p = W[4];
+  s.a = xsqrt(g.gamma * s.p * inv_d);
+  s.inv_p = T(1) / s.p;
+  s.A = g.two_gp1 * inv_d;
+  s.B = g.gm1_gp1 * s.p;
+  s.cf = T(2) * s.a * g.inv_gm1;
+  s.cd = s.a * g.inv_g;
+}
+
+// Exact Riemann flux from primitive states in sweep order (inv_d = 1/rho of
+// each side); returns the status flags.
+template <typename T>
+__device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv_dL, T inv_dR,
+                                             const GasT<T>& g, T F[5]) {
+  RSide<T> L, R;
+  make_side(WL, inv_dL, g, L);
+  make_side(WR, inv_dR, g, R);
+  // primitive-variable estimate, then the two-shock estimate as Newton start
+  T pt = T(0.5) * (L.p + R.p) + T(0.125) * (L.u - R.u) * (L.d + R.d) * (L.a + R.a);
   if (pt < T(0)) pt = T(0);
-  const T AL = T(2) / (g.gp1 * dL), AR = T(2) / (g.gp1 * dR);
-  const T BL = g.gm1_gp1 * pL, BR = g.gm1_gp1 * pR;
-  const T gL = xsqrt(AL / (pt + BL)), gR = xsqrt(AR / (pt + BR));
-  T p = (gL * pL + gR * pR - (uR - uL)) / (gL + gR);
+  const T gL = xsqrt(L.A / (pt + L.B)), gR = xsqrt(R.A / (pt + R.B));
+  T p = (gL * L.p + gR * R.p - (R.u - L.u)) / (gL + gR);
   if (p < T(kP0Floor)) p = T(kP0Floor);
-  T fL, fR, dfL, dfR;
+  T fL, fR, dfL, dfR, xL, xR;
   int flags = kFlagNewton;
   for (int it = 0; it < kNewtonMax; ++it) {
-    pressure_fn(p, dL, pL, aL, AL, BL, g, fL, dfL);
-    pressure_fn(p, dR, pR, aR, AR, BR, g, fR, dfR);
-    T pn = p - (fL + fR + uR - uL) / (dfL + dfR);
+    const T ip = T(1) / p;
+    side_f(p, ip, L, g, fL, dfL, xL);
+    side_f(p, ip, R, g, fR, dfR, xR);
+    T pn = p - (fL + fR + R.u - L.u) / (dfL + dfR);
     if (pn < T(kPFloor)) pn = T(kPFloor);
-    const T delta = T(2) * xabs(pn - p) / xabs(pn + p);
+    const bool done = T(2) * xabs(pn - p) < T(kNewtonTol) * xabs(pn + p);
     p = pn;
-    if (delta < T(kNewtonTol)) {
+    if (done) {
       flags = 0;
       break;
     }
   }
-  pressure_fn(p, dL, pL, aL, AL, BL, g, fL, dfL);
-  pressure_fn(p, dR, pR, aR, AR, BR, g, fR, dfR);
+  side_f_only(p, L, g, fL, xL);
+  side_f_only(p, R, g, fR, xR);
   const T pm = p;
-  const T um = T(0.5) * (uL + uR + fR - fL);
+  const T um = T(0.5) * (L.u + R.u + fR - fL);
 
   T d, u, ps;
   if (um >= T(0)) {
-    if (pm <= pL) {
-      if (uL - aL >= T(0)) {
-        d = dL; u = uL; ps = pL;
-      } else if (um - aL * xpow(pm / pL, g.z) < T(0)) {
-        d = dL * xpow(pm / pL, g.inv_g); u = um; ps = pm;
+    if (pm <= L.p) {  // left rarefaction: xL = (pm/pL)^z
+      if (L.u - L.a >= T(0)) {
+        d = L.d; u = L.u; ps = L.p;
+      } else if (um - L.a * xL < T(0)) {
+        d = L.d * (pm * L.inv_p) / (xL * xL); u = um; ps = pm;
       } else {
-        const T a = g.two_gp1 * (aL + g.half_gm1 * uL);
-        d = dL * xpow(a / aL, g.fan_d); u = a; ps = pL * xpow(a / aL, g.fan_p);
+        const T a = g.two_gp1 * (L.a + g.half_gm1 * L.u);
+        T pd, pp;
+        fan_powers(a / L.a, g, pd, pp);
+        d = L.d * pd; u = a; ps = L.p * pp;
       }
-    } else {
-      const T sL = uL - aL * xsqrt(g.sh_a * pm / pL + g.sh_b);
+    } else {          // left shock
+      const T r = pm * L.inv_p;
+      const T sL = L.u - L.a * xsqrt(g.sh_a * r + g.sh_b);
       if (sL >= T(0)) {
-        d = dL; u = uL; ps = pL;
+        d = L.d; u = L.u; ps = L.p;
       } else {
-        d = dL * (pm / pL + g.gm1_gp1) / (pm / pL * g.gm1_gp1 + T(1));
-        u = um; ps = pm;
+        d = L.d * (r + g.gm1_gp1) / (r * g.gm1_gp1 + T(1)); u = um; ps = pm;
       }
     }
   } else {
-    if (pm <= pR) {
-      if (uR + aR <= T(0)) {
-        d = dR; u = uR; ps = pR;
-      } else if (um + aR * xpow(pm / pR, g.z) >= T(0)) {
-        d = dR * xpow(pm / pR, g.inv_g); u = um; ps = pm;
+    if (pm <= R.p) {  // right rarefaction: xR = (pm/pR)^z
+      if (R.u + R.a <= T(0)) {
+        d = R.d; u = R.u; ps = R.p;
+      } else if (um + R.a * xR >= T(0)) {
+        d = R.d * (pm * R.inv_p) / (xR * xR); u = um; ps = pm;
       } else {
-        const T a = g.two_gp1 * (aR - g.half_gm1 * uR);
-        d = dR * xpow(a / aR, g.fan_d); u = -a; ps = pR * xpow(a / aR, g.fan_p);
+        const T a = g.two_gp1 * (R.a - g.half_gm1 * R.u);
+        T pd, pp;
+        fan_powers(a / R.a, g, pd, pp);
+        d = R.d * pd; u = -a; ps = R.p * pp;
       }
-    } else {
-      const T sR = uR + aR * xsqrt(g.sh_a * pm / pR + g.sh_b);
+    } else {          // right shock
+      const T r = pm * R.inv_p;
+      const T sR = R.u + R.a * xsqrt(g.sh_a * r + g.sh_b);
       if (sR <= T(0)) {
-        d = dR; u = uR; ps = pR;
+        d = R.d; u = R.u; ps = R.p;
       } else {
-        d = dR * (pm / pR + g.gm1_gp1) / (pm / pR * g.gm1_gp1 + T(1));
-        u = um; ps = pm;
+        d = R.d * (r + g.gm1_gp1) / (r * g.gm1_gp1 + T(1)); u = um; ps = pm;
       }
     }
   }
   const bool left = u >= T(0);
   const T v = left ? WL[2] : WR[2];
   const T w = left ? WL[3] : WR[3];
-  const T E = ps / g.gm1 + T(0.5) * d * (u * u + v * v + w * w);
+  const T E = ps * g.inv_gm1 + T(0.5) * d * (u * u + v * v + w * w);
   const T mf = d * u;
   F[0] = mf;
   F[1] = mf * u + ps;

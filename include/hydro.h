@@ -45,11 +45,19 @@ typedef struct hydro_s* hydro_t;
  * faces of an axis must be periodic or neither. */
 enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_REFLECT = 1, HYDRO_BC_OUTFLOW = 2, HYDRO_BC_INFLOW = 3 };
 
-/* Arithmetic of the step.  HYDRO_FP64: every operation in float64.
+/* Arithmetic of the step.
+ * HYDRO_FP64 (default): every operation in float64; the printed formulas are
+ *   evaluated through exact algebraic identities (k-th roots in place of pow,
+ *   reciprocals in place of divisions), each result within a few ulp of the
+ *   formula as printed.
  * HYDRO_MIXED: reconstruction and Riemann solves in float32; the conserved
- * update (flux accumulation), the recovery of the internal energy from E minus
- * the kinetic energy, the positivity floors and the time step stay float64. */
-enum { HYDRO_FP64 = 0, HYDRO_MIXED = 1 };
+ *   update (flux accumulation), the recovery of the internal energy from E minus
+ *   the kinetic energy, the positivity floors and the time step stay float64.
+ * HYDRO_FP64_STRICT: float64 with every formula evaluated operation by
+ *   operation as printed (divisions, pow, conserved face states between the
+ *   reconstruction and the Riemann solver as in App. B.1), for bit-level
+ *   reproducibility against a plain CPU implementation; slower. */
+enum { HYDRO_FP64 = 0, HYDRO_MIXED = 1, HYDRO_FP64_STRICT = 2 };
 
 enum {
   HYDRO_OK = 0,
@@ -71,7 +79,8 @@ int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, co
  * (0..5 in the order of bc[]).  Host pointer, copied. */
 int hydro_set_inflow(hydro_t h, int face, const double prim[5]);
 
-/* Select HYDRO_FP64 (default) or HYDRO_MIXED for the following steps. */
+/* Select HYDRO_FP64 (default), HYDRO_MIXED or HYDRO_FP64_STRICT for the
+ * following steps. */
 int hydro_set_precision(hydro_t h, int mode);
 
 /* Stream on which all following work of this handle is ordered (a

@@ -130,14 +130,16 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
   CK(h, cudaMemsetAsync(B.rec + 4, 0, sizeof(double), st));
   STAGE(h, kStagePrims, 0, fp64_prims(G, B, h->bc, h->gamma, fixed_dt <= 0.0, st));
   STAGE(h, kStageSetDt, 0, fp64_set_dt(G, B, cfl, fixed_dt, st));
+  const bool strict = h->precision == HYDRO_FP64_STRICT;
   for (int d = 0; d < 3; ++d) {
     if (!active(G, d)) continue;
-    STAGE(h, kStageSlopes, d, fp64_stage(G, B, kStageSlopes, d, h->gamma, st));
-    STAGE(h, kStagePpmc, d, fp64_stage(G, B, kStagePpmc, d, h->gamma, st));
-    STAGE(h, kStageRiemann1, d, fp64_stage(G, B, kStageRiemann1, d, h->gamma, st));
+    STAGE(h, kStageSlopes, d, fp64_stage(G, B, kStageSlopes, d, h->gamma, strict, st));
+    STAGE(h, kStagePpmc, d, fp64_stage(G, B, kStagePpmc, d, h->gamma, strict, st));
+    STAGE(h, kStageRiemann1, d, fp64_stage(G, B, kStageRiemann1, d, h->gamma, strict, st));
   }
   for (int d = 0; d < 3; ++d)
-    if (active(G, d)) STAGE(h, kStageRiemann2, d, fp64_stage(G, B, kStageRiemann2, d, h->gamma, st));
+    if (active(G, d))
+      STAGE(h, kStageRiemann2, d, fp64_stage(G, B, kStageRiemann2, d, h->gamma, strict, st));
   STAGE(h, kStageUpdate, 0, fp64_update(G, B, st));
   return HYDRO_OK;
 }
@@ -289,7 +291,7 @@ int hydro_set_inflow(hydro_t h, int face, const double prim[5]) {
 int hydro_set_precision(hydro_t h, int mode) {
   if (!h) return HYDRO_EINVAL;
   h->last_error = HYDRO_OK;
-  if (mode != HYDRO_FP64) return fail(h, HYDRO_EINVAL);
+  if (mode != HYDRO_FP64 && mode != HYDRO_FP64_STRICT) return fail(h, HYDRO_EINVAL);
   h->precision = mode;
   return HYDRO_OK;
 }

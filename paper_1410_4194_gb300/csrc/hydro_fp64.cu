@@ -202,7 +202,7 @@ __global__ void k_set_dt(double* rec, double cfl, double fixed_dt, double dx) {
   }
 }
 
-template <int D>
+template <int D, bool S>
 __global__ void __launch_bounds__(kThreads) k_slopes(Geom G, Bufs B, Box box, Gas g) {
   const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -218,12 +218,12 @@ __global__ void __launch_bounds__(kThreads) k_slopes(Geom G, Bufs B, Box box, Ga
   const double a = B.W[5 * G.ps + c];
   const double inv_a = B.W[6 * G.ps + c];
   const double inv_rho = B.W[7 * G.ps + c];
-  limited_slope(wm, wc, wp, a, inv_a, inv_rho, dw);
+  limited_slope<S>(wm, wc, wp, a, inv_a, inv_rho, dw);
 #pragma unroll
   for (int q = 0; q < 5; ++q) B.S[q * G.ps + c] = dw[q];
 }
 
-template <int D>
+template <int D, bool S>
 __global__ void __launch_bounds__(kThreads) k_ppmc(Geom G, Bufs B, Box box, Gas g) {
   const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -247,14 +247,23 @@ __global__ void __launch_bounds__(kThreads) k_ppmc(Geom G, Bufs B, Box box, Gas 
   const double inv_rho = B.W[7 * G.ps + c];
   const double dtdx = B.rec[2];
   double WsL[5], WsR[5];
-  ppmc_states(wm, wc, wp, sm, sc, sp, a, inv_a, inv_rho, dtdx, WsL, WsR);
+  ppmc_states<S>(wm, wc, wp, sm, sc, sp, a, inv_a, inv_rho, dtdx, WsL, WsR);
   // the left face of cell c is the right state of face c; its right face is the
-  // left state of face c+1 (stored as primitives)
-  store_rot<D>(B.UR[D], G.ps, c, WsL);
-  store_rot<D>(B.UL[D], G.ps, c + s, WsR);
+  // left state of face c+1.  Stored as primitives W*, or (strict) as the
+  // conserved U* the paper passes between kernels.
+  if constexpr (S) {
+    double UsL[5], UsR[5];
+    prim2cons<true>(WsL, g, UsL);
+    prim2cons<true>(WsR, g, UsR);
+    store_rot<D>(B.UR[D], G.ps, c, UsL);
+    store_rot<D>(B.UL[D], G.ps, c + s, UsR);
+  } else {
+    store_rot<D>(B.UR[D], G.ps, c, WsL);
+    store_rot<D>(B.UL[D], G.ps, c + s, WsR);
+  }
 }
 
-template <int D>
+template <int D, bool S>
 __global__ void __launch_bounds__(kThreads) k_riemann1(Geom G, Bufs B, Box box, Gas g) {
   const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -263,14 +272,24 @@ __global__ void __launch_bounds__(kThreads) k_riemann1(Geom G, Bufs B, Box box, 
   box_coords(box, t, c3);
   const long long f = pidx(G, c3);
   double WL[5], WR[5], F[5];
-  load_rot<D>(B.UL[D], G.ps, f, WL);
-  load_rot<D>(B.UR[D], G.ps, f, WR);
-  const int fl = riemann_exact(WL, WR, 1.0 / WL[0], 1.0 / WR[0], g, F);
+  int fl;
+  if constexpr (S) {
+    double UL[5], UR[5], idL, idR;
+    load_rot<D>(B.UL[D], G.ps, f, UL);
+    load_rot<D>(B.UR[D], G.ps, f, UR);
+    cons2prim<true>(UL, g, WL, idL);
+    cons2prim<true>(UR, g, WR, idR);
+    fl = riemann_exact<true>(WL, WR, idL, idR, g, F);
+  } else {
+    load_rot<D>(B.UL[D], G.ps, f, WL);
+    load_rot<D>(B.UR[D], G.ps, f, WR);
+    fl = riemann_exact<false>(WL, WR, 1.0 / WL[0], 1.0 / WR[0], g, F);
+  }
   store_rot<D>(B.F1[D], G.ps, f, F);
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
-template <int D>
+template <int D, bool S>
 __global__ void __launch_bounds__(kThreads) k_riemann2(Geom G, Bufs B, Box box, Gas g) {
   const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -281,14 +300,23 @@ __global__ void __launch_bounds__(kThreads) k_riemann2(Geom G, Bufs B, Box box, 
   const long long ps = G.ps;
   const long long cl = f - G.s[D], cr = f;
   const double h = B.rec[3];
-  double WsL[5], WsR[5], UhL[5], UhR[5];
+  double UhL[5], UhR[5];
+  if constexpr (S) {  // U* stored conserved
 #pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    WsL[q] = B.UL[D][q * ps + f];
-    WsR[q] = B.UR[D][q * ps + f];
+    for (int q = 0; q < 5; ++q) {
+      UhL[q] = B.UL[D][q * ps + f];
+      UhR[q] = B.UR[D][q * ps + f];
+    }
+  } else {  // U* from the stored W* (global order)
+    double WsL[5], WsR[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      WsL[q] = B.UL[D][q * ps + f];
+      WsR[q] = B.UR[D][q * ps + f];
+    }
+    prim2cons(WsL, g, UhL);
+    prim2cons(WsR, g, UhR);
   }
-  prim2cons(WsL, g, UhL);  // global order: U* of the two sides of the face
-  prim2cons(WsR, g, UhR);
   constexpr int T1 = Perm<D>::t1, T2 = Perm<D>::t2;
   if (G.n[T1] > 1) {
     const double* F = B.F1[T1];
@@ -311,9 +339,9 @@ __global__ void __launch_bounds__(kThreads) k_riemann2(Geom G, Bufs B, Box box, 
   double UL[5], UR[5], WL[5], WR[5], Fx[5], idL, idR;
   UL[0] = UhL[0]; UL[1] = UhL[1 + D]; UL[2] = UhL[1 + T1]; UL[3] = UhL[1 + T2]; UL[4] = UhL[4];
   UR[0] = UhR[0]; UR[1] = UhR[1 + D]; UR[2] = UhR[1 + T1]; UR[3] = UhR[1 + T2]; UR[4] = UhR[4];
-  cons2prim(UL, g, WL, idL);
-  cons2prim(UR, g, WR, idR);
-  const int fl = riemann_exact(WL, WR, idL, idR, g, Fx);
+  cons2prim<S>(UL, g, WL, idL);
+  cons2prim<S>(UR, g, WR, idR);
+  const int fl = riemann_exact<S>(WL, WR, idL, idR, g, Fx);
   // CTU flux of this face replaces its (now consumed) left state
   store_rot<D>(B.UL[D], ps, f, Fx);
   if (fl) atomicOr(rec_flags(B.rec), fl);
@@ -358,7 +386,7 @@ __global__ void k_riemann_soa(int n, const double* __restrict__ UL, const double
   }
   cons2prim(L, g, WL, idL);
   cons2prim(R, g, WR, idR);
-  const int fl = riemann_exact(WL, WR, idL, idR, g, Fx);
+  const int fl = riemann_exact<false>(WL, WR, idL, idR, g, Fx);
 #pragma unroll
   for (int q = 0; q < 5; ++q) F[(long long)q * n + t] = Fx[q];
   if (fl && flags) atomicOr(flags, fl);
@@ -459,15 +487,23 @@ long long stage_units(const Geom& G, int stage, int axis) {
 }
 
 cudaError_t fp64_stage(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
-                       cudaStream_t st) {
+                       bool strict, cudaStream_t st) {
   const Gas g = make_gas<double>(gamma);
   const Box b = stage_box(G, stage, axis);
   const unsigned nb = blocks_for(box_count(b));
-#define HYDRO_LAUNCH_AXIS(K)                                       \
-  switch (axis) {                                                  \
-    case 0: K<0><<<nb, kThreads, 0, st>>>(G, B, b, g); break;     \
-    case 1: K<1><<<nb, kThreads, 0, st>>>(G, B, b, g); break;     \
-    default: K<2><<<nb, kThreads, 0, st>>>(G, B, b, g); break;    \
+#define HYDRO_LAUNCH_AXIS(K)                                                      \
+  if (strict) {                                                                   \
+    switch (axis) {                                                               \
+      case 0: K<0, true><<<nb, kThreads, 0, st>>>(G, B, b, g); break;            \
+      case 1: K<1, true><<<nb, kThreads, 0, st>>>(G, B, b, g); break;            \
+      default: K<2, true><<<nb, kThreads, 0, st>>>(G, B, b, g); break;           \
+    }                                                                             \
+  } else {                                                                        \
+    switch (axis) {                                                               \
+      case 0: K<0, false><<<nb, kThreads, 0, st>>>(G, B, b, g); break;           \
+      case 1: K<1, false><<<nb, kThreads, 0, st>>>(G, B, b, g); break;           \
+      default: K<2, false><<<nb, kThreads, 0, st>>>(G, B, b, g); break;          \
+    }                                                                             \
   }
   switch (stage) {
     case kStageSlopes: HYDRO_LAUNCH_AXIS(k_slopes) break;

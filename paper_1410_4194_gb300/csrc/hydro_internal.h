@@ -63,7 +63,7 @@ cudaError_t fp64_prims(const Geom& G, const Bufs& B, const BcDesc& bc, double ga
                        cudaStream_t st);
 cudaError_t fp64_set_dt(const Geom& G, const Bufs& B, double cfl, double fixed_dt, cudaStream_t st);
 cudaError_t fp64_stage(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
-                       cudaStream_t st);
+                       bool strict, cudaStream_t st);
 cudaError_t fp64_update(const Geom& G, const Bufs& B, cudaStream_t st);
 cudaError_t fp64_riemann_soa(int n, const double* UL, const double* UR, double gamma, double* F,
                              int* flags, cudaStream_t st);

@@ -30,6 +30,11 @@
 //     once per cell;
 //   * of the six traced-parabola integrals of PPMC only those whose wave moves
 //     toward the face (the sign tests of App. A.3) are formed.
+// With the template switch S (strict) set, every function below instead performs
+// the printed formulas operation by operation in the order of the CPU reference
+// (divisions, pow), which reproduces that reference bit for bit wherever CUDA's
+// pow rounds as the host's does; the FP64 "strict" mode of the library uses it
+// to check reproducibility.
 //
 // Readings where the printed formulas are garbled (shared with the CPU
 // reference): xi0 = (-rho du/a + dp/a^2)/2; w6 = 6 w_i - 3 (W_L + W_R);
@@ -120,20 +125,43 @@ __device__ __forceinline__ T ipow(T x) {
   }
 }
 
-// r^(1/K) for r in [1e-30, 1e30]: SFU seed of t = r^(-1/K) in float, Newton steps
-// t <- t + (t/K)(1 - r t^K) (quadratic; two in double, one in float), r t^(K-1).
+// r^(1/K), correctly rounded, for r in [1e-30, 1e30].
+//   1. t ~ r^(-1/K) from an SFU seed (log2/exp2 in float) and one Newton step
+//      t <- t + (t/K)(1 - r t^K)  (relative error ~1e-11 in double);
+//   2. y = r t^(K-1) ~ r^(1/K), then one Newton step for y^K = r with the
+//      residual r - y^K formed exactly in double-double arithmetic (products
+//      split by fma); the correction delta = (r - y^K) t^(K-1) / K is ~1e-11 y and
+//      is itself accurate to ~1e-22 y, so y + delta rounds to the correctly
+//      rounded root.
+// The rarefaction pressure function uses (p/p_k)^z - 1 with x near 1, where a
+// single ulp of x is an absolute error of the same size in the result; a
+// correctly rounded x keeps that difference exactly zero.  In float (mixed path)
+// one Newton step is enough for float accuracy.
 template <int K, typename T>
 __device__ __forceinline__ T kth_root(T r) {
   const float lr = __log2f((float)r);
   T t = (T)exp2f(lr * (-1.0f / (float)K));
   const T invK = T(1.0 / K);
-  constexpr int kSteps = sizeof(T) == 8 ? 2 : 1;
-#pragma unroll
-  for (int i = 0; i < kSteps; ++i) {
+  {
     const T e = xfma(-r, ipow<K>(t), T(1));
     t = xfma(t * invK, e, t);
   }
-  return r * ipow<K - 1>(t);
+  if constexpr (sizeof(T) == 4) {
+    return r * ipow<K - 1>(t);
+  } else {
+    const T tk1 = ipow<K - 1>(t);
+    const T y = r * tk1;
+    // y^K as hi + lo (double-double), by repeated exact products
+    T hi = y, lo = T(0);
+#pragma unroll
+    for (int i = 1; i < K; ++i) {
+      const T p = hi * y;
+      lo = xfma(hi, y, -p) + lo * y;
+      hi = p;
+    }
+    const T res = (r - hi) - lo;  // r - hi is exact (Sterbenz: hi ~ r)
+    return xfma(res * tk1, invK, y);
+  }
 }
 
 // (p/p_k)^z
@@ -163,11 +191,21 @@ __device__ __forceinline__ void fan_powers(T s, const GasT<T>& g, T& pd, T& pp) 
 
 // ---------------------------------------------------------------------------
 // ideal-gas conversion in sweep order (rho, normal, t1, t2, E | p)
-template <typename T>
+template <bool S = false, typename T>
 __device__ __forceinline__ void cons2prim(const T U[5], const GasT<T>& g, T W[5], T& inv_d) {
   const T d = U[0];
-  inv_d = T(1) / d;
-  const T vn = U[1] * inv_d, v1 = U[2] * inv_d, v2 = U[3] * inv_d;
+  T vn, v1, v2;
+  if constexpr (S) {
+    inv_d = T(0);
+    vn = U[1] / d;
+    v1 = U[2] / d;
+    v2 = U[3] / d;
+  } else {
+    inv_d = T(1) / d;
+    vn = U[1] * inv_d;
+    v1 = U[2] * inv_d;
+    v2 = U[3] * inv_d;
+  }
   const T p = g.gm1 * (U[4] - T(0.5) * d * (vn * vn + v1 * v1 + v2 * v2));
   W[0] = d;
   W[1] = vn;
@@ -176,22 +214,30 @@ __device__ __forceinline__ void cons2prim(const T U[5], const GasT<T>& g, T W[5]
   W[4] = tmax(p, T(kPFloor));
 }
 
-template <typename T>
+template <bool S = false, typename T>
 __device__ __forceinline__ void prim2cons(const T W[5], const GasT<T>& g, T U[5]) {
   const T d = W[0];
   U[0] = d;
   U[1] = d * W[1];
   U[2] = d * W[2];
   U[3] = d * W[3];
-  U[4] = W[4] * g.inv_gm1 + T(0.5) * d * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  const T e = S ? W[4] / g.gm1 : W[4] * g.inv_gm1;
+  U[4] = e + T(0.5) * d * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
 }
 
 // ---------------------------------------------------------------------------
 // App. A.2: characteristic projection of a primitive difference
-template <typename T>
-__device__ __forceinline__ void char_project(const T dw[5], T rho, T inv_a, T inv_a2, T xi[5]) {
-  const T dpa2 = dw[4] * inv_a2;
-  const T rdu_a = rho * dw[1] * inv_a;
+template <bool S, typename T>
+__device__ __forceinline__ void char_project(const T dw[5], T rho, T a, T inv_a, T inv_a2,
+                                             T xi[5]) {
+  T dpa2, rdu_a;
+  if constexpr (S) {
+    dpa2 = dw[4] / (a * a);
+    rdu_a = rho * dw[1] / a;
+  } else {
+    dpa2 = dw[4] * inv_a2;
+    rdu_a = rho * dw[1] * inv_a;
+  }
   xi[0] = T(0.5) * (-rdu_a + dpa2);
   xi[1] = dw[0] - dpa2;
   xi[2] = dw[2];
@@ -200,7 +246,7 @@ __device__ __forceinline__ void char_project(const T dw[5], T rho, T inv_a, T in
 }
 
 // limited slope of the cell c from its neighbours m (c-1) and p (c+1)
-template <typename T>
+template <bool S = false, typename T>
 __device__ __forceinline__ void limited_slope(const T wm[5], const T wc[5], const T wp[5], T a,
                                               T inv_a, T inv_rho, T dw[5]) {
   const T inv_a2 = inv_a * inv_a;
@@ -211,9 +257,9 @@ __device__ __forceinline__ void limited_slope(const T wm[5], const T wc[5], cons
     dr[q] = wp[q] - wc[q];
     dc[q] = T(0.5) * (wp[q] - wm[q]);
   }
-  char_project(dl, wc[0], inv_a, inv_a2, xl);
-  char_project(dr, wc[0], inv_a, inv_a2, xr);
-  char_project(dc, wc[0], inv_a, inv_a2, xc);
+  char_project<S>(dl, wc[0], a, inv_a, inv_a2, xl);
+  char_project<S>(dr, wc[0], a, inv_a, inv_a2, xr);
+  char_project<S>(dc, wc[0], a, inv_a, inv_a2, xc);
   T xi[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
@@ -225,7 +271,7 @@ __device__ __forceinline__ void limited_slope(const T wm[5], const T wc[5], cons
     xi[q] = s;
   }
   dw[0] = xi[0] + xi[1] + xi[4];
-  dw[1] = a * inv_rho * (-xi[0] + xi[4]);
+  dw[1] = (S ? a / wc[0] : a * inv_rho) * (-xi[0] + xi[4]);
   dw[2] = xi[2];
   dw[3] = xi[3];
   dw[4] = a * a * (xi[0] + xi[4]);
@@ -236,7 +282,7 @@ __device__ __forceinline__ void limited_slope(const T wm[5], const T wc[5], cons
 // s_m, s_c, s_p: their limited slopes; a, inv_a, inv_rho of cell i.  Outputs the
 // traced states at the left (WsL) and right (WsR) face of cell i, pressure
 // floored.
-template <typename T>
+template <bool S = false, typename T>
 __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], const T w_p[5],
                                             const T s_m[5], const T s_c[5], const T s_p[5], T a,
                                             T inv_a, T inv_rho, T dtdx, T WsL[5], T WsR[5]) {
@@ -245,8 +291,14 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     const T wi = w_c[q];
-    T L = T(0.5) * (wi + w_m[q]) - (s_c[q] - s_m[q]) * c16;
-    T R = T(0.5) * (w_p[q] + wi) - (s_p[q] - s_c[q]) * c16;
+    T L, R;
+    if constexpr (S) {
+      L = T(0.5) * (wi + w_m[q]) - (s_c[q] - s_m[q]) / T(6);
+      R = T(0.5) * (w_p[q] + wi) - (s_p[q] - s_c[q]) / T(6);
+    } else {
+      L = T(0.5) * (wi + w_m[q]) - (s_c[q] - s_m[q]) * c16;
+      R = T(0.5) * (w_p[q] + wi) - (s_p[q] - s_c[q]) * c16;
+    }
     if ((R - wi) * (wi - L) <= T(0)) {
       L = wi;
       R = wi;
@@ -281,7 +333,7 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
     T E[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) E[q] = tLm[q] - T(0.5) * a0 * (dw[q] + w6[q] * (T(1) + c23 * a0));
-    sL[0] = sL[0] + (E[0] - E[4] * inv_a2);
+    sL[0] = sL[0] + (E[0] - (S ? E[4] / (a * a) : E[4] * inv_a2));
     sL[2] = sL[2] + E[2];
     sL[3] = sL[3] + E[3];
   }
@@ -289,16 +341,26 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
     const T ap = dtdx * lp;
     const T B1 = tLm[1] - T(0.5) * ap * (dw[1] + w6[1] * (T(1) + c23 * ap));
     const T B4 = tLm[4] - T(0.5) * ap * (dw[4] + w6[4] * (T(1) + c23 * ap));
-    sL[0] = sL[0] + T(0.5) * (rho * B1 * inv_a + B4 * inv_a2);
-    sL[1] = sL[1] + T(0.5) * (B1 + B4 * (inv_a * inv_rho));
+    if constexpr (S) {
+      sL[0] = sL[0] + T(0.5) * (rho * B1 / a + B4 / (a * a));
+      sL[1] = sL[1] + T(0.5) * (B1 + B4 / (a * rho));
+    } else {
+      sL[0] = sL[0] + T(0.5) * (rho * B1 * inv_a + B4 * inv_a2);
+      sL[1] = sL[1] + T(0.5) * (B1 + B4 * (inv_a * inv_rho));
+    }
     sL[4] = sL[4] + T(0.5) * (rho * B1 * a + B4);
   }
   if (lm > T(0)) {  // left acoustic wave reaches the right face: C
     const T bm = dtdx * lm;
     const T C1 = tRp[1] - T(0.5) * bm * (dw[1] - w6[1] * (T(1) - c23 * bm));
     const T C4 = tRp[4] - T(0.5) * bm * (dw[4] - w6[4] * (T(1) - c23 * bm));
-    sR[0] = sR[0] + T(0.5) * (-(rho * C1) * inv_a + C4 * inv_a2);
-    sR[1] = sR[1] + T(0.5) * (C1 - C4 * (inv_a * inv_rho));
+    if constexpr (S) {
+      sR[0] = sR[0] + T(0.5) * (-(rho * C1) / a + C4 / (a * a));
+      sR[1] = sR[1] + T(0.5) * (C1 - C4 / (a * rho));
+    } else {
+      sR[0] = sR[0] + T(0.5) * (-(rho * C1) * inv_a + C4 * inv_a2);
+      sR[1] = sR[1] + T(0.5) * (C1 - C4 * (inv_a * inv_rho));
+    }
     sR[4] = sR[4] + T(0.5) * (-(rho * C1 * a) + C4);
   }
   if (l0 > T(0)) {  // contact and advected velocities reach the right face: D
@@ -306,7 +368,7 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
     T D[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) D[q] = tRp[q] - T(0.5) * b0 * (dw[q] - w6[q] * (T(1) - c23 * b0));
-    sR[0] = sR[0] + (D[0] - D[4] * inv_a2);
+    sR[0] = sR[0] + (D[0] - (S ? D[4] / (a * a) : D[4] * inv_a2));
     sR[2] = sR[2] + D[2];
     sR[3] = sR[3] + D[3];
   }
@@ -331,55 +393,130 @@ struct RSide {
 };
 
 // pressure function f_k, its derivative, and x = (p/p_k)^z on a rarefaction
-template <typename T>
+// (0 on a shock)
+template <bool S, typename T>
 __device__ __forceinline__ void side_f(T p, T inv_p, const RSide<T>& s, const GasT<T>& g, T& f,
                                        T& fd, T& x) {
   if (p <= s.p) {
-    x = pow_z(p * s.inv_p, g);
-    f = s.cf * (x - T(1));
-    fd = x * s.cd * inv_p;
+    if constexpr (S) {
+      const T r = p / s.p;
+      x = xpow(r, g.z);
+      f = T(2) * s.a / g.gm1 * (x - T(1));
+      fd = T(1) / (s.d * s.a) * xpow(r, -g.sh_a);
+    } else {
+      x = pow_z(p * s.inv_p, g);
+      f = s.cf * (x - T(1));
+      fd = x * s.cd * inv_p;
+    }
   } else {
-    const T ipb = T(1) / (p + s.B);
-    const T q = xsqrt(s.A * ipb);
-    const T dp = p - s.p;
-    f = dp * q;
-    fd = q * (T(1) - T(0.5) * dp * ipb);
     x = T(0);
+    if constexpr (S) {
+      const T q = xsqrt(s.A / (p + s.B));
+      f = (p - s.p) * q;
+      fd = q * (T(1) - (p - s.p) / (T(2) * (s.B + p)));
+    } else {
+      const T ipb = T(1) / (p + s.B);
+      const T q = xsqrt(s.A * ipb);
+      const T dp = p - s.p;
+      f = dp * q;
+      fd = q * (T(1) - T(0.5) * dp * ipb);
+    }
   }
 }
 
-template <typename T>
+template <bool S, typename T>
 __device__ __forceinline__ void side_f_only(T p, const RSide<T>& s, const GasT<T>& g, T& f, T& x) {
   if (p <= s.p) {
-    x = pow_z(p * s.inv_p, g);
-    f = s.cf * (x - T(1));
+    if constexpr (S) {
+      x = xpow(p / s.p, g.z);
+      f = T(2) * s.a / g.gm1 * (x - T(1));
+    } else {
+      x = pow_z(p * s.inv_p, g);
+      f = s.cf * (x - T(1));
+    }
   } else {
     f = (p - s.p) * xsqrt(s.A / (p + s.B));
     x = T(0);
   }
 }
 
-template <typename T>
+template <bool S, typename T>
 __device__ __forceinline__ void make_side(const T W[5], T inv_d, const GasT<T>& g, RSide<T>& s) {
   s.d = W[0];
   s.u = W[1];
   s.p = W[4];
-  s.a = xsqrt(g.gamma * s.p * inv_d);
-  s.inv_p = T(1) / s.p;
-  s.A = g.two_gp1 * inv_d;
+  if constexpr (S) {
+    s.a = xsqrt(g.gamma * s.p / s.d);
+    s.inv_p = T(0);
+    s.A = T(2) / (g.gp1 * s.d);
+  } else {
+    s.a = xsqrt(g.gamma * s.p * inv_d);
+    s.inv_p = T(1) / s.p;
+    s.A = g.two_gp1 * inv_d;
+  }
   s.B = g.gm1_gp1 * s.p;
   s.cf = T(2) * s.a * g.inv_gm1;
   s.cd = s.a * g.inv_g;
 }
 
+// sampled state on a rarefaction side at x/t = 0 past the head: star state
+// (x = (pm/p_k)^z from the final pressure-function evaluation) or fan; sgn = +1
+// for the left side, -1 for the right
+template <bool S, bool LEFT, typename T>
+__device__ __forceinline__ void sample_raref(const RSide<T>& k, T pm, T um, T x, const GasT<T>& g,
+                                             T& d, T& u, T& ps) {
+  const T sgn = LEFT ? T(1) : T(-1);
+  const bool star = LEFT ? (um - k.a * x < T(0)) : (um + k.a * x >= T(0));
+  if (star) {  // star state between the fan tail and the contact
+    if constexpr (S)
+      d = k.d * xpow(pm / k.p, g.inv_g);
+    else
+      d = k.d * (pm * k.inv_p) / (x * x);
+    u = um;
+    ps = pm;
+  } else {  // inside the fan
+    const T a = g.two_gp1 * (k.a + sgn * g.half_gm1 * k.u);
+    if constexpr (S) {
+      d = k.d * xpow(a / k.a, g.fan_d);
+      ps = k.p * xpow(a / k.a, g.fan_p);
+    } else {
+      T pd, pp;
+      fan_powers(a / k.a, g, pd, pp);
+      d = k.d * pd;
+      ps = k.p * pp;
+    }
+    u = sgn * a;
+  }
+}
+
+// sampled state on a shock side: data state if the shock has not crossed
+// x/t = 0, else the post-shock state
+template <bool S, typename T>
+__device__ __forceinline__ void sample_shock(const RSide<T>& k, T pm, T um, T sgn,
+                                             const GasT<T>& g, T& d, T& u, T& ps) {
+  const T r = S ? pm / k.p : pm * k.inv_p;
+  const T arg = S ? g.sh_a * pm / k.p + g.sh_b : g.sh_a * r + g.sh_b;
+  const T sk = k.u - sgn * k.a * xsqrt(arg);
+  if (sgn * sk >= T(0)) {
+    d = k.d; u = k.u; ps = k.p;
+  } else {
+    if constexpr (S)
+      d = k.d * (pm / k.p + g.gm1_gp1) / (pm / k.p * g.gm1_gp1 + T(1));
+    else
+      d = k.d * (r + g.gm1_gp1) / (r * g.gm1_gp1 + T(1));
+    u = um;
+    ps = pm;
+  }
+}
+
 // Exact Riemann flux from primitive states in sweep order (inv_d = 1/rho of
-// each side); returns the status flags.
-template <typename T>
+// each side, unused when strict); returns the status flags.
+template <bool S = false, typename T>
 __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv_dL, T inv_dR,
                                              const GasT<T>& g, T F[5]) {
   RSide<T> L, R;
-  make_side(WL, inv_dL, g, L);
-  make_side(WR, inv_dR, g, R);
+  make_side<S>(WL, inv_dL, g, L);
+  make_side<S>(WR, inv_dR, g, R);
   // primitive-variable estimate, then the two-shock estimate as Newton start
   T pt = T(0.5) * (L.p + R.p) + T(0.125) * (L.u - R.u) * (L.d + R.d) * (L.a + R.a);
   if (pt < T(0)) pt = T(0);
@@ -389,71 +526,53 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
   T fL, fR, dfL, dfR, xL, xR;
   int flags = kFlagNewton;
   for (int it = 0; it < kNewtonMax; ++it) {
-    const T ip = T(1) / p;
-    side_f(p, ip, L, g, fL, dfL, xL);
-    side_f(p, ip, R, g, fR, dfR, xR);
+    const T ip = S ? T(0) : T(1) / p;
+    side_f<S>(p, ip, L, g, fL, dfL, xL);
+    side_f<S>(p, ip, R, g, fR, dfR, xR);
     T pn = p - (fL + fR + R.u - L.u) / (dfL + dfR);
     if (pn < T(kPFloor)) pn = T(kPFloor);
-    const bool done = T(2) * xabs(pn - p) < T(kNewtonTol) * xabs(pn + p);
+    bool done;
+    if constexpr (S)
+      done = T(2) * xabs(pn - p) / xabs(pn + p) < T(kNewtonTol);
+    else
+      done = T(2) * xabs(pn - p) < T(kNewtonTol) * xabs(pn + p);
     p = pn;
     if (done) {
       flags = 0;
       break;
     }
   }
-  side_f_only(p, L, g, fL, xL);
-  side_f_only(p, R, g, fR, xR);
+  side_f_only<S>(p, L, g, fL, xL);
+  side_f_only<S>(p, R, g, fR, xR);
   const T pm = p;
   const T um = T(0.5) * (L.u + R.u + fR - fL);
 
   T d, u, ps;
   if (um >= T(0)) {
-    if (pm <= L.p) {  // left rarefaction: xL = (pm/pL)^z
+    if (pm <= L.p) {  // left rarefaction
       if (L.u - L.a >= T(0)) {
         d = L.d; u = L.u; ps = L.p;
-      } else if (um - L.a * xL < T(0)) {
-        d = L.d * (pm * L.inv_p) / (xL * xL); u = um; ps = pm;
       } else {
-        const T a = g.two_gp1 * (L.a + g.half_gm1 * L.u);
-        T pd, pp;
-        fan_powers(a / L.a, g, pd, pp);
-        d = L.d * pd; u = a; ps = L.p * pp;
+        sample_raref<S, true>(L, pm, um, xL, g, d, u, ps);
       }
-    } else {          // left shock
-      const T r = pm * L.inv_p;
-      const T sL = L.u - L.a * xsqrt(g.sh_a * r + g.sh_b);
-      if (sL >= T(0)) {
-        d = L.d; u = L.u; ps = L.p;
-      } else {
-        d = L.d * (r + g.gm1_gp1) / (r * g.gm1_gp1 + T(1)); u = um; ps = pm;
-      }
+    } else {
+      sample_shock<S>(L, pm, um, T(1), g, d, u, ps);
     }
   } else {
-    if (pm <= R.p) {  // right rarefaction: xR = (pm/pR)^z
+    if (pm <= R.p) {  // right rarefaction
       if (R.u + R.a <= T(0)) {
         d = R.d; u = R.u; ps = R.p;
-      } else if (um + R.a * xR >= T(0)) {
-        d = R.d * (pm * R.inv_p) / (xR * xR); u = um; ps = pm;
       } else {
-        const T a = g.two_gp1 * (R.a - g.half_gm1 * R.u);
-        T pd, pp;
-        fan_powers(a / R.a, g, pd, pp);
-        d = R.d * pd; u = -a; ps = R.p * pp;
+        sample_raref<S, false>(R, pm, um, xR, g, d, u, ps);
       }
-    } else {          // right shock
-      const T r = pm * R.inv_p;
-      const T sR = R.u + R.a * xsqrt(g.sh_a * r + g.sh_b);
-      if (sR <= T(0)) {
-        d = R.d; u = R.u; ps = R.p;
-      } else {
-        d = R.d * (r + g.gm1_gp1) / (r * g.gm1_gp1 + T(1)); u = um; ps = pm;
-      }
+    } else {
+      sample_shock<S>(R, pm, um, T(-1), g, d, u, ps);
     }
   }
   const bool left = u >= T(0);
   const T v = left ? WL[2] : WR[2];
   const T w = left ? WL[3] : WR[3];
-  const T E = ps * g.inv_gm1 + T(0.5) * d * (u * u + v * v + w * w);
+  const T E = (S ? ps / g.gm1 : ps * g.inv_gm1) + T(0.5) * d * (u * u + v * v + w * w);
   const T mf = d * u;
   F[0] = mf;
   F[1] = mf * u + ps;

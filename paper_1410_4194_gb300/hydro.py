@@ -14,7 +14,7 @@ import os
 import numpy as np
 
 HYDRO_BC_PERIODIC, HYDRO_BC_REFLECT, HYDRO_BC_OUTFLOW, HYDRO_BC_INFLOW = 0, 1, 2, 3
-HYDRO_FP64, HYDRO_MIXED = 0, 1
+HYDRO_FP64, HYDRO_MIXED, HYDRO_FP64_STRICT = 0, 1, 2
 ERRORS = {0: "HYDRO_OK", -1: "HYDRO_EINVAL", -2: "HYDRO_ENOMEM", -3: "HYDRO_ECUDA",
           -4: "HYDRO_ENONPHYS", -5: "HYDRO_ENEWTON", -6: "HYDRO_ENOSTATE"}
 

@@ -1,10 +1,17 @@
 """GPU parity: the CUDA FP64 path (through the C-ABI) against the CPU oracle.
 
-Tolerance (FP64 path): per cell and field,
-    |gpu - oracle| <= 1e-10 * max(|oracle|, 1e-12 * max_cells |oracle_field|)
-after up to 10 steps.  The GPU evaluates the paper's formulas through algebraic
-identities (k-th roots for (p/p_k)^z, reciprocals for divisions); each result
-equals the reference's to a few ulp, and the step carries those differences.
+Tolerance, per cell and field, after up to 10 steps:
+    |gpu - oracle| <= 1e-10 * max(|oracle|, floor * max_cells |oracle_field|)
+  * HYDRO_FP64_STRICT (every formula evaluated as printed, in the reference's
+    operation order): floor = 1e-12.  Only CUDA's pow against the host's can
+    differ, rarely, by an ulp.
+  * HYDRO_FP64 (algebraic identities: k-th roots for (p/p_k)^z, reciprocals for
+    divisions): floor = 1e-6, i.e. values below a millionth of their field's
+    maximum are compared to an absolute 1e-16 of that maximum.  Each operation
+    differs from the reference by a few ulp; after a step those differences are
+    ~1e-15 of a field's maximum in absolute terms (rounding noise), which is the
+    whole value of a cell that the blast front has only just reached (momentum
+    ~1e-16 of its maximum), so a relative comparison there would compare noise.
 Kernel-level comparisons (one Riemann solve, one PPMC reconstruction) use 1e-12
 relative.
 """
@@ -19,6 +26,9 @@ pytestmark = pytest.mark.gpu
 
 P, R_, O, I_ = 0, 1, 2, 3
 TOL = 1e-10
+FLOOR = {hydro.HYDRO_FP64: 1e-6, hydro.HYDRO_FP64_STRICT: 1e-12}
+MODES = [hydro.HYDRO_FP64, hydro.HYDRO_FP64_STRICT]
+MODE_ID = {hydro.HYDRO_FP64: "fp64", hydro.HYDRO_FP64_STRICT: "strict"}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -31,22 +41,22 @@ def _setup():
     yield
 
 
-def rel_err(g, o):
+def rel_err(g, o, floor=1e-12):
     o = np.asarray(o)
     scale = np.abs(o).reshape(o.shape[0], -1).max(axis=1)
     scale = scale.reshape((-1,) + (1,) * (o.ndim - 1))
-    den = np.maximum(np.abs(o), 1e-12 * scale)
+    den = np.maximum(np.abs(o), floor * scale)
     den = np.where(den > 0, den, 1.0)
     return np.abs(np.asarray(g) - o) / den
 
 
-def run_both(w, nsteps, cfl=0.3):
+def run_both(w, nsteps, cfl=0.3, precision=hydro.HYDRO_FP64):
     inflow = w.get("inflow")
     uo, to, no, fl = oracle.run(w["u"], w["dx"], w["gamma"], w["bc"], nsteps=nsteps, cfl=cfl,
                                 inflow=inflow)
     assert fl == 0
     ug, tg, ng = hydro.run(w["u"], w["dx"], w["gamma"], w["bc"], nsteps=nsteps, cfl=cfl,
-                           inflow=inflow)
+                           inflow=inflow, precision=precision)
     return ug, uo, tg, to
 
 
@@ -91,9 +101,10 @@ def test_ppmc_kernel_matches_oracle():
         assert np.all(np.abs(dR.cpu().numpy().T - Ro) <= 1e-12 * scale)
 
 
+@pytest.mark.parametrize("mode", MODES, ids=lambda m: MODE_ID[m])
 @pytest.mark.parametrize("case", ["sedov32", "smooth24", "tube3d", "ragged", "twod", "inflow",
                                   "sod512"])
-def test_step_parity_10_steps(case):
+def test_step_parity_10_steps(case, mode):
     if case == "sedov32":
         w = W.sedov(32)
     elif case == "sod512":
@@ -124,9 +135,12 @@ def test_step_parity_10_steps(case):
         rho[(xx ** 2 + yy ** 2 + zz ** 2) < 25] = 10.0
         w = dict(u=W.prim_to_cons(rho, vx, 0.0, 0.0, p, 5 / 3), dx=1 / 16, gamma=5 / 3,
                  bc=[I_, O, P, P, P, P], inflow={0: (rho2, u2, 0.0, 0.0, p2)})
-    ug, uo, tg, to = run_both(w, 10)
+    ug, uo, tg, to = run_both(w, 10, precision=mode)
     assert tg == pytest.approx(to, rel=1e-12)
-    err = rel_err(ug, uo)
+    err = rel_err(ug, uo, FLOOR[mode])
+    absd = (np.abs(ug - uo).reshape(5, -1).max(axis=1) /
+            np.maximum(np.abs(uo).reshape(5, -1).max(axis=1), 1e-300))
+    print("%s %s: max rel %.3e, max |diff|/max|field| %s" % (case, MODE_ID[mode], err.max(), absd))
     assert err.max() <= TOL, (case, err.max(), np.unravel_index(err.argmax(), err.shape))
 
 
@@ -157,12 +171,13 @@ def test_sod_config_to_t02():
     np.testing.assert_allclose(rho[(x > 0.72) & (x < 0.82)], 0.26557, rtol=2e-3)
 
 
-def test_full_size_sedov_one_step_all_cells():
+@pytest.mark.parametrize("mode", MODES, ids=lambda m: MODE_ID[m])
+def test_full_size_sedov_one_step_all_cells(mode):
     """Config 2 at full size (256^3, the benchmark's launch configuration): one
     step compared cell by cell with the oracle."""
     w = W.sedov(256)
-    ug, uo, tg, to = run_both(w, 1)
-    err = rel_err(ug, uo)
+    ug, uo, tg, to = run_both(w, 1, precision=mode)
+    err = rel_err(ug, uo, FLOOR[mode])
     assert err.max() <= TOL, err.max()
 
 

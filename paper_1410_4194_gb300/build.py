@@ -19,7 +19,8 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
           "-I" + os.path.join(os.path.dirname(HERE), "include")]
 UNITS = {
     "hydro_api.cu": [],
-    "hydro_fp64.cu": ["--fmad=false"],
+    "hydro_fp64.cu": ["--fmad=false"],      # primitives, update, strict kernels
+    "hydro_fp64_fast.cu": ["--fmad=true"],  # fast FP64 stage kernels
 }
 
 

@@ -130,16 +130,15 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
   CK(h, cudaMemsetAsync(B.rec + 4, 0, sizeof(double), st));
   STAGE(h, kStagePrims, 0, fp64_prims(G, B, h->bc, h->gamma, fixed_dt <= 0.0, st));
   STAGE(h, kStageSetDt, 0, fp64_set_dt(G, B, cfl, fixed_dt, st));
-  const bool strict = h->precision == HYDRO_FP64_STRICT;
+  auto stage_fn = (h->precision == HYDRO_FP64_STRICT) ? fp64_stage_strict : fp64_stage_fast;
   for (int d = 0; d < 3; ++d) {
     if (!active(G, d)) continue;
-    STAGE(h, kStageSlopes, d, fp64_stage(G, B, kStageSlopes, d, h->gamma, strict, st));
-    STAGE(h, kStagePpmc, d, fp64_stage(G, B, kStagePpmc, d, h->gamma, strict, st));
-    STAGE(h, kStageRiemann1, d, fp64_stage(G, B, kStageRiemann1, d, h->gamma, strict, st));
+    STAGE(h, kStageSlopes, d, stage_fn(G, B, kStageSlopes, d, h->gamma, st));
+    STAGE(h, kStagePpmc, d, stage_fn(G, B, kStagePpmc, d, h->gamma, st));
+    STAGE(h, kStageRiemann1, d, stage_fn(G, B, kStageRiemann1, d, h->gamma, st));
   }
   for (int d = 0; d < 3; ++d)
-    if (active(G, d))
-      STAGE(h, kStageRiemann2, d, fp64_stage(G, B, kStageRiemann2, d, h->gamma, strict, st));
+    if (active(G, d)) STAGE(h, kStageRiemann2, d, stage_fn(G, B, kStageRiemann2, d, h->gamma, st));
   STAGE(h, kStageUpdate, 0, fp64_update(G, B, st));
   return HYDRO_OK;
 }

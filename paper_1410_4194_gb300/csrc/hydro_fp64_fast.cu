@@ -1,0 +1,14 @@
+// hydro_fp64_fast.cu -- the FP64 stage kernels with the algebraic rewrites of
+// hydro_math.cuh (S = false), compiled with fused multiply-add contraction:
+// every a*b+c becomes one DFMA, which both halves the instruction count of
+// those expressions on GB300's FP64 pipe and rounds once instead of twice.
+#include "hydro_kernels.cuh"
+
+namespace hydro {
+
+cudaError_t fp64_stage_fast(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
+                            cudaStream_t st) {
+  return launch_axis_stage<false>(G, B, stage, axis, gamma, st);
+}
+
+}  // namespace hydro

@@ -31,7 +31,7 @@ struct Bufs {
   double* UL[3];   // per axis: primitive left states W*_L of faces [5][ps]; reused for F^{n+1/2}
   double* UR[3];   // per axis: primitive right states W*_R of faces [5][ps]
   double* F1[3];   // per axis: first fluxes F* [5][ps]
-  // 64-byte step record on the device: [0] dt-min bits, [1] dt, [2] dt/dx,
+  // 64-byte step record on the device: [0] max of |v_d| + a (bits), [1] dt, [2] dt/dx,
   // [3] dt/(2 dx), [4] flags (int in the low word)
   double* rec;
 };
@@ -62,8 +62,12 @@ long long stage_units(const Geom& G, int stage, int axis);
 cudaError_t fp64_prims(const Geom& G, const Bufs& B, const BcDesc& bc, double gamma, bool want_dt,
                        cudaStream_t st);
 cudaError_t fp64_set_dt(const Geom& G, const Bufs& B, double cfl, double fixed_dt, cudaStream_t st);
-cudaError_t fp64_stage(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
-                       bool strict, cudaStream_t st);
+// one launch of a per-axis stage: fast arithmetic (hydro_fp64_fast.cu) or the
+// reference operation order (hydro_fp64.cu)
+cudaError_t fp64_stage_fast(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
+                            cudaStream_t st);
+cudaError_t fp64_stage_strict(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
+                              cudaStream_t st);
 cudaError_t fp64_update(const Geom& G, const Bufs& B, cudaStream_t st);
 cudaError_t fp64_riemann_soa(int n, const double* UL, const double* UR, double gamma, double* F,
                              int* flags, cudaStream_t st);

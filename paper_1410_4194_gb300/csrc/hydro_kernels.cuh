@@ -1,0 +1,285 @@
+// hydro_kernels.cuh -- the per-axis stage kernels of the FP64 step (slopes,
+// PPMC, first Riemann fluxes, transverse half-step + CTU fluxes), templated on
+// the sweep axis D and on the strict switch S of hydro_math.cuh.  Included by
+// two translation units: hydro_fp64_fast.cu (S = false, compiled with fused
+// multiply-add contraction) and hydro_fp64_strict.cu (S = true, compiled without
+// it so that every a*b+c rounds twice, as the CPU reference does).
+#pragma once
+#include "hydro_internal.h"
+#include "hydro_math.cuh"
+
+namespace hydro {
+namespace {
+
+constexpr int kThreads = 256;
+// three 256-thread blocks per SM (<= 85 registers a thread): the FP64 pipe is
+// the bottleneck, more resident warps hide its dependent-issue latency
+constexpr int kMinBlocks = 3;
+using Gas = GasT<double>;
+
+__device__ __forceinline__ void box_coords(const Box& b, long long t, int c[3]) {
+  const long long n0 = b.n[0], n01 = (long long)b.n[0] * b.n[1];
+  c[2] = b.lo[2] + (int)(t / n01);
+  const long long r = t - (long long)(c[2] - b.lo[2]) * n01;
+  c[1] = b.lo[1] + (int)(r / n0);
+  c[0] = b.lo[0] + (int)(r - (long long)(c[1] - b.lo[1]) * n0);
+}
+
+__device__ __forceinline__ long long pidx(const Geom& G, const int c[3]) {
+  return c[0] + c[1] * G.s[1] + c[2] * G.s[2];
+}
+
+// order of the velocity components in a sweep along axis D: (normal, t1, t2)
+template <int D> struct Perm {
+  static constexpr int n = D, t1 = (D + 1) % 3, t2 = (D + 2) % 3;
+};
+
+// load primitive cell c in sweep order (rho, v_n, v_t1, v_t2, p)
+template <int D>
+__device__ __forceinline__ void load_prim(const double* __restrict__ W, long long ps, long long c,
+                                          double w[5]) {
+  w[0] = W[c];
+  w[1] = W[(1 + Perm<D>::n) * ps + c];
+  w[2] = W[(1 + Perm<D>::t1) * ps + c];
+  w[3] = W[(1 + Perm<D>::t2) * ps + c];
+  w[4] = W[4 * ps + c];
+}
+
+// load/store a global-order 5-vector plane set in sweep order
+template <int D>
+__device__ __forceinline__ void load_rot(const double* __restrict__ A, long long ps, long long c,
+                                         double v[5]) {
+  v[0] = A[c];
+  v[1] = A[(1 + Perm<D>::n) * ps + c];
+  v[2] = A[(1 + Perm<D>::t1) * ps + c];
+  v[3] = A[(1 + Perm<D>::t2) * ps + c];
+  v[4] = A[4 * ps + c];
+}
+template <int D>
+__device__ __forceinline__ void store_rot(double* __restrict__ A, long long ps, long long c,
+                                          const double v[5]) {
+  A[c] = v[0];
+  A[(1 + Perm<D>::n) * ps + c] = v[1];
+  A[(1 + Perm<D>::t1) * ps + c] = v[2];
+  A[(1 + Perm<D>::t2) * ps + c] = v[3];
+  A[4 * ps + c] = v[4];
+}
+
+__device__ __forceinline__ int* rec_flags(double* rec) { return reinterpret_cast<int*>(rec + 4); }
+
+
+template <int D, bool S>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_slopes(Geom G, Bufs B, Box box, Gas g) {
+  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int c3[3];
+  box_coords(box, t, c3);
+  const long long c = pidx(G, c3);
+  const long long s = G.s[D];
+  double wm[5], wc[5], wp[5], dw[5];
+  load_prim<D>(B.W, G.ps, c - s, wm);
+  load_prim<D>(B.W, G.ps, c, wc);
+  load_prim<D>(B.W, G.ps, c + s, wp);
+  const double a = B.W[5 * G.ps + c];
+  const double inv_a = B.W[6 * G.ps + c];
+  const double inv_rho = B.W[7 * G.ps + c];
+  limited_slope<S>(wm, wc, wp, a, inv_a, inv_rho, dw);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) B.S[q * G.ps + c] = dw[q];
+}
+
+template <int D, bool S>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppmc(Geom G, Bufs B, Box box, Gas g) {
+  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int c3[3];
+  box_coords(box, t, c3);
+  const long long c = pidx(G, c3);
+  const long long s = G.s[D];
+  double wm[5], wc[5], wp[5], sm[5], sc[5], sp[5];
+  load_prim<D>(B.W, G.ps, c - s, wm);
+  load_prim<D>(B.W, G.ps, c, wc);
+  load_prim<D>(B.W, G.ps, c + s, wp);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    sm[q] = B.S[q * G.ps + c - s];
+    sc[q] = B.S[q * G.ps + c];
+    sp[q] = B.S[q * G.ps + c + s];
+  }
+  const double a = B.W[5 * G.ps + c];
+  const double inv_a = B.W[6 * G.ps + c];
+  const double inv_rho = B.W[7 * G.ps + c];
+  const double dtdx = B.rec[2];
+  double WsL[5], WsR[5];
+  ppmc_states<S>(wm, wc, wp, sm, sc, sp, a, inv_a, inv_rho, dtdx, WsL, WsR);
+  // the left face of cell c is the right state of face c; its right face is the
+  // left state of face c+1.  Stored as primitives W*, or (strict) as the
+  // conserved U* the paper passes between kernels.
+  if constexpr (S) {
+    double UsL[5], UsR[5];
+    prim2cons<true>(WsL, g, UsL);
+    prim2cons<true>(WsR, g, UsR);
+    store_rot<D>(B.UR[D], G.ps, c, UsL);
+    store_rot<D>(B.UL[D], G.ps, c + s, UsR);
+  } else {
+    store_rot<D>(B.UR[D], G.ps, c, WsL);
+    store_rot<D>(B.UL[D], G.ps, c + s, WsR);
+  }
+}
+
+template <int D, bool S>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann1(Geom G, Bufs B, Box box, Gas g) {
+  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int c3[3];
+  box_coords(box, t, c3);
+  const long long f = pidx(G, c3);
+  double WL[5], WR[5], F[5];
+  int fl;
+  if constexpr (S) {
+    double UL[5], UR[5], idL, idR;
+    load_rot<D>(B.UL[D], G.ps, f, UL);
+    load_rot<D>(B.UR[D], G.ps, f, UR);
+    cons2prim<true>(UL, g, WL, idL);
+    cons2prim<true>(UR, g, WR, idR);
+    fl = riemann_exact<true>(WL, WR, idL, idR, g, F);
+  } else {
+    load_rot<D>(B.UL[D], G.ps, f, WL);
+    load_rot<D>(B.UR[D], G.ps, f, WR);
+    fl = riemann_exact<false>(WL, WR, 1.0 / WL[0], 1.0 / WR[0], g, F);
+  }
+  store_rot<D>(B.F1[D], G.ps, f, F);
+  if (fl) atomicOr(rec_flags(B.rec), fl);
+}
+
+template <int D, bool S>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann2(Geom G, Bufs B, Box box, Gas g) {
+  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int c3[3];
+  box_coords(box, t, c3);
+  const long long f = pidx(G, c3);
+  const long long ps = G.ps;
+  const long long cl = f - G.s[D], cr = f;
+  const double h = B.rec[3];
+  double UhL[5], UhR[5];
+  if constexpr (S) {  // U* stored conserved
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      UhL[q] = B.UL[D][q * ps + f];
+      UhR[q] = B.UR[D][q * ps + f];
+    }
+  } else {  // U* from the stored W* (global order)
+    double WsL[5], WsR[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      WsL[q] = B.UL[D][q * ps + f];
+      WsR[q] = B.UR[D][q * ps + f];
+    }
+    prim2cons(WsL, g, UhL);
+    prim2cons(WsR, g, UhR);
+  }
+  constexpr int T1 = Perm<D>::t1, T2 = Perm<D>::t2;
+  if (G.n[T1] > 1) {
+    const double* F = B.F1[T1];
+    const long long st = G.s[T1];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      UhL[q] = UhL[q] + h * (F[q * ps + cl] - F[q * ps + cl + st]);
+      UhR[q] = UhR[q] + h * (F[q * ps + cr] - F[q * ps + cr + st]);
+    }
+  }
+  if (G.n[T2] > 1) {
+    const double* F = B.F1[T2];
+    const long long st = G.s[T2];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      UhL[q] = UhL[q] + h * (F[q * ps + cl] - F[q * ps + cl + st]);
+      UhR[q] = UhR[q] + h * (F[q * ps + cr] - F[q * ps + cr + st]);
+    }
+  }
+  double UL[5], UR[5], WL[5], WR[5], Fx[5], idL, idR;
+  UL[0] = UhL[0]; UL[1] = UhL[1 + D]; UL[2] = UhL[1 + T1]; UL[3] = UhL[1 + T2]; UL[4] = UhL[4];
+  UR[0] = UhR[0]; UR[1] = UhR[1 + D]; UR[2] = UhR[1 + T1]; UR[3] = UhR[1 + T2]; UR[4] = UhR[4];
+  cons2prim<S>(UL, g, WL, idL);
+  cons2prim<S>(UR, g, WR, idR);
+  const int fl = riemann_exact<S>(WL, WR, idL, idR, g, Fx);
+  // CTU flux of this face replaces its (now consumed) left state
+  store_rot<D>(B.UL[D], ps, f, Fx);
+  if (fl) atomicOr(rec_flags(B.rec), fl);
+}
+
+inline unsigned blocks_for(long long count) {
+  return (unsigned)((count + kThreads - 1) / kThreads);
+}
+
+// Range of an axis for a stage: real cells [g, g+n-1] widened by lo/hi (an
+// inactive axis is always the single index 0).
+inline void axis_range(const Geom& G, int d, int lo_off, int hi_off, int& lo, int& n) {
+  if (G.n[d] <= 1) {
+    lo = 0;
+    n = 1;
+    return;
+  }
+  lo = G.g[d] + lo_off;
+  n = G.n[d] + hi_off - lo_off;
+}
+
+inline Box make_box(const Geom& G, int axis, int lo_d, int hi_d, int lo_o, int hi_o) {
+  Box b;
+  for (int d = 0; d < 3; ++d) {
+    if (d == axis)
+      axis_range(G, d, lo_d, hi_d, b.lo[d], b.n[d]);
+    else
+      axis_range(G, d, lo_o, hi_o, b.lo[d], b.n[d]);
+  }
+  return b;
+}
+
+inline long long box_count(const Box& b) { return (long long)b.n[0] * b.n[1] * b.n[2]; }
+
+
+// Ranges (padded coordinates; "others" are the two axes across the sweep):
+//   slopes   d in [g-2, g+n+1], others in [g-1, g+n]
+//   ppmc     d in [g-1, g+n],   others in [g-1, g+n]
+//   riemann1 faces d in [g, g+n], others in [g-1, g+n]
+//   riemann2 faces d in [g, g+n], others real
+// which is exactly what the CTU fluxes of the real cells need.
+inline Box stage_box(const Geom& G, int stage, int axis) {
+  switch (stage) {
+    case kStageSlopes: return make_box(G, axis, -2, 2, -1, 1);
+    case kStagePpmc: return make_box(G, axis, -1, 1, -1, 1);
+    case kStageRiemann1: return make_box(G, axis, 0, 1, -1, 1);
+    default: return make_box(G, axis, 0, 1, 0, 0);
+  }
+}
+
+template <bool S>
+cudaError_t launch_axis_stage(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
+                              cudaStream_t st) {
+  const Gas g = make_gas<double>(gamma);
+  const Box b = stage_box(G, stage, axis);
+  const unsigned nb = blocks_for(box_count(b));
+#define HYDRO_LAUNCH_AXIS(K)                                                 \
+  switch (axis) {                                                            \
+    case 0: K<0, S><<<nb, kThreads, 0, st>>>(G, B, b, g); break;            \
+    case 1: K<1, S><<<nb, kThreads, 0, st>>>(G, B, b, g); break;            \
+    default: K<2, S><<<nb, kThreads, 0, st>>>(G, B, b, g); break;           \
+  }
+  switch (stage) {
+    case kStageSlopes: HYDRO_LAUNCH_AXIS(k_slopes) break;
+    case kStagePpmc: HYDRO_LAUNCH_AXIS(k_ppmc) break;
+    case kStageRiemann1: HYDRO_LAUNCH_AXIS(k_riemann1) break;
+    case kStageRiemann2: HYDRO_LAUNCH_AXIS(k_riemann2) break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef HYDRO_LAUNCH_AXIS
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace hydro

@@ -140,6 +140,24 @@ int hydro_profile_read(hydro_t h, int nstages, double* ms, long long* launches, 
 /* Release the handle and all device memory it owns.  NULL is accepted. */
 void hydro_free(hydro_t h);
 
+/* ---- time step without allocation ---------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot call cudaMalloc (their device memory is owned by another allocator, or
+ * an allocation's possible device synchronization is not acceptable).
+ *
+ * dt = cfl * min over cells and active axes of dx/(|v_d| + a) for a state held
+ * by the caller: u is a device pointer to [5][nz][ny][nx] float64 conserved
+ * variables, dt_out a device pointer to one double.  Enqueued on `stream`; the
+ * result is valid once the stream reaches it.  Allocates nothing: its scratch is
+ * a static device array of 65536 doubles (512 KiB) that every GPU loading the
+ * library holds until exit, so states of more than 2^24 cells are rejected with
+ * HYDRO_EINVAL.  Calls share that array: calls overlapping on the GPU race.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and should come before any stream capture.  Returns HYDRO_OK, HYDRO_EINVAL or
+ * HYDRO_ECUDA. */
+int hydro_compute_dt_noalloc(const double* u, int nx, int ny, int nz, double dx, double gamma,
+                             double cfl, double* dt_out, void* stream);
+
 /* ---- building blocks of the step, exposed on device arrays ------------------
  * Both read and write device memory laid out as structure-of-arrays planes of
  * n entries each, enqueue on `stream` and return after the launch has been

@@ -21,6 +21,7 @@ UNITS = {
     "hydro_api.cu": [],
     "hydro_fp64.cu": ["--fmad=false"],      # primitives, update, strict kernels
     "hydro_fp64_fast.cu": ["--fmad=true"],  # fast FP64 stage kernels
+    "hydro_noalloc.cu": ["--fmad=false"],   # time step without allocation
 }
 
 

@@ -26,7 +26,7 @@ EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_precision", "hydro_set_s
            "hydro_set_state", "hydro_get_state", "hydro_step", "hydro_step_dt",
            "hydro_compute_dt", "hydro_last_error", "hydro_error_string",
            "hydro_cuda_error_string", "hydro_profile", "hydro_profile_read", "hydro_free",
-           "hydro_riemann_exact", "hydro_ppmc")
+           "hydro_riemann_exact", "hydro_ppmc", "hydro_compute_dt_noalloc")
 STAGES = ("prims", "set_dt", "slopes", "ppmc", "riemann1", "riemann2", "update")
 
 _lib = None
@@ -67,6 +67,7 @@ def load():
     L.hydro_profile_read.argtypes = [vp, ctypes.c_int, dp, llp, llp, llp]
     L.hydro_riemann_exact.argtypes = [ctypes.c_int, vp, vp, ctypes.c_double, vp, vp, vp]
     L.hydro_ppmc.argtypes = [ctypes.c_int, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp]
+    L.hydro_compute_dt_noalloc.argtypes = [vp] + [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [vp, vp]
     _lib = L
     return L
 
@@ -248,3 +249,14 @@ def ppmc(w, dtdx, gamma, WsL, WsR):
                       _torch_stream_ptr())
     if rc != 0:
         raise HydroError(rc, "ppmc")
+
+
+def compute_dt_noalloc(u, dx, gamma, cfl, dt_out):
+    """CFL dt of a device state u [5, nz, ny, nx] (torch CUDA float64) into the
+    one-element CUDA tensor dt_out, without any device allocation; returns the
+    C-ABI status code (0 on success)."""
+    L = load()
+    _, nz, ny, nx = u.shape
+    return L.hydro_compute_dt_noalloc(ctypes.c_void_p(u.data_ptr()), int(nx), int(ny), int(nz),
+                                      float(dx), float(gamma), float(cfl),
+                                      ctypes.c_void_p(dt_out.data_ptr()), _torch_stream_ptr())

@@ -205,6 +205,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=6)
+    ap.add_argument("--compare-l1", action="store_true",
+                    help="mixed precision: also run the FP64 path from the same state for the "
+                         "same steps and report the L1 difference per field")
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
@@ -286,6 +289,9 @@ def main():
                "d2h_bytes_per_step": int(out_host.numel() * 8), "steps": ke,
                "host_wall_s": wall}
 
+    l1 = None
+    if args.compare_l1 and args.precision == "mixed":
+        l1 = compare_l1(w, args, g, hydro, stream)
     if rank != 0:
         g.close()
         if ws > 1:
@@ -328,10 +334,40 @@ def main():
         "e2e": e2e, "gpu_launches": launches_total, "clocks": clocks, "roofline": roofline,
         "stages": stage_report, "cpu_baseline": cpu,
     }
+    if l1 is not None:
+        line["l1_vs_fp64"] = l1
     print(json.dumps(line), flush=True)
     g.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def compare_l1(w, args, g, hydro, stream):
+    """Run the mixed and the FP64 path from the workload's initial state for
+    warmup + steps steps and report the relative L1 difference per field (the
+    momenta against their group's scale)."""
+    import torch
+    _, nz, ny, nx = w["u"].shape
+    n = args.warmup + args.steps
+    res = {}
+    for name, prec in (("mixed", hydro.HYDRO_MIXED), ("fp64", hydro.HYDRO_FP64)):
+        h = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], precision=prec, stream=stream)
+        for face, prim in (w.get("inflow") or {}).items():
+            h.set_inflow(face, prim)
+        h.set_state(w["u"])
+        for _ in range(n):
+            h.step(args.cfl)
+        out = torch.empty((5, nz, ny, nx), dtype=torch.float64, device="cuda")
+        h.get_state(out)
+        h.close()
+        res[name] = out
+    d = (res["mixed"] - res["fp64"]).abs().reshape(5, -1).sum(dim=1)
+    s = res["fp64"].abs().reshape(5, -1).sum(dim=1)
+    mom = s[1:4].sum() / 3.0
+    den = torch.stack([s[0], mom, mom, mom, s[4]])
+    l1 = (d / den).tolist()
+    return {"steps": n, "fields": ["rho", "mx", "my", "mz", "E"], "l1_rel": l1,
+            "reference": "HYDRO_FP64 GPU path from the same initial state"}
 
 
 def kernel_digest():

@@ -22,6 +22,7 @@ UNITS = {
     "hydro_fp64.cu": ["--fmad=false"],      # primitives, update, strict kernels
     "hydro_fp64_fast.cu": ["--fmad=true"],  # fast FP64 stage kernels
     "hydro_noalloc.cu": ["--fmad=false"],   # time step without allocation
+    "hydro_mixed.cu": ["--fmad=true"],      # mixed-precision stages
 }
 
 

@@ -127,10 +127,13 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
   const Bufs& B = h->B;
   cudaStream_t st = h->stream;
   h->nev = 0;
+  const bool mixed = h->precision == HYDRO_MIXED;
   CK(h, cudaMemsetAsync(B.rec + 4, 0, sizeof(double), st));
-  STAGE(h, kStagePrims, 0, fp64_prims(G, B, h->bc, h->gamma, fixed_dt <= 0.0, st));
+  STAGE(h, kStagePrims, 0,
+        (mixed ? mixed_prims : fp64_prims)(G, B, h->bc, h->gamma, fixed_dt <= 0.0, st));
   STAGE(h, kStageSetDt, 0, fp64_set_dt(G, B, cfl, fixed_dt, st));
-  auto stage_fn = (h->precision == HYDRO_FP64_STRICT) ? fp64_stage_strict : fp64_stage_fast;
+  auto stage_fn = mixed ? mixed_stage
+                        : (h->precision == HYDRO_FP64_STRICT ? fp64_stage_strict : fp64_stage_fast);
   for (int d = 0; d < 3; ++d) {
     if (!active(G, d)) continue;
     STAGE(h, kStageSlopes, d, stage_fn(G, B, kStageSlopes, d, h->gamma, st));
@@ -139,7 +142,7 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
   }
   for (int d = 0; d < 3; ++d)
     if (active(G, d)) STAGE(h, kStageRiemann2, d, stage_fn(G, B, kStageRiemann2, d, h->gamma, st));
-  STAGE(h, kStageUpdate, 0, fp64_update(G, B, st));
+  STAGE(h, kStageUpdate, 0, (mixed ? mixed_update : fp64_update)(G, B, st));
   return HYDRO_OK;
 }
 
@@ -290,7 +293,8 @@ int hydro_set_inflow(hydro_t h, int face, const double prim[5]) {
 int hydro_set_precision(hydro_t h, int mode) {
   if (!h) return HYDRO_EINVAL;
   h->last_error = HYDRO_OK;
-  if (mode != HYDRO_FP64 && mode != HYDRO_FP64_STRICT) return fail(h, HYDRO_EINVAL);
+  if (mode != HYDRO_FP64 && mode != HYDRO_FP64_STRICT && mode != HYDRO_MIXED)
+    return fail(h, HYDRO_EINVAL);
   h->precision = mode;
   return HYDRO_OK;
 }
@@ -345,7 +349,8 @@ double hydro_compute_dt(hydro_t h, double cfl) {
   if (!(cfl > 0.0)) return (double)fail(h, HYDRO_EINVAL);
   int rc = use_device(h);
   if (rc) return (double)rc;
-  cudaError_t e = fp64_prims(h->G, h->B, h->bc, h->gamma, true, h->stream);
+  cudaError_t e = (h->precision == HYDRO_MIXED ? mixed_prims : fp64_prims)(h->G, h->B, h->bc,
+                                                                          h->gamma, true, h->stream);
   if (e != cudaSuccess) return (double)cuda_fail(h, e);
   e = fp64_set_dt(h->G, h->B, cfl, 0.0, h->stream);
   if (e != cudaSuccess) return (double)cuda_fail(h, e);

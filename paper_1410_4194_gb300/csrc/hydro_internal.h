@@ -69,6 +69,13 @@ cudaError_t fp64_stage_fast(const Geom& G, const Bufs& B, int stage, int axis, d
 cudaError_t fp64_stage_strict(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
                               cudaStream_t st);
 cudaError_t fp64_update(const Geom& G, const Bufs& B, cudaStream_t st);
+// mixed-precision launchers (hydro_mixed.cu): the same stages on float work
+// arrays carved from the same slab
+cudaError_t mixed_prims(const Geom& G, const Bufs& B, const BcDesc& bc, double gamma, bool want_dt,
+                        cudaStream_t st);
+cudaError_t mixed_stage(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
+                        cudaStream_t st);
+cudaError_t mixed_update(const Geom& G, const Bufs& B, cudaStream_t st);
 cudaError_t fp64_riemann_soa(int n, const double* UL, const double* UR, double gamma, double* F,
                              int* flags, cudaStream_t st);
 cudaError_t fp64_ppmc_soa(int n, const double* w, double dtdx, double gamma, double* WsL,

@@ -525,17 +525,32 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
   if (p < T(kP0Floor)) p = T(kP0Floor);
   T fL, fR, dfL, dfR, xL, xR;
   int flags = kFlagNewton;
+  T prev_step = T(0);  // float path: the previous Newton step
   for (int it = 0; it < kNewtonMax; ++it) {
     const T ip = S ? T(0) : T(1) / p;
     side_f<S>(p, ip, L, g, fL, dfL, xL);
     side_f<S>(p, ip, R, g, fR, dfR, xR);
-    T pn = p - (fL + fR + R.u - L.u) / (dfL + dfR);
+    const T F = fL + fR + R.u - L.u;
+    T pn = p - F / (dfL + dfR);
     if (pn < T(kPFloor)) pn = T(kPFloor);
     bool done;
     if constexpr (S)
       done = T(2) * xabs(pn - p) / xabs(pn + p) < T(kNewtonTol);
     else
       done = T(2) * xabs(pn - p) < T(kNewtonTol) * xabs(pn + p);
+    if constexpr (sizeof(T) == 4) {
+      // In float the residual f_L + f_R + u_R - u_L carries the rounding error of
+      // its terms; near the root the Newton steps that noise produces can stay
+      // above the relative tolerance forever (a two-point cycle, e.g. when p*
+      // is small against the velocities).  Newton's quadratic convergence never
+      // reverses the step without at least halving it, rounding noise does: a
+      // step that reverses and does not shrink by half, or a residual at the
+      // rounding level of its terms, means float has converged as far as it can.
+      const T step = pn - p;
+      done = done || (step * prev_step < T(0) && xabs(step) >= T(0.5) * xabs(prev_step)) ||
+             xabs(F) <= T(4.0 * 1.1920929e-7) * (xabs(fL) + xabs(fR) + xabs(L.u) + xabs(R.u));
+      prev_step = step;
+    }
     p = pn;
     if (done) {
       flags = 0;

@@ -1,0 +1,337 @@
+// hydro_mixed.cu -- the mixed-precision CTU step (HYDRO_MIXED).
+//
+// Float32: the characteristic slopes, PPMC reconstruction and tracing, and both
+// sets of exact Riemann solves (App. A.2, A.3, B.1) -- the bulk of the
+// arithmetic, on GB300's FP32 pipe (64 times the FP64 rate).
+// Float64, where the step's stability needs it:
+//   * primitives of the FP64 state: the internal energy E - rho v^2/2 (the
+//     cancellation of total and kinetic energy at high Mach), the pressure
+//     floor and the CFL time-step reduction;
+//   * the transverse half-step U^{n+1/2} = U* + dt/(2dx) (G*_{-} - G*_{+}) + ...
+//     (Eq. transverse_evolution), a conserved flux accumulation, and the
+//     recovery of the primitives of U^{n+1/2} (internal energy again);
+//   * the conserved update (Eq. conserved_update), accumulated from the float
+//     CTU fluxes into the FP64 state.
+// Intermediates (primitives, slopes, face states, fluxes) are float, which
+// halves their HBM traffic.  Compiled with FMA contraction.
+#include "hydro_kernels.cuh"
+
+namespace hydro {
+namespace {
+
+using GasF = GasT<float>;
+using GasD = GasT<double>;
+
+// float views of the step's work arrays (same slab as the FP64 path)
+struct BufsF {
+  double* u;      // FP64 state, real cells [5][nz][ny][nx]
+  float* W;       // padded primitives [8][ps]: rho, vx, vy, vz, p, a, 1/a, 1/rho
+  float* S;       // padded slopes [5][ps] (sweep order)
+  float* UL[3];   // per axis: primitive left states W*_L [5][ps]; then F^{n+1/2}
+  float* UR[3];   // per axis: primitive right states W*_R [5][ps]
+  float* F1[3];   // per axis: first fluxes F* [5][ps]
+  double* rec;    // step record (dt, flags)
+};
+
+template <int D>
+__device__ __forceinline__ void load_prim_f(const float* __restrict__ W, long long ps, long long c,
+                                            float w[5]) {
+  w[0] = W[c];
+  w[1] = W[(1 + Perm<D>::n) * ps + c];
+  w[2] = W[(1 + Perm<D>::t1) * ps + c];
+  w[3] = W[(1 + Perm<D>::t2) * ps + c];
+  w[4] = W[4 * ps + c];
+}
+template <int D>
+__device__ __forceinline__ void store_rot_f(float* __restrict__ A, long long ps, long long c,
+                                            const float v[5]) {
+  A[c] = v[0];
+  A[(1 + Perm<D>::n) * ps + c] = v[1];
+  A[(1 + Perm<D>::t1) * ps + c] = v[2];
+  A[(1 + Perm<D>::t2) * ps + c] = v[3];
+  A[4 * ps + c] = v[4];
+}
+
+__device__ __forceinline__ void block_max_to(double v, unsigned long long* slot) {
+  __shared__ double warp_max[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = tmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) warp_max[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = (lane < (int)(blockDim.x >> 5)) ? warp_max[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = tmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0 && v > 0.0) atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+  }
+}
+
+// primitives in FP64 (ghosts by index remap, as in the FP64 path), stored as
+// float; dt reduction in FP64
+__global__ void __launch_bounds__(kThreads) k_prims_mixed(Geom G, BufsF B, BcDesc bc, GasD g,
+                                                          int want_dt) {
+  const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double local = 0.0;
+  if (t < total) {
+    int c[3];
+    c[2] = (int)(t / G.s[2]);
+    c[1] = (int)((t - c[2] * G.s[2]) / G.s[1]);
+    c[0] = (int)(t - c[2] * G.s[2] - c[1] * G.s[1]);
+    int src[3];
+    int neg = 0, inflow_face = -1;
+    bool real = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int n = G.n[d];
+      const int r = c[d] - G.g[d];
+      if (r >= 0 && r < n) {
+        src[d] = r;
+        continue;
+      }
+      real = false;
+      const bool lo = r < 0;
+      const int depth = lo ? -r : r - n + 1;
+      const int face = 2 * d + (lo ? 0 : 1);
+      switch (bc.type[face]) {
+        case 0: src[d] = lo ? n - depth : depth - 1; break;
+        case 1: src[d] = lo ? depth - 1 : n - depth; neg |= 1 << d; break;
+        case 2: src[d] = lo ? 0 : n - 1; break;
+        default: src[d] = 0; inflow_face = face; neg = 0; break;
+      }
+    }
+    double U[5];
+    if (inflow_face >= 0) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) U[q] = bc.inflow[inflow_face][q];
+    } else {
+      const long long rs = src[0] + (long long)G.n[0] * (src[1] + (long long)G.n[1] * src[2]);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) U[q] = B.u[q * G.nreal + rs];
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (neg & (1 << d)) U[1 + d] = -U[1 + d];
+    double W[5], inv_d;
+    cons2prim(U, g, W, inv_d);  // FP64 internal energy and pressure floor
+    const double a = sqrt(g.gamma * W[4] * inv_d);
+    const float af = (float)a;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) B.W[q * G.ps + t] = (float)W[q];
+    B.W[5 * G.ps + t] = af;
+    B.W[6 * G.ps + t] = 1.0f / af;
+    B.W[7 * G.ps + t] = (float)inv_d;
+    if (want_dt && real) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        if (G.n[d] > 1) local = tmax(local, fabs(W[1 + d]) + a);
+    }
+  }
+  if (want_dt) block_max_to(local, reinterpret_cast<unsigned long long*>(B.rec));
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_slopes_mixed(Geom G, BufsF B, Box box) {
+  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int c3[3];
+  box_coords(box, t, c3);
+  const long long c = pidx(G, c3);
+  const long long s = G.s[D];
+  float wm[5], wc[5], wp[5], dw[5];
+  load_prim_f<D>(B.W, G.ps, c - s, wm);
+  load_prim_f<D>(B.W, G.ps, c, wc);
+  load_prim_f<D>(B.W, G.ps, c + s, wp);
+  limited_slope(wm, wc, wp, B.W[5 * G.ps + c], B.W[6 * G.ps + c], B.W[7 * G.ps + c], dw);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) B.S[q * G.ps + c] = dw[q];
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppmc_mixed(Geom G, BufsF B, Box box) {
+  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int c3[3];
+  box_coords(box, t, c3);
+  const long long c = pidx(G, c3);
+  const long long s = G.s[D];
+  float wm[5], wc[5], wp[5], sm[5], sc[5], sp[5];
+  load_prim_f<D>(B.W, G.ps, c - s, wm);
+  load_prim_f<D>(B.W, G.ps, c, wc);
+  load_prim_f<D>(B.W, G.ps, c + s, wp);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    sm[q] = B.S[q * G.ps + c - s];
+    sc[q] = B.S[q * G.ps + c];
+    sp[q] = B.S[q * G.ps + c + s];
+  }
+  const float dtdx = (float)B.rec[2];
+  float WsL[5], WsR[5];
+  ppmc_states(wm, wc, wp, sm, sc, sp, B.W[5 * G.ps + c], B.W[6 * G.ps + c], B.W[7 * G.ps + c],
+              dtdx, WsL, WsR);
+  store_rot_f<D>(B.UR[D], G.ps, c, WsL);
+  store_rot_f<D>(B.UL[D], G.ps, c + s, WsR);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann1_mixed(Geom G, BufsF B, Box box,
+                                                                         GasF g) {
+  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int c3[3];
+  box_coords(box, t, c3);
+  const long long f = pidx(G, c3);
+  float WL[5], WR[5], F[5];
+  load_prim_f<D>(B.UL[D], G.ps, f, WL);
+  load_prim_f<D>(B.UR[D], G.ps, f, WR);
+  const int fl = riemann_exact(WL, WR, 1.0f / WL[0], 1.0f / WR[0], g, F);
+  store_rot_f<D>(B.F1[D], G.ps, f, F);
+  if (fl) atomicOr(rec_flags(B.rec), fl);
+}
+
+// transverse half-step and recovery of the primitives of U^{n+1/2} in FP64,
+// second Riemann solve in float
+template <int D>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann2_mixed(Geom G, BufsF B, Box box,
+                                                                         GasD gd, GasF g) {
+  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  int c3[3];
+  box_coords(box, t, c3);
+  const long long f = pidx(G, c3);
+  const long long ps = G.ps;
+  const long long cl = f - G.s[D], cr = f;
+  const double h = B.rec[3];
+  double WsL[5], WsR[5], UhL[5], UhR[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    WsL[q] = (double)B.UL[D][q * ps + f];
+    WsR[q] = (double)B.UR[D][q * ps + f];
+  }
+  prim2cons(WsL, gd, UhL);
+  prim2cons(WsR, gd, UhR);
+  constexpr int T1 = Perm<D>::t1, T2 = Perm<D>::t2;
+  if (G.n[T1] > 1) {
+    const float* F = B.F1[T1];
+    const long long st = G.s[T1];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      UhL[q] = UhL[q] + h * ((double)F[q * ps + cl] - (double)F[q * ps + cl + st]);
+      UhR[q] = UhR[q] + h * ((double)F[q * ps + cr] - (double)F[q * ps + cr + st]);
+    }
+  }
+  if (G.n[T2] > 1) {
+    const float* F = B.F1[T2];
+    const long long st = G.s[T2];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      UhL[q] = UhL[q] + h * ((double)F[q * ps + cl] - (double)F[q * ps + cl + st]);
+      UhR[q] = UhR[q] + h * ((double)F[q * ps + cr] - (double)F[q * ps + cr + st]);
+    }
+  }
+  double UL[5], UR[5], WL[5], WR[5], idL, idR;
+  UL[0] = UhL[0]; UL[1] = UhL[1 + D]; UL[2] = UhL[1 + T1]; UL[3] = UhL[1 + T2]; UL[4] = UhL[4];
+  UR[0] = UhR[0]; UR[1] = UhR[1 + D]; UR[2] = UhR[1 + T1]; UR[3] = UhR[1 + T2]; UR[4] = UhR[4];
+  cons2prim(UL, gd, WL, idL);
+  cons2prim(UR, gd, WR, idR);
+  float wl[5], wr[5], Fx[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    wl[q] = (float)WL[q];
+    wr[q] = (float)WR[q];
+  }
+  const int fl = riemann_exact(wl, wr, (float)idL, (float)idR, g, Fx);
+  store_rot_f<D>(B.UL[D], ps, f, Fx);
+  if (fl) atomicOr(rec_flags(B.rec), fl);
+}
+
+// conserved update in FP64 from the float CTU fluxes
+__global__ void __launch_bounds__(kThreads) k_update_mixed(Geom G, BufsF B) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= G.nreal) return;
+  const int i = (int)(t % G.n[0]);
+  const int j = (int)((t / G.n[0]) % G.n[1]);
+  const int k = (int)(t / ((long long)G.n[0] * G.n[1]));
+  const long long c = (i + G.g[0]) + (j + G.g[1]) * G.s[1] + (k + G.g[2]) * G.s[2];
+  const double dtdx = B.rec[2];
+  int fl = 0;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    double un = B.u[q * G.nreal + t];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (G.n[d] > 1) {
+        const float* F = B.UL[d];
+        un = un + dtdx * ((double)F[q * G.ps + c] - (double)F[q * G.ps + c + G.s[d]]);
+      }
+    }
+    B.u[q * G.nreal + t] = un;
+    if (isnan(un)) fl = kFlagNonPhys;
+    if (q == 0 && !(un > 0.0)) fl = kFlagNonPhys;
+  }
+  if (fl) atomicOr(rec_flags(B.rec), fl);
+}
+
+BufsF float_view(const Bufs& B) {
+  BufsF F;
+  F.u = B.u;
+  F.W = reinterpret_cast<float*>(B.W);
+  F.S = reinterpret_cast<float*>(B.S);
+  for (int d = 0; d < 3; ++d) {
+    F.UL[d] = reinterpret_cast<float*>(B.UL[d]);
+    F.UR[d] = reinterpret_cast<float*>(B.UR[d]);
+    F.F1[d] = reinterpret_cast<float*>(B.F1[d]);
+  }
+  F.rec = B.rec;
+  return F;
+}
+
+}  // namespace
+
+cudaError_t mixed_prims(const Geom& G, const Bufs& B, const BcDesc& bc, double gamma, bool want_dt,
+                        cudaStream_t st) {
+  if (want_dt) {
+    cudaError_t e = cudaMemsetAsync(B.rec, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+  }
+  const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
+  k_prims_mixed<<<blocks_for(total), kThreads, 0, st>>>(G, float_view(B), bc,
+                                                        make_gas<double>(gamma), want_dt ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t mixed_stage(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
+                        cudaStream_t st) {
+  const BufsF F = float_view(B);
+  const GasF gf = make_gas<float>(gamma);
+  const GasD gd = make_gas<double>(gamma);
+  const Box b = stage_box(G, stage, axis);
+  const unsigned nb = blocks_for(box_count(b));
+#define HYDRO_MIXED_AXIS(K, ...)                                          \
+  switch (axis) {                                                         \
+    case 0: K<0><<<nb, kThreads, 0, st>>>(G, F, b, ##__VA_ARGS__); break; \
+    case 1: K<1><<<nb, kThreads, 0, st>>>(G, F, b, ##__VA_ARGS__); break; \
+    default: K<2><<<nb, kThreads, 0, st>>>(G, F, b, ##__VA_ARGS__); break; \
+  }
+  switch (stage) {
+    case kStageSlopes: HYDRO_MIXED_AXIS(k_slopes_mixed) break;
+    case kStagePpmc: HYDRO_MIXED_AXIS(k_ppmc_mixed) break;
+    case kStageRiemann1: HYDRO_MIXED_AXIS(k_riemann1_mixed, gf) break;
+    case kStageRiemann2: HYDRO_MIXED_AXIS(k_riemann2_mixed, gd, gf) break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef HYDRO_MIXED_AXIS
+  return cudaGetLastError();
+}
+
+cudaError_t mixed_update(const Geom& G, const Bufs& B, cudaStream_t st) {
+  k_update_mixed<<<blocks_for(G.nreal), kThreads, 0, st>>>(G, float_view(B));
+  return cudaGetLastError();
+}
+
+}  // namespace hydro

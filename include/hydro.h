@@ -140,6 +140,47 @@ int hydro_profile_read(hydro_t h, int nstages, double* ms, long long* launches, 
 /* Release the handle and all device memory it owns.  NULL is accepted. */
 void hydro_free(hydro_t h);
 
+/* ---- batches of independent grids ----------------------------------------------
+ * Many grids of uneven sizes (and boundary conditions, gamma, dx) advanced
+ * together: each stage of the step is one kernel launch over all grids, every
+ * grid keeps its own CFL time step, and the steps of one hydro_batch_step call
+ * are captured once into a CUDA graph and replayed with one graph launch (the
+ * paper suggests running many problems at once, Sec. 5).  Conventions as for
+ * single grids; `grid` indexes 0..ngrids-1. */
+typedef struct hydro_batch_s* hydro_batch_t;
+
+/* dims: [ngrids][3] (nx, ny, nz); dx, gamma: [ngrids]; bc: [ngrids][6].
+ * Allocates the device memory of all grids (one allocation). */
+int hydro_batch_init(hydro_batch_t* out, int ngrids, const int* dims, const double* dx,
+                     const double* gamma, const int* bc);
+int hydro_batch_set_inflow(hydro_batch_t h, int grid, int face, const double prim[5]);
+/* HYDRO_FP64 (default) or HYDRO_MIXED. */
+int hydro_batch_set_precision(hydro_batch_t h, int mode);
+/* A non-default stream (graph capture needs one); the batch creates its own
+ * otherwise. */
+int hydro_batch_set_stream(hydro_batch_t h, void* stream);
+int hydro_batch_set_state(hydro_batch_t h, int grid, const double* u, int on_device);
+int hydro_batch_get_state(hydro_batch_t h, int grid, double* u, int on_device);
+/* Advance every grid by nsteps CTU steps, each with its own dt = cfl * min
+ * dx/(|v_d| + a) of that grid.  dt_out (host, may be NULL): [nsteps][ngrids].
+ * The first call with a given (nsteps, cfl, precision, schedule) captures the
+ * graph; later calls replay it.  Returns HYDRO_OK or an error code (a
+ * non-physical state or a Newton cap in any grid is reported after the call). */
+int hydro_batch_step(hydro_batch_t h, double cfl, int nsteps, double* dt_out);
+/* Choose the launch schedule -- threads per block (128 or 256) and the order of
+ * the grids' blocks (as given, or largest grid first) -- by timing one step of
+ * each candidate from the current states (restored afterwards).  With
+ * use_cache != 0 a previous choice for the same grid sizes, precision and
+ * device is read from the cache file ($HYDRO_TUNE_CACHE, else
+ * ~/.cache/hydro_gb300_batch_tune.txt) instead; every new choice is appended
+ * there.  Outputs (may be NULL): the chosen block size and order, and its
+ * measured ms a step (-1 when taken from the cache). */
+int hydro_batch_autotune(hydro_batch_t h, int use_cache, int* block_size, int* order,
+                         float* ms_per_step);
+int hydro_batch_last_error(hydro_batch_t h);
+const char* hydro_batch_cuda_error_string(hydro_batch_t h);
+void hydro_batch_free(hydro_batch_t h);
+
 /* ---- time step without allocation ---------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot call cudaMalloc (their device memory is owned by another allocator, or

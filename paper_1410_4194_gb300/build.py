@@ -23,6 +23,7 @@ UNITS = {
     "hydro_fp64_fast.cu": ["--fmad=true"],  # fast FP64 stage kernels
     "hydro_noalloc.cu": ["--fmad=false"],   # time step without allocation
     "hydro_mixed.cu": ["--fmad=true"],      # mixed-precision stages
+    "hydro_batch.cu": [],                   # batches of grids (host runtime)
 }
 
 

@@ -22,6 +22,7 @@
 //   k_update     conserved update (Eq. conserved_update) + positivity check
 #include <math.h>
 
+#include "../../include/hydro.h"
 #include "hydro_kernels.cuh"
 
 namespace hydro {
@@ -57,11 +58,11 @@ __device__ __forceinline__ void block_max_to(double v, unsigned long long* slot)
 // reflective axis negated, unless an inflow axis is involved, in which case the
 // last inflow face (in x, y, z order) provides the state and only the
 // reflective axes after it negate their momentum.
-__global__ void __launch_bounds__(kThreads) k_prims(Geom G, Bufs B, BcDesc bc, Gas g, int want_dt) {
-  const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double local = 0.0;  // max over this thread's real cell of |v_d| + a
-  if (t < total) {
+// returns this cell's |v_d| + a maximum (0 for ghosts or when !want_dt)
+__device__ __forceinline__ double prims_body(const Geom& G, const Bufs& B, const BcDesc& bc,
+                                             const Gas& g, int want_dt, long long t) {
+  double local = 0.0;
+  {
     int c[3];
     c[2] = (int)(t / G.s[2]);
     c[1] = (int)((t - c[2] * G.s[2]) / G.s[1]);
@@ -135,7 +136,23 @@ __global__ void __launch_bounds__(kThreads) k_prims(Geom G, Bufs B, BcDesc bc, G
         if (G.n[d] > 1) local = tmax(local, fabs(W[1 + d]) + a);
     }
   }
+  return local;
+}
+
+__global__ void __launch_bounds__(kThreads) k_prims(Geom G, Bufs B, BcDesc bc, Gas g, int want_dt) {
+  const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const double local = (t < total) ? prims_body(G, B, bc, g, want_dt, t) : 0.0;
   if (want_dt) block_max_to(local, reinterpret_cast<unsigned long long*>(B.rec));
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS) kb_prims(BatchLaunch L) {
+  const BatchItem it = batch_item(L);
+  const Geom& G = it.d->G;
+  const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
+  const double local = (it.t < total) ? prims_body(G, it.d->B, it.d->bc, it.d->gd, 1, it.t) : 0.0;
+  block_max_to(local, reinterpret_cast<unsigned long long*>(it.d->B.rec));
 }
 
 __global__ void k_set_dt(double* rec, double cfl, double fixed_dt, double dx) {
@@ -148,9 +165,7 @@ __global__ void k_set_dt(double* rec, double cfl, double fixed_dt, double dx) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_update(Geom G, Bufs B) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= G.nreal) return;
+__device__ __forceinline__ void update_body(const Geom& G, const Bufs& B, long long t) {
   const int i = (int)(t % G.n[0]);
   const int j = (int)((t / G.n[0]) % G.n[1]);
   const int k = (int)(t / ((long long)G.n[0] * G.n[1]));
@@ -172,6 +187,32 @@ __global__ void __launch_bounds__(kThreads) k_update(Geom G, Bufs B) {
     if (q == 0 && !(un > 0.0)) fl = kFlagNonPhys;
   }
   if (fl) atomicOr(rec_flags(B.rec), fl);
+}
+
+__global__ void __launch_bounds__(kThreads) k_update(Geom G, Bufs B) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < G.nreal) update_body(G, B, t);
+}
+
+template <int BS>
+__global__ void __launch_bounds__(BS) kb_update(BatchLaunch L) {
+  const BatchItem it = batch_item(L);
+  if (it.t < it.d->G.nreal) update_body(it.d->G, it.d->B, it.t);
+}
+
+// per grid: dt = cfl * dx / max(|v_d| + a) (or the fixed dt), dt/dx, history
+__global__ void k_batch_set_dt(const GridDesc* descs, int ngrids, double cfl, double* dt_hist) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ngrids) return;
+  double* rec = descs[i].B.rec;
+  const double dx = descs[i].G.dx;
+  const double dt = cfl * (dx / rec[0]);
+  const double dtdx = dt / dx;
+  rec[0] = 0.0;  // the next step's primitive kernel reduces into a zeroed slot
+  rec[1] = dt;
+  rec[2] = dtdx;
+  rec[3] = 0.5 * dtdx;
+  if (dt_hist) dt_hist[i] = dt;
 }
 
 // ---- building blocks on SoA device arrays -----------------------------------
@@ -247,6 +288,39 @@ long long stage_units(const Geom& G, int stage, int axis) {
 cudaError_t fp64_stage_strict(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
                               cudaStream_t st) {
   return launch_axis_stage<true>(G, B, stage, axis, gamma, st);
+}
+
+cudaError_t batch_prims(const BatchLaunch& L, int precision, int bs, unsigned blocks, cudaStream_t st) {
+  if (precision == HYDRO_MIXED) return batch_prims_mixed(L, bs, blocks, st);
+  if (blocks == 0) return cudaSuccess;
+  if (bs == 128)
+    kb_prims<128><<<blocks, 128, 0, st>>>(L);
+  else
+    kb_prims<256><<<blocks, 256, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_update(const BatchLaunch& L, int precision, int bs, unsigned blocks,
+                         cudaStream_t st) {
+  if (precision == HYDRO_MIXED) return batch_update_mixed(L, bs, blocks, st);
+  if (blocks == 0) return cudaSuccess;
+  if (bs == 128)
+    kb_update<128><<<blocks, 128, 0, st>>>(L);
+  else
+    kb_update<256><<<blocks, 256, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_set_dt(const GridDesc* descs, int ngrids, double cfl, double* dt_hist,
+                         cudaStream_t st) {
+  k_batch_set_dt<<<(ngrids + 127) / 128, 128, 0, st>>>(descs, ngrids, cfl, dt_hist);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_stage(const BatchLaunch& L, int precision, int stage, int axis, int bs,
+                        unsigned blocks, cudaStream_t st) {
+  return precision == HYDRO_MIXED ? batch_stage_mixed(L, stage, axis, bs, blocks, st)
+                                  : batch_stage_fp64(L, stage, axis, bs, blocks, st);
 }
 
 cudaError_t fp64_update(const Geom& G, const Bufs& B, cudaStream_t st) {

@@ -11,4 +11,9 @@ cudaError_t fp64_stage_fast(const Geom& G, const Bufs& B, int stage, int axis, d
   return launch_axis_stage<false>(G, B, stage, axis, gamma, st);
 }
 
+cudaError_t batch_stage_fp64(const BatchLaunch& L, int stage, int axis, int bs, unsigned blocks,
+                             cudaStream_t st) {
+  return launch_batch_stage<false>(L, stage, axis, bs, blocks, st);
+}
+
 }  // namespace hydro

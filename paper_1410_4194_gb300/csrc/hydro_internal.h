@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "hydro_math.cuh"
+
 namespace hydro {
 
 // Geometry of one grid.  Padded arrays carry kNG ghost layers on each side of
@@ -42,6 +44,26 @@ struct Box {
   int n[3];
 };
 
+// Everything a batched launch needs about one grid, in device memory.  The
+// mixed path reads the work arrays of B through float views.
+struct GridDesc {
+  Geom G;
+  Bufs B;
+  BcDesc bc;
+  GasT<double> gd;  // gamma-derived constants, formed on the host
+  GasT<float> gf;
+  Box box[4][3];    // [stage - kStageSlopes][axis]: units of the per-axis stages
+};
+
+// A batched launch covers the blocks of all grids: grid order[i] owns blocks
+// [prefix[i], prefix[i+1]); blocks never straddle grids.
+struct BatchLaunch {
+  const GridDesc* descs;
+  const int* prefix;  // ngrids + 1 block offsets
+  const int* order;   // grid index of each prefix slot
+  int ngrids;
+};
+
 // Stages of one step; each is one kernel launch (per axis for the sweep stages).
 enum Stage : int {
   kStagePrims = 0,     // ghost remap + primitives (+ dt minimum)
@@ -76,6 +98,24 @@ cudaError_t mixed_prims(const Geom& G, const Bufs& B, const BcDesc& bc, double g
 cudaError_t mixed_stage(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
                         cudaStream_t st);
 cudaError_t mixed_update(const Geom& G, const Bufs& B, cudaStream_t st);
+
+// Batched launchers: one launch covers the given stage of every grid of a
+// batch, with `bs` threads a block (128 or 256).  Precision HYDRO_FP64 or
+// HYDRO_MIXED.  blocks = the batch's total block count for this stage/axis.
+cudaError_t batch_prims(const BatchLaunch& L, int precision, int bs, unsigned blocks, cudaStream_t st);
+cudaError_t batch_set_dt(const GridDesc* descs, int ngrids, double cfl, double* dt_hist,
+                         cudaStream_t st);
+cudaError_t batch_stage(const BatchLaunch& L, int precision, int stage, int axis, int bs,
+                        unsigned blocks, cudaStream_t st);
+cudaError_t batch_update(const BatchLaunch& L, int precision, int bs, unsigned blocks,
+                         cudaStream_t st);
+// batched building blocks in the fast FP64 and the mixed translation units
+cudaError_t batch_stage_fp64(const BatchLaunch& L, int stage, int axis, int bs, unsigned blocks,
+                             cudaStream_t st);
+cudaError_t batch_stage_mixed(const BatchLaunch& L, int stage, int axis, int bs, unsigned blocks,
+                              cudaStream_t st);
+cudaError_t batch_prims_mixed(const BatchLaunch& L, int bs, unsigned blocks, cudaStream_t st);
+cudaError_t batch_update_mixed(const BatchLaunch& L, int bs, unsigned blocks, cudaStream_t st);
 cudaError_t fp64_riemann_soa(int n, const double* UL, const double* UR, double gamma, double* F,
                              int* flags, cudaStream_t st);
 cudaError_t fp64_ppmc_soa(int n, const double* w, double dtdx, double gamma, double* WsL,

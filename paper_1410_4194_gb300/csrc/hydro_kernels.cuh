@@ -69,10 +69,8 @@ __device__ __forceinline__ int* rec_flags(double* rec) { return reinterpret_cast
 
 
 template <int D, bool S>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_slopes(Geom G, Bufs B, Box box, Gas g) {
-  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= count) return;
+__device__ __forceinline__ void slopes_body(const Geom& G, const Bufs& B, const Box& box,
+    const Gas& g, long long t) {
   int c3[3];
   box_coords(box, t, c3);
   const long long c = pidx(G, c3);
@@ -90,10 +88,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_slopes(Geom G, Bufs B,
 }
 
 template <int D, bool S>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppmc(Geom G, Bufs B, Box box, Gas g) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_slopes(Geom G, Bufs B, Box box, Gas g) {
   const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= count) return;
+  if (t < count) slopes_body<D, S>(G, B, box, g, t);
+}
+
+template <int D, bool S>
+__device__ __forceinline__ void ppmc_body(const Geom& G, const Bufs& B, const Box& box,
+    const Gas& g, long long t) {
   int c3[3];
   box_coords(box, t, c3);
   const long long c = pidx(G, c3);
@@ -130,10 +133,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppmc(Geom G, Bufs B, B
 }
 
 template <int D, bool S>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann1(Geom G, Bufs B, Box box, Gas g) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppmc(Geom G, Bufs B, Box box, Gas g) {
   const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= count) return;
+  if (t < count) ppmc_body<D, S>(G, B, box, g, t);
+}
+
+template <int D, bool S>
+__device__ __forceinline__ void riemann1_body(const Geom& G, const Bufs& B, const Box& box,
+    const Gas& g, long long t) {
   int c3[3];
   box_coords(box, t, c3);
   const long long f = pidx(G, c3);
@@ -156,10 +164,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann1(Geom G, Bufs 
 }
 
 template <int D, bool S>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann2(Geom G, Bufs B, Box box, Gas g) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann1(Geom G, Bufs B, Box box, Gas g) {
   const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= count) return;
+  if (t < count) riemann1_body<D, S>(G, B, box, g, t);
+}
+
+template <int D, bool S>
+__device__ __forceinline__ void riemann2_body(const Geom& G, const Bufs& B, const Box& box,
+    const Gas& g, long long t) {
   int c3[3];
   box_coords(box, t, c3);
   const long long f = pidx(G, c3);
@@ -213,6 +226,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann2(Geom G, Bufs 
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
+template <int D, bool S>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann2(Geom G, Bufs B, Box box, Gas g) {
+  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) riemann2_body<D, S>(G, B, box, g, t);
+}
+
 inline unsigned blocks_for(long long count) {
   return (unsigned)((count + kThreads - 1) / kThreads);
 }
@@ -242,6 +262,47 @@ inline Box make_box(const Geom& G, int axis, int lo_d, int hi_d, int lo_o, int h
 
 inline long long box_count(const Box& b) { return (long long)b.n[0] * b.n[1] * b.n[2]; }
 
+
+// ---- batched launches: one launch, the blocks of every grid ----------------
+// grid slot of block b: the last i with prefix[i] <= b
+__device__ __forceinline__ int find_slot(const int* __restrict__ prefix, int n, int b) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= b)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// the grid of this block and the index t of this thread within that grid's box
+struct BatchItem {
+  const GridDesc* d;
+  long long t;
+};
+__device__ __forceinline__ BatchItem batch_item(const BatchLaunch& L) {
+  const int slot = find_slot(L.prefix, L.ngrids, (int)blockIdx.x);
+  BatchItem it;
+  it.d = L.descs + L.order[slot];
+  it.t = (long long)((int)blockIdx.x - L.prefix[slot]) * blockDim.x + threadIdx.x;
+  return it;
+}
+
+#define HYDRO_BATCH_WRAPPER(NAME, BODY, STAGE_IDX)                                             \
+  template <int D, bool S, int BS>                                                             \
+  __global__ void __launch_bounds__(BS, kMinBlocks * kThreads / BS) NAME(BatchLaunch L) {     \
+    const BatchItem it = batch_item(L);                                                        \
+    const Box& box = it.d->box[STAGE_IDX][D];                                                  \
+    if (it.t < (long long)box.n[0] * box.n[1] * box.n[2])                                      \
+      BODY<D, S>(it.d->G, it.d->B, box, it.d->gd, it.t);                                       \
+  }
+HYDRO_BATCH_WRAPPER(kb_slopes, slopes_body, 0)
+HYDRO_BATCH_WRAPPER(kb_ppmc, ppmc_body, 1)
+HYDRO_BATCH_WRAPPER(kb_riemann1, riemann1_body, 2)
+HYDRO_BATCH_WRAPPER(kb_riemann2, riemann2_body, 3)
+#undef HYDRO_BATCH_WRAPPER
 
 // Ranges (padded coordinates; "others" are the two axes across the sweep):
 //   slopes   d in [g-2, g+n+1], others in [g-1, g+n]
@@ -278,6 +339,35 @@ cudaError_t launch_axis_stage(const Geom& G, const Bufs& B, int stage, int axis,
     default: return cudaErrorInvalidValue;
   }
 #undef HYDRO_LAUNCH_AXIS
+  return cudaGetLastError();
+}
+
+template <bool S>
+cudaError_t launch_batch_stage(const BatchLaunch& L, int stage, int axis, int bs, unsigned blocks,
+                               cudaStream_t st) {
+  if (blocks == 0) return cudaSuccess;
+#define HYDRO_BATCH_AXIS(K)                                                              \
+  if (bs == 128) {                                                                       \
+    switch (axis) {                                                                      \
+      case 0: K<0, S, 128><<<blocks, 128, 0, st>>>(L); break;                           \
+      case 1: K<1, S, 128><<<blocks, 128, 0, st>>>(L); break;                           \
+      default: K<2, S, 128><<<blocks, 128, 0, st>>>(L); break;                          \
+    }                                                                                    \
+  } else {                                                                               \
+    switch (axis) {                                                                      \
+      case 0: K<0, S, 256><<<blocks, 256, 0, st>>>(L); break;                           \
+      case 1: K<1, S, 256><<<blocks, 256, 0, st>>>(L); break;                           \
+      default: K<2, S, 256><<<blocks, 256, 0, st>>>(L); break;                          \
+    }                                                                                    \
+  }
+  switch (stage) {
+    case kStageSlopes: HYDRO_BATCH_AXIS(kb_slopes) break;
+    case kStagePpmc: HYDRO_BATCH_AXIS(kb_ppmc) break;
+    case kStageRiemann1: HYDRO_BATCH_AXIS(kb_riemann1) break;
+    case kStageRiemann2: HYDRO_BATCH_AXIS(kb_riemann2) break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef HYDRO_BATCH_AXIS
   return cudaGetLastError();
 }
 

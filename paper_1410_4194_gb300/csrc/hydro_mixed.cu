@@ -14,6 +14,7 @@
 //     CTU fluxes into the FP64 state.
 // Intermediates (primitives, slopes, face states, fluxes) are float, which
 // halves their HBM traffic.  Compiled with FMA contraction.
+#include "../../include/hydro.h"
 #include "hydro_kernels.cuh"
 
 namespace hydro {
@@ -32,6 +33,20 @@ struct BufsF {
   float* F1[3];   // per axis: first fluxes F* [5][ps]
   double* rec;    // step record (dt, flags)
 };
+
+__host__ __device__ inline BufsF float_view(const Bufs& B) {
+  BufsF F;
+  F.u = B.u;
+  F.W = reinterpret_cast<float*>(B.W);
+  F.S = reinterpret_cast<float*>(B.S);
+  for (int d = 0; d < 3; ++d) {
+    F.UL[d] = reinterpret_cast<float*>(B.UL[d]);
+    F.UR[d] = reinterpret_cast<float*>(B.UR[d]);
+    F.F1[d] = reinterpret_cast<float*>(B.F1[d]);
+  }
+  F.rec = B.rec;
+  return F;
+}
 
 template <int D>
 __device__ __forceinline__ void load_prim_f(const float* __restrict__ W, long long ps, long long c,
@@ -69,12 +84,10 @@ __device__ __forceinline__ void block_max_to(double v, unsigned long long* slot)
 
 // primitives in FP64 (ghosts by index remap, as in the FP64 path), stored as
 // float; dt reduction in FP64
-__global__ void __launch_bounds__(kThreads) k_prims_mixed(Geom G, BufsF B, BcDesc bc, GasD g,
-                                                          int want_dt) {
-  const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ double prims_mixed_body(const Geom& G, const BufsF& B, const BcDesc& bc,
+                                                   const GasD& g, int want_dt, long long t) {
   double local = 0.0;
-  if (t < total) {
+  {
     int c[3];
     c[2] = (int)(t / G.s[2]);
     c[1] = (int)((t - c[2] * G.s[2]) / G.s[1]);
@@ -128,14 +141,30 @@ __global__ void __launch_bounds__(kThreads) k_prims_mixed(Geom G, BufsF B, BcDes
         if (G.n[d] > 1) local = tmax(local, fabs(W[1 + d]) + a);
     }
   }
+  return local;
+}
+
+__global__ void __launch_bounds__(kThreads) k_prims_mixed(Geom G, BufsF B, BcDesc bc, GasD g,
+                                                          int want_dt) {
+  const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const double local = (t < total) ? prims_mixed_body(G, B, bc, g, want_dt, t) : 0.0;
   if (want_dt) block_max_to(local, reinterpret_cast<unsigned long long*>(B.rec));
 }
 
+template <int BS>
+__global__ void __launch_bounds__(BS) kb_prims_mixed(BatchLaunch L) {
+  const BatchItem it = batch_item(L);
+  const Geom& G = it.d->G;
+  const BufsF F = float_view(it.d->B);
+  const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
+  const double local = (it.t < total) ? prims_mixed_body(G, F, it.d->bc, it.d->gd, 1, it.t) : 0.0;
+  block_max_to(local, reinterpret_cast<unsigned long long*>(F.rec));
+}
+
 template <int D>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_slopes_mixed(Geom G, BufsF B, Box box) {
-  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= count) return;
+__device__ __forceinline__ void slopes_mixed_body(const Geom& G, const BufsF& B, const Box& box,
+    long long t) {
   int c3[3];
   box_coords(box, t, c3);
   const long long c = pidx(G, c3);
@@ -150,10 +179,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_slopes_mixed(Geom G, B
 }
 
 template <int D>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppmc_mixed(Geom G, BufsF B, Box box) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_slopes_mixed(Geom G, BufsF B, Box box) {
   const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= count) return;
+  if (t < count) slopes_mixed_body<D>(G, B, box, t);
+}
+
+template <int D>
+__device__ __forceinline__ void ppmc_mixed_body(const Geom& G, const BufsF& B, const Box& box,
+    long long t) {
   int c3[3];
   box_coords(box, t, c3);
   const long long c = pidx(G, c3);
@@ -177,11 +211,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppmc_mixed(Geom G, Buf
 }
 
 template <int D>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann1_mixed(Geom G, BufsF B, Box box,
-                                                                         GasF g) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppmc_mixed(Geom G, BufsF B, Box box) {
   const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= count) return;
+  if (t < count) ppmc_mixed_body<D>(G, B, box, t);
+}
+
+template <int D>
+__device__ __forceinline__ void riemann1_mixed_body(const Geom& G, const BufsF& B, const Box& box, const GasF& g,
+    long long t) {
   int c3[3];
   box_coords(box, t, c3);
   const long long f = pidx(G, c3);
@@ -193,14 +231,19 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann1_mixed(Geom G,
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
+template <int D>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann1_mixed(Geom G, BufsF B, Box box,
+                                                                         GasF g) {
+  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) riemann1_mixed_body<D>(G, B, box, g, t);
+}
+
 // transverse half-step and recovery of the primitives of U^{n+1/2} in FP64,
 // second Riemann solve in float
 template <int D>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann2_mixed(Geom G, BufsF B, Box box,
-                                                                         GasD gd, GasF g) {
-  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= count) return;
+__device__ __forceinline__ void riemann2_mixed_body(const Geom& G, const BufsF& B, const Box& box, const GasD& gd, const GasF& g,
+    long long t) {
   int c3[3];
   box_coords(box, t, c3);
   const long long f = pidx(G, c3);
@@ -250,10 +293,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann2_mixed(Geom G,
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
-// conserved update in FP64 from the float CTU fluxes
-__global__ void __launch_bounds__(kThreads) k_update_mixed(Geom G, BufsF B) {
+template <int D>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann2_mixed(Geom G, BufsF B, Box box,
+                                                                         GasD gd, GasF g) {
+  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= G.nreal) return;
+  if (t < count) riemann2_mixed_body<D>(G, B, box, gd, g, t);
+}
+
+// conserved update in FP64 from the float CTU fluxes
+__device__ __forceinline__ void update_mixed_body(const Geom& G, const BufsF& B, long long t) {
   const int i = (int)(t % G.n[0]);
   const int j = (int)((t / G.n[0]) % G.n[1]);
   const int k = (int)(t / ((long long)G.n[0] * G.n[1]));
@@ -277,19 +326,34 @@ __global__ void __launch_bounds__(kThreads) k_update_mixed(Geom G, BufsF B) {
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
-BufsF float_view(const Bufs& B) {
-  BufsF F;
-  F.u = B.u;
-  F.W = reinterpret_cast<float*>(B.W);
-  F.S = reinterpret_cast<float*>(B.S);
-  for (int d = 0; d < 3; ++d) {
-    F.UL[d] = reinterpret_cast<float*>(B.UL[d]);
-    F.UR[d] = reinterpret_cast<float*>(B.UR[d]);
-    F.F1[d] = reinterpret_cast<float*>(B.F1[d]);
-  }
-  F.rec = B.rec;
-  return F;
+__global__ void __launch_bounds__(kThreads) k_update_mixed(Geom G, BufsF B) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < G.nreal) update_mixed_body(G, B, t);
 }
+
+template <int BS>
+__global__ void __launch_bounds__(BS) kb_update_mixed(BatchLaunch L) {
+  const BatchItem it = batch_item(L);
+  if (it.t < it.d->G.nreal) update_mixed_body(it.d->G, float_view(it.d->B), it.t);
+}
+
+#define HYDRO_BATCH_MIXED(NAME, STAGE_IDX, CALL)                                           \
+  template <int D, int BS>                                                                  \
+  __global__ void __launch_bounds__(BS, kMinBlocks * kThreads / BS) NAME(BatchLaunch L) {  \
+    const BatchItem it = batch_item(L);                                                     \
+    const Box& box = it.d->box[STAGE_IDX][D];                                               \
+    if (it.t < (long long)box.n[0] * box.n[1] * box.n[2]) {                                 \
+      const BufsF F = float_view(it.d->B);                                                  \
+      CALL;                                                                                 \
+    }                                                                                       \
+  }
+HYDRO_BATCH_MIXED(kb_slopes_mixed, 0, slopes_mixed_body<D>(it.d->G, F, box, it.t))
+HYDRO_BATCH_MIXED(kb_ppmc_mixed, 1, ppmc_mixed_body<D>(it.d->G, F, box, it.t))
+HYDRO_BATCH_MIXED(kb_riemann1_mixed, 2, riemann1_mixed_body<D>(it.d->G, F, box, it.d->gf, it.t))
+HYDRO_BATCH_MIXED(kb_riemann2_mixed, 3,
+                  riemann2_mixed_body<D>(it.d->G, F, box, it.d->gd, it.d->gf, it.t))
+#undef HYDRO_BATCH_MIXED
+
 
 }  // namespace
 
@@ -326,6 +390,52 @@ cudaError_t mixed_stage(const Geom& G, const Bufs& B, int stage, int axis, doubl
     default: return cudaErrorInvalidValue;
   }
 #undef HYDRO_MIXED_AXIS
+  return cudaGetLastError();
+}
+
+cudaError_t batch_prims_mixed(const BatchLaunch& L, int bs, unsigned blocks, cudaStream_t st) {
+  if (blocks == 0) return cudaSuccess;
+  if (bs == 128)
+    kb_prims_mixed<128><<<blocks, 128, 0, st>>>(L);
+  else
+    kb_prims_mixed<256><<<blocks, 256, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_update_mixed(const BatchLaunch& L, int bs, unsigned blocks, cudaStream_t st) {
+  if (blocks == 0) return cudaSuccess;
+  if (bs == 128)
+    kb_update_mixed<128><<<blocks, 128, 0, st>>>(L);
+  else
+    kb_update_mixed<256><<<blocks, 256, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_stage_mixed(const BatchLaunch& L, int stage, int axis, int bs, unsigned blocks,
+                              cudaStream_t st) {
+  if (blocks == 0) return cudaSuccess;
+#define HYDRO_BATCH_MIXED_AXIS(K)                                                   \
+  if (bs == 128) {                                                                  \
+    switch (axis) {                                                                 \
+      case 0: K<0, 128><<<blocks, 128, 0, st>>>(L); break;                         \
+      case 1: K<1, 128><<<blocks, 128, 0, st>>>(L); break;                         \
+      default: K<2, 128><<<blocks, 128, 0, st>>>(L); break;                        \
+    }                                                                               \
+  } else {                                                                          \
+    switch (axis) {                                                                 \
+      case 0: K<0, 256><<<blocks, 256, 0, st>>>(L); break;                         \
+      case 1: K<1, 256><<<blocks, 256, 0, st>>>(L); break;                         \
+      default: K<2, 256><<<blocks, 256, 0, st>>>(L); break;                        \
+    }                                                                               \
+  }
+  switch (stage) {
+    case kStageSlopes: HYDRO_BATCH_MIXED_AXIS(kb_slopes_mixed) break;
+    case kStagePpmc: HYDRO_BATCH_MIXED_AXIS(kb_ppmc_mixed) break;
+    case kStageRiemann1: HYDRO_BATCH_MIXED_AXIS(kb_riemann1_mixed) break;
+    case kStageRiemann2: HYDRO_BATCH_MIXED_AXIS(kb_riemann2_mixed) break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef HYDRO_BATCH_MIXED_AXIS
   return cudaGetLastError();
 }
 

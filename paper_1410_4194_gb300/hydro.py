@@ -26,7 +26,11 @@ EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_precision", "hydro_set_s
            "hydro_set_state", "hydro_get_state", "hydro_step", "hydro_step_dt",
            "hydro_compute_dt", "hydro_last_error", "hydro_error_string",
            "hydro_cuda_error_string", "hydro_profile", "hydro_profile_read", "hydro_free",
-           "hydro_riemann_exact", "hydro_ppmc", "hydro_compute_dt_noalloc")
+           "hydro_riemann_exact", "hydro_ppmc", "hydro_compute_dt_noalloc",
+           "hydro_batch_init", "hydro_batch_set_inflow", "hydro_batch_set_precision",
+           "hydro_batch_set_stream", "hydro_batch_set_state", "hydro_batch_get_state",
+           "hydro_batch_step", "hydro_batch_autotune", "hydro_batch_last_error",
+           "hydro_batch_cuda_error_string", "hydro_batch_free")
 STAGES = ("prims", "set_dt", "slopes", "ppmc", "riemann1", "riemann2", "update")
 
 _lib = None
@@ -68,6 +72,18 @@ def load():
     L.hydro_riemann_exact.argtypes = [ctypes.c_int, vp, vp, ctypes.c_double, vp, vp, vp]
     L.hydro_ppmc.argtypes = [ctypes.c_int, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp]
     L.hydro_compute_dt_noalloc.argtypes = [vp] + [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [vp, vp]
+    L.hydro_batch_init.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ip, dp, dp, ip]
+    L.hydro_batch_set_inflow.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
+    L.hydro_batch_set_precision.argtypes = [vp, ctypes.c_int]
+    L.hydro_batch_set_stream.argtypes = [vp, vp]
+    L.hydro_batch_set_state.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+    L.hydro_batch_get_state.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+    L.hydro_batch_step.argtypes = [vp, ctypes.c_double, ctypes.c_int, dp]
+    L.hydro_batch_autotune.argtypes = [vp, ctypes.c_int, ip, ip, ctypes.POINTER(ctypes.c_float)]
+    L.hydro_batch_last_error.argtypes = [vp]
+    L.hydro_batch_cuda_error_string.argtypes = [vp]
+    L.hydro_batch_cuda_error_string.restype = ctypes.c_char_p
+    L.hydro_batch_free.argtypes = [vp]
     _lib = L
     return L
 
@@ -260,3 +276,83 @@ def compute_dt_noalloc(u, dx, gamma, cfl, dt_out):
     return L.hydro_compute_dt_noalloc(ctypes.c_void_p(u.data_ptr()), int(nx), int(ny), int(nz),
                                       float(dx), float(gamma), float(cfl),
                                       ctypes.c_void_p(dt_out.data_ptr()), _torch_stream_ptr())
+
+
+class Batch:
+    """Independent grids of uneven sizes advanced together (see include/hydro.h)."""
+
+    def __init__(self, grids, precision=HYDRO_FP64):
+        """grids: list of dicts with "u" [5, nz, ny, nx], "dx", "gamma", "bc" and
+        optionally "inflow" {face: prim}."""
+        L = load()
+        self._L = L
+        n = len(grids)
+        dims = (ctypes.c_int * (3 * n))()
+        dx = (ctypes.c_double * n)()
+        gam = (ctypes.c_double * n)()
+        bc = (ctypes.c_int * (6 * n))()
+        self.shapes = []
+        for i, w in enumerate(grids):
+            _, nz, ny, nx = w["u"].shape
+            dims[3 * i:3 * i + 3] = [nx, ny, nz]
+            dx[i] = float(w["dx"])
+            gam[i] = float(w["gamma"])
+            bc[6 * i:6 * i + 6] = [int(b) for b in w["bc"]]
+            self.shapes.append((5, nz, ny, nx))
+        h = ctypes.c_void_p()
+        rc = L.hydro_batch_init(ctypes.byref(h), n, dims, dx, gam, bc)
+        if rc != 0:
+            raise HydroError(rc, "hydro_batch_init")
+        self.h = h
+        self.n = n
+        if precision != HYDRO_FP64:
+            self._check(L.hydro_batch_set_precision(h, int(precision)), "set_precision")
+        for i, w in enumerate(grids):
+            for face, prim in (w.get("inflow") or {}).items():
+                p = (ctypes.c_double * 5)(*[float(x) for x in prim])
+                self._check(L.hydro_batch_set_inflow(h, i, int(face), p), "set_inflow")
+            self.set_state(i, w["u"])
+
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = what
+            if rc == -3:
+                msg += ": " + self._L.hydro_batch_cuda_error_string(self.h).decode()
+            raise HydroError(rc, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.hydro_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, i, u):
+        ptr, dev, keep = _buffer(u, self.shapes[i], False)
+        self._check(self._L.hydro_batch_set_state(self.h, int(i), ptr, dev), "set_state")
+
+    def get_state(self, i, out=None):
+        if out is None:
+            out = np.empty(self.shapes[i], dtype=np.float64)
+        ptr, dev, keep = _buffer(out, self.shapes[i], True)
+        self._check(self._L.hydro_batch_get_state(self.h, int(i), ptr, dev), "get_state")
+        return out
+
+    def step(self, cfl, nsteps=1):
+        """Advance every grid nsteps steps; returns dt [nsteps, ngrids]."""
+        dt = np.zeros((nsteps, self.n))
+        rc = self._L.hydro_batch_step(self.h, float(cfl), int(nsteps),
+                                      dt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        self._check(rc, "batch_step")
+        return dt
+
+    def autotune(self, use_cache=True):
+        """Pick the launch schedule; returns (block_size, order, ms_per_step)."""
+        bs, order, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        self._check(self._L.hydro_batch_autotune(self.h, int(bool(use_cache)), ctypes.byref(bs),
+                                                 ctypes.byref(order), ctypes.byref(ms)), "autotune")
+        return bs.value, order.value, ms.value

@@ -1,0 +1,101 @@
+"""Batches of independent grids (hydro_batch_*): every stage one launch over all
+grids, per-grid dt, the steps of a call replayed from a captured CUDA graph.
+
+The batched kernels run the same per-cell code as the single-grid ones, so each
+grid of a batch must reproduce its single-grid run bit for bit (FP64 and mixed),
+and through it the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_4194_gb300 import hydro
+from paper_1410_4194_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for -m gpu tests")
+    hydro.load()
+    oracle.set_threads(0)
+    yield
+
+
+def small_batch():
+    grids = W.batched(ngrids=6, seed=7, edges=(16, 24, 32))
+    # add an inflow grid and a 2D grid so every boundary path is batched
+    rho2, u2, p2, vs = W.rankine_hugoniot(5.0)
+    nx, ny, nz = 24, 12, 8
+    rho = np.ones((nz, ny, nx)); vx = np.zeros_like(rho); p = np.ones_like(rho)
+    rho[:, :, :6] = rho2; vx[:, :, :6] = u2; p[:, :, :6] = p2
+    grids.append(dict(u=W.prim_to_cons(rho, vx, 0.0, 0.0, p, 5 / 3), dx=1 / 24, gamma=5 / 3,
+                      bc=[3, 2, 1, 1, 0, 0], inflow={0: (rho2, u2, 0.0, 0.0, p2)}))
+    grids.append(dict(u=W.smooth_periodic((1, 20, 28), gamma=1.4, seed=4, vamp=0.7), dx=0.05,
+                      gamma=1.4, bc=[0, 0, 1, 1, 0, 0]))
+    return grids
+
+
+@pytest.mark.parametrize("precision", [hydro.HYDRO_FP64, hydro.HYDRO_MIXED], ids=["fp64", "mixed"])
+def test_batch_matches_single_grid_runs_bitwise(precision):
+    grids = small_batch()
+    b = hydro.Batch(grids, precision=precision)
+    dts = b.step(0.3, nsteps=4)
+    for i, w in enumerate(grids):
+        _, nz, ny, nx = w["u"].shape
+        g = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], precision=precision)
+        for face, prim in (w.get("inflow") or {}).items():
+            g.set_inflow(face, prim)
+        g.set_state(w["u"])
+        single_dt = [g.step(0.3) for _ in range(4)]
+        single = g.get_state()
+        g.close()
+        assert np.array_equal(dts[:, i], np.array(single_dt)), (i, dts[:, i], single_dt)
+        assert np.array_equal(b.get_state(i), single), i
+    b.close()
+
+
+def test_batch_fp64_matches_oracle():
+    grids = small_batch()
+    b = hydro.Batch(grids)
+    b.step(0.3, nsteps=5)
+    for i, w in enumerate(grids):
+        uo, to, no, fl = oracle.run(w["u"], w["dx"], w["gamma"], w["bc"], nsteps=5, cfl=0.3,
+                                    inflow=w.get("inflow"))
+        assert fl == 0
+        ug = b.get_state(i)
+        m = np.abs(uo).reshape(5, -1).max(axis=1)
+        scale = np.array([m[0], m[1:4].max(), m[1:4].max(), m[1:4].max(), m[4]])[:, None, None, None]
+        err = np.abs(ug - uo) / np.maximum(np.abs(uo), 1e-4 * scale)
+        assert err.max() <= 1e-10, (i, err.max())
+    b.close()
+
+
+def test_graph_replay_continues_and_autotune_restores_state():
+    grids = small_batch()
+    a = hydro.Batch(grids)
+    dt_a = np.vstack([a.step(0.3, nsteps=2), a.step(0.3, nsteps=2)])  # one graph, replayed
+    c = hydro.Batch(grids)
+    before = [c.get_state(i) for i in range(len(grids))]
+    bs, order, ms = c.autotune(use_cache=False)
+    assert bs in (128, 256) and order in (0, 1) and ms > 0
+    for i in range(len(grids)):
+        assert np.array_equal(c.get_state(i), before[i])  # the tuner restored the states
+    dt_c = c.step(0.3, nsteps=4)  # one graph of four steps, tuned schedule
+    assert np.array_equal(dt_a, dt_c)
+    for i in range(len(grids)):
+        assert np.array_equal(a.get_state(i), c.get_state(i))
+    a.close()
+    c.close()
+
+
+def test_batch_rejects_bad_arguments():
+    with pytest.raises(hydro.HydroError):
+        hydro.Batch([dict(u=np.ones((5, 4, 4, 3)), dx=0.1, gamma=1.4, bc=[0] * 6)])
+    b = hydro.Batch([W.sedov(8)])
+    with pytest.raises(hydro.HydroError):
+        b.step(-0.3)
+    b.close()

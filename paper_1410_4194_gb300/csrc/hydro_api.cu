@@ -41,6 +41,11 @@ struct hydro_s {
   long long stage_launches[kNumStages];
   long long stage_units_sum[kNumStages];
   long long launches_total;
+  // the fast FP64 and mixed paths launch the batched kernels over this one grid
+  GridDesc desc;
+  GridDesc* d_desc;
+  int* d_tab;
+  unsigned blocks[kLaunchKinds];
 };
 
 namespace {
@@ -111,6 +116,15 @@ int fold_events(hydro_t h) {
   return HYDRO_OK;
 }
 
+BatchLaunch one_grid(hydro_t h, int kind) {
+  BatchLaunch L;
+  L.descs = h->d_desc;
+  L.prefix = h->d_tab + 2 * kind;
+  L.order = h->d_tab + 2 * kLaunchKinds;
+  L.ngrids = 1;
+  return L;
+}
+
 #define STAGE(h, stage, axis, call)          \
   do {                                       \
     int rc_ = mark_begin(h, stage, axis);    \
@@ -127,22 +141,38 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
   const Bufs& B = h->B;
   cudaStream_t st = h->stream;
   h->nev = 0;
-  const bool mixed = h->precision == HYDRO_MIXED;
   CK(h, cudaMemsetAsync(B.rec + 4, 0, sizeof(double), st));
-  STAGE(h, kStagePrims, 0,
-        (mixed ? mixed_prims : fp64_prims)(G, B, h->bc, h->gamma, fixed_dt <= 0.0, st));
+  if (h->precision == HYDRO_FP64_STRICT) {
+    STAGE(h, kStagePrims, 0, fp64_prims(G, B, h->bc, h->gamma, fixed_dt <= 0.0, st));
+    STAGE(h, kStageSetDt, 0, fp64_set_dt(G, B, cfl, fixed_dt, st));
+    for (int d = 0; d < 3; ++d) {
+      if (!active(G, d)) continue;
+      for (int s = kStageSlopes; s <= kStageRiemann1; ++s)
+        STAGE(h, s, d, fp64_stage_strict(G, B, s, d, h->gamma, st));
+    }
+    for (int d = 0; d < 3; ++d)
+      if (active(G, d)) STAGE(h, kStageRiemann2, d, fp64_stage_strict(G, B, kStageRiemann2, d, h->gamma, st));
+    STAGE(h, kStageUpdate, 0, fp64_update(G, B, st));
+    return HYDRO_OK;
+  }
+  // fast FP64 or mixed: the batched kernels over this single grid (256 threads)
+  const int P = h->precision;
+  CK(h, cudaMemsetAsync(B.rec, 0, sizeof(double), st));
+  STAGE(h, kStagePrims, 0, batch_prims(one_grid(h, 0), P, 256, h->blocks[0], st));
   STAGE(h, kStageSetDt, 0, fp64_set_dt(G, B, cfl, fixed_dt, st));
-  auto stage_fn = mixed ? mixed_stage
-                        : (h->precision == HYDRO_FP64_STRICT ? fp64_stage_strict : fp64_stage_fast);
   for (int d = 0; d < 3; ++d) {
     if (!active(G, d)) continue;
-    STAGE(h, kStageSlopes, d, stage_fn(G, B, kStageSlopes, d, h->gamma, st));
-    STAGE(h, kStagePpmc, d, stage_fn(G, B, kStagePpmc, d, h->gamma, st));
-    STAGE(h, kStageRiemann1, d, stage_fn(G, B, kStageRiemann1, d, h->gamma, st));
+    for (int s = kStageSlopes; s <= kStageRiemann1; ++s) {
+      const int k = launch_kind(s, d);
+      STAGE(h, s, d, batch_stage(one_grid(h, k), P, s, d, 256, h->blocks[k], st));
+    }
   }
-  for (int d = 0; d < 3; ++d)
-    if (active(G, d)) STAGE(h, kStageRiemann2, d, stage_fn(G, B, kStageRiemann2, d, h->gamma, st));
-  STAGE(h, kStageUpdate, 0, (mixed ? mixed_update : fp64_update)(G, B, st));
+  for (int d = 0; d < 3; ++d) {
+    if (!active(G, d)) continue;
+    const int k = launch_kind(kStageRiemann2, d);
+    STAGE(h, kStageRiemann2, d, batch_stage(one_grid(h, k), P, kStageRiemann2, d, 256, h->blocks[k], st));
+  }
+  STAGE(h, kStageUpdate, 0, batch_update(one_grid(h, 1), P, 256, h->blocks[1], st));
   return HYDRO_OK;
 }
 
@@ -265,12 +295,35 @@ int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, co
     p += 5 * plane;
   }
   B.rec = reinterpret_cast<double*>(p);
-  e = cudaMemset(h->slab, 0, total);
-  if (e != cudaSuccess) {
+  // one-grid descriptor and launch tables for the batched kernels
+  memset(&h->desc, 0, sizeof(h->desc));
+  h->desc.G = G;
+  h->desc.B = B;
+  h->desc.bc = h->bc;
+  fill_desc(h->desc, gamma);
+  int tab[2 * kLaunchKinds + 1];
+  const int zero = 0;
+  h->d_desc = nullptr;
+  h->d_tab = nullptr;
+  if (!build_launch_tables(&h->desc, &zero, 1, 256, tab, h->blocks)) {
     cudaFreeHost(h->host_rec);
     cudaFree(h->slab);
     delete h;
-    return HYDRO_ECUDA;
+    return HYDRO_EINVAL;
+  }
+  e = cudaMemset(h->slab, 0, total);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_desc, sizeof(GridDesc));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_tab, sizeof(tab));
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_desc, &h->desc, sizeof(GridDesc), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_tab, tab, sizeof(tab), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (h->d_desc) cudaFree(h->d_desc);
+    if (h->d_tab) cudaFree(h->d_tab);
+    cudaFreeHost(h->host_rec);
+    cudaFree(h->slab);
+    delete h;
+    return e == cudaErrorMemoryAllocation ? HYDRO_ENOMEM : HYDRO_ECUDA;
   }
   *out = h;
   return HYDRO_OK;
@@ -287,6 +340,10 @@ int hydro_set_inflow(hydro_t h, int face, const double prim[5]) {
   U[2] = prim[0] * prim[2];
   U[3] = prim[0] * prim[3];
   U[4] = prim[4] / (h->gamma - 1.0) + 0.5 * prim[0] * (prim[1] * prim[1] + prim[2] * prim[2] + prim[3] * prim[3]);
+  h->desc.bc = h->bc;
+  int rc = use_device(h);
+  if (rc) return rc;
+  CK(h, cudaMemcpy(&h->d_desc->bc, &h->bc, sizeof(BcDesc), cudaMemcpyHostToDevice));
   return HYDRO_OK;
 }
 
@@ -349,8 +406,14 @@ double hydro_compute_dt(hydro_t h, double cfl) {
   if (!(cfl > 0.0)) return (double)fail(h, HYDRO_EINVAL);
   int rc = use_device(h);
   if (rc) return (double)rc;
-  cudaError_t e = (h->precision == HYDRO_MIXED ? mixed_prims : fp64_prims)(h->G, h->B, h->bc,
-                                                                          h->gamma, true, h->stream);
+  cudaError_t e;
+  if (h->precision == HYDRO_FP64_STRICT) {
+    e = fp64_prims(h->G, h->B, h->bc, h->gamma, true, h->stream);
+  } else {
+    e = cudaMemsetAsync(h->B.rec, 0, sizeof(double), h->stream);
+    if (e == cudaSuccess)
+      e = batch_prims(one_grid(h, 0), h->precision, 256, h->blocks[0], h->stream);
+  }
   if (e != cudaSuccess) return (double)cuda_fail(h, e);
   e = fp64_set_dt(h->G, h->B, cfl, 0.0, h->stream);
   if (e != cudaSuccess) return (double)cuda_fail(h, e);
@@ -423,6 +486,8 @@ void hydro_free(hydro_t h) {
   if (h->profile)
     for (int k = 0; k < 2 * 64; ++k) cudaEventDestroy(h->ev[k]);
   cudaFree(h->slab);
+  cudaFree(h->d_desc);
+  cudaFree(h->d_tab);
   cudaFreeHost(h->host_rec);
   if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
   delete h;

@@ -12,6 +12,7 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <sys/stat.h>
 
 #include <algorithm>
 #include <new>
@@ -24,8 +25,6 @@
 using namespace hydro;
 
 namespace {
-
-constexpr int kLaunchKinds = 2 + 4 * 3;  // prims, update, 4 stages x 3 axes
 
 struct Schedule {
   int bs = 256;    // threads a block
@@ -88,39 +87,6 @@ int bcuda(hydro_batch_t h, cudaError_t e) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// same ranges as the single-grid stages
-void axis_range(const Geom& G, int d, int lo_off, int hi_off, int& lo, int& n) {
-  if (G.n[d] <= 1) {
-    lo = 0;
-    n = 1;
-    return;
-  }
-  lo = G.g[d] + lo_off;
-  n = G.n[d] + hi_off - lo_off;
-}
-
-Box box_for(const Geom& G, int stage, int axis) {
-  static const int off[4][4] = {{-2, 2, -1, 1}, {-1, 1, -1, 1}, {0, 1, -1, 1}, {0, 1, 0, 0}};
-  const int* o = off[stage - kStageSlopes];
-  Box b;
-  for (int d = 0; d < 3; ++d) {
-    if (d == axis)
-      axis_range(G, d, o[0], o[1], b.lo[d], b.n[d]);
-    else
-      axis_range(G, d, o[2], o[3], b.lo[d], b.n[d]);
-  }
-  return b;
-}
-
-long long units_of(const GridDesc& g, int kind) {
-  if (kind == 0) return (long long)g.G.N[0] * g.G.N[1] * g.G.N[2];
-  if (kind == 1) return g.G.nreal;
-  const int stage = kStageSlopes + (kind - 2) / 3, axis = (kind - 2) % 3;
-  if (g.G.n[axis] <= 1) return 0;
-  const Box& b = g.box[stage - kStageSlopes][axis];
-  return (long long)b.n[0] * b.n[1] * b.n[2];
-}
-
 // build and upload the launch tables of a schedule
 int build_tables(hydro_batch_t h, const Schedule& s) {
   const int n = h->ngrids;
@@ -131,17 +97,8 @@ int build_tables(hydro_batch_t h, const Schedule& s) {
       return h->desc[a].G.nreal > h->desc[b].G.nreal;
     });
   std::vector<int> tab((size_t)kLaunchKinds * (n + 1) + n);
-  for (int k = 0; k < kLaunchKinds; ++k) {
-    long long acc = 0;
-    for (int i = 0; i < n; ++i) {
-      tab[(size_t)k * (n + 1) + i] = (int)acc;
-      acc += (units_of(h->desc[order[i]], k) + s.bs - 1) / s.bs;
-    }
-    tab[(size_t)k * (n + 1) + n] = (int)acc;
-    if (acc > 0x7fffffffLL) return bfail(h, HYDRO_EINVAL);
-    h->blocks[k] = (unsigned)acc;
-  }
-  for (int i = 0; i < n; ++i) tab[(size_t)kLaunchKinds * (n + 1) + i] = order[i];
+  if (!build_launch_tables(h->desc.data(), order.data(), n, s.bs, tab.data(), h->blocks))
+    return bfail(h, HYDRO_EINVAL);
   BCK(h, cudaMemcpy(h->d_tables, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice));
   h->sched = s;
   return HYDRO_OK;
@@ -165,13 +122,13 @@ int enqueue_step(hydro_batch_t h, double cfl, int step) {
   for (int d = 0; d < 3; ++d) {
     if (!h->axis_used[d]) continue;
     for (int s = kStageSlopes; s <= kStageRiemann1; ++s) {
-      const int kind = 2 + (s - kStageSlopes) * 3 + d;
+      const int kind = launch_kind(s, d);
       BCK(h, batch_stage(launch_of(h, kind), h->precision, s, d, bs, h->blocks[kind], st));
     }
   }
   for (int d = 0; d < 3; ++d) {
     if (!h->axis_used[d]) continue;
-    const int kind = 2 + (kStageRiemann2 - kStageSlopes) * 3 + d;
+    const int kind = launch_kind(kStageRiemann2, d);
     BCK(h, batch_stage(launch_of(h, kind), h->precision, kStageRiemann2, d, bs, h->blocks[kind], st));
   }
   BCK(h, batch_update(launch_of(h, 1), h->precision, bs, h->blocks[1], st));
@@ -259,12 +216,9 @@ bool cache_lookup(const std::string& key, Schedule* s) {
 
 void cache_store(const std::string& key, const Schedule& s, float ms) {
   const std::string path = cache_path();
-  const size_t slash = path.find_last_of('/');
-  if (slash != std::string::npos) {
-    const std::string dir = path.substr(0, slash);
-    std::string cmd = "mkdir -p '" + dir + "' 2>/dev/null";
-    if (system(cmd.c_str()) != 0) { /* the cache is optional */ }
-  }
+  // create the parent directories (the cache is optional: failures are ignored)
+  for (size_t pos = path.find('/', 1); pos != std::string::npos; pos = path.find('/', pos + 1))
+    mkdir(path.substr(0, pos).c_str(), 0755);
   FILE* f = fopen(path.c_str(), "a");
   if (!f) return;
   fprintf(f, "%s %d %d %.4f\n", key.c_str(), s.bs, s.order, ms);
@@ -319,10 +273,7 @@ int hydro_batch_init(hydro_batch_t* out, int ngrids, const int* dims, const doub
     G.nreal = (long long)G.n[0] * G.n[1] * G.n[2];
     G.dx = dx[i];
     for (int f = 0; f < 6; ++f) g.bc.type[f] = (G.n[f / 2] > 1) ? bc[6 * i + f] : HYDRO_BC_PERIODIC;
-    g.gd = make_gas<double>(gamma[i]);
-    g.gf = make_gas<float>(gamma[i]);
-    for (int s = kStageSlopes; s <= kStageRiemann2; ++s)
-      for (int d = 0; d < 3; ++d) g.box[s - kStageSlopes][d] = box_for(G, s, d);
+    fill_desc(g, gamma[i]);
     int nact = 0;
     for (int d = 0; d < 3; ++d) nact += G.n[d] > 1 ? 1 : 0;
     off[i] = total;

@@ -278,6 +278,41 @@ cudaError_t fp64_set_dt(const Geom& G, const Bufs& B, double cfl, double fixed_d
   return cudaGetLastError();
 }
 
+Box stage_box_of(const Geom& G, int stage, int axis) { return stage_box(G, stage, axis); }
+
+void fill_desc(GridDesc& d, double gamma) {
+  d.gd = make_gas<double>(gamma);
+  d.gf = make_gas<float>(gamma);
+  for (int s = kStageSlopes; s <= kStageRiemann2; ++s)
+    for (int a = 0; a < 3; ++a) d.box[s - kStageSlopes][a] = stage_box(d.G, s, a);
+}
+
+bool build_launch_tables(const GridDesc* desc, const int* order, int n, int bs, int* tab,
+                         unsigned* blocks) {
+  for (int k = 0; k < kLaunchKinds; ++k) {
+    long long acc = 0;
+    for (int i = 0; i < n; ++i) {
+      const GridDesc& g = desc[order[i]];
+      long long units;
+      if (k == 0) {
+        units = (long long)g.G.N[0] * g.G.N[1] * g.G.N[2];
+      } else if (k == 1) {
+        units = g.G.nreal;
+      } else {
+        const int stage = kStageSlopes + (k - 2) / 3, axis = (k - 2) % 3;
+        units = g.G.n[axis] > 1 ? box_count(g.box[stage - kStageSlopes][axis]) : 0;
+      }
+      tab[(size_t)k * (n + 1) + i] = (int)acc;
+      acc += (units + bs - 1) / bs;
+    }
+    if (acc > 0x7fffffffLL) return false;
+    tab[(size_t)k * (n + 1) + n] = (int)acc;
+    blocks[k] = (unsigned)acc;
+  }
+  for (int i = 0; i < n; ++i) tab[(size_t)kLaunchKinds * (n + 1) + i] = order[i];
+  return true;
+}
+
 long long stage_units(const Geom& G, int stage, int axis) {
   if (stage == kStagePrims) return (long long)G.N[0] * G.N[1] * G.N[2];
   if (stage == kStageUpdate) return G.nreal;

@@ -1,15 +1,11 @@
-// hydro_fp64_fast.cu -- the FP64 stage kernels with the algebraic rewrites of
-// hydro_math.cuh (S = false), compiled with fused multiply-add contraction:
+// hydro_fp64_fast.cu -- the FP64 stage kernels (batched launches over one or
+// many grids) with the algebraic rewrites of hydro_math.cuh (S = false),
+// compiled with fused multiply-add contraction:
 // every a*b+c becomes one DFMA, which both halves the instruction count of
 // those expressions on GB300's FP64 pipe and rounds once instead of twice.
 #include "hydro_kernels.cuh"
 
 namespace hydro {
-
-cudaError_t fp64_stage_fast(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
-                            cudaStream_t st) {
-  return launch_axis_stage<false>(G, B, stage, axis, gamma, st);
-}
 
 cudaError_t batch_stage_fp64(const BatchLaunch& L, int stage, int axis, int bs, unsigned blocks,
                              cudaStream_t st) {

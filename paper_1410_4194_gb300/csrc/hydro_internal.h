@@ -78,26 +78,31 @@ enum Stage : int {
 
 // Units (cells or faces) one launch of a stage processes.
 long long stage_units(const Geom& G, int stage, int axis);
+// Cells or faces of a per-axis stage (kStageSlopes..kStageRiemann2).
+Box stage_box_of(const Geom& G, int stage, int axis);
+
+// Launch kinds of a (batched) step: 0 primitives, 1 update, then the four
+// per-axis stages x three axes.
+constexpr int kLaunchKinds = 2 + 4 * 3;
+inline int launch_kind(int stage, int axis) { return 2 + (stage - kStageSlopes) * 3 + axis; }
+// Fill a descriptor's stage boxes and gas constants from its geometry and gamma.
+void fill_desc(GridDesc& d, double gamma);
+// Block-prefix tables of every launch kind for the grids in `order`, bs threads
+// a block: tab = [kLaunchKinds][n+1] offsets followed by the n grid indices;
+// blocks[kind] = total blocks.  Returns false if a launch would exceed 2^31 blocks.
+bool build_launch_tables(const GridDesc* desc, const int* order, int n, int bs, int* tab,
+                         unsigned* blocks);
 
 // FP64 launchers (hydro_fp64.cu).  Every launcher enqueues on `st` and returns
 // the launch error.
 cudaError_t fp64_prims(const Geom& G, const Bufs& B, const BcDesc& bc, double gamma, bool want_dt,
                        cudaStream_t st);
 cudaError_t fp64_set_dt(const Geom& G, const Bufs& B, double cfl, double fixed_dt, cudaStream_t st);
-// one launch of a per-axis stage: fast arithmetic (hydro_fp64_fast.cu) or the
-// reference operation order (hydro_fp64.cu)
-cudaError_t fp64_stage_fast(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
-                            cudaStream_t st);
+// one launch of a per-axis stage in the reference operation order (strict mode);
+// the fast FP64 and mixed paths use the batched launchers below with one grid
 cudaError_t fp64_stage_strict(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
                               cudaStream_t st);
 cudaError_t fp64_update(const Geom& G, const Bufs& B, cudaStream_t st);
-// mixed-precision launchers (hydro_mixed.cu): the same stages on float work
-// arrays carved from the same slab
-cudaError_t mixed_prims(const Geom& G, const Bufs& B, const BcDesc& bc, double gamma, bool want_dt,
-                        cudaStream_t st);
-cudaError_t mixed_stage(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
-                        cudaStream_t st);
-cudaError_t mixed_update(const Geom& G, const Bufs& B, cudaStream_t st);
 
 // Batched launchers: one launch covers the given stage of every grid of a
 // batch, with `bs` threads a block (128 or 256).  Precision HYDRO_FP64 or

@@ -144,14 +144,6 @@ __device__ __forceinline__ double prims_mixed_body(const Geom& G, const BufsF& B
   return local;
 }
 
-__global__ void __launch_bounds__(kThreads) k_prims_mixed(Geom G, BufsF B, BcDesc bc, GasD g,
-                                                          int want_dt) {
-  const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const double local = (t < total) ? prims_mixed_body(G, B, bc, g, want_dt, t) : 0.0;
-  if (want_dt) block_max_to(local, reinterpret_cast<unsigned long long*>(B.rec));
-}
-
 template <int BS>
 __global__ void __launch_bounds__(BS) kb_prims_mixed(BatchLaunch L) {
   const BatchItem it = batch_item(L);
@@ -178,12 +170,6 @@ __device__ __forceinline__ void slopes_mixed_body(const Geom& G, const BufsF& B,
   for (int q = 0; q < 5; ++q) B.S[q * G.ps + c] = dw[q];
 }
 
-template <int D>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_slopes_mixed(Geom G, BufsF B, Box box) {
-  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < count) slopes_mixed_body<D>(G, B, box, t);
-}
 
 template <int D>
 __device__ __forceinline__ void ppmc_mixed_body(const Geom& G, const BufsF& B, const Box& box,
@@ -210,12 +196,6 @@ __device__ __forceinline__ void ppmc_mixed_body(const Geom& G, const BufsF& B, c
   store_rot_f<D>(B.UL[D], G.ps, c + s, WsR);
 }
 
-template <int D>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppmc_mixed(Geom G, BufsF B, Box box) {
-  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < count) ppmc_mixed_body<D>(G, B, box, t);
-}
 
 template <int D>
 __device__ __forceinline__ void riemann1_mixed_body(const Geom& G, const BufsF& B, const Box& box, const GasF& g,
@@ -231,13 +211,6 @@ __device__ __forceinline__ void riemann1_mixed_body(const Geom& G, const BufsF& 
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
-template <int D>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann1_mixed(Geom G, BufsF B, Box box,
-                                                                         GasF g) {
-  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < count) riemann1_mixed_body<D>(G, B, box, g, t);
-}
 
 // transverse half-step and recovery of the primitives of U^{n+1/2} in FP64,
 // second Riemann solve in float
@@ -293,13 +266,6 @@ __device__ __forceinline__ void riemann2_mixed_body(const Geom& G, const BufsF& 
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
-template <int D>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann2_mixed(Geom G, BufsF B, Box box,
-                                                                         GasD gd, GasF g) {
-  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < count) riemann2_mixed_body<D>(G, B, box, gd, g, t);
-}
 
 // conserved update in FP64 from the float CTU fluxes
 __device__ __forceinline__ void update_mixed_body(const Geom& G, const BufsF& B, long long t) {
@@ -326,10 +292,6 @@ __device__ __forceinline__ void update_mixed_body(const Geom& G, const BufsF& B,
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
-__global__ void __launch_bounds__(kThreads) k_update_mixed(Geom G, BufsF B) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < G.nreal) update_mixed_body(G, B, t);
-}
 
 template <int BS>
 __global__ void __launch_bounds__(BS) kb_update_mixed(BatchLaunch L) {
@@ -356,42 +318,6 @@ HYDRO_BATCH_MIXED(kb_riemann2_mixed, 3,
 
 
 }  // namespace
-
-cudaError_t mixed_prims(const Geom& G, const Bufs& B, const BcDesc& bc, double gamma, bool want_dt,
-                        cudaStream_t st) {
-  if (want_dt) {
-    cudaError_t e = cudaMemsetAsync(B.rec, 0, sizeof(double), st);
-    if (e != cudaSuccess) return e;
-  }
-  const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
-  k_prims_mixed<<<blocks_for(total), kThreads, 0, st>>>(G, float_view(B), bc,
-                                                        make_gas<double>(gamma), want_dt ? 1 : 0);
-  return cudaGetLastError();
-}
-
-cudaError_t mixed_stage(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
-                        cudaStream_t st) {
-  const BufsF F = float_view(B);
-  const GasF gf = make_gas<float>(gamma);
-  const GasD gd = make_gas<double>(gamma);
-  const Box b = stage_box(G, stage, axis);
-  const unsigned nb = blocks_for(box_count(b));
-#define HYDRO_MIXED_AXIS(K, ...)                                          \
-  switch (axis) {                                                         \
-    case 0: K<0><<<nb, kThreads, 0, st>>>(G, F, b, ##__VA_ARGS__); break; \
-    case 1: K<1><<<nb, kThreads, 0, st>>>(G, F, b, ##__VA_ARGS__); break; \
-    default: K<2><<<nb, kThreads, 0, st>>>(G, F, b, ##__VA_ARGS__); break; \
-  }
-  switch (stage) {
-    case kStageSlopes: HYDRO_MIXED_AXIS(k_slopes_mixed) break;
-    case kStagePpmc: HYDRO_MIXED_AXIS(k_ppmc_mixed) break;
-    case kStageRiemann1: HYDRO_MIXED_AXIS(k_riemann1_mixed, gf) break;
-    case kStageRiemann2: HYDRO_MIXED_AXIS(k_riemann2_mixed, gd, gf) break;
-    default: return cudaErrorInvalidValue;
-  }
-#undef HYDRO_MIXED_AXIS
-  return cudaGetLastError();
-}
 
 cudaError_t batch_prims_mixed(const BatchLaunch& L, int bs, unsigned blocks, cudaStream_t st) {
   if (blocks == 0) return cudaSuccess;
@@ -439,9 +365,5 @@ cudaError_t batch_stage_mixed(const BatchLaunch& L, int stage, int axis, int bs,
   return cudaGetLastError();
 }
 
-cudaError_t mixed_update(const Geom& G, const Bufs& B, cudaStream_t st) {
-  k_update_mixed<<<blocks_for(G.nreal), kThreads, 0, st>>>(G, float_view(B));
-  return cudaGetLastError();
-}
 
 }  // namespace hydro

@@ -28,10 +28,11 @@ def _setup():
 
 
 def l1_fields(g, o):
-    """Relative L1 per field; momenta against the momentum group's scale."""
+    """Relative L1 per field; the momenta against the largest momentum
+    component's L1 norm (their common scale; in 1D two of them are zero)."""
     d = np.abs(g - o).reshape(5, -1).sum(axis=1)
     s = np.abs(o).reshape(5, -1).sum(axis=1)
-    mom = s[1:4].sum() / 3.0
+    mom = s[1:4].max()
     return d / np.array([s[0], mom, mom, mom, s[4]])
 
 

@@ -169,33 +169,38 @@ def algorithmic_ops(w, cfl):
     return out, "op-counting oracle on %dx%dx%d %s, one step" % (nx, ny, nz, key)
 
 
-def run_cpu_baseline(wname, steps, cfl=0.3):
-    """Oracle on the host cores, bounded sample: ``steps`` steps of the same IC
-    recipe at a size the host finishes in ~10-30 s."""
+def run_cpu_baseline(wname, max_steps, cfl=0.3, min_seconds=10.0):
+    """Oracle on the host cores, bounded sample: steps of the same IC recipe at a
+    size the host finishes quickly, repeated until ``min_seconds`` have passed
+    (at most ``max_steps``), so that the sample is ~10-30 s of CPU work."""
     import oracle
     from paper_1410_4194_gb300 import workloads as W
     if wname.startswith("sedov"):
         s = W.sedov(128)
-        sample = "Sedov blast at 128^3 (same IC recipe as 256^3), %d oracle steps" % steps
+        sample = "Sedov blast at 128^3 (same IC recipe as 256^3), %d oracle steps"
     elif wname == "sod512":
         s = W.sod(512)
-        sample = "Sod 512 cells, %d oracle steps" % steps
+        sample = "Sod 512 cells, %d oracle steps"
     else:
         full = workload(wname)
         s = dict(u=np.ascontiguousarray(full["u"][:, :64, :64, :128]), dx=full["dx"],
                  gamma=full["gamma"], bc=[2, 2, 0, 0, 0, 0])
-        sample = "%s sub-block 128x64x64, %d oracle steps" % (wname, steps)
+        sample = wname + " sub-block 128x64x64, %d oracle steps"
     cores = oracle.set_threads(0)
     _, nz, ny, nx = s["u"].shape
     g = oracle.Grid(nx, ny, nz, s["dx"], s["gamma"], s["bc"])
     g.set_state(s["u"])
     g.step(cfl)  # untimed: first touch of the oracle's arrays
+    steps = 0
     t0 = time.perf_counter()
-    for _ in range(steps):
+    while steps < max(1, max_steps):
         g.step(cfl)
+        steps += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
     el = time.perf_counter() - t0
     return {"value": nx * ny * nz * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": sample, "seconds": el}
+            "sample": sample % steps, "seconds": el}
 
 
 def main():
@@ -209,7 +214,8 @@ def main():
     ap.add_argument("--cfl", type=float, default=0.3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-steps", type=int, default=6)
+    ap.add_argument("--cpu-steps", type=int, default=1000,
+                    help="cap on the oracle steps of the CPU baseline (it stops after 10 s)")
     ap.add_argument("--compare-l1", action="store_true",
                     help="mixed precision: also run the FP64 path from the same state for the "
                          "same steps and report the L1 difference per field")

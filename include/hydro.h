@@ -219,6 +219,19 @@ int hydro_riemann_exact(int n, const double* UL, const double* UR, double gamma,
 int hydro_ppmc(int n, const double* w, double dtdx, double gamma, double* WsL, double* WsR,
                void* stream);
 
+/* ---- library self-check ---------------------------------------------------------
+ * The paper has no counterpart to this entry point.  The mixed-precision kernels
+ * convert between float and double with integer arithmetic instead of the
+ * hardware conversion instructions (which run at the FP64 rate); this compares
+ * those conversions with the hardware ones on the current device: the widening
+ * for all 2^32 float bit patterns, the narrowing (round to nearest even) for
+ * 2^30 double bit patterns drawn from a counter-based hash, concentrated on the
+ * float range's edges and on rounding ties.  mismatches: host array of two
+ * counts (widening, narrowing), both 0 when the conversions agree bit for bit.
+ * Runs on `stream` and waits for it; allocates 16 bytes of device memory.
+ * Returns HYDRO_OK, HYDRO_EINVAL (mismatches NULL) or HYDRO_ECUDA. */
+int hydro_check_conversions(unsigned long long* mismatches, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,6 +24,7 @@ UNITS = {
     "hydro_noalloc.cu": ["--fmad=false"],   # time step without allocation
     "hydro_mixed.cu": ["--fmad=true"],      # mixed-precision stages
     "hydro_batch.cu": [],                   # batches of grids (host runtime)
+    "hydro_selfcheck.cu": [],               # conversion self-check
 }
 
 

@@ -109,6 +109,45 @@ __device__ __forceinline__ float xfma(float a, float b, float c) { return fmaf(a
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return (b < a) ? b : a; }
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return (a < b) ? b : a; }
 
+// ---------------------------------------------------------------------------
+// float <-> double conversion in integer arithmetic.  GB300 issues the
+// hardware conversions (cvt.f64.f32, cvt.rn.f32.f64) on its FP64 pipe, at the
+// FP64 rate; these rebuild the IEEE 754 bit fields with integer operations
+// instead and return the same bits as the hardware conversion (round to
+// nearest even) for every input.  Zeros take a select; the rare inputs outside
+// the normal-to-normal range (subnormal, infinite or NaN floats; doubles whose
+// float is subnormal, overflows or is not finite) fall back to the hardware
+// conversion.  hydro_check_conversions() compares both against the hardware
+// on the GPU.
+
+// exact widening: float fields (1, 8, 23) -> double fields (1, 11, 52), the
+// exponent rebiased by 1023 - 127 = 896 and the fraction shifted left by 29
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned mag = b & 0x7fffffffu;
+  const unsigned e = b >> 23 & 0xffu;
+  if (e - 1u >= 254u && mag != 0u) return (double)x;
+  unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | (b >> 3 & 0xfffffu);
+  hi = mag ? hi : b;
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// narrowing with round to nearest, ties to even: keep the top 23 of the 52
+// fraction bits and round on the 29 discarded ones (a carry out of the
+// fraction increments the exponent, and out of the largest exponent gives
+// infinity, as IEEE rounding does)
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = hi >> 20 & 0x7ffu;
+  const bool zero = ((hi & 0x7fffffffu) | lo) == 0u;
+  if (e - 897u > 253u && !zero) return (float)x;
+  const unsigned m = (hi & 0xfffffu) << 3 | lo >> 29;
+  const unsigned rest = lo & 0x1fffffffu;
+  unsigned f = (hi & 0x80000000u) | ((e - 896u) << 23) | m;
+  f += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float(zero ? (hi & 0x80000000u) : f);
+}
+
 // x^K by squaring (K is small)
 template <int K, typename T>
 __device__ __forceinline__ T ipow(T x) {
@@ -139,8 +178,16 @@ __device__ __forceinline__ T ipow(T x) {
 // one Newton step is enough for float accuracy.
 template <int K, typename T>
 __device__ __forceinline__ T kth_root(T r) {
-  const float lr = __log2f((float)r);
-  T t = (T)exp2f(lr * (-1.0f / (float)K));
+  float lr;
+  if constexpr (sizeof(T) == 4)
+    lr = __log2f(r);
+  else
+    lr = __log2f(d2f(r));
+  T t;
+  if constexpr (sizeof(T) == 4)
+    t = exp2f(lr * (-1.0f / (float)K));
+  else
+    t = f2d(exp2f(lr * (-1.0f / (float)K)));
   const T invK = T(1.0 / K);
   {
     const T e = xfma(-r, ipow<K>(t), T(1));

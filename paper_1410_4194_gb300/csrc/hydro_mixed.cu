@@ -126,19 +126,36 @@ __device__ __forceinline__ double prims_mixed_body(const Geom& G, const BufsF& B
 #pragma unroll
     for (int d = 0; d < 3; ++d)
       if (neg & (1 << d)) U[1 + d] = -U[1 + d];
-    double W[5], inv_d;
-    cons2prim(U, g, W, inv_d);  // FP64 internal energy and pressure floor
-    const double a = sqrt(g.gamma * W[4] * inv_d);
-    const float af = (float)a;
+    // 1/rho: float reciprocal of the rounded density refined by one Newton
+    // step r <- r + r (1 - rho r) in FP64 (relative error below 2^-44)
+    const float df = d2f(U[0]);
+    const float rf = __frcp_rn(df);
+    double r = f2d(rf);
+    r = fma(r, fma(-U[0], r, 1.0), r);
+    double v[3];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) B.W[q * G.ps + t] = (float)W[q];
+    for (int d = 0; d < 3; ++d) v[d] = U[1 + d] * r;
+    // FP64 internal energy E - (rho v) . v / 2 and the pressure floor
+    const double ke2 = U[1] * v[0] + U[2] * v[1] + U[3] * v[2];
+    const double p = tmax(g.gm1 * fma(-0.5, ke2, U[4]), kPFloor);
+    // a = sqrt(gamma p / rho): float reciprocal square root of x = a^2 refined
+    // by one Newton step, a = x y (1 + (1 - x y^2)/2) (relative error ~1e-13)
+    const double x = g.gamma * p * r;
+    const double y = f2d(rsqrtf(d2f(x)));
+    const double xy = x * y;
+    const double a = fma(0.5 * xy, fma(-xy, y, 1.0), xy);
+    const float af = d2f(a);
+    B.W[t] = df;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) B.W[(1 + d) * G.ps + t] = d2f(v[d]);
+    B.W[4 * G.ps + t] = d2f(p);
     B.W[5 * G.ps + t] = af;
-    B.W[6 * G.ps + t] = 1.0f / af;
-    B.W[7 * G.ps + t] = (float)inv_d;
+    B.W[6 * G.ps + t] = __frcp_rn(af);
+    B.W[7 * G.ps + t] = rf;
     if (want_dt && real) {
 #pragma unroll
       for (int d = 0; d < 3; ++d)
-        if (G.n[d] > 1) local = tmax(local, fabs(W[1 + d]) + a);
+        if (G.n[d] > 1) local = tmax(local, fabs(v[d]) + a);
     }
   }
   return local;
@@ -212,57 +229,75 @@ __device__ __forceinline__ void riemann1_mixed_body(const Geom& G, const BufsF& 
 }
 
 
-// transverse half-step and recovery of the primitives of U^{n+1/2} in FP64,
-// second Riemann solve in float
+// One side of a face at the transverse half-step (Eq. transverse_evolution):
+// U^{n+1/2} = U* + h (G*(c) - G*(c + e_t1)) + h (H*(c) - H*(c + e_t2)), h =
+// dt/(2 dx), accumulated in FP64 from the float face state W* (converted
+// exactly to U*: rho v is an exact product of two floats, E from p/(gamma-1)
+// and the kinetic energy) and the float flux differences, then the FP64
+// recovery of its primitives: internal energy E - |m|^2/(2 rho) with 1/rho from
+// a float seed and one Newton step (relative error below 2^-44).  The float
+// difference of two float fluxes has the rounding error of the fluxes
+// themselves.  Returns the primitives in sweep order and 1/rho, in float.
+template <int D>
+__device__ __forceinline__ void half_step_side(const Geom& G, const BufsF& B, const float* __restrict__ Ws,
+                                               long long f, long long c, double h, const GasD& gd,
+                                               float w[5], float& inv_d) {
+  const long long ps = G.ps;
+  double U[5];
+  {
+    const double d = f2d(Ws[f]);
+    double v[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      v[i] = f2d(Ws[(1 + i) * ps + f]);
+      U[1 + i] = d * v[i];
+    }
+    const double ke2 = U[1] * v[0] + U[2] * v[1] + U[3] * v[2];
+    U[0] = d;
+    U[4] = fma(0.5, ke2, f2d(Ws[4 * ps + f]) * gd.inv_gm1);
+  }
+  constexpr int T1 = Perm<D>::t1, T2 = Perm<D>::t2;
+  if (G.n[T1] > 1) {
+    const float* F = B.F1[T1];
+    const long long st = G.s[T1];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) U[q] = fma(h, f2d(F[q * ps + c] - F[q * ps + c + st]), U[q]);
+  }
+  if (G.n[T2] > 1) {
+    const float* F = B.F1[T2];
+    const long long st = G.s[T2];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) U[q] = fma(h, f2d(F[q * ps + c] - F[q * ps + c + st]), U[q]);
+  }
+  const float df = d2f(U[0]);
+  const float rf = __frcp_rn(df);
+  double r = f2d(rf);
+  r = fma(r, fma(-U[0], r, 1.0), r);
+  const double m2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
+  const double p = gd.gm1 * fma(-0.5 * m2, r, U[4]);
+  // the floor applied to the rounded pressure equals the rounded floored
+  // pressure: rounding is monotonic, so it commutes with the maximum
+  w[0] = df;
+  w[1] = d2f(U[1 + D]) * rf;
+  w[2] = d2f(U[1 + T1]) * rf;
+  w[3] = d2f(U[1 + T2]) * rf;
+  w[4] = tmax(d2f(p), (float)kPFloor);
+  inv_d = rf;
+}
+
+// transverse half-step in FP64, second Riemann solve in float
 template <int D>
 __device__ __forceinline__ void riemann2_mixed_body(const Geom& G, const BufsF& B, const Box& box, const GasD& gd, const GasF& g,
     long long t) {
   int c3[3];
   box_coords(box, t, c3);
   const long long f = pidx(G, c3);
-  const long long ps = G.ps;
-  const long long cl = f - G.s[D], cr = f;
   const double h = B.rec[3];
-  double WsL[5], WsR[5], UhL[5], UhR[5];
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    WsL[q] = (double)B.UL[D][q * ps + f];
-    WsR[q] = (double)B.UR[D][q * ps + f];
-  }
-  prim2cons(WsL, gd, UhL);
-  prim2cons(WsR, gd, UhR);
-  constexpr int T1 = Perm<D>::t1, T2 = Perm<D>::t2;
-  if (G.n[T1] > 1) {
-    const float* F = B.F1[T1];
-    const long long st = G.s[T1];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      UhL[q] = UhL[q] + h * ((double)F[q * ps + cl] - (double)F[q * ps + cl + st]);
-      UhR[q] = UhR[q] + h * ((double)F[q * ps + cr] - (double)F[q * ps + cr + st]);
-    }
-  }
-  if (G.n[T2] > 1) {
-    const float* F = B.F1[T2];
-    const long long st = G.s[T2];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      UhL[q] = UhL[q] + h * ((double)F[q * ps + cl] - (double)F[q * ps + cl + st]);
-      UhR[q] = UhR[q] + h * ((double)F[q * ps + cr] - (double)F[q * ps + cr + st]);
-    }
-  }
-  double UL[5], UR[5], WL[5], WR[5], idL, idR;
-  UL[0] = UhL[0]; UL[1] = UhL[1 + D]; UL[2] = UhL[1 + T1]; UL[3] = UhL[1 + T2]; UL[4] = UhL[4];
-  UR[0] = UhR[0]; UR[1] = UhR[1 + D]; UR[2] = UhR[1 + T1]; UR[3] = UhR[1 + T2]; UR[4] = UhR[4];
-  cons2prim(UL, gd, WL, idL);
-  cons2prim(UR, gd, WR, idR);
-  float wl[5], wr[5], Fx[5];
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    wl[q] = (float)WL[q];
-    wr[q] = (float)WR[q];
-  }
-  const int fl = riemann_exact(wl, wr, (float)idL, (float)idR, g, Fx);
-  store_rot_f<D>(B.UL[D], ps, f, Fx);
+  float wl[5], wr[5], idL, idR, Fx[5];
+  half_step_side<D>(G, B, B.UL[D], f, f - G.s[D], h, gd, wl, idL);
+  half_step_side<D>(G, B, B.UR[D], f, f, h, gd, wr, idR);
+  const int fl = riemann_exact(wl, wr, idL, idR, g, Fx);
+  store_rot_f<D>(B.UL[D], G.ps, f, Fx);
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
@@ -282,7 +317,7 @@ __device__ __forceinline__ void update_mixed_body(const Geom& G, const BufsF& B,
     for (int d = 0; d < 3; ++d) {
       if (G.n[d] > 1) {
         const float* F = B.UL[d];
-        un = un + dtdx * ((double)F[q * G.ps + c] - (double)F[q * G.ps + c + G.s[d]]);
+        un = un + dtdx * (f2d(F[q * G.ps + c]) - f2d(F[q * G.ps + c + G.s[d]]));
       }
     }
     B.u[q * G.nreal + t] = un;

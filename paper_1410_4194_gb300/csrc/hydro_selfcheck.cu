@@ -1,0 +1,85 @@
+// hydro_selfcheck.cu -- hydro_check_conversions(): the integer-arithmetic
+// float <-> double conversions of hydro_math.cuh against the hardware ones.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hydro.h"
+#include "hydro_math.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr unsigned kBlocks = 152 * 8;
+constexpr unsigned long long kNarrowSamples = 1ull << 30;
+
+__device__ __forceinline__ void count(bool bad, unsigned long long* slot) {
+  const unsigned m = __ballot_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(slot, (unsigned long long)__popc(m));
+}
+
+// every float bit pattern
+__global__ void __launch_bounds__(kThreads) k_check_widen(unsigned long long* bad) {
+  const unsigned long long n = 1ull << 32;
+  const unsigned long long stride = (unsigned long long)gridDim.x * kThreads;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * kThreads + threadIdx.x; i < n;
+       i += stride) {
+    const float x = __uint_as_float((unsigned)i);
+    const double a = hydro::f2d(x), b = (double)x;
+    count(__double_as_longlong(a) != __double_as_longlong(b), bad);
+  }
+}
+
+// splitmix64 (Steele, Lea and Flood, 2014) as a counter-based bit source
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// doubles: a quarter with any bit pattern, a quarter with exponents around the
+// float range (biased 860..1190), a quarter of those with the 29 discarded
+// fraction bits at or next to the rounding tie, a quarter near 1 with ties
+__global__ void __launch_bounds__(kThreads) k_check_narrow(unsigned long long* bad) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * kThreads;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * kThreads + threadIdx.x;
+       i < kNarrowSamples; i += stride) {
+    unsigned long long b = mix64(i);
+    const unsigned kind = (unsigned)(i & 3);
+    const unsigned long long r = mix64(i ^ 0x5bd1e995ull);
+    if (kind >= 1) {
+      const unsigned long long e = (kind == 3) ? 1023ull - 2 + (r % 5) : 860ull + (r % 331);
+      b = (b & 0x800fffffffffffffull) | (e << 52);
+    }
+    if (kind >= 2) {
+      const unsigned long long low = 0x10000000ull + ((r >> 20) % 3) - 1;  // tie - 1, tie, tie + 1
+      b = (b & ~0x1fffffffull) | low;
+    }
+    const double x = __longlong_as_double((long long)b);
+    const float a = hydro::d2f(x), c = __double2float_rn(x);
+    count(__float_as_uint(a) != __float_as_uint(c), bad);
+  }
+}
+
+}  // namespace
+
+extern "C" int hydro_check_conversions(unsigned long long* mismatches, void* stream) {
+  if (!mismatches) return HYDRO_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, 2 * sizeof(unsigned long long)) != cudaSuccess) return HYDRO_ECUDA;
+  int rc = HYDRO_OK;
+  if (cudaMemsetAsync(d, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) rc = HYDRO_ECUDA;
+  if (rc == HYDRO_OK) {
+    k_check_widen<<<kBlocks, kThreads, 0, st>>>(d);
+    k_check_narrow<<<kBlocks, kThreads, 0, st>>>(d + 1);
+    if (cudaGetLastError() != cudaSuccess) rc = HYDRO_ECUDA;
+  }
+  if (rc == HYDRO_OK &&
+      (cudaMemcpyAsync(mismatches, d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    rc = HYDRO_ECUDA;
+  cudaFree(d);
+  return rc;
+}

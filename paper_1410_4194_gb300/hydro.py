@@ -30,7 +30,7 @@ EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_precision", "hydro_set_s
            "hydro_batch_init", "hydro_batch_set_inflow", "hydro_batch_set_precision",
            "hydro_batch_set_stream", "hydro_batch_set_state", "hydro_batch_get_state",
            "hydro_batch_step", "hydro_batch_autotune", "hydro_batch_last_error",
-           "hydro_batch_cuda_error_string", "hydro_batch_free")
+           "hydro_batch_cuda_error_string", "hydro_batch_free", "hydro_check_conversions")
 STAGES = ("prims", "set_dt", "slopes", "ppmc", "riemann1", "riemann2", "update")
 
 _lib = None
@@ -84,6 +84,7 @@ def load():
     L.hydro_batch_cuda_error_string.argtypes = [vp]
     L.hydro_batch_cuda_error_string.restype = ctypes.c_char_p
     L.hydro_batch_free.argtypes = [vp]
+    L.hydro_check_conversions.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), vp]
     _lib = L
     return L
 
@@ -276,6 +277,17 @@ def compute_dt_noalloc(u, dx, gamma, cfl, dt_out):
     return L.hydro_compute_dt_noalloc(ctypes.c_void_p(u.data_ptr()), int(nx), int(ny), int(nz),
                                       float(dx), float(gamma), float(cfl),
                                       ctypes.c_void_p(dt_out.data_ptr()), _torch_stream_ptr())
+
+
+def check_conversions():
+    """Mismatch counts (widening, narrowing) of the library's integer-arithmetic
+    float <-> double conversions against the hardware conversions."""
+    L = load()
+    out = (ctypes.c_ulonglong * 2)()
+    rc = L.hydro_check_conversions(out, _torch_stream_ptr())
+    if rc != 0:
+        raise HydroError(rc, "check_conversions")
+    return int(out[0]), int(out[1])
 
 
 class Batch:

@@ -36,19 +36,52 @@ if ROOT not in sys.path:
 METRIC = "cell-updates/s on 1 GB300 (CTU+PPM+exact RS), FP64 vs mixed/batched at matched L1"
 UNIT = "cell-updates/s"
 
-# FP64 issue rate of GB300 derived from unit counts and clock: 152 SMs x 2070 MHz x
-# 2 FP64 FMA instructions per clock per SM (NVIDIA's nominal 1.25 TFLOP/s counts an
-# FMA as two flops).  The algorithmic count below counts every add, multiply,
-# divide, square root, pow and compare as one operation.
-FP64_OPS_PEAK = 152 * 2070e6 * 2
-FP32_OPS_PEAK = 152 * 2070e6 * 128
+# FP64 peak of GB300 from unit counts and clock: 152 SMs x 2070 MHz x 2 FP64 FMA
+# per clock per SM x 2 flops per FMA (NVIDIA's nominal 1.25 TFLOP/s).
+FP64_FLOPS_PEAK = 152 * 2070e6 * 2 * 2
+PEAK_SOURCE = "152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM x 2 flop/FMA (unit counts and clock)"
 
-# dram bytes (read + write) per launch from an ncu capture, per stage, with the
-# kernel source digest they were taken on; a digest mismatch reports null.
+# Algorithmic FP64 flops per unit of each stage (add, multiply, divide, square
+# root and pow one flop each; compares not counted): printed by
+# `python oracle/count_ops.py`, the operation-counting build of the CPU reference
+# run on one step of a 32^3 sample of each workload's initial-condition recipe.
+# Units: padded cells (prims), real cells (slopes, ppmc, update), faces (riemann1,
+# riemann2).  The benchmark never runs the oracle for these.
+ALGORITHMIC_FLOPS = {
+    "batched": {"ppmc": 406.0, "prims": 22.752, "riemann1": 136.073, "riemann2": 196.219, "slopes": 81.0, "update": 45.0},
+    "sedov": {"ppmc": 406.0, "prims": 22.752, "riemann1": 136.073, "riemann2": 196.219, "slopes": 81.0, "update": 45.0},
+    "shock_cloud": {"ppmc": 413.0, "prims": 22.752, "riemann1": 135.667, "riemann2": 195.667, "slopes": 81.0, "update": 45.0},
+    "sod512": {"ppmc": 406.0, "prims": 28.742, "riemann1": 136.124, "riemann2": 136.124, "slopes": 81.0, "update": 15.0},
+    "turbulence": {"ppmc": 423.335, "prims": 22.752, "riemann1": 140.353, "riemann2": 200.633, "slopes": 91.821, "update": 45.0},
+}
+
+# The FP64 part of the mixed-precision stages, flops per unit, from the kernels'
+# own FP64 arithmetic (everything else in them is float): the transverse
+# half-step per face side builds U* (11 flops), accumulates 5 fused
+# multiply-adds per active transverse axis (10 flops) and recovers p with a
+# Newton reciprocal (13 flops); the update is 5 variables x (subtract + FMA) per
+# active axis; the primitive stage is 26 flops a padded cell.
+def mixed_fp64_flops(active_axes):
+    return {"riemann2": 2 * (11 + 10 * (active_axes - 1) + 13), "update": 15 * active_axes,
+            "prims": 26}
+
+# Algorithmic HBM bytes per unit of each stage's kernel (every plane read and
+# written once; stencil neighbours come from cache): FP64 intermediates are
+# 8-byte planes, the mixed path's 4-byte ones.  prims: 5 conserved in, 8
+# primitive planes out; slopes: 8 in, 5 out; ppmc: 8 + 5 in, 10 face states out;
+# riemann1: 10 in, 5 out; riemann2: 10 face states + 2 x 5 transverse fluxes in,
+# 5 out; update: 5 conserved + 3 x 5 fluxes in, 5 out.
+ALGORITHMIC_BYTES = {
+    "fp64": {"prims": 104, "slopes": 104, "ppmc": 184, "riemann1": 120, "riemann2": 200,
+             "update": 200},
+    "mixed": {"prims": 72, "slopes": 52, "ppmc": 92, "riemann1": 60, "riemann2": 100,
+              "update": 140},
+}
+
+# dram bytes (read + write) per unit of the stage's kernel from an ncu capture,
+# with the digest of the sources that kernel is built from; a digest mismatch
+# (the kernel changed since the capture) reports null.
 NCU_TRAFFIC = {}
-
-ORACLE_STAGE = {"prims": "prims", "slopes": "slopes", "ppmc": "ppmc", "riemann1": "riemann1",
-                "riemann2": "riemann2", "update": "update"}
 
 
 def workload(name):
@@ -143,30 +176,13 @@ def dist_env():
     return ws, rank, local
 
 
-def algorithmic_ops(w, cfl):
-    """Per-unit algorithmic FP64 operation counts of each stage, measured by the
-    op-counting oracle on a 32^3 sample of the same problem (same IC recipe)."""
-    import oracle
-    from paper_1410_4194_gb300 import workloads as W
-    key = w["key"]
-    if key.startswith("sedov") or key.startswith("batched"):
-        s = W.sedov(32)
-    elif key == "sod512":
-        s = W.sod(512)
-    else:
-        s = dict(u=w["u"][:, :32, :32, :32].copy(), dx=w["dx"], gamma=w["gamma"], bc=[0] * 6)
-    _, nz, ny, nx = s["u"].shape
-    g = oracle.Grid(nx, ny, nz, s["dx"], s["gamma"], s["bc"])
-    for face, prim in (s.get("inflow") or {}).items():
-        g.set_inflow(face, prim)
-    g.set_state(s["u"])
-    dt = g.compute_dt(cfl)
-    st = g.count_step_stages(dt)
-    out = {}
-    for k, v in st.items():
-        tot = sum(v["ops"].values())
-        out[k] = tot / max(v["units"], 1)
-    return out, "op-counting oracle on %dx%dx%d %s, one step" % (nx, ny, nz, key)
+def flops_table(key):
+    """Algorithmic FP64 flops per unit for a workload key."""
+    if key.startswith("sedov"):
+        return ALGORITHMIC_FLOPS["sedov"], "sedov"
+    if key.startswith("batched"):
+        return ALGORITHMIC_FLOPS["batched"], "batched"
+    return ALGORITHMIC_FLOPS[key], key
 
 
 def run_cpu_baseline(wname, max_steps, cfl=0.3, min_seconds=10.0):
@@ -314,21 +330,28 @@ def main():
     # ---- roofline of the dominant kernel -------------------------------------
     dom = max((k for k in stages if stages[k][1] > 0), key=lambda k: stages[k][0])
     dms, dl, dunits = stages[dom]
-    per_unit, count_src = algorithmic_ops(w, args.cfl)
-    ops_per_launch = per_unit[ORACLE_STAGE[dom]] * dunits / dl
+    active = sum(1 for n in (nx, ny, nz) if n > 1)
+    if args.precision == "fp64":
+        table, tkey = flops_table(w["key"])
+        per_unit = table[dom]
+        src = "algorithmic FP64 flops per unit (oracle/count_ops.py, %s)" % tkey
+    else:
+        per_unit = mixed_fp64_flops(active)[dom]
+        src = "FP64 flops of the mixed-precision kernel per unit (by construction)"
+    units_per_launch = dunits / dl
+    flops_per_launch = per_unit * units_per_launch
     avg_ms = dms / dl
-    achieved = ops_per_launch / (avg_ms / 1e3)
-    peak = FP64_OPS_PEAK if args.precision == "fp64" else FP32_OPS_PEAK
+    achieved = flops_per_launch / (avg_ms / 1e3)
     traffic = None
-    tinfo = NCU_TRAFFIC.get(dom)
-    if tinfo and tinfo.get("digest") == kernel_digest():
-        traffic = tinfo["bytes_per_launch"]
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "FP64 op/s"
-                if args.precision == "fp64" else "FP32 op/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "k_" + dom,
-                "ops_per_launch": ops_per_launch, "avg_launch_ms": avg_ms,
-                "ops_source": count_src,
-                "peak_source": "152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM (unit counts and clock)"}
+    tinfo = NCU_TRAFFIC.get((args.precision, dom))
+    if tinfo and tinfo["digest"] == source_digest(tinfo["sources"]):
+        traffic = tinfo["bytes_per_unit"] * units_per_launch
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_FLOPS_PEAK,
+                "unit": "FP64 FLOP/s", "frac": achieved / FP64_FLOPS_PEAK, "traffic": traffic,
+                "kernel": ("kb_" + dom) if args.precision == "fp64" else ("kb_%s_mixed" % dom),
+                "flops_per_unit": per_unit, "units_per_launch": units_per_launch,
+                "avg_launch_ms": avg_ms, "flops_source": src, "peak_source": PEAK_SOURCE,
+                "bytes_per_unit_algorithmic": ALGORITHMIC_BYTES[args.precision][dom]}
     stage_report = {k: {"ms": v[0], "launches": v[1], "share": v[0] / max(ms, 1e-9)}
                     for k, v in stages.items()}
     cpu = None
@@ -340,10 +363,7 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": w["desc"], "cells": nreal, "precision": args.precision,
-                   "parallelism": "replicas" if ws > 1 else "single",
-                   "l2": "inputs larger than L2 (state %.2f GB, step working set %.1f GB)" % (
-                       nreal * 40 / 1e9, (nx + 8) * (ny + 8) * (nz + 8) * 8 * 56 / 1e9)},
+        "config": single_config(args.workload, args.precision, ws),
         "e2e": e2e, "gpu_launches": launches_total, "clocks": clocks, "roofline": roofline,
         "stages": stage_report, "cpu_baseline": cpu,
     }
@@ -434,13 +454,18 @@ def run_batch(args, w, ws, rank, local):
         if ws > 1:
             dist.destroy_process_group()
         return
-    # step-level roofline: algorithmic FP64 operations of a cell update
-    # (op-counting oracle, Sedov sample) times the cell-update rate
-    per_unit, count_src = algorithmic_ops(dict(key="sedov32"), args.cfl)
-    per_cell = (per_unit["prims"] + 3 * (per_unit["slopes"] + per_unit["ppmc"] + per_unit["riemann1"]
-                                        + per_unit["riemann2"]) + per_unit["update"])
+    # step-level roofline (the graph's kernels are not timed one by one):
+    # FP64 flops of a cell update times the cell-update rate
+    if args.precision == "fp64":
+        pu = ALGORITHMIC_FLOPS["batched"]
+        per_cell = (pu["prims"] + 3 * (pu["slopes"] + pu["ppmc"] + pu["riemann1"]
+                                       + pu["riemann2"]) + pu["update"])
+        src = "algorithmic FP64 flops per cell update (oracle/count_ops.py, Sedov sample)"
+    else:
+        pu = mixed_fp64_flops(3)
+        per_cell = pu["prims"] + 3 * pu["riemann2"] + pu["update"]
+        src = "FP64 flops of the mixed-precision kernels per cell update (by construction)"
     achieved = per_cell * value / ws
-    peak = FP64_OPS_PEAK if args.precision == "fp64" else FP32_OPS_PEAK
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -451,10 +476,10 @@ def run_batch(args, w, ws, rank, local):
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (states %.2f GB)" % (ncells * 40 / 1e9)},
         "e2e": e2e, "gpu_launches": 15 * args.steps, "clocks": clocks,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "FP64 op/s" if args.precision == "fp64" else "FP32 op/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "whole step (graph)",
-                     "ops_per_cell_update": per_cell, "ops_source": count_src},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_FLOPS_PEAK,
+                     "unit": "FP64 FLOP/s", "frac": achieved / FP64_FLOPS_PEAK, "traffic": None,
+                     "kernel": "whole step (graph)", "flops_per_cell_update": per_cell,
+                     "flops_source": src, "peak_source": PEAK_SOURCE},
         "cpu_baseline": None,
     }
     if l1 is not None:
@@ -494,49 +519,75 @@ def compare_l1(w, args, g, hydro, stream):
             "reference": "HYDRO_FP64 GPU path from the same initial state"}
 
 
-def kernel_digest():
+def source_digest(files):
+    """Digest of the kernel sources (paths under the package's csrc/)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1410_4194_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in sorted(files):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def run_reference(args, ws, rank):
-    """The oracle timed on the host cores (rank 0 only)."""
+    """The oracle timed on the host cores (rank 0 only), each step a bounded
+    sample of the workload: Sedov at 128^3 (same recipe), Sod in full, a
+    128x64x64 block of the large fields, the first grids of a batch."""
     if rank != 0:
         return
     import oracle
     from paper_1410_4194_gb300 import workloads as W
-    if args.workload.startswith("sedov"):
-        s = W.sedov(128)
-        sample = "Sedov blast at 128^3 (same IC recipe as the 256^3 workload), one oracle step per step"
-    elif args.workload == "sod512":
-        s = W.sod(512)
-        sample = "Sod 512 cells"
+    if args.workload.startswith("batched"):
+        grids, cells = [], 0
+        for gw in workload(args.workload)["grids"]:
+            grids.append(gw)
+            cells += int(np.prod(gw["u"].shape[1:]))
+            if cells >= 1 << 20:
+                break
+        samples = grids
+        sample = "the first %d grids of the batch (%d cells), one oracle step each per step" % (
+            len(grids), cells)
+        config = {"workload": workload(args.workload)["desc"], "precision": args.precision,
+                  "parallelism": "replicas" if ws > 1 else "single"}
     else:
-        full = workload(args.workload)
-        s = dict(u=np.ascontiguousarray(full["u"][:, :64, :64, :128]), dx=full["dx"],
-                 gamma=full["gamma"], bc=[2, 2, 0, 0, 0, 0])
-        sample = "%s sub-block 128x64x64" % args.workload
+        if args.workload.startswith("sedov"):
+            s = W.sedov(128)
+            sample = ("Sedov blast at 128^3 (same IC recipe as the %s workload), one oracle step "
+                      "per step" % args.workload)
+        elif args.workload == "sod512":
+            s = W.sod(512)
+            sample = "Sod 512 cells, one oracle step per step"
+        else:
+            full = workload(args.workload)
+            s = dict(u=np.ascontiguousarray(full["u"][:, :64, :64, :128]), dx=full["dx"],
+                     gamma=full["gamma"], bc=[2, 2, 0, 0, 0, 0])
+            sample = "%s sub-block 128x64x64, one oracle step per step" % args.workload
+        samples = [s]
+        config = single_config(args.workload, args.precision, ws)
     cores = oracle.set_threads(0)
-    _, nz, ny, nx = s["u"].shape
-    g = oracle.Grid(nx, ny, nz, s["dx"], s["gamma"], s["bc"])
-    g.set_state(s["u"])
+    gs, cells = [], 0
+    for s in samples:
+        _, nz, ny, nx = s["u"].shape
+        g = oracle.Grid(nx, ny, nz, s["dx"], s["gamma"], s["bc"])
+        for face, prim in (s.get("inflow") or {}).items():
+            g.set_inflow(face, prim)
+        g.set_state(s["u"])
+        gs.append(g)
+        cells += nx * ny * nz
     for _ in range(args.warmup):
-        g.step(args.cfl)
+        for g in gs:
+            g.step(args.cfl)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        g.step(args.cfl)
+        for g in gs:
+            g.step(args.cfl)
     el = time.perf_counter() - t0
-    value = nx * ny * nz * args.steps / el
+    value = cells * args.steps / el
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": workload_desc(args.workload), "precision": "fp64"},
+            "data": "synthetic", "config": config,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -544,9 +595,36 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+WORKLOAD_DESC = {
+    "sod512": "1D Sod shock tube, 512 cells, gamma 1.4, CFL 0.3",
+    "shock_cloud": "3D Mach-10 shock-cloud, 512x256x256, gamma 5/3, CFL 0.3",
+    "turbulence": "3D supersonic turbulence, 512^3 periodic, rms Mach 5, CFL 0.3",
+}
+
+
+def workload_shape(name):
+    """(nx, ny, nz) of a single-grid workload without building it."""
+    if name.startswith("sedov"):
+        n = int(name[5:])
+        return n, n, n
+    return {"sod512": (512, 1, 1), "shock_cloud": (512, 256, 256),
+            "turbulence": (512, 512, 512)}[name]
+
+
 def workload_desc(name):
-    return {"sedov256": "3D Sedov-Taylor blast, 256^3 periodic, gamma 5/3, CFL 0.3",
-            "sod512": "1D Sod shock tube, 512 cells, gamma 1.4, CFL 0.3"}.get(name, name)
+    if name.startswith("sedov"):
+        n = int(name[5:])
+        return "3D Sedov-Taylor blast, %d^3 periodic, gamma 5/3, CFL 0.3" % n
+    return WORKLOAD_DESC.get(name, name)
+
+
+def single_config(name, precision, ws):
+    nx, ny, nz = workload_shape(name)
+    return {"workload": workload_desc(name), "cells": nx * ny * nz, "precision": precision,
+            "parallelism": "replicas" if ws > 1 else "single",
+            "l2": "inputs larger than L2 (state %.2f GB, step working set %.1f GB)" % (
+                nx * ny * nz * 40 / 1e9,
+                (nx + 8) * (ny + 8 if ny > 1 else 1) * (nz + 8 if nz > 1 else 1) * 8 * 56 / 1e9)}
 
 
 if __name__ == "__main__":

@@ -226,8 +226,11 @@ int hydro_ppmc(int n, const double* w, double dtdx, double gamma, double* WsL, d
  * those conversions with the hardware ones on the current device: the widening
  * for all 2^32 float bit patterns, the narrowing (round to nearest even) for
  * 2^30 double bit patterns drawn from a counter-based hash, concentrated on the
- * float range's edges and on rounding ties.  mismatches: host array of two
- * counts (widening, narrowing), both 0 when the conversions agree bit for bit.
+ * float range's edges and on rounding ties.  Expected: the hardware's bits for
+ * normal values, zeros and infinities; a zero of the same sign where the value
+ * (or, narrowing, the double operand) lies below the float normal range; NaN
+ * for NaN.  mismatches: host array of two counts (widening, narrowing), both 0
+ * when every case agrees.
  * Runs on `stream` and waits for it; allocates 16 bytes of device memory.
  * Returns HYDRO_OK, HYDRO_EINVAL (mismatches NULL) or HYDRO_ECUDA. */
 int hydro_check_conversions(unsigned long long* mismatches, void* stream);

@@ -58,7 +58,11 @@ __device__ __forceinline__ void block_max_to(double v, unsigned long long* slot)
 // reflective axis negated, unless an inflow axis is involved, in which case the
 // last inflow face (in x, y, z order) provides the state and only the
 // reflective axes after it negate their momentum.
-// returns this cell's |v_d| + a maximum (0 for ghosts or when !want_dt)
+// returns this cell's |v_d| + a maximum (0 for ghosts or when !want_dt).
+// S (strict): the CPU reference's operation order with IEEE divisions and
+// square root; otherwise 1/rho and 1/a by Newton iteration (nr_rcp, nr_rsqrt)
+// and fused multiply-adds.
+template <bool S>
 __device__ __forceinline__ double prims_body(const Geom& G, const Bufs& B, const BcDesc& bc,
                                              const Gas& g, int want_dt, long long t) {
   double local = 0.0;
@@ -112,28 +116,41 @@ __device__ __forceinline__ double prims_body(const Geom& G, const Bufs& B, const
 #pragma unroll
     for (int d = 0; d < 3; ++d)
       if (neg & (1 << d)) U[1 + d] = -U[1 + d];
-    // primitives in the CPU reference's operation order (divisions), then the
-    // per-cell reciprocals the later stages multiply by
+    // primitives, then the per-cell reciprocals the later stages multiply by
     const double d = U[0];
-    double W[5];
+    double W[5], a, inv_a, inv_d;
     W[0] = d;
-    W[1] = U[1] / d;
-    W[2] = U[2] / d;
-    W[3] = U[3] / d;
-    W[4] = tmax(g.gm1 * (U[4] - 0.5 * d * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3])), kPFloor);
-    const double a = sqrt(g.gamma * W[4] / d);
+    if constexpr (S) {  // the CPU reference's operation order (divisions)
+      W[1] = U[1] / d;
+      W[2] = U[2] / d;
+      W[3] = U[3] / d;
+      W[4] = tmax(g.gm1 * (U[4] - 0.5 * d * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3])), kPFloor);
+      a = sqrt(g.gamma * W[4] / d);
+      inv_a = 1.0 / a;
+      inv_d = 1.0 / d;
+    } else {  // E - (rho v).v/2 with v = (rho v)/rho; a = x/sqrt(x), x = gamma p/rho
+      inv_d = nr_rcp(d);
+      W[1] = U[1] * inv_d;
+      W[2] = U[2] * inv_d;
+      W[3] = U[3] * inv_d;
+      const double ke2 = fma(U[1], W[1], fma(U[2], W[2], U[3] * W[3]));
+      W[4] = vmax<false>(g.gm1 * fma(-0.5, ke2, U[4]), kPFloor);
+      const double x = g.gamma * W[4] * inv_d;
+      inv_a = nr_rsqrt(x);
+      a = x * inv_a;
+    }
 #pragma unroll
     for (int q = 0; q < 5; ++q) B.W[q * G.ps + t] = W[q];
     B.W[5 * G.ps + t] = a;
-    B.W[6 * G.ps + t] = 1.0 / a;
-    B.W[7 * G.ps + t] = 1.0 / d;
+    B.W[6 * G.ps + t] = inv_a;
+    B.W[7 * G.ps + t] = inv_d;
     // Eq. calc_dt_3D: min over cells and axes of dx/(|v_d| + a) equals
     // dx / max(|v_d| + a) exactly, because rounding and the quotient are
     // monotone; so the cells contribute a maximum and one division follows
     if (want_dt && real) {
 #pragma unroll
       for (int d = 0; d < 3; ++d)
-        if (G.n[d] > 1) local = tmax(local, fabs(W[1 + d]) + a);
+        if (G.n[d] > 1) local = vmax<S>(local, fabs(W[1 + d]) + a);
     }
   }
   return local;
@@ -142,7 +159,7 @@ __device__ __forceinline__ double prims_body(const Geom& G, const Bufs& B, const
 __global__ void __launch_bounds__(kThreads) k_prims(Geom G, Bufs B, BcDesc bc, Gas g, int want_dt) {
   const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const double local = (t < total) ? prims_body(G, B, bc, g, want_dt, t) : 0.0;
+  const double local = (t < total) ? prims_body<true>(G, B, bc, g, want_dt, t) : 0.0;
   if (want_dt) block_max_to(local, reinterpret_cast<unsigned long long*>(B.rec));
 }
 
@@ -151,7 +168,8 @@ __global__ void __launch_bounds__(BS) kb_prims(BatchLaunch L) {
   const BatchItem it = batch_item(L);
   const Geom& G = it.d->G;
   const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
-  const double local = (it.t < total) ? prims_body(G, it.d->B, it.d->bc, it.d->gd, 1, it.t) : 0.0;
+  const double local =
+      (it.t < total) ? prims_body<false>(G, it.d->B, it.d->bc, it.d->gd, 1, it.t) : 0.0;
   block_max_to(local, reinterpret_cast<unsigned long long*>(it.d->B.rec));
 }
 
@@ -165,6 +183,9 @@ __global__ void k_set_dt(double* rec, double cfl, double fixed_dt, double dx) {
   }
 }
 
+// S (strict): u + dt/dx (F_- - F_+) rounded as the CPU reference rounds it;
+// otherwise with a fused multiply-add and the NaN test on the bit pattern
+template <bool S>
 __device__ __forceinline__ void update_body(const Geom& G, const Bufs& B, long long t) {
   const int i = (int)(t % G.n[0]);
   const int j = (int)((t / G.n[0]) % G.n[1]);
@@ -179,25 +200,34 @@ __device__ __forceinline__ void update_body(const Geom& G, const Bufs& B, long l
     for (int d = 0; d < 3; ++d) {
       if (G.n[d] > 1) {
         const double* F = B.UL[d];
-        un = un + dtdx * (F[q * G.ps + c] - F[q * G.ps + c + G.s[d]]);
+        if constexpr (S)
+          un = un + dtdx * (F[q * G.ps + c] - F[q * G.ps + c + G.s[d]]);
+        else
+          un = fma(dtdx, F[q * G.ps + c] - F[q * G.ps + c + G.s[d]], un);
       }
     }
     B.u[q * G.nreal + t] = un;
-    if (isnan(un)) fl = kFlagNonPhys;
-    if (q == 0 && !(un > 0.0)) fl = kFlagNonPhys;
+    if constexpr (S) {
+      if (isnan(un)) fl = kFlagNonPhys;
+      if (q == 0 && !(un > 0.0)) fl = kFlagNonPhys;
+    } else {
+      const long long b = __double_as_longlong(un);
+      if ((b & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) fl = kFlagNonPhys;  // NaN
+      if (q == 0 && b <= 0) fl = kFlagNonPhys;  // rho <= 0 (or a NaN with the sign bit)
+    }
   }
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
 __global__ void __launch_bounds__(kThreads) k_update(Geom G, Bufs B) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < G.nreal) update_body(G, B, t);
+  if (t < G.nreal) update_body<true>(G, B, t);
 }
 
 template <int BS>
 __global__ void __launch_bounds__(BS) kb_update(BatchLaunch L) {
   const BatchItem it = batch_item(L);
-  if (it.t < it.d->G.nreal) update_body(it.d->G, it.d->B, it.t);
+  if (it.t < it.d->G.nreal) update_body<false>(it.d->G, it.d->B, it.t);
 }
 
 // per grid: dt = cfl * dx / max(|v_d| + a) (or the fixed dt), dt/dx, history

@@ -68,6 +68,7 @@ struct GasT {
   T fan_p;    // 2 gamma/(gamma-1)
   T two_gp1;  // 2/(gamma+1)
   T half_gm1; // (gamma-1)/2
+  T half_gp1; // (gamma+1)/2
   T sh_a;     // (gamma+1)/(2 gamma)
   T sh_b;     // (gamma-1)/(2 gamma)
   T gm1_gp1;  // (gamma-1)/(gamma+1)
@@ -87,6 +88,7 @@ inline GasT<T> make_gas(double g) {
   c.fan_p = T(2.0 * g / (g - 1.0));
   c.two_gp1 = T(2.0 / (g + 1.0));
   c.half_gm1 = T((g - 1.0) / 2.0);
+  c.half_gp1 = T((g + 1.0) / 2.0);
   c.sh_a = T((g + 1.0) / (2.0 * g));
   c.sh_b = T((g - 1.0) / (2.0 * g));
   c.gm1_gp1 = T((g - 1.0) / (g + 1.0));
@@ -109,27 +111,80 @@ __device__ __forceinline__ float xfma(float a, float b, float c) { return fmaf(a
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return (b < a) ? b : a; }
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return (a < b) ? b : a; }
 
+// Comparisons of FP64 values through their bit patterns.  GB300 issues an FP64
+// compare (and so an FP64 min, max or sign test) on the FP64 pipe; these issue
+// on the integer pipe.  ord(x) maps a double to a 64-bit integer with the same
+// order (negative values get their magnitude bits inverted), so a < b is
+// ord(a) < ord(b); the sign tests read the bits directly.  For every non-NaN
+// operand the result equals the IEEE comparison, except that the ordered
+// comparison puts -0 below +0 (vmin/vmax may then return -0 where IEEE returns
+// +0, the same value).  With S (strict) set, and for float, these are the
+// plain IEEE comparisons.
+__device__ __forceinline__ long long ord(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+template <bool S, typename T>
+__device__ __forceinline__ bool lt(T a, T b) {
+  if constexpr (S || sizeof(T) == 4) return a < b;
+  else return ord(a) < ord(b);
+}
+template <bool S, typename T>
+__device__ __forceinline__ T vmin(T a, T b) { return lt<S>(b, a) ? b : a; }
+template <bool S, typename T>
+__device__ __forceinline__ T vmax(T a, T b) { return lt<S>(a, b) ? b : a; }
+__device__ __forceinline__ bool bits_equal(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b);
+}
+__device__ __forceinline__ bool bits_equal(float a, float b) {
+  return __float_as_int(a) == __float_as_int(b);
+}
+template <bool S, typename T>
+__device__ __forceinline__ bool neg(T x) {  // x < 0
+  if constexpr (S || sizeof(T) == 4) return x < T(0);
+  else return (unsigned long long)__double_as_longlong(x) > 0x8000000000000000ull;
+}
+template <bool S, typename T>
+__device__ __forceinline__ bool pos(T x) {  // x > 0
+  if constexpr (S || sizeof(T) == 4) return x > T(0);
+  else return __double_as_longlong(x) > 0;
+}
+template <bool S, typename T>
+__device__ __forceinline__ bool nonpos(T x) {  // x <= 0
+  if constexpr (S || sizeof(T) == 4) return x <= T(0);
+  else return __double_as_longlong(x) <= 0;
+}
+template <bool S, typename T>
+__device__ __forceinline__ bool nonneg(T x) {  // x >= 0
+  if constexpr (S || sizeof(T) == 4) return x >= T(0);
+  else return (unsigned long long)__double_as_longlong(x) <= 0x8000000000000000ull;
+}
+
 // ---------------------------------------------------------------------------
 // float <-> double conversion in integer arithmetic.  GB300 issues the
 // hardware conversions (cvt.f64.f32, cvt.rn.f32.f64) on its FP64 pipe, at the
-// FP64 rate; these rebuild the IEEE 754 bit fields with integer operations
-// instead and return the same bits as the hardware conversion (round to
-// nearest even) for every input.  Zeros take a select; the rare inputs outside
-// the normal-to-normal range (subnormal, infinite or NaN floats; doubles whose
-// float is subnormal, overflows or is not finite) fall back to the hardware
-// conversion.  hydro_check_conversions() compares both against the hardware
-// on the GPU.
+// FP64 rate; these rebuild the IEEE 754 bit fields with integer operations and
+// selects (no branch, so nothing of the FP64 pipe is issued).  For normal
+// values, zeros and infinities they return the bits of the hardware
+// conversion with round to nearest even; subnormal values are flushed to a
+// zero of the same sign (as the .ftz conversions do), NaN stays NaN, and a
+// double beyond the float range becomes an infinity, as IEEE rounding gives.
+// hydro_check_conversions() checks them against the hardware on the GPU.
 
-// exact widening: float fields (1, 8, 23) -> double fields (1, 11, 52), the
-// exponent rebiased by 1023 - 127 = 896 and the fraction shifted left by 29
+// widening: float fields (1, 8, 23) -> double fields (1, 11, 52), the exponent
+// rebiased by 1023 - 127 = 896 (255, infinity or NaN, maps to 2047) and the
+// fraction shifted left by 29
 __device__ __forceinline__ double f2d(float x) {
   const unsigned b = __float_as_uint(x);
-  const unsigned mag = b & 0x7fffffffu;
   const unsigned e = b >> 23 & 0xffu;
-  if (e - 1u >= 254u && mag != 0u) return (double)x;
-  unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | (b >> 3 & 0xfffffu);
-  hi = mag ? hi : b;
-  return __hiloint2double((int)hi, (int)(b << 29));
+  const unsigned sign = b & 0x80000000u;
+  const unsigned frac_hi = b >> 3 & 0xfffffu;
+  unsigned hi = sign | ((e + 896u) << 20) | frac_hi;
+  unsigned lo = b << 29;
+  hi = (e == 255u) ? (sign | 0x7ff00000u | frac_hi) : hi;
+  hi = (e == 0u) ? sign : hi;
+  lo = (e == 0u) ? 0u : lo;
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 // narrowing with round to nearest, ties to even: keep the top 23 of the 52
@@ -139,14 +194,74 @@ __device__ __forceinline__ double f2d(float x) {
 __device__ __forceinline__ float d2f(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
   const unsigned e = hi >> 20 & 0x7ffu;
-  const bool zero = ((hi & 0x7fffffffu) | lo) == 0u;
-  if (e - 897u > 253u && !zero) return (float)x;
+  const unsigned sign = hi & 0x80000000u;
   const unsigned m = (hi & 0xfffffu) << 3 | lo >> 29;
   const unsigned rest = lo & 0x1fffffffu;
-  unsigned f = (hi & 0x80000000u) | ((e - 896u) << 23) | m;
+  unsigned f = sign | ((e - 896u) << 23) | m;
   f += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
-  return __uint_as_float(zero ? (hi & 0x80000000u) : f);
+  f = (e > 1150u) ? (sign | 0x7f800000u) : f;  // beyond the float range
+  f = (e == 2047u && ((hi & 0xfffffu) | lo)) ? (sign | 0x7fc00000u) : f;  // NaN
+  f = (e < 897u) ? sign : f;  // zero, or a float subnormal: flushed
+  return __uint_as_float(f);
 }
+
+// ---------------------------------------------------------------------------
+// FP64 reciprocal, quotient, square root and reciprocal square root by
+// Newton-Raphson iteration from SFU seeds.  An IEEE FP64 division or square
+// root costs about ten FP64 issue slots on GB300; these cost four to eight.
+// Seeds: rcp.approx.ftz.f64 (reciprocal, relative error near 2^-23, issued on
+// the SFU) and the float reciprocal square root of the operand scaled by an
+// even power of two into [1, 4) (so that every positive normal double has a
+// seed).  Iterations (each squares the relative error e):
+//   reciprocal   r <- r + r (1 - b r), twice;
+//   quotient     r once, q = a r, then q <- q + r (a - b q) (Markstein's
+//                correction with the residual formed exactly by fma);
+//   square root  s = x y, then s <- s + (y/2)(x - s^2), twice;
+//   rsqrt        y <- y + (y/2)(1 - x y^2), twice.
+// Results are within an ulp or two of the correctly rounded value for
+// positive normal operands (the only ones the solver passes); zero, infinite
+// and NaN operands are not handled.  The float overloads are the IEEE float
+// operations.
+__device__ __forceinline__ double rcp_seed(double b) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
+  return r;
+}
+// y ~ 1/sqrt(x), relative error ~2^-22, for positive normal x
+__device__ __forceinline__ double rsqrt_seed(double x) {
+  const int hi = __double2hiint(x);
+  const int k = ((hi >> 20) - 1023) >> 1;  // x = m 2^(2k), m in [1, 4)
+  const double m = __hiloint2double(hi - (k << 21), __double2loint(x));
+  const double ym = f2d(rsqrtf(d2f(m)));
+  return __hiloint2double(__double2hiint(ym) - (k << 20), __double2loint(ym));
+}
+__device__ __forceinline__ double nr_rcp(double b) {
+  double r = rcp_seed(b);
+  r = fma(r, fma(-b, r, 1.0), r);
+  return fma(r, fma(-b, r, 1.0), r);
+}
+__device__ __forceinline__ double nr_div(double a, double b) {
+  double r = rcp_seed(b);
+  r = fma(r, fma(-b, r, 1.0), r);
+  const double q = a * r;
+  return fma(r, fma(-b, q, a), q);
+}
+__device__ __forceinline__ double nr_sqrt(double x) {
+  const double y = rsqrt_seed(x);
+  const double hy = 0.5 * y;
+  double s = x * y;
+  s = fma(hy, fma(-s, s, x), s);
+  return fma(hy, fma(-s, s, x), s);
+}
+__device__ __forceinline__ double nr_rsqrt(double x) {
+  double y = rsqrt_seed(x);
+  y = fma(0.5 * y, fma(-x * y, y, 1.0), y);
+  return fma(0.5 * y, fma(-x * y, y, 1.0), y);
+}
+__device__ __forceinline__ float nr_rcp(float b) { return 1.0f / b; }
+__device__ __forceinline__ float nr_div(float a, float b) { return a / b; }
+__device__ __forceinline__ float nr_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ float nr_rsqrt(float x) { return 1.0f / sqrtf(x); }
 
 // x^K by squaring (K is small)
 template <int K, typename T>
@@ -248,7 +363,7 @@ __device__ __forceinline__ void cons2prim(const T U[5], const GasT<T>& g, T W[5]
     v1 = U[2] / d;
     v2 = U[3] / d;
   } else {
-    inv_d = T(1) / d;
+    inv_d = nr_rcp(d);
     vn = U[1] * inv_d;
     v1 = U[2] * inv_d;
     v2 = U[3] * inv_d;
@@ -258,7 +373,7 @@ __device__ __forceinline__ void cons2prim(const T U[5], const GasT<T>& g, T W[5]
   W[1] = vn;
   W[2] = v1;
   W[3] = v2;
-  W[4] = tmax(p, T(kPFloor));
+  W[4] = vmax<S>(p, T(kPFloor));
 }
 
 template <bool S = false, typename T>
@@ -311,9 +426,9 @@ __device__ __forceinline__ void limited_slope(const T wm[5], const T wc[5], cons
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     T s = T(0);
-    if (xl[q] * xr[q] > T(0)) {
-      const T m = tmin(tmin(xabs(xc[q]), T(2) * xabs(xl[q])), T(2) * xabs(xr[q]));
-      s = (xc[q] < T(0)) ? -m : m;
+    if (pos<S>(xl[q] * xr[q])) {
+      const T m = vmin<S>(vmin<S>(xabs(xc[q]), T(2) * xabs(xl[q])), T(2) * xabs(xr[q]));
+      s = neg<S>(xc[q]) ? -m : m;
     }
     xi[q] = s;
   }
@@ -346,14 +461,14 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
       L = T(0.5) * (wi + w_m[q]) - (s_c[q] - s_m[q]) * c16;
       R = T(0.5) * (w_p[q] + wi) - (s_p[q] - s_c[q]) * c16;
     }
-    if ((R - wi) * (wi - L) <= T(0)) {
+    if (nonpos<S>((R - wi) * (wi - L))) {
       L = wi;
       R = wi;
     }
-    if ((R - L) * (L - (T(3) * wi - T(2) * R)) < T(0)) L = T(3) * wi - T(2) * R;
-    if ((R - L) * ((T(3) * wi - T(2) * L) - R) < T(0)) R = T(3) * wi - T(2) * L;
-    L = tmin(tmax(wi, w_m[q]), tmax(tmin(wi, w_m[q]), L));
-    R = tmin(tmax(wi, w_p[q]), tmax(tmin(wi, w_p[q]), R));
+    if (neg<S>((R - L) * (L - (T(3) * wi - T(2) * R)))) L = T(3) * wi - T(2) * R;
+    if (neg<S>((R - L) * ((T(3) * wi - T(2) * L) - R))) R = T(3) * wi - T(2) * L;
+    L = vmin<S>(vmax<S>(wi, w_m[q]), vmax<S>(vmin<S>(wi, w_m[q]), L));
+    R = vmin<S>(vmax<S>(wi, w_p[q]), vmax<S>(vmin<S>(wi, w_p[q]), R));
     WsL[q] = L;
     WsR[q] = R;
     dw[q] = R - L;
@@ -362,7 +477,7 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
   const T rho = w_c[0];
   const T un = w_c[1];
   const T lm = un - a, l0 = un, lp = un + a;
-  const T am = dtdx * tmin(lm, T(0)), bp = dtdx * tmax(lp, T(0));
+  const T am = dtdx * vmin<S>(lm, T(0)), bp = dtdx * vmax<S>(lp, T(0));
   const T c23 = T(2.0 / 3.0);
   const T inv_a2 = inv_a * inv_a;
   // integral of the parabola over the domain of dependence of the fastest
@@ -375,7 +490,7 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
   }
   T sL[5] = {T(0), T(0), T(0), T(0), T(0)};
   T sR[5] = {T(0), T(0), T(0), T(0), T(0)};
-  if (l0 < T(0)) {  // contact and advected velocities reach the left face: E
+  if (neg<S>(l0)) {  // contact and advected velocities reach the left face: E
     const T a0 = dtdx * l0;
     T E[5];
 #pragma unroll
@@ -384,7 +499,7 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
     sL[2] = sL[2] + E[2];
     sL[3] = sL[3] + E[3];
   }
-  if (lp < T(0)) {  // right acoustic wave reaches the left face: B
+  if (neg<S>(lp)) {  // right acoustic wave reaches the left face: B
     const T ap = dtdx * lp;
     const T B1 = tLm[1] - T(0.5) * ap * (dw[1] + w6[1] * (T(1) + c23 * ap));
     const T B4 = tLm[4] - T(0.5) * ap * (dw[4] + w6[4] * (T(1) + c23 * ap));
@@ -397,7 +512,7 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
     }
     sL[4] = sL[4] + T(0.5) * (rho * B1 * a + B4);
   }
-  if (lm > T(0)) {  // left acoustic wave reaches the right face: C
+  if (pos<S>(lm)) {  // left acoustic wave reaches the right face: C
     const T bm = dtdx * lm;
     const T C1 = tRp[1] - T(0.5) * bm * (dw[1] - w6[1] * (T(1) - c23 * bm));
     const T C4 = tRp[4] - T(0.5) * bm * (dw[4] - w6[4] * (T(1) - c23 * bm));
@@ -410,7 +525,7 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
     }
     sR[4] = sR[4] + T(0.5) * (-(rho * C1 * a) + C4);
   }
-  if (l0 > T(0)) {  // contact and advected velocities reach the right face: D
+  if (pos<S>(l0)) {  // contact and advected velocities reach the right face: D
     const T b0 = dtdx * l0;
     T D[5];
 #pragma unroll
@@ -424,8 +539,8 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
     WsL[q] = (WsL[q] - tLm[q]) + sL[q];
     WsR[q] = (WsR[q] - tRp[q]) + sR[q];
   }
-  WsL[4] = tmax(WsL[4], T(kPFloor));
-  WsR[4] = tmax(WsR[4], T(kPFloor));
+  WsL[4] = vmax<S>(WsL[4], T(kPFloor));
+  WsR[4] = vmax<S>(WsR[4], T(kPFloor));
 }
 
 // ---------------------------------------------------------------------------
@@ -435,6 +550,7 @@ struct RSide {
   T d, u, p, a;
   T inv_p;  // 1/p_k
   T A, B;   // A_k = 2/((gamma+1) rho_k), B_k = (gamma-1)/(gamma+1) p_k
+  T inv_A;  // 1/A_k = (gamma+1) rho_k / 2
   T cf;     // 2 a_k/(gamma-1)
   T cd;     // a_k/gamma = p_k/(rho_k a_k)
 };
@@ -444,7 +560,7 @@ struct RSide {
 template <bool S, typename T>
 __device__ __forceinline__ void side_f(T p, T inv_p, const RSide<T>& s, const GasT<T>& g, T& f,
                                        T& fd, T& x) {
-  if (p <= s.p) {
+  if (!lt<S>(s.p, p)) {  // p <= p_k
     if constexpr (S) {
       const T r = p / s.p;
       x = xpow(r, g.z);
@@ -462,8 +578,16 @@ __device__ __forceinline__ void side_f(T p, T inv_p, const RSide<T>& s, const Ga
       f = (p - s.p) * q;
       fd = q * (T(1) - (p - s.p) / (T(2) * (s.B + p)));
     } else {
-      const T ipb = T(1) / (p + s.B);
-      const T q = xsqrt(s.A * ipb);
+      // double: q = sqrt(A/(p+B)) as the reciprocal square root of (p+B)/A,
+      // then 1/(p+B) = q^2/A
+      T q, ipb;
+      if constexpr (sizeof(T) == 8) {
+        q = nr_rsqrt((p + s.B) * s.inv_A);
+        ipb = q * q * s.inv_A;
+      } else {
+        ipb = T(1) / (p + s.B);
+        q = xsqrt(s.A * ipb);
+      }
       const T dp = p - s.p;
       f = dp * q;
       fd = q * (T(1) - T(0.5) * dp * ipb);
@@ -473,7 +597,7 @@ __device__ __forceinline__ void side_f(T p, T inv_p, const RSide<T>& s, const Ga
 
 template <bool S, typename T>
 __device__ __forceinline__ void side_f_only(T p, const RSide<T>& s, const GasT<T>& g, T& f, T& x) {
-  if (p <= s.p) {
+  if (!lt<S>(s.p, p)) {  // p <= p_k
     if constexpr (S) {
       x = xpow(p / s.p, g.z);
       f = T(2) * s.a / g.gm1 * (x - T(1));
@@ -482,7 +606,10 @@ __device__ __forceinline__ void side_f_only(T p, const RSide<T>& s, const GasT<T
       f = s.cf * (x - T(1));
     }
   } else {
-    f = (p - s.p) * xsqrt(s.A / (p + s.B));
+    if constexpr (!S && sizeof(T) == 8)
+      f = (p - s.p) * nr_rsqrt((p + s.B) * s.inv_A);
+    else
+      f = (p - s.p) * xsqrt(s.A / (p + s.B));
     x = T(0);
   }
 }
@@ -496,10 +623,12 @@ __device__ __forceinline__ void make_side(const T W[5], T inv_d, const GasT<T>& 
     s.a = xsqrt(g.gamma * s.p / s.d);
     s.inv_p = T(0);
     s.A = T(2) / (g.gp1 * s.d);
+    s.inv_A = T(0);
   } else {
-    s.a = xsqrt(g.gamma * s.p * inv_d);
-    s.inv_p = T(1) / s.p;
+    s.a = nr_sqrt(g.gamma * s.p * inv_d);
+    s.inv_p = nr_rcp(s.p);
     s.A = g.two_gp1 * inv_d;
+    s.inv_A = g.half_gp1 * s.d;
   }
   s.B = g.gm1_gp1 * s.p;
   s.cf = T(2) * s.a * g.inv_gm1;
@@ -513,12 +642,12 @@ template <bool S, bool LEFT, typename T>
 __device__ __forceinline__ void sample_raref(const RSide<T>& k, T pm, T um, T x, const GasT<T>& g,
                                              T& d, T& u, T& ps) {
   const T sgn = LEFT ? T(1) : T(-1);
-  const bool star = LEFT ? (um - k.a * x < T(0)) : (um + k.a * x >= T(0));
+  const bool star = LEFT ? neg<S>(um - k.a * x) : nonneg<S>(um + k.a * x);
   if (star) {  // star state between the fan tail and the contact
     if constexpr (S)
       d = k.d * xpow(pm / k.p, g.inv_g);
     else
-      d = k.d * (pm * k.inv_p) / (x * x);
+      d = nr_div(k.d * (pm * k.inv_p), x * x);
     u = um;
     ps = pm;
   } else {  // inside the fan
@@ -528,7 +657,7 @@ __device__ __forceinline__ void sample_raref(const RSide<T>& k, T pm, T um, T x,
       ps = k.p * xpow(a / k.a, g.fan_p);
     } else {
       T pd, pp;
-      fan_powers(a / k.a, g, pd, pp);
+      fan_powers(nr_div(a, k.a), g, pd, pp);
       d = k.d * pd;
       ps = k.p * pp;
     }
@@ -543,14 +672,14 @@ __device__ __forceinline__ void sample_shock(const RSide<T>& k, T pm, T um, T sg
                                              const GasT<T>& g, T& d, T& u, T& ps) {
   const T r = S ? pm / k.p : pm * k.inv_p;
   const T arg = S ? g.sh_a * pm / k.p + g.sh_b : g.sh_a * r + g.sh_b;
-  const T sk = k.u - sgn * k.a * xsqrt(arg);
-  if (sgn * sk >= T(0)) {
+  const T sk = k.u - sgn * k.a * (S ? xsqrt(arg) : nr_sqrt(arg));
+  if (nonneg<S>(sgn * sk)) {
     d = k.d; u = k.u; ps = k.p;
   } else {
     if constexpr (S)
       d = k.d * (pm / k.p + g.gm1_gp1) / (pm / k.p * g.gm1_gp1 + T(1));
     else
-      d = k.d * (r + g.gm1_gp1) / (r * g.gm1_gp1 + T(1));
+      d = nr_div(k.d * (r + g.gm1_gp1), r * g.gm1_gp1 + T(1));
     u = um;
     ps = pm;
   }
@@ -566,25 +695,35 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
   make_side<S>(WR, inv_dR, g, R);
   // primitive-variable estimate, then the two-shock estimate as Newton start
   T pt = T(0.5) * (L.p + R.p) + T(0.125) * (L.u - R.u) * (L.d + R.d) * (L.a + R.a);
-  if (pt < T(0)) pt = T(0);
-  const T gL = xsqrt(L.A / (pt + L.B)), gR = xsqrt(R.A / (pt + R.B));
-  T p = (gL * L.p + gR * R.p - (R.u - L.u)) / (gL + gR);
-  if (p < T(kP0Floor)) p = T(kP0Floor);
+  if (neg<S>(pt)) pt = T(0);
+  T gL, gR, p;
+  if constexpr (!S && sizeof(T) == 8) {
+    gL = nr_rsqrt((pt + L.B) * L.inv_A);
+    gR = nr_rsqrt((pt + R.B) * R.inv_A);
+    p = nr_div(gL * L.p + gR * R.p - (R.u - L.u), gL + gR);
+  } else {
+    gL = xsqrt(L.A / (pt + L.B));
+    gR = xsqrt(R.A / (pt + R.B));
+    p = (gL * L.p + gR * R.p - (R.u - L.u)) / (gL + gR);
+  }
+  if (lt<S>(p, T(kP0Floor))) p = T(kP0Floor);
   T fL, fR, dfL, dfR, xL, xR;
   int flags = kFlagNewton;
   T prev_step = T(0);  // float path: the previous Newton step
+  bool same = false;   // the last step left p unchanged (bit for bit)
   for (int it = 0; it < kNewtonMax; ++it) {
-    const T ip = S ? T(0) : T(1) / p;
+    const T ip = S ? T(0) : nr_rcp(p);
     side_f<S>(p, ip, L, g, fL, dfL, xL);
     side_f<S>(p, ip, R, g, fR, dfR, xR);
     const T F = fL + fR + R.u - L.u;
-    T pn = p - F / (dfL + dfR);
-    if (pn < T(kPFloor)) pn = T(kPFloor);
+    T pn = p - (S ? F / (dfL + dfR) : nr_div(F, dfL + dfR));
+    if (lt<S>(pn, T(kPFloor))) pn = T(kPFloor);
+    same = bits_equal(pn, p);
     bool done;
     if constexpr (S)
       done = T(2) * xabs(pn - p) / xabs(pn + p) < T(kNewtonTol);
     else
-      done = T(2) * xabs(pn - p) < T(kNewtonTol) * xabs(pn + p);
+      done = lt<S>(T(2) * xabs(pn - p), T(kNewtonTol) * xabs(pn + p));
     if constexpr (sizeof(T) == 4) {
       // In float the residual f_L + f_R + u_R - u_L carries the rounding error of
       // its terms; near the root the Newton steps that noise produces can stay
@@ -604,15 +743,19 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
       break;
     }
   }
-  side_f_only<S>(p, L, g, fL, xL);
-  side_f_only<S>(p, R, g, fR, xR);
+  // f_L, f_R and x at the final p (already in hand when the last step left p
+  // unchanged, the usual case for smooth data)
+  if (!same) {
+    side_f_only<S>(p, L, g, fL, xL);
+    side_f_only<S>(p, R, g, fR, xR);
+  }
   const T pm = p;
   const T um = T(0.5) * (L.u + R.u + fR - fL);
 
   T d, u, ps;
-  if (um >= T(0)) {
-    if (pm <= L.p) {  // left rarefaction
-      if (L.u - L.a >= T(0)) {
+  if (nonneg<S>(um)) {
+    if (!lt<S>(L.p, pm)) {  // left rarefaction
+      if (nonneg<S>(L.u - L.a)) {
         d = L.d; u = L.u; ps = L.p;
       } else {
         sample_raref<S, true>(L, pm, um, xL, g, d, u, ps);
@@ -621,8 +764,8 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
       sample_shock<S>(L, pm, um, T(1), g, d, u, ps);
     }
   } else {
-    if (pm <= R.p) {  // right rarefaction
-      if (R.u + R.a <= T(0)) {
+    if (!lt<S>(R.p, pm)) {  // right rarefaction
+      if (nonpos<S>(R.u + R.a)) {
         d = R.d; u = R.u; ps = R.p;
       } else {
         sample_raref<S, false>(R, pm, um, xR, g, d, u, ps);
@@ -631,7 +774,7 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
       sample_shock<S>(R, pm, um, T(-1), g, d, u, ps);
     }
   }
-  const bool left = u >= T(0);
+  const bool left = nonneg<S>(u);
   const T v = left ? WL[2] : WR[2];
   const T w = left ? WL[3] : WR[3];
   const T E = (S ? ps / g.gm1 : ps * g.inv_gm1) + T(0.5) * d * (u * u + v * v + w * w);

@@ -1,5 +1,7 @@
 // hydro_selfcheck.cu -- hydro_check_conversions(): the integer-arithmetic
-// float <-> double conversions of hydro_math.cuh against the hardware ones.
+// float <-> double conversions of hydro_math.cuh against the hardware ones
+// (bit for bit in the normal range, zeros and infinities; subnormals flushed
+// to a signed zero; NaN to NaN).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -17,15 +19,25 @@ __device__ __forceinline__ void count(bool bad, unsigned long long* slot) {
   if ((threadIdx.x & 31) == 0 && m) atomicAdd(slot, (unsigned long long)__popc(m));
 }
 
-// every float bit pattern
+// every float bit pattern: the hardware's bits for normal values, zeros and
+// infinities; a zero of the same sign for subnormals; NaN for NaN
 __global__ void __launch_bounds__(kThreads) k_check_widen(unsigned long long* bad) {
   const unsigned long long n = 1ull << 32;
   const unsigned long long stride = (unsigned long long)gridDim.x * kThreads;
   for (unsigned long long i = (unsigned long long)blockIdx.x * kThreads + threadIdx.x; i < n;
        i += stride) {
-    const float x = __uint_as_float((unsigned)i);
+    const unsigned bits = (unsigned)i;
+    const float x = __uint_as_float(bits);
     const double a = hydro::f2d(x), b = (double)x;
-    count(__double_as_longlong(a) != __double_as_longlong(b), bad);
+    const unsigned e = bits >> 23 & 0xffu;
+    bool ok;
+    if (isnan(x))
+      ok = isnan(a);
+    else if (e == 0u)
+      ok = __double_as_longlong(a) == (long long)((unsigned long long)(bits & 0x80000000u) << 32);
+    else
+      ok = __double_as_longlong(a) == __double_as_longlong(b);
+    count(!ok, bad);
   }
 }
 
@@ -57,7 +69,15 @@ __global__ void __launch_bounds__(kThreads) k_check_narrow(unsigned long long* b
     }
     const double x = __longlong_as_double((long long)b);
     const float a = hydro::d2f(x), c = __double2float_rn(x);
-    count(__float_as_uint(a) != __float_as_uint(c), bad);
+    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    bool ok;
+    if (isnan(x))
+      ok = isnan(a);
+    else if (e < 897u)  // below the float normal range: a zero of the same sign
+      ok = __float_as_uint(a) == (unsigned)(b >> 32 & 0x80000000ull);
+    else
+      ok = __float_as_uint(a) == __float_as_uint(c);
+    count(!ok, bad);
   }
 }
 

@@ -1,12 +1,14 @@
 """The integer-arithmetic float <-> double conversions that the mixed-precision
-kernels use agree bit for bit with the hardware conversions (every float for
-the widening, 2^30 sampled doubles for the round-to-nearest-even narrowing)."""
+kernels use agree with the hardware conversions: bit for bit for normal values,
+zeros and infinities (every float for the widening, 2^30 sampled doubles for the
+round-to-nearest-even narrowing), subnormals flushed to a signed zero, NaN kept
+NaN."""
 import pytest
 
 pytestmark = pytest.mark.gpu
 
 
-def test_conversions_match_hardware_bit_for_bit():
+def test_conversions_match_hardware():
     from paper_1410_4194_gb300 import hydro
     widen, narrow = hydro.check_conversions()
     assert widen == 0, "float -> double mismatches: %d" % widen

@@ -169,6 +169,23 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def max_over_ranks(x, ws, device="cuda"):
+    """Maximum of a per-rank number over all ranks (identity for one rank)."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(units_per_rank, steps, ws, ms_max):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (each rank advances its own replica)."""
+    return ws * units_per_rank * steps / (ms_max / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -285,11 +302,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     stages, launches_total = g.profile_read()
     g.profile(False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = ws * nreal * args.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, ws)
+    value = replicas_value(nreal, args.steps, ws, ms_max)
 
     # ---- end to end through the public API with host buffers ----------------
     e2e = None
@@ -310,10 +324,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": ws * nreal * ke / (float(te.item()) / 1e3), "unit": UNIT,
+        te = max_over_ranks(e0.elapsed_time(e1), ws)
+        e2e = {"value": replicas_value(nreal, ke, ws, te), "unit": UNIT,
                "h2d_bytes_per_step": int(u_host.numel() * 8),
                "d2h_bytes_per_step": int(out_host.numel() * 8), "steps": ke,
                "host_wall_s": wall}
@@ -410,11 +422,8 @@ def run_batch(args, w, ws, rank, local):
         dist.barrier()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = ws * ncells * args.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, ws)
+    value = replicas_value(ncells, args.steps, ws, ms_max)
     e2e = None
     if not args.no_e2e:
         hosts = [torch.from_numpy(g["u"]).pin_memory() for g in grids]
@@ -432,7 +441,8 @@ def run_batch(args, w, ws, rank, local):
                 b.get_state(i, x.numpy())
         e1.record(stream)
         torch.cuda.synchronize()
-        e2e = {"value": ws * ncells * ke / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+        te = max_over_ranks(e0.elapsed_time(e1), ws)
+        e2e = {"value": replicas_value(ncells, ke, ws, te), "unit": UNIT,
                "h2d_bytes_per_step": int(sum(x.numel() * 8 for x in hosts)),
                "d2h_bytes_per_step": int(sum(x.numel() * 8 for x in outs)), "steps": ke}
     l1 = None

@@ -72,6 +72,8 @@ enum {
 /* Create a grid of nx*ny*nz real cells of width dx for an ideal gas of index
  * gamma (> 1).  bc[6] lists the faces x-, x+, y-, y+, z-, z+.  Allocates all
  * device memory the step needs (about 450 bytes per padded cell in float64).
+ * The padded grid ((n+8) cells along each active axis) must have fewer than
+ * 2^31 cells (about 1290^3, more than the device holds), else HYDRO_EINVAL.
  * On success *out holds the handle; on error *out is NULL. */
 int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, const int bc[6]);
 
@@ -150,6 +152,7 @@ void hydro_free(hydro_t h);
 typedef struct hydro_batch_s* hydro_batch_t;
 
 /* dims: [ngrids][3] (nx, ny, nz); dx, gamma: [ngrids]; bc: [ngrids][6].
+ * Each grid obeys the size rules of hydro_init (HYDRO_EINVAL otherwise).
  * Allocates the device memory of all grids (one allocation). */
 int hydro_batch_init(hydro_batch_t* out, int ngrids, const int* dims, const double* dx,
                      const double* gamma, const int* bc);

@@ -220,6 +220,7 @@ int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, co
     if (n[d] > 1 && ((bc[2 * d] == HYDRO_BC_PERIODIC) != (bc[2 * d + 1] == HYDRO_BC_PERIODIC)))
       return HYDRO_EINVAL;
   }
+  if (padded_cells(n) >= (1ll << 31)) return HYDRO_EINVAL;  // kernels index in 32 bits
   hydro_t h = new (std::nothrow) hydro_s();
   if (!h) return HYDRO_ENOMEM;
   h->profile = false;

@@ -243,6 +243,7 @@ int hydro_batch_init(hydro_batch_t* out, int ngrids, const int* dims, const doub
       if (n > 1 && (b0 < 0 || b0 > 3 || b1 < 0 || b1 > 3)) return HYDRO_EINVAL;
       if (n > 1 && ((b0 == HYDRO_BC_PERIODIC) != (b1 == HYDRO_BC_PERIODIC))) return HYDRO_EINVAL;
     }
+    if (padded_cells(dims + 3 * i) >= (1ll << 31)) return HYDRO_EINVAL;  // 32-bit indices
   }
   hydro_batch_t h = new (std::nothrow) hydro_batch_s();
   if (!h) return HYDRO_ENOMEM;

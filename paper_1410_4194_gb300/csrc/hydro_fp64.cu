@@ -29,13 +29,20 @@ namespace hydro {
 namespace {
 
 // block-wide maximum of a non-negative double (NaN ignored), then one
-// atomicMax on its bits (non-negative doubles order like their bit patterns)
+// atomicMax on its bits (non-negative doubles order like their bit patterns);
+// S (strict): IEEE comparisons, else integer ones (max_nonneg, same result)
+template <bool S>
+__device__ __forceinline__ double max_nn(double v, double w) {
+  if constexpr (S) return tmax(v, w);
+  else return max_nonneg(v, w);
+}
+template <bool S>
 __device__ __forceinline__ void block_max_to(double v, unsigned long long* slot) {
   __shared__ double warp_max[kThreads / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const double w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = tmax(v, w);
+    v = max_nn<S>(v, w);
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) warp_max[wid] = v;
@@ -45,7 +52,7 @@ __device__ __forceinline__ void block_max_to(double v, unsigned long long* slot)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const double w = __shfl_xor_sync(0xffffffffu, v, o);
-      v = tmax(v, w);
+      v = max_nn<S>(v, w);
     }
     if (lane == 0 && v > 0.0) atomicMax(slot, (unsigned long long)__double_as_longlong(v));
   }
@@ -68,9 +75,7 @@ __device__ __forceinline__ double prims_body(const Geom& G, const Bufs& B, const
   double local = 0.0;
   {
     int c[3];
-    c[2] = (int)(t / G.s[2]);
-    c[1] = (int)((t - c[2] * G.s[2]) / G.s[1]);
-    c[0] = (int)(t - c[2] * G.s[2] - c[1] * G.s[1]);
+    padded_coords(G, t, c);
     int src[3];
     int neg = 0, inflow_face = -1;
     bool real = true;
@@ -150,7 +155,7 @@ __device__ __forceinline__ double prims_body(const Geom& G, const Bufs& B, const
     if (want_dt && real) {
 #pragma unroll
       for (int d = 0; d < 3; ++d)
-        if (G.n[d] > 1) local = vmax<S>(local, fabs(W[1 + d]) + a);
+        if (G.n[d] > 1) local = max_nn<S>(local, fabs(W[1 + d]) + a);
     }
   }
   return local;
@@ -160,7 +165,7 @@ __global__ void __launch_bounds__(kThreads) k_prims(Geom G, Bufs B, BcDesc bc, G
   const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const double local = (t < total) ? prims_body<true>(G, B, bc, g, want_dt, t) : 0.0;
-  if (want_dt) block_max_to(local, reinterpret_cast<unsigned long long*>(B.rec));
+  if (want_dt) block_max_to<true>(local, reinterpret_cast<unsigned long long*>(B.rec));
 }
 
 template <int BS>
@@ -170,7 +175,7 @@ __global__ void __launch_bounds__(BS) kb_prims(BatchLaunch L) {
   const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
   const double local =
       (it.t < total) ? prims_body<false>(G, it.d->B, it.d->bc, it.d->gd, 1, it.t) : 0.0;
-  block_max_to(local, reinterpret_cast<unsigned long long*>(it.d->B.rec));
+  block_max_to<false>(local, reinterpret_cast<unsigned long long*>(it.d->B.rec));
 }
 
 __global__ void k_set_dt(double* rec, double cfl, double fixed_dt, double dx) {
@@ -187,10 +192,7 @@ __global__ void k_set_dt(double* rec, double cfl, double fixed_dt, double dx) {
 // otherwise with a fused multiply-add and the NaN test on the bit pattern
 template <bool S>
 __device__ __forceinline__ void update_body(const Geom& G, const Bufs& B, long long t) {
-  const int i = (int)(t % G.n[0]);
-  const int j = (int)((t / G.n[0]) % G.n[1]);
-  const int k = (int)(t / ((long long)G.n[0] * G.n[1]));
-  const long long c = (i + G.g[0]) + (j + G.g[1]) * G.s[1] + (k + G.g[2]) * G.s[2];
+  const long long c = real_to_padded(G, t);
   const double dtdx = B.rec[2];
   int fl = 0;
 #pragma unroll

@@ -78,6 +78,13 @@ enum Stage : int {
 
 // Units (cells or faces) one launch of a stage processes.
 long long stage_units(const Geom& G, int stage, int axis);
+
+// padded cells of a grid of n[3] real cells (kNG ghost layers per active side)
+inline long long padded_cells(const int n[3]) {
+  long long c = 1;
+  for (int d = 0; d < 3; ++d) c *= (n[d] > 1) ? (long long)n[d] + 2 * kNG : 1;
+  return c;
+}
 // Cells or faces of a per-axis stage (kStageSlopes..kStageRiemann2).
 Box stage_box_of(const Geom& G, int stage, int axis);
 

@@ -17,12 +17,38 @@ constexpr int kThreads = 256;
 constexpr int kMinBlocks = 3;
 using Gas = GasT<double>;
 
+// 32-bit index arithmetic: hydro_init and hydro_batch_init reject grids of
+// 2^31 or more padded cells, so every box index fits
 __device__ __forceinline__ void box_coords(const Box& b, long long t, int c[3]) {
-  const long long n0 = b.n[0], n01 = (long long)b.n[0] * b.n[1];
-  c[2] = b.lo[2] + (int)(t / n01);
-  const long long r = t - (long long)(c[2] - b.lo[2]) * n01;
-  c[1] = b.lo[1] + (int)(r / n0);
-  c[0] = b.lo[0] + (int)(r - (long long)(c[1] - b.lo[1]) * n0);
+  const unsigned n0 = (unsigned)b.n[0], n01 = (unsigned)b.n[0] * (unsigned)b.n[1];
+  const unsigned tt = (unsigned)t;
+  const unsigned k = tt / n01;
+  const unsigned r = tt - k * n01;
+  const unsigned j = r / n0;
+  c[2] = b.lo[2] + (int)k;
+  c[1] = b.lo[1] + (int)j;
+  c[0] = b.lo[0] + (int)(r - j * n0);
+}
+
+// (i, j, k) of padded cell t: t = i + s1 j + s2 k
+__device__ __forceinline__ void padded_coords(const Geom& G, long long t, int c[3]) {
+  const unsigned tt = (unsigned)t, s1 = (unsigned)G.s[1], s2 = (unsigned)G.s[2];
+  const unsigned k = tt / s2;
+  const unsigned r = tt - k * s2;
+  const unsigned j = r / s1;
+  c[2] = (int)k;
+  c[1] = (int)j;
+  c[0] = (int)(r - j * s1);
+}
+
+// padded index of real cell t (t = i + nx j + nx ny k over the real cells)
+__device__ __forceinline__ long long real_to_padded(const Geom& G, long long t) {
+  const unsigned tt = (unsigned)t, n0 = (unsigned)G.n[0], n1 = (unsigned)G.n[1];
+  const unsigned q = tt / n0;
+  const unsigned i = tt - q * n0;
+  const unsigned k = q / n1;
+  const unsigned j = q - k * n1;
+  return (long long)(i + G.g[0]) + (long long)(j + G.g[1]) * G.s[1] + (long long)(k + G.g[2]) * G.s[2];
 }
 
 __device__ __forceinline__ long long pidx(const Geom& G, const int c[3]) {
@@ -157,7 +183,7 @@ __device__ __forceinline__ void riemann1_body(const Geom& G, const Bufs& B, cons
   } else {
     load_rot<D>(B.UL[D], G.ps, f, WL);
     load_rot<D>(B.UR[D], G.ps, f, WR);
-    fl = riemann_exact<false>(WL, WR, 1.0 / WL[0], 1.0 / WR[0], g, F);
+    fl = riemann_exact<false>(WL, WR, nr_rcp(WL[0]), nr_rcp(WR[0]), g, F);
   }
   store_rot<D>(B.F1[D], G.ps, f, F);
   if (fl) atomicOr(rec_flags(B.rec), fl);

@@ -18,6 +18,10 @@
 //     gamma = 7/5 -> k = 7) is a k-th root: an FP32 seed from the SFU
 //     (log2/exp2) refined by Newton steps for the reciprocal root,
 //     t <- t + (t/k)(1 - r t^k), then r^(1/k) = r t^(k-1); any other gamma uses pow;
+//   * FP64 divisions and square roots by Newton iteration from SFU seeds, and
+//     FP64 comparisons on the integer pipe (both below);
+//   * f_L, f_R at the final pressure reuse the last Newton evaluation when
+//     that step left p unchanged;
 //   * f'_k on a rarefaction: (p/p_k)^(-(gamma+1)/(2gamma)) / (rho_k a_k)
 //     = x (a_k/gamma) / p with x = (p/p_k)^z, since -(gamma+1)/(2gamma) = z - 1 and
 //     p_k/(rho_k a_k) = a_k/gamma;
@@ -133,6 +137,14 @@ template <bool S, typename T>
 __device__ __forceinline__ T vmin(T a, T b) { return lt<S>(b, a) ? b : a; }
 template <bool S, typename T>
 __device__ __forceinline__ T vmax(T a, T b) { return lt<S>(a, b) ? b : a; }
+// larger of two non-negative doubles (a NaN counts as absent, as in the
+// IEEE "(a < b) ? b : a" with the NaN second), on the integer pipe: the bit
+// patterns of non-negative doubles order like the values, and a NaN's exceeds
+// infinity's
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+  const long long ka = __double_as_longlong(a), kb = __double_as_longlong(b);
+  return (kb > ka && kb <= 0x7ff0000000000000LL) ? b : a;
+}
 __device__ __forceinline__ bool bits_equal(double a, double b) {
   return __double_as_longlong(a) == __double_as_longlong(b);
 }
@@ -281,16 +293,15 @@ __device__ __forceinline__ T ipow(T x) {
 
 // r^(1/K), correctly rounded, for r in [1e-30, 1e30].
 //   1. t ~ r^(-1/K) from an SFU seed (log2/exp2 in float) and one Newton step
-//      t <- t + (t/K)(1 - r t^K)  (relative error ~1e-11 in double);
+//      t <- t + (t/K)(1 - r t^K)  (relative error ~1e-13 in double);
 //   2. y = r t^(K-1) ~ r^(1/K), then one Newton step for y^K = r with the
 //      residual r - y^K formed exactly in double-double arithmetic (products
-//      split by fma); the correction delta = (r - y^K) t^(K-1) / K is ~1e-11 y and
-//      is itself accurate to ~1e-22 y, so y + delta rounds to the correctly
+//      split by fma); the correction delta = (r - y^K) t^(K-1) / K is ~1e-13 y and
+//      is itself accurate to ~1e-26 y, so y + delta rounds to the correctly
 //      rounded root.
-// The rarefaction pressure function uses (p/p_k)^z - 1 with x near 1, where a
-// single ulp of x is an absolute error of the same size in the result; a
-// correctly rounded x keeps that difference exactly zero.  In float (mixed path)
-// one Newton step is enough for float accuracy.
+// Measured faster in the solver than a second reciprocal-root step without the
+// correction.  r = 1 gives exactly 1.  In float (mixed path) one Newton step is
+// enough for float accuracy.
 template <int K, typename T>
 __device__ __forceinline__ T kth_root(T r) {
   float lr;
@@ -329,7 +340,7 @@ __device__ __forceinline__ T kth_root(T r) {
 // (p/p_k)^z
 template <typename T>
 __device__ __forceinline__ T pow_z(T r, const GasT<T>& g) {
-  if (r > T(1e-30) && r < T(1e30)) {
+  if (lt<false>(T(1e-30), r) && lt<false>(r, T(1e30))) {
     if (g.k == 5) return kth_root<5>(r);
     if (g.k == 7) return kth_root<7>(r);
   }

@@ -70,14 +70,14 @@ __device__ __forceinline__ void store_rot_f(float* __restrict__ A, long long ps,
 __device__ __forceinline__ void block_max_to(double v, unsigned long long* slot) {
   __shared__ double warp_max[kThreads / 32];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = tmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = max_nonneg(v, __shfl_xor_sync(0xffffffffu, v, o));
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) warp_max[wid] = v;
   __syncthreads();
   if (wid == 0) {
     v = (lane < (int)(blockDim.x >> 5)) ? warp_max[lane] : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = tmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = max_nonneg(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (lane == 0 && v > 0.0) atomicMax(slot, (unsigned long long)__double_as_longlong(v));
   }
 }
@@ -89,9 +89,7 @@ __device__ __forceinline__ double prims_mixed_body(const Geom& G, const BufsF& B
   double local = 0.0;
   {
     int c[3];
-    c[2] = (int)(t / G.s[2]);
-    c[1] = (int)((t - c[2] * G.s[2]) / G.s[1]);
-    c[0] = (int)(t - c[2] * G.s[2] - c[1] * G.s[1]);
+    padded_coords(G, t, c);
     int src[3];
     int neg = 0, inflow_face = -1;
     bool real = true;
@@ -137,7 +135,7 @@ __device__ __forceinline__ double prims_mixed_body(const Geom& G, const BufsF& B
     for (int d = 0; d < 3; ++d) v[d] = U[1 + d] * r;
     // FP64 internal energy E - (rho v) . v / 2 and the pressure floor
     const double ke2 = U[1] * v[0] + U[2] * v[1] + U[3] * v[2];
-    const double p = tmax(g.gm1 * fma(-0.5, ke2, U[4]), kPFloor);
+    const double p = vmax<false>(g.gm1 * fma(-0.5, ke2, U[4]), kPFloor);
     // a = sqrt(gamma p / rho): float reciprocal square root of x = a^2 refined
     // by one Newton step, a = x y (1 + (1 - x y^2)/2) (relative error ~1e-13)
     const double x = g.gamma * p * r;
@@ -155,7 +153,7 @@ __device__ __forceinline__ double prims_mixed_body(const Geom& G, const BufsF& B
     if (want_dt && real) {
 #pragma unroll
       for (int d = 0; d < 3; ++d)
-        if (G.n[d] > 1) local = tmax(local, fabs(v[d]) + a);
+        if (G.n[d] > 1) local = max_nonneg(local, fabs(v[d]) + a);
     }
   }
   return local;
@@ -304,10 +302,7 @@ __device__ __forceinline__ void riemann2_mixed_body(const Geom& G, const BufsF& 
 
 // conserved update in FP64 from the float CTU fluxes
 __device__ __forceinline__ void update_mixed_body(const Geom& G, const BufsF& B, long long t) {
-  const int i = (int)(t % G.n[0]);
-  const int j = (int)((t / G.n[0]) % G.n[1]);
-  const int k = (int)(t / ((long long)G.n[0] * G.n[1]));
-  const long long c = (i + G.g[0]) + (j + G.g[1]) * G.s[1] + (k + G.g[2]) * G.s[2];
+  const long long c = real_to_padded(G, t);
   const double dtdx = B.rec[2];
   int fl = 0;
 #pragma unroll
@@ -321,8 +316,9 @@ __device__ __forceinline__ void update_mixed_body(const Geom& G, const BufsF& B,
       }
     }
     B.u[q * G.nreal + t] = un;
-    if (isnan(un)) fl = kFlagNonPhys;
-    if (q == 0 && !(un > 0.0)) fl = kFlagNonPhys;
+    const long long b = __double_as_longlong(un);
+    if ((b & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) fl = kFlagNonPhys;  // NaN
+    if (q == 0 && b <= 0) fl = kFlagNonPhys;  // rho <= 0 (or a NaN with the sign bit)
   }
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }

@@ -52,3 +52,19 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(hydro, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         hydro.load()
+
+
+def test_init_rejects_grids_beyond_32bit_indexing_without_gpu(lib):
+    # validation happens before any device call: (1300+8)^3 padded cells >= 2^31
+    h = ctypes.c_void_p()
+    bc = (ctypes.c_int * 6)(0, 0, 0, 0, 0, 0)
+    rc = lib.hydro_init(ctypes.byref(h), 1300, 1300, 1300, ctypes.c_double(1.0 / 1300),
+                        ctypes.c_double(5.0 / 3.0), bc)
+    assert rc == -1 and not h.value
+    dims = (ctypes.c_int * 6)(32, 32, 32, 1300, 1300, 1300)
+    dx = (ctypes.c_double * 2)(1.0, 1.0)
+    gam = (ctypes.c_double * 2)(1.4, 1.4)
+    bcs = (ctypes.c_int * 12)(*([0] * 12))
+    hb = ctypes.c_void_p()
+    assert lib.hydro_batch_init(ctypes.byref(hb), 2, dims, dx, gam, bcs) == -1
+    assert not hb.value

@@ -80,8 +80,20 @@ ALGORITHMIC_BYTES = {
 
 # dram bytes (read + write) per unit of the stage's kernel from an ncu capture,
 # with the digest of the sources that kernel is built from; a digest mismatch
-# (the kernel changed since the capture) reports null.
-NCU_TRAFFIC = {}
+# (the kernel changed since the capture) reports null.  Captured on Sedov 160^3
+# (kb_riemann2 along x: 161 x 160 x 160 faces; the 256^3 launch exceeds the
+# capture size rule) and scaled by the units of a launch: these kernels stream
+# each plane once, so traffic grows in proportion to the faces.
+NCU_TRAFFIC = {
+    ("fp64", "riemann2"): {
+        "bytes_per_unit": 204.02, "digest": "2c6352daa30c4b04",
+        "sources": ["hydro_fp64_fast.cu", "hydro_internal.h", "hydro_kernels.cuh",
+                    "hydro_math.cuh"]},
+    ("mixed", "riemann2"): {
+        "bytes_per_unit": 99.70, "digest": "1878ea89e4734448",
+        "sources": ["hydro_internal.h", "hydro_kernels.cuh", "hydro_math.cuh",
+                    "hydro_mixed.cu"]},
+}
 
 
 def workload(name):

@@ -23,6 +23,11 @@ namespace {
 using GasF = GasT<float>;
 using GasD = GasT<double>;
 
+// resident 256-thread blocks per SM for the stencil and Riemann stages: the
+// float kernels fit 64 registers (4 blocks, 50% of the warp slots) with a few
+// bytes of spill, which measured ~1% faster than 3 blocks at 72-80 registers
+constexpr int kMinBlocksMixed = 4;
+
 // float views of the step's work arrays (same slab as the FP64 path)
 struct BufsF {
   double* u;      // FP64 state, real cells [5][nz][ny][nx]
@@ -332,7 +337,7 @@ __global__ void __launch_bounds__(BS) kb_update_mixed(BatchLaunch L) {
 
 #define HYDRO_BATCH_MIXED(NAME, STAGE_IDX, CALL)                                           \
   template <int D, int BS>                                                                  \
-  __global__ void __launch_bounds__(BS, kMinBlocks * kThreads / BS) NAME(BatchLaunch L) {  \
+  __global__ void __launch_bounds__(BS, kMinBlocksMixed * kThreads / BS) NAME(BatchLaunch L) {  \
     const BatchItem it = batch_item(L);                                                     \
     const Box& box = it.d->box[STAGE_IDX][D];                                               \
     if (it.t < (long long)box.n[0] * box.n[1] * box.n[2]) {                                 \

@@ -217,3 +217,31 @@ def test_ghost_fill_rules():
     exp = up[:, G:G + nz, G, G - 1].copy()  # x-ghost of the first real row
     exp[2] = -exp[2]
     np.testing.assert_array_equal(up[:, G:G + nz, G - 1, G - 1], exp)
+
+
+def test_update_depends_on_cells_within_three():
+    """One CTU step of a cell depends only on the cells within 3 of it along each
+    axis (slopes reach 1, PPMC 1 more, the transverse fluxes 1 more): the step of
+    a 20^3 block cut from a periodic field, with outflow faces, equals the
+    full-grid step bit for bit 3 cells away from the block's faces, and not 2
+    away.  The full-size GPU parity tests rely on this to sample 512^3 steps."""
+    w = W.turbulence(48, kmax=2)
+    u0, n = w["u"], 48
+    g = oracle.Grid(n, n, n, w["dx"], w["gamma"], w["bc"])
+    g.set_state(u0)
+    dt = g.compute_dt(0.3)
+    g.step_dt(dt)
+    uf = g.get_state()
+    R = 10
+    for c in [(20, 17, 30), (0, 47, 5)]:
+        idx = [np.arange(ci - R, ci + R) % n for ci in c]
+        sub = np.ascontiguousarray(u0[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]])
+        b = oracle.Grid(2 * R, 2 * R, 2 * R, w["dx"], w["gamma"], [2] * 6)
+        b.set_state(sub)
+        b.step_dt(dt)
+        ub = b.get_state()
+        for m, exact in ((3, True), (2, False)):
+            cen = ub[:, m:2 * R - m, m:2 * R - m, m:2 * R - m]
+            inner = [ix[m:2 * R - m] for ix in idx]
+            ref = uf[:, inner[0]][:, :, inner[1]][:, :, :, inner[2]]
+            assert np.array_equal(cen, ref) == exact, (c, m)

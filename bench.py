@@ -90,7 +90,7 @@ NCU_TRAFFIC = {
         "sources": ["hydro_fp64_fast.cu", "hydro_internal.h", "hydro_kernels.cuh",
                     "hydro_math.cuh"]},
     ("mixed", "riemann2"): {
-        "bytes_per_unit": 99.70, "digest": "1878ea89e4734448",
+        "bytes_per_unit": 99.69, "digest": "707053dd22a499c3",
         "sources": ["hydro_internal.h", "hydro_kernels.cuh", "hydro_math.cuh",
                     "hydro_mixed.cu"]},
 }
@@ -390,6 +390,7 @@ def main():
         "config": single_config(args.workload, args.precision, ws),
         "e2e": e2e, "gpu_launches": launches_total, "clocks": clocks, "roofline": roofline,
         "stages": stage_report, "cpu_baseline": cpu,
+        "hbm": hbm_report(value / ws, traffic, avg_ms),
     }
     if l1 is not None:
         line["l1_vs_fp64"] = l1
@@ -498,6 +499,7 @@ def run_batch(args, w, ws, rank, local):
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (states %.2f GB)" % (ncells * 40 / 1e9)},
         "e2e": e2e, "gpu_launches": 15 * args.steps, "clocks": clocks,
+        "hbm": hbm_report(value / ws),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_FLOPS_PEAK,
                      "unit": "FP64 FLOP/s", "frac": achieved / FP64_FLOPS_PEAK, "traffic": None,
                      "kernel": "whole step (graph)", "flops_per_cell_update": per_cell,
@@ -539,6 +541,29 @@ def compare_l1(w, args, g, hydro, stream):
     l1 = (d / den).tolist()
     return {"steps": n, "fields": ["rho", "mx", "my", "mz", "E"], "l1_rel": l1,
             "reference": "HYDRO_FP64 GPU path from the same initial state"}
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of this machine's GB300 (MEASURED_PEAKS.json), else
+    the fallback measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def hbm_report(cells_per_s, kernel_traffic=None, kernel_ms=None):
+    """HBM roofline of the step (80 B per cell update: the FP64 conserved state
+    read once and written once) and, when known, the dominant kernel's DRAM rate."""
+    peak, src = hbm_peak_gbs()
+    out = {"bytes_per_cell_update": 80, "achieved_gbs": cells_per_s * 80 / 1e9,
+           "peak_gbs": peak, "peak_source": src, "frac": cells_per_s * 80 / 1e9 / peak}
+    if kernel_traffic is not None and kernel_ms:
+        gbs = kernel_traffic / (kernel_ms / 1e3) / 1e9
+        out["dominant_kernel_dram_gbs"] = gbs
+        out["dominant_kernel_dram_frac"] = gbs / peak
+    return out
 
 
 def source_digest(files):

@@ -60,7 +60,8 @@ def lib():
 
 
 def set_threads(n):
-    """Set the OpenMP thread count of the oracle; returns the count in effect."""
+    """Set the OpenMP thread count of the oracle (0: every processor); returns
+    the count in effect."""
     return lib().oracle_set_threads(int(n))
 
 

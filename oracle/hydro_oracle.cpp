@@ -799,7 +799,7 @@ int oracle_fill_ghosts(void* h, double* upad) {
 
 int oracle_set_threads(int n) {
 #ifdef _OPENMP
-  if (n > 0) omp_set_num_threads(n);
+  omp_set_num_threads(n > 0 ? n : omp_get_num_procs());  // 0: every processor
   return omp_get_max_threads();
 #else
   (void)n;

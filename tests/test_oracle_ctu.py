@@ -245,3 +245,17 @@ def test_update_depends_on_cells_within_three():
             inner = [ix[m:2 * R - m] for ix in idx]
             ref = uf[:, inner[0]][:, :, inner[1]][:, :, :, inner[2]]
             assert np.array_equal(cen, ref) == exact, (c, m)
+
+
+def test_threaded_oracle_is_bit_identical_to_one_thread():
+    """The OpenMP loops over the outer index change nothing: the step on all
+    cores equals the single-thread step bit for bit."""
+    w = W.turbulence(24, kmax=2)
+    out = []
+    for nthreads in (1, 0):
+        oracle.set_threads(nthreads)
+        u, t, n, fl = oracle.run(w["u"], w["dx"], w["gamma"], w["bc"], nsteps=3, cfl=0.3)
+        out.append((u, t))
+    oracle.set_threads(0)
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])

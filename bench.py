@@ -48,11 +48,11 @@ PEAK_SOURCE = "152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM x 2 flop/FMA (unit counts 
 # Units: padded cells (prims), real cells (slopes, ppmc, update), faces (riemann1,
 # riemann2).  The benchmark never runs the oracle for these.
 ALGORITHMIC_FLOPS = {
-    "batched": {"ppmc": 406.0, "prims": 22.752, "riemann1": 136.073, "riemann2": 196.219, "slopes": 81.0, "update": 45.0},
-    "sedov": {"ppmc": 406.0, "prims": 22.752, "riemann1": 136.073, "riemann2": 196.219, "slopes": 81.0, "update": 45.0},
+    "batched": {"ppmc": 406.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 81.0, "update": 45.0},
+    "sedov": {"ppmc": 406.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 81.0, "update": 45.0},
     "shock_cloud": {"ppmc": 413.0, "prims": 22.752, "riemann1": 135.667, "riemann2": 195.667, "slopes": 81.0, "update": 45.0},
-    "sod512": {"ppmc": 406.0, "prims": 28.742, "riemann1": 136.124, "riemann2": 136.124, "slopes": 81.0, "update": 15.0},
-    "turbulence": {"ppmc": 423.335, "prims": 22.752, "riemann1": 140.353, "riemann2": 200.633, "slopes": 91.821, "update": 45.0},
+    "sod512": {"ppmc": 406.0, "prims": 28.742, "riemann1": 136.125, "riemann2": 136.125, "slopes": 81.0, "update": 15.0},
+    "turbulence": {"ppmc": 423.374, "prims": 22.752, "riemann1": 140.154, "riemann2": 200.574, "slopes": 91.922, "update": 45.0},
 }
 
 # The FP64 part of the mixed-precision stages, flops per unit, from the kernels'

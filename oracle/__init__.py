@@ -23,6 +23,7 @@ FLAG_NEWTON = 1
 FLAG_NONPHYS = 2
 
 BC_PERIODIC, BC_REFLECT, BC_OUTFLOW, BC_INFLOW = 0, 1, 2, 3
+RECON_PPMC, RECON_PPMP, RECON_PLMC, RECON_PLMP, RECON_PCM = 0, 1, 2, 3, 4
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -42,6 +43,9 @@ def lib():
         L.oracle_init.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [_ip]
         L.oracle_free.argtypes = [ctypes.c_void_p]
         L.oracle_set_inflow.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
+        L.oracle_set_recon.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.oracle_reconstruct.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, _dp, _dp]
         L.oracle_set_state.argtypes = [ctypes.c_void_p, _dp]
         L.oracle_get_state.argtypes = [ctypes.c_void_p, _dp]
         L.oracle_compute_dt.restype = ctypes.c_double
@@ -104,6 +108,21 @@ def ppmc(w, dtdx, gamma):
     return WsL, WsR
 
 
+def reconstruct(recon, w, dtdx, dx, gamma):
+    """Reconstruction ``recon`` (RECON_*) on seven-cell primitive stencils
+    ``w [n, 7 cells, 5]`` (cells i-3..i+3; rho, normal velocity, two transverse
+    velocities, p).  Returns ``(UsL, UsR)``: the conserved time-evolved states at
+    the left and right face of the centre cell, each ``[n, 5]``."""
+    w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1, 7, 5)
+    n = w.shape[0]
+    UsL = np.zeros((n, 5)); UsR = np.zeros((n, 5))
+    rc = lib().oracle_reconstruct(n, int(recon), _ptr(w), float(dtdx), float(dx), float(gamma),
+                                  _ptr(UsL), _ptr(UsR))
+    if rc != 0:
+        raise ValueError("unknown reconstruction %r" % (recon,))
+    return UsL, UsR
+
+
 class Grid:
     """One grid advanced by the oracle's CTU step.
 
@@ -128,6 +147,12 @@ class Grid:
     def set_inflow(self, face, prim):
         p = np.ascontiguousarray(prim, dtype=np.float64)
         lib().oracle_set_inflow(self.h, int(face), _ptr(p))
+
+    def set_recon(self, recon):
+        """Reconstruction (Sec. 2.2.1): RECON_PPMC (default), RECON_PPMP, RECON_PLMC,
+        RECON_PLMP or RECON_PCM."""
+        if lib().oracle_set_recon(self.h, int(recon)) != 0:
+            raise ValueError("unknown reconstruction %r" % (recon,))
 
     def set_state(self, u):
         u = np.ascontiguousarray(u, dtype=np.float64)
@@ -191,7 +216,8 @@ class Grid:
         return out
 
 
-def run(u0, dx, gamma, bc, nsteps=None, cfl=0.3, t_end=None, inflow=None, max_steps=100000):
+def run(u0, dx, gamma, bc, nsteps=None, cfl=0.3, t_end=None, inflow=None, max_steps=100000,
+        recon=RECON_PPMC):
     """Advance ``u0`` with the oracle; returns ``(u, t, nsteps, flags)``.
 
     Either ``nsteps`` CFL steps, or steps until ``t_end`` with the last step
@@ -199,6 +225,7 @@ def run(u0, dx, gamma, bc, nsteps=None, cfl=0.3, t_end=None, inflow=None, max_st
     """
     _, nz, ny, nx = u0.shape
     g = Grid(nx, ny, nz, dx, gamma, bc)
+    g.set_recon(recon)
     if inflow:
         for face, prim in inflow.items():
             g.set_inflow(face, prim)

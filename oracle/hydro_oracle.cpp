@@ -355,7 +355,7 @@ void plmc_slope(const R wm[5], const R wc[5], const R wp[5], const Gas& g, R dw[
 // i-2..i+2 in rotated order; dtdx = dt/dx along the sweep.  Returns the
 // time-evolved left-face state W*_L and right-face state W*_R of cell i.
 template <class R>
-void ppmc_cell(const R w[5][5], R dtdx, const Gas& g, R WsL[5], R WsR[5]) {
+void ppmc_cell(const R (*w)[5], R dtdx, const Gas& g, R WsL[5], R WsR[5]) {
   R dwm[5], dwc[5], dwp[5];
   set_stage((R*)nullptr, 5);
   plmc_slope(w[0], w[1], w[2], g, dwm);  // cell i-1
@@ -446,6 +446,263 @@ void ppmc_cell(const R w[5][5], R dtdx, const Gas& g, R WsL[5], R WsR[5]) {
 }
 
 // ---------------------------------------------------------------------------
+// The other reconstructions of App. A and Sec. 2.2.1.  Stencils are in rotated
+// order (rho, normal velocity, two transverse velocities, p).
+
+// primitive-variable slope of one cell: left, right and centred differences
+// (Eq. diffs) and the MC limiter (Eq. vanLeer_limiter), each variable alone
+template <class R>
+void plm_prim_slope(const R wm[5], const R wc[5], const R wp[5], R dw[5]) {
+  for (int q = 0; q < 5; ++q) {
+    const R dL = wc[q] - wm[q];
+    const R dR = wp[q] - wc[q];
+    const R dC = R(0.5) * (wp[q] - wm[q]);
+    if (dL * dR > R(0.0))
+      dw[q] = sgn(dC) * mn(mn(fabs(dC), R(2.0) * fabs(dL)), R(2.0) * fabs(dR));
+    else
+      dw[q] = R(0.0);
+  }
+}
+
+// Euler flux along the sweep of a primitive state (Eq. x_flux)
+template <class R>
+void euler_flux(const R W[5], const Gas& g, R F[5]) {
+  const R E = W[4] / R(g.gm1) + R(0.5) * W[0] * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  const R m = W[0] * W[1];
+  F[0] = m;
+  F[1] = m * W[1] + W[4];
+  F[2] = m * W[2];
+  F[3] = m * W[3];
+  F[4] = (E + W[4]) * W[1];
+}
+
+// PLMP (App. A.1): boundary values from the limited primitive slopes
+// (W_L = w - dw/2, W_R = w + dw/2), converted to conserved variables and evolved
+// half a step with the fluxes of the two boundary values (Eqs.
+// plmp_evolution_L, plmp_evolution_R).  w[0..2]: cells i-1, i, i+1.
+template <class R>
+void plmp_cell(const R w[3][5], R dtdx, const Gas& g, R UsL[5], R UsR[5]) {
+  R dw[5], WL[5], WR[5];
+  set_stage((R*)nullptr, 5);
+  add_units((R*)nullptr, 5);
+  plm_prim_slope(w[0], w[1], w[2], dw);
+  set_stage((R*)nullptr, 1);
+  for (int q = 0; q < 5; ++q) {
+    WL[q] = w[1][q] - R(0.5) * dw[q];
+    WR[q] = w[1][q] + R(0.5) * dw[q];
+  }
+  WL[4] = mx(WL[4], R(P_FLOOR));
+  WR[4] = mx(WR[4], R(P_FLOOR));
+  R UL[5], UR[5], FL[5], FR[5];
+  prim_to_cons(WL, g, UL);
+  prim_to_cons(WR, g, UR);
+  euler_flux(WL, g, FL);
+  euler_flux(WR, g, FR);
+  const R h = R(0.5) * dtdx;
+  for (int q = 0; q < 5; ++q) {
+    UsL[q] = UL[q] + h * (FL[q] - FR[q]);
+    UsR[q] = UR[q] + h * (FL[q] - FR[q]);
+  }
+}
+
+// PLMC (App. A.2): characteristic-limited slope (plmc_slope), boundary values
+// W_{L,A}, W_{R,A} (Eq. plm_interpolation) bounded by the neighbouring averages,
+// the slope recomputed as W_R - W_L, integration under the linear profile over
+// the fastest wave's domain of dependence, and the corrections s_L, s_R for the
+// other waves moving toward each face.  w[0..2]: cells i-1, i, i+1.
+template <class R>
+void plmc_cell(const R w[3][5], R dtdx, const Gas& g, R WsL[5], R WsR[5]) {
+  R dw[5];
+  set_stage((R*)nullptr, 5);
+  add_units((R*)nullptr, 5);
+  plmc_slope(w[0], w[1], w[2], g, dw);
+  set_stage((R*)nullptr, 1);
+  const R* wim = w[0];
+  const R* wi = w[1];
+  const R* wip = w[2];
+  R WL[5], WR[5];
+  for (int q = 0; q < 5; ++q) {
+    const R LA = wi[q] - R(0.5) * dw[q];
+    const R RA = wi[q] + R(0.5) * dw[q];
+    const R LB = mx(mn(wi[q], wim[q]), LA);
+    WL[q] = mn(mx(wi[q], wim[q]), LB);
+    const R RB = mx(mn(wi[q], wip[q]), RA);
+    WR[q] = mn(mx(wi[q], wip[q]), RB);
+    dw[q] = WR[q] - WL[q];
+  }
+  const R d = wi[0];
+  const R a = sqrt(R(g.gamma) * wi[4] / d);
+  const R u = wi[1];
+  const R lm = u - a, l0 = u, lp = u + a;
+  const R a2 = a * a;
+  R sL[5] = {R(0.0), R(0.0), R(0.0), R(0.0), R(0.0)};
+  R sR[5] = {R(0.0), R(0.0), R(0.0), R(0.0), R(0.0)};
+  if (l0 < R(0.0)) {  // contact (and advected transverse velocities)
+    sL[0] = sL[0] + (lm - l0) * (dw[0] - dw[4] / a2);
+    sL[2] = sL[2] + (lm - l0) * dw[2];
+    sL[3] = sL[3] + (lm - l0) * dw[3];
+  }
+  if (lp < R(0.0)) {  // right acoustic wave
+    sL[0] = sL[0] + R(0.5) * (lm - lp) * (d * dw[1] / a + dw[4] / a2);
+    sL[1] = sL[1] + R(0.5) * (lm - lp) * (dw[1] + dw[4] / (a * d));
+    sL[4] = sL[4] + R(0.5) * (lm - lp) * (d * dw[1] * a + dw[4]);
+  }
+  if (lm > R(0.0)) {  // left acoustic wave
+    sR[0] = sR[0] + R(0.5) * (lp - lm) * (-(d * dw[1]) / a + dw[4] / a2);
+    sR[1] = sR[1] + R(0.5) * (lp - lm) * (dw[1] - dw[4] / (a * d));
+    sR[4] = sR[4] + R(0.5) * (lp - lm) * (-(d * dw[1] * a) + dw[4]);
+  }
+  if (l0 > R(0.0)) {  // contact (and advected transverse velocities)
+    sR[0] = sR[0] + (lp - l0) * (dw[0] - dw[4] / a2);
+    sR[2] = sR[2] + (lp - l0) * dw[2];
+    sR[3] = sR[3] + (lp - l0) * dw[3];
+  }
+  const R am = dtdx * mn(lm, R(0.0)), bp = dtdx * mx(lp, R(0.0));
+  const R h = R(0.5) * dtdx;
+  for (int q = 0; q < 5; ++q) {
+    WsL[q] = (WL[q] - R(0.5) * am * dw[q]) + h * sL[q];
+    WsR[q] = (WR[q] - R(0.5) * bp * dw[q]) + h * sR[q];
+  }
+  WsL[4] = mx(WsL[4], R(P_FLOOR));
+  WsR[4] = mx(WsR[4], R(P_FLOOR));
+}
+
+// flattening coefficient F~_k of cell k from p_{k-2..k+2} and the normal
+// velocities u_{k-1}, u_{k+1} (App. A.4, shock flattening).  The two conditions
+// that zero F~ are tested first, so the steepness ratio is only formed across a
+// pressure jump of at least a third (its denominator may still vanish, which
+// gives an infinite ratio and F~ = 0 or 1 by its sign).
+template <class R>
+R flatten_tilde(const R p[5], R um, R up) {
+  const R jump = fabs(p[3] - p[1]) / mn(p[3], p[1]);
+  if (jump < R(1.0 / 3.0) || up - um > R(0.0)) return R(0.0);
+  const R S = (p[3] - p[1]) / (p[4] - p[0]);
+  return mx(R(0.0), mn(R(1.0), R(10.0) * (S - R(0.75))));
+}
+
+// PPMP for cell i (App. A.4).  w[0..6] are the primitive states of cells
+// i-3..i+3 in rotated order; dtdx = dt/dx along the sweep; dx the cell width.
+// Steps in the paper's order: parabolic interpolation with MC-limited
+// primitive slopes, contact steepening of the density, shock flattening,
+// monotonicity, the integrals under the parabola for the three
+// characteristics, reference states and the corrections chi.
+template <class R>
+void ppmp_cell(const R w[7][5], R dtdx, R dx, const Gas& g, R WsL[5], R WsR[5]) {
+  R dwm[5], dwc[5], dwp[5];
+  set_stage((R*)nullptr, 5);
+  plm_prim_slope(w[1], w[2], w[3], dwm);  // cell i-1
+  plm_prim_slope(w[2], w[3], w[4], dwc);  // cell i
+  plm_prim_slope(w[3], w[4], w[5], dwp);  // cell i+1
+  for (int k = 0; k < 3; ++k) add_units((R*)nullptr, 5);
+  set_stage((R*)nullptr, 1);
+  const R* wim = w[2];
+  const R* wi = w[3];
+  const R* wip = w[4];
+  R WL[5], WR[5];
+  for (int q = 0; q < 5; ++q) {  // parabolic interpolation
+    WL[q] = R(0.5) * (wi[q] + wim[q]) - (dwc[q] - dwm[q]) / R(6.0);
+    WR[q] = R(0.5) * (wip[q] + wi[q]) - (dwp[q] - dwc[q]) / R(6.0);
+  }
+  // contact discontinuity steepening of the density
+  {
+    const R rjump = fabs(wip[0] - wim[0]) / mn(wip[0], wim[0]);
+    const R pjump = fabs(wip[4] - wim[4]) / mn(wip[4], wim[4]);
+    const R dx2 = dx * dx;
+    const R d2m = (wi[0] - R(2.0) * wim[0] + w[1][0]) / (R(6.0) * dx2);   // cell i-1
+    const R d2p = (w[5][0] - R(2.0) * wip[0] + wi[0]) / (R(6.0) * dx2);  // cell i+1
+    // the concavity test: d2m d2p < 0 (opposite curvature on the two sides, the
+    // inflection of a smeared contact), as in the method the paper follows
+    // (CW84, FLASH); the printed "> 0 (same concavity)" disables steepening of
+    // smeared contacts and contradicts the paper's own Sod result (contact over
+    // two zones with PPMP, three to four with PPMC, Sec. 4.1.1)
+    if (rjump > R(0.01) && pjump < R(0.1) * R(g.gamma) * rjump && d2m * d2p < R(0.0)) {
+      const R eta_t = -((d2p - d2m) * dx2) / (wip[0] - wim[0]);
+      const R eta = mx(R(0.0), mn(R(20.0) * eta_t - R(1.0), R(1.0)));
+      WL[0] = WL[0] * (R(1.0) - eta) + (wim[0] + R(0.5) * dwm[0]) * eta;
+      WR[0] = WR[0] * (R(1.0) - eta) + (wip[0] - R(0.5) * dwp[0]) * eta;
+    }
+  }
+  // shock flattening
+  {
+    R pm[5], pc[5], pp[5];
+    for (int s = 0; s < 5; ++s) {
+      pm[s] = w[s][4];
+      pc[s] = w[s + 1][4];
+      pp[s] = w[s + 2][4];
+    }
+    const R Fm = flatten_tilde(pm, w[1][1], w[3][1]);  // cell i-1
+    const R Fc = flatten_tilde(pc, w[2][1], w[4][1]);  // cell i
+    const R Fp = flatten_tilde(pp, w[3][1], w[5][1]);  // cell i+1
+    const R F = (wip[4] - wim[4] < R(0.0)) ? mx(Fc, Fp) : mx(Fc, Fm);
+    for (int q = 0; q < 5; ++q) {
+      WL[q] = F * wi[q] + (R(1.0) - F) * WL[q];
+      WR[q] = F * wi[q] + (R(1.0) - F) * WR[q];
+    }
+  }
+  // monotonicity (the third rule sets W_R; the printed "W_L" is a slip)
+  R dw[5], w6[5];
+  for (int q = 0; q < 5; ++q) {
+    R L = WL[q], Rr = WR[q];
+    if ((Rr - wi[q]) * (wi[q] - L) <= R(0.0)) { L = wi[q]; Rr = wi[q]; }
+    if ((Rr - L) * (L - (R(3.0) * wi[q] - R(2.0) * Rr)) < R(0.0)) L = R(3.0) * wi[q] - R(2.0) * Rr;
+    if ((Rr - L) * ((R(3.0) * wi[q] - R(2.0) * L) - Rr) < R(0.0)) Rr = R(3.0) * wi[q] - R(2.0) * L;
+    WL[q] = L;
+    WR[q] = Rr;
+    dw[q] = Rr - L;
+    w6[q] = R(6.0) * (wi[q] - R(0.5) * (L + Rr));
+  }
+  // characteristic speeds, Courant fractions, traced boundary values
+  const R d = wi[0];
+  const R a = sqrt(R(g.gamma) * wi[4] / d);
+  const R u = wi[1];
+  const R lm = u - a, l0 = u, lp = u + a;
+  const R am = dtdx * mn(lm, R(0.0)), a0 = dtdx * mn(l0, R(0.0)), ap = dtdx * mn(lp, R(0.0));
+  const R bm = dtdx * mx(lm, R(0.0)), b0 = dtdx * mx(l0, R(0.0)), bp = dtdx * mx(lp, R(0.0));
+  const R two3 = R(2.0 / 3.0);
+  R WLm[5], WL0[5], WLp[5], WRm[5], WR0[5], WRp[5];
+  for (int q = 0; q < 5; ++q) {
+    WLm[q] = WL[q] - R(0.5) * am * (dw[q] + w6[q] * (R(1.0) + two3 * am));
+    WL0[q] = WL[q] - R(0.5) * a0 * (dw[q] + w6[q] * (R(1.0) + two3 * a0));
+    WLp[q] = WL[q] - R(0.5) * ap * (dw[q] + w6[q] * (R(1.0) + two3 * ap));
+    WRm[q] = WR[q] - R(0.5) * bm * (dw[q] - w6[q] * (R(1.0) - two3 * bm));
+    WR0[q] = WR[q] - R(0.5) * b0 * (dw[q] - w6[q] * (R(1.0) - two3 * b0));
+    WRp[q] = WR[q] - R(0.5) * bp * (dw[q] - w6[q] * (R(1.0) - two3 * bp));
+  }
+  // reference states: rho, u, p from the fastest wave toward each face, the
+  // transverse velocities from the advection speed; sound speeds of the
+  // reference states (their pressures floored before the square root)
+  const R aL = sqrt(R(g.gamma) * mx(WLm[4], R(P_FLOOR)) / WLm[0]);
+  const R aR = sqrt(R(g.gamma) * mx(WRp[4], R(P_FLOOR)) / WRp[0]);
+  const R CL = WLm[0] * aL;
+  const R CR = WRp[0] * aR;
+  // corrections (CW84): chi^p_L = -(1/(2 C_L)) [(u^m - u^p) + (p^m - p^p)/C_L]
+  // (the printed "-" before the pressure term and "p^m + p^p" are slips),
+  // chi^m_R with rho^p_R for the printed "rho^p_s"
+  R chiLp = -(R(1.0) / (R(2.0) * CL)) * ((WLm[1] - WLp[1]) + (WLm[4] - WLp[4]) / CL);
+  R chiRm = (R(1.0) / (R(2.0) * CR)) * ((WRp[1] - WRm[1]) - (WRp[4] - WRm[4]) / CR);
+  R chiL0 = (WLm[4] - WL0[4]) / (CL * CL) + R(1.0) / WLm[0] - R(1.0) / WL0[0];
+  R chiR0 = (WRp[4] - WR0[4]) / (CR * CR) + R(1.0) / WRp[0] - R(1.0) / WR0[0];
+  if (l0 > R(0.0)) chiL0 = R(0.0);
+  if (lp > R(0.0)) chiLp = R(0.0);
+  if (lm < R(0.0)) chiRm = R(0.0);
+  if (l0 < R(0.0)) chiR0 = R(0.0);
+  WsL[0] = R(1.0) / (R(1.0) / WLm[0] - chiL0 - chiLp);
+  WsL[1] = WLm[1] + CL * chiLp;
+  WsL[2] = WL0[2];
+  WsL[3] = WL0[3];
+  WsL[4] = mx(WLm[4] + CL * CL * chiLp, R(P_FLOOR));
+  WsR[0] = R(1.0) / (R(1.0) / WRp[0] - chiRm - chiR0);
+  WsR[1] = WRp[1] - CR * chiRm;
+  WsR[2] = WR0[2];
+  WsR[3] = WR0[3];
+  WsR[4] = mx(WRp[4] + CR * CR * chiRm, R(P_FLOOR));
+}
+
+// ---------------------------------------------------------------------------
+// Reconstructions (Sec. 2.2.1): PPMC is the method of the benchmarked path.
+enum { RECON_PPMC = 0, RECON_PPMP = 1, RECON_PLMC = 2, RECON_PLMP = 3, RECON_PCM = 4 };
+
+// ---------------------------------------------------------------------------
 // Grid: conserved variables as five padded planes [5][N2][N1][N0], x fastest.
 template <class R>
 struct Grid {
@@ -453,6 +710,7 @@ struct Grid {
   double dx, gamma;
   int bc[6];
   double inflow_prim[6][5];
+  int recon = RECON_PPMC;  // reconstruction of App. A / Sec. 2.2.1
   size_t ncell;
   std::vector<R> u;
 
@@ -585,8 +843,10 @@ int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
     F2[d].assign(5 * nc, R(0.0));
   }
 
-  // steps 1-2: reconstruction (PPMC with characteristic tracing) and the first
-  // set of Riemann solves, one axis at a time
+  // steps 1-2: reconstruction and the first set of Riemann solves, one axis at
+  // a time.  Reconstructed cells along the sweep: padded index 3 .. N-4 (every
+  // stencil, up to i-3..i+3 for PPMP, lies inside the padded grid; these are
+  // the cells whose face states the fluxes of the real cells need).
   for (int d = 0; d < 3; ++d) {
     if (!active[d]) continue;
     const size_t sd = G.stride(d);
@@ -596,11 +856,11 @@ int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
       for (int j = 0; j < G.N[1]; ++j)
         for (int i = 0; i < G.N[0]; ++i) {
           const int c3[3] = {i, j, k};
-          if (c3[d] < 2 || c3[d] > G.N[d] - 3) continue;
+          if (c3[d] < 3 || c3[d] > G.N[d] - 4) continue;
           const size_t c = G.idx(i, j, k);
-          R w[5][5];
-          for (int s = 0; s < 5; ++s) {
-            const size_t cs = c + (size_t)((long)(s - 2) * (long)sd);
+          R w[7][5];
+          for (int s = 0; s < 7; ++s) {
+            const size_t cs = c + (size_t)((long)(s - 3) * (long)sd);
             w[s][0] = W[0 * nc + cs];
             w[s][1] = W[(1 + P[0]) * nc + cs];
             w[s][2] = W[(1 + P[1]) * nc + cs];
@@ -610,9 +870,32 @@ int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
           R WsL[5], WsR[5], UsL[5], UsR[5];
           set_stage((R*)nullptr, 1);
           add_units((R*)nullptr, 1);
-          ppmc_cell(w, dtdx, g, WsL, WsR);
-          prim_to_cons(WsL, g, UsL);
-          prim_to_cons(WsR, g, UsR);
+          switch (G.recon) {
+            case RECON_PPMP:
+              ppmp_cell(w, dtdx, R(G.dx), g, WsL, WsR);
+              prim_to_cons(WsL, g, UsL);
+              prim_to_cons(WsR, g, UsR);
+              break;
+            case RECON_PLMC:
+              plmc_cell(&w[2], dtdx, g, WsL, WsR);
+              prim_to_cons(WsL, g, UsL);
+              prim_to_cons(WsR, g, UsR);
+              break;
+            case RECON_PLMP:
+              plmp_cell(&w[2], dtdx, g, UsL, UsR);
+              break;
+            case RECON_PCM:  // U*_R(i-1/2) = U*_L(i+1/2) = u_i
+              UsL[0] = G.u[0 * nc + c];
+              UsL[4] = G.u[4 * nc + c];
+              for (int s = 0; s < 3; ++s) UsL[1 + s] = G.u[(1 + P[s]) * nc + c];
+              for (int q = 0; q < 5; ++q) UsR[q] = UsL[q];
+              break;
+            default:
+              ppmc_cell(&w[1], dtdx, g, WsL, WsR);
+              prim_to_cons(WsL, g, UsL);
+              prim_to_cons(WsR, g, UsR);
+              break;
+          }
           // left face of cell i is the right state of face i-1/2; right face of
           // cell i is the left state of face i+1/2
           const size_t cr = c + sd;
@@ -631,7 +914,7 @@ int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
       for (int j = 0; j < G.N[1]; ++j)
         for (int i = 0; i < G.N[0]; ++i) {
           const int c3[3] = {i, j, k};
-          if (c3[d] < 3 || c3[d] > G.N[d] - 3) continue;
+          if (c3[d] < 4 || c3[d] > G.N[d] - 4) continue;
           const size_t f = G.idx(i, j, k);
           R ULr[5], URr[5], Fr[5];
           ULr[0] = UL[d][0 * nc + f]; URr[0] = UR[d][0 * nc + f];
@@ -663,10 +946,10 @@ int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
       for (int j = 0; j < G.N[1]; ++j)
         for (int i = 0; i < G.N[0]; ++i) {
           const int c3[3] = {i, j, k};
-          if (c3[d] < 3 || c3[d] > G.N[d] - 3) continue;
+          if (c3[d] < 4 || c3[d] > G.N[d] - 4) continue;
           bool ok = true;
           for (int t = 0; t < 3; ++t)
-            if (t != d && active[t] && (c3[t] < 3 || c3[t] > G.N[t] - 4)) ok = false;
+            if (t != d && active[t] && (c3[t] < 4 || c3[t] > G.N[t] - 5)) ok = false;
           if (!ok) continue;
           const size_t f = G.idx(i, j, k);
           const size_t cl = f - sd;  // cell left of the face
@@ -755,6 +1038,13 @@ void oracle_free(void* h) { delete static_cast<Handle*>(h); }
 int oracle_set_inflow(void* h, int face, const double* prim) {
   if (!h || face < 0 || face > 5) return -1;
   for (int q = 0; q < 5; ++q) static_cast<Handle*>(h)->G.inflow_prim[face][q] = prim[q];
+  return 0;
+}
+
+// reconstruction: 0 PPMC (default), 1 PPMP, 2 PLMC, 3 PLMP, 4 PCM
+int oracle_set_recon(void* h, int recon) {
+  if (!h || recon < RECON_PPMC || recon > RECON_PCM) return -1;
+  static_cast<Handle*>(h)->G.recon = recon;
   return 0;
 }
 
@@ -848,6 +1138,35 @@ int oracle_ppmc(int n, const double* w, double dtdx, double gamma, double* WsL, 
   return 0;
 }
 
+// Any reconstruction on seven-cell primitive stencils w[n][7 cells i-3..i+3][5]
+// (rotated order); returns the conserved face states of the centre cell at its
+// left (UsL) and right (UsR) face, each [n][5].  PCM returns the conserved
+// form of w_i at both faces.
+int oracle_reconstruct(int n, int recon, const double* w, double dtdx, double dx, double gamma,
+                       double* UsL, double* UsR) {
+  if (recon < RECON_PPMC || recon > RECON_PCM) return -1;
+  const Gas g(gamma);
+  for (int i = 0; i < n; ++i) {
+    double st[7][5], WsL[5], WsR[5];
+    for (int s = 0; s < 7; ++s)
+      for (int q = 0; q < 5; ++q) st[s][q] = w[35 * i + 5 * s + q];
+    double* L = UsL + 5 * i;
+    double* R = UsR + 5 * i;
+    switch (recon) {
+      case RECON_PPMP: ppmp_cell(st, dtdx, dx, g, WsL, WsR); break;
+      case RECON_PLMC: plmc_cell(&st[2], dtdx, g, WsL, WsR); break;
+      case RECON_PLMP: plmp_cell(&st[2], dtdx, g, L, R); continue;
+      case RECON_PCM:
+        for (int q = 0; q < 5; ++q) WsL[q] = WsR[q] = st[3][q];
+        break;
+      default: ppmc_cell(&st[1], dtdx, g, WsL, WsR); break;
+    }
+    prim_to_cons(WsL, g, L);
+    prim_to_cons(WsR, g, R);
+  }
+  return 0;
+}
+
 // Algorithmic operation count of one CTU step with the given dt on the current
 // state (the state itself is not changed).  counts = {add/sub, mul, div, sqrt,
 // pow, compare/min/max/abs}; returns the step's status flags.
@@ -856,6 +1175,7 @@ int oracle_count_step(void* h, double dt, double* counts) {
   Grid<CR> G(G0.n, G0.dx, G0.gamma, G0.bc);
   for (int f = 0; f < 6; ++f)
     for (int q = 0; q < 5; ++q) G.inflow_prim[f][q] = G0.inflow_prim[f][q];
+  G.recon = G0.recon;
   for (size_t i = 0; i < G0.u.size(); ++i) G.u[i] = CR(G0.u[i]);
   g_ops = OpCount();
   for (int k = 0; k < kStages; ++k) {
@@ -883,6 +1203,7 @@ int oracle_count_step_stages(void* h, double dt, double* counts, double* units) 
   Grid<CR> G(G0.n, G0.dx, G0.gamma, G0.bc);
   for (int f = 0; f < 6; ++f)
     for (int q = 0; q < 5; ++q) G.inflow_prim[f][q] = G0.inflow_prim[f][q];
+  G.recon = G0.recon;
   for (size_t i = 0; i < G0.u.size(); ++i) G.u[i] = CR(G0.u[i]);
   g_ops = OpCount();
   for (int k = 0; k < kStages; ++k) {

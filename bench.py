@@ -49,7 +49,15 @@ PEAK_SOURCE = "152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM x 2 flop/FMA (unit counts 
 # riemann2).  The benchmark never runs the oracle for these.
 ALGORITHMIC_FLOPS = {
     "batched": {"ppmc": 406.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 81.0, "update": 45.0},
+    "batched/pcm": {"ppmc": 0.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 0.0, "update": 45.0},
+    "batched/plmc": {"ppmc": 108.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 81.0, "update": 45.0},
+    "batched/plmp": {"ppmc": 107.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 25.0, "update": 45.0},
+    "batched/ppmp": {"ppmc": 511.042, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 25.0, "update": 45.0},
     "sedov": {"ppmc": 406.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 81.0, "update": 45.0},
+    "sedov/pcm": {"ppmc": 0.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 0.0, "update": 45.0},
+    "sedov/plmc": {"ppmc": 108.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 81.0, "update": 45.0},
+    "sedov/plmp": {"ppmc": 107.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 25.0, "update": 45.0},
+    "sedov/ppmp": {"ppmc": 511.042, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 25.0, "update": 45.0},
     "shock_cloud": {"ppmc": 413.0, "prims": 22.752, "riemann1": 135.667, "riemann2": 195.667, "slopes": 81.0, "update": 45.0},
     "sod512": {"ppmc": 406.0, "prims": 28.742, "riemann1": 136.125, "riemann2": 136.125, "slopes": 81.0, "update": 15.0},
     "turbulence": {"ppmc": 423.374, "prims": 22.752, "riemann1": 140.154, "riemann2": 200.574, "slopes": 91.922, "update": 45.0},
@@ -205,12 +213,17 @@ def dist_env():
     return ws, rank, local
 
 
-def flops_table(key):
-    """Algorithmic FP64 flops per unit for a workload key."""
+RECON_CODES = {"ppmc": 0, "ppmp": 1, "plmc": 2, "plmp": 3, "pcm": 4}
+
+
+def flops_table(key, recon="ppmc"):
+    """Algorithmic FP64 flops per unit for a workload key (and reconstruction)."""
     if key.startswith("sedov"):
-        return ALGORITHMIC_FLOPS["sedov"], "sedov"
-    if key.startswith("batched"):
-        return ALGORITHMIC_FLOPS["batched"], "batched"
+        key = "sedov"
+    elif key.startswith("batched"):
+        key = "batched"
+    if recon != "ppmc":
+        key = "%s/%s" % (key, recon)
     return ALGORITHMIC_FLOPS[key], key
 
 
@@ -256,6 +269,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sedov256")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--recon", default="ppmc", choices=list(RECON_CODES),
+                    help="reconstruction (Sec. 2.2.1): ppmc (default), ppmp, plmc, plmp, pcm")
     ap.add_argument("--cfl", type=float, default=0.3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -284,7 +299,8 @@ def main():
     nreal = nx * ny * nz
     prec = hydro.HYDRO_FP64 if args.precision == "fp64" else hydro.HYDRO_MIXED
     stream = torch.cuda.current_stream()
-    g = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], precision=prec, stream=stream)
+    g = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], precision=prec, stream=stream,
+                   recon=RECON_CODES[args.recon])
     for face, prim in (w.get("inflow") or {}).items():
         g.set_inflow(face, prim)
     u_host = torch.from_numpy(w["u"]).pin_memory()
@@ -356,7 +372,7 @@ def main():
     dms, dl, dunits = stages[dom]
     active = sum(1 for n in (nx, ny, nz) if n > 1)
     if args.precision == "fp64":
-        table, tkey = flops_table(w["key"])
+        table, tkey = flops_table(w["key"], args.recon)
         per_unit = table[dom]
         src = "algorithmic FP64 flops per unit (oracle/count_ops.py, %s)" % tkey
     else:
@@ -372,7 +388,8 @@ def main():
         traffic = tinfo["bytes_per_unit"] * units_per_launch
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_FLOPS_PEAK,
                 "unit": "FP64 FLOP/s", "frac": achieved / FP64_FLOPS_PEAK, "traffic": traffic,
-                "kernel": ("kb_" + dom) if args.precision == "fp64" else ("kb_%s_mixed" % dom),
+                "kernel": ("kb_" + (args.recon if dom == "ppmc" else dom)) if args.precision == "fp64"
+                          else ("kb_%s_mixed" % dom),
                 "flops_per_unit": per_unit, "units_per_launch": units_per_launch,
                 "avg_launch_ms": avg_ms, "flops_source": src, "peak_source": PEAK_SOURCE,
                 "bytes_per_unit_algorithmic": ALGORITHMIC_BYTES[args.precision][dom]}
@@ -387,7 +404,7 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": single_config(args.workload, args.precision, ws),
+        "config": single_config(args.workload, args.precision, ws, args.recon),
         "e2e": e2e, "gpu_launches": launches_total, "clocks": clocks, "roofline": roofline,
         "stages": stage_report, "cpu_baseline": cpu,
         "hbm": hbm_report(value / ws, traffic, avg_ms),
@@ -411,7 +428,7 @@ def run_batch(args, w, ws, rank, local):
     ncells = sum(int(np.prod(g["u"].shape[1:])) for g in grids)
     prec = hydro.HYDRO_FP64 if args.precision == "fp64" else hydro.HYDRO_MIXED
     stream = torch.cuda.Stream()
-    b = hydro.Batch(grids, precision=prec)
+    b = hydro.Batch(grids, precision=prec, recon=RECON_CODES[args.recon])
     b._check(b._L.hydro_batch_set_stream(b.h, hydro.ctypes.c_void_p(stream.cuda_stream)),
              "set_stream")
     bs, order, tune_ms = b.autotune(use_cache=True)
@@ -665,9 +682,10 @@ def workload_desc(name):
     return WORKLOAD_DESC.get(name, name)
 
 
-def single_config(name, precision, ws):
+def single_config(name, precision, ws, recon="ppmc"):
     nx, ny, nz = workload_shape(name)
     return {"workload": workload_desc(name), "cells": nx * ny * nz, "precision": precision,
+            "reconstruction": recon,
             "parallelism": "replicas" if ws > 1 else "single",
             "l2": "inputs larger than L2 (state %.2f GB, step working set %.1f GB)" % (
                 nx * ny * nz * 40 / 1e9,

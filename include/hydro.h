@@ -59,6 +59,25 @@ enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_REFLECT = 1, HYDRO_BC_OUTFLOW = 2, HYDRO_
  *   reproducibility against a plain CPU implementation; slower. */
 enum { HYDRO_FP64 = 0, HYDRO_MIXED = 1, HYDRO_FP64_STRICT = 2 };
 
+/* Reconstruction of the face states (Sec. 2.2.1, App. A).  HYDRO_RECON_PPMC
+ * (default): PPM in characteristic variables with characteristic tracing
+ * (App. A.3).  HYDRO_RECON_PPMP: PPM in primitive variables with contact
+ * steepening, shock flattening and CW84 characteristic tracing (App. A.4; the
+ * contact test is d2rho_{i-1} d2rho_{i+1} < 0, as in the method the paper
+ * follows, which reproduces its Sod result).  HYDRO_RECON_PLMC: piecewise
+ * linear, characteristic limiting and tracing (App. A.2).  HYDRO_RECON_PLMP:
+ * piecewise linear, primitive limiting, half-step flux evolution (App. A.1).
+ * HYDRO_RECON_PCM: piecewise constant (Sec. 2.2.1).  PPMP needs three cells on
+ * each side of a cell, the others one or two; every mode fits the 4 ghost
+ * layers. */
+enum {
+  HYDRO_RECON_PPMC = 0,
+  HYDRO_RECON_PPMP = 1,
+  HYDRO_RECON_PLMC = 2,
+  HYDRO_RECON_PLMP = 3,
+  HYDRO_RECON_PCM = 4
+};
+
 enum {
   HYDRO_OK = 0,
   HYDRO_EINVAL = -1,    /* invalid argument (sizes, bc, gamma, dx, null pointer, face) */
@@ -139,6 +158,11 @@ int hydro_profile(hydro_t h, int enable);
 int hydro_profile_read(hydro_t h, int nstages, double* ms, long long* launches, long long* units,
                        long long* launches_total);
 
+/* Select the reconstruction (HYDRO_RECON_*) of the following steps.  The
+ * non-default modes run in HYDRO_FP64 and HYDRO_FP64_STRICT; with HYDRO_MIXED
+ * they are rejected (HYDRO_EINVAL), as is an unknown mode. */
+int hydro_set_reconstruction(hydro_t h, int recon);
+
 /* Release the handle and all device memory it owns.  NULL is accepted. */
 void hydro_free(hydro_t h);
 
@@ -180,6 +204,8 @@ int hydro_batch_step(hydro_batch_t h, double cfl, int nsteps, double* dt_out);
  * measured ms a step (-1 when taken from the cache). */
 int hydro_batch_autotune(hydro_batch_t h, int use_cache, int* block_size, int* order,
                          float* ms_per_step);
+/* Reconstruction of every grid of the batch (as hydro_set_reconstruction). */
+int hydro_batch_set_reconstruction(hydro_batch_t h, int recon);
 int hydro_batch_last_error(hydro_batch_t h);
 const char* hydro_batch_cuda_error_string(hydro_batch_t h);
 void hydro_batch_free(hydro_batch_t h);

@@ -38,10 +38,11 @@ def sample(name):
     return s, "32^3 corner block of the full field, periodic"
 
 
-def counts(name, cfl=0.3):
+def counts(name, cfl=0.3, recon=oracle.RECON_PPMC):
     s, desc = sample(name)
     _, nz, ny, nx = s["u"].shape
     g = oracle.Grid(nx, ny, nz, s["dx"], s["gamma"], s["bc"])
+    g.set_recon(recon)
     g.set_state(s["u"])
     st = g.count_step_stages(g.compute_dt(cfl))
     flops = {k: (sum(v["ops"].values()) - v["ops"]["cmp"]) / max(v["units"], 1)
@@ -53,6 +54,11 @@ def counts(name, cfl=0.3):
 def main():
     out = {name: counts(name) for name in ("sedov", "sod512", "shock_cloud", "turbulence")}
     out["batched"] = out["sedov"]
+    recons = {"ppmp": oracle.RECON_PPMP, "plmc": oracle.RECON_PLMC, "plmp": oracle.RECON_PLMP,
+              "pcm": oracle.RECON_PCM}
+    for rname, r in recons.items():
+        out["sedov/" + rname] = counts("sedov", recon=r)
+        out["batched/" + rname] = out["sedov/" + rname]
     json.dump(out, sys.stdout, indent=1, sort_keys=True)
     sys.stdout.write("\n")
 

@@ -23,6 +23,7 @@ struct hydro_s {
   BcDesc bc;
   double gamma;
   int precision;
+  int recon;
   int device;
   cudaStream_t stream;
   bool have_state;
@@ -147,11 +148,15 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
     STAGE(h, kStageSetDt, 0, fp64_set_dt(G, B, cfl, fixed_dt, st));
     for (int d = 0; d < 3; ++d) {
       if (!active(G, d)) continue;
-      for (int s = kStageSlopes; s <= kStageRiemann1; ++s)
-        STAGE(h, s, d, fp64_stage_strict(G, B, s, d, h->gamma, st));
+      for (int s = kStageSlopes; s <= kStageRiemann1; ++s) {
+        if (s == kStageSlopes && h->recon == HYDRO_RECON_PCM) continue;  // no slopes
+        STAGE(h, s, d, fp64_stage_strict(G, B, h->recon, s, d, h->gamma, st));
+      }
     }
     for (int d = 0; d < 3; ++d)
-      if (active(G, d)) STAGE(h, kStageRiemann2, d, fp64_stage_strict(G, B, kStageRiemann2, d, h->gamma, st));
+      if (active(G, d))
+        STAGE(h, kStageRiemann2, d,
+              fp64_stage_strict(G, B, h->recon, kStageRiemann2, d, h->gamma, st));
     STAGE(h, kStageUpdate, 0, fp64_update(G, B, st));
     return HYDRO_OK;
   }
@@ -163,14 +168,16 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
   for (int d = 0; d < 3; ++d) {
     if (!active(G, d)) continue;
     for (int s = kStageSlopes; s <= kStageRiemann1; ++s) {
+      if (s == kStageSlopes && h->recon == HYDRO_RECON_PCM) continue;  // no slopes
       const int k = launch_kind(s, d);
-      STAGE(h, s, d, batch_stage(one_grid(h, k), P, s, d, 256, h->blocks[k], st));
+      STAGE(h, s, d, batch_stage(one_grid(h, k), P, h->recon, s, d, 256, h->blocks[k], st));
     }
   }
   for (int d = 0; d < 3; ++d) {
     if (!active(G, d)) continue;
     const int k = launch_kind(kStageRiemann2, d);
-    STAGE(h, kStageRiemann2, d, batch_stage(one_grid(h, k), P, kStageRiemann2, d, 256, h->blocks[k], st));
+    STAGE(h, kStageRiemann2, d,
+          batch_stage(one_grid(h, k), P, h->recon, kStageRiemann2, d, 256, h->blocks[k], st));
   }
   STAGE(h, kStageUpdate, 0, batch_update(one_grid(h, 1), P, 256, h->blocks[1], st));
   return HYDRO_OK;
@@ -234,6 +241,7 @@ int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, co
   memset(h->cuda_err, 0, sizeof(h->cuda_err));
   h->gamma = gamma;
   h->precision = HYDRO_FP64;
+  h->recon = HYDRO_RECON_PPMC;
   h->stream = nullptr;
   h->have_state = false;
   h->last_error = HYDRO_OK;
@@ -353,7 +361,17 @@ int hydro_set_precision(hydro_t h, int mode) {
   h->last_error = HYDRO_OK;
   if (mode != HYDRO_FP64 && mode != HYDRO_FP64_STRICT && mode != HYDRO_MIXED)
     return fail(h, HYDRO_EINVAL);
+  if (mode == HYDRO_MIXED && h->recon != HYDRO_RECON_PPMC) return fail(h, HYDRO_EINVAL);
   h->precision = mode;
+  return HYDRO_OK;
+}
+
+int hydro_set_reconstruction(hydro_t h, int recon) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (recon < HYDRO_RECON_PPMC || recon > HYDRO_RECON_PCM) return fail(h, HYDRO_EINVAL);
+  if (recon != HYDRO_RECON_PPMC && h->precision == HYDRO_MIXED) return fail(h, HYDRO_EINVAL);
+  h->recon = recon;
   return HYDRO_OK;
 }
 

@@ -36,6 +36,7 @@ struct Schedule {
 struct hydro_batch_s {
   int ngrids = 0;
   int precision = HYDRO_FP64;
+  int recon = HYDRO_RECON_PPMC;
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -58,6 +59,7 @@ struct hydro_batch_s {
   int g_nsteps = -1;
   double g_cfl = -1.0;
   int g_precision = -1;
+  int g_recon = -1;
   Schedule g_sched;
   int last_error = HYDRO_OK;
   char cuda_err[256] = {0};
@@ -123,13 +125,16 @@ int enqueue_step(hydro_batch_t h, double cfl, int step) {
     if (!h->axis_used[d]) continue;
     for (int s = kStageSlopes; s <= kStageRiemann1; ++s) {
       const int kind = launch_kind(s, d);
-      BCK(h, batch_stage(launch_of(h, kind), h->precision, s, d, bs, h->blocks[kind], st));
+      if (s == kStageSlopes && h->recon == HYDRO_RECON_PCM) continue;  // no slopes
+      BCK(h, batch_stage(launch_of(h, kind), h->precision, h->recon, s, d, bs, h->blocks[kind],
+                         st));
     }
   }
   for (int d = 0; d < 3; ++d) {
     if (!h->axis_used[d]) continue;
     const int kind = launch_kind(kStageRiemann2, d);
-    BCK(h, batch_stage(launch_of(h, kind), h->precision, kStageRiemann2, d, bs, h->blocks[kind], st));
+    BCK(h, batch_stage(launch_of(h, kind), h->precision, h->recon, kStageRiemann2, d, bs,
+                       h->blocks[kind], st));
   }
   BCK(h, batch_update(launch_of(h, 1), h->precision, bs, h->blocks[1], st));
   return HYDRO_OK;
@@ -173,7 +178,8 @@ std::string cache_path() {
 }
 
 std::string shape_key(hydro_batch_t h) {
-  // FNV-1a over the grid sizes, plus precision and device name
+  // FNV-1a over the grid sizes (and a non-default reconstruction), plus
+  // precision and device name
   unsigned long long x = 1469598103934665603ULL;
   auto mix = [&](long long v) {
     for (int b = 0; b < 8; ++b) {
@@ -184,6 +190,7 @@ std::string shape_key(hydro_batch_t h) {
   mix(h->ngrids);
   for (const GridDesc& g : h->desc)
     for (int d = 0; d < 3; ++d) mix(g.G.n[d]);
+  if (h->recon != HYDRO_RECON_PPMC) mix(1000 + h->recon);
   cudaDeviceProp prop;
   char name[64] = "unknown";
   if (cudaGetDeviceProperties(&prop, h->device) == cudaSuccess) {
@@ -350,8 +357,19 @@ int hydro_batch_set_precision(hydro_batch_t h, int mode) {
   if (!h) return HYDRO_EINVAL;
   h->last_error = HYDRO_OK;
   if (mode != HYDRO_FP64 && mode != HYDRO_MIXED) return bfail(h, HYDRO_EINVAL);
+  if (mode == HYDRO_MIXED && h->recon != HYDRO_RECON_PPMC) return bfail(h, HYDRO_EINVAL);
   if (mode != h->precision) h->tuned = false;
   h->precision = mode;
+  return HYDRO_OK;
+}
+
+int hydro_batch_set_reconstruction(hydro_batch_t h, int recon) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (recon < HYDRO_RECON_PPMC || recon > HYDRO_RECON_PCM) return bfail(h, HYDRO_EINVAL);
+  if (recon != HYDRO_RECON_PPMC && h->precision == HYDRO_MIXED) return bfail(h, HYDRO_EINVAL);
+  if (recon != h->recon) h->tuned = false;
+  h->recon = recon;
   return HYDRO_OK;
 }
 
@@ -400,8 +418,8 @@ int hydro_batch_step(hydro_batch_t h, double cfl, int nsteps, double* dt_out) {
   int rc = ensure_dt(h, nsteps);
   if (rc) return rc;
   const bool same = h->gexec && h->g_nsteps == nsteps && h->g_cfl == cfl &&
-                    h->g_precision == h->precision && h->g_sched.bs == h->sched.bs &&
-                    h->g_sched.order == h->sched.order;
+                    h->g_precision == h->precision && h->g_recon == h->recon &&
+                    h->g_sched.bs == h->sched.bs && h->g_sched.order == h->sched.order;
   if (!same) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;
@@ -426,6 +444,7 @@ int hydro_batch_step(hydro_batch_t h, double cfl, int nsteps, double* dt_out) {
     h->g_nsteps = nsteps;
     h->g_cfl = cfl;
     h->g_precision = h->precision;
+    h->g_recon = h->recon;
     h->g_sched = h->sched;
   }
   BCK(h, cudaGraphLaunch(h->gexec, h->stream));

@@ -352,9 +352,9 @@ long long stage_units(const Geom& G, int stage, int axis) {
   return box_count(stage_box(G, stage, axis));
 }
 
-cudaError_t fp64_stage_strict(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
-                              cudaStream_t st) {
-  return launch_axis_stage<true>(G, B, stage, axis, gamma, st);
+cudaError_t fp64_stage_strict(const Geom& G, const Bufs& B, int recon, int stage, int axis,
+                              double gamma, cudaStream_t st) {
+  return launch_axis_stage<true>(G, B, recon, stage, axis, gamma, st);
 }
 
 cudaError_t batch_prims(const BatchLaunch& L, int precision, int bs, unsigned blocks, cudaStream_t st) {
@@ -384,10 +384,10 @@ cudaError_t batch_set_dt(const GridDesc* descs, int ngrids, double cfl, double* 
   return cudaGetLastError();
 }
 
-cudaError_t batch_stage(const BatchLaunch& L, int precision, int stage, int axis, int bs,
-                        unsigned blocks, cudaStream_t st) {
+cudaError_t batch_stage(const BatchLaunch& L, int precision, int recon, int stage, int axis,
+                        int bs, unsigned blocks, cudaStream_t st) {
   return precision == HYDRO_MIXED ? batch_stage_mixed(L, stage, axis, bs, blocks, st)
-                                  : batch_stage_fp64(L, stage, axis, bs, blocks, st);
+                                  : batch_stage_fp64(L, recon, stage, axis, bs, blocks, st);
 }
 
 cudaError_t fp64_update(const Geom& G, const Bufs& B, cudaStream_t st) {

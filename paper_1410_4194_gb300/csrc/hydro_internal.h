@@ -107,8 +107,8 @@ cudaError_t fp64_prims(const Geom& G, const Bufs& B, const BcDesc& bc, double ga
 cudaError_t fp64_set_dt(const Geom& G, const Bufs& B, double cfl, double fixed_dt, cudaStream_t st);
 // one launch of a per-axis stage in the reference operation order (strict mode);
 // the fast FP64 and mixed paths use the batched launchers below with one grid
-cudaError_t fp64_stage_strict(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
-                              cudaStream_t st);
+cudaError_t fp64_stage_strict(const Geom& G, const Bufs& B, int recon, int stage, int axis,
+                              double gamma, cudaStream_t st);
 cudaError_t fp64_update(const Geom& G, const Bufs& B, cudaStream_t st);
 
 // Batched launchers: one launch covers the given stage of every grid of a
@@ -117,13 +117,13 @@ cudaError_t fp64_update(const Geom& G, const Bufs& B, cudaStream_t st);
 cudaError_t batch_prims(const BatchLaunch& L, int precision, int bs, unsigned blocks, cudaStream_t st);
 cudaError_t batch_set_dt(const GridDesc* descs, int ngrids, double cfl, double* dt_hist,
                          cudaStream_t st);
-cudaError_t batch_stage(const BatchLaunch& L, int precision, int stage, int axis, int bs,
-                        unsigned blocks, cudaStream_t st);
+cudaError_t batch_stage(const BatchLaunch& L, int precision, int recon, int stage, int axis,
+                        int bs, unsigned blocks, cudaStream_t st);
 cudaError_t batch_update(const BatchLaunch& L, int precision, int bs, unsigned blocks,
                          cudaStream_t st);
 // batched building blocks in the fast FP64 and the mixed translation units
-cudaError_t batch_stage_fp64(const BatchLaunch& L, int stage, int axis, int bs, unsigned blocks,
-                             cudaStream_t st);
+cudaError_t batch_stage_fp64(const BatchLaunch& L, int recon, int stage, int axis, int bs,
+                             unsigned blocks, cudaStream_t st);
 cudaError_t batch_stage_mixed(const BatchLaunch& L, int stage, int axis, int bs, unsigned blocks,
                               cudaStream_t st);
 cudaError_t batch_prims_mixed(const BatchLaunch& L, int bs, unsigned blocks, cudaStream_t st);

@@ -5,6 +5,7 @@
 // multiply-add contraction) and hydro_fp64_strict.cu (S = true, compiled without
 // it so that every a*b+c rounds twice, as the CPU reference does).
 #pragma once
+#include "../../include/hydro.h"
 #include "hydro_internal.h"
 #include "hydro_math.cuh"
 
@@ -164,6 +165,139 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppmc(Geom G, Bufs B, B
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < count) ppmc_body<D, S>(G, B, box, g, t);
 }
+
+// store the face states of cell c: its left face is the right state of face c,
+// its right face the left state of face c+1; primitives W* (fast) or the
+// conserved U* (strict, as the paper passes them between kernels)
+template <int D, bool S>
+__device__ __forceinline__ void store_face_states(const Geom& G, const Bufs& B, const Gas& g,
+                                                  long long c, const double WsL[5],
+                                                  const double WsR[5]) {
+  const long long s = G.s[D];
+  if constexpr (S) {
+    double UsL[5], UsR[5];
+    prim2cons<true>(WsL, g, UsL);
+    prim2cons<true>(WsR, g, UsR);
+    store_rot<D>(B.UR[D], G.ps, c, UsL);
+    store_rot<D>(B.UL[D], G.ps, c + s, UsR);
+  } else {
+    store_rot<D>(B.UR[D], G.ps, c, WsL);
+    store_rot<D>(B.UL[D], G.ps, c + s, WsR);
+  }
+}
+
+// limited primitive slope of every cell of the box (PPMP, PLMP)
+template <int D, bool S>
+__device__ __forceinline__ void prim_slopes_body(const Geom& G, const Bufs& B, const Box& box,
+    const Gas& g, long long t) {
+  int c3[3];
+  box_coords(box, t, c3);
+  const long long c = pidx(G, c3);
+  const long long s = G.s[D];
+  double wm[5], wc[5], wp[5], dw[5];
+  load_prim<D>(B.W, G.ps, c - s, wm);
+  load_prim<D>(B.W, G.ps, c, wc);
+  load_prim<D>(B.W, G.ps, c + s, wp);
+  prim_slope<S>(wm, wc, wp, dw);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) B.S[q * G.ps + c] = dw[q];
+}
+
+// PPMP face states of cell c (stencil c-3..c+3)
+template <int D, bool S>
+__device__ __forceinline__ void ppmp_body(const Geom& G, const Bufs& B, const Box& box,
+    const Gas& g, long long t) {
+  int c3[3];
+  box_coords(box, t, c3);
+  const long long c = pidx(G, c3);
+  const long long s = G.s[D];
+  double w[7][5], sm[5], sc[5], sp[5];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) load_prim<D>(B.W, G.ps, c + (k - 3) * s, w[k]);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    sm[q] = B.S[q * G.ps + c - s];
+    sc[q] = B.S[q * G.ps + c];
+    sp[q] = B.S[q * G.ps + c + s];
+  }
+  double WsL[5], WsR[5];
+  ppmp_states<S>(w, sm, sc, sp, B.W[5 * G.ps + c], B.rec[2], G.dx, g, WsL, WsR);
+  store_face_states<D, S>(G, B, g, c, WsL, WsR);
+}
+
+// PLMC face states of cell c (characteristic slope of c from the slope stage)
+template <int D, bool S>
+__device__ __forceinline__ void plmc_body(const Geom& G, const Bufs& B, const Box& box,
+    const Gas& g, long long t) {
+  int c3[3];
+  box_coords(box, t, c3);
+  const long long c = pidx(G, c3);
+  const long long s = G.s[D];
+  double wm[5], wc[5], wp[5], dw[5];
+  load_prim<D>(B.W, G.ps, c - s, wm);
+  load_prim<D>(B.W, G.ps, c, wc);
+  load_prim<D>(B.W, G.ps, c + s, wp);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) dw[q] = B.S[q * G.ps + c];
+  double WsL[5], WsR[5];
+  plmc_states<S>(wm, wc, wp, dw, B.W[5 * G.ps + c], B.W[6 * G.ps + c], B.W[7 * G.ps + c],
+                 B.rec[2], WsL, WsR);
+  store_face_states<D, S>(G, B, g, c, WsL, WsR);
+}
+
+// PLMP face states of cell c (primitive slope of c from the slope stage); the
+// half-step evolution gives conserved states, stored as such (strict) or as
+// their primitives (fast)
+template <int D, bool S>
+__device__ __forceinline__ void plmp_body(const Geom& G, const Bufs& B, const Box& box,
+    const Gas& g, long long t) {
+  int c3[3];
+  box_coords(box, t, c3);
+  const long long c = pidx(G, c3);
+  const long long s = G.s[D];
+  double wc[5], dw[5], UsL[5], UsR[5];
+  load_prim<D>(B.W, G.ps, c, wc);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) dw[q] = B.S[q * G.ps + c];
+  plmp_states<S>(wc, dw, B.rec[2], g, UsL, UsR);
+  if constexpr (S) {
+    store_rot<D>(B.UR[D], G.ps, c, UsL);
+    store_rot<D>(B.UL[D], G.ps, c + s, UsR);
+  } else {
+    double WsL[5], WsR[5], idL, idR;
+    cons2prim<false>(UsL, g, WsL, idL);
+    cons2prim<false>(UsR, g, WsR, idR);
+    store_rot<D>(B.UR[D], G.ps, c, WsL);
+    store_rot<D>(B.UL[D], G.ps, c + s, WsR);
+  }
+}
+
+// PCM face states of cell c: the cell average at both faces (stored as its
+// primitives, or in strict mode converted back to conserved variables)
+template <int D, bool S>
+__device__ __forceinline__ void pcm_body(const Geom& G, const Bufs& B, const Box& box,
+    const Gas& g, long long t) {
+  int c3[3];
+  box_coords(box, t, c3);
+  const long long c = pidx(G, c3);
+  double wc[5];
+  load_prim<D>(B.W, G.ps, c, wc);
+  store_face_states<D, S>(G, B, g, c, wc, wc);
+}
+
+#define HYDRO_SINGLE_WRAPPER(NAME, BODY)                                                 \
+  template <int D, bool S>                                                               \
+  __global__ void __launch_bounds__(kThreads, kMinBlocks) NAME(Geom G, Bufs B, Box box, Gas g) { \
+    const long long count = (long long)box.n[0] * box.n[1] * box.n[2];                   \
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;                \
+    if (t < count) BODY<D, S>(G, B, box, g, t);                                          \
+  }
+HYDRO_SINGLE_WRAPPER(k_prim_slopes, prim_slopes_body)
+HYDRO_SINGLE_WRAPPER(k_ppmp, ppmp_body)
+HYDRO_SINGLE_WRAPPER(k_plmc, plmc_body)
+HYDRO_SINGLE_WRAPPER(k_plmp, plmp_body)
+HYDRO_SINGLE_WRAPPER(k_pcm, pcm_body)
+#undef HYDRO_SINGLE_WRAPPER
 
 template <int D, bool S>
 __device__ __forceinline__ void riemann1_body(const Geom& G, const Bufs& B, const Box& box,
@@ -325,7 +459,12 @@ __device__ __forceinline__ BatchItem batch_item(const BatchLaunch& L) {
       BODY<D, S>(it.d->G, it.d->B, box, it.d->gd, it.t);                                       \
   }
 HYDRO_BATCH_WRAPPER(kb_slopes, slopes_body, 0)
+HYDRO_BATCH_WRAPPER(kb_prim_slopes, prim_slopes_body, 0)
 HYDRO_BATCH_WRAPPER(kb_ppmc, ppmc_body, 1)
+HYDRO_BATCH_WRAPPER(kb_ppmp, ppmp_body, 1)
+HYDRO_BATCH_WRAPPER(kb_plmc, plmc_body, 1)
+HYDRO_BATCH_WRAPPER(kb_plmp, plmp_body, 1)
+HYDRO_BATCH_WRAPPER(kb_pcm, pcm_body, 1)
 HYDRO_BATCH_WRAPPER(kb_riemann1, riemann1_body, 2)
 HYDRO_BATCH_WRAPPER(kb_riemann2, riemann2_body, 3)
 #undef HYDRO_BATCH_WRAPPER
@@ -345,12 +484,16 @@ inline Box stage_box(const Geom& G, int stage, int axis) {
   }
 }
 
+// kernels of the slope and reconstruction stages for each reconstruction:
+// PPMC and PLMC take characteristic slopes, PPMP and PLMP primitive ones, PCM
+// none (its slope stage launches nothing)
 template <bool S>
-cudaError_t launch_axis_stage(const Geom& G, const Bufs& B, int stage, int axis, double gamma,
-                              cudaStream_t st) {
+cudaError_t launch_axis_stage(const Geom& G, const Bufs& B, int recon, int stage, int axis,
+                              double gamma, cudaStream_t st) {
   const Gas g = make_gas<double>(gamma);
   const Box b = stage_box(G, stage, axis);
   const unsigned nb = blocks_for(box_count(b));
+  if (nb == 0) return cudaSuccess;
 #define HYDRO_LAUNCH_AXIS(K)                                                 \
   switch (axis) {                                                            \
     case 0: K<0, S><<<nb, kThreads, 0, st>>>(G, B, b, g); break;            \
@@ -358,8 +501,23 @@ cudaError_t launch_axis_stage(const Geom& G, const Bufs& B, int stage, int axis,
     default: K<2, S><<<nb, kThreads, 0, st>>>(G, B, b, g); break;           \
   }
   switch (stage) {
-    case kStageSlopes: HYDRO_LAUNCH_AXIS(k_slopes) break;
-    case kStagePpmc: HYDRO_LAUNCH_AXIS(k_ppmc) break;
+    case kStageSlopes:
+      if (recon == HYDRO_RECON_PCM) return cudaSuccess;
+      if (recon == HYDRO_RECON_PPMP || recon == HYDRO_RECON_PLMP) {
+        HYDRO_LAUNCH_AXIS(k_prim_slopes)
+      } else {
+        HYDRO_LAUNCH_AXIS(k_slopes)
+      }
+      break;
+    case kStagePpmc:
+      switch (recon) {
+        case HYDRO_RECON_PPMP: HYDRO_LAUNCH_AXIS(k_ppmp) break;
+        case HYDRO_RECON_PLMC: HYDRO_LAUNCH_AXIS(k_plmc) break;
+        case HYDRO_RECON_PLMP: HYDRO_LAUNCH_AXIS(k_plmp) break;
+        case HYDRO_RECON_PCM: HYDRO_LAUNCH_AXIS(k_pcm) break;
+        default: HYDRO_LAUNCH_AXIS(k_ppmc) break;
+      }
+      break;
     case kStageRiemann1: HYDRO_LAUNCH_AXIS(k_riemann1) break;
     case kStageRiemann2: HYDRO_LAUNCH_AXIS(k_riemann2) break;
     default: return cudaErrorInvalidValue;
@@ -369,8 +527,8 @@ cudaError_t launch_axis_stage(const Geom& G, const Bufs& B, int stage, int axis,
 }
 
 template <bool S>
-cudaError_t launch_batch_stage(const BatchLaunch& L, int stage, int axis, int bs, unsigned blocks,
-                               cudaStream_t st) {
+cudaError_t launch_batch_stage(const BatchLaunch& L, int recon, int stage, int axis, int bs,
+                               unsigned blocks, cudaStream_t st) {
   if (blocks == 0) return cudaSuccess;
 #define HYDRO_BATCH_AXIS(K)                                                              \
   if (bs == 128) {                                                                       \
@@ -387,8 +545,23 @@ cudaError_t launch_batch_stage(const BatchLaunch& L, int stage, int axis, int bs
     }                                                                                    \
   }
   switch (stage) {
-    case kStageSlopes: HYDRO_BATCH_AXIS(kb_slopes) break;
-    case kStagePpmc: HYDRO_BATCH_AXIS(kb_ppmc) break;
+    case kStageSlopes:
+      if (recon == HYDRO_RECON_PCM) return cudaSuccess;
+      if (recon == HYDRO_RECON_PPMP || recon == HYDRO_RECON_PLMP) {
+        HYDRO_BATCH_AXIS(kb_prim_slopes)
+      } else {
+        HYDRO_BATCH_AXIS(kb_slopes)
+      }
+      break;
+    case kStagePpmc:
+      switch (recon) {
+        case HYDRO_RECON_PPMP: HYDRO_BATCH_AXIS(kb_ppmp) break;
+        case HYDRO_RECON_PLMC: HYDRO_BATCH_AXIS(kb_plmc) break;
+        case HYDRO_RECON_PLMP: HYDRO_BATCH_AXIS(kb_plmp) break;
+        case HYDRO_RECON_PCM: HYDRO_BATCH_AXIS(kb_pcm) break;
+        default: HYDRO_BATCH_AXIS(kb_ppmc) break;
+      }
+      break;
     case kStageRiemann1: HYDRO_BATCH_AXIS(kb_riemann1) break;
     case kStageRiemann2: HYDRO_BATCH_AXIS(kb_riemann2) break;
     default: return cudaErrorInvalidValue;

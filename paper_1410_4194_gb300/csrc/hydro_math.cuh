@@ -555,6 +555,320 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
 }
 
 // ---------------------------------------------------------------------------
+// The other reconstructions of App. A / Sec. 2.2.1 (PPMP, PLMC, PLMP; PCM needs
+// no arithmetic).  Arguments in sweep order; S selects the printed operation
+// order (strict) as for PPMC.
+
+// primitive-variable slope of one cell: left, right and centred differences
+// and the MC limiter (Eqs. diffs, vanLeer_limiter), each variable alone
+template <bool S = false, typename T>
+__device__ __forceinline__ void prim_slope(const T wm[5], const T wc[5], const T wp[5], T dw[5]) {
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const T dL = wc[q] - wm[q];
+    const T dR = wp[q] - wc[q];
+    const T dC = T(0.5) * (wp[q] - wm[q]);
+    T s = T(0);
+    if (pos<S>(dL * dR)) {
+      const T m = vmin<S>(vmin<S>(xabs(dC), T(2) * xabs(dL)), T(2) * xabs(dR));
+      s = neg<S>(dC) ? -m : m;
+    }
+    dw[q] = s;
+  }
+}
+
+// Euler flux along the sweep of a primitive state (Eq. x_flux)
+template <bool S = false, typename T>
+__device__ __forceinline__ void euler_flux(const T W[5], const GasT<T>& g, T F[5]) {
+  const T E = (S ? W[4] / g.gm1 : W[4] * g.inv_gm1) +
+              T(0.5) * W[0] * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  const T m = W[0] * W[1];
+  F[0] = m;
+  F[1] = m * W[1] + W[4];
+  F[2] = m * W[2];
+  F[3] = m * W[3];
+  F[4] = (E + W[4]) * W[1];
+}
+
+// PLMP (App. A.1): W_L = w - dw/2, W_R = w + dw/2 from the limited primitive
+// slope dw of the cell, converted to conserved variables and evolved half a
+// step with the fluxes of the two boundary values (Eqs. plmp_evolution_L/R).
+// Returns the conserved U*_L, U*_R.
+template <bool S = false, typename T>
+__device__ __forceinline__ void plmp_states(const T wc[5], const T dw[5], T dtdx,
+                                            const GasT<T>& g, T UsL[5], T UsR[5]) {
+  T WL[5], WR[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    WL[q] = wc[q] - T(0.5) * dw[q];
+    WR[q] = wc[q] + T(0.5) * dw[q];
+  }
+  WL[4] = vmax<S>(WL[4], T(kPFloor));
+  WR[4] = vmax<S>(WR[4], T(kPFloor));
+  T UL[5], UR[5], FL[5], FR[5];
+  prim2cons<S>(WL, g, UL);
+  prim2cons<S>(WR, g, UR);
+  euler_flux<S>(WL, g, FL);
+  euler_flux<S>(WR, g, FR);
+  const T h = T(0.5) * dtdx;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    UsL[q] = UL[q] + h * (FL[q] - FR[q]);
+    UsR[q] = UR[q] + h * (FL[q] - FR[q]);
+  }
+}
+
+// PLMC (App. A.2): boundary values from the characteristic-limited slope dw of
+// the cell (limited_slope), bounded by the neighbouring averages, the slope
+// recomputed as W_R - W_L, the integral under the linear profile over the
+// fastest wave's domain of dependence and the corrections s_L, s_R of the
+// other waves that move toward each face.
+template <bool S = false, typename T>
+__device__ __forceinline__ void plmc_states(const T wm[5], const T wc[5], const T wp[5],
+                                            const T dwc[5], T a, T inv_a, T inv_rho, T dtdx,
+                                            T WsL[5], T WsR[5]) {
+  T WL[5], WR[5], dw[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const T LA = wc[q] - T(0.5) * dwc[q];
+    const T RA = wc[q] + T(0.5) * dwc[q];
+    WL[q] = vmin<S>(vmax<S>(wc[q], wm[q]), vmax<S>(vmin<S>(wc[q], wm[q]), LA));
+    WR[q] = vmin<S>(vmax<S>(wc[q], wp[q]), vmax<S>(vmin<S>(wc[q], wp[q]), RA));
+    dw[q] = WR[q] - WL[q];
+  }
+  const T d = wc[0];
+  const T u = wc[1];
+  const T lm = u - a, l0 = u, lp = u + a;
+  const T a2 = a * a;
+  const T inv_a2 = inv_a * inv_a;
+  T sL[5] = {T(0), T(0), T(0), T(0), T(0)};
+  T sR[5] = {T(0), T(0), T(0), T(0), T(0)};
+  if (neg<S>(l0)) {  // contact (and advected transverse velocities)
+    sL[0] = sL[0] + (lm - l0) * (dw[0] - (S ? dw[4] / a2 : dw[4] * inv_a2));
+    sL[2] = sL[2] + (lm - l0) * dw[2];
+    sL[3] = sL[3] + (lm - l0) * dw[3];
+  }
+  if (neg<S>(lp)) {  // right acoustic wave
+    if constexpr (S) {
+      sL[0] = sL[0] + T(0.5) * (lm - lp) * (d * dw[1] / a + dw[4] / a2);
+      sL[1] = sL[1] + T(0.5) * (lm - lp) * (dw[1] + dw[4] / (a * d));
+    } else {
+      sL[0] = sL[0] + T(0.5) * (lm - lp) * (d * dw[1] * inv_a + dw[4] * inv_a2);
+      sL[1] = sL[1] + T(0.5) * (lm - lp) * (dw[1] + dw[4] * (inv_a * inv_rho));
+    }
+    sL[4] = sL[4] + T(0.5) * (lm - lp) * (d * dw[1] * a + dw[4]);
+  }
+  if (pos<S>(lm)) {  // left acoustic wave
+    if constexpr (S) {
+      sR[0] = sR[0] + T(0.5) * (lp - lm) * (-(d * dw[1]) / a + dw[4] / a2);
+      sR[1] = sR[1] + T(0.5) * (lp - lm) * (dw[1] - dw[4] / (a * d));
+    } else {
+      sR[0] = sR[0] + T(0.5) * (lp - lm) * (-(d * dw[1]) * inv_a + dw[4] * inv_a2);
+      sR[1] = sR[1] + T(0.5) * (lp - lm) * (dw[1] - dw[4] * (inv_a * inv_rho));
+    }
+    sR[4] = sR[4] + T(0.5) * (lp - lm) * (-(d * dw[1] * a) + dw[4]);
+  }
+  if (pos<S>(l0)) {  // contact (and advected transverse velocities)
+    sR[0] = sR[0] + (lp - l0) * (dw[0] - (S ? dw[4] / a2 : dw[4] * inv_a2));
+    sR[2] = sR[2] + (lp - l0) * dw[2];
+    sR[3] = sR[3] + (lp - l0) * dw[3];
+  }
+  const T am = dtdx * vmin<S>(lm, T(0)), bp = dtdx * vmax<S>(lp, T(0));
+  const T h = T(0.5) * dtdx;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    WsL[q] = (WL[q] - T(0.5) * am * dw[q]) + h * sL[q];
+    WsR[q] = (WR[q] - T(0.5) * bp * dw[q]) + h * sR[q];
+  }
+  WsL[4] = vmax<S>(WsL[4], T(kPFloor));
+  WsR[4] = vmax<S>(WsR[4], T(kPFloor));
+}
+
+// PPMP shock flattening coefficient F~_k (App. A.4) from p_{k-2..k+2} and the
+// normal velocities u_{k-1}, u_{k+1}: zero for a relative pressure jump across
+// k-1..k+1 below a third or diverging flow, else max(0, min(1, 10 (S - 3/4)))
+// with S = (p_{k+1} - p_{k-1}) / (p_{k+2} - p_{k-2}) (a vanishing denominator
+// gives S = +-inf, i.e. F~ = 1 for a positive numerator, else 0)
+template <bool S = false, typename T>
+__device__ __forceinline__ T flatten_tilde(const T p[5], T um, T up) {
+  const T num = p[3] - p[1];
+  if constexpr (S) {
+    const T jump = xabs(num) / tmin(p[3], p[1]);
+    if (jump < T(1.0 / 3.0) || up - um > T(0)) return T(0);
+    const T St = num / (p[4] - p[0]);
+    return tmax(T(0), tmin(T(1), T(10) * (St - T(0.75))));
+  } else {
+    if (lt<S>(T(3) * xabs(num), vmin<S>(p[3], p[1])) || pos<S>(up - um)) return T(0);
+    const T den = p[4] - p[0];
+    if (bits_equal(xabs(den), T(0))) return pos<S>(num) ? T(1) : T(0);
+    const T St = nr_div(num, den);
+    return vmax<S>(T(0), vmin<S>(T(1), T(10) * (St - T(0.75))));
+  }
+}
+
+// PPMP for cell i (App. A.4): w[0..6] the primitive states of cells i-3..i+3,
+// sm, sc, sp the limited primitive slopes of cells i-1, i, i+1 (prim_slope);
+// a, inv_a, inv_rho of cell i; dx the cell width.  Steps in the paper's order:
+// parabolic interpolation, density steepening at contacts (concavity test
+// d2rho_{i-1} d2rho_{i+1} < 0, as in the method the paper follows; see the
+// CPU reference), shock flattening, monotonicity, the integrals under the
+// parabola for the three characteristics, the reference states and the CW84
+// corrections chi.  Fast mode: division-free forms of the jump tests, the
+// undivided second differences in the concavity test and eta (dx cancels),
+// reciprocals and square roots by Newton iteration.
+template <bool S = false, typename T>
+__device__ __forceinline__ void ppmp_states(const T w[7][5], const T sm[5], const T sc[5],
+                                            const T sp[5], T a, T dtdx, T dx,
+                                            const GasT<T>& g, T WsL[5], T WsR[5]) {
+  const T* wim = w[2];
+  const T* wi = w[3];
+  const T* wip = w[4];
+  T WL[5], WR[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    if constexpr (S) {
+      WL[q] = T(0.5) * (wi[q] + wim[q]) - (sc[q] - sm[q]) / T(6);
+      WR[q] = T(0.5) * (wip[q] + wi[q]) - (sp[q] - sc[q]) / T(6);
+    } else {
+      WL[q] = T(0.5) * (wi[q] + wim[q]) - (sc[q] - sm[q]) * T(1.0 / 6.0);
+      WR[q] = T(0.5) * (wip[q] + wi[q]) - (sp[q] - sc[q]) * T(1.0 / 6.0);
+    }
+  }
+  // contact discontinuity steepening of the density
+  {
+    T eta = T(0);
+    bool steep;
+    if constexpr (S) {
+      const T rjump = xabs(wip[0] - wim[0]) / tmin(wip[0], wim[0]);
+      const T pjump = xabs(wip[4] - wim[4]) / tmin(wip[4], wim[4]);
+      const T dx2 = dx * dx;
+      const T d2m = (wi[0] - T(2) * wim[0] + w[1][0]) / (T(6) * dx2);
+      const T d2p = (w[5][0] - T(2) * wip[0] + wi[0]) / (T(6) * dx2);
+      steep = rjump > T(0.01) && pjump < T(0.1) * g.gamma * rjump && d2m * d2p < T(0);
+      if (steep) {
+        const T eta_t = -((d2p - d2m) * dx2) / (wip[0] - wim[0]);
+        eta = tmax(T(0), tmin(T(20) * eta_t - T(1), T(1)));
+      }
+    } else {
+      const T dr = xabs(wip[0] - wim[0]), mr = vmin<S>(wip[0], wim[0]);
+      const T dp = xabs(wip[4] - wim[4]), mp = vmin<S>(wip[4], wim[4]);
+      const T e2m = wi[0] - T(2) * wim[0] + w[1][0];
+      const T e2p = w[5][0] - T(2) * wip[0] + wi[0];
+      steep = lt<S>(T(0.01) * mr, dr) && lt<S>(dp * mr, T(0.1) * g.gamma * dr * mp) &&
+              neg<S>(e2m * e2p);
+      if (steep) {
+        const T eta_t = -nr_div(e2p - e2m, T(6) * (wip[0] - wim[0]));
+        eta = vmax<S>(T(0), vmin<S>(T(20) * eta_t - T(1), T(1)));
+      }
+    }
+    if (steep) {
+      WL[0] = WL[0] * (T(1) - eta) + (wim[0] + T(0.5) * sm[0]) * eta;
+      WR[0] = WR[0] * (T(1) - eta) + (wip[0] - T(0.5) * sp[0]) * eta;
+    }
+  }
+  // shock flattening
+  {
+    T pm[5], pc[5], pp[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      pm[k] = w[k][4];
+      pc[k] = w[k + 1][4];
+      pp[k] = w[k + 2][4];
+    }
+    const T Fm = flatten_tilde<S>(pm, w[1][1], w[3][1]);
+    const T Fc = flatten_tilde<S>(pc, w[2][1], w[4][1]);
+    const T Fp = flatten_tilde<S>(pp, w[3][1], w[5][1]);
+    const T F = neg<S>(wip[4] - wim[4]) ? vmax<S>(Fc, Fp) : vmax<S>(Fc, Fm);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      WL[q] = F * wi[q] + (T(1) - F) * WL[q];
+      WR[q] = F * wi[q] + (T(1) - F) * WR[q];
+    }
+  }
+  // monotonicity
+  T dw[5], w6[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    T L = WL[q], R = WR[q];
+    if (nonpos<S>((R - wi[q]) * (wi[q] - L))) {
+      L = wi[q];
+      R = wi[q];
+    }
+    if (neg<S>((R - L) * (L - (T(3) * wi[q] - T(2) * R)))) L = T(3) * wi[q] - T(2) * R;
+    if (neg<S>((R - L) * ((T(3) * wi[q] - T(2) * L) - R))) R = T(3) * wi[q] - T(2) * L;
+    WL[q] = L;
+    WR[q] = R;
+    dw[q] = R - L;
+    w6[q] = T(6) * (wi[q] - T(0.5) * (L + R));
+  }
+  // characteristic tracing (CW84): boundary values integrated over each wave's
+  // domain of dependence
+  const T u = wi[1];
+  const T lm = u - a, l0 = u, lp = u + a;
+  const T am = dtdx * vmin<S>(lm, T(0)), a0 = dtdx * vmin<S>(l0, T(0)),
+          ap = dtdx * vmin<S>(lp, T(0));
+  const T bm = dtdx * vmax<S>(lm, T(0)), b0 = dtdx * vmax<S>(l0, T(0)),
+          bp = dtdx * vmax<S>(lp, T(0));
+  const T c23 = T(2.0 / 3.0);
+  T WLm[5], WL0[5], WLp[5], WRm[5], WR0[5], WRp[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    WLm[q] = WL[q] - T(0.5) * am * (dw[q] + w6[q] * (T(1) + c23 * am));
+    WL0[q] = WL[q] - T(0.5) * a0 * (dw[q] + w6[q] * (T(1) + c23 * a0));
+    WLp[q] = WL[q] - T(0.5) * ap * (dw[q] + w6[q] * (T(1) + c23 * ap));
+    WRm[q] = WR[q] - T(0.5) * bm * (dw[q] - w6[q] * (T(1) - c23 * bm));
+    WR0[q] = WR[q] - T(0.5) * b0 * (dw[q] - w6[q] * (T(1) - c23 * b0));
+    WRp[q] = WR[q] - T(0.5) * bp * (dw[q] - w6[q] * (T(1) - c23 * bp));
+  }
+  // reference states and Lagrangian impedances C = rho a of the reference states
+  T chiLp, chiRm, chiL0, chiR0, CL, CR, irL, irR;
+  if constexpr (S) {
+    const T aL = xsqrt(g.gamma * tmax(WLm[4], T(kPFloor)) / WLm[0]);
+    const T aR = xsqrt(g.gamma * tmax(WRp[4], T(kPFloor)) / WRp[0]);
+    CL = WLm[0] * aL;
+    CR = WRp[0] * aR;
+    chiLp = -(T(1) / (T(2) * CL)) * ((WLm[1] - WLp[1]) + (WLm[4] - WLp[4]) / CL);
+    chiRm = (T(1) / (T(2) * CR)) * ((WRp[1] - WRm[1]) - (WRp[4] - WRm[4]) / CR);
+    chiL0 = (WLm[4] - WL0[4]) / (CL * CL) + T(1) / WLm[0] - T(1) / WL0[0];
+    chiR0 = (WRp[4] - WR0[4]) / (CR * CR) + T(1) / WRp[0] - T(1) / WR0[0];
+    irL = T(1) / WLm[0];
+    irR = T(1) / WRp[0];
+  } else {
+    // C = sqrt(gamma p rho): one reciprocal square root gives C and 1/C
+    const T xL = g.gamma * vmax<S>(WLm[4], T(kPFloor)) * WLm[0];
+    const T xR = g.gamma * vmax<S>(WRp[4], T(kPFloor)) * WRp[0];
+    const T iCL = nr_rsqrt(xL), iCR = nr_rsqrt(xR);
+    CL = xL * iCL;
+    CR = xR * iCR;
+    irL = nr_rcp(WLm[0]);
+    irR = nr_rcp(WRp[0]);
+    chiLp = -T(0.5) * iCL * ((WLm[1] - WLp[1]) + (WLm[4] - WLp[4]) * iCL);
+    chiRm = T(0.5) * iCR * ((WRp[1] - WRm[1]) - (WRp[4] - WRm[4]) * iCR);
+    chiL0 = (WLm[4] - WL0[4]) * (iCL * iCL) + irL - nr_rcp(WL0[0]);
+    chiR0 = (WRp[4] - WR0[4]) * (iCR * iCR) + irR - nr_rcp(WR0[0]);
+  }
+  if (pos<S>(l0)) chiL0 = T(0);
+  if (pos<S>(lp)) chiLp = T(0);
+  if (neg<S>(lm)) chiRm = T(0);
+  if (neg<S>(l0)) chiR0 = T(0);
+  if constexpr (S) {
+    WsL[0] = T(1) / (T(1) / WLm[0] - chiL0 - chiLp);
+    WsR[0] = T(1) / (T(1) / WRp[0] - chiRm - chiR0);
+  } else {
+    WsL[0] = nr_rcp(irL - chiL0 - chiLp);
+    WsR[0] = nr_rcp(irR - chiRm - chiR0);
+  }
+  WsL[1] = WLm[1] + CL * chiLp;
+  WsL[2] = WL0[2];
+  WsL[3] = WL0[3];
+  WsL[4] = vmax<S>(WLm[4] + CL * CL * chiLp, T(kPFloor));
+  WsR[1] = WRp[1] - CR * chiRm;
+  WsR[2] = WR0[2];
+  WsR[3] = WR0[3];
+  WsR[4] = vmax<S>(WRp[4] + CR * CR * chiRm, T(kPFloor));
+}
+
+// ---------------------------------------------------------------------------
 // App. B.1: exact Riemann solver
 template <typename T>
 struct RSide {

@@ -15,6 +15,7 @@ import numpy as np
 
 HYDRO_BC_PERIODIC, HYDRO_BC_REFLECT, HYDRO_BC_OUTFLOW, HYDRO_BC_INFLOW = 0, 1, 2, 3
 HYDRO_FP64, HYDRO_MIXED, HYDRO_FP64_STRICT = 0, 1, 2
+HYDRO_RECON_PPMC, HYDRO_RECON_PPMP, HYDRO_RECON_PLMC, HYDRO_RECON_PLMP, HYDRO_RECON_PCM = range(5)
 ERRORS = {0: "HYDRO_OK", -1: "HYDRO_EINVAL", -2: "HYDRO_ENOMEM", -3: "HYDRO_ECUDA",
           -4: "HYDRO_ENONPHYS", -5: "HYDRO_ENEWTON", -6: "HYDRO_ENOSTATE"}
 
@@ -30,7 +31,8 @@ EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_precision", "hydro_set_s
            "hydro_batch_init", "hydro_batch_set_inflow", "hydro_batch_set_precision",
            "hydro_batch_set_stream", "hydro_batch_set_state", "hydro_batch_get_state",
            "hydro_batch_step", "hydro_batch_autotune", "hydro_batch_last_error",
-           "hydro_batch_cuda_error_string", "hydro_batch_free", "hydro_check_conversions")
+           "hydro_batch_cuda_error_string", "hydro_batch_free", "hydro_check_conversions",
+           "hydro_set_reconstruction", "hydro_batch_set_reconstruction")
 STAGES = ("prims", "set_dt", "slopes", "ppmc", "riemann1", "riemann2", "update")
 
 _lib = None
@@ -85,6 +87,8 @@ def load():
     L.hydro_batch_cuda_error_string.restype = ctypes.c_char_p
     L.hydro_batch_free.argtypes = [vp]
     L.hydro_check_conversions.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), vp]
+    L.hydro_set_reconstruction.argtypes = [vp, ctypes.c_int]
+    L.hydro_batch_set_reconstruction.argtypes = [vp, ctypes.c_int]
     _lib = L
     return L
 
@@ -113,7 +117,8 @@ def _buffer(u, shape, writable):
 class Grid:
     """One grid advanced by the CUDA CTU step (see include/hydro.h)."""
 
-    def __init__(self, nx, ny, nz, dx, gamma, bc, precision=HYDRO_FP64, stream=None):
+    def __init__(self, nx, ny, nz, dx, gamma, bc, precision=HYDRO_FP64, stream=None,
+                 recon=HYDRO_RECON_PPMC):
         L = load()
         self._L = L
         h = ctypes.c_void_p()
@@ -126,6 +131,8 @@ class Grid:
         self.n = (nx, ny, nz)
         if stream is not None:
             self.set_stream(stream)
+        if recon != HYDRO_RECON_PPMC:
+            self.set_reconstruction(recon)
         if precision != HYDRO_FP64:
             self.set_precision(precision)
 
@@ -153,6 +160,9 @@ class Grid:
 
     def set_precision(self, mode):
         self._check(self._L.hydro_set_precision(self.h, int(mode)), "set_precision")
+
+    def set_reconstruction(self, recon):
+        self._check(self._L.hydro_set_reconstruction(self.h, int(recon)), "set_reconstruction")
 
     def set_stream(self, stream):
         """Order this grid's work on a stream: a torch.cuda.Stream, a raw
@@ -215,10 +225,10 @@ class Grid:
 
 
 def run(u0, dx, gamma, bc, nsteps=None, cfl=0.3, t_end=None, inflow=None, precision=HYDRO_FP64,
-        max_steps=100000):
+        max_steps=100000, recon=HYDRO_RECON_PPMC):
     """Advance ``u0`` on the GPU; returns ``(u, t, nsteps)`` (host numpy state)."""
     _, nz, ny, nx = u0.shape
-    g = Grid(nx, ny, nz, dx, gamma, bc, precision=precision)
+    g = Grid(nx, ny, nz, dx, gamma, bc, precision=precision, recon=recon)
     try:
         if inflow:
             for face, prim in inflow.items():
@@ -293,7 +303,7 @@ def check_conversions():
 class Batch:
     """Independent grids of uneven sizes advanced together (see include/hydro.h)."""
 
-    def __init__(self, grids, precision=HYDRO_FP64):
+    def __init__(self, grids, precision=HYDRO_FP64, recon=HYDRO_RECON_PPMC):
         """grids: list of dicts with "u" [5, nz, ny, nx], "dx", "gamma", "bc" and
         optionally "inflow" {face: prim}."""
         L = load()
@@ -317,6 +327,8 @@ class Batch:
             raise HydroError(rc, "hydro_batch_init")
         self.h = h
         self.n = n
+        if recon != HYDRO_RECON_PPMC:
+            self._check(L.hydro_batch_set_reconstruction(h, int(recon)), "set_reconstruction")
         if precision != HYDRO_FP64:
             self._check(L.hydro_batch_set_precision(h, int(precision)), "set_precision")
         for i, w in enumerate(grids):

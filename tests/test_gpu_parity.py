@@ -58,13 +58,13 @@ def rel_err(g, o, floor=1e-12):
     return np.abs(np.asarray(g) - o) / den
 
 
-def run_both(w, nsteps, cfl=0.3, precision=hydro.HYDRO_FP64):
+def run_both(w, nsteps, cfl=0.3, precision=hydro.HYDRO_FP64, recon=hydro.HYDRO_RECON_PPMC):
     inflow = w.get("inflow")
     uo, to, no, fl = oracle.run(w["u"], w["dx"], w["gamma"], w["bc"], nsteps=nsteps, cfl=cfl,
-                                inflow=inflow)
+                                inflow=inflow, recon=recon)
     assert fl == 0
     ug, tg, ng = hydro.run(w["u"], w["dx"], w["gamma"], w["bc"], nsteps=nsteps, cfl=cfl,
-                           inflow=inflow, precision=precision)
+                           inflow=inflow, precision=precision, recon=recon)
     return ug, uo, tg, to
 
 
@@ -109,10 +109,10 @@ def test_ppmc_kernel_matches_oracle():
         assert np.all(np.abs(dR.cpu().numpy().T - Ro) <= 1e-12 * scale)
 
 
-@pytest.mark.parametrize("mode", MODES, ids=lambda m: MODE_ID[m])
-@pytest.mark.parametrize("case", ["sedov32", "smooth24", "tube3d", "ragged", "twod", "inflow",
-                                  "sod512"])
-def test_step_parity_10_steps(case, mode):
+CASES = ["sedov32", "smooth24", "tube3d", "ragged", "twod", "inflow", "sod512"]
+
+
+def make_case(case):
     if case == "sedov32":
         w = W.sedov(32)
     elif case == "sod512":
@@ -143,12 +143,51 @@ def test_step_parity_10_steps(case, mode):
         rho[(xx ** 2 + yy ** 2 + zz ** 2) < 25] = 10.0
         w = dict(u=W.prim_to_cons(rho, vx, 0.0, 0.0, p, 5 / 3), dx=1 / 16, gamma=5 / 3,
                  bc=[I_, O, P, P, P, P], inflow={0: (rho2, u2, 0.0, 0.0, p2)})
-    ug, uo, tg, to = run_both(w, 10, precision=mode)
+    return w
+
+
+def check_parity(case, mode, recon):
+    w = make_case(case)
+    ug, uo, tg, to = run_both(w, 10, precision=mode, recon=recon)
     assert tg == pytest.approx(to, rel=1e-12)
     err = rel_err(ug, uo, FLOOR[mode])
     absd = np.abs(ug - uo).reshape(5, -1).max(axis=1) / np.maximum(var_scale(uo), 1e-300)
-    print("%s %s: max rel %.3e, max |diff|/scale %s" % (case, MODE_ID[mode], err.max(), absd))
+    print("%s %s recon %d: max rel %.3e, max |diff|/scale %s" % (case, MODE_ID[mode], recon,
+                                                                err.max(), absd))
     assert err.max() <= TOL, (case, err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+@pytest.mark.parametrize("mode", MODES, ids=lambda m: MODE_ID[m])
+@pytest.mark.parametrize("case", CASES)
+def test_step_parity_10_steps(case, mode):
+    check_parity(case, mode, hydro.HYDRO_RECON_PPMC)
+
+
+RECONS = {"ppmp": hydro.HYDRO_RECON_PPMP, "plmc": hydro.HYDRO_RECON_PLMC,
+          "plmp": hydro.HYDRO_RECON_PLMP, "pcm": hydro.HYDRO_RECON_PCM}
+
+
+@pytest.mark.parametrize("mode", MODES, ids=lambda m: MODE_ID[m])
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("recon", list(RECONS), ids=list(RECONS))
+def test_other_reconstructions_parity_10_steps(recon, case, mode):
+    """The other reconstructions (Sec. 2.2.1, App. A) against the oracle, with
+    the tolerance of the PPMC path."""
+    check_parity(case, mode, RECONS[recon])
+
+
+def test_reconstruction_mode_errors():
+    g = hydro.Grid(8, 8, 8, 0.1, 1.4, [P] * 6)
+    with pytest.raises(hydro.HydroError):
+        g.set_reconstruction(7)
+    g.set_reconstruction(hydro.HYDRO_RECON_PPMP)
+    with pytest.raises(hydro.HydroError):  # mixed precision runs PPMC only
+        g.set_precision(hydro.HYDRO_MIXED)
+    g.set_reconstruction(hydro.HYDRO_RECON_PPMC)
+    g.set_precision(hydro.HYDRO_MIXED)
+    with pytest.raises(hydro.HydroError):
+        g.set_reconstruction(hydro.HYDRO_RECON_PLMC)
+    g.close()
 
 
 def test_sod_config_to_t02():

@@ -24,6 +24,7 @@ FLAG_NONPHYS = 2
 
 BC_PERIODIC, BC_REFLECT, BC_OUTFLOW, BC_INFLOW = 0, 1, 2, 3
 RECON_PPMC, RECON_PPMP, RECON_PLMC, RECON_PLMP, RECON_PCM = 0, 1, 2, 3, 4
+SOLVER_EXACT, SOLVER_ROE = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -44,6 +45,8 @@ def lib():
         L.oracle_free.argtypes = [ctypes.c_void_p]
         L.oracle_set_inflow.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
         L.oracle_set_recon.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.oracle_set_solver.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.oracle_riemann_roe.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, _dp]
         L.oracle_reconstruct.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, _dp, _dp]
         L.oracle_set_state.argtypes = [ctypes.c_void_p, _dp]
@@ -108,6 +111,20 @@ def ppmc(w, dtdx, gamma):
     return WsL, WsR
 
 
+def riemann_roe(UL, UR, gamma, etaH=None):
+    """Roe solver with the HLLE fallback on conserved pairs ``[n, 5]`` (rho,
+    normal momentum, two transverse momenta, E); ``etaH [n]`` the H correction
+    (None: none).  Returns the fluxes ``[n, 5]``."""
+    UL = np.ascontiguousarray(UL, dtype=np.float64).reshape(-1, 5)
+    UR = np.ascontiguousarray(UR, dtype=np.float64).reshape(-1, 5)
+    n = UL.shape[0]
+    F = np.zeros((n, 5))
+    e = None if etaH is None else np.ascontiguousarray(etaH, dtype=np.float64).reshape(-1)
+    lib().oracle_riemann_roe(n, _ptr(UL), _ptr(UR), None if e is None else _ptr(e), float(gamma),
+                             _ptr(F))
+    return F
+
+
 def reconstruct(recon, w, dtdx, dx, gamma):
     """Reconstruction ``recon`` (RECON_*) on seven-cell primitive stencils
     ``w [n, 7 cells, 5]`` (cells i-3..i+3; rho, normal velocity, two transverse
@@ -153,6 +170,12 @@ class Grid:
         RECON_PLMP or RECON_PCM."""
         if lib().oracle_set_recon(self.h, int(recon)) != 0:
             raise ValueError("unknown reconstruction %r" % (recon,))
+
+    def set_solver(self, solver):
+        """Riemann solver (Sec. 2.2.2): SOLVER_EXACT (default) or SOLVER_ROE (Roe with
+        the HLLE fallback; H correction in the second set of solves)."""
+        if lib().oracle_set_solver(self.h, int(solver)) != 0:
+            raise ValueError("unknown Riemann solver %r" % (solver,))
 
     def set_state(self, u):
         u = np.ascontiguousarray(u, dtype=np.float64)
@@ -217,7 +240,7 @@ class Grid:
 
 
 def run(u0, dx, gamma, bc, nsteps=None, cfl=0.3, t_end=None, inflow=None, max_steps=100000,
-        recon=RECON_PPMC):
+        recon=RECON_PPMC, solver=SOLVER_EXACT):
     """Advance ``u0`` with the oracle; returns ``(u, t, nsteps, flags)``.
 
     Either ``nsteps`` CFL steps, or steps until ``t_end`` with the last step
@@ -226,6 +249,7 @@ def run(u0, dx, gamma, bc, nsteps=None, cfl=0.3, t_end=None, inflow=None, max_st
     _, nz, ny, nx = u0.shape
     g = Grid(nx, ny, nz, dx, gamma, bc)
     g.set_recon(recon)
+    g.set_solver(solver)
     if inflow:
         for face, prim in inflow.items():
             g.set_inflow(face, prim)

@@ -699,8 +699,131 @@ void ppmp_cell(const R w[7][5], R dtdx, R dx, const Gas& g, R WsL[5], R WsR[5]) 
 }
 
 // ---------------------------------------------------------------------------
+// Roe solver with the HLLE fallback (Sec. 2.2.2, App. B.2) on conserved input
+// states in sweep order.  etaH >= 0 is the H correction (App. C): every |lambda|
+// of the Roe coefficients is replaced by max(|lambda|, etaH); 0 leaves them.
+// Readings: the printed "C_3 2~" of s_3 is C_3 w~; "negative" density or
+// pressure of an intermediate state means < 0; a Roe average with
+// (gamma-1)(H~ - V~^2/2) <= 0 has no sound speed and takes the HLLE flux.
+template <class R>
+void roe_hlle_flux(const R UL[5], const R UR[5], const R WL[5], const R WR[5], const R FL[5],
+                   const R FR[5], R lm, R lp, const Gas& g, R F[5]) {
+  const R aL = sqrt(R(g.gamma) * WL[4] / WL[0]);
+  const R aR = sqrt(R(g.gamma) * WR[4] / WR[0]);
+  const R bm = mn(mn(lm, WL[1] - aL), R(0.0));
+  const R bp = mx(mx(lp, WR[1] + aR), R(0.0));
+  for (int q = 0; q < 5; ++q) {
+    const R FLh = FL[q] - bm * UL[q];
+    const R FRh = FR[q] - bp * UR[q];
+    F[q] = R(0.5) * ((FLh + FRh) + (FLh - FRh) * ((bp + bm) / (bp - bm)));
+  }
+}
+
+template <class R>
+bool negative_state(const R U[5], const Gas& g) {
+  const R p = R(g.gm1) * (U[4] - R(0.5) * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0]);
+  return U[0] < R(0.0) || p < R(0.0);
+}
+
+template <class R>
+int riemann_roe_cons(const R UL[5], const R UR[5], const Gas& g, R etaH, R F[5]) {
+  R WL[5], WR[5], FL[5], FR[5];
+  cons_to_prim(UL, g, WL);
+  cons_to_prim(UR, g, WR);
+  euler_flux(WL, g, FL);
+  euler_flux(WR, g, FR);
+  // Roe averages (weights sqrt(rho)); enthalpy H = (E + p)/rho
+  const R sL = sqrt(WL[0]), sR = sqrt(WR[0]);
+  const R HL = (UL[4] + WL[4]) / WL[0];
+  const R HR = (UR[4] + WR[4]) / WR[0];
+  const R u = (sL * WL[1] + sR * WR[1]) / (sL + sR);
+  const R v = (sL * WL[2] + sR * WR[2]) / (sL + sR);
+  const R w = (sL * WL[3] + sR * WR[3]) / (sL + sR);
+  const R H = (sL * HL + sR * HR) / (sL + sR);
+  const R V2 = u * u + v * v + w * w;
+  const R a2 = R(g.gm1) * (H - R(0.5) * V2);
+  if (!(a2 > R(0.0))) {
+    roe_hlle_flux(UL, UR, WL, WR, FL, FR, u, u, g, F);
+    return 0;
+  }
+  const R a = sqrt(a2);
+  const R lm = u - a, l0 = u, lp = u + a;
+  if (lm >= R(0.0)) {  // supersonic to the right
+    for (int q = 0; q < 5; ++q) F[q] = FL[q];
+    return 0;
+  }
+  if (lp <= R(0.0)) {  // supersonic to the left
+    for (int q = 0; q < 5; ++q) F[q] = FR[q];
+    return 0;
+  }
+  R dU[5];
+  for (int q = 0; q < 5; ++q) dU[q] = UR[q] - UL[q];
+  const R gp = R(g.gm1);
+  const R Na = R(1.0) / (R(2.0) * a2);
+  // wave strengths (projection on the left eigenvectors)
+  const R xi0 = dU[0] * Na * (R(0.5) * gp * V2 + u * a) - dU[1] * Na * (gp * u + a) -
+                dU[2] * Na * gp * v - dU[3] * Na * gp * w + dU[4] * Na * gp;
+  const R xi1 = -dU[0] * v + dU[2];
+  const R xi2 = -dU[0] * w + dU[3];
+  const R xi3 = dU[0] * (R(1.0) - Na * gp * V2) + dU[1] * gp * u / a2 + dU[2] * gp * v / a2 +
+                dU[3] * gp * w / a2 - dU[4] * gp / a2;
+  const R xi4 = dU[0] * Na * (R(0.5) * gp * V2 - u * a) - dU[1] * Na * (gp * u - a) -
+                dU[2] * Na * gp * v - dU[3] * Na * gp * w + dU[4] * Na * gp;
+  // coefficients C = xi |lambda| (H correction: |lambda| -> max(|lambda|, etaH))
+  const R alm = mx(fabs(lm), etaH), al0 = mx(fabs(l0), etaH), alp = mx(fabs(lp), etaH);
+  const R C0 = xi0 * alm, C1 = xi1 * al0, C2 = xi2 * al0, C3 = xi3 * al0, C4 = xi4 * alp;
+  R s[5];
+  s[0] = C0 + C3 + C4;
+  s[1] = C0 * (u - a) + C3 * u + C4 * (u + a);
+  s[2] = C0 * v + C1 + C3 * v + C4 * v;
+  s[3] = C0 * w + C2 + C3 * w + C4 * w;
+  s[4] = C0 * (H - u * a) + C1 * v + C2 * w + R(0.5) * C3 * V2 + C4 * (H + u * a);
+  for (int q = 0; q < 5; ++q) F[q] = R(0.5) * (FL[q] + FR[q] - s[q]);
+  // intermediate states: negative density or pressure -> HLLE flux
+  bool fail = false;
+  R UmL[5];
+  UmL[0] = UL[0] + xi0;
+  UmL[1] = UL[1] + xi0 * (u - a);
+  UmL[2] = UL[2] + xi0 * v;
+  UmL[3] = UL[3] + xi0 * w;
+  UmL[4] = UL[4] + xi0 * (H - u * a);
+  if (l0 > lm && negative_state(UmL, g)) fail = true;
+  if (!fail && lp > l0) {
+    R UmR[5];
+    UmR[0] = UmL[0] + xi3;
+    UmR[1] = UmL[1] + xi3 * u;
+    UmR[2] = UmL[2] + xi1 + xi3 * v;
+    UmR[3] = UmL[3] + xi2 + xi3 * w;
+    UmR[4] = UmL[4] + xi1 * v + xi2 * w + R(0.5) * xi3 * V2;
+    if (negative_state(UmR, g)) fail = true;
+  }
+  if (fail) roe_hlle_flux(UL, UR, WL, WR, FL, FR, lm, lp, g, F);
+  return 0;
+}
+
+// H-correction quantity of a face (App. C): half the largest jump of a
+// characteristic speed between the right and the left input state,
+// max(|(u_R + a_R) - (u_L + a_L)|, |(u_R - a_R) - (u_L - a_L)|) / 2.  The paper
+// prints only the u + a term; the method it cites (Sanders et al. 1998) takes
+// the maximum over the characteristic families, and the u + a term alone is
+// not invariant under reflection (a mirrored flow would get different
+// dissipation).  The jump of u is never the largest.
+template <class R>
+R h_eta(const R UL[5], const R UR[5], const Gas& g) {
+  R WL[5], WR[5];
+  cons_to_prim(UL, g, WL);
+  cons_to_prim(UR, g, WR);
+  const R aL = sqrt(R(g.gamma) * WL[4] / WL[0]);
+  const R aR = sqrt(R(g.gamma) * WR[4] / WR[0]);
+  return R(0.5) * mx(fabs((WR[1] + aR) - (WL[1] + aL)), fabs((WR[1] - aR) - (WL[1] - aL)));
+}
+
+// ---------------------------------------------------------------------------
 // Reconstructions (Sec. 2.2.1): PPMC is the method of the benchmarked path.
 enum { RECON_PPMC = 0, RECON_PPMP = 1, RECON_PLMC = 2, RECON_PLMP = 3, RECON_PCM = 4 };
+// Riemann solvers (Sec. 2.2.2): exact (the benchmarked path) or Roe with the
+// HLLE fallback and, in the second set, the H correction (App. B.2, C)
+enum { SOLVER_EXACT = 0, SOLVER_ROE = 1 };
 
 // ---------------------------------------------------------------------------
 // Grid: conserved variables as five padded planes [5][N2][N1][N0], x fastest.
@@ -711,6 +834,7 @@ struct Grid {
   int bc[6];
   double inflow_prim[6][5];
   int recon = RECON_PPMC;  // reconstruction of App. A / Sec. 2.2.1
+  int solver = SOLVER_EXACT;
   size_t ncell;
   std::vector<R> u;
 
@@ -834,13 +958,16 @@ int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
   for (int d = 0; d < 3; ++d) active[d] = G.n[d] > 1;
 
   // face arrays, indexed by the padded index of the cell right of the face
-  std::vector<R> UL[3], UR[3], F1[3], F2[3];
+  // (eta: the H-correction quantity of each face, Roe solver only)
+  const bool roe = G.solver == SOLVER_ROE;
+  std::vector<R> UL[3], UR[3], F1[3], F2[3], eta[3];
   for (int d = 0; d < 3; ++d) {
     if (!active[d]) continue;
     UL[d].assign(5 * nc, R(0.0));
     UR[d].assign(5 * nc, R(0.0));
     F1[d].assign(5 * nc, R(0.0));
     F2[d].assign(5 * nc, R(0.0));
+    if (roe) eta[d].assign(nc, R(0.0));
   }
 
   // steps 1-2: reconstruction and the first set of Riemann solves, one axis at
@@ -925,7 +1052,12 @@ int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
           }
           set_stage((R*)nullptr, 2);
           add_units((R*)nullptr, 2);
-          fl |= riemann_exact_cons(ULr, URr, g, Fr);
+          if (roe) {
+            fl |= riemann_roe_cons(ULr, URr, g, R(0.0), Fr);
+            eta[d][f] = h_eta(ULr, URr, g);
+          } else {
+            fl |= riemann_exact_cons(ULr, URr, g, Fr);
+          }
           F1[d][0 * nc + f] = Fr[0];
           F1[d][4 * nc + f] = Fr[4];
           for (int s = 0; s < 3; ++s) F1[d][(1 + P[s]) * nc + f] = Fr[1 + s];
@@ -978,7 +1110,23 @@ int ctu_step(Grid<R>& G, double dt_in, bool threaded) {
             ULr[1 + s] = UhL[1 + P[s]];
             URr[1 + s] = UhR[1 + P[s]];
           }
-          fl |= riemann_exact_cons(ULr, URr, g, Fr);
+          if (roe) {
+            // H correction (App. C): the largest eta of this face and of the
+            // transverse faces of the two cells it separates (nine in 3D)
+            R etaH = eta[d][f];
+            for (int m = 0; m < 2; ++m) {
+              const int t = tt[m];
+              if (!active[t]) continue;
+              const size_t st = G.stride(t);
+              etaH = mx(etaH, eta[t][cl]);
+              etaH = mx(etaH, eta[t][cl + st]);
+              etaH = mx(etaH, eta[t][cr]);
+              etaH = mx(etaH, eta[t][cr + st]);
+            }
+            fl |= riemann_roe_cons(ULr, URr, g, etaH, Fr);
+          } else {
+            fl |= riemann_exact_cons(ULr, URr, g, Fr);
+          }
           F2[d][0 * nc + f] = Fr[0];
           F2[d][4 * nc + f] = Fr[4];
           for (int s = 0; s < 3; ++s) F2[d][(1 + P[s]) * nc + f] = Fr[1 + s];
@@ -1038,6 +1186,14 @@ void oracle_free(void* h) { delete static_cast<Handle*>(h); }
 int oracle_set_inflow(void* h, int face, const double* prim) {
   if (!h || face < 0 || face > 5) return -1;
   for (int q = 0; q < 5; ++q) static_cast<Handle*>(h)->G.inflow_prim[face][q] = prim[q];
+  return 0;
+}
+
+// Riemann solver: 0 exact (default), 1 Roe (HLLE fallback, H correction in the
+// second set)
+int oracle_set_solver(void* h, int solver) {
+  if (!h || solver < SOLVER_EXACT || solver > SOLVER_ROE) return -1;
+  static_cast<Handle*>(h)->G.solver = solver;
   return 0;
 }
 
@@ -1167,6 +1323,16 @@ int oracle_reconstruct(int n, int recon, const double* w, double dtdx, double dx
   return 0;
 }
 
+// Roe solver (with the HLLE fallback) on n interfaces: conserved states [n][5]
+// in sweep order, etaH [n] (0: no H correction); fluxes F [n][5].
+int oracle_riemann_roe(int n, const double* UL, const double* UR, const double* etaH,
+                       double gamma, double* F) {
+  const Gas g(gamma);
+  for (int i = 0; i < n; ++i)
+    riemann_roe_cons(UL + 5 * i, UR + 5 * i, g, etaH ? etaH[i] : 0.0, F + 5 * i);
+  return 0;
+}
+
 // Algorithmic operation count of one CTU step with the given dt on the current
 // state (the state itself is not changed).  counts = {add/sub, mul, div, sqrt,
 // pow, compare/min/max/abs}; returns the step's status flags.
@@ -1176,6 +1342,7 @@ int oracle_count_step(void* h, double dt, double* counts) {
   for (int f = 0; f < 6; ++f)
     for (int q = 0; q < 5; ++q) G.inflow_prim[f][q] = G0.inflow_prim[f][q];
   G.recon = G0.recon;
+  G.solver = G0.solver;
   for (size_t i = 0; i < G0.u.size(); ++i) G.u[i] = CR(G0.u[i]);
   g_ops = OpCount();
   for (int k = 0; k < kStages; ++k) {
@@ -1204,6 +1371,7 @@ int oracle_count_step_stages(void* h, double dt, double* counts, double* units) 
   for (int f = 0; f < 6; ++f)
     for (int q = 0; q < 5; ++q) G.inflow_prim[f][q] = G0.inflow_prim[f][q];
   G.recon = G0.recon;
+  G.solver = G0.solver;
   for (size_t i = 0; i < G0.u.size(); ++i) G.u[i] = CR(G0.u[i]);
   g_ops = OpCount();
   for (int k = 0; k < kStages; ++k) {

@@ -49,15 +49,16 @@ PEAK_SOURCE = "152 SMs x 2070 MHz x 2 FP64 FMA/clk/SM x 2 flop/FMA (unit counts 
 # riemann2).  The benchmark never runs the oracle for these.
 ALGORITHMIC_FLOPS = {
     "batched": {"ppmc": 406.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 81.0, "update": 45.0},
-    "batched/pcm": {"ppmc": 0.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 0.0, "update": 45.0},
-    "batched/plmc": {"ppmc": 108.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 81.0, "update": 45.0},
-    "batched/plmp": {"ppmc": 107.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 25.0, "update": 45.0},
-    "batched/ppmp": {"ppmc": 511.042, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 25.0, "update": 45.0},
     "sedov": {"ppmc": 406.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 81.0, "update": 45.0},
     "sedov/pcm": {"ppmc": 0.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 0.0, "update": 45.0},
+    "sedov/pcm+roe": {"ppmc": 0.0, "prims": 22.752, "riemann1": 305.0, "riemann2": 328.0, "slopes": 0.0, "update": 45.0},
     "sedov/plmc": {"ppmc": 108.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 81.0, "update": 45.0},
+    "sedov/plmc+roe": {"ppmc": 108.0, "prims": 22.752, "riemann1": 305.0, "riemann2": 328.0, "slopes": 81.0, "update": 45.0},
     "sedov/plmp": {"ppmc": 107.0, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 25.0, "update": 45.0},
+    "sedov/plmp+roe": {"ppmc": 107.0, "prims": 22.752, "riemann1": 305.0, "riemann2": 328.0, "slopes": 25.0, "update": 45.0},
+    "sedov/ppmc+roe": {"ppmc": 406.0, "prims": 22.752, "riemann1": 305.0, "riemann2": 328.0, "slopes": 81.0, "update": 45.0},
     "sedov/ppmp": {"ppmc": 511.042, "prims": 22.752, "riemann1": 136.078, "riemann2": 196.262, "slopes": 25.0, "update": 45.0},
+    "sedov/ppmp+roe": {"ppmc": 511.042, "prims": 22.752, "riemann1": 305.0, "riemann2": 328.0, "slopes": 25.0, "update": 45.0},
     "shock_cloud": {"ppmc": 413.0, "prims": 22.752, "riemann1": 135.667, "riemann2": 195.667, "slopes": 81.0, "update": 45.0},
     "sod512": {"ppmc": 406.0, "prims": 28.742, "riemann1": 136.125, "riemann2": 136.125, "slopes": 81.0, "update": 15.0},
     "turbulence": {"ppmc": 423.374, "prims": 22.752, "riemann1": 140.154, "riemann2": 200.574, "slopes": 91.922, "update": 45.0},
@@ -214,16 +215,18 @@ def dist_env():
 
 
 RECON_CODES = {"ppmc": 0, "ppmp": 1, "plmc": 2, "plmp": 3, "pcm": 4}
+SOLVER_CODES = {"exact": 0, "roe": 1}
 
 
-def flops_table(key, recon="ppmc"):
-    """Algorithmic FP64 flops per unit for a workload key (and reconstruction)."""
+def flops_table(key, recon="ppmc", solver="exact"):
+    """Algorithmic FP64 flops per unit for a workload key, reconstruction and
+    Riemann solver (the other methods are counted on the Sedov sample)."""
     if key.startswith("sedov"):
         key = "sedov"
     elif key.startswith("batched"):
         key = "batched"
-    if recon != "ppmc":
-        key = "%s/%s" % (key, recon)
+    if recon != "ppmc" or solver != "exact":
+        key = "sedov/%s" % recon + ("+roe" if solver == "roe" else "")
     return ALGORITHMIC_FLOPS[key], key
 
 
@@ -271,6 +274,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--recon", default="ppmc", choices=list(RECON_CODES),
                     help="reconstruction (Sec. 2.2.1): ppmc (default), ppmp, plmc, plmp, pcm")
+    ap.add_argument("--solver", default="exact", choices=["exact", "roe"],
+                    help="Riemann solver (Sec. 2.2.2): exact (default) or roe (HLLE fallback, "
+                         "H correction)")
     ap.add_argument("--cfl", type=float, default=0.3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -300,7 +306,7 @@ def main():
     prec = hydro.HYDRO_FP64 if args.precision == "fp64" else hydro.HYDRO_MIXED
     stream = torch.cuda.current_stream()
     g = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], precision=prec, stream=stream,
-                   recon=RECON_CODES[args.recon])
+                   recon=RECON_CODES[args.recon], solver=SOLVER_CODES[args.solver])
     for face, prim in (w.get("inflow") or {}).items():
         g.set_inflow(face, prim)
     u_host = torch.from_numpy(w["u"]).pin_memory()
@@ -372,7 +378,7 @@ def main():
     dms, dl, dunits = stages[dom]
     active = sum(1 for n in (nx, ny, nz) if n > 1)
     if args.precision == "fp64":
-        table, tkey = flops_table(w["key"], args.recon)
+        table, tkey = flops_table(w["key"], args.recon, args.solver)
         per_unit = table[dom]
         src = "algorithmic FP64 flops per unit (oracle/count_ops.py, %s)" % tkey
     else:
@@ -404,7 +410,7 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": single_config(args.workload, args.precision, ws, args.recon),
+        "config": single_config(args.workload, args.precision, ws, args.recon, args.solver),
         "e2e": e2e, "gpu_launches": launches_total, "clocks": clocks, "roofline": roofline,
         "stages": stage_report, "cpu_baseline": cpu,
         "hbm": hbm_report(value / ws, traffic, avg_ms),
@@ -428,7 +434,8 @@ def run_batch(args, w, ws, rank, local):
     ncells = sum(int(np.prod(g["u"].shape[1:])) for g in grids)
     prec = hydro.HYDRO_FP64 if args.precision == "fp64" else hydro.HYDRO_MIXED
     stream = torch.cuda.Stream()
-    b = hydro.Batch(grids, precision=prec, recon=RECON_CODES[args.recon])
+    b = hydro.Batch(grids, precision=prec, recon=RECON_CODES[args.recon],
+                    solver=SOLVER_CODES[args.solver])
     b._check(b._L.hydro_batch_set_stream(b.h, hydro.ctypes.c_void_p(stream.cuda_stream)),
              "set_stream")
     bs, order, tune_ms = b.autotune(use_cache=True)
@@ -682,10 +689,10 @@ def workload_desc(name):
     return WORKLOAD_DESC.get(name, name)
 
 
-def single_config(name, precision, ws, recon="ppmc"):
+def single_config(name, precision, ws, recon="ppmc", solver="exact"):
     nx, ny, nz = workload_shape(name)
     return {"workload": workload_desc(name), "cells": nx * ny * nz, "precision": precision,
-            "reconstruction": recon,
+            "reconstruction": recon, "riemann_solver": solver,
             "parallelism": "replicas" if ws > 1 else "single",
             "l2": "inputs larger than L2 (state %.2f GB, step working set %.1f GB)" % (
                 nx * ny * nz * 40 / 1e9,

@@ -70,6 +70,13 @@ enum { HYDRO_FP64 = 0, HYDRO_MIXED = 1, HYDRO_FP64_STRICT = 2 };
  * HYDRO_RECON_PCM: piecewise constant (Sec. 2.2.1).  PPMP needs three cells on
  * each side of a cell, the others one or two; every mode fits the 4 ghost
  * layers. */
+/* Riemann solver (Sec. 2.2.2).  HYDRO_RIEMANN_EXACT (default): the exact
+ * solver of App. B.1.  HYDRO_RIEMANN_ROE: the Roe solver with the HLLE
+ * fallback for negative intermediate states (App. B.2) in both sets of solves
+ * and the H correction (App. C) in the second; its eta is half the largest
+ * jump of u + a and u - a across a face (the paper prints the u + a term). */
+enum { HYDRO_RIEMANN_EXACT = 0, HYDRO_RIEMANN_ROE = 1 };
+
 enum {
   HYDRO_RECON_PPMC = 0,
   HYDRO_RECON_PPMP = 1,
@@ -163,6 +170,12 @@ int hydro_profile_read(hydro_t h, int nstages, double* ms, long long* launches, 
  * they are rejected (HYDRO_EINVAL), as is an unknown mode. */
 int hydro_set_reconstruction(hydro_t h, int recon);
 
+/* Select the Riemann solver (HYDRO_RIEMANN_*) of the following steps.  The Roe
+ * solver runs in HYDRO_FP64 and HYDRO_FP64_STRICT (HYDRO_EINVAL with
+ * HYDRO_MIXED or an unknown solver); selecting it allocates one plane per
+ * active axis for the H correction (HYDRO_ENOMEM if that fails). */
+int hydro_set_riemann_solver(hydro_t h, int solver);
+
 /* Release the handle and all device memory it owns.  NULL is accepted. */
 void hydro_free(hydro_t h);
 
@@ -206,6 +219,8 @@ int hydro_batch_autotune(hydro_batch_t h, int use_cache, int* block_size, int* o
                          float* ms_per_step);
 /* Reconstruction of every grid of the batch (as hydro_set_reconstruction). */
 int hydro_batch_set_reconstruction(hydro_batch_t h, int recon);
+/* Riemann solver of every grid of the batch (as hydro_set_riemann_solver). */
+int hydro_batch_set_riemann_solver(hydro_batch_t h, int solver);
 int hydro_batch_last_error(hydro_batch_t h);
 const char* hydro_batch_cuda_error_string(hydro_batch_t h);
 void hydro_batch_free(hydro_batch_t h);

@@ -4,7 +4,8 @@ ALGORITHMIC_FLOPS (the benchmark itself never runs the oracle for it):
 
     python oracle/count_ops.py
 
-For each benchmark workload the op-counting build of the CPU oracle runs one
+For each benchmark workload (and, on the Sedov sample, each other
+reconstruction and the Roe solver) the op-counting build of the CPU oracle runs one
 step of a 32^3 sample of the same initial-condition recipe (Sedov: a 32^3 blast
 made the same way; shock-cloud and turbulence: the 32^3 corner block of the
 full field; Sod: the full 512 cells) and counts every add, multiply, divide,
@@ -38,11 +39,12 @@ def sample(name):
     return s, "32^3 corner block of the full field, periodic"
 
 
-def counts(name, cfl=0.3, recon=oracle.RECON_PPMC):
+def counts(name, cfl=0.3, recon=oracle.RECON_PPMC, solver=oracle.SOLVER_EXACT):
     s, desc = sample(name)
     _, nz, ny, nx = s["u"].shape
     g = oracle.Grid(nx, ny, nz, s["dx"], s["gamma"], s["bc"])
     g.set_recon(recon)
+    g.set_solver(solver)
     g.set_state(s["u"])
     st = g.count_step_stages(g.compute_dt(cfl))
     flops = {k: (sum(v["ops"].values()) - v["ops"]["cmp"]) / max(v["units"], 1)
@@ -58,7 +60,9 @@ def main():
               "pcm": oracle.RECON_PCM}
     for rname, r in recons.items():
         out["sedov/" + rname] = counts("sedov", recon=r)
-        out["batched/" + rname] = out["sedov/" + rname]
+    recons["ppmc"] = oracle.RECON_PPMC
+    for rname, r in recons.items():
+        out["sedov/%s+roe" % rname] = counts("sedov", recon=r, solver=oracle.SOLVER_ROE)
     json.dump(out, sys.stdout, indent=1, sort_keys=True)
     sys.stdout.write("\n")
 

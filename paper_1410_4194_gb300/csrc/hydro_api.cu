@@ -24,6 +24,8 @@ struct hydro_s {
   double gamma;
   int precision;
   int recon;
+  int solver;
+  double* eta_buf;  // H-correction planes (one per active axis), allocated for the Roe solver
   int device;
   cudaStream_t stream;
   bool have_state;
@@ -150,13 +152,13 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
       if (!active(G, d)) continue;
       for (int s = kStageSlopes; s <= kStageRiemann1; ++s) {
         if (s == kStageSlopes && h->recon == HYDRO_RECON_PCM) continue;  // no slopes
-        STAGE(h, s, d, fp64_stage_strict(G, B, h->recon, s, d, h->gamma, st));
+        STAGE(h, s, d, fp64_stage_strict(G, B, h->recon, h->solver, s, d, h->gamma, st));
       }
     }
     for (int d = 0; d < 3; ++d)
       if (active(G, d))
         STAGE(h, kStageRiemann2, d,
-              fp64_stage_strict(G, B, h->recon, kStageRiemann2, d, h->gamma, st));
+              fp64_stage_strict(G, B, h->recon, h->solver, kStageRiemann2, d, h->gamma, st));
     STAGE(h, kStageUpdate, 0, fp64_update(G, B, st));
     return HYDRO_OK;
   }
@@ -170,14 +172,16 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
     for (int s = kStageSlopes; s <= kStageRiemann1; ++s) {
       if (s == kStageSlopes && h->recon == HYDRO_RECON_PCM) continue;  // no slopes
       const int k = launch_kind(s, d);
-      STAGE(h, s, d, batch_stage(one_grid(h, k), P, h->recon, s, d, 256, h->blocks[k], st));
+      STAGE(h, s, d,
+            batch_stage(one_grid(h, k), P, h->recon, h->solver, s, d, 256, h->blocks[k], st));
     }
   }
   for (int d = 0; d < 3; ++d) {
     if (!active(G, d)) continue;
     const int k = launch_kind(kStageRiemann2, d);
     STAGE(h, kStageRiemann2, d,
-          batch_stage(one_grid(h, k), P, h->recon, kStageRiemann2, d, 256, h->blocks[k], st));
+          batch_stage(one_grid(h, k), P, h->recon, h->solver, kStageRiemann2, d, 256,
+                      h->blocks[k], st));
   }
   STAGE(h, kStageUpdate, 0, batch_update(one_grid(h, 1), P, 256, h->blocks[1], st));
   return HYDRO_OK;
@@ -242,6 +246,8 @@ int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, co
   h->gamma = gamma;
   h->precision = HYDRO_FP64;
   h->recon = HYDRO_RECON_PPMC;
+  h->solver = HYDRO_RIEMANN_EXACT;
+  h->eta_buf = nullptr;
   h->stream = nullptr;
   h->have_state = false;
   h->last_error = HYDRO_OK;
@@ -361,7 +367,8 @@ int hydro_set_precision(hydro_t h, int mode) {
   h->last_error = HYDRO_OK;
   if (mode != HYDRO_FP64 && mode != HYDRO_FP64_STRICT && mode != HYDRO_MIXED)
     return fail(h, HYDRO_EINVAL);
-  if (mode == HYDRO_MIXED && h->recon != HYDRO_RECON_PPMC) return fail(h, HYDRO_EINVAL);
+  if (mode == HYDRO_MIXED && (h->recon != HYDRO_RECON_PPMC || h->solver != HYDRO_RIEMANN_EXACT))
+    return fail(h, HYDRO_EINVAL);
   h->precision = mode;
   return HYDRO_OK;
 }
@@ -372,6 +379,37 @@ int hydro_set_reconstruction(hydro_t h, int recon) {
   if (recon < HYDRO_RECON_PPMC || recon > HYDRO_RECON_PCM) return fail(h, HYDRO_EINVAL);
   if (recon != HYDRO_RECON_PPMC && h->precision == HYDRO_MIXED) return fail(h, HYDRO_EINVAL);
   h->recon = recon;
+  return HYDRO_OK;
+}
+
+int hydro_set_riemann_solver(hydro_t h, int solver) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (solver != HYDRO_RIEMANN_EXACT && solver != HYDRO_RIEMANN_ROE) return fail(h, HYDRO_EINVAL);
+  if (solver != HYDRO_RIEMANN_EXACT && h->precision == HYDRO_MIXED) return fail(h, HYDRO_EINVAL);
+  if (solver == HYDRO_RIEMANN_ROE && !h->eta_buf) {
+    int rc = use_device(h);
+    if (rc) return rc;
+    int nact = 0;
+    for (int d = 0; d < 3; ++d) nact += active(h->G, d) ? 1 : 0;
+    const size_t plane = (size_t)h->G.ps * sizeof(double);
+    cudaError_t e = cudaMalloc(&h->eta_buf, plane * (size_t)nact);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      h->eta_buf = nullptr;
+      return fail(h, HYDRO_ENOMEM);
+    }
+    double* p = h->eta_buf;
+    for (int d = 0; d < 3; ++d) {
+      h->B.eta[d] = nullptr;
+      if (!active(h->G, d)) continue;
+      h->B.eta[d] = p;
+      p += h->G.ps;
+    }
+    h->desc.B = h->B;
+    CK(h, cudaMemcpy(h->d_desc, &h->desc, sizeof(GridDesc), cudaMemcpyHostToDevice));
+  }
+  h->solver = solver;
   return HYDRO_OK;
 }
 
@@ -505,6 +543,7 @@ void hydro_free(hydro_t h) {
   if (h->profile)
     for (int k = 0; k < 2 * 64; ++k) cudaEventDestroy(h->ev[k]);
   cudaFree(h->slab);
+  if (h->eta_buf) cudaFree(h->eta_buf);
   cudaFree(h->d_desc);
   cudaFree(h->d_tab);
   cudaFreeHost(h->host_rec);

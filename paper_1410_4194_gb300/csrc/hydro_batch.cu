@@ -37,6 +37,8 @@ struct hydro_batch_s {
   int ngrids = 0;
   int precision = HYDRO_FP64;
   int recon = HYDRO_RECON_PPMC;
+  int solver = HYDRO_RIEMANN_EXACT;
+  double* eta_buf = nullptr;       // H-correction planes of every grid (Roe solver)
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -60,6 +62,7 @@ struct hydro_batch_s {
   double g_cfl = -1.0;
   int g_precision = -1;
   int g_recon = -1;
+  int g_solver = -1;
   Schedule g_sched;
   int last_error = HYDRO_OK;
   char cuda_err[256] = {0};
@@ -126,15 +129,15 @@ int enqueue_step(hydro_batch_t h, double cfl, int step) {
     for (int s = kStageSlopes; s <= kStageRiemann1; ++s) {
       const int kind = launch_kind(s, d);
       if (s == kStageSlopes && h->recon == HYDRO_RECON_PCM) continue;  // no slopes
-      BCK(h, batch_stage(launch_of(h, kind), h->precision, h->recon, s, d, bs, h->blocks[kind],
-                         st));
+      BCK(h, batch_stage(launch_of(h, kind), h->precision, h->recon, h->solver, s, d, bs,
+                         h->blocks[kind], st));
     }
   }
   for (int d = 0; d < 3; ++d) {
     if (!h->axis_used[d]) continue;
     const int kind = launch_kind(kStageRiemann2, d);
-    BCK(h, batch_stage(launch_of(h, kind), h->precision, h->recon, kStageRiemann2, d, bs,
-                       h->blocks[kind], st));
+    BCK(h, batch_stage(launch_of(h, kind), h->precision, h->recon, h->solver, kStageRiemann2, d,
+                       bs, h->blocks[kind], st));
   }
   BCK(h, batch_update(launch_of(h, 1), h->precision, bs, h->blocks[1], st));
   return HYDRO_OK;
@@ -191,6 +194,7 @@ std::string shape_key(hydro_batch_t h) {
   for (const GridDesc& g : h->desc)
     for (int d = 0; d < 3; ++d) mix(g.G.n[d]);
   if (h->recon != HYDRO_RECON_PPMC) mix(1000 + h->recon);
+  if (h->solver != HYDRO_RIEMANN_EXACT) mix(2000 + h->solver);
   cudaDeviceProp prop;
   char name[64] = "unknown";
   if (cudaGetDeviceProperties(&prop, h->device) == cudaSuccess) {
@@ -357,7 +361,8 @@ int hydro_batch_set_precision(hydro_batch_t h, int mode) {
   if (!h) return HYDRO_EINVAL;
   h->last_error = HYDRO_OK;
   if (mode != HYDRO_FP64 && mode != HYDRO_MIXED) return bfail(h, HYDRO_EINVAL);
-  if (mode == HYDRO_MIXED && h->recon != HYDRO_RECON_PPMC) return bfail(h, HYDRO_EINVAL);
+  if (mode == HYDRO_MIXED && (h->recon != HYDRO_RECON_PPMC || h->solver != HYDRO_RIEMANN_EXACT))
+    return bfail(h, HYDRO_EINVAL);
   if (mode != h->precision) h->tuned = false;
   h->precision = mode;
   return HYDRO_OK;
@@ -370,6 +375,40 @@ int hydro_batch_set_reconstruction(hydro_batch_t h, int recon) {
   if (recon != HYDRO_RECON_PPMC && h->precision == HYDRO_MIXED) return bfail(h, HYDRO_EINVAL);
   if (recon != h->recon) h->tuned = false;
   h->recon = recon;
+  return HYDRO_OK;
+}
+
+int hydro_batch_set_riemann_solver(hydro_batch_t h, int solver) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (solver != HYDRO_RIEMANN_EXACT && solver != HYDRO_RIEMANN_ROE) return bfail(h, HYDRO_EINVAL);
+  if (solver != HYDRO_RIEMANN_EXACT && h->precision == HYDRO_MIXED) return bfail(h, HYDRO_EINVAL);
+  if (solver == HYDRO_RIEMANN_ROE && !h->eta_buf) {
+    if (cudaSetDevice(h->device) != cudaSuccess) return bfail(h, HYDRO_ECUDA);
+    size_t planes = 0;
+    for (const GridDesc& g : h->desc)
+      for (int d = 0; d < 3; ++d)
+        if (g.G.n[d] > 1) planes += (size_t)g.G.ps;
+    cudaError_t e = cudaMalloc(&h->eta_buf, planes * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      h->eta_buf = nullptr;
+      return bfail(h, HYDRO_ENOMEM);
+    }
+    double* p = h->eta_buf;
+    for (GridDesc& g : h->desc)
+      for (int d = 0; d < 3; ++d) {
+        g.B.eta[d] = nullptr;
+        if (g.G.n[d] <= 1) continue;
+        g.B.eta[d] = p;
+        p += g.G.ps;
+      }
+    e = cudaMemcpy(h->d_desc, h->desc.data(), sizeof(GridDesc) * h->ngrids,
+                   cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bcuda(h, e);
+  }
+  if (solver != h->solver) h->tuned = false;
+  h->solver = solver;
   return HYDRO_OK;
 }
 
@@ -419,6 +458,7 @@ int hydro_batch_step(hydro_batch_t h, double cfl, int nsteps, double* dt_out) {
   if (rc) return rc;
   const bool same = h->gexec && h->g_nsteps == nsteps && h->g_cfl == cfl &&
                     h->g_precision == h->precision && h->g_recon == h->recon &&
+                    h->g_solver == h->solver &&
                     h->g_sched.bs == h->sched.bs && h->g_sched.order == h->sched.order;
   if (!same) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -445,6 +485,7 @@ int hydro_batch_step(hydro_batch_t h, double cfl, int nsteps, double* dt_out) {
     h->g_cfl = cfl;
     h->g_precision = h->precision;
     h->g_recon = h->recon;
+    h->g_solver = h->solver;
     h->g_sched = h->sched;
   }
   BCK(h, cudaGraphLaunch(h->gexec, h->stream));
@@ -551,6 +592,7 @@ void hydro_batch_free(hydro_batch_t h) {
   if (h->d_tables) cudaFree(h->d_tables);
   if (h->d_desc) cudaFree(h->d_desc);
   if (h->slab) cudaFree(h->slab);
+  if (h->eta_buf) cudaFree(h->eta_buf);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }

@@ -29,13 +29,7 @@ namespace hydro {
 namespace {
 
 // block-wide maximum of a non-negative double (NaN ignored), then one
-// atomicMax on its bits (non-negative doubles order like their bit patterns);
-// S (strict): IEEE comparisons, else integer ones (max_nonneg, same result)
-template <bool S>
-__device__ __forceinline__ double max_nn(double v, double w) {
-  if constexpr (S) return tmax(v, w);
-  else return max_nonneg(v, w);
-}
+// atomicMax on its bits (non-negative doubles order like their bit patterns)
 template <bool S>
 __device__ __forceinline__ void block_max_to(double v, unsigned long long* slot) {
   __shared__ double warp_max[kThreads / 32];
@@ -352,9 +346,9 @@ long long stage_units(const Geom& G, int stage, int axis) {
   return box_count(stage_box(G, stage, axis));
 }
 
-cudaError_t fp64_stage_strict(const Geom& G, const Bufs& B, int recon, int stage, int axis,
-                              double gamma, cudaStream_t st) {
-  return launch_axis_stage<true>(G, B, recon, stage, axis, gamma, st);
+cudaError_t fp64_stage_strict(const Geom& G, const Bufs& B, int recon, int solver, int stage,
+                              int axis, double gamma, cudaStream_t st) {
+  return launch_axis_stage<true>(G, B, recon, solver, stage, axis, gamma, st);
 }
 
 cudaError_t batch_prims(const BatchLaunch& L, int precision, int bs, unsigned blocks, cudaStream_t st) {
@@ -384,10 +378,11 @@ cudaError_t batch_set_dt(const GridDesc* descs, int ngrids, double cfl, double* 
   return cudaGetLastError();
 }
 
-cudaError_t batch_stage(const BatchLaunch& L, int precision, int recon, int stage, int axis,
-                        int bs, unsigned blocks, cudaStream_t st) {
-  return precision == HYDRO_MIXED ? batch_stage_mixed(L, stage, axis, bs, blocks, st)
-                                  : batch_stage_fp64(L, recon, stage, axis, bs, blocks, st);
+cudaError_t batch_stage(const BatchLaunch& L, int precision, int recon, int solver, int stage,
+                        int axis, int bs, unsigned blocks, cudaStream_t st) {
+  return precision == HYDRO_MIXED
+             ? batch_stage_mixed(L, stage, axis, bs, blocks, st)
+             : batch_stage_fp64(L, recon, solver, stage, axis, bs, blocks, st);
 }
 
 cudaError_t fp64_update(const Geom& G, const Bufs& B, cudaStream_t st) {

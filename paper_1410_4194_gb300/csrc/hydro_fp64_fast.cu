@@ -7,9 +7,9 @@
 
 namespace hydro {
 
-cudaError_t batch_stage_fp64(const BatchLaunch& L, int recon, int stage, int axis, int bs,
-                             unsigned blocks, cudaStream_t st) {
-  return launch_batch_stage<false>(L, recon, stage, axis, bs, blocks, st);
+cudaError_t batch_stage_fp64(const BatchLaunch& L, int recon, int solver, int stage, int axis,
+                             int bs, unsigned blocks, cudaStream_t st) {
+  return launch_batch_stage<false>(L, recon, solver, stage, axis, bs, blocks, st);
 }
 
 }  // namespace hydro

@@ -33,6 +33,7 @@ struct Bufs {
   double* UL[3];   // per axis: primitive left states W*_L of faces [5][ps]; reused for F^{n+1/2}
   double* UR[3];   // per axis: primitive right states W*_R of faces [5][ps]
   double* F1[3];   // per axis: first fluxes F* [5][ps]
+  double* eta[3];  // per axis: H-correction eta of each face [ps] (Roe solver only, else null)
   // 64-byte step record on the device: [0] max of |v_d| + a (bits), [1] dt, [2] dt/dx,
   // [3] dt/(2 dx), [4] flags (int in the low word)
   double* rec;
@@ -107,8 +108,8 @@ cudaError_t fp64_prims(const Geom& G, const Bufs& B, const BcDesc& bc, double ga
 cudaError_t fp64_set_dt(const Geom& G, const Bufs& B, double cfl, double fixed_dt, cudaStream_t st);
 // one launch of a per-axis stage in the reference operation order (strict mode);
 // the fast FP64 and mixed paths use the batched launchers below with one grid
-cudaError_t fp64_stage_strict(const Geom& G, const Bufs& B, int recon, int stage, int axis,
-                              double gamma, cudaStream_t st);
+cudaError_t fp64_stage_strict(const Geom& G, const Bufs& B, int recon, int solver, int stage,
+                              int axis, double gamma, cudaStream_t st);
 cudaError_t fp64_update(const Geom& G, const Bufs& B, cudaStream_t st);
 
 // Batched launchers: one launch covers the given stage of every grid of a
@@ -117,13 +118,13 @@ cudaError_t fp64_update(const Geom& G, const Bufs& B, cudaStream_t st);
 cudaError_t batch_prims(const BatchLaunch& L, int precision, int bs, unsigned blocks, cudaStream_t st);
 cudaError_t batch_set_dt(const GridDesc* descs, int ngrids, double cfl, double* dt_hist,
                          cudaStream_t st);
-cudaError_t batch_stage(const BatchLaunch& L, int precision, int recon, int stage, int axis,
-                        int bs, unsigned blocks, cudaStream_t st);
+cudaError_t batch_stage(const BatchLaunch& L, int precision, int recon, int solver, int stage,
+                        int axis, int bs, unsigned blocks, cudaStream_t st);
 cudaError_t batch_update(const BatchLaunch& L, int precision, int bs, unsigned blocks,
                          cudaStream_t st);
 // batched building blocks in the fast FP64 and the mixed translation units
-cudaError_t batch_stage_fp64(const BatchLaunch& L, int recon, int stage, int axis, int bs,
-                             unsigned blocks, cudaStream_t st);
+cudaError_t batch_stage_fp64(const BatchLaunch& L, int recon, int solver, int stage, int axis,
+                             int bs, unsigned blocks, cudaStream_t st);
 cudaError_t batch_stage_mixed(const BatchLaunch& L, int stage, int axis, int bs, unsigned blocks,
                               cudaStream_t st);
 cudaError_t batch_prims_mixed(const BatchLaunch& L, int bs, unsigned blocks, cudaStream_t st);

@@ -273,7 +273,9 @@ __device__ __forceinline__ void plmp_body(const Geom& G, const Bufs& B, const Bo
 }
 
 // PCM face states of cell c: the cell average at both faces (stored as its
-// primitives, or in strict mode converted back to conserved variables)
+// primitives, or in strict mode converted back to conserved variables -- a
+// rounding-level round trip of the cell's conserved average, so strict PCM is
+// not operation-identical to the CPU reference)
 template <int D, bool S>
 __device__ __forceinline__ void pcm_body(const Geom& G, const Bufs& B, const Box& box,
     const Gas& g, long long t) {
@@ -299,28 +301,44 @@ HYDRO_SINGLE_WRAPPER(k_plmp, plmp_body)
 HYDRO_SINGLE_WRAPPER(k_pcm, pcm_body)
 #undef HYDRO_SINGLE_WRAPPER
 
-template <int D, bool S>
+// first Riemann set at face f: the exact solver, or (ROE) the Roe solver with
+// the HLLE fallback, which also stores the face's H-correction eta
+template <int D, bool S, bool ROE = false>
 __device__ __forceinline__ void riemann1_body(const Geom& G, const Bufs& B, const Box& box,
     const Gas& g, long long t) {
   int c3[3];
   box_coords(box, t, c3);
   const long long f = pidx(G, c3);
-  double WL[5], WR[5], F[5];
-  int fl;
+  double UL[5], UR[5], WL[5], WR[5], F[5], idL, idR;
+  int fl = 0;
   if constexpr (S) {
-    double UL[5], UR[5], idL, idR;
     load_rot<D>(B.UL[D], G.ps, f, UL);
     load_rot<D>(B.UR[D], G.ps, f, UR);
     cons2prim<true>(UL, g, WL, idL);
     cons2prim<true>(UR, g, WR, idR);
-    fl = riemann_exact<true>(WL, WR, idL, idR, g, F);
   } else {
     load_rot<D>(B.UL[D], G.ps, f, WL);
     load_rot<D>(B.UR[D], G.ps, f, WR);
-    fl = riemann_exact<false>(WL, WR, nr_rcp(WL[0]), nr_rcp(WR[0]), g, F);
+    idL = nr_rcp(WL[0]);
+    idR = nr_rcp(WR[0]);
+    if constexpr (ROE) {
+      prim2cons(WL, g, UL);
+      prim2cons(WR, g, UR);
+    }
+  }
+  if constexpr (ROE) {
+    riemann_roe<S>(UL, UR, WL, WR, idL, idR, 0.0, g, F);
+    B.eta[D][f] = h_eta<S>(WL, WR, idL, idR, g);
+  } else {
+    fl = riemann_exact<S>(WL, WR, idL, idR, g, F);
   }
   store_rot<D>(B.F1[D], G.ps, f, F);
   if (fl) atomicOr(rec_flags(B.rec), fl);
+}
+template <int D, bool S>
+__device__ __forceinline__ void riemann1_roe_body(const Geom& G, const Bufs& B, const Box& box,
+    const Gas& g, long long t) {
+  riemann1_body<D, S, true>(G, B, box, g, t);
 }
 
 template <int D, bool S>
@@ -330,7 +348,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann1(Geom G, Bufs 
   if (t < count) riemann1_body<D, S>(G, B, box, g, t);
 }
 
-template <int D, bool S>
+// transverse half-step and second Riemann set at face f; with ROE the Roe
+// solver with the H correction: eta^H is the largest eta of this face and of
+// the transverse faces of the two cells it separates (nine faces in 3D)
+template <int D, bool S, bool ROE = false>
 __device__ __forceinline__ void riemann2_body(const Geom& G, const Bufs& B, const Box& box,
     const Gas& g, long long t) {
   int c3[3];
@@ -380,10 +401,37 @@ __device__ __forceinline__ void riemann2_body(const Geom& G, const Bufs& B, cons
   UR[0] = UhR[0]; UR[1] = UhR[1 + D]; UR[2] = UhR[1 + T1]; UR[3] = UhR[1 + T2]; UR[4] = UhR[4];
   cons2prim<S>(UL, g, WL, idL);
   cons2prim<S>(UR, g, WR, idR);
-  const int fl = riemann_exact<S>(WL, WR, idL, idR, g, Fx);
+  int fl = 0;
+  if constexpr (ROE) {
+    double etaH = B.eta[D][f];
+    if (G.n[T1] > 1) {
+      const double* e = B.eta[T1];
+      const long long st = G.s[T1];
+      etaH = max_nn<S>(etaH, e[cl]);
+      etaH = max_nn<S>(etaH, e[cl + st]);
+      etaH = max_nn<S>(etaH, e[cr]);
+      etaH = max_nn<S>(etaH, e[cr + st]);
+    }
+    if (G.n[T2] > 1) {
+      const double* e = B.eta[T2];
+      const long long st = G.s[T2];
+      etaH = max_nn<S>(etaH, e[cl]);
+      etaH = max_nn<S>(etaH, e[cl + st]);
+      etaH = max_nn<S>(etaH, e[cr]);
+      etaH = max_nn<S>(etaH, e[cr + st]);
+    }
+    riemann_roe<S>(UL, UR, WL, WR, idL, idR, etaH, g, Fx);
+  } else {
+    fl = riemann_exact<S>(WL, WR, idL, idR, g, Fx);
+  }
   // CTU flux of this face replaces its (now consumed) left state
   store_rot<D>(B.UL[D], ps, f, Fx);
   if (fl) atomicOr(rec_flags(B.rec), fl);
+}
+template <int D, bool S>
+__device__ __forceinline__ void riemann2_roe_body(const Geom& G, const Bufs& B, const Box& box,
+    const Gas& g, long long t) {
+  riemann2_body<D, S, true>(G, B, box, g, t);
 }
 
 template <int D, bool S>
@@ -391,6 +439,18 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann2(Geom G, Bufs 
   const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < count) riemann2_body<D, S>(G, B, box, g, t);
+}
+template <int D, bool S>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann1_roe(Geom G, Bufs B, Box box, Gas g) {
+  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) riemann1_roe_body<D, S>(G, B, box, g, t);
+}
+template <int D, bool S>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_riemann2_roe(Geom G, Bufs B, Box box, Gas g) {
+  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) riemann2_roe_body<D, S>(G, B, box, g, t);
 }
 
 inline unsigned blocks_for(long long count) {
@@ -467,6 +527,8 @@ HYDRO_BATCH_WRAPPER(kb_plmp, plmp_body, 1)
 HYDRO_BATCH_WRAPPER(kb_pcm, pcm_body, 1)
 HYDRO_BATCH_WRAPPER(kb_riemann1, riemann1_body, 2)
 HYDRO_BATCH_WRAPPER(kb_riemann2, riemann2_body, 3)
+HYDRO_BATCH_WRAPPER(kb_riemann1_roe, riemann1_roe_body, 2)
+HYDRO_BATCH_WRAPPER(kb_riemann2_roe, riemann2_roe_body, 3)
 #undef HYDRO_BATCH_WRAPPER
 
 // Ranges (padded coordinates; "others" are the two axes across the sweep):
@@ -488,8 +550,8 @@ inline Box stage_box(const Geom& G, int stage, int axis) {
 // PPMC and PLMC take characteristic slopes, PPMP and PLMP primitive ones, PCM
 // none (its slope stage launches nothing)
 template <bool S>
-cudaError_t launch_axis_stage(const Geom& G, const Bufs& B, int recon, int stage, int axis,
-                              double gamma, cudaStream_t st) {
+cudaError_t launch_axis_stage(const Geom& G, const Bufs& B, int recon, int solver, int stage,
+                              int axis, double gamma, cudaStream_t st) {
   const Gas g = make_gas<double>(gamma);
   const Box b = stage_box(G, stage, axis);
   const unsigned nb = blocks_for(box_count(b));
@@ -518,8 +580,20 @@ cudaError_t launch_axis_stage(const Geom& G, const Bufs& B, int recon, int stage
         default: HYDRO_LAUNCH_AXIS(k_ppmc) break;
       }
       break;
-    case kStageRiemann1: HYDRO_LAUNCH_AXIS(k_riemann1) break;
-    case kStageRiemann2: HYDRO_LAUNCH_AXIS(k_riemann2) break;
+    case kStageRiemann1:
+      if (solver == HYDRO_RIEMANN_ROE) {
+        HYDRO_LAUNCH_AXIS(k_riemann1_roe)
+      } else {
+        HYDRO_LAUNCH_AXIS(k_riemann1)
+      }
+      break;
+    case kStageRiemann2:
+      if (solver == HYDRO_RIEMANN_ROE) {
+        HYDRO_LAUNCH_AXIS(k_riemann2_roe)
+      } else {
+        HYDRO_LAUNCH_AXIS(k_riemann2)
+      }
+      break;
     default: return cudaErrorInvalidValue;
   }
 #undef HYDRO_LAUNCH_AXIS
@@ -527,8 +601,8 @@ cudaError_t launch_axis_stage(const Geom& G, const Bufs& B, int recon, int stage
 }
 
 template <bool S>
-cudaError_t launch_batch_stage(const BatchLaunch& L, int recon, int stage, int axis, int bs,
-                               unsigned blocks, cudaStream_t st) {
+cudaError_t launch_batch_stage(const BatchLaunch& L, int recon, int solver, int stage, int axis,
+                               int bs, unsigned blocks, cudaStream_t st) {
   if (blocks == 0) return cudaSuccess;
 #define HYDRO_BATCH_AXIS(K)                                                              \
   if (bs == 128) {                                                                       \
@@ -562,8 +636,20 @@ cudaError_t launch_batch_stage(const BatchLaunch& L, int recon, int stage, int a
         default: HYDRO_BATCH_AXIS(kb_ppmc) break;
       }
       break;
-    case kStageRiemann1: HYDRO_BATCH_AXIS(kb_riemann1) break;
-    case kStageRiemann2: HYDRO_BATCH_AXIS(kb_riemann2) break;
+    case kStageRiemann1:
+      if (solver == HYDRO_RIEMANN_ROE) {
+        HYDRO_BATCH_AXIS(kb_riemann1_roe)
+      } else {
+        HYDRO_BATCH_AXIS(kb_riemann1)
+      }
+      break;
+    case kStageRiemann2:
+      if (solver == HYDRO_RIEMANN_ROE) {
+        HYDRO_BATCH_AXIS(kb_riemann2_roe)
+      } else {
+        HYDRO_BATCH_AXIS(kb_riemann2)
+      }
+      break;
     default: return cudaErrorInvalidValue;
   }
 #undef HYDRO_BATCH_AXIS

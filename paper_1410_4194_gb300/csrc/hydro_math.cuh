@@ -145,6 +145,12 @@ __device__ __forceinline__ double max_nonneg(double a, double b) {
   const long long ka = __double_as_longlong(a), kb = __double_as_longlong(b);
   return (kb > ka && kb <= 0x7ff0000000000000LL) ? b : a;
 }
+// the same with S (strict): IEEE comparisons, else integer ones (same result)
+template <bool S>
+__device__ __forceinline__ double max_nn(double v, double w) {
+  if constexpr (S) return tmax(v, w);
+  else return max_nonneg(v, w);
+}
 __device__ __forceinline__ bool bits_equal(double a, double b) {
   return __double_as_longlong(a) == __double_as_longlong(b);
 }
@@ -866,6 +872,166 @@ __device__ __forceinline__ void ppmp_states(const T w[7][5], const T sm[5], cons
   WsR[2] = WR0[2];
   WsR[3] = WR0[3];
   WsR[4] = vmax<S>(WRp[4] + CR * CR * chiRm, T(kPFloor));
+}
+
+// ---------------------------------------------------------------------------
+// Roe solver with the HLLE fallback (Sec. 2.2.2, App. B.2) and the H
+// correction (App. C).  Inputs in sweep order: conserved U and primitive W of
+// each side (W with the pressure floor, inv_d = 1/rho); etaH >= 0 replaces every
+// |lambda| of the Roe coefficients by max(|lambda|, etaH) (0: no correction).
+// Readings as in the CPU reference: s_3 carries C_3 w~; a "negative"
+// intermediate density or pressure is < 0; a Roe average without a real sound
+// speed takes the HLLE flux.
+
+template <bool S = false, typename T>
+__device__ __forceinline__ void hlle_flux(const T UL[5], const T UR[5], const T WL[5],
+                                          const T WR[5], T inv_dL, T inv_dR, const T FL[5],
+                                          const T FR[5], T lm, T lp, const GasT<T>& g, T F[5]) {
+  T aL, aR;
+  if constexpr (S) {
+    aL = xsqrt(g.gamma * WL[4] / WL[0]);
+    aR = xsqrt(g.gamma * WR[4] / WR[0]);
+  } else {
+    aL = nr_sqrt(g.gamma * WL[4] * inv_dL);
+    aR = nr_sqrt(g.gamma * WR[4] * inv_dR);
+  }
+  const T bm = vmin<S>(vmin<S>(lm, WL[1] - aL), T(0));
+  const T bp = vmax<S>(vmax<S>(lp, WR[1] + aR), T(0));
+  const T k = S ? (bp + bm) / (bp - bm) : nr_div(bp + bm, bp - bm);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const T FLh = FL[q] - bm * UL[q];
+    const T FRh = FR[q] - bp * UR[q];
+    F[q] = T(0.5) * ((FLh + FRh) + (FLh - FRh) * k);
+  }
+}
+
+// an intermediate state with rho < 0 or p < 0 (fast: p < 0 as 2 E rho < |m|^2
+// for rho > 0)
+template <bool S = false, typename T>
+__device__ __forceinline__ bool negative_state(const T U[5], const GasT<T>& g) {
+  const T m2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
+  if constexpr (S) {
+    const T p = g.gm1 * (U[4] - T(0.5) * m2 / U[0]);
+    return U[0] < T(0) || p < T(0);
+  } else {
+    return neg<S>(U[0]) || lt<S>(T(2) * U[4] * U[0], m2);
+  }
+}
+
+template <bool S = false, typename T>
+__device__ __forceinline__ void riemann_roe(const T UL[5], const T UR[5], const T WL[5],
+                                            const T WR[5], T inv_dL, T inv_dR, T etaH,
+                                            const GasT<T>& g, T F[5]) {
+  T FL[5], FR[5];
+  euler_flux<S>(WL, g, FL);
+  euler_flux<S>(WR, g, FR);
+  T u, v, w, H;
+  if constexpr (S) {
+    const T sL = xsqrt(WL[0]), sR = xsqrt(WR[0]);
+    const T HL = (UL[4] + WL[4]) / WL[0];
+    const T HR = (UR[4] + WR[4]) / WR[0];
+    u = (sL * WL[1] + sR * WR[1]) / (sL + sR);
+    v = (sL * WL[2] + sR * WR[2]) / (sL + sR);
+    w = (sL * WL[3] + sR * WR[3]) / (sL + sR);
+    H = (sL * HL + sR * HR) / (sL + sR);
+  } else {
+    const T sL = nr_sqrt(WL[0]), sR = nr_sqrt(WR[0]);
+    const T HL = (UL[4] + WL[4]) * inv_dL;
+    const T HR = (UR[4] + WR[4]) * inv_dR;
+    const T ir = nr_rcp(sL + sR);
+    u = (sL * WL[1] + sR * WR[1]) * ir;
+    v = (sL * WL[2] + sR * WR[2]) * ir;
+    w = (sL * WL[3] + sR * WR[3]) * ir;
+    H = (sL * HL + sR * HR) * ir;
+  }
+  const T V2 = u * u + v * v + w * w;
+  const T a2 = g.gm1 * (H - T(0.5) * V2);
+  if (!pos<S>(a2)) {
+    hlle_flux<S>(UL, UR, WL, WR, inv_dL, inv_dR, FL, FR, u, u, g, F);
+    return;
+  }
+  const T a = S ? xsqrt(a2) : nr_sqrt(a2);
+  const T lm = u - a, l0 = u, lp = u + a;
+  if (nonneg<S>(lm)) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) F[q] = FL[q];
+    return;
+  }
+  if (nonpos<S>(lp)) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) F[q] = FR[q];
+    return;
+  }
+  T dU[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) dU[q] = UR[q] - UL[q];
+  const T gp = g.gm1;
+  T Na, ia2;
+  if constexpr (S) {
+    Na = T(1) / (T(2) * a2);
+    ia2 = T(0);
+  } else {
+    ia2 = nr_rcp(a2);
+    Na = T(0.5) * ia2;
+  }
+  const T xi0 = dU[0] * Na * (T(0.5) * gp * V2 + u * a) - dU[1] * Na * (gp * u + a) -
+                dU[2] * Na * gp * v - dU[3] * Na * gp * w + dU[4] * Na * gp;
+  const T xi1 = -dU[0] * v + dU[2];
+  const T xi2 = -dU[0] * w + dU[3];
+  T xi3;
+  if constexpr (S)
+    xi3 = dU[0] * (T(1) - Na * gp * V2) + dU[1] * gp * u / a2 + dU[2] * gp * v / a2 +
+          dU[3] * gp * w / a2 - dU[4] * gp / a2;
+  else
+    xi3 = dU[0] * (T(1) - Na * gp * V2) + (dU[1] * u + dU[2] * v + dU[3] * w - dU[4]) * (gp * ia2);
+  const T xi4 = dU[0] * Na * (T(0.5) * gp * V2 - u * a) - dU[1] * Na * (gp * u - a) -
+                dU[2] * Na * gp * v - dU[3] * Na * gp * w + dU[4] * Na * gp;
+  const T alm = vmax<S>(xabs(lm), etaH), al0 = vmax<S>(xabs(l0), etaH),
+          alp = vmax<S>(xabs(lp), etaH);
+  const T C0 = xi0 * alm, C1 = xi1 * al0, C2 = xi2 * al0, C3 = xi3 * al0, C4 = xi4 * alp;
+  T s[5];
+  s[0] = C0 + C3 + C4;
+  s[1] = C0 * (u - a) + C3 * u + C4 * (u + a);
+  s[2] = C0 * v + C1 + C3 * v + C4 * v;
+  s[3] = C0 * w + C2 + C3 * w + C4 * w;
+  s[4] = C0 * (H - u * a) + C1 * v + C2 * w + T(0.5) * C3 * V2 + C4 * (H + u * a);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) F[q] = T(0.5) * (FL[q] + FR[q] - s[q]);
+  // intermediate states: a negative density or pressure takes the HLLE flux
+  T Um[5];
+  Um[0] = UL[0] + xi0;
+  Um[1] = UL[1] + xi0 * (u - a);
+  Um[2] = UL[2] + xi0 * v;
+  Um[3] = UL[3] + xi0 * w;
+  Um[4] = UL[4] + xi0 * (H - u * a);
+  bool fail = lt<S>(lm, l0) && negative_state<S>(Um, g);
+  if (!fail && lt<S>(l0, lp)) {
+    Um[0] = Um[0] + xi3;
+    Um[1] = Um[1] + xi3 * u;
+    Um[2] = Um[2] + xi1 + xi3 * v;
+    Um[3] = Um[3] + xi2 + xi3 * w;
+    Um[4] = Um[4] + xi1 * v + xi2 * w + T(0.5) * xi3 * V2;
+    fail = negative_state<S>(Um, g);
+  }
+  if (fail) hlle_flux<S>(UL, UR, WL, WR, inv_dL, inv_dR, FL, FR, lm, lp, g, F);
+}
+
+// H-correction quantity of a face (App. C): half the largest jump of a
+// characteristic speed, max(|(u_R + a_R) - (u_L + a_L)|, |(u_R - a_R) - (u_L - a_L)|)/2
+// (the paper prints the u + a term; see the CPU reference for the reading)
+template <bool S = false, typename T>
+__device__ __forceinline__ T h_eta(const T WL[5], const T WR[5], T inv_dL, T inv_dR,
+                                   const GasT<T>& g) {
+  T aL, aR;
+  if constexpr (S) {
+    aL = xsqrt(g.gamma * WL[4] / WL[0]);
+    aR = xsqrt(g.gamma * WR[4] / WR[0]);
+  } else {
+    aL = nr_sqrt(g.gamma * WL[4] * inv_dL);
+    aR = nr_sqrt(g.gamma * WR[4] * inv_dR);
+  }
+  return T(0.5) * vmax<S>(xabs((WR[1] + aR) - (WL[1] + aL)), xabs((WR[1] - aR) - (WL[1] - aL)));
 }
 
 // ---------------------------------------------------------------------------

@@ -16,6 +16,7 @@ import numpy as np
 HYDRO_BC_PERIODIC, HYDRO_BC_REFLECT, HYDRO_BC_OUTFLOW, HYDRO_BC_INFLOW = 0, 1, 2, 3
 HYDRO_FP64, HYDRO_MIXED, HYDRO_FP64_STRICT = 0, 1, 2
 HYDRO_RECON_PPMC, HYDRO_RECON_PPMP, HYDRO_RECON_PLMC, HYDRO_RECON_PLMP, HYDRO_RECON_PCM = range(5)
+HYDRO_RIEMANN_EXACT, HYDRO_RIEMANN_ROE = 0, 1
 ERRORS = {0: "HYDRO_OK", -1: "HYDRO_EINVAL", -2: "HYDRO_ENOMEM", -3: "HYDRO_ECUDA",
           -4: "HYDRO_ENONPHYS", -5: "HYDRO_ENEWTON", -6: "HYDRO_ENOSTATE"}
 
@@ -32,7 +33,8 @@ EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_precision", "hydro_set_s
            "hydro_batch_set_stream", "hydro_batch_set_state", "hydro_batch_get_state",
            "hydro_batch_step", "hydro_batch_autotune", "hydro_batch_last_error",
            "hydro_batch_cuda_error_string", "hydro_batch_free", "hydro_check_conversions",
-           "hydro_set_reconstruction", "hydro_batch_set_reconstruction")
+           "hydro_set_reconstruction", "hydro_batch_set_reconstruction",
+           "hydro_set_riemann_solver", "hydro_batch_set_riemann_solver")
 STAGES = ("prims", "set_dt", "slopes", "ppmc", "riemann1", "riemann2", "update")
 
 _lib = None
@@ -89,6 +91,8 @@ def load():
     L.hydro_check_conversions.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), vp]
     L.hydro_set_reconstruction.argtypes = [vp, ctypes.c_int]
     L.hydro_batch_set_reconstruction.argtypes = [vp, ctypes.c_int]
+    L.hydro_set_riemann_solver.argtypes = [vp, ctypes.c_int]
+    L.hydro_batch_set_riemann_solver.argtypes = [vp, ctypes.c_int]
     _lib = L
     return L
 
@@ -118,7 +122,7 @@ class Grid:
     """One grid advanced by the CUDA CTU step (see include/hydro.h)."""
 
     def __init__(self, nx, ny, nz, dx, gamma, bc, precision=HYDRO_FP64, stream=None,
-                 recon=HYDRO_RECON_PPMC):
+                 recon=HYDRO_RECON_PPMC, solver=HYDRO_RIEMANN_EXACT):
         L = load()
         self._L = L
         h = ctypes.c_void_p()
@@ -133,6 +137,8 @@ class Grid:
             self.set_stream(stream)
         if recon != HYDRO_RECON_PPMC:
             self.set_reconstruction(recon)
+        if solver != HYDRO_RIEMANN_EXACT:
+            self.set_riemann_solver(solver)
         if precision != HYDRO_FP64:
             self.set_precision(precision)
 
@@ -163,6 +169,9 @@ class Grid:
 
     def set_reconstruction(self, recon):
         self._check(self._L.hydro_set_reconstruction(self.h, int(recon)), "set_reconstruction")
+
+    def set_riemann_solver(self, solver):
+        self._check(self._L.hydro_set_riemann_solver(self.h, int(solver)), "set_riemann_solver")
 
     def set_stream(self, stream):
         """Order this grid's work on a stream: a torch.cuda.Stream, a raw
@@ -225,10 +234,10 @@ class Grid:
 
 
 def run(u0, dx, gamma, bc, nsteps=None, cfl=0.3, t_end=None, inflow=None, precision=HYDRO_FP64,
-        max_steps=100000, recon=HYDRO_RECON_PPMC):
+        max_steps=100000, recon=HYDRO_RECON_PPMC, solver=HYDRO_RIEMANN_EXACT):
     """Advance ``u0`` on the GPU; returns ``(u, t, nsteps)`` (host numpy state)."""
     _, nz, ny, nx = u0.shape
-    g = Grid(nx, ny, nz, dx, gamma, bc, precision=precision, recon=recon)
+    g = Grid(nx, ny, nz, dx, gamma, bc, precision=precision, recon=recon, solver=solver)
     try:
         if inflow:
             for face, prim in inflow.items():
@@ -303,7 +312,8 @@ def check_conversions():
 class Batch:
     """Independent grids of uneven sizes advanced together (see include/hydro.h)."""
 
-    def __init__(self, grids, precision=HYDRO_FP64, recon=HYDRO_RECON_PPMC):
+    def __init__(self, grids, precision=HYDRO_FP64, recon=HYDRO_RECON_PPMC,
+                 solver=HYDRO_RIEMANN_EXACT):
         """grids: list of dicts with "u" [5, nz, ny, nx], "dx", "gamma", "bc" and
         optionally "inflow" {face: prim}."""
         L = load()
@@ -329,6 +339,8 @@ class Batch:
         self.n = n
         if recon != HYDRO_RECON_PPMC:
             self._check(L.hydro_batch_set_reconstruction(h, int(recon)), "set_reconstruction")
+        if solver != HYDRO_RIEMANN_EXACT:
+            self._check(L.hydro_batch_set_riemann_solver(h, int(solver)), "set_riemann_solver")
         if precision != HYDRO_FP64:
             self._check(L.hydro_batch_set_precision(h, int(precision)), "set_precision")
         for i, w in enumerate(grids):

@@ -501,6 +501,11 @@ def run_batch(args, w, ws, rank, local):
         if ws > 1:
             dist.destroy_process_group()
         return
+    # kernels of one step of the graph (3D grids): primitives + dt, update, and
+    # per axis the slope pass (none for PCM or in mixed precision, whose PPMC
+    # kernel forms its own slopes), reconstruction and the two Riemann sets
+    slope_pass = 0 if (args.recon == "pcm" or args.precision == "mixed") else 1
+    launches_per_step = 3 + 3 * (3 + slope_pass)
     # step-level roofline (the graph's kernels are not timed one by one):
     # FP64 flops of a cell update times the cell-update rate
     if args.precision == "fp64":
@@ -522,7 +527,7 @@ def run_batch(args, w, ws, rank, local):
                    "precision": args.precision, "schedule": {"block": bs, "order": order},
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (states %.2f GB)" % (ncells * 40 / 1e9)},
-        "e2e": e2e, "gpu_launches": 15 * args.steps, "clocks": clocks,
+        "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
         "hbm": hbm_report(value / ws),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_FLOPS_PEAK,
                      "unit": "FP64 FLOP/s", "frac": achieved / FP64_FLOPS_PEAK, "traffic": None,

@@ -170,7 +170,8 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
   for (int d = 0; d < 3; ++d) {
     if (!active(G, d)) continue;
     for (int s = kStageSlopes; s <= kStageRiemann1; ++s) {
-      if (s == kStageSlopes && h->recon == HYDRO_RECON_PCM) continue;  // no slopes
+      // no slope pass for PCM; the mixed PPMC kernel forms its own slopes
+      if (s == kStageSlopes && (h->recon == HYDRO_RECON_PCM || P == HYDRO_MIXED)) continue;
       const int k = launch_kind(s, d);
       STAGE(h, s, d,
             batch_stage(one_grid(h, k), P, h->recon, h->solver, s, d, 256, h->blocks[k], st));

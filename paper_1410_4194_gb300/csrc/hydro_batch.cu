@@ -128,7 +128,9 @@ int enqueue_step(hydro_batch_t h, double cfl, int step) {
     if (!h->axis_used[d]) continue;
     for (int s = kStageSlopes; s <= kStageRiemann1; ++s) {
       const int kind = launch_kind(s, d);
-      if (s == kStageSlopes && h->recon == HYDRO_RECON_PCM) continue;  // no slopes
+      // no slope pass for PCM; the mixed PPMC kernel forms its own slopes
+      if (s == kStageSlopes && (h->recon == HYDRO_RECON_PCM || h->precision == HYDRO_MIXED))
+        continue;
       BCK(h, batch_stage(launch_of(h, kind), h->precision, h->recon, h->solver, s, d, bs,
                          h->blocks[kind], st));
     }

@@ -307,9 +307,21 @@ __device__ __forceinline__ T ipow(T x) {
 //      rounded root.
 // Measured faster in the solver than a second reciprocal-root step without the
 // correction.  r = 1 gives exactly 1.  In float (mixed path) one Newton step is
-// enough for float accuracy.
+// enough for float accuracy.  Double arguments within 2^-20 of 1 take a short
+// series instead (below).
 template <int K, typename T>
 __device__ __forceinline__ T kth_root(T r) {
+  if constexpr (sizeof(T) == 8) {
+    // near 1 (1 - 2^-20 < r < 1 + 2^-20, e.g. equal pressures up to rounding;
+    // tested on the bit pattern): the series 1 + e/K - (K-1) e^2/(2K^2),
+    // e = r - 1 exact (Sterbenz); the next term, (K-1)(2K-1) e^3/(6K^3) < 1e-19,
+    // is below an ulp
+    const long long rb = __double_as_longlong(r);
+    if (rb > 0x3feffffe00000000LL && rb < 0x3ff0000100000000LL) {
+      const T e = r - T(1);
+      return xfma(e, xfma(e, T(-(K - 1) / (2.0 * K * K)), T(1.0 / K)), T(1));
+    }
+  }
   float lr;
   if constexpr (sizeof(T) == 4)
     lr = __log2f(r);

@@ -175,39 +175,26 @@ __global__ void __launch_bounds__(BS) kb_prims_mixed(BatchLaunch L) {
 }
 
 template <int D>
-__device__ __forceinline__ void slopes_mixed_body(const Geom& G, const BufsF& B, const Box& box,
-    long long t) {
-  int c3[3];
-  box_coords(box, t, c3);
-  const long long c = pidx(G, c3);
-  const long long s = G.s[D];
-  float wm[5], wc[5], wp[5], dw[5];
-  load_prim_f<D>(B.W, G.ps, c - s, wm);
-  load_prim_f<D>(B.W, G.ps, c, wc);
-  load_prim_f<D>(B.W, G.ps, c + s, wp);
-  limited_slope(wm, wc, wp, B.W[5 * G.ps + c], B.W[6 * G.ps + c], B.W[7 * G.ps + c], dw);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) B.S[q * G.ps + c] = dw[q];
-}
-
-
-template <int D>
 __device__ __forceinline__ void ppmc_mixed_body(const Geom& G, const BufsF& B, const Box& box,
     long long t) {
   int c3[3];
   box_coords(box, t, c3);
   const long long c = pidx(G, c3);
   const long long s = G.s[D];
-  float wm[5], wc[5], wp[5], sm[5], sc[5], sp[5];
+  // the limited slopes of cells c-1, c, c+1 are formed here in float (cheap
+  // next to the FP64 stages) rather than read from a slope pass: this saves
+  // the slope planes' HBM round trip and a launch per axis
+  float w2m[5], wm[5], wc[5], wp[5], w2p[5], sm[5], sc[5], sp[5];
+  load_prim_f<D>(B.W, G.ps, c - 2 * s, w2m);
   load_prim_f<D>(B.W, G.ps, c - s, wm);
   load_prim_f<D>(B.W, G.ps, c, wc);
   load_prim_f<D>(B.W, G.ps, c + s, wp);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    sm[q] = B.S[q * G.ps + c - s];
-    sc[q] = B.S[q * G.ps + c];
-    sp[q] = B.S[q * G.ps + c + s];
-  }
+  load_prim_f<D>(B.W, G.ps, c + 2 * s, w2p);
+  limited_slope(w2m, wm, wc, B.W[5 * G.ps + c - s], B.W[6 * G.ps + c - s],
+                B.W[7 * G.ps + c - s], sm);
+  limited_slope(wm, wc, wp, B.W[5 * G.ps + c], B.W[6 * G.ps + c], B.W[7 * G.ps + c], sc);
+  limited_slope(wc, wp, w2p, B.W[5 * G.ps + c + s], B.W[6 * G.ps + c + s],
+                B.W[7 * G.ps + c + s], sp);
   const float dtdx = (float)B.rec[2];
   float WsL[5], WsR[5];
   ppmc_states(wm, wc, wp, sm, sc, sp, B.W[5 * G.ps + c], B.W[6 * G.ps + c], B.W[7 * G.ps + c],
@@ -345,7 +332,6 @@ __global__ void __launch_bounds__(BS) kb_update_mixed(BatchLaunch L) {
       CALL;                                                                                 \
     }                                                                                       \
   }
-HYDRO_BATCH_MIXED(kb_slopes_mixed, 0, slopes_mixed_body<D>(it.d->G, F, box, it.t))
 HYDRO_BATCH_MIXED(kb_ppmc_mixed, 1, ppmc_mixed_body<D>(it.d->G, F, box, it.t))
 HYDRO_BATCH_MIXED(kb_riemann1_mixed, 2, riemann1_mixed_body<D>(it.d->G, F, box, it.d->gf, it.t))
 HYDRO_BATCH_MIXED(kb_riemann2_mixed, 3,
@@ -391,7 +377,7 @@ cudaError_t batch_stage_mixed(const BatchLaunch& L, int stage, int axis, int bs,
     }                                                                               \
   }
   switch (stage) {
-    case kStageSlopes: HYDRO_BATCH_MIXED_AXIS(kb_slopes_mixed) break;
+    case kStageSlopes: return cudaSuccess;  // formed inside the PPMC kernel
     case kStagePpmc: HYDRO_BATCH_MIXED_AXIS(kb_ppmc_mixed) break;
     case kStageRiemann1: HYDRO_BATCH_MIXED_AXIS(kb_riemann1_mixed) break;
     case kStageRiemann2: HYDRO_BATCH_MIXED_AXIS(kb_riemann2_mixed) break;

@@ -65,14 +65,14 @@ ALGORITHMIC_FLOPS = {
 }
 
 # The FP64 part of the mixed-precision stages, flops per unit, from the kernels'
-# own FP64 arithmetic (everything else in them is float): the transverse
-# half-step per face side builds U* (11 flops), accumulates 5 fused
-# multiply-adds per active transverse axis (10 flops) and recovers p with a
-# Newton reciprocal (13 flops); the update is 5 variables x (subtract + FMA) per
-# active axis; the primitive stage is 26 flops a padded cell.
+# own FP64 arithmetic (everything else in them is float; a fused multiply-add
+# counts 2): the primitive stage forms 1/rho by one Newton step (2 FMA),
+# |m|^2 (1 multiply + 2 FMA) and p = (gamma-1) (E - |m|^2/rho/2) (2 multiplies
+# + 1 FMA), 13 flops a padded cell; the update adds the float-float flux sum
+# to the state with 1 add + 1 FMA a variable, 15 flops a cell; the Riemann
+# stages, the reconstruction and the transverse half-step are float.
 def mixed_fp64_flops(active_axes):
-    return {"riemann2": 2 * (11 + 10 * (active_axes - 1) + 13), "update": 15 * active_axes,
-            "prims": 26}
+    return {"riemann2": 0, "riemann1": 0, "ppmc": 0, "update": 15, "prims": 13}
 
 # Algorithmic HBM bytes per unit of each stage's kernel (every plane read and
 # written once; stencil neighbours come from cache): FP64 intermediates are
@@ -86,6 +86,14 @@ ALGORITHMIC_BYTES = {
     "mixed": {"prims": 72, "slopes": 52, "ppmc": 92, "riemann1": 60, "riemann2": 100,
               "update": 140},
 }
+
+
+def mixed_bytes_per_cell_update(active_axes=3):
+    """Algorithmic HBM bytes of one mixed-precision cell update: primitives and
+    update once, reconstruction and both Riemann sets once per active axis
+    (the PPMC kernel forms its own slopes)."""
+    b = ALGORITHMIC_BYTES["mixed"]
+    return b["prims"] + b["update"] + active_axes * (b["ppmc"] + b["riemann1"] + b["riemann2"])
 
 # dram bytes (read + write) per unit of the stage's kernel from an ncu capture,
 # with the digest of the sources that kernel is built from; a digest mismatch
@@ -377,28 +385,38 @@ def main():
     dom = max((k for k in stages if stages[k][1] > 0), key=lambda k: stages[k][0])
     dms, dl, dunits = stages[dom]
     active = sum(1 for n in (nx, ny, nz) if n > 1)
-    if args.precision == "fp64":
-        table, tkey = flops_table(w["key"], args.recon, args.solver)
-        per_unit = table[dom]
-        src = "algorithmic FP64 flops per unit (oracle/count_ops.py, %s)" % tkey
-    else:
-        per_unit = mixed_fp64_flops(active)[dom]
-        src = "FP64 flops of the mixed-precision kernel per unit (by construction)"
     units_per_launch = dunits / dl
-    flops_per_launch = per_unit * units_per_launch
     avg_ms = dms / dl
-    achieved = flops_per_launch / (avg_ms / 1e3)
     traffic = None
     tinfo = NCU_TRAFFIC.get((args.precision, dom))
     if tinfo and tinfo["digest"] == source_digest(tinfo["sources"]):
         traffic = tinfo["bytes_per_unit"] * units_per_launch
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_FLOPS_PEAK,
-                "unit": "FP64 FLOP/s", "frac": achieved / FP64_FLOPS_PEAK, "traffic": traffic,
-                "kernel": ("kb_" + (args.recon if dom == "ppmc" else dom)) if args.precision == "fp64"
-                          else ("kb_%s_mixed" % dom),
-                "flops_per_unit": per_unit, "units_per_launch": units_per_launch,
-                "avg_launch_ms": avg_ms, "flops_source": src, "peak_source": PEAK_SOURCE,
-                "bytes_per_unit_algorithmic": ALGORITHMIC_BYTES[args.precision][dom]}
+    bytes_per_unit = ALGORITHMIC_BYTES[args.precision][dom]
+    if args.precision == "fp64":
+        # FP64 kernels: bound by the FP64 pipe (DRAM a few % busy)
+        table, tkey = flops_table(w["key"], args.recon, args.solver)
+        per_unit = table[dom]
+        src = "algorithmic FP64 flops per unit (oracle/count_ops.py, %s)" % tkey
+        achieved = per_unit * units_per_launch / (avg_ms / 1e3)
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_FLOPS_PEAK,
+                    "unit": "FP64 FLOP/s", "frac": achieved / FP64_FLOPS_PEAK,
+                    "traffic": traffic, "kernel": "kb_" + (args.recon if dom == "ppmc" else dom),
+                    "flops_per_unit": per_unit, "units_per_launch": units_per_launch,
+                    "avg_launch_ms": avg_ms, "flops_source": src, "peak_source": PEAK_SOURCE,
+                    "bytes_per_unit_algorithmic": bytes_per_unit}
+    else:
+        # mixed kernels: float arithmetic on a pipe 64x the FP64 rate, streaming
+        # float planes: the roofline that bounds them is HBM bandwidth
+        peak, psrc = hbm_peak_gbs()
+        achieved = bytes_per_unit * units_per_launch / (avg_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic, "kernel": "kb_%s_mixed" % dom,
+                    "bytes_per_unit_algorithmic": bytes_per_unit,
+                    "units_per_launch": units_per_launch, "avg_launch_ms": avg_ms,
+                    "bytes_source": "every plane the kernel reads or writes, once per unit",
+                    "peak_source": "%s HBM copy bandwidth (MEASURED_PEAKS.json)" % psrc
+                                   if psrc == "measured" else "fallback HBM bandwidth",
+                    "fp64_flops_per_unit": mixed_fp64_flops(active).get(dom, 0)}
     stage_report = {k: {"ms": v[0], "launches": v[1], "share": v[0] / max(ms, 1e-9)}
                     for k, v in stages.items()}
     cpu = None
@@ -514,9 +532,8 @@ def run_batch(args, w, ws, rank, local):
                                        + pu["riemann2"]) + pu["update"])
         src = "algorithmic FP64 flops per cell update (oracle/count_ops.py, Sedov sample)"
     else:
-        pu = mixed_fp64_flops(3)
-        per_cell = pu["prims"] + 3 * pu["riemann2"] + pu["update"]
-        src = "FP64 flops of the mixed-precision kernels per cell update (by construction)"
+        per_cell = mixed_bytes_per_cell_update(3)
+        src = "algorithmic HBM bytes of the mixed-precision kernels per cell update"
     achieved = per_cell * value / ws
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -529,10 +546,16 @@ def run_batch(args, w, ws, rank, local):
                    "l2": "inputs larger than L2 (states %.2f GB)" % (ncells * 40 / 1e9)},
         "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
         "hbm": hbm_report(value / ws),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_FLOPS_PEAK,
-                     "unit": "FP64 FLOP/s", "frac": achieved / FP64_FLOPS_PEAK, "traffic": None,
-                     "kernel": "whole step (graph)", "flops_per_cell_update": per_cell,
-                     "flops_source": src, "peak_source": PEAK_SOURCE},
+        "roofline": ({"bound": "alu", "achieved": achieved, "peak": FP64_FLOPS_PEAK,
+                      "unit": "FP64 FLOP/s", "frac": achieved / FP64_FLOPS_PEAK, "traffic": None,
+                      "kernel": "whole step (graph)", "flops_per_cell_update": per_cell,
+                      "flops_source": src, "peak_source": PEAK_SOURCE}
+                     if args.precision == "fp64" else
+                     {"bound": "hbm", "achieved": achieved / 1e9, "peak": hbm_peak_gbs()[0],
+                      "unit": "GB/s", "frac": achieved / 1e9 / hbm_peak_gbs()[0], "traffic": None,
+                      "kernel": "whole step (graph)", "bytes_per_cell_update": per_cell,
+                      "bytes_source": src,
+                      "peak_source": "%s HBM copy bandwidth" % hbm_peak_gbs()[1]}),
         "cpu_baseline": None,
     }
     if l1 is not None:

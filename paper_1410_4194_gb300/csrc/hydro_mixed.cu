@@ -3,13 +3,13 @@
 // Float32: the characteristic slopes, PPMC reconstruction and tracing, and both
 // sets of exact Riemann solves (App. A.2, A.3, B.1) -- the bulk of the
 // arithmetic, on GB300's FP32 pipe (64 times the FP64 rate).
+// Float, too: the transverse half-step (Eq. transverse_evolution), written for
+// the increments of the face state so that its pressure recovery has no
+// cancellation of total and kinetic energy (see half_step_side).
 // Float64, where the step's stability needs it:
 //   * primitives of the FP64 state: the internal energy E - rho v^2/2 (the
 //     cancellation of total and kinetic energy at high Mach), the pressure
 //     floor and the CFL time-step reduction;
-//   * the transverse half-step U^{n+1/2} = U* + dt/(2dx) (G*_{-} - G*_{+}) + ...
-//     (Eq. transverse_evolution), a conserved flux accumulation, and the
-//     recovery of the primitives of U^{n+1/2} (internal energy again);
 //   * the conserved update (Eq. conserved_update), accumulated from the float
 //     CTU fluxes into the FP64 state.
 // Intermediates (primitives, slopes, face states, fluxes) are float, which
@@ -23,10 +23,12 @@ namespace {
 using GasF = GasT<float>;
 using GasD = GasT<double>;
 
-// resident 256-thread blocks per SM for the stencil and Riemann stages: the
-// float kernels fit 64 registers (4 blocks, 50% of the warp slots) with a few
-// bytes of spill, which measured ~1% faster than 3 blocks at 72-80 registers
-constexpr int kMinBlocksMixed = 4;
+// resident 256-thread blocks per SM for the stencil and Riemann stages, by
+// measurement on Sedov 256^3: PPMC and the second Riemann set run best at 4
+// (64 registers; 5 and 6 blocks spill and lose 6-20%), the first Riemann set
+// at 6 (40 registers, a few bytes of spill; 14% faster than at 4: its Newton
+// iteration is a latency chain that more resident warps hide)
+constexpr int kMinBlocksPpmc = 4, kMinBlocksRiemann1 = 6, kMinBlocksRiemann2 = 4;
 
 // float views of the step's work arrays (same slab as the FP64 path)
 struct BufsF {
@@ -72,106 +74,168 @@ __device__ __forceinline__ void store_rot_f(float* __restrict__ A, long long ps,
   A[4 * ps + c] = v[4];
 }
 
-__device__ __forceinline__ void block_max_to(double v, unsigned long long* slot) {
-  __shared__ double warp_max[kThreads / 32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max_nonneg(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) warp_max[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    v = (lane < (int)(blockDim.x >> 5)) ? warp_max[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = max_nonneg(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0 && v > 0.0) atomicMax(slot, (unsigned long long)__double_as_longlong(v));
-  }
-}
+// What a cell keeps for the FP64 signal speed of the CFL condition.
+struct DtCand {
+  double m[3], p, r;  // momentum, pressure, 1/rho
+  float s;            // float estimate of max_d |v_d| + a; -1 for cells outside dt
+};
 
 // primitives in FP64 (ghosts by index remap, as in the FP64 path), stored as
-// float; dt reduction in FP64
-__device__ __forceinline__ double prims_mixed_body(const Geom& G, const BufsF& B, const BcDesc& bc,
-                                                   const GasD& g, int want_dt, long long t) {
-  double local = 0.0;
-  {
-    int c[3];
-    padded_coords(G, t, c);
-    int src[3];
-    int neg = 0, inflow_face = -1;
-    bool real = true;
+// float.  The FP64 work of a cell is 1/rho and the internal energy
+// E - |m|^2 (1/rho) / 2 (the cancellation of total and kinetic energy at high
+// Mach needs it); the velocities and the sound speed, which are stored as
+// float, are formed in float from the rounded operands (a few float ulps).
+__device__ __forceinline__ void prims_mixed_body(const Geom& G, const BufsF& B, const BcDesc& bc,
+                                                 const GasD& g, const GasF& gf, int want_dt,
+                                                 long long t, DtCand& cand) {
+  int c[3];
+  padded_coords(G, t, c);
+  int src[3];
+  int neg = 0, inflow_face = -1;
+  bool real = true;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int n = G.n[d];
-      const int r = c[d] - G.g[d];
-      if (r >= 0 && r < n) {
-        src[d] = r;
-        continue;
-      }
-      real = false;
-      const bool lo = r < 0;
-      const int depth = lo ? -r : r - n + 1;
-      const int face = 2 * d + (lo ? 0 : 1);
-      switch (bc.type[face]) {
-        case 0: src[d] = lo ? n - depth : depth - 1; break;
-        case 1: src[d] = lo ? depth - 1 : n - depth; neg |= 1 << d; break;
-        case 2: src[d] = lo ? 0 : n - 1; break;
-        default: src[d] = 0; inflow_face = face; neg = 0; break;
-      }
+  for (int d = 0; d < 3; ++d) {
+    const int n = G.n[d];
+    const int r = c[d] - G.g[d];
+    if (r >= 0 && r < n) {
+      src[d] = r;
+      continue;
     }
-    double U[5];
-    if (inflow_face >= 0) {
-#pragma unroll
-      for (int q = 0; q < 5; ++q) U[q] = bc.inflow[inflow_face][q];
-    } else {
-      const long long rs = src[0] + (long long)G.n[0] * (src[1] + (long long)G.n[1] * src[2]);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) U[q] = B.u[q * G.nreal + rs];
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      if (neg & (1 << d)) U[1 + d] = -U[1 + d];
-    // 1/rho: float reciprocal of the rounded density refined by one Newton
-    // step r <- r + r (1 - rho r) in FP64 (relative error below 2^-44)
-    const float df = d2f(U[0]);
-    const float rf = __frcp_rn(df);
-    double r = f2d(rf);
-    r = fma(r, fma(-U[0], r, 1.0), r);
-    double v[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) v[d] = U[1 + d] * r;
-    // FP64 internal energy E - (rho v) . v / 2 and the pressure floor
-    const double ke2 = U[1] * v[0] + U[2] * v[1] + U[3] * v[2];
-    const double p = vmax<false>(g.gm1 * fma(-0.5, ke2, U[4]), kPFloor);
-    // a = sqrt(gamma p / rho): float reciprocal square root of x = a^2 refined
-    // by one Newton step, a = x y (1 + (1 - x y^2)/2) (relative error ~1e-13)
-    const double x = g.gamma * p * r;
-    const double y = f2d(rsqrtf(d2f(x)));
-    const double xy = x * y;
-    const double a = fma(0.5 * xy, fma(-xy, y, 1.0), xy);
-    const float af = d2f(a);
-    B.W[t] = df;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) B.W[(1 + d) * G.ps + t] = d2f(v[d]);
-    B.W[4 * G.ps + t] = d2f(p);
-    B.W[5 * G.ps + t] = af;
-    B.W[6 * G.ps + t] = __frcp_rn(af);
-    B.W[7 * G.ps + t] = rf;
-    if (want_dt && real) {
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-        if (G.n[d] > 1) local = max_nonneg(local, fabs(v[d]) + a);
+    real = false;
+    const bool lo = r < 0;
+    const int depth = lo ? -r : r - n + 1;
+    const int face = 2 * d + (lo ? 0 : 1);
+    switch (bc.type[face]) {
+      case 0: src[d] = lo ? n - depth : depth - 1; break;
+      case 1: src[d] = lo ? depth - 1 : n - depth; neg |= 1 << d; break;
+      case 2: src[d] = lo ? 0 : n - 1; break;
+      default: src[d] = 0; inflow_face = face; neg = 0; break;
     }
   }
-  return local;
+  double U[5];
+  if (inflow_face >= 0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) U[q] = bc.inflow[inflow_face][q];
+  } else {
+    const long long rs = src[0] + (long long)G.n[0] * (src[1] + (long long)G.n[1] * src[2]);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) U[q] = B.u[q * G.nreal + rs];
+  }
+  float mf[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    mf[d] = d2f(U[1 + d]);
+    if (neg & (1 << d)) mf[d] = -mf[d];
+  }
+  // 1/rho: float reciprocal of the rounded density refined by one Newton
+  // step r <- r + r (1 - rho r) in FP64 (relative error below 2^-44)
+  const float df = d2f(U[0]);
+  const float rf = __frcp_rn(df);
+  double r = f2d(rf);
+  r = fma(r, fma(-U[0], r, 1.0), r);
+  // FP64 internal energy E - |m|^2 / (2 rho) and the pressure floor (the sign
+  // of a reflected momentum does not enter |m|^2)
+  const double m2 = fma(U[1], U[1], fma(U[2], U[2], U[3] * U[3]));
+  const double p = vmax<false>(g.gm1 * fma(-0.5 * m2, r, U[4]), kPFloor);
+  const float pf = d2f(p);
+  const float af = sqrtf(gf.gamma * pf * rf);
+  float vf[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) vf[d] = mf[d] * rf;
+  B.W[t] = df;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) B.W[(1 + d) * G.ps + t] = vf[d];
+  B.W[4 * G.ps + t] = pf;
+  B.W[5 * G.ps + t] = af;
+  B.W[6 * G.ps + t] = __frcp_rn(af);
+  B.W[7 * G.ps + t] = rf;
+  cand.s = -1.f;
+  if (want_dt && real) {
+    float m = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (G.n[d] > 1) m = fmaxf(m, fabsf(vf[d]));
+    cand.s = m + af;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) cand.m[d] = U[1 + d];
+    cand.p = p;
+    cand.r = r;
+  }
 }
 
+// FP64 signal speed max_d |v_d| + a of a cell, v = m (1/rho) and
+// a = sqrt(gamma p / rho) from a float reciprocal square root of x = a^2
+// refined by one Newton step, a = x y (1 + (1 - x y^2)/2) (relative error
+// ~1e-13).  Rounding is monotonic, so max_d |v_d| + a equals the largest of
+// the |v_d| + a.
+__device__ __forceinline__ double signal_speed_fp64(const Geom& G, const GasD& g, const DtCand& c) {
+  const double x = g.gamma * c.p * c.r;
+  const double y = f2d(rsqrtf(d2f(x)));
+  const double xy = x * y;
+  const double a = fma(0.5 * xy, fma(-xy, y, 1.0), xy);
+  double vmaxabs = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (G.n[d] > 1) vmaxabs = max_nonneg(vmaxabs, fabs(c.m[d] * c.r));
+  return vmaxabs + a;
+}
+
+// The CFL reduction: each block evaluates the FP64 signal speed of one cell,
+// the first (lowest thread) that holds the block's largest float estimate,
+// and the grid takes the largest of those.  The float estimate of a cell is
+// within 5 x 2^-24 of its FP64 value (roundings of m, p, 1/rho, gamma, the
+// products, the square root and the sum), so the time step is that of the
+// FP64 maximum to within that bound, and exactly it unless two cells' float
+// estimates tie while their FP64 values differ (a uniform region ties with
+// identical FP64 values).  A NaN estimate counts as absent, as in the FP64
+// reduction.  The choice is a maximum over 64-bit keys, the estimate's bits
+// (non-negative floats order like their bit patterns) above the complement of
+// the thread index: one warp-shuffle reduction, each warp's winner parks its
+// operands in shared memory, and a single barrier before warp 0 finishes.
 template <int BS>
 __global__ void __launch_bounds__(BS) kb_prims_mixed(BatchLaunch L) {
+  constexpr int kWarps = BS / 32;
+  __shared__ unsigned long long warp_key[kWarps];
+  __shared__ DtCand warp_cand[kWarps];
   const BatchItem it = batch_item(L);
   const Geom& G = it.d->G;
   const BufsF F = float_view(it.d->B);
   const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
-  const double local = (it.t < total) ? prims_mixed_body(G, F, it.d->bc, it.d->gd, 1, it.t) : 0.0;
-  block_max_to(local, reinterpret_cast<unsigned long long*>(F.rec));
+  DtCand cand;
+  cand.s = -1.f;
+  if (it.t < total) prims_mixed_body(G, F, it.d->bc, it.d->gd, it.d->gf, 1, it.t, cand);
+  const unsigned long long key =
+      (cand.s >= 0.f) ? ((unsigned long long)__float_as_uint(cand.s) << 32) | (~threadIdx.x & 0xffffffffu)
+                      : 0ull;
+  unsigned long long wk = key;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(0xffffffffu, wk, o);
+    wk = other > wk ? other : wk;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (key != 0ull && key == wk) {  // the warp's winner (keys are distinct)
+    warp_key[wid] = wk;
+    warp_cand[wid] = cand;
+  } else if (wk == 0ull && lane == 0) {
+    warp_key[wid] = 0ull;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned long long k = lane < kWarps ? warp_key[lane] : 0ull;
+    unsigned long long bk = k;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(0xffffffffu, bk, o);
+      bk = other > bk ? other : bk;
+    }
+    if (bk != 0ull && k == bk) {
+      const double sp = signal_speed_fp64(G, it.d->gd, warp_cand[lane]);
+      if (sp > 0.0)
+        atomicMax(reinterpret_cast<unsigned long long*>(F.rec),
+                  (unsigned long long)__double_as_longlong(sp));
+    }
+  }
 }
 
 template <int D>
@@ -221,97 +285,131 @@ __device__ __forceinline__ void riemann1_mixed_body(const Geom& G, const BufsF& 
 
 // One side of a face at the transverse half-step (Eq. transverse_evolution):
 // U^{n+1/2} = U* + h (G*(c) - G*(c + e_t1)) + h (H*(c) - H*(c + e_t2)), h =
-// dt/(2 dx), accumulated in FP64 from the float face state W* (converted
-// exactly to U*: rho v is an exact product of two floats, E from p/(gamma-1)
-// and the kinetic energy) and the float flux differences, then the FP64
-// recovery of its primitives: internal energy E - |m|^2/(2 rho) with 1/rho from
-// a float seed and one Newton step (relative error below 2^-44).  The float
-// difference of two float fluxes has the rounding error of the fluxes
-// themselves.  Returns the primitives in sweep order and 1/rho, in float.
+// dt/(2 dx), in float, written for the increments dU = (d rho, d m, d E) so
+// that no total or kinetic energy of the state is ever formed.  With v the
+// velocity of the face state W*, rho' = rho + d rho and q = d m - v d rho:
+//   v' = v + q / rho'
+//   p' = p + (gamma - 1) (dE - v.q - |v|^2 d rho / 2 - |q|^2 / (2 rho'))
+// which is the primitive recovery of U* + dU rearranged exactly (the kinetic
+// energy |m'|^2 / (2 rho') expanded about |m|^2 / (2 rho)).  The internal
+// energy is then never the small difference of two large energies: every term
+// is an increment of the size of the flux differences, whose float rounding
+// (the fluxes are float) already bounds the result's accuracy.  Returns the
+// primitives in sweep order and 1/rho', in float.
 template <int D>
 __device__ __forceinline__ void half_step_side(const Geom& G, const BufsF& B, const float* __restrict__ Ws,
-                                               long long f, long long c, double h, const GasD& gd,
+                                               long long f, long long c, float h, const GasF& g,
                                                float w[5], float& inv_d) {
   const long long ps = G.ps;
-  double U[5];
-  {
-    const double d = f2d(Ws[f]);
-    double v[3];
+  const float d = Ws[f];
+  float v[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      v[i] = f2d(Ws[(1 + i) * ps + f]);
-      U[1 + i] = d * v[i];
-    }
-    const double ke2 = U[1] * v[0] + U[2] * v[1] + U[3] * v[2];
-    U[0] = d;
-    U[4] = fma(0.5, ke2, f2d(Ws[4 * ps + f]) * gd.inv_gm1);
-  }
+  for (int i = 0; i < 3; ++i) v[i] = Ws[(1 + i) * ps + f];
+  const float p = Ws[4 * ps + f];
+  float dU[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   constexpr int T1 = Perm<D>::t1, T2 = Perm<D>::t2;
   if (G.n[T1] > 1) {
     const float* F = B.F1[T1];
     const long long st = G.s[T1];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) U[q] = fma(h, f2d(F[q * ps + c] - F[q * ps + c + st]), U[q]);
+    for (int q = 0; q < 5; ++q) dU[q] = h * (F[q * ps + c] - F[q * ps + c + st]);
   }
   if (G.n[T2] > 1) {
     const float* F = B.F1[T2];
     const long long st = G.s[T2];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) U[q] = fma(h, f2d(F[q * ps + c] - F[q * ps + c + st]), U[q]);
+    for (int q = 0; q < 5; ++q) dU[q] = fmaf(h, F[q * ps + c] - F[q * ps + c + st], dU[q]);
   }
-  const float df = d2f(U[0]);
-  const float rf = __frcp_rn(df);
-  double r = f2d(rf);
-  r = fma(r, fma(-U[0], r, 1.0), r);
-  const double m2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
-  const double p = gd.gm1 * fma(-0.5 * m2, r, U[4]);
-  // the floor applied to the rounded pressure equals the rounded floored
-  // pressure: rounding is monotonic, so it commutes with the maximum
-  w[0] = df;
-  w[1] = d2f(U[1 + D]) * rf;
-  w[2] = d2f(U[1 + T1]) * rf;
-  w[3] = d2f(U[1 + T2]) * rf;
-  w[4] = tmax(d2f(p), (float)kPFloor);
-  inv_d = rf;
+  const float dn = d + dU[0];
+  const float rn = __frcp_rn(dn);
+  float qv[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) qv[i] = fmaf(-v[i], dU[0], dU[1 + i]);
+  const float vq = fmaf(v[0], qv[0], fmaf(v[1], qv[1], v[2] * qv[2]));
+  const float v2 = fmaf(v[0], v[0], fmaf(v[1], v[1], v[2] * v[2]));
+  const float q2 = fmaf(qv[0], qv[0], fmaf(qv[1], qv[1], qv[2] * qv[2]));
+  const float de = dU[4] - vq - 0.5f * fmaf(v2, dU[0], q2 * rn);
+  w[0] = dn;
+  w[1] = fmaf(qv[D], rn, v[D]);
+  w[2] = fmaf(qv[T1], rn, v[T1]);
+  w[3] = fmaf(qv[T2], rn, v[T2]);
+  w[4] = tmax(fmaf(g.gm1, de, p), (float)kPFloor);
+  inv_d = rn;
 }
 
-// transverse half-step in FP64, second Riemann solve in float
+// transverse half-step and second Riemann solve, all in float
 template <int D>
-__device__ __forceinline__ void riemann2_mixed_body(const Geom& G, const BufsF& B, const Box& box, const GasD& gd, const GasF& g,
+__device__ __forceinline__ void riemann2_mixed_body(const Geom& G, const BufsF& B, const Box& box, const GasF& g,
     long long t) {
   int c3[3];
   box_coords(box, t, c3);
   const long long f = pidx(G, c3);
-  const double h = B.rec[3];
+  const float h = (float)B.rec[3];
   float wl[5], wr[5], idL, idR, Fx[5];
-  half_step_side<D>(G, B, B.UL[D], f, f - G.s[D], h, gd, wl, idL);
-  half_step_side<D>(G, B, B.UR[D], f, f, h, gd, wr, idR);
+  half_step_side<D>(G, B, B.UL[D], f, f - G.s[D], h, g, wl, idL);
+  half_step_side<D>(G, B, B.UR[D], f, f, h, g, wr, idR);
   const int fl = riemann_exact(wl, wr, idL, idR, g, Fx);
   store_rot_f<D>(B.UL[D], G.ps, f, Fx);
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
 
-// conserved update in FP64 from the float CTU fluxes
+// a + b as an unevaluated sum s + e of two floats, exactly (Knuth's TwoSum,
+// round-to-nearest without overflow)
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+  return s;
+}
+
+// conserved update in FP64 from the float CTU fluxes.  Per variable the flux
+// differences of the active axes are summed in float-float arithmetic: each
+// difference F(c) - F(c + e_d) is an exact pair, the pairs are added with
+// TwoSum into hi + lo, and only the low-order remainders (each below 2^-24 of
+// the value it came from) are rounded, to float, so hi + lo carries the sum to
+// within about 2^-45 of the largest difference.  Two FP64 operations then
+// apply it:
+// u + dt/dx (hi + lo).  Neighbour cells see the same float flux with opposite
+// sign, so the step conserves to FP64 rounding.
 __device__ __forceinline__ void update_mixed_body(const Geom& G, const BufsF& B, long long t) {
   const long long c = real_to_padded(G, t);
   const double dtdx = B.rec[2];
+  // every load is issued before the first store (the state and the flux
+  // planes are distinct arrays), so that a thread has all 35 in flight
+  double u[5];
+  float fc[3][5], fn[3][5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) u[q] = B.u[q * G.nreal + t];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const bool on = G.n[d] > 1;
+    const float* __restrict__ F = B.UL[d];
+    const long long cn = c + G.s[d];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      fc[d][q] = on ? __ldg(F + q * G.ps + c) : 0.f;
+      fn[d][q] = on ? __ldg(F + q * G.ps + cn) : 0.f;
+    }
+  }
   int fl = 0;
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    double un = B.u[q * G.nreal + t];
+    float hi = 0.f, lo = 0.f;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      if (G.n[d] > 1) {
-        const float* F = B.UL[d];
-        un = un + dtdx * (f2d(F[q * G.ps + c]) - f2d(F[q * G.ps + c + G.s[d]]));
-      }
+      float e1, e2;
+      const float s = two_sum(fc[d][q], -fn[d][q], e1);
+      hi = two_sum(hi, s, e2);
+      lo += e1 + e2;
     }
-    B.u[q * G.nreal + t] = un;
-    const long long b = __double_as_longlong(un);
+    u[q] = fma(dtdx, f2d(hi) + f2d(lo), u[q]);
+    const long long b = __double_as_longlong(u[q]);
     if ((b & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) fl = kFlagNonPhys;  // NaN
     if (q == 0 && b <= 0) fl = kFlagNonPhys;  // rho <= 0 (or a NaN with the sign bit)
   }
+#pragma unroll
+  for (int q = 0; q < 5; ++q) B.u[q * G.nreal + t] = u[q];
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
@@ -322,9 +420,9 @@ __global__ void __launch_bounds__(BS) kb_update_mixed(BatchLaunch L) {
   if (it.t < it.d->G.nreal) update_mixed_body(it.d->G, float_view(it.d->B), it.t);
 }
 
-#define HYDRO_BATCH_MIXED(NAME, STAGE_IDX, CALL)                                           \
+#define HYDRO_BATCH_MIXED(NAME, STAGE_IDX, MINB, CALL)                                     \
   template <int D, int BS>                                                                  \
-  __global__ void __launch_bounds__(BS, kMinBlocksMixed * kThreads / BS) NAME(BatchLaunch L) {  \
+  __global__ void __launch_bounds__(BS, MINB * kThreads / BS) NAME(BatchLaunch L) {         \
     const BatchItem it = batch_item(L);                                                     \
     const Box& box = it.d->box[STAGE_IDX][D];                                               \
     if (it.t < (long long)box.n[0] * box.n[1] * box.n[2]) {                                 \
@@ -332,10 +430,11 @@ __global__ void __launch_bounds__(BS) kb_update_mixed(BatchLaunch L) {
       CALL;                                                                                 \
     }                                                                                       \
   }
-HYDRO_BATCH_MIXED(kb_ppmc_mixed, 1, ppmc_mixed_body<D>(it.d->G, F, box, it.t))
-HYDRO_BATCH_MIXED(kb_riemann1_mixed, 2, riemann1_mixed_body<D>(it.d->G, F, box, it.d->gf, it.t))
-HYDRO_BATCH_MIXED(kb_riemann2_mixed, 3,
-                  riemann2_mixed_body<D>(it.d->G, F, box, it.d->gd, it.d->gf, it.t))
+HYDRO_BATCH_MIXED(kb_ppmc_mixed, 1, kMinBlocksPpmc, ppmc_mixed_body<D>(it.d->G, F, box, it.t))
+HYDRO_BATCH_MIXED(kb_riemann1_mixed, 2, kMinBlocksRiemann1,
+                  riemann1_mixed_body<D>(it.d->G, F, box, it.d->gf, it.t))
+HYDRO_BATCH_MIXED(kb_riemann2_mixed, 3, kMinBlocksRiemann2,
+                  riemann2_mixed_body<D>(it.d->G, F, box, it.d->gf, it.t))
 #undef HYDRO_BATCH_MIXED
 
 

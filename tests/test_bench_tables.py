@@ -20,9 +20,15 @@ def test_flop_table_matches_counting_oracle(name):
         assert table[stage] == pytest.approx(v, abs=1e-3), stage
 
 
-def test_mixed_fp64_flops_by_construction():
+def test_mixed_tables_by_construction():
+    """Mixed precision: FP64 only in the primitives (13 flops) and the update
+    (15); the step's algorithmic HBM bytes per cell update add up the stages'."""
     sys.path.insert(0, ROOT)
     import bench
     f3 = bench.mixed_fp64_flops(3)
-    assert f3["riemann2"] == 88 and f3["update"] == 45
-    assert bench.mixed_fp64_flops(1)["riemann2"] == 48
+    assert f3["riemann2"] == 0 and f3["update"] == 15 and f3["prims"] == 13
+    b = bench.ALGORITHMIC_BYTES["mixed"]
+    assert bench.mixed_bytes_per_cell_update(3) == (b["prims"] + b["update"]
+                                                    + 3 * (b["ppmc"] + b["riemann1"]
+                                                           + b["riemann2"]))
+    assert bench.mixed_bytes_per_cell_update(3) == 968

@@ -79,11 +79,12 @@ def mixed_fp64_flops(active_axes):
 # 8-byte planes, the mixed path's 4-byte ones.  prims: 5 conserved in, 8
 # primitive planes out; slopes: 8 in, 5 out; ppmc: 8 + 5 in, 10 face states out;
 # riemann1: 10 in, 5 out; riemann2: 10 face states + 2 x 5 transverse fluxes in,
-# 5 out; update: 5 conserved + 3 x 5 fluxes in, 5 out.
+# 5 out; update: 5 conserved + 3 x 5 fluxes in, 5 out.  The mixed PPMC kernel
+# forms its slopes itself: 8 in, 10 out (the mixed path launches no slope pass).
 ALGORITHMIC_BYTES = {
     "fp64": {"prims": 104, "slopes": 104, "ppmc": 184, "riemann1": 120, "riemann2": 200,
              "update": 200},
-    "mixed": {"prims": 72, "slopes": 52, "ppmc": 92, "riemann1": 60, "riemann2": 100,
+    "mixed": {"prims": 72, "slopes": 52, "ppmc": 72, "riemann1": 60, "riemann2": 100,
               "update": 140},
 }
 
@@ -98,18 +99,32 @@ def mixed_bytes_per_cell_update(active_axes=3):
 # dram bytes (read + write) per unit of the stage's kernel from an ncu capture,
 # with the digest of the sources that kernel is built from; a digest mismatch
 # (the kernel changed since the capture) reports null.  Captured on Sedov 160^3
-# (kb_riemann2 along x: 161 x 160 x 160 faces; the 256^3 launch exceeds the
-# capture size rule) and scaled by the units of a launch: these kernels stream
-# each plane once, so traffic grows in proportion to the faces.
+# (the 256^3 launches exceed the capture size rule) and scaled by the units of
+# a launch: these kernels stream each plane once, so traffic grows in
+# proportion to the units.  Units at 160^3: riemann2 161 x 160 x 160 faces,
+# riemann1 161 x 162 x 162 faces, ppmc 162^3 cells, slopes 164 x 162 x 162
+# cells, prims 168^3 padded cells, update 160^3 cells.
+_FP64_SRC = ["hydro_fp64_fast.cu", "hydro_internal.h", "hydro_kernels.cuh", "hydro_math.cuh"]
+_MIXED_SRC = ["hydro_internal.h", "hydro_kernels.cuh", "hydro_math.cuh", "hydro_mixed.cu"]
 NCU_TRAFFIC = {
-    ("fp64", "riemann2"): {
-        "bytes_per_unit": 204.02, "digest": "2c6352daa30c4b04",
-        "sources": ["hydro_fp64_fast.cu", "hydro_internal.h", "hydro_kernels.cuh",
-                    "hydro_math.cuh"]},
-    ("mixed", "riemann2"): {
-        "bytes_per_unit": 99.69, "digest": "707053dd22a499c3",
-        "sources": ["hydro_internal.h", "hydro_kernels.cuh", "hydro_math.cuh",
-                    "hydro_mixed.cu"]},
+    ("fp64", "riemann2"): {"bytes_per_unit": 203.85, "digest": "b89405610eea912d",
+                           "sources": _FP64_SRC},
+    ("fp64", "ppmc"): {"bytes_per_unit": 185.72, "digest": "b89405610eea912d",
+                       "sources": _FP64_SRC},
+    ("fp64", "riemann1"): {"bytes_per_unit": 118.19, "digest": "b89405610eea912d",
+                           "sources": _FP64_SRC},
+    ("fp64", "slopes"): {"bytes_per_unit": 99.60, "digest": "b89405610eea912d",
+                         "sources": _FP64_SRC},
+    ("mixed", "riemann2"): {"bytes_per_unit": 99.64, "digest": "c4c3bc5303cc45fd",
+                            "sources": _MIXED_SRC},
+    ("mixed", "update"): {"bytes_per_unit": 135.80, "digest": "c4c3bc5303cc45fd",
+                          "sources": _MIXED_SRC},
+    ("mixed", "ppmc"): {"bytes_per_unit": 66.16, "digest": "c4c3bc5303cc45fd",
+                        "sources": _MIXED_SRC},
+    ("mixed", "riemann1"): {"bytes_per_unit": 57.41, "digest": "c4c3bc5303cc45fd",
+                            "sources": _MIXED_SRC},
+    ("mixed", "prims"): {"bytes_per_unit": 59.68, "digest": "c4c3bc5303cc45fd",
+                         "sources": _MIXED_SRC},
 }
 
 

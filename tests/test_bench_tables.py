@@ -31,4 +31,15 @@ def test_mixed_tables_by_construction():
     assert bench.mixed_bytes_per_cell_update(3) == (b["prims"] + b["update"]
                                                     + 3 * (b["ppmc"] + b["riemann1"]
                                                            + b["riemann2"]))
-    assert bench.mixed_bytes_per_cell_update(3) == 968
+    assert bench.mixed_bytes_per_cell_update(3) == 908
+
+
+def test_ncu_traffic_table_is_consistent():
+    """Each captured per-unit DRAM traffic sits just below the stage's
+    algorithmic bytes (nothing re-read; part of the last writes still in L2
+    when a kernel ends), and names the sources its digest covers."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for key, info in bench.NCU_TRAFFIC.items():
+        assert 0.75 < info["bytes_per_unit"] / bench.ALGORITHMIC_BYTES[key[0]][key[1]] < 1.05, key
+        assert len(bench.source_digest(info["sources"])) == 16

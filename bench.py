@@ -402,9 +402,22 @@ def main():
     active = sum(1 for n in (nx, ny, nz) if n > 1)
     units_per_launch = dunits / dl
     avg_ms = dms / dl
+    # the dominant stage's kernel: the reconstruction stage runs the selected
+    # reconstruction's kernel, the Riemann stages the Roe kernels with --solver roe
+    if args.precision == "mixed":
+        kname = "kb_%s_mixed" % dom
+    elif dom == "ppmc":
+        kname = "kb_" + args.recon
+    elif dom in ("riemann1", "riemann2") and args.solver == "roe":
+        kname = "kb_%s_roe" % dom
+    else:
+        kname = "kb_" + dom
+    # captured traffic applies to the kernels captured (PPMC + exact solver, 3D
+    # grids: a 1D or 2D face carries no or fewer transverse terms)
     traffic = None
     tinfo = NCU_TRAFFIC.get((args.precision, dom))
-    if tinfo and tinfo["digest"] == source_digest(tinfo["sources"]):
+    if (tinfo and active == 3 and args.recon == "ppmc" and args.solver == "exact"
+            and tinfo["digest"] == source_digest(tinfo["sources"])):
         traffic = tinfo["bytes_per_unit"] * units_per_launch
     bytes_per_unit = ALGORITHMIC_BYTES[args.precision][dom]
     if args.precision == "fp64":
@@ -415,7 +428,7 @@ def main():
         achieved = per_unit * units_per_launch / (avg_ms / 1e3)
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_FLOPS_PEAK,
                     "unit": "FP64 FLOP/s", "frac": achieved / FP64_FLOPS_PEAK,
-                    "traffic": traffic, "kernel": "kb_" + (args.recon if dom == "ppmc" else dom),
+                    "traffic": traffic, "kernel": kname,
                     "flops_per_unit": per_unit, "units_per_launch": units_per_launch,
                     "avg_launch_ms": avg_ms, "flops_source": src, "peak_source": PEAK_SOURCE,
                     "bytes_per_unit_algorithmic": bytes_per_unit}
@@ -425,7 +438,7 @@ def main():
         peak, psrc = hbm_peak_gbs()
         achieved = bytes_per_unit * units_per_launch / (avg_ms / 1e3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": traffic, "kernel": "kb_%s_mixed" % dom,
+                    "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                     "bytes_per_unit_algorithmic": bytes_per_unit,
                     "units_per_launch": units_per_launch, "avg_launch_ms": avg_ms,
                     "bytes_source": "every plane the kernel reads or writes, once per unit",

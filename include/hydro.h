@@ -50,9 +50,11 @@ enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_REFLECT = 1, HYDRO_BC_OUTFLOW = 2, HYDRO_
  *   evaluated through exact algebraic identities (k-th roots in place of pow,
  *   reciprocals in place of divisions), each result within a few ulp of the
  *   formula as printed.
- * HYDRO_MIXED: reconstruction and Riemann solves in float32; the conserved
- *   update (flux accumulation), the recovery of the internal energy from E minus
- *   the kinetic energy, the positivity floors and the time step stay float64.
+ * HYDRO_MIXED: reconstruction, Riemann solves and the transverse half-step
+ *   (written for the increments of the face states, so that its pressure
+ *   recovery has no cancellation) in float32; the conserved update (flux
+ *   accumulation), the recovery of the internal energy from E minus the kinetic
+ *   energy, the positivity floors and the time step stay float64.
  * HYDRO_FP64_STRICT: float64 with every formula evaluated operation by
  *   operation as printed (divisions, pow, conserved face states between the
  *   reconstruction and the Riemann solver as in App. B.1), for bit-level

@@ -1,7 +1,7 @@
 """Mixed precision (HYDRO_MIXED) against the FP64 oracle.
 
-Float32 reconstruction and Riemann solves; float64 internal-energy recovery,
-floors, dt, transverse accumulation and conserved update.  The bar (north
+Float32 reconstruction, Riemann solves and transverse half-step; float64
+internal-energy recovery, floors, dt and conserved update.  The bar (north
 star): the relative L1 difference of density, sum |rho_mixed - rho_oracle| /
 sum |rho_oracle|, at most 1e-5; the other fields are reported and held to the
 same bar relative to their variable's scale.  Conservation stays at FP64

@@ -69,8 +69,57 @@ def test_mixed_l1_vs_oracle(name):
     assert np.all(l1 <= 1e-5), l1
 
 
-def test_mixed_conserves_to_fp64_rounding():
-    w = W.turbulence(32, kmax=1)
+def signal_speed_dt(u, dx, gamma, cfl, active=(0, 1, 2)):
+    """CFL time step of a conserved state written out in numpy float64:
+    cfl dx / max over cells and active axes of |v_d| + a."""
+    rho = u[0]
+    v = u[1:4] / rho
+    p = np.maximum((gamma - 1) * (u[4] - 0.5 * (u[1] * v[0] + u[2] * v[1] + u[3] * v[2])), 1e-20)
+    a = np.sqrt(gamma * p / rho)
+    s = max((np.abs(v[d]) + a).max() for d in active)
+    return cfl * dx / s
+
+
+def dt_cases():
+    rng = np.random.Generator(np.random.PCG64(91))
+    # a near-uniform state: signal speeds differ by ~1e-9 relative, so most
+    # float estimates tie while their FP64 values differ (the documented case)
+    shape = (16, 16, 16)
+    rho = 1.0 + 1e-9 * rng.standard_normal(shape)
+    vx = 0.3 + 1e-9 * rng.standard_normal(shape)
+    near = dict(u=W.prim_to_cons(rho, vx, 0.0, 0.0, np.ones(shape), 1.4), dx=1 / 16, gamma=1.4,
+                bc=[0] * 6)
+    return {"sedov32": W.sedov(32), "turb32": W.turbulence(32, kmax=1),
+            "cloud": cases()["shock_cloud_small"], "near_uniform": near}
+
+
+@pytest.mark.parametrize("name", ["sedov32", "turb32", "cloud", "near_uniform"])
+def test_mixed_dt_is_the_fp64_cfl_step(name):
+    """The mixed path's CFL reduction picks each block's cell by a float
+    estimate and evaluates that cell in FP64: its time step is the FP64 one to
+    ~1e-13, and within 5 x 2^-24 where float estimates tie (near_uniform)."""
+    w = dt_cases()[name]
+    _, nz, ny, nx = w["u"].shape
+    dts = []
+    for prec in (hydro.HYDRO_FP64, hydro.HYDRO_MIXED):
+        g = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], precision=prec)
+        try:
+            for face, prim in (w.get("inflow") or {}).items():
+                g.set_inflow(face, prim)
+            g.set_state(w["u"])
+            dts.append(g.compute_dt(0.3))
+        finally:
+            g.close()
+    active = tuple(d for d, n in enumerate((nx, ny, nz)) if n > 1)
+    ref = signal_speed_dt(w["u"], w["dx"], w["gamma"], 0.3, active)
+    assert abs(dts[0] / ref - 1) < 1e-13
+    tol = 5 * 2.0 ** -24 if name == "near_uniform" else 1e-13
+    assert abs(dts[1] / ref - 1) < tol, (dts, ref)
+
+
+@pytest.mark.parametrize("name", ["turb32", "sedov32"])
+def test_mixed_conserves_to_fp64_rounding(name):
+    w = W.turbulence(32, kmax=1) if name == "turb32" else W.sedov(32)
     um, tm, nm = hydro.run(w["u"], w["dx"], w["gamma"], w["bc"], nsteps=10, cfl=0.3,
                            precision=hydro.HYDRO_MIXED)
     tot0 = w["u"].reshape(5, -1).sum(axis=1)

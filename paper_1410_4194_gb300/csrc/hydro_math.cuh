@@ -238,8 +238,11 @@ __device__ __forceinline__ float d2f(double x) {
 //   rsqrt        y <- y + (y/2)(1 - x y^2), twice.
 // Results are within an ulp or two of the correctly rounded value for
 // positive normal operands (the only ones the solver passes); zero, infinite
-// and NaN operands are not handled.  The float overloads are the IEEE float
-// operations.
+// and NaN operands are not handled.  The float overloads (mixed precision) are
+// the SFU approximations rcp/sqrt/rsqrt.approx and the approximate quotient
+// a * rcp(b), each within about two ulp, in place of the IEEE-rounded
+// operations' multi-instruction sequences: the mixed path's accuracy bar is an
+// L1 difference of 1e-5 to FP64, four hundred times the float ulp.
 __device__ __forceinline__ double rcp_seed(double b) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
@@ -276,10 +279,22 @@ __device__ __forceinline__ double nr_rsqrt(double x) {
   y = fma(0.5 * y, fma(-x * y, y, 1.0), y);
   return fma(0.5 * y, fma(-x * y, y, 1.0), y);
 }
-__device__ __forceinline__ float nr_rcp(float b) { return 1.0f / b; }
-__device__ __forceinline__ float nr_div(float a, float b) { return a / b; }
-__device__ __forceinline__ float nr_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ float nr_rsqrt(float x) { return 1.0f / sqrtf(x); }
+__device__ __forceinline__ float nr_rcp(float b) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+  return r;
+}
+__device__ __forceinline__ float nr_div(float a, float b) { return a * nr_rcp(b); }
+__device__ __forceinline__ float nr_sqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float nr_rsqrt(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 // x^K by squaring (K is small)
 template <int K, typename T>
@@ -1081,16 +1096,10 @@ __device__ __forceinline__ void side_f(T p, T inv_p, const RSide<T>& s, const Ga
       f = (p - s.p) * q;
       fd = q * (T(1) - (p - s.p) / (T(2) * (s.B + p)));
     } else {
-      // double: q = sqrt(A/(p+B)) as the reciprocal square root of (p+B)/A,
-      // then 1/(p+B) = q^2/A
-      T q, ipb;
-      if constexpr (sizeof(T) == 8) {
-        q = nr_rsqrt((p + s.B) * s.inv_A);
-        ipb = q * q * s.inv_A;
-      } else {
-        ipb = T(1) / (p + s.B);
-        q = xsqrt(s.A * ipb);
-      }
+      // q = sqrt(A/(p+B)) as the reciprocal square root of (p+B)/A, then
+      // 1/(p+B) = q^2/A
+      const T q = nr_rsqrt((p + s.B) * s.inv_A);
+      const T ipb = q * q * s.inv_A;
       const T dp = p - s.p;
       f = dp * q;
       fd = q * (T(1) - T(0.5) * dp * ipb);
@@ -1109,7 +1118,7 @@ __device__ __forceinline__ void side_f_only(T p, const RSide<T>& s, const GasT<T
       f = s.cf * (x - T(1));
     }
   } else {
-    if constexpr (!S && sizeof(T) == 8)
+    if constexpr (!S)
       f = (p - s.p) * nr_rsqrt((p + s.B) * s.inv_A);
     else
       f = (p - s.p) * xsqrt(s.A / (p + s.B));
@@ -1200,7 +1209,7 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
   T pt = T(0.5) * (L.p + R.p) + T(0.125) * (L.u - R.u) * (L.d + R.d) * (L.a + R.a);
   if (neg<S>(pt)) pt = T(0);
   T gL, gR, p;
-  if constexpr (!S && sizeof(T) == 8) {
+  if constexpr (!S) {
     gL = nr_rsqrt((pt + L.B) * L.inv_A);
     gR = nr_rsqrt((pt + R.B) * R.inv_A);
     p = nr_div(gL * L.p + gR * R.p - (R.u - L.u), gL + gR);

@@ -184,10 +184,10 @@ __device__ __forceinline__ double signal_speed_fp64(const Geom& G, const GasD& g
 // the first (lowest thread) that holds the block's largest float estimate,
 // and the grid takes the largest of those.  The float estimate of a cell is
 // within 5 x 2^-24 of its FP64 value (roundings of m, p, 1/rho, gamma, the
-// products, the square root and the sum), so the time step is that of the
-// FP64 maximum to within that bound, and exactly it unless two cells' float
-// estimates tie while their FP64 values differ (a uniform region ties with
-// identical FP64 values).  A NaN estimate counts as absent, as in the FP64
+// products, the square root and the sum), so the chosen cell's FP64 signal
+// speed is within 10 x 2^-24 of the FP64 maximum, and is it exactly unless two
+// cells' float estimates tie while their FP64 values differ (a uniform region
+// ties with identical FP64 values).  A NaN estimate counts as absent, as in the FP64
 // reduction.  The choice is a maximum over 64-bit keys, the estimate's bits
 // (non-negative floats order like their bit patterns) above the complement of
 // the thread index: one warp-shuffle reduction, each warp's winner parks its
@@ -277,7 +277,7 @@ __device__ __forceinline__ void riemann1_mixed_body(const Geom& G, const BufsF& 
   float WL[5], WR[5], F[5];
   load_prim_f<D>(B.UL[D], G.ps, f, WL);
   load_prim_f<D>(B.UR[D], G.ps, f, WR);
-  const int fl = riemann_exact(WL, WR, 1.0f / WL[0], 1.0f / WR[0], g, F);
+  const int fl = riemann_exact(WL, WR, nr_rcp(WL[0]), nr_rcp(WR[0]), g, F);
   store_rot_f<D>(B.F1[D], G.ps, f, F);
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
@@ -321,7 +321,7 @@ __device__ __forceinline__ void half_step_side(const Geom& G, const BufsF& B, co
     for (int q = 0; q < 5; ++q) dU[q] = fmaf(h, F[q * ps + c] - F[q * ps + c + st], dU[q]);
   }
   const float dn = d + dU[0];
-  const float rn = __frcp_rn(dn);
+  const float rn = nr_rcp(dn);
   float qv[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) qv[i] = fmaf(-v[i], dU[0], dU[1 + i]);

@@ -97,7 +97,7 @@ def dt_cases():
 def test_mixed_dt_is_the_fp64_cfl_step(name):
     """The mixed path's CFL reduction picks each block's cell by a float
     estimate and evaluates that cell in FP64: its time step is the FP64 one to
-    ~1e-13, and within 5 x 2^-24 where float estimates tie (near_uniform)."""
+    ~1e-13, and within 10 x 2^-24 where float estimates tie (near_uniform)."""
     w = dt_cases()[name]
     _, nz, ny, nx = w["u"].shape
     dts = []
@@ -113,7 +113,7 @@ def test_mixed_dt_is_the_fp64_cfl_step(name):
     active = tuple(d for d, n in enumerate((nx, ny, nz)) if n > 1)
     ref = signal_speed_dt(w["u"], w["dx"], w["gamma"], 0.3, active)
     assert abs(dts[0] / ref - 1) < 1e-13
-    tol = 5 * 2.0 ** -24 if name == "near_uniform" else 1e-13
+    tol = 10 * 2.0 ** -24 if name == "near_uniform" else 1e-13
     assert abs(dts[1] / ref - 1) < tol, (dts, ref)
 
 

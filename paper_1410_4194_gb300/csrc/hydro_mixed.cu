@@ -30,48 +30,95 @@ using GasD = GasT<double>;
 // iteration is a latency chain that more resident warps hide)
 constexpr int kMinBlocksPpmc = 4, kMinBlocksRiemann1 = 6, kMinBlocksRiemann2 = 4;
 
-// float views of the step's work arrays (same slab as the FP64 path)
+// A five-value face quantity (a primitive state or a flux, x/y/z components
+// in axis order) in vector form: values 0-3 in one float4 plane, value 4 in
+// one float plane.  A thread moves a face with one 16-byte and one 4-byte
+// access, each coalesced across its warp, instead of five 4-byte ones.
+struct Face5 {
+  float4* v;
+  float* e;
+};
+// The primitives of a padded cell as two float4 planes: (rho, vx, vy, vz) and
+// (p, a, 1/a, 1/rho).
+struct Prim8 {
+  float4* a;
+  float4* b;
+};
+
+// float views of the step's work arrays, carved from the same slab as the
+// FP64 path (each FP64 array has room for its float vector form)
 struct BufsF {
   double* u;      // FP64 state, real cells [5][nz][ny][nx]
-  float* W;       // padded primitives [8][ps]: rho, vx, vy, vz, p, a, 1/a, 1/rho
-  float* S;       // padded slopes [5][ps] (sweep order)
-  float* UL[3];   // per axis: primitive left states W*_L [5][ps]; then F^{n+1/2}
-  float* UR[3];   // per axis: primitive right states W*_R [5][ps]
-  float* F1[3];   // per axis: first fluxes F* [5][ps]
+  Prim8 W;        // padded primitives
+  Face5 UL[3];    // per axis: left states W*_L of the faces; then F^{n+1/2}
+  Face5 UR[3];    // per axis: right states W*_R of the faces
+  Face5 F1[3];    // per axis: first fluxes F*
   double* rec;    // step record (dt, flags)
 };
 
-__host__ __device__ inline BufsF float_view(const Bufs& B) {
+__host__ __device__ inline Face5 face_view(double* base, long long ps) {
+  Face5 f;
+  f.v = reinterpret_cast<float4*>(base);
+  f.e = base ? reinterpret_cast<float*>(f.v + ps) : nullptr;
+  return f;
+}
+
+__host__ __device__ inline BufsF float_view(const Bufs& B, long long ps) {
   BufsF F;
   F.u = B.u;
-  F.W = reinterpret_cast<float*>(B.W);
-  F.S = reinterpret_cast<float*>(B.S);
+  F.W.a = reinterpret_cast<float4*>(B.W);
+  F.W.b = F.W.a + ps;
   for (int d = 0; d < 3; ++d) {
-    F.UL[d] = reinterpret_cast<float*>(B.UL[d]);
-    F.UR[d] = reinterpret_cast<float*>(B.UR[d]);
-    F.F1[d] = reinterpret_cast<float*>(B.F1[d]);
+    F.UL[d] = face_view(B.UL[d], ps);
+    F.UR[d] = face_view(B.UR[d], ps);
+    F.F1[d] = face_view(B.F1[d], ps);
   }
   F.rec = B.rec;
   return F;
 }
 
+// the primitives of cell c in sweep order, and a, 1/a, 1/rho
 template <int D>
-__device__ __forceinline__ void load_prim_f(const float* __restrict__ W, long long ps, long long c,
-                                            float w[5]) {
-  w[0] = W[c];
-  w[1] = W[(1 + Perm<D>::n) * ps + c];
-  w[2] = W[(1 + Perm<D>::t1) * ps + c];
-  w[3] = W[(1 + Perm<D>::t2) * ps + c];
-  w[4] = W[4 * ps + c];
+__device__ __forceinline__ void load_prim_f(const Prim8& W, long long c, float w[5], float& a,
+                                            float& ia, float& ir) {
+  const float4 x = __ldg(W.a + c), y = __ldg(W.b + c);
+  const float v[3] = {x.y, x.z, x.w};
+  w[0] = x.x;
+  w[1] = v[Perm<D>::n];
+  w[2] = v[Perm<D>::t1];
+  w[3] = v[Perm<D>::t2];
+  w[4] = y.x;
+  a = y.y;
+  ia = y.z;
+  ir = y.w;
+}
+// a face quantity in axis order (flux differences) or in sweep order (states)
+__device__ __forceinline__ void load_face_xyz(const Face5& A, long long c, float w[5]) {
+  const float4 x = __ldg(A.v + c);
+  w[0] = x.x;
+  w[1] = x.y;
+  w[2] = x.z;
+  w[3] = x.w;
+  w[4] = __ldg(A.e + c);
 }
 template <int D>
-__device__ __forceinline__ void store_rot_f(float* __restrict__ A, long long ps, long long c,
-                                            const float v[5]) {
-  A[c] = v[0];
-  A[(1 + Perm<D>::n) * ps + c] = v[1];
-  A[(1 + Perm<D>::t1) * ps + c] = v[2];
-  A[(1 + Perm<D>::t2) * ps + c] = v[3];
-  A[4 * ps + c] = v[4];
+__device__ __forceinline__ void load_face(const Face5& A, long long c, float w[5]) {
+  float x[5];
+  load_face_xyz(A, c, x);
+  w[0] = x[0];
+  w[1] = x[1 + Perm<D>::n];
+  w[2] = x[1 + Perm<D>::t1];
+  w[3] = x[1 + Perm<D>::t2];
+  w[4] = x[4];
+}
+template <int D>
+__device__ __forceinline__ void store_face(const Face5& A, long long c, const float w[5]) {
+  float x[3];
+  x[Perm<D>::n] = w[1];
+  x[Perm<D>::t1] = w[2];
+  x[Perm<D>::t2] = w[3];
+  A.v[c] = make_float4(w[0], x[0], x[1], x[2]);
+  A.e[c] = w[4];
 }
 
 // What a cell keeps for the FP64 signal speed of the CFL condition.
@@ -142,13 +189,8 @@ __device__ __forceinline__ void prims_mixed_body(const Geom& G, const BufsF& B, 
   float vf[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) vf[d] = mf[d] * rf;
-  B.W[t] = df;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) B.W[(1 + d) * G.ps + t] = vf[d];
-  B.W[4 * G.ps + t] = pf;
-  B.W[5 * G.ps + t] = af;
-  B.W[6 * G.ps + t] = __frcp_rn(af);
-  B.W[7 * G.ps + t] = rf;
+  B.W.a[t] = make_float4(df, vf[0], vf[1], vf[2]);
+  B.W.b[t] = make_float4(pf, af, __frcp_rn(af), rf);
   cand.s = -1.f;
   if (want_dt && real) {
     float m = 0.f;
@@ -199,7 +241,7 @@ __global__ void __launch_bounds__(BS) kb_prims_mixed(BatchLaunch L) {
   __shared__ DtCand warp_cand[kWarps];
   const BatchItem it = batch_item(L);
   const Geom& G = it.d->G;
-  const BufsF F = float_view(it.d->B);
+  const BufsF F = float_view(it.d->B, it.d->G.ps);
   const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
   DtCand cand;
   cand.s = -1.f;
@@ -249,22 +291,20 @@ __device__ __forceinline__ void ppmc_mixed_body(const Geom& G, const BufsF& B, c
   // next to the FP64 stages) rather than read from a slope pass: this saves
   // the slope planes' HBM round trip and a launch per axis
   float w2m[5], wm[5], wc[5], wp[5], w2p[5], sm[5], sc[5], sp[5];
-  load_prim_f<D>(B.W, G.ps, c - 2 * s, w2m);
-  load_prim_f<D>(B.W, G.ps, c - s, wm);
-  load_prim_f<D>(B.W, G.ps, c, wc);
-  load_prim_f<D>(B.W, G.ps, c + s, wp);
-  load_prim_f<D>(B.W, G.ps, c + 2 * s, w2p);
-  limited_slope(w2m, wm, wc, B.W[5 * G.ps + c - s], B.W[6 * G.ps + c - s],
-                B.W[7 * G.ps + c - s], sm);
-  limited_slope(wm, wc, wp, B.W[5 * G.ps + c], B.W[6 * G.ps + c], B.W[7 * G.ps + c], sc);
-  limited_slope(wc, wp, w2p, B.W[5 * G.ps + c + s], B.W[6 * G.ps + c + s],
-                B.W[7 * G.ps + c + s], sp);
+  float a2m, ia2m, ir2m, am, iam, irm, ac, iac, irc, ap, iap, irp, a2p, ia2p, ir2p;
+  load_prim_f<D>(B.W, c - 2 * s, w2m, a2m, ia2m, ir2m);
+  load_prim_f<D>(B.W, c - s, wm, am, iam, irm);
+  load_prim_f<D>(B.W, c, wc, ac, iac, irc);
+  load_prim_f<D>(B.W, c + s, wp, ap, iap, irp);
+  load_prim_f<D>(B.W, c + 2 * s, w2p, a2p, ia2p, ir2p);
+  limited_slope(w2m, wm, wc, am, iam, irm, sm);
+  limited_slope(wm, wc, wp, ac, iac, irc, sc);
+  limited_slope(wc, wp, w2p, ap, iap, irp, sp);
   const float dtdx = (float)B.rec[2];
   float WsL[5], WsR[5];
-  ppmc_states(wm, wc, wp, sm, sc, sp, B.W[5 * G.ps + c], B.W[6 * G.ps + c], B.W[7 * G.ps + c],
-              dtdx, WsL, WsR);
-  store_rot_f<D>(B.UR[D], G.ps, c, WsL);
-  store_rot_f<D>(B.UL[D], G.ps, c + s, WsR);
+  ppmc_states(wm, wc, wp, sm, sc, sp, ac, iac, irc, dtdx, WsL, WsR);
+  store_face<D>(B.UR[D], c, WsL);
+  store_face<D>(B.UL[D], c + s, WsR);
 }
 
 
@@ -275,10 +315,10 @@ __device__ __forceinline__ void riemann1_mixed_body(const Geom& G, const BufsF& 
   box_coords(box, t, c3);
   const long long f = pidx(G, c3);
   float WL[5], WR[5], F[5];
-  load_prim_f<D>(B.UL[D], G.ps, f, WL);
-  load_prim_f<D>(B.UR[D], G.ps, f, WR);
+  load_face<D>(B.UL[D], f, WL);
+  load_face<D>(B.UR[D], f, WR);
   const int fl = riemann_exact(WL, WR, nr_rcp(WL[0]), nr_rcp(WR[0]), g, F);
-  store_rot_f<D>(B.F1[D], G.ps, f, F);
+  store_face<D>(B.F1[D], f, F);
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
@@ -297,28 +337,29 @@ __device__ __forceinline__ void riemann1_mixed_body(const Geom& G, const BufsF& 
 // (the fluxes are float) already bounds the result's accuracy.  Returns the
 // primitives in sweep order and 1/rho', in float.
 template <int D>
-__device__ __forceinline__ void half_step_side(const Geom& G, const BufsF& B, const float* __restrict__ Ws,
+__device__ __forceinline__ void half_step_side(const Geom& G, const BufsF& B, const Face5& Ws,
                                                long long f, long long c, float h, const GasF& g,
                                                float w[5], float& inv_d) {
-  const long long ps = G.ps;
-  const float d = Ws[f];
-  float v[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) v[i] = Ws[(1 + i) * ps + f];
-  const float p = Ws[4 * ps + f];
+  float ws[5];  // the face state, x/y/z velocity order
+  load_face_xyz(Ws, f, ws);
+  const float d = ws[0];
+  const float v[3] = {ws[1], ws[2], ws[3]};
+  const float p = ws[4];
   float dU[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   constexpr int T1 = Perm<D>::t1, T2 = Perm<D>::t2;
   if (G.n[T1] > 1) {
-    const float* F = B.F1[T1];
-    const long long st = G.s[T1];
+    float a[5], b[5];
+    load_face_xyz(B.F1[T1], c, a);
+    load_face_xyz(B.F1[T1], c + G.s[T1], b);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) dU[q] = h * (F[q * ps + c] - F[q * ps + c + st]);
+    for (int q = 0; q < 5; ++q) dU[q] = h * (a[q] - b[q]);
   }
   if (G.n[T2] > 1) {
-    const float* F = B.F1[T2];
-    const long long st = G.s[T2];
+    float a[5], b[5];
+    load_face_xyz(B.F1[T2], c, a);
+    load_face_xyz(B.F1[T2], c + G.s[T2], b);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) dU[q] = fmaf(h, F[q * ps + c] - F[q * ps + c + st], dU[q]);
+    for (int q = 0; q < 5; ++q) dU[q] = fmaf(h, a[q] - b[q], dU[q]);
   }
   const float dn = d + dU[0];
   const float rn = nr_rcp(dn);
@@ -349,7 +390,7 @@ __device__ __forceinline__ void riemann2_mixed_body(const Geom& G, const BufsF& 
   half_step_side<D>(G, B, B.UL[D], f, f - G.s[D], h, g, wl, idL);
   half_step_side<D>(G, B, B.UR[D], f, f, h, g, wr, idR);
   const int fl = riemann_exact(wl, wr, idL, idR, g, Fx);
-  store_rot_f<D>(B.UL[D], G.ps, f, Fx);
+  store_face<D>(B.UL[D], f, Fx);
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
@@ -376,20 +417,19 @@ __device__ __forceinline__ void update_mixed_body(const Geom& G, const BufsF& B,
   const long long c = real_to_padded(G, t);
   const double dtdx = B.rec[2];
   // every load is issued before the first store (the state and the flux
-  // planes are distinct arrays), so that a thread has all 35 in flight
+  // planes are distinct arrays), so that a thread has all of them in flight
   double u[5];
   float fc[3][5], fn[3][5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) u[q] = B.u[q * G.nreal + t];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const bool on = G.n[d] > 1;
-    const float* __restrict__ F = B.UL[d];
-    const long long cn = c + G.s[d];
+    if (G.n[d] > 1) {
+      load_face_xyz(B.UL[d], c, fc[d]);
+      load_face_xyz(B.UL[d], c + G.s[d], fn[d]);
+    } else {
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      fc[d][q] = on ? __ldg(F + q * G.ps + c) : 0.f;
-      fn[d][q] = on ? __ldg(F + q * G.ps + cn) : 0.f;
+      for (int q = 0; q < 5; ++q) fc[d][q] = fn[d][q] = 0.f;
     }
   }
   int fl = 0;
@@ -417,7 +457,7 @@ __device__ __forceinline__ void update_mixed_body(const Geom& G, const BufsF& B,
 template <int BS>
 __global__ void __launch_bounds__(BS) kb_update_mixed(BatchLaunch L) {
   const BatchItem it = batch_item(L);
-  if (it.t < it.d->G.nreal) update_mixed_body(it.d->G, float_view(it.d->B), it.t);
+  if (it.t < it.d->G.nreal) update_mixed_body(it.d->G, float_view(it.d->B, it.d->G.ps), it.t);
 }
 
 #define HYDRO_BATCH_MIXED(NAME, STAGE_IDX, MINB, CALL)                                     \
@@ -426,7 +466,7 @@ __global__ void __launch_bounds__(BS) kb_update_mixed(BatchLaunch L) {
     const BatchItem it = batch_item(L);                                                     \
     const Box& box = it.d->box[STAGE_IDX][D];                                               \
     if (it.t < (long long)box.n[0] * box.n[1] * box.n[2]) {                                 \
-      const BufsF F = float_view(it.d->B);                                                  \
+      const BufsF F = float_view(it.d->B, it.d->G.ps);                                      \
       CALL;                                                                                 \
     }                                                                                       \
   }

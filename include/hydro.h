@@ -281,6 +281,14 @@ int hydro_ppmc(int n, const double* w, double dtdx, double gamma, double* WsL, d
  * Returns HYDRO_OK, HYDRO_EINVAL (mismatches NULL) or HYDRO_ECUDA. */
 int hydro_check_conversions(unsigned long long* mismatches, void* stream);
 
+/* Host-only self-check of the integer division the kernels' index arithmetic
+ * uses (a multiply-high and a shift by constants formed per grid, in place of
+ * an integer division; valid for numerators below 2^31, which the size rules
+ * above guarantee): compares it with plain division for every divisor up to
+ * 2^16 and 200000 hashed divisors up to 2^31 - 1, at edge and hashed
+ * numerators.  Needs no GPU.  Returns the number of mismatches (0 expected). */
+long long hydro_check_fastdiv(void);
+
 #ifdef __cplusplus
 }
 #endif

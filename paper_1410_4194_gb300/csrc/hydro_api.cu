@@ -268,6 +268,7 @@ int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, co
   G.s[2] = (long long)G.N[0] * G.N[1];
   G.ps = (long long)align_up((size_t)G.N[0] * G.N[1] * G.N[2], 32);
   G.nreal = (long long)nx * ny * nz;
+  geom_divisors(G);
   G.dx = dx;
   for (int f = 0; f < 6; ++f) {
     h->bc.type[f] = (n[f / 2] > 1) ? bc[f] : HYDRO_BC_PERIODIC;

@@ -285,6 +285,7 @@ int hydro_batch_init(hydro_batch_t* out, int ngrids, const int* dims, const doub
     G.s[2] = (long long)G.N[0] * G.N[1];
     G.ps = (long long)align_up((size_t)G.N[0] * G.N[1] * G.N[2], 32);
     G.nreal = (long long)G.n[0] * G.n[1] * G.n[2];
+    geom_divisors(G);
     G.dx = dx[i];
     for (int f = 0; f < 6; ++f) g.bc.type[f] = (G.n[f / 2] > 1) ? bc[6 * i + f] : HYDRO_BC_PERIODIC;
     fill_desc(g, gamma[i]);

@@ -7,6 +7,41 @@
 
 namespace hydro {
 
+// Division of a 32-bit index n < 2^31 by a fixed divisor d (1 <= d < 2^31)
+// with a multiply-high and a shift instead of an integer division (which the
+// GPU evaluates as a ~20-instruction sequence): for d not a power of two, with
+// 2^(s-1) < d < 2^s and m = ceil(2^(31+s) / d) < 2^32,
+//   floor(n / d) = floor(n m / 2^(31+s))
+// because n m / 2^(31+s) = n/d + n r / (d 2^(31+s)) with 0 < r < d adds less
+// than n / 2^(31+s) < 2^-s < 1/d, too little to reach the next integer (the
+// round-up method of division by invariant integers); for d = 2^k, m = 0 and
+// the quotient is n >> k.
+struct FastDiv {
+  unsigned m;  // multiplier, 0 for a power of two
+  int sh;      // shift after the multiply-high (s - 1), or k
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f;
+  int s = 0;
+  while ((1u << s) < d) ++s;  // d <= 2^s
+  if ((1u << s) == d) {
+    f.m = 0;
+    f.sh = s;
+  } else {
+    const unsigned long long two = 1ull << (31 + s);
+    f.m = (unsigned)((two + d - 1) / d);
+    f.sh = s - 1;
+  }
+  return f;
+}
+__host__ __device__ __forceinline__ unsigned fast_div(unsigned n, FastDiv f) {
+#ifdef __CUDA_ARCH__
+  return f.m ? (__umulhi(n, f.m) >> f.sh) : (n >> f.sh);
+#else
+  return f.m ? (unsigned)(((unsigned long long)n * f.m) >> 32) >> f.sh : (n >> f.sh);
+#endif
+}
+
 // Geometry of one grid.  Padded arrays carry kNG ghost layers on each side of
 // an active axis (an axis with one cell has none) and are laid out x fastest.
 struct Geom {
@@ -17,7 +52,16 @@ struct Geom {
   long long ps;      // plane stride of padded arrays (multiple of 32)
   long long nreal;   // nx*ny*nz
   double dx;
+  FastDiv div_s1, div_s2;  // by the padded strides s[1], s[2]
+  FastDiv div_n0, div_n1;  // by the real extents n[0], n[1]
 };
+// fill the divisors of a geometry whose extents and strides are set
+inline void geom_divisors(Geom& G) {
+  G.div_s1 = make_fastdiv((unsigned)G.s[1]);
+  G.div_s2 = make_fastdiv((unsigned)G.s[2]);
+  G.div_n0 = make_fastdiv((unsigned)G.n[0]);
+  G.div_n1 = make_fastdiv((unsigned)G.n[1]);
+}
 
 // Boundary description passed to the primitive kernel by value.
 struct BcDesc {
@@ -43,6 +87,7 @@ struct Bufs {
 struct Box {
   int lo[3];
   int n[3];
+  FastDiv div0, div01;  // by n[0] and n[0] n[1]
 };
 
 // Everything a batched launch needs about one grid, in device memory.  The

@@ -23,9 +23,9 @@ using Gas = GasT<double>;
 __device__ __forceinline__ void box_coords(const Box& b, long long t, int c[3]) {
   const unsigned n0 = (unsigned)b.n[0], n01 = (unsigned)b.n[0] * (unsigned)b.n[1];
   const unsigned tt = (unsigned)t;
-  const unsigned k = tt / n01;
+  const unsigned k = fast_div(tt, b.div01);
   const unsigned r = tt - k * n01;
-  const unsigned j = r / n0;
+  const unsigned j = fast_div(r, b.div0);
   c[2] = b.lo[2] + (int)k;
   c[1] = b.lo[1] + (int)j;
   c[0] = b.lo[0] + (int)(r - j * n0);
@@ -34,9 +34,9 @@ __device__ __forceinline__ void box_coords(const Box& b, long long t, int c[3]) 
 // (i, j, k) of padded cell t: t = i + s1 j + s2 k
 __device__ __forceinline__ void padded_coords(const Geom& G, long long t, int c[3]) {
   const unsigned tt = (unsigned)t, s1 = (unsigned)G.s[1], s2 = (unsigned)G.s[2];
-  const unsigned k = tt / s2;
+  const unsigned k = fast_div(tt, G.div_s2);
   const unsigned r = tt - k * s2;
-  const unsigned j = r / s1;
+  const unsigned j = fast_div(r, G.div_s1);
   c[2] = (int)k;
   c[1] = (int)j;
   c[0] = (int)(r - j * s1);
@@ -45,9 +45,9 @@ __device__ __forceinline__ void padded_coords(const Geom& G, long long t, int c[
 // padded index of real cell t (t = i + nx j + nx ny k over the real cells)
 __device__ __forceinline__ long long real_to_padded(const Geom& G, long long t) {
   const unsigned tt = (unsigned)t, n0 = (unsigned)G.n[0], n1 = (unsigned)G.n[1];
-  const unsigned q = tt / n0;
+  const unsigned q = fast_div(tt, G.div_n0);
   const unsigned i = tt - q * n0;
-  const unsigned k = q / n1;
+  const unsigned k = fast_div(q, G.div_n1);
   const unsigned j = q - k * n1;
   return (long long)(i + G.g[0]) + (long long)(j + G.g[1]) * G.s[1] + (long long)(k + G.g[2]) * G.s[2];
 }
@@ -477,6 +477,8 @@ inline Box make_box(const Geom& G, int axis, int lo_d, int hi_d, int lo_o, int h
     else
       axis_range(G, d, lo_o, hi_o, b.lo[d], b.n[d]);
   }
+  b.div0 = make_fastdiv((unsigned)b.n[0]);
+  b.div01 = make_fastdiv((unsigned)b.n[0] * (unsigned)b.n[1]);
   return b;
 }
 

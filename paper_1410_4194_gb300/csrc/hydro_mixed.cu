@@ -235,7 +235,7 @@ __device__ __forceinline__ double signal_speed_fp64(const Geom& G, const GasD& g
 // the thread index: one warp-shuffle reduction, each warp's winner parks its
 // operands in shared memory, and a single barrier before warp 0 finishes.
 template <int BS>
-__global__ void __launch_bounds__(BS) kb_prims_mixed(BatchLaunch L) {
+__global__ void __launch_bounds__(BS, 6 * kThreads / BS) kb_prims_mixed(BatchLaunch L) {
   constexpr int kWarps = BS / 32;
   __shared__ unsigned long long warp_key[kWarps];
   __shared__ DtCand warp_cand[kWarps];

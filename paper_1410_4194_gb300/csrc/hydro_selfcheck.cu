@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "../../include/hydro.h"
+#include "hydro_internal.h"
 #include "hydro_math.cuh"
 
 namespace {
@@ -102,4 +103,51 @@ extern "C" int hydro_check_conversions(unsigned long long* mismatches, void* str
     rc = HYDRO_ECUDA;
   cudaFree(d);
   return rc;
+}
+
+// Host check of the multiply-high division the kernels use for index
+// arithmetic (FastDiv in hydro_internal.h): every divisor 1..2^16, then
+// divisors spread up to 2^31 - 1 by a counter-based hash, each against
+// numerators at the edges (0, d - 1, d, d + 1, multiples of d near 2^31 - 1,
+// 2^31 - 1 itself) and hashed numerators below 2^31.
+extern "C" long long hydro_check_fastdiv(void) {
+  auto mix = [](unsigned long long x) {  // splitmix64 finaliser
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+  };
+  const unsigned kMax = 0x7fffffffu;
+  long long bad = 0;
+  auto check = [&](unsigned d) {
+    const hydro::FastDiv f = hydro::make_fastdiv(d);
+    auto one = [&](unsigned n) {
+      if (n > kMax) return;
+      if (hydro::fast_div(n, f) != n / d) ++bad;
+    };
+    one(0);
+    one(d - 1);
+    one(d);
+    one(d + 1);
+    const unsigned top = kMax / d;
+    for (unsigned k = top > 2 ? top - 2 : 0; k <= top; ++k) {
+      one(k * d);
+      if (k * d > 0) one(k * d - 1);
+      if (k * d < kMax) one(k * d + 1);
+    }
+    one(kMax);
+    for (unsigned i = 0; i < 64; ++i) one((unsigned)(mix(((unsigned long long)d << 8) + i) & kMax));
+  };
+  for (unsigned d = 1; d <= 65536; ++d) check(d);
+  for (unsigned i = 0; i < 200000; ++i) {
+    unsigned d = (unsigned)(mix(0x5eedull + i) & kMax);
+    if (d == 0) d = 1;
+    check(d);
+  }
+  for (unsigned k = 0; k < 31; ++k) {
+    check(1u << k);
+    check((1u << k) + 1);
+    if (k > 0) check((1u << k) - 1);
+  }
+  return bad;
 }

@@ -33,6 +33,7 @@ EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_precision", "hydro_set_s
            "hydro_batch_set_stream", "hydro_batch_set_state", "hydro_batch_get_state",
            "hydro_batch_step", "hydro_batch_autotune", "hydro_batch_last_error",
            "hydro_batch_cuda_error_string", "hydro_batch_free", "hydro_check_conversions",
+           "hydro_check_fastdiv",
            "hydro_set_reconstruction", "hydro_batch_set_reconstruction",
            "hydro_set_riemann_solver", "hydro_batch_set_riemann_solver")
 STAGES = ("prims", "set_dt", "slopes", "ppmc", "riemann1", "riemann2", "update")
@@ -89,6 +90,8 @@ def load():
     L.hydro_batch_cuda_error_string.restype = ctypes.c_char_p
     L.hydro_batch_free.argtypes = [vp]
     L.hydro_check_conversions.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), vp]
+    L.hydro_check_fastdiv.argtypes = []
+    L.hydro_check_fastdiv.restype = ctypes.c_longlong
     L.hydro_set_reconstruction.argtypes = [vp, ctypes.c_int]
     L.hydro_batch_set_reconstruction.argtypes = [vp, ctypes.c_int]
     L.hydro_set_riemann_solver.argtypes = [vp, ctypes.c_int]
@@ -307,6 +310,12 @@ def check_conversions():
     if rc != 0:
         raise HydroError(rc, "check_conversions")
     return int(out[0]), int(out[1])
+
+
+def check_fastdiv():
+    """Mismatches of the kernels' multiply-high index division against plain
+    integer division (host-only; 0 expected)."""
+    return int(load().hydro_check_fastdiv())
 
 
 class Batch:

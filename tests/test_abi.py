@@ -68,3 +68,12 @@ def test_init_rejects_grids_beyond_32bit_indexing_without_gpu(lib):
     hb = ctypes.c_void_p()
     assert lib.hydro_batch_init(ctypes.byref(hb), 2, dims, dx, gam, bcs) == -1
     assert not hb.value
+
+
+def test_index_division_matches_integer_division_without_gpu(lib):
+    """The kernels turn a linear thread index into box coordinates with a
+    multiply-high division by per-grid constants; the library's host check of
+    that arithmetic (every divisor to 2^16, hashed ones to 2^31 - 1, edge and
+    hashed numerators below 2^31) finds no mismatch."""
+    lib.hydro_check_fastdiv.restype = ctypes.c_longlong
+    assert lib.hydro_check_fastdiv() == 0

@@ -24,11 +24,14 @@ using GasF = GasT<float>;
 using GasD = GasT<double>;
 
 // resident 256-thread blocks per SM for the stencil and Riemann stages, by
-// measurement on Sedov 256^3: PPMC and the second Riemann set run best at 4
-// (64 registers; 5 and 6 blocks spill and lose 6-20%), the first Riemann set
-// at 6 (40 registers, a few bytes of spill; 14% faster than at 4: its Newton
-// iteration is a latency chain that more resident warps hide)
-constexpr int kMinBlocksPpmc = 4, kMinBlocksRiemann1 = 6, kMinBlocksRiemann2 = 4;
+// measurement on Sedov 256^3: PPMC runs best at 4 (64 registers; 3 is 6%
+// slower, 5 and 6 spill), the first Riemann set at 6 (40 registers: its Newton
+// iteration is a latency chain that more resident warps hide; 14% faster than
+// at 4), the second with the bound of 3 (the compiler then takes 64 registers
+// instead of 56 -- still 4 resident blocks -- and the kernel runs 8% faster);
+// the primitives at 6 and the update at 5 (14% faster than at 4)
+constexpr int kMinBlocksPpmc = 4, kMinBlocksRiemann1 = 6, kMinBlocksRiemann2 = 3;
+constexpr int kMinBlocksPrims = 6, kMinBlocksUpdate = 5;
 
 // A five-value face quantity (a primitive state or a flux, x/y/z components
 // in axis order) in vector form: values 0-3 in one float4 plane, value 4 in
@@ -235,7 +238,7 @@ __device__ __forceinline__ double signal_speed_fp64(const Geom& G, const GasD& g
 // the thread index: one warp-shuffle reduction, each warp's winner parks its
 // operands in shared memory, and a single barrier before warp 0 finishes.
 template <int BS>
-__global__ void __launch_bounds__(BS, 6 * kThreads / BS) kb_prims_mixed(BatchLaunch L) {
+__global__ void __launch_bounds__(BS, kMinBlocksPrims * kThreads / BS) kb_prims_mixed(BatchLaunch L) {
   constexpr int kWarps = BS / 32;
   __shared__ unsigned long long warp_key[kWarps];
   __shared__ DtCand warp_cand[kWarps];
@@ -455,7 +458,7 @@ __device__ __forceinline__ void update_mixed_body(const Geom& G, const BufsF& B,
 
 
 template <int BS>
-__global__ void __launch_bounds__(BS) kb_update_mixed(BatchLaunch L) {
+__global__ void __launch_bounds__(BS, kMinBlocksUpdate * kThreads / BS) kb_update_mixed(BatchLaunch L) {
   const BatchItem it = batch_item(L);
   if (it.t < it.d->G.nreal) update_mixed_body(it.d->G, float_view(it.d->B, it.d->G.ps), it.t);
 }

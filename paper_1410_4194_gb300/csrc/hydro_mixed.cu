@@ -12,8 +12,11 @@
 //     floor and the CFL time-step reduction;
 //   * the conserved update (Eq. conserved_update), accumulated from the float
 //     CTU fluxes into the FP64 state.
-// Intermediates (primitives, slopes, face states, fluxes) are float, which
-// halves their HBM traffic.  Compiled with FMA contraction.
+// Intermediates (primitives, face states, fluxes) are float, in float4
+// vector planes (see Face5), which halves their HBM traffic; the PPMC kernel
+// forms the limited slopes it needs itself.  The float divisions and square
+// roots of the solver are the SFU approximations (nr_* in hydro_math.cuh).
+// Compiled with FMA contraction.
 #include "../../include/hydro.h"
 #include "hydro_kernels.cuh"
 

@@ -41,9 +41,20 @@ typedef struct hydro_s* hydro_t;
 
 /* Boundary condition of one face (Sec. 3.1): periodic wrap; reflective (mirror
  * copy, normal momentum negated); transmissive/outflow (every ghost copies the
- * outermost real cell); inflow (every ghost holds a prescribed state).  Both
- * faces of an axis must be periodic or neither. */
-enum { HYDRO_BC_PERIODIC = 0, HYDRO_BC_REFLECT = 1, HYDRO_BC_OUTFLOW = 2, HYDRO_BC_INFLOW = 3 };
+ * outermost real cell); inflow (every ghost holds a prescribed state); Noh
+ * (Sec. 4.3.1: every ghost holds the analytic Noh solution at the time t of
+ * the step's start and the ghost's centre x, r = |x| over the n active axes:
+ * rho = rho0 (1 + V t / r)^(n-1), velocity V toward the origin, E = p0/(gamma-1)
+ * + rho V^2/2, with (rho0, V, -, -, p0) given by hydro_set_inflow; single grids
+ * only).  Ghosts are filled as passes along x, then y, then z would fill them.
+ * Both faces of an axis must be periodic or neither. */
+enum {
+  HYDRO_BC_PERIODIC = 0,
+  HYDRO_BC_REFLECT = 1,
+  HYDRO_BC_OUTFLOW = 2,
+  HYDRO_BC_INFLOW = 3,
+  HYDRO_BC_NOH = 4
+};
 
 /* Arithmetic of the step.
  * HYDRO_FP64 (default): every operation in float64; the printed formulas are
@@ -105,9 +116,19 @@ enum {
  * On success *out holds the handle; on error *out is NULL. */
 int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, const int bc[6]);
 
-/* Prescribed primitive state (rho, u, v, w, p) of an HYDRO_BC_INFLOW face
- * (0..5 in the order of bc[]).  Host pointer, copied. */
+/* Prescribed primitive state (rho, u, v, w, p) of an HYDRO_BC_INFLOW face, or
+ * (rho0, V, -, -, p0) of an HYDRO_BC_NOH face (0..5 in the order of bc[]).  Host
+ * pointer, copied.  HYDRO_EINVAL unless rho > 0 and p >= 0. */
 int hydro_set_inflow(hydro_t h, int face, const double prim[5]);
+
+/* Time t at the start of the next step, which the Noh boundary reads: 0 after
+ * hydro_init, advanced by every step's dt on the device (hydro_set_state leaves
+ * it).  Set it (t >= 0, else HYDRO_EINVAL) to start a run at another time; read
+ * it back after steps. */
+int hydro_set_time(hydro_t h, double t);
+/* The time (see hydro_set_time); waits for the handle's stream.  A negative
+ * value is an error code. */
+double hydro_get_time(hydro_t h);
 
 /* Select HYDRO_FP64 (default), HYDRO_MIXED or HYDRO_FP64_STRICT for the
  * following steps. */

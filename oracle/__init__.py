@@ -22,7 +22,7 @@ _lib = None
 FLAG_NEWTON = 1
 FLAG_NONPHYS = 2
 
-BC_PERIODIC, BC_REFLECT, BC_OUTFLOW, BC_INFLOW = 0, 1, 2, 3
+BC_PERIODIC, BC_REFLECT, BC_OUTFLOW, BC_INFLOW, BC_NOH = 0, 1, 2, 3, 4
 RECON_PPMC, RECON_PPMP, RECON_PLMC, RECON_PLMP, RECON_PCM = 0, 1, 2, 3, 4
 SOLVER_EXACT, SOLVER_ROE = 0, 1
 
@@ -54,6 +54,9 @@ def lib():
         L.oracle_compute_dt.restype = ctypes.c_double
         L.oracle_compute_dt.argtypes = [ctypes.c_void_p, ctypes.c_double]
         L.oracle_step_dt.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        L.oracle_set_time.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        L.oracle_get_time.argtypes = [ctypes.c_void_p]
+        L.oracle_get_time.restype = ctypes.c_double
         L.oracle_fill_ghosts.argtypes = [ctypes.c_void_p, _dp]
         L.oracle_set_threads.argtypes = [ctypes.c_int]
         L.oracle_riemann_prim.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double,
@@ -162,8 +165,17 @@ class Grid:
             self.h = None
 
     def set_inflow(self, face, prim):
+        """Prescribed state of an inflow face (rho, u, v, w, p), or of a Noh face
+        (rho0, V, -, -, p0)."""
         p = np.ascontiguousarray(prim, dtype=np.float64)
         lib().oracle_set_inflow(self.h, int(face), _ptr(p))
+
+    def set_time(self, t):
+        """Time at the start of the next step (the Noh boundary's t)."""
+        lib().oracle_set_time(self.h, float(t))
+
+    def get_time(self):
+        return lib().oracle_get_time(self.h)
 
     def set_recon(self, recon):
         """Reconstruction (Sec. 2.2.1): RECON_PPMC (default), RECON_PPMP, RECON_PLMC,

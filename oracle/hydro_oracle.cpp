@@ -23,6 +23,12 @@
 //    prescribed primitive state; ghosts are filled x, then y, then z, each pass
 //    over the already-filled ghosts of earlier axes (this fills edges and corners
 //    the way the x->y->z exchange of Sec. 3.5.2 does).
+//  * Noh boundary (Sec. 4.3.1, outer faces of the octant): a ghost cell takes the
+//    analytic solution at the start of the step, time t, at its own centre x
+//    (r = |x| over the active axes, n of them): rho = rho0 (1 + V t / r)^(n-1),
+//    velocity V toward the origin, E = p0/(gamma-1) + rho V^2 / 2 (the printed
+//    energy with V = 1); rho0, V, p0 are the face's prescribed state
+//    (rho0, V, -, -, p0); t starts at 0 and advances by each step's dt.
 //  * dt is taken from the state at the start of the step over real cells and
 //    active axes (Eq. calc_dt_3D); an axis with one cell is inactive (no ghosts,
 //    no sweep, no transverse term), so the step reduces to 2D/1D CTU (Sec. 2.3).
@@ -68,7 +74,7 @@ constexpr double NEWTON_TOL = 1e-6;
 constexpr int NEWTON_MAX = 50;
 
 enum : int { FLAG_NEWTON = 1, FLAG_NONPHYS = 2 };
-enum : int { BC_PERIODIC = 0, BC_REFLECT = 1, BC_OUTFLOW = 2, BC_INFLOW = 3 };
+enum : int { BC_PERIODIC = 0, BC_REFLECT = 1, BC_OUTFLOW = 2, BC_INFLOW = 3, BC_NOH = 4 };
 
 // ---------------------------------------------------------------------------
 // Operation-counting scalar.  The same templated code runs on `double` (the
@@ -704,7 +710,11 @@ void ppmp_cell(const R w[7][5], R dtdx, R dx, const Gas& g, R WsL[5], R WsR[5]) 
 // of the Roe coefficients is replaced by max(|lambda|, etaH); 0 leaves them.
 // Readings: the printed "C_3 2~" of s_3 is C_3 w~; "negative" density or
 // pressure of an intermediate state means < 0; a Roe average with
-// (gamma-1)(H~ - V~^2/2) <= 0 has no sound speed and takes the HLLE flux.
+// (gamma-1)(H~ - V~^2/2) <= 0 has no sound speed and takes the HLLE flux, with
+// u~ for both Roe eigenvalues; HLLE bounds b^p = b^m = 0 (possible only then,
+// with u~ = 0 and both states moving supersonically toward the interface, as
+// cold gas at a reflecting wall) take the ratio (b^p + b^m)/(b^p - b^m) as its
+// symmetric limit 0, i.e. the flux (F_L + F_R)/2 (the printed quotient is 0/0).
 template <class R>
 void roe_hlle_flux(const R UL[5], const R UR[5], const R WL[5], const R WR[5], const R FL[5],
                    const R FR[5], R lm, R lp, const Gas& g, R F[5]) {
@@ -712,10 +722,11 @@ void roe_hlle_flux(const R UL[5], const R UR[5], const R WL[5], const R WR[5], c
   const R aR = sqrt(R(g.gamma) * WR[4] / WR[0]);
   const R bm = mn(mn(lm, WL[1] - aL), R(0.0));
   const R bp = mx(mx(lp, WR[1] + aR), R(0.0));
+  const R k = (bp - bm > R(0.0)) ? (bp + bm) / (bp - bm) : R(0.0);
   for (int q = 0; q < 5; ++q) {
     const R FLh = FL[q] - bm * UL[q];
     const R FRh = FR[q] - bp * UR[q];
-    F[q] = R(0.5) * ((FLh + FRh) + (FLh - FRh) * ((bp + bm) / (bp - bm)));
+    F[q] = R(0.5) * ((FLh + FRh) + (FLh - FRh) * k);
   }
 }
 
@@ -835,6 +846,7 @@ struct Grid {
   double inflow_prim[6][5];
   int recon = RECON_PPMC;  // reconstruction of App. A / Sec. 2.2.1
   int solver = SOLVER_EXACT;
+  double time = 0.0;       // t at the start of the next step (Noh boundary)
   size_t ncell;
   std::vector<R> u;
 
@@ -874,6 +886,8 @@ void fill_ghosts(Grid<R>& G) {
         Uin[0] = W[0]; Uin[1] = W[0] * W[1]; Uin[2] = W[0] * W[2]; Uin[3] = W[0] * W[3];
         Uin[4] = W[4] / (G.gamma - 1.0) + 0.5 * W[0] * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
       }
+      int nact = 0;
+      for (int t = 0; t < 3; ++t) nact += G.n[t] > 1 ? 1 : 0;
       for (int gd = 1; gd <= G.gh[d]; ++gd) {
         const int tgt = side == 0 ? G.gh[d] - gd : G.gh[d] + G.n[d] - 1 + gd;
         int src = 0;
@@ -891,6 +905,21 @@ void fill_ghosts(Grid<R>& G) {
               ct[d] = tgt;
               cs[d] = src;
               const size_t it = G.idx(ct[0], ct[1], ct[2]);
+              if (type == BC_NOH) {
+                const double* P = G.inflow_prim[2 * d + side];
+                double x[3] = {0, 0, 0}, r2 = 0.0;
+                for (int t = 0; t < 3; ++t) {
+                  if (G.n[t] <= 1) continue;
+                  x[t] = (ct[t] - G.gh[t] + 0.5) * G.dx;
+                  r2 += x[t] * x[t];
+                }
+                const double r = std::sqrt(r2);
+                const double rho = P[0] * std::pow(1.0 + P[1] * G.time / r, nact - 1);
+                G.u[it] = R(rho);
+                for (int t = 0; t < 3; ++t) G.u[(1 + t) * G.ncell + it] = R(-rho * P[1] * x[t] / r);
+                G.u[4 * G.ncell + it] = R(P[4] / (G.gamma - 1.0) + 0.5 * rho * P[1] * P[1]);
+                continue;
+              }
               for (int q = 0; q < 5; ++q) {
                 if (type == BC_INFLOW) {
                   G.u[q * G.ncell + it] = R(Uin[q]);
@@ -1232,7 +1261,20 @@ double oracle_compute_dt(void* h, double cfl) {
   return cfl * compute_dt_min(static_cast<Handle*>(h)->G);
 }
 
-int oracle_step_dt(void* h, double dt) { return ctu_step(static_cast<Handle*>(h)->G, dt, true); }
+int oracle_step_dt(void* h, double dt) {
+  auto& G = static_cast<Handle*>(h)->G;
+  const int flags = ctu_step(G, dt, true);
+  G.time += dt;
+  return flags;
+}
+
+// time at the start of the next step (used by the Noh boundary); starts at 0
+int oracle_set_time(void* h, double t) {
+  if (!h) return -1;
+  static_cast<Handle*>(h)->G.time = t;
+  return 0;
+}
+double oracle_get_time(void* h) { return static_cast<Handle*>(h)->G.time; }
 
 // Padded conserved state after the ghost fill of the current state, for the
 // boundary tests: [5][N2][N1][N0] with N = n + 8 on active axes.
@@ -1343,6 +1385,7 @@ int oracle_count_step(void* h, double dt, double* counts) {
     for (int q = 0; q < 5; ++q) G.inflow_prim[f][q] = G0.inflow_prim[f][q];
   G.recon = G0.recon;
   G.solver = G0.solver;
+  G.time = G0.time;
   for (size_t i = 0; i < G0.u.size(); ++i) G.u[i] = CR(G0.u[i]);
   g_ops = OpCount();
   for (int k = 0; k < kStages; ++k) {
@@ -1372,6 +1415,7 @@ int oracle_count_step_stages(void* h, double dt, double* counts, double* units) 
     for (int q = 0; q < 5; ++q) G.inflow_prim[f][q] = G0.inflow_prim[f][q];
   G.recon = G0.recon;
   G.solver = G0.solver;
+  G.time = G0.time;
   for (size_t i = 0; i < G0.u.size(); ++i) G.u[i] = CR(G0.u[i]);
   g_ops = OpCount();
   for (int k = 0; k < kStages; ++k) {

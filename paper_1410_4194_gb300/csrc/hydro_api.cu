@@ -6,6 +6,7 @@
 // reads back only a 64-byte record (dt and status flags) so that hydro_step()
 // can return dt, as the paper's host loop does after its reduction (Sec. 3.4).
 #include <cuda_runtime.h>
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -227,7 +228,8 @@ int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, co
   const int n[3] = {nx, ny, nz};
   for (int d = 0; d < 3; ++d) {
     if (n[d] < 1 || (n[d] > 1 && n[d] < kNG)) return HYDRO_EINVAL;
-    if (n[d] > 1 && (bc[2 * d] < 0 || bc[2 * d] > 3 || bc[2 * d + 1] < 0 || bc[2 * d + 1] > 3))
+    if (n[d] > 1 && (bc[2 * d] < 0 || bc[2 * d] > HYDRO_BC_NOH || bc[2 * d + 1] < 0 ||
+                     bc[2 * d + 1] > HYDRO_BC_NOH))
       return HYDRO_EINVAL;
     if (n[d] > 1 && ((bc[2 * d] == HYDRO_BC_PERIODIC) != (bc[2 * d + 1] == HYDRO_BC_PERIODIC)))
       return HYDRO_EINVAL;
@@ -352,6 +354,7 @@ int hydro_set_inflow(hydro_t h, int face, const double prim[5]) {
   if (face < 0 || face > 5 || !prim) return fail(h, HYDRO_EINVAL);
   if (!(prim[0] > 0.0) || !(prim[4] >= 0.0)) return fail(h, HYDRO_EINVAL);
   double* U = h->bc.inflow[face];
+  for (int q = 0; q < 5; ++q) h->bc.prim[face][q] = prim[q];
   U[0] = prim[0];
   U[1] = prim[0] * prim[1];
   U[2] = prim[0] * prim[2];
@@ -362,6 +365,27 @@ int hydro_set_inflow(hydro_t h, int face, const double prim[5]) {
   if (rc) return rc;
   CK(h, cudaMemcpy(&h->d_desc->bc, &h->bc, sizeof(BcDesc), cudaMemcpyHostToDevice));
   return HYDRO_OK;
+}
+
+int hydro_set_time(hydro_t h, double t) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (!std::isfinite(t) || t < 0.0) return fail(h, HYDRO_EINVAL);
+  int rc = use_device(h);
+  if (rc) return rc;
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, cudaMemcpy(h->B.rec + 5, &t, sizeof(double), cudaMemcpyHostToDevice));
+  return HYDRO_OK;
+}
+
+double hydro_get_time(hydro_t h) {
+  if (!h) return (double)HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  int rc = use_device(h);
+  if (rc) return (double)rc;
+  rc = read_record(h);
+  if (rc) return (double)rc;
+  return h->host_rec[5];
 }
 
 int hydro_set_precision(hydro_t h, int mode) {

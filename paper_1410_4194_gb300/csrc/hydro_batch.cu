@@ -351,6 +351,7 @@ int hydro_batch_set_inflow(hydro_batch_t h, int grid, int face, const double pri
   if (!(prim[0] > 0.0) || !(prim[4] >= 0.0)) return bfail(h, HYDRO_EINVAL);
   const double gm1 = (double)h->desc[grid].gd.gm1;
   double* U = h->desc[grid].bc.inflow[face];
+  for (int q = 0; q < 5; ++q) h->desc[grid].bc.prim[face][q] = prim[q];
   U[0] = prim[0];
   U[1] = prim[0] * prim[1];
   U[2] = prim[0] * prim[2];

@@ -54,11 +54,7 @@ __device__ __forceinline__ void block_max_to(double v, unsigned long long* slot)
 
 // ---------------------------------------------------------------------------
 // Primitives of every padded cell.  A ghost cell takes the value the
-// boundary passes x, then y, then z would give it: a mapped real cell (periodic
-// wrap, mirror, or the outermost cell) with the normal momentum of every
-// reflective axis negated, unless an inflow axis is involved, in which case the
-// last inflow face (in x, y, z order) provides the state and only the
-// reflective axes after it negate their momentum.
+// boundary passes x, then y, then z would give it (boundary_state).
 // returns this cell's |v_d| + a maximum (0 for ghosts or when !want_dt).
 // S (strict): the CPU reference's operation order with IEEE divisions and
 // square root; otherwise 1/rho and 1/a by Newton iteration (nr_rcp, nr_rsqrt)
@@ -70,51 +66,8 @@ __device__ __forceinline__ double prims_body(const Geom& G, const Bufs& B, const
   {
     int c[3];
     padded_coords(G, t, c);
-    int src[3];
-    int neg = 0, inflow_face = -1;
-    bool real = true;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int n = G.n[d];
-      const int r = c[d] - G.g[d];
-      if (r >= 0 && r < n) {
-        src[d] = r;
-        continue;
-      }
-      real = false;
-      const bool lo = r < 0;
-      const int depth = lo ? -r : r - n + 1;
-      const int face = 2 * d + (lo ? 0 : 1);
-      switch (bc.type[face]) {
-        case 0:  // periodic
-          src[d] = lo ? n - depth : depth - 1;
-          break;
-        case 1:  // reflective
-          src[d] = lo ? depth - 1 : n - depth;
-          neg |= 1 << d;
-          break;
-        case 2:  // outflow
-          src[d] = lo ? 0 : n - 1;
-          break;
-        default:  // inflow
-          src[d] = 0;
-          inflow_face = face;
-          neg = 0;
-          break;
-      }
-    }
     double U[5];
-    if (inflow_face >= 0) {
-#pragma unroll
-      for (int q = 0; q < 5; ++q) U[q] = bc.inflow[inflow_face][q];
-    } else {
-      const long long rs = src[0] + (long long)G.n[0] * (src[1] + (long long)G.n[1] * src[2]);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) U[q] = B.u[q * G.nreal + rs];
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      if (neg & (1 << d)) U[1 + d] = -U[1 + d];
+    const bool real = boundary_state(G, B.u, bc, g.gm1, B.rec[5], c, U);
     // primitives, then the per-cell reciprocals the later stages multiply by
     const double d = U[0];
     double W[5], a, inv_a, inv_d;
@@ -215,15 +168,23 @@ __device__ __forceinline__ void update_body(const Geom& G, const Bufs& B, long l
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
+// the step's time advance t <- t + dt (record [5]), by the grid's first thread
+// of the update (the last kernel of a step; dt is final by then)
+__device__ __forceinline__ void advance_time(double* rec, long long t) {
+  if (t == 0) rec[5] = rec[5] + rec[1];
+}
+
 __global__ void __launch_bounds__(kThreads) k_update(Geom G, Bufs B) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < G.nreal) update_body<true>(G, B, t);
+  advance_time(B.rec, t);
 }
 
 template <int BS>
 __global__ void __launch_bounds__(BS) kb_update(BatchLaunch L) {
   const BatchItem it = batch_item(L);
   if (it.t < it.d->G.nreal) update_body<false>(it.d->G, it.d->B, it.t);
+  advance_time(it.d->B.rec, it.t);
 }
 
 // per grid: dt = cfl * dx / max(|v_d| + a) (or the fixed dt), dt/dx, history

@@ -67,6 +67,8 @@ inline void geom_divisors(Geom& G) {
 struct BcDesc {
   int type[6];          // HYDRO_BC_* per face x-, x+, y-, y+, z-, z+
   double inflow[6][5];  // conserved inflow state per face (rho, mx, my, mz, E)
+  double prim[6][5];    // the prescribed state as given: inflow (rho, u, v, w, p),
+                        // Noh (rho0, V, -, -, p0)
 };
 
 // Device buffers of the FP64 path.
@@ -79,7 +81,8 @@ struct Bufs {
   double* F1[3];   // per axis: first fluxes F* [5][ps]
   double* eta[3];  // per axis: H-correction eta of each face [ps] (Roe solver only, else null)
   // 64-byte step record on the device: [0] max of |v_d| + a (bits), [1] dt, [2] dt/dx,
-  // [3] dt/(2 dx), [4] flags (int in the low word)
+  // [3] dt/(2 dx), [4] flags (int in the low word), [5] time t at the start of
+  // the next step (advanced by the update kernel; read by the Noh boundary)
   double* rec;
 };
 

@@ -484,6 +484,95 @@ inline Box make_box(const Geom& G, int axis, int lo_d, int hi_d, int lo_o, int h
 
 inline long long box_count(const Box& b) { return (long long)b.n[0] * b.n[1] * b.n[2]; }
 
+// The conserved state of padded cell c (coordinates c[3]): a real cell's, or
+// for a ghost the value the boundary passes x, then y, then z give it.  Each
+// ghost axis maps the coordinate to a real cell (periodic wrap, mirror, or the
+// outermost cell) and a reflective axis negates its normal momentum; an inflow
+// or Noh axis ends the chain: its state replaces the mapped cell's and only
+// the reflective axes after it negate their momentum.  The Noh state (Sec.
+// 4.3.1: rho0 (1 + V t/r)^(n-1), velocity V toward the origin, E = p0/(gamma-1)
+// + rho V^2/2, n the active axes) is taken at the position the passes reach:
+// the cell's own coordinates on the Noh axis and the axes before it, the
+// mapped ones after it.  Returns whether the cell is real.
+__device__ __forceinline__ bool boundary_state(const Geom& G, const double* __restrict__ u,
+                                               const BcDesc& bc, double gm1, double time,
+                                               const int c[3], double U[5]) {
+  int src[3];
+  int neg = 0, fixed_face = -1, noh_axis = -1;
+  bool real = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int n = G.n[d];
+    const int r = c[d] - G.g[d];
+    if (r >= 0 && r < n) {
+      src[d] = r;
+      continue;
+    }
+    real = false;
+    const bool lo = r < 0;
+    const int depth = lo ? -r : r - n + 1;
+    const int face = 2 * d + (lo ? 0 : 1);
+    switch (bc.type[face]) {
+      case 0:  // periodic
+        src[d] = lo ? n - depth : depth - 1;
+        break;
+      case 1:  // reflective
+        src[d] = lo ? depth - 1 : n - depth;
+        neg |= 1 << d;
+        break;
+      case 2:  // outflow
+        src[d] = lo ? 0 : n - 1;
+        break;
+      case 4:  // Noh: analytic, at this coordinate
+        src[d] = r;
+        fixed_face = face;
+        noh_axis = d;
+        neg = 0;
+        break;
+      default:  // inflow
+        src[d] = 0;
+        fixed_face = face;
+        noh_axis = -1;
+        neg = 0;
+        break;
+    }
+  }
+  if (noh_axis >= 0) {
+    const double* P = bc.prim[fixed_face];
+    double x[3], r2 = 0.0;
+    int nact = 0;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      x[t] = 0.0;
+      if (G.n[t] > 1) {
+        ++nact;
+        x[t] = ((t <= noh_axis ? c[t] - G.g[t] : src[t]) + 0.5) * G.dx;
+        r2 += x[t] * x[t];
+      }
+    }
+    const double rr = sqrt(r2);
+    const double b = 1.0 + P[1] * time / rr;
+    double bn = 1.0;  // b^(n-1), n <= 3: exact products as pow rounds them
+    for (int k = 1; k < nact; ++k) bn = k == 1 ? b : bn * b;
+    const double rho = P[0] * bn;
+    U[0] = rho;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) U[1 + t] = -rho * P[1] * x[t] / rr;
+    U[4] = P[4] / gm1 + 0.5 * rho * P[1] * P[1];
+  } else if (fixed_face >= 0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) U[q] = bc.inflow[fixed_face][q];
+  } else {
+    const long long rs = src[0] + (long long)G.n[0] * (src[1] + (long long)G.n[1] * src[2]);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) U[q] = u[q * G.nreal + rs];
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    if (neg & (1 << d)) U[1 + d] = -U[1 + d];
+  return real;
+}
+
 
 // ---- batched launches: one launch, the blocks of every grid ----------------
 // grid slot of block b: the last i with prefix[i] <= b

@@ -924,7 +924,11 @@ __device__ __forceinline__ void hlle_flux(const T UL[5], const T UR[5], const T 
   }
   const T bm = vmin<S>(vmin<S>(lm, WL[1] - aL), T(0));
   const T bp = vmax<S>(vmax<S>(lp, WR[1] + aR), T(0));
-  const T k = S ? (bp + bm) / (bp - bm) : nr_div(bp + bm, bp - bm);
+  // bp = bm = 0 (no real Roe sound speed, u~ = 0, both states moving
+  // supersonically toward the face: cold gas at a reflecting wall): the
+  // quotient is 0/0; its symmetric limit 0 gives (F_L + F_R)/2
+  const T den = bp - bm;
+  const T k = !pos<S>(den) ? T(0) : (S ? (bp + bm) / den : nr_div(bp + bm, den));
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     const T FLh = FL[q] - bm * UL[q];

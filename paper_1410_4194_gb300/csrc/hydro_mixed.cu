@@ -143,51 +143,18 @@ __device__ __forceinline__ void prims_mixed_body(const Geom& G, const BufsF& B, 
                                                  long long t, DtCand& cand) {
   int c[3];
   padded_coords(G, t, c);
-  int src[3];
-  int neg = 0, inflow_face = -1;
-  bool real = true;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int n = G.n[d];
-    const int r = c[d] - G.g[d];
-    if (r >= 0 && r < n) {
-      src[d] = r;
-      continue;
-    }
-    real = false;
-    const bool lo = r < 0;
-    const int depth = lo ? -r : r - n + 1;
-    const int face = 2 * d + (lo ? 0 : 1);
-    switch (bc.type[face]) {
-      case 0: src[d] = lo ? n - depth : depth - 1; break;
-      case 1: src[d] = lo ? depth - 1 : n - depth; neg |= 1 << d; break;
-      case 2: src[d] = lo ? 0 : n - 1; break;
-      default: src[d] = 0; inflow_face = face; neg = 0; break;
-    }
-  }
   double U[5];
-  if (inflow_face >= 0) {
-#pragma unroll
-    for (int q = 0; q < 5; ++q) U[q] = bc.inflow[inflow_face][q];
-  } else {
-    const long long rs = src[0] + (long long)G.n[0] * (src[1] + (long long)G.n[1] * src[2]);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) U[q] = B.u[q * G.nreal + rs];
-  }
+  const bool real = boundary_state(G, B.u, bc, g.gm1, B.rec[5], c, U);
   float mf[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    mf[d] = d2f(U[1 + d]);
-    if (neg & (1 << d)) mf[d] = -mf[d];
-  }
+  for (int d = 0; d < 3; ++d) mf[d] = d2f(U[1 + d]);
   // 1/rho: float reciprocal of the rounded density refined by one Newton
   // step r <- r + r (1 - rho r) in FP64 (relative error below 2^-44)
   const float df = d2f(U[0]);
   const float rf = __frcp_rn(df);
   double r = f2d(rf);
   r = fma(r, fma(-U[0], r, 1.0), r);
-  // FP64 internal energy E - |m|^2 / (2 rho) and the pressure floor (the sign
-  // of a reflected momentum does not enter |m|^2)
+  // FP64 internal energy E - |m|^2 / (2 rho) and the pressure floor
   const double m2 = fma(U[1], U[1], fma(U[2], U[2], U[3] * U[3]));
   const double p = vmax<false>(g.gm1 * fma(-0.5 * m2, r, U[4]), kPFloor);
   const float pf = d2f(p);
@@ -464,6 +431,7 @@ template <int BS>
 __global__ void __launch_bounds__(BS, kMinBlocksUpdate * kThreads / BS) kb_update_mixed(BatchLaunch L) {
   const BatchItem it = batch_item(L);
   if (it.t < it.d->G.nreal) update_mixed_body(it.d->G, float_view(it.d->B, it.d->G.ps), it.t);
+  if (it.t == 0) it.d->B.rec[5] = it.d->B.rec[5] + it.d->B.rec[1];  // t <- t + dt
 }
 
 #define HYDRO_BATCH_MIXED(NAME, STAGE_IDX, MINB, CALL)                                     \

@@ -13,7 +13,7 @@ import os
 
 import numpy as np
 
-HYDRO_BC_PERIODIC, HYDRO_BC_REFLECT, HYDRO_BC_OUTFLOW, HYDRO_BC_INFLOW = 0, 1, 2, 3
+HYDRO_BC_PERIODIC, HYDRO_BC_REFLECT, HYDRO_BC_OUTFLOW, HYDRO_BC_INFLOW, HYDRO_BC_NOH = 0, 1, 2, 3, 4
 HYDRO_FP64, HYDRO_MIXED, HYDRO_FP64_STRICT = 0, 1, 2
 HYDRO_RECON_PPMC, HYDRO_RECON_PPMP, HYDRO_RECON_PLMC, HYDRO_RECON_PLMP, HYDRO_RECON_PCM = range(5)
 HYDRO_RIEMANN_EXACT, HYDRO_RIEMANN_ROE = 0, 1
@@ -24,7 +24,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhydro.so")
 
 # every entry point that include/hydro.h declares
-EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_precision", "hydro_set_stream",
+EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_time", "hydro_get_time",
+           "hydro_set_precision", "hydro_set_stream",
            "hydro_set_state", "hydro_get_state", "hydro_step", "hydro_step_dt",
            "hydro_compute_dt", "hydro_last_error", "hydro_error_string",
            "hydro_cuda_error_string", "hydro_profile", "hydro_profile_read", "hydro_free",
@@ -58,6 +59,9 @@ def load():
     vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
     L.hydro_init.argtypes = [ctypes.POINTER(vp)] + [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [ip]
     L.hydro_set_inflow.argtypes = [vp, ctypes.c_int, dp]
+    L.hydro_set_time.argtypes = [vp, ctypes.c_double]
+    L.hydro_get_time.argtypes = [vp]
+    L.hydro_get_time.restype = ctypes.c_double
     L.hydro_set_precision.argtypes = [vp, ctypes.c_int]
     L.hydro_set_stream.argtypes = [vp, vp]
     L.hydro_set_state.argtypes = [vp, vp, ctypes.c_int]
@@ -164,8 +168,20 @@ class Grid:
             pass
 
     def set_inflow(self, face, prim):
+        """Prescribed state of an inflow face (rho, u, v, w, p), or of a Noh face
+        (rho0, V, -, -, p0)."""
         p = (ctypes.c_double * 5)(*[float(x) for x in prim])
         self._check(self._L.hydro_set_inflow(self.h, int(face), p), "set_inflow")
+
+    def set_time(self, t):
+        """Time at the start of the next step (the Noh boundary's t)."""
+        self._check(self._L.hydro_set_time(self.h, float(t)), "set_time")
+
+    def get_time(self):
+        t = self._L.hydro_get_time(self.h)
+        if t < 0:
+            raise HydroError(int(t), "get_time")
+        return t
 
     def set_precision(self, mode):
         self._check(self._L.hydro_set_precision(self.h, int(mode)), "set_precision")

@@ -307,3 +307,80 @@ def test_error_paths():
     assert dt < 0 and g.last_error() == -4
     with pytest.raises(hydro.HydroError):
         g.step_dt(-1.0)
+
+
+# ---- Noh's strong shock (Sec. 4.3.1): analytic outer boundary, cold gas ------
+def noh_case(n, nd):
+    from tests.test_oracle_noh import noh_case as make
+    u0, dx, bc, inflow, r = make(n, nd)
+    return dict(u=u0, dx=dx, gamma=5.0 / 3.0, bc=bc, inflow=inflow)
+
+
+@pytest.mark.parametrize("mode", MODES, ids=lambda m: MODE_ID[m])
+@pytest.mark.parametrize("nd,n,recon,solver", [
+    (3, 16, hydro.HYDRO_RECON_PPMC, hydro.HYDRO_RIEMANN_EXACT),
+    (3, 16, hydro.HYDRO_RECON_PPMC, hydro.HYDRO_RIEMANN_ROE),
+    (2, 32, hydro.HYDRO_RECON_PLMP, hydro.HYDRO_RIEMANN_EXACT),
+    (2, 32, hydro.HYDRO_RECON_PLMP, hydro.HYDRO_RIEMANN_ROE)],
+    ids=["3d_ppmc_exact", "3d_ppmc_roe", "2d_plmp_exact", "2d_plmp_roe"])
+def test_noh_parity_10_steps(nd, n, recon, solver, mode):
+    """The Noh boundary (time-dependent analytic ghosts, evaluated on the GPU
+    at the time the update kernel advances) and the reflecting walls' cold
+    supersonic collisions (the HLLE limit with zero bounds, Roe solver) match
+    the oracle with the tolerance of the PPMC path -- except one combination:
+    the Roe solver on PPMC states of this cold gas (p = 1e-6 under a kinetic
+    energy of 0.5) forms intermediate pressures whose sign, which picks the Roe
+    or the HLLE flux, is decided at the rounding level, so the fast mode's
+    fused arithmetic takes some of those branches the other way.  Only the
+    strict mode, the oracle's operation order, reproduces those decisions
+    (the fast mode tests p < 0 as 2 E rho < |m|^2, the same condition rounded
+    differently); the fast mode is held there to an L1 bound."""
+    w = noh_case(n, nd)
+    ug, uo, tg, to = run_both(w, 10, precision=mode, recon=recon, solver=solver)
+    if (mode == hydro.HYDRO_FP64 and solver == hydro.HYDRO_RIEMANN_ROE
+            and recon == hydro.HYDRO_RECON_PPMC):
+        d = np.abs(ug - uo).reshape(5, -1).sum(axis=1)
+        s = np.abs(uo).reshape(5, -1).sum(axis=1)
+        l1 = d / np.array([s[0], s[1:4].max(), s[1:4].max(), s[1:4].max(), s[4]])
+        print("noh %dd ppmc roe fast vs oracle: L1 %s, t %.17g vs %.17g" % (nd, l1, tg, to))
+        assert abs(tg / to - 1) < 1e-4
+        assert np.all(l1 <= 1e-4), l1  # measured 2.0e-5 on every field
+        return
+    assert tg == pytest.approx(to, rel=1e-13)
+    err = rel_err(ug, uo, FLOOR[mode])
+    assert err.max() <= TOL, (err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+def test_noh_mixed_precision_l1():
+    w = noh_case(16, 3)
+    uo, to, no, fl = oracle.run(w["u"], w["dx"], w["gamma"], w["bc"], nsteps=10, cfl=0.3,
+                                inflow=w["inflow"])
+    assert fl == 0
+    um, tm, nm = hydro.run(w["u"], w["dx"], w["gamma"], w["bc"], nsteps=10, cfl=0.3,
+                           inflow=w["inflow"], precision=hydro.HYDRO_MIXED)
+    d = np.abs(um - uo).reshape(5, -1).sum(axis=1)
+    s = np.abs(uo).reshape(5, -1).sum(axis=1)
+    l1 = d / np.array([s[0], s[1:4].max(), s[1:4].max(), s[1:4].max(), s[4]])
+    assert np.all(l1 <= 1e-5), l1
+
+
+def test_time_is_kept_on_the_device():
+    w = noh_case(16, 2)
+    g = hydro.Grid(16, 16, 1, w["dx"], w["gamma"], w["bc"])
+    try:
+        for f, p in w["inflow"].items():
+            g.set_inflow(f, p)
+        g.set_state(w["u"])
+        assert g.get_time() == 0.0
+        total = 0.0
+        for _ in range(3):
+            total += g.step(0.3)
+        assert g.get_time() == total
+        g.set_time(0.25)
+        assert g.get_time() == 0.25
+        g.set_state(w["u"])  # a new state keeps the time
+        assert g.get_time() == 0.25
+        with pytest.raises(hydro.HydroError):
+            g.set_time(-1.0)
+    finally:
+        g.close()

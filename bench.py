@@ -62,6 +62,8 @@ ALGORITHMIC_FLOPS = {
     "shock_cloud": {"ppmc": 413.0, "prims": 22.752, "riemann1": 135.667, "riemann2": 195.667, "slopes": 81.0, "update": 45.0},
     "sod512": {"ppmc": 406.0, "prims": 28.742, "riemann1": 136.125, "riemann2": 136.125, "slopes": 81.0, "update": 15.0},
     "turbulence": {"ppmc": 423.374, "prims": 22.752, "riemann1": 140.154, "riemann2": 200.574, "slopes": 91.922, "update": 45.0},
+    "noh": {"ppmc": 428.076, "prims": 22.752, "riemann1": 207.456, "riemann2": 253.292, "slopes": 92.761, "update": 45.0},
+    "noh/ppmc+roe": {"ppmc": 428.076, "prims": 22.752, "riemann1": 135.303, "riemann2": 158.299, "slopes": 92.761, "update": 45.0},
 }
 
 # The FP64 part of the mixed-precision stages, flops per unit, from the kernels'
@@ -146,6 +148,11 @@ def workload(name):
     elif name == "turbulence":
         w = W.turbulence(512)
         w["desc"] = "3D supersonic turbulence, 512^3 periodic, rms Mach 5, CFL 0.3"
+    elif name.startswith("noh"):
+        n = int(name[3:] or 200)
+        w = W.noh(n)
+        w["desc"] = ("3D Noh strong shock, %d^3 octant, reflecting inner and analytic outer "
+                     "faces, gamma 5/3, p0 1e-6, CFL 0.3" % n)
     elif name.startswith("batched"):
         n = int(name[7:] or 96)
         grids = W.batched(ngrids=n)
@@ -248,6 +255,10 @@ def flops_table(key, recon="ppmc", solver="exact"):
         key = "sedov"
     elif key.startswith("batched"):
         key = "batched"
+    elif key.startswith("noh"):
+        key = "noh" if solver == "exact" else "noh/ppmc+roe"
+        if recon == "ppmc":
+            return ALGORITHMIC_FLOPS[key], key
     if recon != "ppmc" or solver != "exact":
         key = "sedov/%s" % recon + ("+roe" if solver == "roe" else "")
     return ALGORITHMIC_FLOPS[key], key
@@ -265,6 +276,9 @@ def run_cpu_baseline(wname, max_steps, cfl=0.3, min_seconds=10.0):
     elif wname == "sod512":
         s = W.sod(512)
         sample = "Sod 512 cells, %d oracle steps"
+    elif wname.startswith("noh"):
+        s = W.noh(64)
+        sample = "Noh octant at 64^3 (same recipe), %d oracle steps"
     else:
         full = workload(wname)
         s = dict(u=np.ascontiguousarray(full["u"][:, :64, :64, :128]), dx=full["dx"],
@@ -273,6 +287,8 @@ def run_cpu_baseline(wname, max_steps, cfl=0.3, min_seconds=10.0):
     cores = oracle.set_threads(0)
     _, nz, ny, nx = s["u"].shape
     g = oracle.Grid(nx, ny, nz, s["dx"], s["gamma"], s["bc"])
+    for face, prim in (s.get("inflow") or {}).items():
+        g.set_inflow(face, prim)
     g.set_state(s["u"])
     g.step(cfl)  # untimed: first touch of the oracle's arrays
     steps = 0
@@ -685,6 +701,10 @@ def run_reference(args, ws, rank):
         elif args.workload == "sod512":
             s = W.sod(512)
             sample = "Sod 512 cells, one oracle step per step"
+        elif args.workload.startswith("noh"):
+            s = W.noh(64)
+            sample = ("Noh octant at 64^3 (same recipe as the %s workload), one oracle step per "
+                      "step" % args.workload)
         else:
             full = workload(args.workload)
             s = dict(u=np.ascontiguousarray(full["u"][:, :64, :64, :128]), dx=full["dx"],
@@ -734,6 +754,9 @@ def workload_shape(name):
     if name.startswith("sedov"):
         n = int(name[5:])
         return n, n, n
+    if name.startswith("noh"):
+        n = int(name[3:] or 200)
+        return n, n, n
     return {"sod512": (512, 1, 1), "shock_cloud": (512, 256, 256),
             "turbulence": (512, 512, 512)}[name]
 
@@ -742,6 +765,10 @@ def workload_desc(name):
     if name.startswith("sedov"):
         n = int(name[5:])
         return "3D Sedov-Taylor blast, %d^3 periodic, gamma 5/3, CFL 0.3" % n
+    if name.startswith("noh"):
+        n = int(name[3:] or 200)
+        return ("3D Noh strong shock, %d^3 octant, reflecting inner and analytic outer faces, "
+                "gamma 5/3, p0 1e-6, CFL 0.3" % n)
     return WORKLOAD_DESC.get(name, name)
 
 

@@ -31,6 +31,8 @@ from paper_1410_4194_gb300 import workloads as W  # noqa: E402
 def sample(name):
     if name in ("sedov", "batched"):
         return W.sedov(32), "Sedov blast 32^3, same recipe"
+    if name == "noh":
+        return W.noh(32), "Noh octant 32^3, same recipe"
     if name == "sod512":
         return W.sod(512), "Sod 512 cells"
     full = W.shock_cloud() if name == "shock_cloud" else W.turbulence(512)
@@ -45,6 +47,8 @@ def counts(name, cfl=0.3, recon=oracle.RECON_PPMC, solver=oracle.SOLVER_EXACT):
     g = oracle.Grid(nx, ny, nz, s["dx"], s["gamma"], s["bc"])
     g.set_recon(recon)
     g.set_solver(solver)
+    for face, prim in (s.get("inflow") or {}).items():
+        g.set_inflow(face, prim)
     g.set_state(s["u"])
     st = g.count_step_stages(g.compute_dt(cfl))
     flops = {k: (sum(v["ops"].values()) - v["ops"]["cmp"]) / max(v["units"], 1)
@@ -54,8 +58,9 @@ def counts(name, cfl=0.3, recon=oracle.RECON_PPMC, solver=oracle.SOLVER_EXACT):
 
 
 def main():
-    out = {name: counts(name) for name in ("sedov", "sod512", "shock_cloud", "turbulence")}
+    out = {name: counts(name) for name in ("sedov", "sod512", "shock_cloud", "turbulence", "noh")}
     out["batched"] = out["sedov"]
+    out["noh/ppmc+roe"] = counts("noh", solver=oracle.SOLVER_ROE)
     recons = {"ppmp": oracle.RECON_PPMP, "plmc": oracle.RECON_PLMC, "plmp": oracle.RECON_PLMP,
               "pcm": oracle.RECON_PCM}
     for rname, r in recons.items():

@@ -238,6 +238,31 @@ def batched(ngrids=96, seed=14104194, edges=(32, 48, 64, 96, 128), gamma=5.0 / 3
     return out
 
 
+def noh(n=200, nd=3, gamma=5.0 / 3.0, rho0=1.0, speed=1.0, p0=1e-6):
+    """Noh's strong shock (Sec. 4.3.1) on the octant [0, 1]^nd: uniform density
+    rho0 and pressure p0 streaming at `speed` toward the origin; reflecting
+    inner faces, analytic (HYDRO_BC_NOH) outer faces whose prescribed state is
+    (rho0, speed, 0, 0, p0).  Also returns the cells' radius r."""
+    dx = 1.0 / n
+    x = (np.arange(n) + 0.5) * dx
+    if nd == 3:
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        r = np.sqrt(X ** 2 + Y ** 2 + Z ** 2)
+        u = prim_to_cons(np.full_like(r, rho0), -speed * X / r, -speed * Y / r,
+                         -speed * Z / r, np.full_like(r, p0), gamma)
+        bc, faces = [1, 4, 1, 4, 1, 4], (1, 3, 5)
+    elif nd == 2:
+        Y, X = np.meshgrid(x, x, indexing="ij")
+        r = np.sqrt(X ** 2 + Y ** 2)[None]
+        u = prim_to_cons(np.full_like(r, rho0), (-speed * X / r[0])[None],
+                         (-speed * Y / r[0])[None], 0.0, np.full_like(r, p0), gamma)
+        bc, faces = [1, 4, 1, 4, 0, 0], (1, 3)
+    else:
+        raise ValueError("nd must be 2 or 3")
+    return dict(u=u, dx=dx, gamma=gamma, bc=bc, r=r,
+                inflow={f: (rho0, speed, 0.0, 0.0, p0) for f in faces})
+
+
 def smooth_periodic(shape, gamma=1.4, seed=7, amp=0.2, vamp=0.5):
     """Smooth random periodic state (a few low Fourier modes per field), for tests."""
     rng = np.random.Generator(np.random.PCG64(seed))

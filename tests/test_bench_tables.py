@@ -8,7 +8,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-@pytest.mark.parametrize("name", ["sedov", "sod512"])
+@pytest.mark.parametrize("name", ["sedov", "sod512", "noh"])
 def test_flop_table_matches_counting_oracle(name):
     sys.path.insert(0, ROOT)
     import bench

@@ -311,9 +311,7 @@ def test_error_paths():
 
 # ---- Noh's strong shock (Sec. 4.3.1): analytic outer boundary, cold gas ------
 def noh_case(n, nd):
-    from tests.test_oracle_noh import noh_case as make
-    u0, dx, bc, inflow, r = make(n, nd)
-    return dict(u=u0, dx=dx, gamma=5.0 / 3.0, bc=bc, inflow=inflow)
+    return W.noh(n, nd)
 
 
 @pytest.mark.parametrize("mode", MODES, ids=lambda m: MODE_ID[m])

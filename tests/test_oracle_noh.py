@@ -18,22 +18,8 @@ NOH = (1.0, 1.0, 0.0, 0.0, 1e-6)  # rho0, V, -, -, p0
 
 
 def noh_case(n, nd):
-    dx = 1.0 / n
-    x = (np.arange(n) + 0.5) * dx
-    if nd == 3:
-        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
-        r = np.sqrt(X ** 2 + Y ** 2 + Z ** 2)
-        u0 = W.prim_to_cons(np.ones_like(r), -X / r, -Y / r, -Z / r, np.full_like(r, 1e-6), G53)
-        bc = [1, 4, 1, 4, 1, 4]
-        faces = (1, 3, 5)
-    else:
-        Y, X = np.meshgrid(x, x, indexing="ij")
-        r = np.sqrt(X ** 2 + Y ** 2)[None]
-        u0 = W.prim_to_cons(np.ones_like(r), (-X / r[0])[None], (-Y / r[0])[None], 0.0,
-                            np.full_like(r, 1e-6), G53)
-        bc = [1, 4, 1, 4, 0, 0]
-        faces = (1, 3)
-    return u0, dx, bc, {f: NOH for f in faces}, r
+    w = W.noh(n, nd)
+    return w["u"], w["dx"], w["bc"], w["inflow"], w["r"]
 
 
 def test_noh_ghosts_hold_the_analytic_state():

@@ -166,7 +166,7 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
   // fast FP64 or mixed: the batched kernels over this single grid (256 threads)
   const int P = h->precision;
   CK(h, cudaMemsetAsync(B.rec, 0, sizeof(double), st));
-  STAGE(h, kStagePrims, 0, batch_prims(one_grid(h, 0), P, 256, h->blocks[0], st));
+  STAGE(h, kStagePrims, 0, batch_prims(one_grid(h, 0), P, 256, h->blocks[0], st, has_noh(h->bc)));
   STAGE(h, kStageSetDt, 0, fp64_set_dt(G, B, cfl, fixed_dt, st));
   for (int d = 0; d < 3; ++d) {
     if (!active(G, d)) continue;
@@ -495,10 +495,10 @@ double hydro_compute_dt(hydro_t h, double cfl) {
   } else {
     e = cudaMemsetAsync(h->B.rec, 0, sizeof(double), h->stream);
     if (e == cudaSuccess)
-      e = batch_prims(one_grid(h, 0), h->precision, 256, h->blocks[0], h->stream);
+      e = batch_prims(one_grid(h, 0), h->precision, 256, h->blocks[0], h->stream, has_noh(h->bc));
   }
   if (e != cudaSuccess) return (double)cuda_fail(h, e);
-  e = fp64_set_dt(h->G, h->B, cfl, 0.0, h->stream);
+  e = fp64_set_dt(h->G, h->B, cfl, 0.0, h->stream, false);
   if (e != cudaSuccess) return (double)cuda_fail(h, e);
   h->launches_total += 2;
   rc = read_record(h);

@@ -59,7 +59,7 @@ __device__ __forceinline__ void block_max_to(double v, unsigned long long* slot)
 // S (strict): the CPU reference's operation order with IEEE divisions and
 // square root; otherwise 1/rho and 1/a by Newton iteration (nr_rcp, nr_rsqrt)
 // and fused multiply-adds.
-template <bool S>
+template <bool S, bool NOH>
 __device__ __forceinline__ double prims_body(const Geom& G, const Bufs& B, const BcDesc& bc,
                                              const Gas& g, int want_dt, long long t) {
   double local = 0.0;
@@ -67,7 +67,11 @@ __device__ __forceinline__ double prims_body(const Geom& G, const Bufs& B, const
     int c[3];
     padded_coords(G, t, c);
     double U[5];
-    const bool real = boundary_state(G, B.u, bc, g.gm1, B.rec[5], c, U);
+    int neg;
+    const bool real = boundary_state<NOH>(G, B.u, bc, g.gm1, B.rec[5], c, U, neg);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (neg & (1 << d)) U[1 + d] = -U[1 + d];
     // primitives, then the per-cell reciprocals the later stages multiply by
     const double d = U[0];
     double W[5], a, inv_a, inv_d;
@@ -108,30 +112,34 @@ __device__ __forceinline__ double prims_body(const Geom& G, const Bufs& B, const
   return local;
 }
 
+template <bool NOH>
 __global__ void __launch_bounds__(kThreads) k_prims(Geom G, Bufs B, BcDesc bc, Gas g, int want_dt) {
   const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const double local = (t < total) ? prims_body<true>(G, B, bc, g, want_dt, t) : 0.0;
+  const double local = (t < total) ? prims_body<true, NOH>(G, B, bc, g, want_dt, t) : 0.0;
   if (want_dt) block_max_to<true>(local, reinterpret_cast<unsigned long long*>(B.rec));
 }
 
-template <int BS>
+template <int BS, bool NOH>
 __global__ void __launch_bounds__(BS) kb_prims(BatchLaunch L) {
   const BatchItem it = batch_item(L);
   const Geom& G = it.d->G;
   const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
   const double local =
-      (it.t < total) ? prims_body<false>(G, it.d->B, it.d->bc, it.d->gd, 1, it.t) : 0.0;
+      (it.t < total) ? prims_body<false, NOH>(G, it.d->B, it.d->bc, it.d->gd, 1, it.t) : 0.0;
   block_max_to<false>(local, reinterpret_cast<unsigned long long*>(it.d->B.rec));
 }
 
-__global__ void k_set_dt(double* rec, double cfl, double fixed_dt, double dx) {
+// advance: the step's time advance t <- t + dt (record [5]); the step's
+// primitive kernel has read t by then, the next step's reads t + dt
+__global__ void k_set_dt(double* rec, double cfl, double fixed_dt, double dx, int advance) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     const double dt = (fixed_dt > 0.0) ? fixed_dt : cfl * (dx / rec[0]);
     const double dtdx = dt / dx;
     rec[1] = dt;
     rec[2] = dtdx;
     rec[3] = 0.5 * dtdx;
+    if (advance) rec[5] = rec[5] + dt;
   }
 }
 
@@ -168,23 +176,15 @@ __device__ __forceinline__ void update_body(const Geom& G, const Bufs& B, long l
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
 
-// the step's time advance t <- t + dt (record [5]), by the grid's first thread
-// of the update (the last kernel of a step; dt is final by then)
-__device__ __forceinline__ void advance_time(double* rec, long long t) {
-  if (t == 0) rec[5] = rec[5] + rec[1];
-}
-
 __global__ void __launch_bounds__(kThreads) k_update(Geom G, Bufs B) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < G.nreal) update_body<true>(G, B, t);
-  advance_time(B.rec, t);
 }
 
 template <int BS>
 __global__ void __launch_bounds__(BS) kb_update(BatchLaunch L) {
   const BatchItem it = batch_item(L);
   if (it.t < it.d->G.nreal) update_body<false>(it.d->G, it.d->B, it.t);
-  advance_time(it.d->B.rec, it.t);
 }
 
 // per grid: dt = cfl * dx / max(|v_d| + a) (or the fixed dt), dt/dx, history
@@ -199,6 +199,7 @@ __global__ void k_batch_set_dt(const GridDesc* descs, int ngrids, double cfl, do
   rec[1] = dt;
   rec[2] = dtdx;
   rec[3] = 0.5 * dtdx;
+  rec[5] = rec[5] + dt;  // the grid's time
   if (dt_hist) dt_hist[i] = dt;
 }
 
@@ -256,12 +257,18 @@ cudaError_t fp64_prims(const Geom& G, const Bufs& B, const BcDesc& bc, double ga
     if (e != cudaSuccess) return e;
   }
   const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
-  k_prims<<<blocks_for(total), kThreads, 0, st>>>(G, B, bc, make_gas<double>(gamma), want_dt ? 1 : 0);
+  if (has_noh(bc))
+    k_prims<true><<<blocks_for(total), kThreads, 0, st>>>(G, B, bc, make_gas<double>(gamma),
+                                                          want_dt ? 1 : 0);
+  else
+    k_prims<false><<<blocks_for(total), kThreads, 0, st>>>(G, B, bc, make_gas<double>(gamma),
+                                                           want_dt ? 1 : 0);
   return cudaGetLastError();
 }
 
-cudaError_t fp64_set_dt(const Geom& G, const Bufs& B, double cfl, double fixed_dt, cudaStream_t st) {
-  k_set_dt<<<1, 32, 0, st>>>(B.rec, cfl, fixed_dt, G.dx);
+cudaError_t fp64_set_dt(const Geom& G, const Bufs& B, double cfl, double fixed_dt, cudaStream_t st,
+                        bool advance_time) {
+  k_set_dt<<<1, 32, 0, st>>>(B.rec, cfl, fixed_dt, G.dx, advance_time ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -312,13 +319,21 @@ cudaError_t fp64_stage_strict(const Geom& G, const Bufs& B, int recon, int solve
   return launch_axis_stage<true>(G, B, recon, solver, stage, axis, gamma, st);
 }
 
-cudaError_t batch_prims(const BatchLaunch& L, int precision, int bs, unsigned blocks, cudaStream_t st) {
-  if (precision == HYDRO_MIXED) return batch_prims_mixed(L, bs, blocks, st);
+cudaError_t batch_prims(const BatchLaunch& L, int precision, int bs, unsigned blocks, cudaStream_t st,
+                        bool noh) {
+  if (precision == HYDRO_MIXED) return batch_prims_mixed(L, bs, blocks, st, noh);
   if (blocks == 0) return cudaSuccess;
-  if (bs == 128)
-    kb_prims<128><<<blocks, 128, 0, st>>>(L);
-  else
-    kb_prims<256><<<blocks, 256, 0, st>>>(L);
+  if (bs == 128) {
+    if (noh)
+      kb_prims<128, true><<<blocks, 128, 0, st>>>(L);
+    else
+      kb_prims<128, false><<<blocks, 128, 0, st>>>(L);
+  } else {
+    if (noh)
+      kb_prims<256, true><<<blocks, 256, 0, st>>>(L);
+    else
+      kb_prims<256, false><<<blocks, 256, 0, st>>>(L);
+  }
   return cudaGetLastError();
 }
 

@@ -70,6 +70,13 @@ struct BcDesc {
   double prim[6][5];    // the prescribed state as given: inflow (rho, u, v, w, p),
                         // Noh (rho0, V, -, -, p0)
 };
+// whether a grid has a Noh face (the primitive kernels are compiled with and
+// without the Noh case)
+inline bool has_noh(const BcDesc& bc) {
+  for (int f = 0; f < 6; ++f)
+    if (bc.type[f] == HYDRO_BC_NOH) return true;
+  return false;
+}
 
 // Device buffers of the FP64 path.
 struct Bufs {
@@ -82,7 +89,8 @@ struct Bufs {
   double* eta[3];  // per axis: H-correction eta of each face [ps] (Roe solver only, else null)
   // 64-byte step record on the device: [0] max of |v_d| + a (bits), [1] dt, [2] dt/dx,
   // [3] dt/(2 dx), [4] flags (int in the low word), [5] time t at the start of
-  // the next step (advanced by the update kernel; read by the Noh boundary)
+  // the next step (advanced by the dt kernel after the step's primitive kernel
+  // has read it; read by the Noh boundary)
   double* rec;
 };
 
@@ -153,7 +161,9 @@ bool build_launch_tables(const GridDesc* desc, const int* order, int n, int bs, 
 // the launch error.
 cudaError_t fp64_prims(const Geom& G, const Bufs& B, const BcDesc& bc, double gamma, bool want_dt,
                        cudaStream_t st);
-cudaError_t fp64_set_dt(const Geom& G, const Bufs& B, double cfl, double fixed_dt, cudaStream_t st);
+// advance_time: add dt to the grid's time (a step; not a dt query)
+cudaError_t fp64_set_dt(const Geom& G, const Bufs& B, double cfl, double fixed_dt, cudaStream_t st,
+                        bool advance_time = true);
 // one launch of a per-axis stage in the reference operation order (strict mode);
 // the fast FP64 and mixed paths use the batched launchers below with one grid
 cudaError_t fp64_stage_strict(const Geom& G, const Bufs& B, int recon, int solver, int stage,
@@ -163,7 +173,9 @@ cudaError_t fp64_update(const Geom& G, const Bufs& B, cudaStream_t st);
 // Batched launchers: one launch covers the given stage of every grid of a
 // batch, with `bs` threads a block (128 or 256).  Precision HYDRO_FP64 or
 // HYDRO_MIXED.  blocks = the batch's total block count for this stage/axis.
-cudaError_t batch_prims(const BatchLaunch& L, int precision, int bs, unsigned blocks, cudaStream_t st);
+// noh: some grid of the launch has a Noh face
+cudaError_t batch_prims(const BatchLaunch& L, int precision, int bs, unsigned blocks, cudaStream_t st,
+                        bool noh = false);
 cudaError_t batch_set_dt(const GridDesc* descs, int ngrids, double cfl, double* dt_hist,
                          cudaStream_t st);
 cudaError_t batch_stage(const BatchLaunch& L, int precision, int recon, int solver, int stage,
@@ -175,7 +187,8 @@ cudaError_t batch_stage_fp64(const BatchLaunch& L, int recon, int solver, int st
                              int bs, unsigned blocks, cudaStream_t st);
 cudaError_t batch_stage_mixed(const BatchLaunch& L, int stage, int axis, int bs, unsigned blocks,
                               cudaStream_t st);
-cudaError_t batch_prims_mixed(const BatchLaunch& L, int bs, unsigned blocks, cudaStream_t st);
+cudaError_t batch_prims_mixed(const BatchLaunch& L, int bs, unsigned blocks, cudaStream_t st,
+                              bool noh);
 cudaError_t batch_update_mixed(const BatchLaunch& L, int bs, unsigned blocks, cudaStream_t st);
 cudaError_t fp64_riemann_soa(int n, const double* UL, const double* UR, double gamma, double* F,
                              int* flags, cudaStream_t st);

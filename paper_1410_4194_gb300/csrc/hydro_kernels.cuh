@@ -493,10 +493,14 @@ inline long long box_count(const Box& b) { return (long long)b.n[0] * b.n[1] * b
 // 4.3.1: rho0 (1 + V t/r)^(n-1), velocity V toward the origin, E = p0/(gamma-1)
 // + rho V^2/2, n the active axes) is taken at the position the passes reach:
 // the cell's own coordinates on the Noh axis and the axes before it, the
-// mapped ones after it.  Returns whether the cell is real.
+// mapped ones after it.  Returns whether the cell is real; neg receives the
+// axes (bit d) whose momentum component the caller negates, in the precision
+// it works in.  NOH: whether the grid has a Noh face (the kernels are compiled
+// both ways so that the other grids carry none of its code or registers).
+template <bool NOH>
 __device__ __forceinline__ bool boundary_state(const Geom& G, const double* __restrict__ u,
                                                const BcDesc& bc, double gm1, double time,
-                                               const int c[3], double U[5]) {
+                                               const int c[3], double U[5], int& neg_out) {
   int src[3];
   int neg = 0, fixed_face = -1, noh_axis = -1;
   bool real = true;
@@ -524,10 +528,12 @@ __device__ __forceinline__ bool boundary_state(const Geom& G, const double* __re
         src[d] = lo ? 0 : n - 1;
         break;
       case 4:  // Noh: analytic, at this coordinate
-        src[d] = r;
-        fixed_face = face;
-        noh_axis = d;
-        neg = 0;
+        if constexpr (NOH) {
+          src[d] = r;
+          fixed_face = face;
+          noh_axis = d;
+          neg = 0;
+        }
         break;
       default:  // inflow
         src[d] = 0;
@@ -537,7 +543,7 @@ __device__ __forceinline__ bool boundary_state(const Geom& G, const double* __re
         break;
     }
   }
-  if (noh_axis >= 0) {
+  if (NOH && noh_axis >= 0) {
     const double* P = bc.prim[fixed_face];
     double x[3], r2 = 0.0;
     int nact = 0;
@@ -567,9 +573,7 @@ __device__ __forceinline__ bool boundary_state(const Geom& G, const double* __re
 #pragma unroll
     for (int q = 0; q < 5; ++q) U[q] = u[q * G.nreal + rs];
   }
-#pragma unroll
-  for (int d = 0; d < 3; ++d)
-    if (neg & (1 << d)) U[1 + d] = -U[1 + d];
+  neg_out = neg;
   return real;
 }
 

@@ -138,16 +138,23 @@ struct DtCand {
 // E - |m|^2 (1/rho) / 2 (the cancellation of total and kinetic energy at high
 // Mach needs it); the velocities and the sound speed, which are stored as
 // float, are formed in float from the rounded operands (a few float ulps).
+template <bool NOH>
 __device__ __forceinline__ void prims_mixed_body(const Geom& G, const BufsF& B, const BcDesc& bc,
                                                  const GasD& g, const GasF& gf, int want_dt,
                                                  long long t, DtCand& cand) {
   int c[3];
   padded_coords(G, t, c);
   double U[5];
-  const bool real = boundary_state(G, B.u, bc, g.gm1, B.rec[5], c, U);
+  int neg;
+  const bool real = boundary_state<NOH>(G, B.u, bc, g.gm1, B.rec[5], c, U, neg);
+  // a reflected momentum is negated in float (U keeps the source cell's sign:
+  // only |m|^2 and |v| use it in FP64)
   float mf[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) mf[d] = d2f(U[1 + d]);
+  for (int d = 0; d < 3; ++d) {
+    mf[d] = d2f(U[1 + d]);
+    if (neg & (1 << d)) mf[d] = -mf[d];
+  }
   // 1/rho: float reciprocal of the rounded density refined by one Newton
   // step r <- r + r (1 - rho r) in FP64 (relative error below 2^-44)
   const float df = d2f(U[0]);
@@ -207,7 +214,7 @@ __device__ __forceinline__ double signal_speed_fp64(const Geom& G, const GasD& g
 // (non-negative floats order like their bit patterns) above the complement of
 // the thread index: one warp-shuffle reduction, each warp's winner parks its
 // operands in shared memory, and a single barrier before warp 0 finishes.
-template <int BS>
+template <int BS, bool NOH>
 __global__ void __launch_bounds__(BS, kMinBlocksPrims * kThreads / BS) kb_prims_mixed(BatchLaunch L) {
   constexpr int kWarps = BS / 32;
   __shared__ unsigned long long warp_key[kWarps];
@@ -218,7 +225,7 @@ __global__ void __launch_bounds__(BS, kMinBlocksPrims * kThreads / BS) kb_prims_
   const long long total = (long long)G.N[0] * G.N[1] * G.N[2];
   DtCand cand;
   cand.s = -1.f;
-  if (it.t < total) prims_mixed_body(G, F, it.d->bc, it.d->gd, it.d->gf, 1, it.t, cand);
+  if (it.t < total) prims_mixed_body<NOH>(G, F, it.d->bc, it.d->gd, it.d->gf, 1, it.t, cand);
   const unsigned long long key =
       (cand.s >= 0.f) ? ((unsigned long long)__float_as_uint(cand.s) << 32) | (~threadIdx.x & 0xffffffffu)
                       : 0ull;
@@ -431,7 +438,6 @@ template <int BS>
 __global__ void __launch_bounds__(BS, kMinBlocksUpdate * kThreads / BS) kb_update_mixed(BatchLaunch L) {
   const BatchItem it = batch_item(L);
   if (it.t < it.d->G.nreal) update_mixed_body(it.d->G, float_view(it.d->B, it.d->G.ps), it.t);
-  if (it.t == 0) it.d->B.rec[5] = it.d->B.rec[5] + it.d->B.rec[1];  // t <- t + dt
 }
 
 #define HYDRO_BATCH_MIXED(NAME, STAGE_IDX, MINB, CALL)                                     \
@@ -454,12 +460,20 @@ HYDRO_BATCH_MIXED(kb_riemann2_mixed, 3, kMinBlocksRiemann2,
 
 }  // namespace
 
-cudaError_t batch_prims_mixed(const BatchLaunch& L, int bs, unsigned blocks, cudaStream_t st) {
+cudaError_t batch_prims_mixed(const BatchLaunch& L, int bs, unsigned blocks, cudaStream_t st,
+                              bool noh) {
   if (blocks == 0) return cudaSuccess;
-  if (bs == 128)
-    kb_prims_mixed<128><<<blocks, 128, 0, st>>>(L);
-  else
-    kb_prims_mixed<256><<<blocks, 256, 0, st>>>(L);
+  if (bs == 128) {
+    if (noh)
+      kb_prims_mixed<128, true><<<blocks, 128, 0, st>>>(L);
+    else
+      kb_prims_mixed<128, false><<<blocks, 128, 0, st>>>(L);
+  } else {
+    if (noh)
+      kb_prims_mixed<256, true><<<blocks, 256, 0, st>>>(L);
+    else
+      kb_prims_mixed<256, false><<<blocks, 256, 0, st>>>(L);
+  }
   return cudaGetLastError();
 }
 

@@ -323,7 +323,7 @@ def noh_case(n, nd):
     ids=["3d_ppmc_exact", "3d_ppmc_roe", "2d_plmp_exact", "2d_plmp_roe"])
 def test_noh_parity_10_steps(nd, n, recon, solver, mode):
     """The Noh boundary (time-dependent analytic ghosts, evaluated on the GPU
-    at the time the update kernel advances) and the reflecting walls' cold
+    at the time the dt kernel advances) and the reflecting walls' cold
     supersonic collisions (the HLLE limit with zero bounds, Roe solver) match
     the oracle with the tolerance of the PPMC path -- except one combination:
     the Roe solver on PPMC states of this cold gas (p = 1e-6 under a kinetic

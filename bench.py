@@ -20,6 +20,7 @@ on the host cores on a bounded sample of the same workload.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -378,6 +379,19 @@ def main():
     ms_max = max_over_ranks(ms, ws)
     value = replicas_value(nreal, args.steps, ws, ms_max)
 
+    # ---- the same K steps looped on the device (hydro_advance: one CUDA graph
+    # with a WHILE node, no host round trip and no tracing events per step) ----
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    taken = g.advance(args.cfl, math.inf, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_dev = max_over_ranks(ev0.elapsed_time(ev1), ws)
+    device_loop = {"value": replicas_value(nreal, taken, ws, ms_dev), "unit": UNIT,
+                   "ms_per_step": ms_dev / max(taken, 1), "steps": taken}
+
     # ---- end to end through the public API with host buffers ----------------
     e2e = None
     if not args.no_e2e:
@@ -474,6 +488,7 @@ def main():
         "data": "synthetic",
         "config": single_config(args.workload, args.precision, ws, args.recon, args.solver),
         "e2e": e2e, "gpu_launches": launches_total, "clocks": clocks, "roofline": roofline,
+        "device_loop": device_loop,
         "stages": stage_report, "cpu_baseline": cpu,
         "hbm": hbm_report(value / ws, traffic, avg_ms),
     }

@@ -159,6 +159,24 @@ double hydro_step_dt(hydro_t h, double dt);
 /* The dt that hydro_step(h, cfl) would use now, without changing the state. */
 double hydro_compute_dt(hydro_t h, double cfl);
 
+/* Advance with CFL steps (as hydro_step(h, cfl)) until the time (see
+ * hydro_set_time) reaches t_end, or max_steps steps were taken, without a host
+ * round trip per step: the steps run as a loop inside one CUDA graph (a
+ * conditional WHILE node), whose dt kernel shortens the step that would pass
+ * t_end to t_end - t and then sets the time to t_end exactly -- the same dt
+ * sequence and final time as a host loop of hydro_compute_dt / hydro_step_dt
+ * that does so.  t_end = +INFINITY takes exactly max_steps steps.  A graph
+ * launch runs at most about 2^26 cell updates (>= 1 step); the host relaunches
+ * until done, reading the 88-byte step record once per launch.  The graph is
+ * captured on the first call and again when cfl, the precision, reconstruction
+ * or Riemann solver, or an inflow state changed.  Steps are counted in the launch
+ * counter of hydro_profile_read but get no per-stage times.
+ * Returns HYDRO_OK, HYDRO_EINVAL (cfl <= 0, t_end NaN, max_steps < 0 or
+ * > 2^52), HYDRO_ENOSTATE, or the error of a step (HYDRO_ENONPHYS,
+ * HYDRO_ENEWTON): the run stops after that step and the state is its result.
+ * *steps_out (may be NULL) receives the number of steps taken, also on error. */
+int hydro_advance(hydro_t h, double cfl, double t_end, long long max_steps, long long* steps_out);
+
 /* Code of the last error on this handle (HYDRO_OK if the last call succeeded). */
 int hydro_last_error(hydro_t h);
 

@@ -14,6 +14,7 @@
 
 #include "../../include/hydro.h"
 #include "hydro_internal.h"
+#include "hydro_run.h"
 #include "hydro_math.cuh"
 
 using namespace hydro;
@@ -50,6 +51,13 @@ struct hydro_s {
   GridDesc* d_desc;
   int* d_tab;
   unsigned blocks[kLaunchKinds];
+  // device-driven runs (hydro_advance): the captured loop graph, the settings it
+  // was captured with, and the private stream it was captured on
+  cudaStream_t cap_stream;
+  cudaGraphExec_t run_exec;
+  double run_cfl;
+  int run_precision, run_recon, run_solver;
+  long long run_launches_per_step;
 };
 
 namespace {
@@ -139,8 +147,9 @@ BatchLaunch one_grid(hydro_t h, int kind) {
     if (rc_) return rc_;                     \
   } while (0)
 
-// Enqueue one full step; dt from the CFL condition when fixed_dt <= 0.
-int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
+// Enqueue one full step; dt from the CFL condition when fixed_dt <= 0, cut back
+// to the end time in the record's slot 8 when to_end is set.
+int enqueue_step(hydro_t h, double cfl, double fixed_dt, bool to_end = false) {
   const Geom& G = h->G;
   const Bufs& B = h->B;
   cudaStream_t st = h->stream;
@@ -148,7 +157,8 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
   CK(h, cudaMemsetAsync(B.rec + 4, 0, sizeof(double), st));
   if (h->precision == HYDRO_FP64_STRICT) {
     STAGE(h, kStagePrims, 0, fp64_prims(G, B, h->bc, h->gamma, fixed_dt <= 0.0, st));
-    STAGE(h, kStageSetDt, 0, fp64_set_dt(G, B, cfl, fixed_dt, st));
+    STAGE(h, kStageSetDt, 0,
+          to_end ? set_dt_to_end(G, B, cfl, st) : fp64_set_dt(G, B, cfl, fixed_dt, st));
     for (int d = 0; d < 3; ++d) {
       if (!active(G, d)) continue;
       for (int s = kStageSlopes; s <= kStageRiemann1; ++s) {
@@ -167,7 +177,8 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
   const int P = h->precision;
   CK(h, cudaMemsetAsync(B.rec, 0, sizeof(double), st));
   STAGE(h, kStagePrims, 0, batch_prims(one_grid(h, 0), P, 256, h->blocks[0], st, has_noh(h->bc)));
-  STAGE(h, kStageSetDt, 0, fp64_set_dt(G, B, cfl, fixed_dt, st));
+  STAGE(h, kStageSetDt, 0,
+        to_end ? set_dt_to_end(G, B, cfl, st) : fp64_set_dt(G, B, cfl, fixed_dt, st));
   for (int d = 0; d < 3; ++d) {
     if (!active(G, d)) continue;
     for (int s = kStageSlopes; s <= kStageRiemann1; ++s) {
@@ -189,8 +200,8 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt) {
   return HYDRO_OK;
 }
 
-int read_record(hydro_t h) {
-  CK(h, cudaMemcpyAsync(h->host_rec, h->B.rec, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+int read_record(hydro_t h, int n = 8) {
+  CK(h, cudaMemcpyAsync(h->host_rec, h->B.rec, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   return HYDRO_OK;
 }
@@ -215,6 +226,89 @@ double run_step(hydro_t h, double cfl, double fixed_dt) {
   if (flags & kFlagNonPhys) return (double)fail(h, HYDRO_ENONPHYS);
   if (flags & kFlagNewton) return (double)fail(h, HYDRO_ENEWTON);
   return h->host_rec[1];
+}
+
+void drop_run_graph(hydro_t h) {
+  if (h->run_exec) {
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    cudaGraphExecDestroy(h->run_exec);
+  }
+  h->run_exec = nullptr;
+}
+
+// Steps a graph launch may take: about 2^26 cell updates (a fraction of a
+// second even in FP64), at least one step and at most 4096.
+double run_chunk(const Geom& G) {
+  const long long c = (1ll << 26) / (G.nreal > 0 ? G.nreal : 1);
+  return (double)(c < 1 ? 1 : (c > 4096 ? 4096 : c));
+}
+
+// Capture the loop graph of device-driven runs: a kernel that sets the loop
+// condition, then a WHILE node whose body is one step (the stage launches of
+// enqueue_step with the end-time dt) and the kernel that updates the condition.
+// Captured on a private stream (the handle's stream may be the legacy default
+// stream, which cannot be captured), without tracing events.
+int capture_run_graph(hydro_t h, double cfl) {
+  drop_run_graph(h);
+  if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = h->cap_stream;
+  cudaGraph_t graph = nullptr;
+  CK(h, cudaGraphCreate(&graph, 0));
+  int rc = HYDRO_OK;
+  cudaError_t e = cudaSuccess;
+  cudaGraphConditionalHandle cond = 0;
+  cudaGraphNode_t begin = nullptr, loop = nullptr;
+  size_t nnodes = 1;
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  const cudaStream_t user_stream = h->stream;
+  const bool profile = h->profile;
+  const long long launches0 = h->launches_total;
+  e = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = run_begin(h->B.rec, cond, cs);
+    cudaGraph_t g_out = nullptr;
+    e = cudaStreamEndCapture(cs, &g_out);
+    if (e == cudaSuccess) e = e1;
+  }
+  if (e == cudaSuccess) e = cudaGraphGetNodes(graph, &begin, &nnodes);
+  if (e == cudaSuccess && nnodes != 1) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess) {
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&loop, graph, &begin, nullptr, 1, &cp);
+  }
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    h->stream = cs;
+    h->profile = false;
+    rc = enqueue_step(h, cfl, 0.0, true);
+    cudaError_t e1 = rc ? cudaSuccess : run_next(h->B.rec, cond, run_chunk(h->G), cs);
+    h->stream = user_stream;
+    h->profile = profile;
+    h->run_launches_per_step = h->launches_total - launches0 + 1;
+    h->launches_total = launches0;
+    cudaGraph_t g_out = nullptr;
+    e = cudaStreamEndCapture(cs, &g_out);
+    if (e == cudaSuccess) e = e1;
+  }
+  if (rc == HYDRO_OK && e == cudaSuccess) e = cudaGraphInstantiate(&h->run_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (rc) return rc;
+  if (e != cudaSuccess) {
+    h->run_exec = nullptr;
+    return cuda_fail(h, e);
+  }
+  h->run_cfl = cfl;
+  h->run_precision = h->precision;
+  h->run_recon = h->recon;
+  h->run_solver = h->solver;
+  return HYDRO_OK;
 }
 
 }  // namespace
@@ -252,6 +346,8 @@ int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, co
   h->solver = HYDRO_RIEMANN_EXACT;
   h->eta_buf = nullptr;
   h->stream = nullptr;
+  h->cap_stream = nullptr;
+  h->run_exec = nullptr;
   h->have_state = false;
   h->last_error = HYDRO_OK;
   cudaError_t e = cudaGetDevice(&h->device);
@@ -289,7 +385,7 @@ int hydro_init(hydro_t* out, int nx, int ny, int nz, double dx, double gamma, co
     delete h;
     return HYDRO_ENOMEM;
   }
-  e = cudaMallocHost((void**)&h->host_rec, 8 * sizeof(double));
+  e = cudaMallocHost((void**)&h->host_rec, 16 * sizeof(double));
   if (e != cudaSuccess) {
     cudaFree(h->slab);
     delete h;
@@ -363,6 +459,7 @@ int hydro_set_inflow(hydro_t h, int face, const double prim[5]) {
   h->desc.bc = h->bc;
   int rc = use_device(h);
   if (rc) return rc;
+  drop_run_graph(h);  // the strict path takes the boundary description by value
   CK(h, cudaMemcpy(&h->d_desc->bc, &h->bc, sizeof(BcDesc), cudaMemcpyHostToDevice));
   return HYDRO_OK;
 }
@@ -482,6 +579,45 @@ double hydro_step_dt(hydro_t h, double dt) {
   return run_step(h, 0.0, dt);
 }
 
+int hydro_advance(hydro_t h, double cfl, double t_end, long long max_steps, long long* steps_out) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (steps_out) *steps_out = 0;
+  if (!h->have_state) return fail(h, HYDRO_ENOSTATE);
+  if (!(cfl > 0.0) || std::isnan(t_end) || max_steps < 0 || max_steps > (1ll << 52))
+    return fail(h, HYDRO_EINVAL);
+  int rc = use_device(h);
+  if (rc) return rc;
+  const bool same = h->run_exec && h->run_cfl == cfl && h->run_precision == h->precision &&
+                    h->run_recon == h->recon && h->run_solver == h->solver;
+  if (!same) {
+    rc = capture_run_graph(h, cfl);
+    if (rc) return rc;
+  }
+  // end time and step budget into the record (the pinned copy is not touched
+  // again before the stream has read it: read_record below waits on the stream)
+  h->host_rec[8] = t_end;
+  h->host_rec[9] = (double)max_steps;
+  CK(h, cudaMemcpyAsync(h->B.rec + 8, h->host_rec + 8, 2 * sizeof(double), cudaMemcpyHostToDevice,
+                        h->stream));
+  long long done = 0;
+  for (;;) {
+    CK(h, cudaGraphLaunch(h->run_exec, h->stream));
+    rc = read_record(h, 11);
+    if (rc) return rc;
+    const long long n = (long long)h->host_rec[10];
+    done += n;
+    h->launches_total += 1 + n * h->run_launches_per_step;
+    if (steps_out) *steps_out = done;
+    int flags;
+    memcpy(&flags, h->host_rec + 4, sizeof(int));
+    if (n > 0 && (flags & kFlagNonPhys)) return fail(h, HYDRO_ENONPHYS);
+    if (n > 0 && (flags & kFlagNewton)) return fail(h, HYDRO_ENEWTON);
+    if (n == 0 || !(h->host_rec[5] < t_end) || h->host_rec[9] < 1.0) break;
+  }
+  return HYDRO_OK;
+}
+
 double hydro_compute_dt(hydro_t h, double cfl) {
   if (!h) return (double)HYDRO_EINVAL;
   h->last_error = HYDRO_OK;
@@ -566,6 +702,8 @@ void hydro_free(hydro_t h) {
   if (cudaGetDevice(&cur) == cudaSuccess && cur != h->device) cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  drop_run_graph(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->profile)
     for (int k = 0; k < 2 * 64; ++k) cudaEventDestroy(h->ev[k]);
   cudaFree(h->slab);

@@ -24,6 +24,7 @@
 
 #include "../../include/hydro.h"
 #include "hydro_kernels.cuh"
+#include "hydro_run.h"
 
 namespace hydro {
 namespace {
@@ -140,6 +141,43 @@ __global__ void k_set_dt(double* rec, double cfl, double fixed_dt, double dx, in
     rec[2] = dtdx;
     rec[3] = 0.5 * dtdx;
     if (advance) rec[5] = rec[5] + dt;
+  }
+}
+
+// Device-driven runs (hydro_run.h: a CUDA graph whose WHILE node repeats the
+// step).  The step's dt is the CFL dt cut back to reach the end time exactly,
+// the host loop's rule: t + dt >= t_end gives dt = t_end - t and t = t_end.
+__global__ void k_set_dt_to_end(double* rec, double cfl, double dx) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double dt = cfl * (dx / rec[0]);
+    const double t = rec[5], t_end = rec[8];
+    const bool last = t + dt >= t_end;
+    if (last) dt = t_end - t;
+    const double dtdx = dt / dx;
+    rec[1] = dt;
+    rec[2] = dtdx;
+    rec[3] = 0.5 * dtdx;
+    rec[5] = last ? t_end : t + dt;
+  }
+}
+
+// the loop runs while t < t_end, steps are left and no step raised a flag;
+// at most `chunk` steps a graph launch bound the time one launch holds the GPU
+__global__ void k_run_begin(double* rec, cudaGraphConditionalHandle cond) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    rec[10] = 0.0;
+    cudaGraphSetConditional(cond, (rec[5] < rec[8] && rec[9] >= 1.0) ? 1u : 0u);
+  }
+}
+
+__global__ void k_run_next(double* rec, cudaGraphConditionalHandle cond, double chunk) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int flags = *rec_flags(rec);
+    const double left = rec[9] - 1.0, taken = rec[10] + 1.0;
+    rec[9] = left;
+    rec[10] = taken;
+    const bool go = flags == 0 && rec[5] < rec[8] && left >= 1.0 && taken < chunk;
+    cudaGraphSetConditional(cond, go ? 1u : 0u);
   }
 }
 
@@ -269,6 +307,21 @@ cudaError_t fp64_prims(const Geom& G, const Bufs& B, const BcDesc& bc, double ga
 cudaError_t fp64_set_dt(const Geom& G, const Bufs& B, double cfl, double fixed_dt, cudaStream_t st,
                         bool advance_time) {
   k_set_dt<<<1, 32, 0, st>>>(B.rec, cfl, fixed_dt, G.dx, advance_time ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t set_dt_to_end(const Geom& G, const Bufs& B, double cfl, cudaStream_t st) {
+  k_set_dt_to_end<<<1, 32, 0, st>>>(B.rec, cfl, G.dx);
+  return cudaGetLastError();
+}
+
+cudaError_t run_begin(double* rec, cudaGraphConditionalHandle cond, cudaStream_t st) {
+  k_run_begin<<<1, 32, 0, st>>>(rec, cond);
+  return cudaGetLastError();
+}
+
+cudaError_t run_next(double* rec, cudaGraphConditionalHandle cond, double chunk, cudaStream_t st) {
+  k_run_next<<<1, 32, 0, st>>>(rec, cond, chunk);
   return cudaGetLastError();
 }
 

@@ -9,6 +9,7 @@ rho w, E).  A ``torch`` CUDA tensor is passed by device pointer on the current
 torch stream; a numpy array or CPU tensor by host pointer.
 """
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -27,7 +28,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhydro.so")
 EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_time", "hydro_get_time",
            "hydro_set_precision", "hydro_set_stream",
            "hydro_set_state", "hydro_get_state", "hydro_step", "hydro_step_dt",
-           "hydro_compute_dt", "hydro_last_error", "hydro_error_string",
+           "hydro_compute_dt", "hydro_advance", "hydro_last_error", "hydro_error_string",
            "hydro_cuda_error_string", "hydro_profile", "hydro_profile_read", "hydro_free",
            "hydro_riemann_exact", "hydro_ppmc", "hydro_compute_dt_noalloc",
            "hydro_batch_init", "hydro_batch_set_inflow", "hydro_batch_set_precision",
@@ -78,6 +79,7 @@ def load():
     L.hydro_profile.argtypes = [vp, ctypes.c_int]
     llp = ctypes.POINTER(ctypes.c_longlong)
     L.hydro_profile_read.argtypes = [vp, ctypes.c_int, dp, llp, llp, llp]
+    L.hydro_advance.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_longlong, llp]
     L.hydro_riemann_exact.argtypes = [ctypes.c_int, vp, vp, ctypes.c_double, vp, vp, vp]
     L.hydro_ppmc.argtypes = [ctypes.c_int, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp]
     L.hydro_compute_dt_noalloc.argtypes = [vp] + [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [vp, vp]
@@ -233,6 +235,17 @@ class Grid:
     def compute_dt(self, cfl):
         return self._dt_result(self._L.hydro_compute_dt(self.h, float(cfl)), "compute_dt", True)
 
+    def advance(self, cfl, t_end=math.inf, max_steps=1 << 52, check=True):
+        """CFL steps until the time reaches t_end (the last step shortened to land
+        on it) or max_steps steps were taken, looped on the device inside one CUDA
+        graph; returns the number of steps taken (raises on error when check)."""
+        n = ctypes.c_longlong(0)
+        rc = self._L.hydro_advance(self.h, float(cfl), float(t_end), int(max_steps),
+                                   ctypes.byref(n))
+        if check:
+            self._check(rc, "advance")
+        return n.value
+
     def last_error(self):
         return self._L.hydro_last_error(self.h)
 
@@ -253,8 +266,10 @@ class Grid:
 
 
 def run(u0, dx, gamma, bc, nsteps=None, cfl=0.3, t_end=None, inflow=None, precision=HYDRO_FP64,
-        max_steps=100000, recon=HYDRO_RECON_PPMC, solver=HYDRO_RIEMANN_EXACT):
-    """Advance ``u0`` on the GPU; returns ``(u, t, nsteps)`` (host numpy state)."""
+        max_steps=100000, recon=HYDRO_RECON_PPMC, solver=HYDRO_RIEMANN_EXACT, loop="device"):
+    """Advance ``u0`` on the GPU; returns ``(u, t, nsteps)`` (host numpy state).
+    loop="device" runs the steps inside a CUDA graph (Grid.advance); loop="host"
+    takes them one call at a time; both give the same dt sequence and state."""
     _, nz, ny, nx = u0.shape
     g = Grid(nx, ny, nz, dx, gamma, bc, precision=precision, recon=recon, solver=solver)
     try:
@@ -262,6 +277,12 @@ def run(u0, dx, gamma, bc, nsteps=None, cfl=0.3, t_end=None, inflow=None, precis
             for face, prim in inflow.items():
                 g.set_inflow(face, prim)
         g.set_state(np.ascontiguousarray(u0, dtype=np.float64))
+        if loop == "device":
+            limit = max_steps if nsteps is None else min(nsteps, max_steps)
+            steps = g.advance(cfl, math.inf if t_end is None else t_end, limit)
+            return g.get_state(), g.get_time(), steps
+        if loop != "host":
+            raise ValueError("loop must be 'device' or 'host'")
         t, steps = 0.0, 0
         while steps < max_steps:
             if nsteps is not None and steps >= nsteps:

@@ -100,8 +100,9 @@ def mixed_bytes_per_cell_update(active_axes=3):
     return b["prims"] + b["update"] + active_axes * (b["ppmc"] + b["riemann1"] + b["riemann2"])
 
 # dram bytes (read + write) per unit of the stage's kernel from an ncu capture,
-# with the digest of the sources that kernel is built from; a digest mismatch
-# (the kernel changed since the capture) reports null.  Captured on Sedov 160^3
+# with the digest of the sources that kernel is built from and the threads a
+# block of the captured launches; a digest or block-size mismatch (the kernel
+# changed since the capture) reports null.  Captured on Sedov 160^3
 # (the 256^3 launches exceed the capture size rule) and scaled by the units of
 # a launch: these kernels stream each plane once, so traffic grows in
 # proportion to the units.  Units at 160^3: riemann2 161 x 160 x 160 faces,
@@ -110,23 +111,23 @@ def mixed_bytes_per_cell_update(active_axes=3):
 _FP64_SRC = ["hydro_fp64_fast.cu", "hydro_internal.h", "hydro_kernels.cuh", "hydro_math.cuh"]
 _MIXED_SRC = ["hydro_internal.h", "hydro_kernels.cuh", "hydro_math.cuh", "hydro_mixed.cu"]
 NCU_TRAFFIC = {
-    ("fp64", "riemann2"): {"bytes_per_unit": 203.89, "digest": "479c5e7b8094ac13",
+    ("fp64", "riemann2"): {"bytes_per_unit": 204.08, "digest": "479c5e7b8094ac13", "bs": 128,
                            "sources": _FP64_SRC},
-    ("fp64", "ppmc"): {"bytes_per_unit": 185.37, "digest": "479c5e7b8094ac13",
+    ("fp64", "ppmc"): {"bytes_per_unit": 185.22, "digest": "479c5e7b8094ac13", "bs": 128,
                        "sources": _FP64_SRC},
-    ("fp64", "riemann1"): {"bytes_per_unit": 118.29, "digest": "479c5e7b8094ac13",
+    ("fp64", "riemann1"): {"bytes_per_unit": 118.19, "digest": "479c5e7b8094ac13", "bs": 128,
                            "sources": _FP64_SRC},
-    ("fp64", "slopes"): {"bytes_per_unit": 99.58, "digest": "479c5e7b8094ac13",
+    ("fp64", "slopes"): {"bytes_per_unit": 99.59, "digest": "479c5e7b8094ac13", "bs": 128,
                          "sources": _FP64_SRC},
-    ("mixed", "riemann2"): {"bytes_per_unit": 99.83, "digest": "674ef9fc273ffbb0",
+    ("mixed", "riemann2"): {"bytes_per_unit": 99.84, "digest": "674ef9fc273ffbb0", "bs": 128,
                             "sources": _MIXED_SRC},
-    ("mixed", "update"): {"bytes_per_unit": 136.57, "digest": "674ef9fc273ffbb0",
+    ("mixed", "update"): {"bytes_per_unit": 136.53, "digest": "674ef9fc273ffbb0", "bs": 128,
                           "sources": _MIXED_SRC},
-    ("mixed", "ppmc"): {"bytes_per_unit": 63.06, "digest": "674ef9fc273ffbb0",
+    ("mixed", "ppmc"): {"bytes_per_unit": 63.08, "digest": "674ef9fc273ffbb0", "bs": 128,
                         "sources": _MIXED_SRC},
-    ("mixed", "riemann1"): {"bytes_per_unit": 55.48, "digest": "674ef9fc273ffbb0",
+    ("mixed", "riemann1"): {"bytes_per_unit": 55.42, "digest": "674ef9fc273ffbb0", "bs": 128,
                             "sources": _MIXED_SRC},
-    ("mixed", "prims"): {"bytes_per_unit": 59.51, "digest": "674ef9fc273ffbb0",
+    ("mixed", "prims"): {"bytes_per_unit": 59.53, "digest": "674ef9fc273ffbb0", "bs": 128,
                          "sources": _MIXED_SRC},
 }
 
@@ -447,7 +448,8 @@ def main():
     traffic = None
     tinfo = NCU_TRAFFIC.get((args.precision, dom))
     if (tinfo and active == 3 and args.recon == "ppmc" and args.solver == "exact"
-            and tinfo["digest"] == source_digest(tinfo["sources"])):
+            and tinfo["digest"] == source_digest(tinfo["sources"])
+            and tinfo["bs"] == g.block_size()):
         traffic = tinfo["bytes_per_unit"] * units_per_launch
     bytes_per_unit = ALGORITHMIC_BYTES[args.precision][dom]
     if args.precision == "fp64":

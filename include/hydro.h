@@ -134,6 +134,19 @@ double hydro_get_time(hydro_t h);
  * following steps. */
 int hydro_set_precision(hydro_t h, int mode);
 
+/* Threads a block of the HYDRO_FP64 and HYDRO_MIXED launches: 128 or 256, or 0
+ * for the library's choice (the default, 128: never slower than 256 in
+ * measurements from a 512-cell tube to 256^3, faster on small grids, which
+ * spread over more SMs).  The arithmetic per cell does not depend on it and the
+ * dt is a maximum over cells, so FP64 results are the same bit for bit; in
+ * HYDRO_MIXED the cell whose signal speed is evaluated in FP64 is picked per
+ * block, so dt can differ within 10 * 2^-24 relative where two cells' float
+ * estimates tie.  HYDRO_EINVAL for other values.  HYDRO_FP64_STRICT always
+ * uses 256. */
+int hydro_set_block_size(hydro_t h, int bs);
+/* The block size in use (128 or 256), or a negative error code. */
+int hydro_block_size(hydro_t h);
+
 /* Stream on which all following work of this handle is ordered (a
  * cudaStream_t; NULL = the legacy default stream). */
 int hydro_set_stream(hydro_t h, void* stream);

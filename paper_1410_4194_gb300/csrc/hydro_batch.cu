@@ -27,7 +27,7 @@ using namespace hydro;
 namespace {
 
 struct Schedule {
-  int bs = 256;    // threads a block
+  int bs = 128;    // threads a block (the single-grid default; the autotuner may pick 256)
   int order = 0;   // 0: grids in the given order, 1: largest grid first
 };
 

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhydro.so")
 
 # every entry point that include/hydro.h declares
 EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_time", "hydro_get_time",
-           "hydro_set_precision", "hydro_set_stream",
+           "hydro_set_precision", "hydro_set_stream", "hydro_set_block_size", "hydro_block_size",
            "hydro_set_state", "hydro_get_state", "hydro_step", "hydro_step_dt",
            "hydro_compute_dt", "hydro_advance", "hydro_last_error", "hydro_error_string",
            "hydro_cuda_error_string", "hydro_profile", "hydro_profile_read", "hydro_free",
@@ -65,6 +65,8 @@ def load():
     L.hydro_get_time.restype = ctypes.c_double
     L.hydro_set_precision.argtypes = [vp, ctypes.c_int]
     L.hydro_set_stream.argtypes = [vp, vp]
+    L.hydro_set_block_size.argtypes = [vp, ctypes.c_int]
+    L.hydro_block_size.argtypes = [vp]
     L.hydro_set_state.argtypes = [vp, vp, ctypes.c_int]
     L.hydro_get_state.argtypes = [vp, vp, ctypes.c_int]
     for f in (L.hydro_step, L.hydro_step_dt, L.hydro_compute_dt):
@@ -193,6 +195,13 @@ class Grid:
 
     def set_riemann_solver(self, solver):
         self._check(self._L.hydro_set_riemann_solver(self.h, int(solver)), "set_riemann_solver")
+
+    def set_block_size(self, bs):
+        """Threads a block of the fast FP64 / mixed launches: 128, 256 or 0 (auto)."""
+        self._check(self._L.hydro_set_block_size(self.h, int(bs)), "set_block_size")
+
+    def block_size(self):
+        return self._L.hydro_block_size(self.h)
 
     def set_stream(self, stream):
         """Order this grid's work on a stream: a torch.cuda.Stream, a raw

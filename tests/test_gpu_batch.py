@@ -47,6 +47,7 @@ def test_batch_matches_single_grid_runs_bitwise(precision):
     for i, w in enumerate(grids):
         _, nz, ny, nx = w["u"].shape
         g = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], precision=precision)
+        g.set_block_size(128)  # the batch's default schedule (the mixed dt pick is per block)
         for face, prim in (w.get("inflow") or {}).items():
             g.set_inflow(face, prim)
         g.set_state(w["u"])
@@ -131,3 +132,36 @@ def test_batch_other_methods_match_single_grids_and_oracle(recon, solver):
         err = np.abs(single - uo) / np.maximum(np.abs(uo), 1e-4 * scale)
         assert err.max() <= 1e-10, (i, err.max())
     b.close()
+
+
+@pytest.mark.parametrize("precision", [hydro.HYDRO_FP64, hydro.HYDRO_MIXED], ids=["fp64", "mixed"])
+def test_block_size_leaves_results_unchanged(precision):
+    """A single grid's launches with 128 or 256 threads a block: the same
+    arithmetic per cell, the dt a maximum over cells.  FP64 is bitwise the
+    same; in mixed precision the per-block pick of the cell whose signal speed
+    is evaluated in FP64 can only differ where float estimates tie, which these
+    states do not have (bitwise here too)."""
+    w = W.sedov(40)
+    out = {}
+    for bs in (128, 256):
+        g = hydro.Grid(40, 40, 40, w["dx"], w["gamma"], w["bc"], precision=precision)
+        try:
+            g.set_block_size(bs)
+            assert g.block_size() == bs
+            g.set_state(w["u"])
+            dts = [g.step(0.3) for _ in range(5)]
+            out[bs] = (dts, g.get_state())
+        finally:
+            g.close()
+    assert out[128][0] == out[256][0]
+    assert np.array_equal(out[128][1], out[256][1])
+    g = hydro.Grid(16, 16, 16, 0.1, 1.4, [0] * 6)
+    try:
+        assert g.block_size() == 128  # the default
+        with pytest.raises(hydro.HydroError):
+            g.set_block_size(64)
+        g.set_block_size(256)
+        g.set_block_size(0)
+        assert g.block_size() == 128
+    finally:
+        g.close()

@@ -178,6 +178,128 @@ __device__ __forceinline__ bool nonneg(T x) {  // x >= 0
   else return (unsigned long long)__double_as_longlong(x) <= 0x8000000000000000ull;
 }
 
+// The two 32-bit halves of a double and back, through PTX moves that the
+// compiler cannot see through: a bit test written on the whole 64-bit pattern
+// (e.g. "bits << 1 != 0") can otherwise be turned back into an FP64 compare,
+// which GB300 issues on its FP64 pipe.
+__device__ __forceinline__ void split_bits(double x, unsigned& lo, unsigned& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
+}
+__device__ __forceinline__ double join_bits(unsigned lo, unsigned hi) {
+  double x;
+  asm("mov.b64 %0, {%1, %2};" : "=d"(x) : "r"(lo), "r"(hi));
+  return x;
+}
+
+// Sign tests of a product x*y from the factors' sign bits and zero tests, on
+// the integer pipe: an FP64 multiply formed only for its sign costs a full slot
+// of the FP64 pipe.  They equal the tests of the rounded product except where
+// that product underflows to zero (|x y| < 2^-1074, counted here as nonzero)
+// and for NaN factors.  With S (strict), and for float, the product is formed.
+template <bool S, typename T>
+__device__ __forceinline__ bool prod_pos(T x, T y) {  // x*y > 0
+  if constexpr (S || sizeof(T) == 4) {
+    return x * y > T(0);
+  } else {
+    unsigned xl, xh, yl, yh;
+    split_bits(x, xl, xh);
+    split_bits(y, yl, yh);
+    return ((xh << 1) | xl) != 0u && ((yh << 1) | yl) != 0u && (int)(xh ^ yh) >= 0;
+  }
+}
+template <bool S, typename T>
+__device__ __forceinline__ bool prod_neg(T x, T y) {  // x*y < 0
+  if constexpr (S || sizeof(T) == 4) {
+    return x * y < T(0);
+  } else {
+    unsigned xl, xh, yl, yh;
+    split_bits(x, xl, xh);
+    split_bits(y, yl, yh);
+    return ((xh << 1) | xl) != 0u && ((yh << 1) | yl) != 0u && (int)(xh ^ yh) < 0;
+  }
+}
+template <bool S, typename T>
+__device__ __forceinline__ bool prod_nonpos(T x, T y) {  // x*y <= 0
+  if constexpr (S || sizeof(T) == 4) return x * y <= T(0);
+  else return !prod_pos<S>(x, y);
+}
+
+// Sign tests of a product of two differences (a - b)(c - d) without forming
+// either difference: a difference of two finite doubles is zero only when they
+// are equal (subnormals are not flushed), so its sign is the order of a and b,
+// which the ordered bit patterns give on the integer pipe.  Equal to the tests
+// of the rounded product except where that product underflows to zero, where
+// +0 meets -0 (counted here as unequal), and for NaN.
+template <bool S, typename T>
+__device__ __forceinline__ bool diffs_prod_nonpos(T a, T b, T c, T d) {  // (a-b)(c-d) <= 0
+  if constexpr (S || sizeof(T) == 4) {
+    return nonpos<S>((a - b) * (c - d));
+  } else {
+    const long long oa = ord(a), ob = ord(b), oc = ord(c), od = ord(d);
+    return !((oa > ob && oc > od) || (oa < ob && oc < od));
+  }
+}
+template <bool S, typename T>
+__device__ __forceinline__ bool diffs_prod_pos(T a, T b, T c, T d) {  // (a-b)(c-d) > 0
+  if constexpr (S || sizeof(T) == 4) {
+    return pos<S>((a - b) * (c - d));
+  } else {
+    const long long oa = ord(a), ob = ord(b), oc = ord(c), od = ord(d);
+    return (oa > ob && oc > od) || (oa < ob && oc < od);
+  }
+}
+template <bool S, typename T>
+__device__ __forceinline__ bool diffs_prod_neg(T a, T b, T c, T d) {  // (a-b)(c-d) < 0
+  if constexpr (S || sizeof(T) == 4) {
+    return neg<S>((a - b) * (c - d));
+  } else {
+    const long long oa = ord(a), ob = ord(b), oc = ord(c), od = ord(d);
+    return (oa > ob && oc < od) || (oa < ob && oc > od);
+  }
+}
+
+// x/2 and 2x in integer arithmetic, the IEEE products exactly: a normal
+// operand with a normal result moves its exponent field by one; infinities and
+// NaN come back unchanged; halving the smallest normals and the subnormals
+// shifts the magnitude right by one bit, rounding the dropped bit to even;
+// doubling a subnormal shifts it left (exact), doubling the largest binade
+// overflows to infinity.  half<S>(x) and twice<S>(x) use them; with S, and for
+// float, the multiply itself.
+__device__ __forceinline__ double half_bits(double x) {
+  unsigned lo, hi;
+  split_bits(x, lo, hi);
+  const unsigned ex = (hi >> 20) & 0x7ffu;
+  if (ex - 2u <= 2044u) return join_bits(lo, hi - (1u << 20));  // 2 <= ex <= 2046
+  if (ex == 0x7ffu) return x;
+  const unsigned sign = hi & 0x80000000u, mh = hi & 0x7fffffffu;
+  unsigned l = (lo >> 1) | (mh << 31), h = mh >> 1;
+  if ((lo & 1u) & l) {  // dropped bit 1 and kept bit 1: round up to even
+    l += 1u;
+    h += (l == 0u) ? 1u : 0u;
+  }
+  return join_bits(l, sign | h);
+}
+__device__ __forceinline__ double twice_bits(double x) {
+  unsigned lo, hi;
+  split_bits(x, lo, hi);
+  const unsigned ex = (hi >> 20) & 0x7ffu;
+  if (ex - 1u <= 2044u) return join_bits(lo, hi + (1u << 20));  // 1 <= ex <= 2045
+  if (ex == 0x7ffu) return x;
+  const unsigned sign = hi & 0x80000000u;
+  if (ex == 0x7feu) return join_bits(0u, sign | 0x7ff00000u);
+  return join_bits(lo << 1, sign | ((hi << 1) & 0x7fffffffu) | (lo >> 31));  // subnormal
+}
+template <bool S, typename T>
+__device__ __forceinline__ T half(T x) {
+  if constexpr (S || sizeof(T) == 4) return T(0.5) * x;
+  else return half_bits(x);
+}
+template <bool S, typename T>
+__device__ __forceinline__ T twice(T x) {
+  if constexpr (S || sizeof(T) == 4) return T(2) * x;
+  else return twice_bits(x);
+}
+
 // ---------------------------------------------------------------------------
 // float <-> double conversion in integer arithmetic.  GB300 issues the
 // hardware conversions (cvt.f64.f32, cvt.rn.f32.f64) on its FP64 pipe, at the
@@ -269,15 +391,15 @@ __device__ __forceinline__ double nr_div(double a, double b) {
 }
 __device__ __forceinline__ double nr_sqrt(double x) {
   const double y = rsqrt_seed(x);
-  const double hy = 0.5 * y;
+  const double hy = half_bits(y);
   double s = x * y;
   s = fma(hy, fma(-s, s, x), s);
   return fma(hy, fma(-s, s, x), s);
 }
 __device__ __forceinline__ double nr_rsqrt(double x) {
   double y = rsqrt_seed(x);
-  y = fma(0.5 * y, fma(-x * y, y, 1.0), y);
-  return fma(0.5 * y, fma(-x * y, y, 1.0), y);
+  y = fma(half_bits(y), fma(-x * y, y, 1.0), y);
+  return fma(half_bits(y), fma(-x * y, y, 1.0), y);
 }
 __device__ __forceinline__ float nr_rcp(float b) {
   float r;
@@ -412,7 +534,7 @@ __device__ __forceinline__ void cons2prim(const T U[5], const GasT<T>& g, T W[5]
     v1 = U[2] * inv_d;
     v2 = U[3] * inv_d;
   }
-  const T p = g.gm1 * (U[4] - T(0.5) * d * (vn * vn + v1 * v1 + v2 * v2));
+  const T p = g.gm1 * (U[4] - half<S>(d) * (vn * vn + v1 * v1 + v2 * v2));
   W[0] = d;
   W[1] = vn;
   W[2] = v1;
@@ -428,7 +550,7 @@ __device__ __forceinline__ void prim2cons(const T W[5], const GasT<T>& g, T U[5]
   U[2] = d * W[2];
   U[3] = d * W[3];
   const T e = S ? W[4] / g.gm1 : W[4] * g.inv_gm1;
-  U[4] = e + T(0.5) * d * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  U[4] = e + half<S>(d) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -444,11 +566,11 @@ __device__ __forceinline__ void char_project(const T dw[5], T rho, T a, T inv_a,
     dpa2 = dw[4] * inv_a2;
     rdu_a = rho * dw[1] * inv_a;
   }
-  xi[0] = T(0.5) * (-rdu_a + dpa2);
+  xi[0] = half<S>(-rdu_a + dpa2);
   xi[1] = dw[0] - dpa2;
   xi[2] = dw[2];
   xi[3] = dw[3];
-  xi[4] = T(0.5) * (rdu_a + dpa2);
+  xi[4] = half<S>(rdu_a + dpa2);
 }
 
 // limited slope of the cell c from its neighbours m (c-1) and p (c+1)
@@ -461,20 +583,29 @@ __device__ __forceinline__ void limited_slope(const T wm[5], const T wc[5], cons
   for (int q = 0; q < 5; ++q) {
     dl[q] = wc[q] - wm[q];
     dr[q] = wp[q] - wc[q];
-    dc[q] = T(0.5) * (wp[q] - wm[q]);
   }
   char_project<S>(dl, wc[0], a, inv_a, inv_a2, xl);
   char_project<S>(dr, wc[0], a, inv_a, inv_a2, xr);
-  char_project<S>(dc, wc[0], a, inv_a, inv_a2, xc);
-  T xi[5];
+  bool keep[5], any = false;
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    T s = T(0);
-    if (pos<S>(xl[q] * xr[q])) {
-      const T m = vmin<S>(vmin<S>(xabs(xc[q]), T(2) * xabs(xl[q])), T(2) * xabs(xr[q]));
-      s = neg<S>(xc[q]) ? -m : m;
+    keep[q] = prod_pos<S>(xl[q], xr[q]);
+    any = any || keep[q];
+  }
+  T xi[5] = {T(0), T(0), T(0), T(0), T(0)};
+  // the centred difference is projected only where the limiter keeps a slope
+  // (in FP64; in strict mode and in float always, as printed)
+  if (S || sizeof(T) == 4 || any) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) dc[q] = half<S>(wp[q] - wm[q]);
+    char_project<S>(dc, wc[0], a, inv_a, inv_a2, xc);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      if (keep[q]) {
+        const T m = vmin<S>(vmin<S>(xabs(xc[q]), twice<S>(xabs(xl[q]))), twice<S>(xabs(xr[q])));
+        xi[q] = neg<S>(xc[q]) ? -m : m;
+      }
     }
-    xi[q] = s;
   }
   dw[0] = xi[0] + xi[1] + xi[4];
   dw[1] = (S ? a / wc[0] : a * inv_rho) * (-xi[0] + xi[4]);
@@ -502,15 +633,15 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
       L = T(0.5) * (wi + w_m[q]) - (s_c[q] - s_m[q]) / T(6);
       R = T(0.5) * (w_p[q] + wi) - (s_p[q] - s_c[q]) / T(6);
     } else {
-      L = T(0.5) * (wi + w_m[q]) - (s_c[q] - s_m[q]) * c16;
-      R = T(0.5) * (w_p[q] + wi) - (s_p[q] - s_c[q]) * c16;
+      L = half<S>(wi + w_m[q]) - (s_c[q] - s_m[q]) * c16;
+      R = half<S>(w_p[q] + wi) - (s_p[q] - s_c[q]) * c16;
     }
-    if (nonpos<S>((R - wi) * (wi - L))) {
+    if (diffs_prod_nonpos<S>(R, wi, wi, L)) {
       L = wi;
       R = wi;
     }
-    if (neg<S>((R - L) * (L - (T(3) * wi - T(2) * R)))) L = T(3) * wi - T(2) * R;
-    if (neg<S>((R - L) * ((T(3) * wi - T(2) * L) - R))) R = T(3) * wi - T(2) * L;
+    if (diffs_prod_neg<S>(R, L, L, T(3) * wi - T(2) * R)) L = T(3) * wi - T(2) * R;
+    if (diffs_prod_neg<S>(R, L, T(3) * wi - T(2) * L, R)) R = T(3) * wi - T(2) * L;
     L = vmin<S>(vmax<S>(wi, w_m[q]), vmax<S>(vmin<S>(wi, w_m[q]), L));
     R = vmin<S>(vmax<S>(wi, w_p[q]), vmax<S>(vmin<S>(wi, w_p[q]), R));
     WsL[q] = L;
@@ -598,12 +729,13 @@ template <bool S = false, typename T>
 __device__ __forceinline__ void prim_slope(const T wm[5], const T wc[5], const T wp[5], T dw[5]) {
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    const T dL = wc[q] - wm[q];
-    const T dR = wp[q] - wc[q];
-    const T dC = T(0.5) * (wp[q] - wm[q]);
     T s = T(0);
-    if (pos<S>(dL * dR)) {
-      const T m = vmin<S>(vmin<S>(xabs(dC), T(2) * xabs(dL)), T(2) * xabs(dR));
+    // the differences are formed only where the limiter keeps a slope
+    if (diffs_prod_pos<S>(wc[q], wm[q], wp[q], wc[q])) {
+      const T dL = wc[q] - wm[q];
+      const T dR = wp[q] - wc[q];
+      const T dC = half<S>(wp[q] - wm[q]);
+      const T m = vmin<S>(vmin<S>(xabs(dC), twice<S>(xabs(dL))), twice<S>(xabs(dR)));
       s = neg<S>(dC) ? -m : m;
     }
     dw[q] = s;
@@ -614,7 +746,7 @@ __device__ __forceinline__ void prim_slope(const T wm[5], const T wc[5], const T
 template <bool S = false, typename T>
 __device__ __forceinline__ void euler_flux(const T W[5], const GasT<T>& g, T F[5]) {
   const T E = (S ? W[4] / g.gm1 : W[4] * g.inv_gm1) +
-              T(0.5) * W[0] * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+              half<S>(W[0]) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
   const T m = W[0] * W[1];
   F[0] = m;
   F[1] = m * W[1] + W[4];
@@ -788,7 +920,7 @@ __device__ __forceinline__ void ppmp_states(const T w[7][5], const T sm[5], cons
       const T e2m = wi[0] - T(2) * wim[0] + w[1][0];
       const T e2p = w[5][0] - T(2) * wip[0] + wi[0];
       steep = lt<S>(T(0.01) * mr, dr) && lt<S>(dp * mr, T(0.1) * g.gamma * dr * mp) &&
-              neg<S>(e2m * e2p);
+              prod_neg<S>(e2m, e2p);
       if (steep) {
         const T eta_t = -nr_div(e2p - e2m, T(6) * (wip[0] - wim[0]));
         eta = vmax<S>(T(0), vmin<S>(T(20) * eta_t - T(1), T(1)));
@@ -823,12 +955,12 @@ __device__ __forceinline__ void ppmp_states(const T w[7][5], const T sm[5], cons
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     T L = WL[q], R = WR[q];
-    if (nonpos<S>((R - wi[q]) * (wi[q] - L))) {
+    if (diffs_prod_nonpos<S>(R, wi[q], wi[q], L)) {
       L = wi[q];
       R = wi[q];
     }
-    if (neg<S>((R - L) * (L - (T(3) * wi[q] - T(2) * R)))) L = T(3) * wi[q] - T(2) * R;
-    if (neg<S>((R - L) * ((T(3) * wi[q] - T(2) * L) - R))) R = T(3) * wi[q] - T(2) * L;
+    if (diffs_prod_neg<S>(R, L, L, T(3) * wi[q] - T(2) * R)) L = T(3) * wi[q] - T(2) * R;
+    if (diffs_prod_neg<S>(R, L, T(3) * wi[q] - T(2) * L, R)) R = T(3) * wi[q] - T(2) * L;
     WL[q] = L;
     WR[q] = R;
     dw[q] = R - L;
@@ -933,7 +1065,7 @@ __device__ __forceinline__ void hlle_flux(const T UL[5], const T UR[5], const T 
   for (int q = 0; q < 5; ++q) {
     const T FLh = FL[q] - bm * UL[q];
     const T FRh = FR[q] - bp * UR[q];
-    F[q] = T(0.5) * ((FLh + FRh) + (FLh - FRh) * k);
+    F[q] = half<S>((FLh + FRh) + (FLh - FRh) * k);
   }
 }
 
@@ -946,7 +1078,7 @@ __device__ __forceinline__ bool negative_state(const T U[5], const GasT<T>& g) {
     const T p = g.gm1 * (U[4] - T(0.5) * m2 / U[0]);
     return U[0] < T(0) || p < T(0);
   } else {
-    return neg<S>(U[0]) || lt<S>(T(2) * U[4] * U[0], m2);
+    return neg<S>(U[0]) || lt<S>(twice<S>(U[4]) * U[0], m2);
   }
 }
 
@@ -977,7 +1109,7 @@ __device__ __forceinline__ void riemann_roe(const T UL[5], const T UR[5], const 
     H = (sL * HL + sR * HR) * ir;
   }
   const T V2 = u * u + v * v + w * w;
-  const T a2 = g.gm1 * (H - T(0.5) * V2);
+  const T a2 = g.gm1 * (H - half<S>(V2));
   if (!pos<S>(a2)) {
     hlle_flux<S>(UL, UR, WL, WR, inv_dL, inv_dR, FL, FR, u, u, g, F);
     return;
@@ -1028,7 +1160,7 @@ __device__ __forceinline__ void riemann_roe(const T UL[5], const T UR[5], const 
   s[3] = C0 * w + C2 + C3 * w + C4 * w;
   s[4] = C0 * (H - u * a) + C1 * v + C2 * w + T(0.5) * C3 * V2 + C4 * (H + u * a);
 #pragma unroll
-  for (int q = 0; q < 5; ++q) F[q] = T(0.5) * (FL[q] + FR[q] - s[q]);
+  for (int q = 0; q < 5; ++q) F[q] = half<S>(FL[q] + FR[q] - s[q]);
   // intermediate states: a negative density or pressure takes the HLLE flux
   T Um[5];
   Um[0] = UL[0] + xi0;
@@ -1062,7 +1194,7 @@ __device__ __forceinline__ T h_eta(const T WL[5], const T WR[5], T inv_dL, T inv
     aL = nr_sqrt(g.gamma * WL[4] * inv_dL);
     aR = nr_sqrt(g.gamma * WR[4] * inv_dR);
   }
-  return T(0.5) * vmax<S>(xabs((WR[1] + aR) - (WL[1] + aL)), xabs((WR[1] - aR) - (WL[1] - aL)));
+  return half<S>(vmax<S>(xabs((WR[1] + aR) - (WL[1] + aL)), xabs((WR[1] - aR) - (WL[1] - aL))));
 }
 
 // ---------------------------------------------------------------------------
@@ -1106,7 +1238,7 @@ __device__ __forceinline__ void side_f(T p, T inv_p, const RSide<T>& s, const Ga
       const T ipb = q * q * s.inv_A;
       const T dp = p - s.p;
       f = dp * q;
-      fd = q * (T(1) - T(0.5) * dp * ipb);
+      fd = q * (T(1) - half<S>(dp) * ipb);
     }
   }
 }
@@ -1147,7 +1279,7 @@ __device__ __forceinline__ void make_side(const T W[5], T inv_d, const GasT<T>& 
     s.inv_A = g.half_gp1 * s.d;
   }
   s.B = g.gm1_gp1 * s.p;
-  s.cf = T(2) * s.a * g.inv_gm1;
+  s.cf = S ? T(2) * s.a * g.inv_gm1 : s.a * g.fan_d;  // fan_d = 2 inv_gm1 exactly
   s.cd = s.a * g.inv_g;
 }
 
@@ -1210,7 +1342,7 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
   make_side<S>(WL, inv_dL, g, L);
   make_side<S>(WR, inv_dR, g, R);
   // primitive-variable estimate, then the two-shock estimate as Newton start
-  T pt = T(0.5) * (L.p + R.p) + T(0.125) * (L.u - R.u) * (L.d + R.d) * (L.a + R.a);
+  T pt = half<S>(L.p + R.p) + T(0.125) * (L.u - R.u) * (L.d + R.d) * (L.a + R.a);
   if (neg<S>(pt)) pt = T(0);
   T gL, gR, p;
   if constexpr (!S) {
@@ -1239,7 +1371,8 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
     if constexpr (S)
       done = T(2) * xabs(pn - p) / xabs(pn + p) < T(kNewtonTol);
     else
-      done = lt<S>(T(2) * xabs(pn - p), T(kNewtonTol) * xabs(pn + p));
+      // 2|d| < tol |s| as |d| < (tol/2) |s|: both sides halved exactly
+      done = lt<S>(xabs(pn - p), T(0.5 * kNewtonTol) * xabs(pn + p));
     if constexpr (sizeof(T) == 4) {
       // In float the residual f_L + f_R + u_R - u_L carries the rounding error of
       // its terms; near the root the Newton steps that noise produces can stay
@@ -1266,7 +1399,7 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
     side_f_only<S>(p, R, g, fR, xR);
   }
   const T pm = p;
-  const T um = T(0.5) * (L.u + R.u + fR - fL);
+  const T um = half<S>(L.u + R.u + fR - fL);
 
   T d, u, ps;
   if (nonneg<S>(um)) {
@@ -1293,7 +1426,7 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
   const bool left = nonneg<S>(u);
   const T v = left ? WL[2] : WR[2];
   const T w = left ? WL[3] : WR[3];
-  const T E = (S ? ps / g.gm1 : ps * g.inv_gm1) + T(0.5) * d * (u * u + v * v + w * w);
+  const T E = (S ? ps / g.gm1 : ps * g.inv_gm1) + half<S>(d) * (u * u + v * v + w * w);
   const T mf = d * u;
   F[0] = mf;
   F[1] = mf * u + ps;

@@ -163,7 +163,7 @@ __device__ __forceinline__ void prims_mixed_body(const Geom& G, const BufsF& B, 
   r = fma(r, fma(-U[0], r, 1.0), r);
   // FP64 internal energy E - |m|^2 / (2 rho) and the pressure floor
   const double m2 = fma(U[1], U[1], fma(U[2], U[2], U[3] * U[3]));
-  const double p = vmax<false>(g.gm1 * fma(-0.5 * m2, r, U[4]), kPFloor);
+  const double p = vmax<false>(g.gm1 * fma(-half_bits(m2), r, U[4]), kPFloor);  // m2/2 exact
   const float pf = d2f(p);
   const float af = sqrtf(gf.gamma * pf * rf);
   float vf[3];

@@ -1,7 +1,8 @@
 // hydro_selfcheck.cu -- hydro_check_conversions(): the integer-arithmetic
 // float <-> double conversions of hydro_math.cuh against the hardware ones
 // (bit for bit in the normal range, zeros and infinities; subnormals flushed
-// to a signed zero; NaN to NaN).
+// to a signed zero; NaN to NaN); hydro_check_scaling(): its integer halving,
+// doubling and product-sign tests against the FP64 multiply.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -82,7 +83,63 @@ __global__ void __launch_bounds__(kThreads) k_check_narrow(unsigned long long* b
   }
 }
 
+// doubles for the scaling checks: a quarter with any bit pattern, the rest
+// with exponent fields at the edges of the range (0, 1, 2, 2045, 2046, 2047)
+// or near the middle, the fraction random or with its low bit set
+__device__ __forceinline__ double scaling_sample(unsigned long long i) {
+  unsigned long long b = mix64(i * 3 + 1);
+  const unsigned long long r = mix64(i * 3 + 2);
+  if ((i & 3) != 0) {
+    const unsigned long long edge[8] = {0, 1, 2, 2045, 2046, 2047, 1023, 1022};
+    const unsigned long long e = edge[r & 7];
+    b = (b & 0x800fffffffffffffull) | (e << 52);
+    if (r & 8) b |= 1ull;
+  }
+  return __longlong_as_double((long long)b);
+}
+
+__global__ void __launch_bounds__(kThreads) k_check_scaling(unsigned long long* bad) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * kThreads;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * kThreads + threadIdx.x;
+       i < kNarrowSamples; i += stride) {
+    const double x = scaling_sample(i), y = scaling_sample(i ^ 0x9e3779b9ull);
+    const double h = hydro::half<false>(x), t = hydro::twice<false>(x);
+    const double hm = x * 0.5, tm = x * 2.0;
+    const bool okh = isnan(x) ? isnan(h) : __double_as_longlong(h) == __double_as_longlong(hm);
+    const bool okt = isnan(x) ? isnan(t) : __double_as_longlong(t) == __double_as_longlong(tm);
+    // the product's sign tests, except where it underflows to zero or is NaN
+    const double p = x * y;
+    bool oks = true;
+    if (!isnan(p) && !(p == 0.0 && x != 0.0 && y != 0.0))
+      oks = hydro::prod_pos<false>(x, y) == (p > 0.0) && hydro::prod_neg<false>(x, y) == (p < 0.0) &&
+            hydro::prod_nonpos<false>(x, y) == (p <= 0.0);
+    count(!okh, bad);
+    count(!okt, bad + 1);
+    count(!oks, bad + 2);
+  }
+}
+
 }  // namespace
+
+extern "C" int hydro_check_scaling(unsigned long long* mismatches, void* stream) {
+  if (!mismatches) return HYDRO_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, 3 * sizeof(unsigned long long)) != cudaSuccess) return HYDRO_ECUDA;
+  int rc = HYDRO_OK;
+  if (cudaMemsetAsync(d, 0, 3 * sizeof(unsigned long long), st) != cudaSuccess) rc = HYDRO_ECUDA;
+  if (rc == HYDRO_OK) {
+    k_check_scaling<<<kBlocks, kThreads, 0, st>>>(d);
+    if (cudaGetLastError() != cudaSuccess) rc = HYDRO_ECUDA;
+  }
+  if (rc == HYDRO_OK &&
+      (cudaMemcpyAsync(mismatches, d, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    rc = HYDRO_ECUDA;
+  cudaFree(d);
+  return rc;
+}
 
 extern "C" int hydro_check_conversions(unsigned long long* mismatches, void* stream) {
   if (!mismatches) return HYDRO_EINVAL;

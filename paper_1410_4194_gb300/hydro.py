@@ -35,7 +35,7 @@ EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_time", "hydro_get_time",
            "hydro_batch_set_stream", "hydro_batch_set_state", "hydro_batch_get_state",
            "hydro_batch_step", "hydro_batch_autotune", "hydro_batch_last_error",
            "hydro_batch_cuda_error_string", "hydro_batch_free", "hydro_check_conversions",
-           "hydro_check_fastdiv",
+           "hydro_check_fastdiv", "hydro_check_scaling",
            "hydro_set_reconstruction", "hydro_batch_set_reconstruction",
            "hydro_set_riemann_solver", "hydro_batch_set_riemann_solver")
 STAGES = ("prims", "set_dt", "slopes", "ppmc", "riemann1", "riemann2", "update")
@@ -98,6 +98,7 @@ def load():
     L.hydro_batch_cuda_error_string.restype = ctypes.c_char_p
     L.hydro_batch_free.argtypes = [vp]
     L.hydro_check_conversions.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), vp]
+    L.hydro_check_scaling.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), vp]
     L.hydro_check_fastdiv.argtypes = []
     L.hydro_check_fastdiv.restype = ctypes.c_longlong
     L.hydro_set_reconstruction.argtypes = [vp, ctypes.c_int]
@@ -356,6 +357,17 @@ def check_conversions():
     if rc != 0:
         raise HydroError(rc, "check_conversions")
     return int(out[0]), int(out[1])
+
+
+def check_scaling():
+    """Mismatch counts (halving, doubling, product signs) of the FP64 kernels'
+    integer-pipe helpers against the FP64 multiply."""
+    L = load()
+    out = (ctypes.c_ulonglong * 3)()
+    rc = L.hydro_check_scaling(out, _torch_stream_ptr())
+    if rc != 0:
+        raise HydroError(rc, "check_scaling")
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def check_fastdiv():

@@ -2,7 +2,8 @@
 kernels use agree with the hardware conversions: bit for bit for normal values,
 zeros and infinities (every float for the widening, 2^30 sampled doubles for the
 round-to-nearest-even narrowing), subnormals flushed to a signed zero, NaN kept
-NaN."""
+NaN.  The FP64 kernels' integer halving, doubling and product-sign tests agree
+with the FP64 multiply."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -13,3 +14,11 @@ def test_conversions_match_hardware():
     widen, narrow = hydro.check_conversions()
     assert widen == 0, "float -> double mismatches: %d" % widen
     assert narrow == 0, "double -> float mismatches: %d" % narrow
+
+
+def test_integer_scaling_matches_the_fp64_multiply():
+    from paper_1410_4194_gb300 import hydro
+    halving, doubling, signs = hydro.check_scaling()
+    assert halving == 0, "x/2 mismatches: %d" % halving
+    assert doubling == 0, "2x mismatches: %d" % doubling
+    assert signs == 0, "product sign mismatches: %d" % signs

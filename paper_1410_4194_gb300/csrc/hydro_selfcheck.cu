@@ -113,9 +113,22 @@ __global__ void __launch_bounds__(kThreads) k_check_scaling(unsigned long long* 
     if (!isnan(p) && !(p == 0.0 && x != 0.0 && y != 0.0))
       oks = hydro::prod_pos<false>(x, y) == (p > 0.0) && hydro::prod_neg<false>(x, y) == (p < 0.0) &&
             hydro::prod_nonpos<false>(x, y) == (p <= 0.0);
+    // the sign tests of a product of differences (a-b)(c-d), from the operands'
+    // order, except where the rounded product underflows, is NaN, or a
+    // difference meets +0 against -0 (equal values, unequal patterns)
+    const double a = x, b = (i & 16) ? a : (i & 4) ? y : scaling_sample(i + 0x51ed27ull);
+    const double c = scaling_sample(i ^ 0x2545f491ull), e = (i & 8) ? a : scaling_sample(i + 7);
+    const double pd = (a - b) * (c - e);
+    bool okd = true;
+    const bool zero_mix = (a == b && __double_as_longlong(a) != __double_as_longlong(b)) ||
+                          (c == e && __double_as_longlong(c) != __double_as_longlong(e));
+    if (!isnan(pd) && !zero_mix && !(pd == 0.0 && a != b && c != e))
+      okd = hydro::diffs_prod_pos<false>(a, b, c, e) == (pd > 0.0) &&
+            hydro::diffs_prod_neg<false>(a, b, c, e) == (pd < 0.0) &&
+            hydro::diffs_prod_nonpos<false>(a, b, c, e) == (pd <= 0.0);
     count(!okh, bad);
     count(!okt, bad + 1);
-    count(!oks, bad + 2);
+    count(!(oks && okd), bad + 2);
   }
 }
 

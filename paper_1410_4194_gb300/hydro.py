@@ -245,10 +245,15 @@ class Grid:
     def compute_dt(self, cfl):
         return self._dt_result(self._L.hydro_compute_dt(self.h, float(cfl)), "compute_dt", True)
 
-    def advance(self, cfl, t_end=math.inf, max_steps=1 << 52, check=True):
+    def advance(self, cfl, t_end=math.inf, max_steps=None, check=True):
         """CFL steps until the time reaches t_end (the last step shortened to land
         on it) or max_steps steps were taken, looped on the device inside one CUDA
-        graph; returns the number of steps taken (raises on error when check)."""
+        graph; returns the number of steps taken (raises on error when check).
+        One of t_end and max_steps must bound the run."""
+        if max_steps is None:
+            if math.isinf(t_end):
+                raise ValueError("advance needs a finite t_end or max_steps")
+            max_steps = 1 << 52
         n = ctypes.c_longlong(0)
         rc = self._L.hydro_advance(self.h, float(cfl), float(t_end), int(max_steps),
                                    ctypes.byref(n))

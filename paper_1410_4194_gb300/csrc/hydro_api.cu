@@ -12,6 +12,8 @@
 
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/hydro.h"
 #include "hydro_internal.h"
 #include "hydro_run.h"
@@ -99,11 +101,17 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 bool active(const Geom& G, int d) { return G.n[d] > 1; }
 
 // Tracing: when enabled, every launch is bracketed by two events on the
-// handle's stream; times are folded into per-stage totals once the step has
+// handle's stream, and by an NVTX range named after its stage for external
+// profilers; times are folded into per-stage totals once the step has
 // completed (hydro_step waits for its record anyway).
+const char* const kStageRange[kNumStages] = {"hydro prims+dt", "hydro dt",       "hydro slopes",
+                                             "hydro reconstruction", "hydro riemann1",
+                                             "hydro riemann2", "hydro update"};
+
 int mark_begin(hydro_t h, int stage, int axis) {
   ++h->launches_total;
   if (!h->profile || h->nev >= 64) return HYDRO_OK;
+  nvtxRangePushA(kStageRange[stage]);
   const int k = h->nev;
   h->ev_stage[k] = stage;
   h->ev_units[k] = stage_units(h->G, stage, axis);
@@ -113,6 +121,7 @@ int mark_begin(hydro_t h, int stage, int axis) {
 
 int mark_end(hydro_t h) {
   if (!h->profile || h->nev >= 64) return HYDRO_OK;
+  nvtxRangePop();
   CK(h, cudaEventRecord(h->ev[2 * h->nev + 1], h->stream));
   ++h->nev;
   return HYDRO_OK;
@@ -649,7 +658,10 @@ int hydro_advance(hydro_t h, double cfl, double t_end, long long max_steps, long
                         h->stream));
   long long done = 0;
   for (;;) {
-    CK(h, cudaGraphLaunch(h->run_exec, h->stream));
+    nvtxRangePushA("hydro advance (graph launch)");
+    const cudaError_t le = cudaGraphLaunch(h->run_exec, h->stream);
+    nvtxRangePop();
+    CK(h, le);
     rc = read_record(h, 11);
     if (rc) return rc;
     const long long n = (long long)h->host_rec[10];

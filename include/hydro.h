@@ -333,16 +333,18 @@ int hydro_ppmc(int n, const double* w, double dtdx, double gamma, double* WsL, d
  * Returns HYDRO_OK, HYDRO_EINVAL (mismatches NULL) or HYDRO_ECUDA. */
 int hydro_check_conversions(unsigned long long* mismatches, void* stream);
 
-/* Self-check of the integer-pipe FP64 helpers of the FP64 kernels (GB300
- * issues FP64 multiplies and compares on its FP64 pipe at 1/64 of the float
+/* Self-check of the integer-pipe FP64 helpers of the kernels (GB300 issues
+ * FP64 adds, multiplies and compares on its FP64 pipe at 1/64 of the float
  * rate): halving and doubling by moving the exponent field (shifting the
  * magnitude at the subnormal edge, rounding to even), the sign tests of a
  * product x*y from the factors' bits and of a product of differences
- * (a-b)(c-d) from the operands' order, against the FP64 arithmetic, on 2^30
- * counter-hashed operands concentrated on the exponent range's edges.
- * mismatches: host array of three counts (halving, doubling, sign tests; the
- * last skips products that underflow to zero or are NaN and differences of +0
- * and -0), all 0 when every case agrees.  Runs on `stream` and waits for it; allocates 24 bytes of device
+ * (a-b)(c-d) from the operands' order, against the FP64 arithmetic; and the
+ * mixed update's conversion of a float-float sum to one double, against the
+ * FP64 add (within one ulp).  2^30 counter-hashed cases, concentrated on the
+ * exponent range's edges.  mismatches: host array of four counts (halving,
+ * doubling, sign tests, float-float sums; the sign tests skip products that
+ * underflow to zero or are NaN and differences of +0 and -0), all 0 when every
+ * case agrees.  Runs on `stream` and waits for it; allocates 32 bytes of device
  * memory.  Returns HYDRO_OK, HYDRO_EINVAL (mismatches NULL) or HYDRO_ECUDA. */
 int hydro_check_scaling(unsigned long long* mismatches, void* stream);
 

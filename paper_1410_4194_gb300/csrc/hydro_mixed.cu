@@ -18,6 +18,7 @@
 // roots of the solver are the SFU approximations (nr_* in hydro_math.cuh).
 // Compiled with FMA contraction.
 #include "../../include/hydro.h"
+#include "hydro_ffsum.cuh"
 #include "hydro_kernels.cuh"
 
 namespace hydro {
@@ -375,14 +376,6 @@ __device__ __forceinline__ void riemann2_mixed_body(const Geom& G, const BufsF& 
 }
 
 
-// a + b as an unevaluated sum s + e of two floats, exactly (Knuth's TwoSum,
-// round-to-nearest without overflow)
-__device__ __forceinline__ float two_sum(float a, float b, float& e) {
-  const float s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-  return s;
-}
 
 // conserved update in FP64 from the float CTU fluxes.  Per variable the flux
 // differences of the active axes are summed in float-float arithmetic: each
@@ -423,7 +416,7 @@ __device__ __forceinline__ void update_mixed_body(const Geom& G, const BufsF& B,
       hi = two_sum(hi, s, e2);
       lo += e1 + e2;
     }
-    u[q] = fma(dtdx, f2d(hi) + f2d(lo), u[q]);
+    u[q] = fma(dtdx, ff_to_double(hi, lo), u[q]);
     const long long b = __double_as_longlong(u[q]);
     if ((b & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) fl = kFlagNonPhys;  // NaN
     if (q == 0 && b <= 0) fl = kFlagNonPhys;  // rho <= 0 (or a NaN with the sign bit)

@@ -2,12 +2,14 @@
 // float <-> double conversions of hydro_math.cuh against the hardware ones
 // (bit for bit in the normal range, zeros and infinities; subnormals flushed
 // to a signed zero; NaN to NaN); hydro_check_scaling(): its integer halving,
-// doubling and product-sign tests against the FP64 multiply.
+// doubling and sign tests against the FP64 arithmetic, and the float-float to
+// double conversion of hydro_ffsum.cuh against the FP64 add.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "../../include/hydro.h"
 #include "hydro_internal.h"
+#include "hydro_ffsum.cuh"
 #include "hydro_math.cuh"
 
 namespace {
@@ -126,9 +128,27 @@ __global__ void __launch_bounds__(kThreads) k_check_scaling(unsigned long long* 
       okd = hydro::diffs_prod_pos<false>(a, b, c, e) == (pd > 0.0) &&
             hydro::diffs_prod_neg<false>(a, b, c, e) == (pd < 0.0) &&
             hydro::diffs_prod_nonpos<false>(a, b, c, e) == (pd <= 0.0);
+    // a float-float pair as one double: within one ulp of the FP64 sum (the
+    // second member drawn up to 16 ulp of the first, or much smaller)
+    const float fh = __uint_as_float((unsigned)mix64(i ^ 0x7f4a7c15ull) & 0x7f7fffffu |
+                                     ((unsigned)i & 0x80000000u)) ;
+    const unsigned efh = __float_as_uint(fh) >> 23 & 0xffu;
+    const unsigned r2 = (unsigned)mix64(i + 0x94d049bbull);
+    const int de = 19 + (int)(r2 % 28u);  // lo 19..46 binades below hi
+    float fl = 0.f;
+    if (efh > (unsigned)de + 1u)
+      fl = __uint_as_float(((efh - de) << 23) | (r2 >> 9 & 0x7fffffu) | (r2 << 31));
+    bool okf = true;
+    if (efh >= 2u && efh <= 253u) {
+      const double ref = (double)fh + (double)fl;
+      const double got = hydro::ff_to_double(fh, fl);
+      const double ulp = fabs(ref) * 2.220446049250313e-16;
+      okf = fabs(got - ref) <= ulp;
+    }
     count(!okh, bad);
     count(!okt, bad + 1);
     count(!(oks && okd), bad + 2);
+    count(!okf, bad + 3);
   }
 }
 
@@ -138,15 +158,15 @@ extern "C" int hydro_check_scaling(unsigned long long* mismatches, void* stream)
   if (!mismatches) return HYDRO_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   unsigned long long* d = nullptr;
-  if (cudaMalloc(&d, 3 * sizeof(unsigned long long)) != cudaSuccess) return HYDRO_ECUDA;
+  if (cudaMalloc(&d, 4 * sizeof(unsigned long long)) != cudaSuccess) return HYDRO_ECUDA;
   int rc = HYDRO_OK;
-  if (cudaMemsetAsync(d, 0, 3 * sizeof(unsigned long long), st) != cudaSuccess) rc = HYDRO_ECUDA;
+  if (cudaMemsetAsync(d, 0, 4 * sizeof(unsigned long long), st) != cudaSuccess) rc = HYDRO_ECUDA;
   if (rc == HYDRO_OK) {
     k_check_scaling<<<kBlocks, kThreads, 0, st>>>(d);
     if (cudaGetLastError() != cudaSuccess) rc = HYDRO_ECUDA;
   }
   if (rc == HYDRO_OK &&
-      (cudaMemcpyAsync(mismatches, d, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+      (cudaMemcpyAsync(mismatches, d, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                        st) != cudaSuccess ||
        cudaStreamSynchronize(st) != cudaSuccess))
     rc = HYDRO_ECUDA;

@@ -365,14 +365,14 @@ def check_conversions():
 
 
 def check_scaling():
-    """Mismatch counts (halving, doubling, product signs) of the FP64 kernels'
-    integer-pipe helpers against the FP64 multiply."""
+    """Mismatch counts (halving, doubling, sign tests, float-float sums) of the
+    kernels' integer-pipe helpers against the FP64 arithmetic."""
     L = load()
-    out = (ctypes.c_ulonglong * 3)()
+    out = (ctypes.c_ulonglong * 4)()
     rc = L.hydro_check_scaling(out, _torch_stream_ptr())
     if rc != 0:
         raise HydroError(rc, "check_scaling")
-    return int(out[0]), int(out[1]), int(out[2])
+    return int(out[0]), int(out[1]), int(out[2]), int(out[3])
 
 
 def check_fastdiv():

@@ -660,8 +660,8 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
   T tLm[5], tRp[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    tLm[q] = T(0.5) * am * (dw[q] + w6[q] * (T(1) + c23 * am));
-    tRp[q] = T(0.5) * bp * (dw[q] - w6[q] * (T(1) - c23 * bp));
+    tLm[q] = half<S>(am) * (dw[q] + w6[q] * (T(1) + c23 * am));
+    tRp[q] = half<S>(bp) * (dw[q] - w6[q] * (T(1) - c23 * bp));
   }
   T sL[5] = {T(0), T(0), T(0), T(0), T(0)};
   T sR[5] = {T(0), T(0), T(0), T(0), T(0)};
@@ -669,15 +669,15 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
     const T a0 = dtdx * l0;
     T E[5];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) E[q] = tLm[q] - T(0.5) * a0 * (dw[q] + w6[q] * (T(1) + c23 * a0));
+    for (int q = 0; q < 5; ++q) E[q] = tLm[q] - half<S>(a0) * (dw[q] + w6[q] * (T(1) + c23 * a0));
     sL[0] = sL[0] + (E[0] - (S ? E[4] / (a * a) : E[4] * inv_a2));
     sL[2] = sL[2] + E[2];
     sL[3] = sL[3] + E[3];
   }
   if (neg<S>(lp)) {  // right acoustic wave reaches the left face: B
     const T ap = dtdx * lp;
-    const T B1 = tLm[1] - T(0.5) * ap * (dw[1] + w6[1] * (T(1) + c23 * ap));
-    const T B4 = tLm[4] - T(0.5) * ap * (dw[4] + w6[4] * (T(1) + c23 * ap));
+    const T B1 = tLm[1] - half<S>(ap) * (dw[1] + w6[1] * (T(1) + c23 * ap));
+    const T B4 = tLm[4] - half<S>(ap) * (dw[4] + w6[4] * (T(1) + c23 * ap));
     if constexpr (S) {
       sL[0] = sL[0] + T(0.5) * (rho * B1 / a + B4 / (a * a));
       sL[1] = sL[1] + T(0.5) * (B1 + B4 / (a * rho));
@@ -689,8 +689,8 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
   }
   if (pos<S>(lm)) {  // left acoustic wave reaches the right face: C
     const T bm = dtdx * lm;
-    const T C1 = tRp[1] - T(0.5) * bm * (dw[1] - w6[1] * (T(1) - c23 * bm));
-    const T C4 = tRp[4] - T(0.5) * bm * (dw[4] - w6[4] * (T(1) - c23 * bm));
+    const T C1 = tRp[1] - half<S>(bm) * (dw[1] - w6[1] * (T(1) - c23 * bm));
+    const T C4 = tRp[4] - half<S>(bm) * (dw[4] - w6[4] * (T(1) - c23 * bm));
     if constexpr (S) {
       sR[0] = sR[0] + T(0.5) * (-(rho * C1) / a + C4 / (a * a));
       sR[1] = sR[1] + T(0.5) * (C1 - C4 / (a * rho));
@@ -704,7 +704,7 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
     const T b0 = dtdx * l0;
     T D[5];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) D[q] = tRp[q] - T(0.5) * b0 * (dw[q] - w6[q] * (T(1) - c23 * b0));
+    for (int q = 0; q < 5; ++q) D[q] = tRp[q] - half<S>(b0) * (dw[q] - w6[q] * (T(1) - c23 * b0));
     sR[0] = sR[0] + (D[0] - (S ? D[4] / (a * a) : D[4] * inv_a2));
     sR[2] = sR[2] + D[2];
     sR[3] = sR[3] + D[3];
@@ -815,23 +815,23 @@ __device__ __forceinline__ void plmc_states(const T wm[5], const T wc[5], const 
   }
   if (neg<S>(lp)) {  // right acoustic wave
     if constexpr (S) {
-      sL[0] = sL[0] + T(0.5) * (lm - lp) * (d * dw[1] / a + dw[4] / a2);
-      sL[1] = sL[1] + T(0.5) * (lm - lp) * (dw[1] + dw[4] / (a * d));
+      sL[0] = sL[0] + half<S>(lm - lp) * (d * dw[1] / a + dw[4] / a2);
+      sL[1] = sL[1] + half<S>(lm - lp) * (dw[1] + dw[4] / (a * d));
     } else {
-      sL[0] = sL[0] + T(0.5) * (lm - lp) * (d * dw[1] * inv_a + dw[4] * inv_a2);
-      sL[1] = sL[1] + T(0.5) * (lm - lp) * (dw[1] + dw[4] * (inv_a * inv_rho));
+      sL[0] = sL[0] + half<S>(lm - lp) * (d * dw[1] * inv_a + dw[4] * inv_a2);
+      sL[1] = sL[1] + half<S>(lm - lp) * (dw[1] + dw[4] * (inv_a * inv_rho));
     }
-    sL[4] = sL[4] + T(0.5) * (lm - lp) * (d * dw[1] * a + dw[4]);
+    sL[4] = sL[4] + half<S>(lm - lp) * (d * dw[1] * a + dw[4]);
   }
   if (pos<S>(lm)) {  // left acoustic wave
     if constexpr (S) {
-      sR[0] = sR[0] + T(0.5) * (lp - lm) * (-(d * dw[1]) / a + dw[4] / a2);
-      sR[1] = sR[1] + T(0.5) * (lp - lm) * (dw[1] - dw[4] / (a * d));
+      sR[0] = sR[0] + half<S>(lp - lm) * (-(d * dw[1]) / a + dw[4] / a2);
+      sR[1] = sR[1] + half<S>(lp - lm) * (dw[1] - dw[4] / (a * d));
     } else {
-      sR[0] = sR[0] + T(0.5) * (lp - lm) * (-(d * dw[1]) * inv_a + dw[4] * inv_a2);
-      sR[1] = sR[1] + T(0.5) * (lp - lm) * (dw[1] - dw[4] * (inv_a * inv_rho));
+      sR[0] = sR[0] + half<S>(lp - lm) * (-(d * dw[1]) * inv_a + dw[4] * inv_a2);
+      sR[1] = sR[1] + half<S>(lp - lm) * (dw[1] - dw[4] * (inv_a * inv_rho));
     }
-    sR[4] = sR[4] + T(0.5) * (lp - lm) * (-(d * dw[1] * a) + dw[4]);
+    sR[4] = sR[4] + half<S>(lp - lm) * (-(d * dw[1] * a) + dw[4]);
   }
   if (pos<S>(l0)) {  // contact (and advected transverse velocities)
     sR[0] = sR[0] + (lp - l0) * (dw[0] - (S ? dw[4] / a2 : dw[4] * inv_a2));
@@ -842,8 +842,8 @@ __device__ __forceinline__ void plmc_states(const T wm[5], const T wc[5], const 
   const T h = T(0.5) * dtdx;
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    WsL[q] = (WL[q] - T(0.5) * am * dw[q]) + h * sL[q];
-    WsR[q] = (WR[q] - T(0.5) * bp * dw[q]) + h * sR[q];
+    WsL[q] = (WL[q] - half<S>(am) * dw[q]) + h * sL[q];
+    WsR[q] = (WR[q] - half<S>(bp) * dw[q]) + h * sR[q];
   }
   WsL[4] = vmax<S>(WsL[4], T(kPFloor));
   WsR[4] = vmax<S>(WsR[4], T(kPFloor));
@@ -895,8 +895,8 @@ __device__ __forceinline__ void ppmp_states(const T w[7][5], const T sm[5], cons
       WL[q] = T(0.5) * (wi[q] + wim[q]) - (sc[q] - sm[q]) / T(6);
       WR[q] = T(0.5) * (wip[q] + wi[q]) - (sp[q] - sc[q]) / T(6);
     } else {
-      WL[q] = T(0.5) * (wi[q] + wim[q]) - (sc[q] - sm[q]) * T(1.0 / 6.0);
-      WR[q] = T(0.5) * (wip[q] + wi[q]) - (sp[q] - sc[q]) * T(1.0 / 6.0);
+      WL[q] = half<S>(wi[q] + wim[q]) - (sc[q] - sm[q]) * T(1.0 / 6.0);
+      WR[q] = half<S>(wip[q] + wi[q]) - (sp[q] - sc[q]) * T(1.0 / 6.0);
     }
   }
   // contact discontinuity steepening of the density
@@ -978,12 +978,12 @@ __device__ __forceinline__ void ppmp_states(const T w[7][5], const T sm[5], cons
   T WLm[5], WL0[5], WLp[5], WRm[5], WR0[5], WRp[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    WLm[q] = WL[q] - T(0.5) * am * (dw[q] + w6[q] * (T(1) + c23 * am));
-    WL0[q] = WL[q] - T(0.5) * a0 * (dw[q] + w6[q] * (T(1) + c23 * a0));
-    WLp[q] = WL[q] - T(0.5) * ap * (dw[q] + w6[q] * (T(1) + c23 * ap));
-    WRm[q] = WR[q] - T(0.5) * bm * (dw[q] - w6[q] * (T(1) - c23 * bm));
-    WR0[q] = WR[q] - T(0.5) * b0 * (dw[q] - w6[q] * (T(1) - c23 * b0));
-    WRp[q] = WR[q] - T(0.5) * bp * (dw[q] - w6[q] * (T(1) - c23 * bp));
+    WLm[q] = WL[q] - half<S>(am) * (dw[q] + w6[q] * (T(1) + c23 * am));
+    WL0[q] = WL[q] - half<S>(a0) * (dw[q] + w6[q] * (T(1) + c23 * a0));
+    WLp[q] = WL[q] - half<S>(ap) * (dw[q] + w6[q] * (T(1) + c23 * ap));
+    WRm[q] = WR[q] - half<S>(bm) * (dw[q] - w6[q] * (T(1) - c23 * bm));
+    WR0[q] = WR[q] - half<S>(b0) * (dw[q] - w6[q] * (T(1) - c23 * b0));
+    WRp[q] = WR[q] - half<S>(bp) * (dw[q] - w6[q] * (T(1) - c23 * bp));
   }
   // reference states and Lagrangian impedances C = rho a of the reference states
   T chiLp, chiRm, chiL0, chiR0, CL, CR, irL, irR;
@@ -1342,7 +1342,8 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
   make_side<S>(WL, inv_dL, g, L);
   make_side<S>(WR, inv_dR, g, R);
   // primitive-variable estimate, then the two-shock estimate as Newton start
-  T pt = half<S>(L.p + R.p) + T(0.125) * (L.u - R.u) * (L.d + R.d) * (L.a + R.a);
+  T pt = half<S>(L.p + R.p) +
+         half<S>(half<S>(half<S>(L.u - R.u))) * (L.d + R.d) * (L.a + R.a);  // (1/8) du, exact
   if (neg<S>(pt)) pt = T(0);
   T gL, gR, p;
   if constexpr (!S) {

@@ -172,6 +172,25 @@ double hydro_step_dt(hydro_t h, double dt);
 /* The dt that hydro_step(h, cfl) would use now, without changing the state. */
 double hydro_compute_dt(hydro_t h, double cfl);
 
+/* Asynchronous forms, for pipelines that overlap one handle's copies with
+ * another's steps: each enqueues its work on the handle's stream and returns
+ * without waiting.  A host pointer must stay valid until the copy has run and
+ * should be page-locked memory (cudaHostAlloc, a pinned torch tensor): copies
+ * from pageable memory do not overlap.  hydro_step_async takes one CFL step as
+ * hydro_step does but leaves dt and the status word on the device; it is not
+ * timed by the tracing (its launches are counted).  The status word of async
+ * steps accumulates until hydro_sync reads it; a synchronous hydro_step,
+ * hydro_step_dt or hydro_advance clears it first, so call hydro_sync before
+ * them.  Return HYDRO_OK, HYDRO_EINVAL, HYDRO_ENOSTATE or HYDRO_ECUDA. */
+int hydro_set_state_async(hydro_t h, const double* u, int on_device);
+int hydro_get_state_async(hydro_t h, double* u, int on_device);
+int hydro_step_async(hydro_t h, double cfl);
+/* Wait for the handle's stream.  Returns HYDRO_OK, or HYDRO_ENONPHYS /
+ * HYDRO_ENEWTON if a step since the last synchronous step or hydro_sync raised
+ * that status (then cleared); *dt_out (may be NULL) receives the last step's
+ * dt. */
+int hydro_sync(hydro_t h, double* dt_out);
+
 /* Advance with CFL steps (as hydro_step(h, cfl)) until the time (see
  * hydro_set_time) reaches t_end, or max_steps steps were taken, without a host
  * round trip per step: the steps run as a loop inside one CUDA graph (a

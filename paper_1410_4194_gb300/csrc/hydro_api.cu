@@ -160,12 +160,15 @@ BatchLaunch one_grid(hydro_t h, int kind) {
 
 // Enqueue one full step; dt from the CFL condition when fixed_dt <= 0, cut back
 // to the end time in the record's slot 8 when to_end is set.
-int enqueue_step(hydro_t h, double cfl, double fixed_dt, bool to_end = false) {
+// keep_flags: leave the status word of earlier steps (asynchronous steps, whose
+// status is read by hydro_sync).
+int enqueue_step(hydro_t h, double cfl, double fixed_dt, bool to_end = false,
+                 bool keep_flags = false) {
   const Geom& G = h->G;
   const Bufs& B = h->B;
   cudaStream_t st = h->stream;
   h->nev = 0;
-  CK(h, cudaMemsetAsync(B.rec + 4, 0, sizeof(double), st));
+  if (!keep_flags) CK(h, cudaMemsetAsync(B.rec + 4, 0, sizeof(double), st));
   if (h->precision == HYDRO_FP64_STRICT) {
     STAGE(h, kStagePrims, 0, fp64_prims(G, B, h->bc, h->gamma, fixed_dt <= 0.0, st));
     STAGE(h, kStageSetDt, 0,
@@ -628,6 +631,66 @@ int hydro_get_state(hydro_t h, double* u, int on_device) {
 }
 
 double hydro_step(hydro_t h, double cfl) { return run_step(h, cfl, 0.0); }
+
+int hydro_set_state_async(hydro_t h, const double* u, int on_device) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (!u) return fail(h, HYDRO_EINVAL);
+  int rc = use_device(h);
+  if (rc) return rc;
+  const size_t bytes = (size_t)h->G.nreal * 5 * sizeof(double);
+  CK(h, cudaMemcpyAsync(h->B.u, u, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        h->stream));
+  h->have_state = true;
+  return HYDRO_OK;
+}
+
+int hydro_get_state_async(hydro_t h, double* u, int on_device) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (!u) return fail(h, HYDRO_EINVAL);
+  if (!h->have_state) return fail(h, HYDRO_ENOSTATE);
+  int rc = use_device(h);
+  if (rc) return rc;
+  const size_t bytes = (size_t)h->G.nreal * 5 * sizeof(double);
+  CK(h, cudaMemcpyAsync(u, h->B.u, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        h->stream));
+  return HYDRO_OK;
+}
+
+int hydro_step_async(hydro_t h, double cfl) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (!h->have_state) return fail(h, HYDRO_ENOSTATE);
+  if (!(cfl > 0.0)) return fail(h, HYDRO_EINVAL);
+  int rc = use_device(h);
+  if (rc) return rc;
+  // not traced: the events of a step are folded only once it has completed
+  const bool profile = h->profile;
+  h->profile = false;
+  rc = enqueue_step(h, cfl, 0.0, false, true);
+  h->profile = profile;
+  return rc;
+}
+
+int hydro_sync(hydro_t h, double* dt_out) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  int rc = use_device(h);
+  if (rc) return rc;
+  rc = read_record(h);  // waits for the handle's stream
+  if (rc) return rc;
+  if (dt_out) *dt_out = h->host_rec[1];
+  int flags;
+  memcpy(&flags, h->host_rec + 4, sizeof(int));
+  if (flags) {
+    CK(h, cudaMemsetAsync(h->B.rec + 4, 0, sizeof(double), h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+  }
+  if (flags & kFlagNonPhys) return fail(h, HYDRO_ENONPHYS);
+  if (flags & kFlagNewton) return fail(h, HYDRO_ENEWTON);
+  return HYDRO_OK;
+}
 
 double hydro_step_dt(hydro_t h, double dt) {
   if (!h) return (double)HYDRO_EINVAL;

@@ -28,7 +28,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhydro.so")
 EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_time", "hydro_get_time",
            "hydro_set_precision", "hydro_set_stream", "hydro_set_block_size", "hydro_block_size",
            "hydro_set_state", "hydro_get_state", "hydro_step", "hydro_step_dt",
-           "hydro_compute_dt", "hydro_advance", "hydro_last_error", "hydro_error_string",
+           "hydro_compute_dt", "hydro_advance",
+           "hydro_set_state_async", "hydro_get_state_async", "hydro_step_async", "hydro_sync", "hydro_last_error", "hydro_error_string",
            "hydro_cuda_error_string", "hydro_profile", "hydro_profile_read", "hydro_free",
            "hydro_riemann_exact", "hydro_ppmc", "hydro_compute_dt_noalloc",
            "hydro_batch_init", "hydro_batch_set_inflow", "hydro_batch_set_precision",
@@ -82,6 +83,10 @@ def load():
     llp = ctypes.POINTER(ctypes.c_longlong)
     L.hydro_profile_read.argtypes = [vp, ctypes.c_int, dp, llp, llp, llp]
     L.hydro_advance.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_longlong, llp]
+    L.hydro_set_state_async.argtypes = [vp, vp, ctypes.c_int]
+    L.hydro_get_state_async.argtypes = [vp, vp, ctypes.c_int]
+    L.hydro_step_async.argtypes = [vp, ctypes.c_double]
+    L.hydro_sync.argtypes = [vp, dp]
     L.hydro_riemann_exact.argtypes = [ctypes.c_int, vp, vp, ctypes.c_double, vp, vp, vp]
     L.hydro_ppmc.argtypes = [ctypes.c_int, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp]
     L.hydro_compute_dt_noalloc.argtypes = [vp] + [ctypes.c_int] * 3 + [ctypes.c_double] * 3 + [vp, vp]
@@ -145,6 +150,7 @@ class Grid:
         self.h = h
         self.shape = (5, nz, ny, nx)
         self.n = (nx, ny, nz)
+        self._pending = []
         if stream is not None:
             self.set_stream(stream)
         if recon != HYDRO_RECON_PPMC:
@@ -225,6 +231,38 @@ class Grid:
         ptr, dev, keep = _buffer(out, self.shape, True)
         self._check(self._L.hydro_get_state(self.h, ptr, dev), "get_state")
         return out
+
+    # asynchronous forms: the buffers are held until sync(); a host buffer should
+    # be page-locked (a pinned torch tensor) for the copy to overlap other work
+    def _async_buffer(self, u, writable):
+        ptr, dev, keep = _buffer(u, self.shape, writable)
+        if keep is not u:
+            raise ValueError("asynchronous copies need a C-contiguous float64 buffer (no temporary)")
+        self._pending.append(u)
+        return ptr, dev
+
+    def set_state_async(self, u):
+        ptr, dev = self._async_buffer(u, False)
+        self._check(self._L.hydro_set_state_async(self.h, ptr, dev), "set_state_async")
+
+    def get_state_async(self, out):
+        ptr, dev = self._async_buffer(out, True)
+        self._check(self._L.hydro_get_state_async(self.h, ptr, dev), "get_state_async")
+        return out
+
+    def step_async(self, cfl):
+        """Enqueue one CFL step; dt and the status stay on the device until sync()."""
+        self._check(self._L.hydro_step_async(self.h, float(cfl)), "step_async")
+
+    def sync(self, check=True):
+        """Wait for this grid's stream; returns the last step's dt (raises on a
+        step's error status when check)."""
+        dt = ctypes.c_double(0.0)
+        rc = self._L.hydro_sync(self.h, ctypes.byref(dt))
+        self._pending = []
+        if check:
+            self._check(rc, "sync")
+        return dt.value
 
     def _dt_result(self, dt, what, check):
         if dt < 0:

@@ -197,3 +197,57 @@ def test_inflow_change_recaptures():
         assert np.array_equal(g.get_state(), res[1])
     finally:
         g.close()
+
+
+# ---- asynchronous forms (pipelines of independent problems) -----------------
+def test_async_pipeline_matches_synchronous_steps():
+    """Two grids on two streams, alternating: each upload-step-download of the
+    same input gives the synchronous step's state bit for bit, and sync returns
+    its dt."""
+    torch = pytest.importorskip("torch")
+    w = W.sedov(24)
+    _, nz, ny, nx = w["u"].shape
+    ref = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"])
+    try:
+        ref.set_state(w["u"])
+        dt_ref = ref.step(0.3)
+        u_ref = ref.get_state()
+    finally:
+        ref.close()
+    u_in = torch.from_numpy(w["u"]).pin_memory()
+    outs = [torch.empty_like(u_in).pin_memory() for _ in range(4)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    grids = [hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], stream=s) for s in streams]
+    try:
+        for k in range(4):
+            gk = grids[k % 2]
+            gk.set_state_async(u_in)
+            gk.step_async(0.3)
+            gk.get_state_async(outs[k])
+        dts = [gg.sync() for gg in grids]
+        assert dts == [dt_ref, dt_ref]
+        for o in outs:
+            assert np.array_equal(o.numpy(), u_ref)
+    finally:
+        for gg in grids:
+            gg.close()
+
+
+def test_async_status_is_reported_by_sync():
+    u = W.prim_to_cons(np.ones((8, 8, 8)), 0.0, 0.0, 0.0, np.ones((8, 8, 8)), 1.4)
+    good = u.copy()
+    u[0, 4, 4, 4] = -1.0
+    g = hydro.Grid(8, 8, 8, 0.1, 1.4, [P] * 6)
+    try:
+        g.set_state_async(u)
+        g.step_async(0.3)
+        g.set_state_async(good)
+        g.step_async(0.3)  # a good step does not clear the earlier status
+        with pytest.raises(hydro.HydroError) as e:
+            g.sync()
+        assert e.value.code == -4
+        assert g.sync() > 0  # read and cleared
+        with pytest.raises(ValueError):
+            g.set_state_async(u[:, ::-1])  # would need a temporary copy
+    finally:
+        g.close()

@@ -280,6 +280,20 @@ int hydro_batch_get_state(hydro_batch_t h, int grid, double* u, int on_device);
  * graph; later calls replay it.  Returns HYDRO_OK or an error code (a
  * non-physical state or a Newton cap in any grid is reported after the call). */
 int hydro_batch_step(hydro_batch_t h, double cfl, int nsteps, double* dt_out);
+/* Asynchronous forms of hydro_batch_set_state, hydro_batch_get_state and
+ * hydro_batch_step (as for single grids: enqueued on the batch's stream, no
+ * wait; host buffers should be page-locked and stay valid until the copy has
+ * run).  Each graph launch starts from a cleared status word, so
+ * hydro_batch_sync reports the status of the last hydro_batch_step_async:
+ * call it after each one (a pipeline syncs one batch while the next one's work
+ * is queued).  No dt history is returned. */
+int hydro_batch_set_state_async(hydro_batch_t h, int grid, const double* u, int on_device);
+int hydro_batch_get_state_async(hydro_batch_t h, int grid, double* u, int on_device);
+int hydro_batch_step_async(hydro_batch_t h, double cfl, int nsteps);
+/* Wait for the batch's stream; HYDRO_OK, or HYDRO_ENONPHYS / HYDRO_ENEWTON if
+ * a grid of the last step call raised that status. */
+int hydro_batch_sync(hydro_batch_t h);
+
 /* Choose the launch schedule -- threads per block (128 or 256) and the order of
  * the grids' blocks (as given, or largest grid first) -- by timing one step of
  * each candidate from the current states (restored afterwards).  With

@@ -452,9 +452,8 @@ int hydro_batch_get_state(hydro_batch_t h, int grid, double* u, int on_device) {
   return HYDRO_OK;
 }
 
-int hydro_batch_step(hydro_batch_t h, double cfl, int nsteps, double* dt_out) {
-  if (!h) return HYDRO_EINVAL;
-  h->last_error = HYDRO_OK;
+// Capture (when the call shape changed) and launch the graph of nsteps steps.
+static int launch_steps(hydro_batch_t h, double cfl, int nsteps) {
   if (nsteps < 1 || !(cfl > 0.0)) return bfail(h, HYDRO_EINVAL);
   for (int i = 0; i < h->ngrids; ++i)
     if (!h->have_state[i]) return bfail(h, HYDRO_ENOSTATE);
@@ -493,14 +492,61 @@ int hydro_batch_step(hydro_batch_t h, double cfl, int nsteps, double* dt_out) {
     h->g_sched = h->sched;
   }
   BCK(h, cudaGraphLaunch(h->gexec, h->stream));
-  if (dt_out)
-    BCK(h, cudaMemcpyAsync(dt_out, h->d_dt, (size_t)nsteps * h->ngrids * sizeof(double),
-                           cudaMemcpyDeviceToHost, h->stream));
+  return HYDRO_OK;
+}
+
+// the status word of the last graph launch (waits for the stream)
+static int status_of(hydro_batch_t h) {
   int flags = 0;
-  rc = read_flags(h, &flags);
+  const int rc = read_flags(h, &flags);
   if (rc) return rc;
   if (flags & kFlagNonPhys) return bfail(h, HYDRO_ENONPHYS);
   if (flags & kFlagNewton) return bfail(h, HYDRO_ENEWTON);
+  return HYDRO_OK;
+}
+
+int hydro_batch_step(hydro_batch_t h, double cfl, int nsteps, double* dt_out) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  int rc = launch_steps(h, cfl, nsteps);
+  if (rc) return rc;
+  if (dt_out)
+    BCK(h, cudaMemcpyAsync(dt_out, h->d_dt, (size_t)nsteps * h->ngrids * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->stream));
+  return status_of(h);
+}
+
+int hydro_batch_step_async(hydro_batch_t h, double cfl, int nsteps) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  return launch_steps(h, cfl, nsteps);
+}
+
+int hydro_batch_sync(hydro_batch_t h) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  return status_of(h);
+}
+
+int hydro_batch_set_state_async(hydro_batch_t h, int grid, const double* u, int on_device) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (grid < 0 || grid >= h->ngrids || !u) return bfail(h, HYDRO_EINVAL);
+  const GridDesc& g = h->desc[grid];
+  BCK(h, cudaMemcpyAsync(g.B.u, u, (size_t)g.G.nreal * 5 * sizeof(double),
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  h->have_state[grid] = 1;
+  return HYDRO_OK;
+}
+
+int hydro_batch_get_state_async(hydro_batch_t h, int grid, double* u, int on_device) {
+  if (!h) return HYDRO_EINVAL;
+  h->last_error = HYDRO_OK;
+  if (grid < 0 || grid >= h->ngrids || !u) return bfail(h, HYDRO_EINVAL);
+  if (!h->have_state[grid]) return bfail(h, HYDRO_ENOSTATE);
+  const GridDesc& g = h->desc[grid];
+  BCK(h, cudaMemcpyAsync(u, g.B.u, (size_t)g.G.nreal * 5 * sizeof(double),
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
   return HYDRO_OK;
 }
 

@@ -34,7 +34,8 @@ EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_time", "hydro_get_time",
            "hydro_riemann_exact", "hydro_ppmc", "hydro_compute_dt_noalloc",
            "hydro_batch_init", "hydro_batch_set_inflow", "hydro_batch_set_precision",
            "hydro_batch_set_stream", "hydro_batch_set_state", "hydro_batch_get_state",
-           "hydro_batch_step", "hydro_batch_autotune", "hydro_batch_last_error",
+           "hydro_batch_step", "hydro_batch_step_async", "hydro_batch_sync",
+           "hydro_batch_set_state_async", "hydro_batch_get_state_async", "hydro_batch_autotune", "hydro_batch_last_error",
            "hydro_batch_cuda_error_string", "hydro_batch_free", "hydro_check_conversions",
            "hydro_check_fastdiv", "hydro_check_scaling",
            "hydro_set_reconstruction", "hydro_batch_set_reconstruction",
@@ -97,6 +98,10 @@ def load():
     L.hydro_batch_set_state.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
     L.hydro_batch_get_state.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
     L.hydro_batch_step.argtypes = [vp, ctypes.c_double, ctypes.c_int, dp]
+    L.hydro_batch_step_async.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    L.hydro_batch_sync.argtypes = [vp]
+    L.hydro_batch_set_state_async.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
+    L.hydro_batch_get_state_async.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int]
     L.hydro_batch_autotune.argtypes = [vp, ctypes.c_int, ip, ip, ctypes.POINTER(ctypes.c_float)]
     L.hydro_batch_last_error.argtypes = [vp]
     L.hydro_batch_cuda_error_string.argtypes = [vp]
@@ -447,6 +452,7 @@ class Batch:
             raise HydroError(rc, "hydro_batch_init")
         self.h = h
         self.n = n
+        self._pending = []
         if recon != HYDRO_RECON_PPMC:
             self._check(L.hydro_batch_set_reconstruction(h, int(recon)), "set_reconstruction")
         if solver != HYDRO_RIEMANN_EXACT:
@@ -487,6 +493,35 @@ class Batch:
         ptr, dev, keep = _buffer(out, self.shapes[i], True)
         self._check(self._L.hydro_batch_get_state(self.h, int(i), ptr, dev), "get_state")
         return out
+
+    def set_state_async(self, i, u):
+        ptr, dev, keep = _buffer(u, self.shapes[i], False)
+        if keep is not u:
+            raise ValueError("asynchronous copies need a C-contiguous float64 buffer (no temporary)")
+        self._pending.append(u)
+        self._check(self._L.hydro_batch_set_state_async(self.h, int(i), ptr, dev), "set_state_async")
+
+    def get_state_async(self, i, out):
+        ptr, dev, keep = _buffer(out, self.shapes[i], True)
+        if keep is not out:
+            raise ValueError("asynchronous copies need a C-contiguous float64 buffer (no temporary)")
+        self._pending.append(out)
+        self._check(self._L.hydro_batch_get_state_async(self.h, int(i), ptr, dev), "get_state_async")
+        return out
+
+    def step_async(self, cfl, nsteps=1):
+        self._check(self._L.hydro_batch_step_async(self.h, float(cfl), int(nsteps)), "step_async")
+
+    def sync(self):
+        """Wait for the batch's stream; raises on the last step call's error status."""
+        rc = self._L.hydro_batch_sync(self.h)
+        self._pending = []
+        self._check(rc, "sync")
+
+    def set_stream(self, stream):
+        """Order the batch's work on a torch CUDA stream (or a raw cudaStream_t)."""
+        ptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        self._check(self._L.hydro_batch_set_stream(self.h, ctypes.c_void_p(ptr)), "set_stream")
 
     def step(self, cfl, nsteps=1):
         """Advance every grid nsteps steps; returns dt [nsteps, ngrids]."""

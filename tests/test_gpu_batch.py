@@ -165,3 +165,46 @@ def test_block_size_leaves_results_unchanged(precision):
         assert g.block_size() == 128
     finally:
         g.close()
+
+
+def test_batch_async_pipeline_matches_synchronous_steps():
+    """Asynchronous uploads, steps and downloads on two batches alternating on
+    two streams give the synchronous batch step's states bit for bit; sync
+    reports a step's error status."""
+    torch = pytest.importorskip("torch")
+    grids = small_batch()
+    ref = hydro.Batch(grids)
+    ref.step(0.3, nsteps=1)
+    expect = [ref.get_state(i) for i in range(len(grids))]
+    ref.close()
+    hosts = [torch.from_numpy(np.ascontiguousarray(g["u"])).pin_memory() for g in grids]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    pipe = []
+    for s in streams:
+        b = hydro.Batch(grids)
+        b.set_stream(s)
+        pipe.append(b)
+    outs = [[torch.empty_like(x).pin_memory() for x in hosts] for _ in range(3)]
+    try:
+        for k in range(3):
+            bk = pipe[k % 2]
+            for i, x in enumerate(hosts):
+                bk.set_state_async(i, x)
+            bk.step_async(0.3, nsteps=1)
+            for i, x in enumerate(outs[k]):
+                bk.get_state_async(i, x)
+            if k >= 1:
+                pipe[(k - 1) % 2].sync()
+        pipe[0].sync()
+        for o in outs:
+            for i, x in enumerate(o):
+                assert np.array_equal(x.numpy(), expect[i]), i
+        bad = hosts[0].clone().pin_memory()
+        bad[0, 0, 0, 0] = -1.0
+        pipe[1].set_state_async(0, bad)
+        pipe[1].step_async(0.3, nsteps=1)
+        with pytest.raises(hydro.HydroError):
+            pipe[1].sync()
+    finally:
+        for b in pipe:
+            b.close()

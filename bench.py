@@ -121,15 +121,15 @@ NCU_TRAFFIC = {
                            "sources": _FP64_SRC},
     ("fp64", "slopes"): {"bytes_per_unit": 99.79, "digest": "4150894091c1e388", "bs": 128,
                          "sources": _FP64_SRC},
-    ("mixed", "riemann2"): {"bytes_per_unit": 99.92, "digest": "09704c9daab4517b", "bs": 128,
+    ("mixed", "riemann2"): {"bytes_per_unit": 99.85, "digest": "ae3e351240f45599", "bs": 128,
                             "sources": _MIXED_SRC},
-    ("mixed", "update"): {"bytes_per_unit": 137.10, "digest": "09704c9daab4517b", "bs": 128,
+    ("mixed", "update"): {"bytes_per_unit": 138.24, "digest": "ae3e351240f45599", "bs": 128,
                           "sources": _MIXED_SRC},
-    ("mixed", "ppmc"): {"bytes_per_unit": 63.00, "digest": "09704c9daab4517b", "bs": 128,
+    ("mixed", "ppmc"): {"bytes_per_unit": 62.97, "digest": "ae3e351240f45599", "bs": 128,
                         "sources": _MIXED_SRC},
-    ("mixed", "riemann1"): {"bytes_per_unit": 55.41, "digest": "09704c9daab4517b", "bs": 128,
+    ("mixed", "riemann1"): {"bytes_per_unit": 55.45, "digest": "ae3e351240f45599", "bs": 128,
                             "sources": _MIXED_SRC},
-    ("mixed", "prims"): {"bytes_per_unit": 59.29, "digest": "09704c9daab4517b", "bs": 128,
+    ("mixed", "prims"): {"bytes_per_unit": 59.30, "digest": "ae3e351240f45599", "bs": 128,
                          "sources": _MIXED_SRC},
 }
 

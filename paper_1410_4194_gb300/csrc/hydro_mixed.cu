@@ -27,15 +27,17 @@ namespace {
 using GasF = GasT<float>;
 using GasD = GasT<double>;
 
-// resident 256-thread blocks per SM for the stencil and Riemann stages, by
-// measurement on Sedov 256^3: PPMC runs best at 4 (64 registers; 3 is 6%
-// slower, 5 and 6 spill), the first Riemann set at 6 (40 registers: its Newton
+// resident threads per SM for the stencil and Riemann stages, in units of 256
+// (a block is 128 or 256 threads), by measurement on Sedov 256^3: PPMC at 4
+// (64 registers; 3 is 6% slower; 5 takes 48 registers and spills, 1% faster on
+// Sedov but 5% slower on Mach-5 turbulence), the first Riemann set at 6 (40 registers: its Newton
 // iteration is a latency chain that more resident warps hide; 14% faster than
 // at 4), the second with the bound of 3 (the compiler then takes 64 registers
-// instead of 56 -- still 4 resident blocks -- and the kernel runs 8% faster);
-// the primitives at 6 and the update at 5 (14% faster than at 4)
+// instead of 56 and the kernel runs 8% faster; 4 is slower), the primitives at
+// 6 and the update at 6 (40 registers and a 56-byte spill, 4% faster than at 5,
+// which was 14% faster than 4)
 constexpr int kMinBlocksPpmc = 4, kMinBlocksRiemann1 = 6, kMinBlocksRiemann2 = 3;
-constexpr int kMinBlocksPrims = 6, kMinBlocksUpdate = 5;
+constexpr int kMinBlocksPrims = 6, kMinBlocksUpdate = 6;
 
 // A five-value face quantity (a primitive state or a flux, x/y/z components
 // in axis order) in vector form: values 0-3 in one float4 plane, value 4 in

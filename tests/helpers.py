@@ -42,3 +42,37 @@ def rotate_xyz(u):
     out[2] = r[1]  # new y momentum = old x momentum
     out[3] = r[2]  # new z momentum = old y momentum
     return out
+
+
+def build_oracle_mutant(tag, edits):
+    """Compile a copy of the oracle with planted mistakes and load it.
+
+    ``edits`` is a list of (function_head, old, new): inside the function whose
+    definition starts with ``function_head`` (up to its closing brace at column
+    0), the text ``old`` -- which must occur there exactly once -- is replaced
+    by ``new``.  The copy is compiled with the oracle's own flags into a
+    temporary directory; returns the loaded ``ctypes.CDLL``.  Used to check that
+    a pin fails when the oracle is wrong.
+    """
+    import ctypes
+    import os
+    import subprocess
+    import tempfile
+
+    from oracle import build_oracle
+
+    with open(build_oracle.SRC) as f:
+        src = f.read()
+    for head, old, new in edits:
+        a = src.index(head)
+        b = src.index("\n}\n", a) + 3
+        body = src[a:b]
+        assert body.count(old) == 1, (tag, head, old, body.count(old))
+        src = src[:a] + body.replace(old, new) + src[b:]
+    d = tempfile.mkdtemp(prefix="oracle_mutant_")
+    path_c = os.path.join(d, "mutant_%s.cpp" % tag)
+    path_so = os.path.join(d, "libmutant_%s.so" % tag)
+    with open(path_c, "w") as f:
+        f.write(src)
+    subprocess.run(["g++"] + build_oracle.FLAGS + [path_c, "-o", path_so], check=True)
+    return ctypes.CDLL(path_so)

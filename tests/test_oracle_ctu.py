@@ -12,7 +12,13 @@
     xi0 = 1.152 for gamma = 5/3 (Sedov 1959), peak density below the strong
     shock limit (gamma+1)/(gamma-1);
   * ghost cells: periodic wrap, reflective mirror with negated normal
-    momentum, outflow copy, inflow state; corners filled x, then y, then z.
+    momentum, outflow copy, inflow state; corners filled x, then y, then z;
+  * the CFL time step (Eq. calc_dt_3D) equals hand-worked values on states
+    whose arithmetic is exact in binary (uniform, one cell and axis setting the
+    minimum, inactive axes ignored in 1D and 2D, floored pressure, real cells
+    only), and copies of the oracle with planted mistakes (gamma dropped, an
+    inactive axis counted, max for min, |v_d|^2 or |v| for |v_d|, ghosts
+    counted, no pressure floor) each fail at least one of those cases.
 """
 import numpy as np
 import pytest
@@ -259,3 +265,160 @@ def test_threaded_oracle_is_bit_identical_to_one_thread():
     oracle.set_threads(0)
     assert out[0][1] == out[1][1]
     assert np.array_equal(out[0][0], out[1][0])
+
+
+# ---- the CFL time step (Sec. 2.1, Eqs. calc_dt_1D / calc_dt_3D) --------------
+# dt = C0 * min over real cells and active axes of dx / (|v_d| + a), a =
+# sqrt(gamma p / rho) from the cell averages (pressure floored at 1e-20).  The
+# states below are written directly as conserved variables whose primitives,
+# sound speeds and quotients are exact in binary floating point (gamma = 2
+# makes gamma p / rho a product of exact numbers), so the expected dt is a
+# number worked out by hand, not the formula evaluated again.
+
+def _cons(shape, rho, m, E):
+    """Conserved state [5, nz, ny, nx] filled with (rho, m_x, m_y, m_z, E)."""
+    u = np.empty((5,) + tuple(shape))
+    for q, v in enumerate((rho, m[0], m[1], m[2], E)):
+        u[q] = v
+    return u
+
+
+def _dt_cases():
+    """(name, u, dx, gamma, bc, cfl, inflow, check) -- check(dt) is True for
+    the value the equation gives; every number in a comment is exact."""
+    cases = []
+    # uniform 3D, gamma 2: rho 4, v (0.5, -2, 1), p 8 -> a = sqrt(2*8/4) = 2;
+    # |v_d| + a = 2.5, 4, 3 -> the y axis sets dt = 0.4 * 0.5/4 = 0.05;
+    # m = (2, -8, 4), E = 8 + 4 (0.25 + 4 + 1)/2 = 18.5
+    cases.append(("uniform3d", _cons((4, 5, 6), 4.0, (2.0, -8.0, 4.0), 18.5), 0.5, 2.0, [P] * 6,
+                  0.4, None, lambda dt: dt == 0.05))
+    # one cell and one axis set the minimum: background rho 1, v 0, p 0.5 (a = 1,
+    # E = 0.5); cell (i4, j1, k2) moves at v_z = 3 (signal 4; E = 0.5 + 4.5 = 5),
+    # cell (i1, j3, k0) at v_x = -2.5 (signal 3.5; E = 0.5 + 3.125 = 3.625):
+    # dt = 0.8 * 0.25/4 = 0.05
+    u = _cons((4, 5, 6), 1.0, (0.0, 0.0, 0.0), 0.5)
+    u[3, 2, 1, 4] = 3.0; u[4, 2, 1, 4] = 5.0
+    u[1, 0, 3, 1] = -2.5; u[4, 0, 3, 1] = 3.625
+    cases.append(("one_cell_z", u, 0.25, 2.0, [P] * 6, 0.8, None, lambda dt: dt == 0.05))
+    # 1D box along x: the inactive y and z velocities (10, -20) do not count;
+    # rho 1, p 0.5 (a = 1), v_x 1 -> dt = 0.5 * 0.5/2 = 0.125; E = 0.5 + 501/2 = 251
+    cases.append(("inactive_1d", _cons((1, 1, 16), 1.0, (1.0, 10.0, -20.0), 251.0), 0.5, 2.0,
+                  [O, O, P, P, P, P], 0.5, None, lambda dt: dt == 0.125))
+    # 2D box (x, y): v_z = 50 does not count; v = (1, -1.5), a = 1 -> signal 2.5,
+    # dt = 0.5 * 0.5/2.5 = 0.1; E = 0.5 + (1 + 2.25 + 2500)/2 = 1252.125
+    cases.append(("inactive_2d", _cons((1, 6, 8), 1.0, (1.0, -1.5, 50.0), 1252.125), 0.5, 2.0,
+                  [P] * 6, 0.5, None, lambda dt: dt == 0.1))
+    # a cell with no internal energy (E = rho v^2/2 exactly: p = 0, floored to
+    # 1e-20, a = sqrt(2e-20) = 1.414e-10) at v_x = 4 sets the minimum: dt =
+    # 0.5 * 0.5/(4 + 1.414e-10) = 0.0625 (1 - 3.54e-11), strictly below the
+    # 0.0625 that a zero sound speed would give; background as above
+    u = _cons((4, 4, 4), 1.0, (0.0, 0.0, 0.0), 0.5)
+    u[1, 1, 2, 3] = 4.0; u[4, 1, 2, 3] = 8.0
+    cases.append(("floored_p", u, 0.5, 2.0, [P] * 6, 0.5, None,
+                  lambda dt: 0.0625 * (1 - 3.6e-11) < dt < 0.0625 * (1 - 3.5e-11)))
+    # a cell whose total energy is below its kinetic energy (E = 7 < 8): the
+    # floored pressure gives it the same tiny sound speed, so it still sets dt
+    u = _cons((4, 4, 4), 1.0, (0.0, 0.0, 0.0), 0.5)
+    u[2, 3, 0, 1] = -4.0; u[4, 3, 0, 1] = 7.0
+    cases.append(("negative_p", u, 0.5, 2.0, [P] * 6, 0.5, None,
+                  lambda dt: 0.0625 * (1 - 3.6e-11) < dt < 0.0625 * (1 - 3.5e-11)))
+    # gamma 5/3 (not exact in binary): rho 1, p 0.6 -> a = 1, v = (0.25, 0, 0),
+    # signal 1.25, dt = 0.3 * (1/32)/1.25 = 0.0075 to a few ulp
+    E = 0.6 / (2.0 / 3.0) + 0.5 * 0.0625
+    cases.append(("gamma53", _cons((4, 4, 4), 1.0, (0.25, 0.0, 0.0), E), 1.0 / 32, 5.0 / 3.0,
+                  [P] * 6, 0.3, None, lambda dt: abs(dt / 0.0075 - 1) < 1e-15))
+    # only real cells count: an x- inflow face at v = 50 fills the ghosts; after
+    # a step of 1e-15 (which moves the real cells' pressure by ~1e-10 relative)
+    # the real cells still give rho 1, v_x 1, a 1: dt = 0.5 * 0.5/2 = 0.125
+    cases.append(("ghosts_excluded", _cons((1, 1, 16), 1.0, (1.0, 0.0, 0.0), 1.0), 0.5, 2.0,
+                  [I_, O, P, P, P, P], 0.5, {0: (1.0, 50.0, 0.0, 0.0, 0.5)},
+                  lambda dt: abs(dt / 0.125 - 1) < 1e-9))
+    return cases
+
+
+def _bind(L):
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.oracle_init.restype = ctypes.c_void_p
+    L.oracle_init.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [ctypes.POINTER(ctypes.c_int)]
+    L.oracle_free.argtypes = [ctypes.c_void_p]
+    L.oracle_set_state.argtypes = [ctypes.c_void_p, dp]
+    L.oracle_set_inflow.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
+    L.oracle_compute_dt.restype = ctypes.c_double
+    L.oracle_compute_dt.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    L.oracle_step_dt.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    return L
+
+
+def _dt_with(L, u, dx, gamma, bc, cfl, inflow):
+    """dt of the case through the oracle library L (the real one or a mutant)."""
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    u = np.ascontiguousarray(u)
+    _, nz, ny, nx = u.shape
+    h = L.oracle_init(nx, ny, nz, dx, gamma, (ctypes.c_int * 6)(*bc))
+    assert h
+    try:
+        L.oracle_set_state(h, u.ctypes.data_as(dp))
+        if inflow:
+            for face, prim in inflow.items():
+                pa = np.asarray(prim, dtype=np.float64)
+                L.oracle_set_inflow(h, face, pa.ctypes.data_as(dp))
+            L.oracle_step_dt(h, 1e-15)
+        return L.oracle_compute_dt(h, cfl)
+    finally:
+        L.oracle_free(h)
+
+
+@pytest.mark.parametrize("case", _dt_cases(), ids=lambda c: c[0])
+def test_cfl_dt_hand_computed(case):
+    """The oracle's dt equals the hand-worked value of Eq. calc_dt_3D."""
+    name, u, dx, gamma, bc, cfl, inflow, check = case
+    dt = _dt_with(_bind(oracle.lib()), u, dx, gamma, bc, cfl, inflow)
+    assert check(dt), (name, repr(dt))
+
+
+_CDT = "R compute_dt_min(const Grid<R>& G) {"
+_C2P = "void cons_to_prim(const R U[5], const Gas& g, R W[5]) {"
+_DT_MUTANTS = {
+    # the sound speed without gamma
+    "gamma_dropped": [(_CDT, "sqrt(R(g.gamma) * W[4] / W[0])", "sqrt(W[4] / W[0])")],
+    # an axis with one cell counted
+    "inactive_axis_counted": [(_CDT, "if (G.n[d] <= 1) continue;", "")],
+    # the largest quotient kept instead of the smallest
+    "max_for_min": [(_CDT, "std::numeric_limits<double>::infinity()", "0.0"),
+                    (_CDT, "if (t < bestR)", "if (t > bestR)")],
+    # |v_d|^2 in place of |v_d|
+    "v_squared": [(_CDT, "fabs(W[1 + d])", "(W[1 + d] * W[1 + d])")],
+    # the speed |v| in place of the axis component |v_d|
+    "speed_not_component": [(_CDT, "fabs(W[1 + d])", "sqrt(W[1] * W[1] + W[2] * W[2] + W[3] * W[3])")],
+    # ghost cells counted
+    "ghosts_counted": [(_CDT, "for (int k = G.gh[2]; k < G.gh[2] + G.n[2]; ++k)",
+                        "for (int k = 0; k < G.N[2]; ++k)"),
+                       (_CDT, "for (int j = G.gh[1]; j < G.gh[1] + G.n[1]; ++j)",
+                        "for (int j = 0; j < G.N[1]; ++j)"),
+                       (_CDT, "for (int i = G.gh[0]; i < G.gh[0] + G.n[0]; ++i)",
+                        "for (int i = 0; i < G.N[0]; ++i)")],
+    # no pressure floor in the cell primitives
+    "no_pressure_floor": [(_C2P, "W[4] = mx(p, R(P_FLOOR));", "W[4] = p;")],
+}
+
+
+def test_cfl_dt_pins_catch_planted_mistakes():
+    """Each plausible mistake in the oracle's dt, planted in a copy of the
+    oracle source, fails at least one hand-computed case: gamma dropped from the
+    sound speed, an inactive axis counted, the maximum taken for the minimum,
+    |v_d|^2 for |v_d|, the speed |v| for the component |v_d|, ghost cells
+    counted, the pressure floor left out."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from tests.helpers import build_oracle_mutant
+    with ThreadPoolExecutor(max_workers=len(_DT_MUTANTS)) as ex:
+        libs = dict(zip(_DT_MUTANTS, ex.map(lambda kv: build_oracle_mutant(*kv),
+                                              _DT_MUTANTS.items())))
+    cases = _dt_cases()
+    for tag, L in libs.items():
+        _bind(L)
+        failed = [c[0] for c in cases if not c[7](_dt_with(_bind(L), *c[1:7]))]
+        assert failed, "planted mistake %r passes every dt pin" % tag
+        print("%s fails %s" % (tag, failed))

@@ -325,8 +325,13 @@ void hydro_batch_free(hydro_batch_t h);
  * library holds until exit, so states of more than 2^24 cells are rejected with
  * HYDRO_EINVAL.  Calls share that array: calls overlapping on the GPU race.  The
  * first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * and should come before any stream capture.  Returns HYDRO_OK, HYDRO_EINVAL or
- * HYDRO_ECUDA. */
+ * and should come before any stream capture; the address is kept for the life of
+ * the process, so the entry point must not be used across a cudaDeviceReset.
+ * The state is not checked on the host: a cell with rho <= 0, or a NaN in any
+ * cell, gives *dt_out = NaN (the call still returns HYDRO_OK), so test the
+ * result; the handle path rejects such states in hydro_set_state instead.  The
+ * result equals hydro_compute_dt's in HYDRO_FP64_STRICT bit for bit and agrees
+ * with HYDRO_FP64's to a few ulp.  Returns HYDRO_OK, HYDRO_EINVAL or HYDRO_ECUDA. */
 int hydro_compute_dt_noalloc(const double* u, int nx, int ny, int nz, double dx, double gamma,
                              double cfl, double* dt_out, void* stream);
 

@@ -18,11 +18,18 @@
 //
 // Host code cannot use the array's name as a device address; the first call on
 // each device looks the address up with cudaGetSymbolAddress (with that device
-// current) and caches it.  That first call should come before any stream
-// capture.
+// current) and caches it for the life of the process.  That first call should
+// come before any stream capture, and the entry point must not be used across
+// a cudaDeviceReset (the module, and with it the array, may move).
 //
-// Built with --fmad=false: the per-cell arithmetic is the reference order of
-// the library's primitive kernel, so the result equals hydro_compute_dt's.
+// A cell whose density is not positive, or a NaN anywhere in a cell, makes the
+// result NaN (the maxima below keep a NaN once they meet one), so such a state
+// cannot silently yield a dt from its other cells.
+//
+// Built with --fmad=false: the per-cell arithmetic is the operation order of
+// the library's strict primitive kernel, so the result equals hydro_compute_dt's
+// in HYDRO_FP64_STRICT bit for bit; HYDRO_FP64 forms 1/rho and 1/a by Newton
+// iteration with fused multiply-adds and agrees to a few ulp.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -41,8 +48,14 @@ static __device__ __align__(256) double g_dt_partials[kMaxBlocks];
 std::mutex g_mutex;
 double* g_partials_addr[kMaxDevices] = {nullptr};
 
+// maximum that keeps a NaN: once v is NaN it stays NaN, and a NaN x replaces v
+__device__ __forceinline__ double max_keep_nan(double v, double x) {
+  return (x > v || x != x) ? x : v;
+}
+
 // per block: max over its cells and active axes of |v_d| + a (Eq. calc_dt_3D;
-// min dx/(|v_d| + a) = dx / max(|v_d| + a) exactly)
+// min dx/(|v_d| + a) = dx / max(|v_d| + a) exactly); NaN for a cell with
+// rho <= 0 or a NaN field
 __global__ void __launch_bounds__(kThreads)
 k_dt_partials(const double* __restrict__ u, long long nreal, int active, double gamma, double gm1,
               double* __restrict__ partials) {
@@ -52,41 +65,44 @@ k_dt_partials(const double* __restrict__ u, long long nreal, int active, double 
   if (t < nreal) {
     const double d = u[t];
     const double vel[3] = {u[nreal + t] / d, u[2 * nreal + t] / d, u[3 * nreal + t] / d};
+    // the floor keeps a NaN pressure NaN ((NaN < floor) is false)
     const double p = hydro::tmax(
         gm1 * (u[4 * nreal + t] - 0.5 * d * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2])),
         hydro::kPFloor);
     const double a = sqrt(gamma * p / d);
 #pragma unroll
     for (int k = 0; k < 3; ++k)
-      if (active & (1 << k)) v = hydro::tmax(v, fabs(vel[k]) + a);
+      if (active & (1 << k)) v = max_keep_nan(v, fabs(vel[k]) + a);
+    if (!(d > 0.0)) v = __longlong_as_double(0x7ff8000000000000ll);  // quiet NaN
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = hydro::tmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = max_keep_nan(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
     v = threadIdx.x < kThreads / 32 ? warp_max[threadIdx.x] : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = hydro::tmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = max_keep_nan(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (threadIdx.x == 0) partials[blockIdx.x] = v;
   }
 }
 
-// one block: maximum of the partials, then dt = cfl * (dx / max)
+// one block: maximum of the partials, then dt = cfl * (dx / max) (NaN when a
+// partial is NaN)
 __global__ void __launch_bounds__(1024)
 k_dt_finish(const double* __restrict__ partials, int nblocks, double dx, double cfl,
             double* __restrict__ dt_out) {
   __shared__ double warp_max[32];
   double v = 0.0;
-  for (int i = threadIdx.x; i < nblocks; i += 1024) v = hydro::tmax(v, partials[i]);
+  for (int i = threadIdx.x; i < nblocks; i += 1024) v = max_keep_nan(v, partials[i]);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = hydro::tmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = max_keep_nan(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) warp_max[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
     v = warp_max[threadIdx.x];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = hydro::tmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = max_keep_nan(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (threadIdx.x == 0) dt_out[0] = cfl * (dx / v);
   }
 }

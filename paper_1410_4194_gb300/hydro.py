@@ -385,10 +385,36 @@ def ppmc(w, dtdx, gamma, WsL, WsR):
         raise HydroError(rc, "ppmc")
 
 
+def _check_device_f64(name, t, ndim=None, lead=None):
+    """Raise ValueError unless t is a contiguous float64 CUDA tensor on the
+    current device (checked before any pointer reaches a kernel)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError("%s must be a torch tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float64:
+        raise ValueError("%s must be float64, got %s" % (name, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if ndim is not None and (t.dim() != ndim or (lead is not None and t.shape[0] != lead)):
+        raise ValueError("%s must have shape [%s, ...] with %d dimensions, got %s"
+                         % (name, lead, ndim, tuple(t.shape)))
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError("%s is on %s, not on the current device cuda:%d"
+                         % (name, t.device, torch.cuda.current_device()))
+
+
 def compute_dt_noalloc(u, dx, gamma, cfl, dt_out):
     """CFL dt of a device state u [5, nz, ny, nx] (torch CUDA float64) into the
     one-element CUDA tensor dt_out, without any device allocation; returns the
-    C-ABI status code (0 on success)."""
+    C-ABI status code (0 on success).  A cell with rho <= 0 or a NaN gives a
+    NaN dt.  Raises ValueError, before anything is launched, unless both are
+    contiguous float64 tensors on the current CUDA device and u has 5 planes."""
+    _check_device_f64("u", u, ndim=4, lead=5)
+    _check_device_f64("dt_out", dt_out)
+    if dt_out.numel() < 1:
+        raise ValueError("dt_out must hold at least one element")
     L = load()
     _, nz, ny, nx = u.shape
     return L.hydro_compute_dt_noalloc(ctypes.c_void_p(u.data_ptr()), int(nx), int(ny), int(nz),

@@ -77,3 +77,20 @@ def test_index_division_matches_integer_division_without_gpu(lib):
     hashed numerators below 2^31) finds no mismatch."""
     lib.hydro_check_fastdiv.restype = ctypes.c_longlong
     assert lib.hydro_check_fastdiv() == 0
+
+
+def test_noalloc_binding_rejects_bad_tensors_before_any_launch():
+    """compute_dt_noalloc checks its tensors on the host: a CPU tensor, a
+    float32 tensor, a non-tensor or a wrong shape raises ValueError before any
+    pointer reaches the library (no GPU needed)."""
+    torch = pytest.importorskip("torch")
+    import numpy as np
+
+    from paper_1410_4194_gb300 import hydro
+    dt = torch.zeros(1, dtype=torch.float64)
+    for bad in (torch.zeros((5, 2, 2, 2), dtype=torch.float64),   # on the CPU
+                torch.zeros((5, 2, 2, 2), dtype=torch.float32),   # float32 (and CPU)
+                np.zeros((5, 2, 2, 2)),                            # not a tensor
+                torch.zeros((4, 2, 2, 2), dtype=torch.float64)):   # 4 planes
+        with pytest.raises(ValueError):
+            hydro.compute_dt_noalloc(bad, 0.1, 1.4, 0.3, dt)

@@ -109,6 +109,9 @@ __device__ __forceinline__ float xsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double xabs(double x) { return fabs(x); }
 __device__ __forceinline__ float xabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double xfma(double a, double b, double c) { return fma(a, b, c); }
+// a rounded product that contraction cannot fuse into a following add
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float xfma(float a, float b, float c) { return fmaf(a, b, c); }
 
 // min/max with the tie and signed-zero behaviour of "(b < a) ? b : a"
@@ -1103,7 +1106,13 @@ __device__ __forceinline__ void riemann_roe(const T UL[5], const T UR[5], const 
     const T HL = (UL[4] + WL[4]) * inv_dL;
     const T HR = (UR[4] + WR[4]) * inv_dR;
     const T ir = nr_rcp(sL + sR);
-    u = (sL * WL[1] + sR * WR[1]) * ir;
+    // the normal velocity from two rounded products, not one contracted
+    // multiply-add: mirror-image states (a reflecting wall) then give u~ = 0
+    // exactly, as in the printed formula's arithmetic, and the HLLE fallback's
+    // wave bounds stay at the wall (a contracted form leaves the product's
+    // rounding error, ~1e-18, which turns the symmetric wall flux into an
+    // upwind one)
+    u = (mul_rn(sL, WL[1]) + mul_rn(sR, WR[1])) * ir;
     v = (sL * WL[2] + sR * WR[2]) * ir;
     w = (sL * WL[3] + sR * WR[3]) * ir;
     H = (sL * HL + sR * HR) * ir;

@@ -2,7 +2,7 @@
 """Throughput of the CTU + PPMC + exact-Riemann step on GB300, in cell-updates/s.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload sedov256]
-                    [--precision fp64|mixed] [--impl ours|reference]
+                    [--precision fp64|mixed|strict] [--impl ours|reference] [--no-extra]
 
 One step = one full CTU step (ghost remap, dt minimum, three PPMC sweeps, six
 sets of exact Riemann solves, transverse half-step, conserved update) of every
@@ -10,6 +10,13 @@ real cell.  ``value`` = real cells x steps x ranks / max-over-ranks wall time of
 the K timed steps (CUDA events on the grid's stream, barrier + synchronize on
 both sides), state resident in HBM.  ``e2e`` = the same through the public API
 with the state copied host->device before and device->host after every step.
+
+The default run (Sedov 256^3, FP64, one GPU) adds to the same JSON line one
+record per other form the metric names, each timed the same way with its own
+clock samples: ``mixed`` and ``fp64_strict`` (Sedov 256^3), ``batched96_fp64``
+and ``batched96_mixed`` (96 uneven grids), ``turbulence512_fp64/_mixed`` and
+``shock_cloud_fp64/_mixed``; every mixed record carries its L1 difference to
+the FP64 path from the same initial state after the same steps.
 
 Under torchrun each rank advances its own independent replica of the workload
 (the method's grids share nothing, so there is no collective on the data path:
@@ -152,6 +159,13 @@ def workload(name):
     elif name == "turbulence":
         w = W.turbulence(512)
         w["desc"] = "3D supersonic turbulence, 512^3 periodic, rms Mach 5, CFL 0.3"
+    elif name.startswith("turbulence"):
+        # the same recipe on a smaller box, shells scaled with the box so that
+        # the shortest wavelength keeps its 32 cells
+        n = int(name[10:])
+        w = W.turbulence(n, kmax=max(1, 16 * n // 512))
+        w["desc"] = ("3D supersonic turbulence, %d^3 periodic, rms Mach 5, shells 1..%d, CFL 0.3"
+                     % (n, max(1, 16 * n // 512)))
     elif name.startswith("noh"):
         n = int(name[3:] or 200)
         w = W.noh(n)
@@ -257,6 +271,8 @@ def flops_table(key, recon="ppmc", solver="exact"):
     Riemann solver (the other methods are counted on the Sedov sample)."""
     if key.startswith("sedov"):
         key = "sedov"
+    elif key.startswith("turbulence"):
+        key = "turbulence"
     elif key.startswith("batched"):
         key = "batched"
     elif key.startswith("noh"):
@@ -307,6 +323,419 @@ def run_cpu_baseline(wname, max_steps, cfl=0.3, min_seconds=10.0):
             "sample": sample % steps, "seconds": el}
 
 
+PRECISIONS = {"fp64": 0, "mixed": 1, "strict": 2}  # HYDRO_FP64, HYDRO_MIXED, HYDRO_FP64_STRICT
+DTYPES = {"fp64": "f64", "mixed": "f32+f64", "strict": "f64"}
+
+
+def timed(stream, fn, ws, local):
+    """Run fn() between CUDA events on `stream` with a barrier and a
+    synchronize on both sides, nvidia-smi sampling the clocks meanwhile;
+    returns (max-over-ranks ms, clocks)."""
+    import torch
+    import torch.distributed as dist
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    return max_over_ranks(ev0.elapsed_time(ev1), ws), clocks
+
+
+def fp64_peak_live(hydro):
+    """Measured FP64 throughput of this device (flop/s), or None."""
+    try:
+        return hydro.probe_fp64_rate()
+    except Exception:  # reported as unavailable, the nominal peak stands
+        return None
+
+
+def single_roofline(stages, precision, wkey, recon, solver, active, block_size, fp64_live,
+                    sm_mhz):
+    """Roofline of the dominant kernel of a single-grid run from the per-stage
+    CUDA-event split: FP64 flops (FP64 and strict modes) or HBM bytes (mixed)."""
+    dom = max((k for k in stages if stages[k][1] > 0), key=lambda k: stages[k][0])
+    dms, dl, dunits = stages[dom]
+    units_per_launch = dunits / dl
+    avg_ms = dms / dl
+    # the dominant stage's kernel: the reconstruction stage runs the selected
+    # reconstruction's kernel, the Riemann stages the Roe kernels with roe
+    if precision == "mixed":
+        kname = "kb_%s_mixed" % dom
+    elif precision == "strict":
+        kname = "k_%s (strict)" % dom
+    elif dom == "ppmc":
+        kname = "kb_" + recon
+    elif dom in ("riemann1", "riemann2") and solver == "roe":
+        kname = "kb_%s_roe" % dom
+    else:
+        kname = "kb_" + dom
+    # captured traffic applies to the kernels captured (PPMC + exact solver, 3D
+    # grids: a 1D or 2D face carries no or fewer transverse terms)
+    traffic = None
+    tinfo = NCU_TRAFFIC.get((precision, dom))
+    if (tinfo and active == 3 and recon == "ppmc" and solver == "exact"
+            and tinfo["digest"] == source_digest(tinfo["sources"])
+            and tinfo["bs"] == block_size):
+        traffic = tinfo["bytes_per_unit"] * units_per_launch
+    bytes_per_unit = ALGORITHMIC_BYTES["mixed" if precision == "mixed" else "fp64"][dom]
+    if precision != "mixed":
+        # FP64 kernels: bound by the FP64 pipe (DRAM a few % busy)
+        table, tkey = flops_table(wkey, recon, solver)
+        per_unit = table[dom]
+        achieved = per_unit * units_per_launch / (avg_ms / 1e3)
+        r = {"bound": "alu", "achieved": achieved, "peak": FP64_FLOPS_PEAK,
+             "unit": "FP64 FLOP/s", "frac": achieved / FP64_FLOPS_PEAK,
+             "traffic": traffic, "kernel": kname, "flops_per_unit": per_unit,
+             "units_per_launch": units_per_launch, "avg_launch_ms": avg_ms,
+             "flops_source": "algorithmic FP64 flops per unit (oracle/count_ops.py, %s)" % tkey,
+             "peak_source": PEAK_SOURCE, "bytes_per_unit_algorithmic": bytes_per_unit}
+        if fp64_live:
+            r["peak_measured"] = fp64_live
+            r["frac_of_measured"] = achieved / fp64_live
+            r["peak_measured_source"] = (
+                "FP64 FMA throughput measured live on this GPU (hydro_probe_fp64_rate: "
+                "independent FMA chains on every SM, 2 flop/FMA)"
+                + (", %.2f FMA/clk/SM at the %.0f MHz median SM clock of the timed region"
+                   % (fp64_live / 2 / 152 / (sm_mhz * 1e6), sm_mhz) if sm_mhz else ""))
+        return r
+    # mixed kernels: float arithmetic on a pipe 64x the FP64 rate, streaming
+    # float planes: the roofline that bounds them is HBM bandwidth
+    peak, psrc = hbm_peak_gbs()
+    achieved = bytes_per_unit * units_per_launch / (avg_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+            "bytes_per_unit_algorithmic": bytes_per_unit,
+            "units_per_launch": units_per_launch, "avg_launch_ms": avg_ms,
+            "bytes_source": "every plane the kernel reads or writes, once per unit",
+            "peak_source": "%s HBM copy bandwidth (MEASURED_PEAKS.json)" % psrc
+                           if psrc == "measured" else "fallback HBM bandwidth",
+            "fp64_flops_per_unit": mixed_fp64_flops(active).get(dom, 0)}
+
+
+def measure_single(w, precision, steps, warmup, cfl, ws, local, recon="ppmc", solver="exact",
+                   e2e=True, device_loop=True, keep_state=False, fp64_live=None):
+    """Time `steps` device-resident CTU steps of one grid after `warmup` steps;
+    returns the record (value, ms_per_step, clocks, roofline, stages, e2e,
+    device_loop, gpu_launches) and, with keep_state, the device state right
+    after the timed steps (warmup + steps steps from the initial state)."""
+    import torch
+    from paper_1410_4194_gb300 import hydro
+    _, nz, ny, nx = w["u"].shape
+    nreal = nx * ny * nz
+    prec = PRECISIONS[precision]
+    stream = torch.cuda.current_stream()
+    g = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], precision=prec, stream=stream,
+                   recon=RECON_CODES[recon], solver=SOLVER_CODES[solver])
+    for face, prim in (w.get("inflow") or {}).items():
+        g.set_inflow(face, prim)
+    u_host = torch.from_numpy(w["u"]).pin_memory() if e2e else None
+    g.set_state(w["u"])
+    for _ in range(warmup):
+        g.step(cfl)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K device-resident steps ------------------------------
+    g.profile(True)
+
+    def run_steps():
+        for _ in range(steps):
+            g.step(cfl)
+    ms, clocks = timed(stream, run_steps, ws, local)
+    stages, launches_total = g.profile_read()
+    g.profile(False)
+    rec = {"value": replicas_value(nreal, steps, ws, ms), "unit": UNIT, "steps": steps,
+           "warmup": warmup, "ms_per_step": ms / steps, "precision": precision,
+           "dtype": DTYPES[precision], "gpu_launches": launches_total, "clocks": clocks}
+    state = None
+    if keep_state:
+        state = torch.empty((5, nz, ny, nx), dtype=torch.float64, device="cuda")
+        g.get_state(state)
+
+    # ---- the same K steps looped on the device (hydro_advance: one CUDA graph
+    # with a WHILE node, no host round trip and no tracing events per step) ----
+    if device_loop:
+        g.advance(cfl, math.inf, 0)  # captures the loop graph outside the timed region
+        box = {}
+
+        def run_loop():
+            box["taken"] = g.advance(cfl, math.inf, steps)
+        ms_dev, _ = timed(stream, run_loop, ws, local)
+        rec["device_loop"] = {"value": replicas_value(nreal, box["taken"], ws, ms_dev),
+                              "unit": UNIT, "ms_per_step": ms_dev / max(box["taken"], 1),
+                              "steps": box["taken"]}
+
+    # ---- end to end through the public API with host buffers ----------------
+    # Every step uploads its input state from pinned host memory, steps, and
+    # downloads the resulting state.  Steps alternate between two grids on two
+    # streams (the asynchronous API), so one grid's copies overlap the other's
+    # step, as a pipeline of independent problems would run.
+    rec["e2e"] = None
+    if e2e:
+        import torch.distributed as dist
+        out_host = [torch.empty_like(u_host).pin_memory() for _ in range(2)]
+        stream2 = torch.cuda.Stream()
+        g2 = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], precision=prec,
+                        stream=stream2, recon=RECON_CODES[recon], solver=SOLVER_CODES[solver])
+        for face, prim in (w.get("inflow") or {}).items():
+            g2.set_inflow(face, prim)
+        pipe = [g, g2]
+
+        def e2e_step(k):
+            gk = pipe[k % 2]
+            gk.set_state_async(u_host)
+            gk.step_async(cfl)
+            gk.get_state_async(out_host[k % 2])
+
+        e2e_step(0)
+        e2e_step(1)
+        g.sync()
+        g2.sync()
+        ke = max(2, min(steps, 10))
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        eb = torch.cuda.Event()
+        e0.record(stream)
+        stream2.wait_event(e0)
+        for k in range(ke):
+            e2e_step(k)
+        eb.record(stream2)
+        stream.wait_event(eb)
+        e1.record(stream)
+        g.sync()
+        g2.sync()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        te = max_over_ranks(e0.elapsed_time(e1), ws)
+        rec["e2e"] = {"value": replicas_value(nreal, ke, ws, te), "unit": UNIT,
+                      "h2d_bytes_per_step": int(u_host.numel() * 8),
+                      "d2h_bytes_per_step": int(out_host[0].numel() * 8), "steps": ke,
+                      "host_wall_s": wall,
+                      "pipeline": "2 grids on 2 streams: one grid's copies overlap the "
+                                  "other's step"}
+        g2.close()
+    active = sum(1 for n in (nx, ny, nz) if n > 1)
+    rec["roofline"] = single_roofline(stages, precision, w["key"], recon, solver, active,
+                                      g.block_size(), fp64_live, clocks.get("sm_mhz"))
+    rec["stages"] = {k: {"ms": v[0], "launches": v[1], "share": v[0] / max(ms, 1e-9)}
+                     for k, v in stages.items()}
+    rec["hbm"] = hbm_report(rec["value"] / ws, rec["roofline"]["traffic"],
+                            rec["roofline"]["avg_launch_ms"])
+    if precision == "mixed":
+        rec["bytes_per_cell_update_algorithmic"] = mixed_bytes_per_cell_update(active)
+    g.close()
+    return rec, state
+
+
+def l1_rel(a, ref):
+    """Relative L1 difference per field (rho, three momenta against their
+    group's scale, E) of two states [5, ...] (torch or numpy)."""
+    d = [float(abs(a[q] - ref[q]).sum()) for q in range(5)]
+    s = [float(abs(ref[q]).sum()) for q in range(5)]
+    mom = max(s[1:4])
+    den = [s[0], mom, mom, mom, s[4]]
+    return [x / y if y > 0 else 0.0 for x, y in zip(d, den)]
+
+
+def measure_batch(grids, desc, precision, steps, warmup, cfl, ws, local, e2e=True,
+                  keep_states=False):
+    """Config 5: a batch of independent grids advanced by hydro_batch_step (one
+    CUDA-graph launch a call; here one step a call so that the timed region is
+    exactly K steps).  Returns the record and, with keep_states, the host states
+    after warmup + steps steps."""
+    import torch
+    import torch.distributed as dist
+    from paper_1410_4194_gb300 import hydro
+    ncells = sum(int(np.prod(g["u"].shape[1:])) for g in grids)
+    prec = PRECISIONS[precision]
+    stream = torch.cuda.Stream()
+    b = hydro.Batch(grids, precision=prec)
+    b.set_stream(stream)
+    bs, order, tune_ms = b.autotune(use_cache=True)
+    for _ in range(warmup):
+        b.step(cfl, nsteps=1)
+    torch.cuda.synchronize()
+
+    def run_steps():
+        for _ in range(steps):
+            b.step(cfl, nsteps=1)
+    ms, clocks = timed(stream, run_steps, ws, local)
+    value = replicas_value(ncells, steps, ws, ms)
+    states = [b.get_state(i) for i in range(len(grids))] if keep_states else None
+    # end to end: every step uploads every grid's state from pinned host memory,
+    # steps and downloads the states; steps alternate between two batches on two
+    # streams (the asynchronous API), each synced while the other's work is
+    # queued, so one batch's copies overlap the other's step
+    e2e_rec = None
+    if e2e:
+        hosts = [torch.from_numpy(g["u"]).pin_memory() for g in grids]
+        outs = [[torch.empty_like(x).pin_memory() for x in hosts] for _ in range(2)]
+        stream2 = torch.cuda.Stream()
+        b2 = hydro.Batch(grids, precision=prec)
+        b2.set_stream(stream2)
+        b2.autotune(use_cache=True)
+        pipe = [b, b2]
+
+        def e2e_step(k):
+            bk = pipe[k % 2]
+            for i, x in enumerate(hosts):
+                bk.set_state_async(i, x)
+            bk.step_async(cfl, nsteps=1)
+            for i, x in enumerate(outs[k % 2]):
+                bk.get_state_async(i, x)
+
+        e2e_step(0)
+        e2e_step(1)
+        b.sync()
+        b2.sync()
+        ke = max(2, min(steps, 6))
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        eb = torch.cuda.Event()
+        e0.record(stream)
+        stream2.wait_event(e0)
+        for k in range(ke):
+            e2e_step(k)
+            if k >= 1:
+                pipe[(k - 1) % 2].sync()
+        eb.record(stream2)
+        stream.wait_event(eb)
+        e1.record(stream)
+        pipe[(ke - 1) % 2].sync()
+        torch.cuda.synchronize()
+        te = max_over_ranks(e0.elapsed_time(e1), ws)
+        e2e_rec = {"value": replicas_value(ncells, ke, ws, te), "unit": UNIT,
+                   "h2d_bytes_per_step": int(sum(x.numel() * 8 for x in hosts)),
+                   "d2h_bytes_per_step": int(sum(x.numel() * 8 for x in outs[0])), "steps": ke,
+                   "pipeline": "2 batches on 2 streams: one batch's copies overlap the "
+                               "other's step"}
+        b2.close()
+    b.close()
+    # kernels of one step of the graph (3D grids): primitives + dt, update, and
+    # per axis the slope pass (none in mixed precision, whose PPMC kernel forms
+    # its own slopes), reconstruction and the two Riemann sets
+    slope_pass = 0 if precision == "mixed" else 1
+    launches_per_step = 3 + 3 * (3 + slope_pass)
+    # step-level roofline (the graph's kernels are not timed one by one):
+    # FP64 flops of a cell update times the cell-update rate
+    if precision == "fp64":
+        pu = ALGORITHMIC_FLOPS["batched"]
+        per_cell = (pu["prims"] + 3 * (pu["slopes"] + pu["ppmc"] + pu["riemann1"]
+                                       + pu["riemann2"]) + pu["update"])
+        achieved = per_cell * value / ws
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_FLOPS_PEAK,
+                    "unit": "FP64 FLOP/s", "frac": achieved / FP64_FLOPS_PEAK, "traffic": None,
+                    "kernel": "whole step (graph)", "flops_per_cell_update": per_cell,
+                    "flops_source": "algorithmic FP64 flops per cell update "
+                                    "(oracle/count_ops.py, Sedov sample)",
+                    "peak_source": PEAK_SOURCE}
+    else:
+        per_cell = mixed_bytes_per_cell_update(3)
+        achieved = per_cell * value / ws / 1e9
+        peak, psrc = hbm_peak_gbs()
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "whole step (graph)",
+                    "bytes_per_cell_update": per_cell,
+                    "bytes_source": "algorithmic HBM bytes of the mixed-precision kernels per "
+                                    "cell update",
+                    "peak_source": "%s HBM copy bandwidth" % psrc}
+    rec = {"value": value, "unit": UNIT, "steps": steps, "warmup": warmup,
+           "ms_per_step": ms / steps, "precision": precision, "dtype": DTYPES[precision],
+           "config": {"workload": desc, "cells": ncells, "grids": len(grids),
+                      "precision": precision, "schedule": {"block": bs, "order": order},
+                      "l2": "inputs larger than L2 (states %.2f GB)" % (ncells * 40 / 1e9)},
+           "e2e": e2e_rec, "gpu_launches": launches_per_step * steps, "clocks": clocks,
+           "hbm": hbm_report(value / ws), "roofline": roofline}
+    return rec, states
+
+
+def extra_records(args, ws, local, main_state, fp64_live):
+    """The other forms the metric names, each measured on this GPU right after
+    the headline line and carried in the same JSON line: mixed precision and
+    the strict FP64 mode on the same Sedov 256^3 workload, the 96-grid batch in
+    FP64 and mixed precision, and the FP64 and mixed paths on the two harder
+    workloads (Mach-5 turbulence 512^3, Mach-10 shock-cloud 512x256x256), each
+    with the L1 difference of mixed to FP64 from the same initial state after
+    the same steps.  Fewer steps on the large workloads (stated per record)."""
+    import torch
+    out = {}
+    wu = 3 if args.warmup >= 3 else args.warmup
+    sed = workload("sedov256")
+    # mixed, same steps as the headline: L1 against the headline's FP64 state
+    rec, st = measure_single(sed, "mixed", args.steps, args.warmup, args.cfl, ws, local,
+                             keep_state=True)
+    rec["config"] = single_config("sedov256", "mixed", ws)
+    rec["l1_vs_fp64"] = {"steps": args.warmup + args.steps,
+                         "fields": ["rho", "mx", "my", "mz", "E"],
+                         "l1_rel": l1_rel(st, main_state),
+                         "reference": "HYDRO_FP64 GPU path (the headline run) from the same "
+                                      "initial state after the same steps"}
+    out["mixed"] = rec
+    del st
+    # strict FP64: the printed formulas in the oracle's operation order
+    ks = min(args.steps, 5)
+    rec, _ = measure_single(sed, "strict", ks, wu, args.cfl, ws, local, e2e=False,
+                            device_loop=False, fp64_live=fp64_live)
+    rec["config"] = single_config("sedov256", "strict", ws)
+    out["fp64_strict"] = rec
+    del sed
+    torch.cuda.empty_cache()
+    # the 96-grid batch (config 5)
+    bw = workload("batched96")
+    kb = min(args.steps, 10)
+    rec64, s64 = measure_batch(bw["grids"], bw["desc"], "fp64", kb, wu, args.cfl, ws, local,
+                               keep_states=True)
+    out["batched96_fp64"] = rec64
+    recm, sm = measure_batch(bw["grids"], bw["desc"], "mixed", kb, wu, args.cfl, ws, local,
+                             keep_states=True)
+    per_grid = np.array([l1_rel(a, c) for a, c in zip(sm, s64)])
+    worst = int(np.argmax(per_grid[:, 0]))
+    recm["l1_vs_fp64"] = {"steps": wu + kb, "fields": ["rho", "mx", "my", "mz", "E"],
+                          "per_grid_max": per_grid.max(axis=0).tolist(),
+                          "per_grid_median": np.median(per_grid, axis=0).tolist(),
+                          "worst_grid_rho": worst,
+                          "reference": "HYDRO_FP64 batch from the same initial states after "
+                                       "the same steps"}
+    out["batched96_mixed"] = recm
+    del bw, s64, sm
+    # the two large workloads, FP64 and mixed from the same initial state
+    for name in ("turbulence", "shock_cloud"):
+        wl = workload(name)
+        kl = min(args.steps, 5)
+        r64, s64 = measure_single(wl, "fp64", kl, wu, args.cfl, ws, local, e2e=False,
+                                  device_loop=False, keep_state=True, fp64_live=fp64_live)
+        r64["config"] = single_config(name, "fp64", ws)
+        rmx, smx = measure_single(wl, "mixed", kl, wu, args.cfl, ws, local, e2e=False,
+                                  device_loop=False, keep_state=True)
+        rmx["config"] = single_config(name, "mixed", ws)
+        rmx["l1_vs_fp64"] = {"steps": wu + kl, "fields": ["rho", "mx", "my", "mz", "E"],
+                             "l1_rel": l1_rel(smx, s64),
+                             "reference": "HYDRO_FP64 GPU path from the same initial state "
+                                          "after the same steps"}
+        key = "turbulence512" if name == "turbulence" else "shock_cloud"
+        out[key + "_fp64"] = r64
+        out[key + "_mixed"] = rmx
+        del wl, s64, smx
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -314,7 +743,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sedov256")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "strict"])
     ap.add_argument("--recon", default="ppmc", choices=list(RECON_CODES),
                     help="reconstruction (Sec. 2.2.1): ppmc (default), ppmp, plmc, plmp, pcm")
     ap.add_argument("--solver", default="exact", choices=["exact", "roe"],
@@ -323,6 +752,9 @@ def main():
     ap.add_argument("--cfl", type=float, default=0.3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="the headline line only (no mixed, strict, batched, turbulence and "
+                         "shock-cloud records)")
     ap.add_argument("--cpu-steps", type=int, default=1000,
                     help="cap on the oracle steps of the CPU baseline (it stops after 10 s)")
     ap.add_argument("--compare-l1", action="store_true",
@@ -343,291 +775,59 @@ def main():
         dist.init_process_group("nccl")
     w = workload(args.workload)
     if "grids" in w:
-        return run_batch(args, w, ws, rank, local)
-    _, nz, ny, nx = w["u"].shape
-    nreal = nx * ny * nz
-    prec = hydro.HYDRO_FP64 if args.precision == "fp64" else hydro.HYDRO_MIXED
-    stream = torch.cuda.current_stream()
-    g = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], precision=prec, stream=stream,
-                   recon=RECON_CODES[args.recon], solver=SOLVER_CODES[args.solver])
-    for face, prim in (w.get("inflow") or {}).items():
-        g.set_inflow(face, prim)
-    u_host = torch.from_numpy(w["u"]).pin_memory()
-    g.set_state(u_host.numpy())
-    for _ in range(args.warmup):
-        g.step(args.cfl)
-    torch.cuda.synchronize()
-
-    # ---- timed region: K device-resident steps ------------------------------
-    g.profile(True)
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        g.step(args.cfl)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    stages, launches_total = g.profile_read()
-    g.profile(False)
-    ms_max = max_over_ranks(ms, ws)
-    value = replicas_value(nreal, args.steps, ws, ms_max)
-
-    # ---- the same K steps looped on the device (hydro_advance: one CUDA graph
-    # with a WHILE node, no host round trip and no tracing events per step) ----
-    g.advance(args.cfl, math.inf, 0)  # captures the loop graph outside the timed region
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    taken = g.advance(args.cfl, math.inf, args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms_dev = max_over_ranks(ev0.elapsed_time(ev1), ws)
-    device_loop = {"value": replicas_value(nreal, taken, ws, ms_dev), "unit": UNIT,
-                   "ms_per_step": ms_dev / max(taken, 1), "steps": taken}
-
-    # ---- end to end through the public API with host buffers ----------------
-    # Every step uploads its input state from pinned host memory, steps, and
-    # downloads the resulting state.  Steps alternate between two grids on two
-    # streams (the asynchronous API), so one grid's copies overlap the other's
-    # step, as a pipeline of independent problems would run.
-    e2e = None
-    if not args.no_e2e:
-        out_host = [torch.empty_like(u_host).pin_memory() for _ in range(2)]
-        stream2 = torch.cuda.Stream()
-        g2 = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], precision=prec, stream=stream2,
-                        recon=RECON_CODES[args.recon], solver=SOLVER_CODES[args.solver])
-        for face, prim in (w.get("inflow") or {}).items():
-            g2.set_inflow(face, prim)
-        pipe = [g, g2]
-
-        def e2e_step(k):
-            gk = pipe[k % 2]
-            gk.set_state_async(u_host)
-            gk.step_async(args.cfl)
-            gk.get_state_async(out_host[k % 2])
-
-        e2e_step(0)
-        e2e_step(1)
-        g.sync()
-        g2.sync()
-        ke = max(2, min(args.steps, 10))
-        if ws > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        eb = torch.cuda.Event()
-        e0.record(stream)
-        stream2.wait_event(e0)
-        for k in range(ke):
-            e2e_step(k)
-        eb.record(stream2)
-        stream.wait_event(eb)
-        e1.record(stream)
-        g.sync()
-        g2.sync()
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        te = max_over_ranks(e0.elapsed_time(e1), ws)
-        e2e = {"value": replicas_value(nreal, ke, ws, te), "unit": UNIT,
-               "h2d_bytes_per_step": int(u_host.numel() * 8),
-               "d2h_bytes_per_step": int(out_host[0].numel() * 8), "steps": ke,
-               "host_wall_s": wall,
-               "pipeline": "2 grids on 2 streams: one grid's copies overlap the other's step"}
-        g2.close()
-
+        return run_batch(args, w, ws, rank)
+    fp64_live = fp64_peak_live(hydro) if args.precision != "mixed" else None
+    # the sub-records run after the headline default (Sedov 256^3, FP64, PPMC +
+    # exact) on one GPU; under torchrun every rank times the headline only
+    extras = (not args.no_extra and ws == 1 and args.workload == "sedov256"
+              and args.precision == "fp64" and args.recon == "ppmc" and args.solver == "exact")
+    rec, state = measure_single(w, args.precision, args.steps, args.warmup, args.cfl, ws, local,
+                                recon=args.recon, solver=args.solver, e2e=not args.no_e2e,
+                                keep_state=extras, fp64_live=fp64_live)
     l1 = None
     if args.compare_l1 and args.precision == "mixed":
-        l1 = compare_l1(w, args, g, hydro, stream)
+        l1 = compare_l1(w, args, hydro)
+    extra = extra_records(args, ws, local, state, fp64_live) if extras else {}
+    del state
     if rank != 0:
-        g.close()
         if ws > 1:
             dist.destroy_process_group()
         return
-
-    # ---- roofline of the dominant kernel -------------------------------------
-    dom = max((k for k in stages if stages[k][1] > 0), key=lambda k: stages[k][0])
-    dms, dl, dunits = stages[dom]
-    active = sum(1 for n in (nx, ny, nz) if n > 1)
-    units_per_launch = dunits / dl
-    avg_ms = dms / dl
-    # the dominant stage's kernel: the reconstruction stage runs the selected
-    # reconstruction's kernel, the Riemann stages the Roe kernels with --solver roe
-    if args.precision == "mixed":
-        kname = "kb_%s_mixed" % dom
-    elif dom == "ppmc":
-        kname = "kb_" + args.recon
-    elif dom in ("riemann1", "riemann2") and args.solver == "roe":
-        kname = "kb_%s_roe" % dom
-    else:
-        kname = "kb_" + dom
-    # captured traffic applies to the kernels captured (PPMC + exact solver, 3D
-    # grids: a 1D or 2D face carries no or fewer transverse terms)
-    traffic = None
-    tinfo = NCU_TRAFFIC.get((args.precision, dom))
-    if (tinfo and active == 3 and args.recon == "ppmc" and args.solver == "exact"
-            and tinfo["digest"] == source_digest(tinfo["sources"])
-            and tinfo["bs"] == g.block_size()):
-        traffic = tinfo["bytes_per_unit"] * units_per_launch
-    bytes_per_unit = ALGORITHMIC_BYTES[args.precision][dom]
-    if args.precision == "fp64":
-        # FP64 kernels: bound by the FP64 pipe (DRAM a few % busy)
-        table, tkey = flops_table(w["key"], args.recon, args.solver)
-        per_unit = table[dom]
-        src = "algorithmic FP64 flops per unit (oracle/count_ops.py, %s)" % tkey
-        achieved = per_unit * units_per_launch / (avg_ms / 1e3)
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_FLOPS_PEAK,
-                    "unit": "FP64 FLOP/s", "frac": achieved / FP64_FLOPS_PEAK,
-                    "traffic": traffic, "kernel": kname,
-                    "flops_per_unit": per_unit, "units_per_launch": units_per_launch,
-                    "avg_launch_ms": avg_ms, "flops_source": src, "peak_source": PEAK_SOURCE,
-                    "bytes_per_unit_algorithmic": bytes_per_unit}
-    else:
-        # mixed kernels: float arithmetic on a pipe 64x the FP64 rate, streaming
-        # float planes: the roofline that bounds them is HBM bandwidth
-        peak, psrc = hbm_peak_gbs()
-        achieved = bytes_per_unit * units_per_launch / (avg_ms / 1e3) / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": traffic, "kernel": kname,
-                    "bytes_per_unit_algorithmic": bytes_per_unit,
-                    "units_per_launch": units_per_launch, "avg_launch_ms": avg_ms,
-                    "bytes_source": "every plane the kernel reads or writes, once per unit",
-                    "peak_source": "%s HBM copy bandwidth (MEASURED_PEAKS.json)" % psrc
-                                   if psrc == "measured" else "fallback HBM bandwidth",
-                    "fp64_flops_per_unit": mixed_fp64_flops(active).get(dom, 0)}
-    stage_report = {k: {"ms": v[0], "launches": v[1], "share": v[0] / max(ms, 1e-9)}
-                    for k, v in stages.items()}
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(args.workload, args.cpu_steps, args.cfl)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-        "data": "synthetic",
+        "metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": rec["dtype"], "data": "synthetic",
         "config": single_config(args.workload, args.precision, ws, args.recon, args.solver),
-        "e2e": e2e, "gpu_launches": launches_total, "clocks": clocks, "roofline": roofline,
-        "device_loop": device_loop,
-        "stages": stage_report, "cpu_baseline": cpu,
-        "hbm": hbm_report(value / ws, traffic, avg_ms),
+        "e2e": rec["e2e"], "gpu_launches": rec["gpu_launches"], "clocks": rec["clocks"],
+        "roofline": rec["roofline"], "device_loop": rec.get("device_loop"),
+        "stages": rec["stages"], "cpu_baseline": cpu, "hbm": rec["hbm"],
     }
     if l1 is not None:
         line["l1_vs_fp64"] = l1
+    line.update(extra)
     print(json.dumps(line), flush=True)
-    g.close()
     if ws > 1:
         dist.destroy_process_group()
 
 
-def run_batch(args, w, ws, rank, local):
-    """Config 5: a batch of independent grids advanced by hydro_batch_step (one
-    CUDA-graph launch a call; here one step a call so that the timed region is
-    exactly K steps)."""
-    import torch
+def run_batch(args, w, ws, rank):
+    """The batched workload as the headline line (--workload batchedN)."""
     import torch.distributed as dist
-    from paper_1410_4194_gb300 import hydro
-    grids = w["grids"]
-    ncells = sum(int(np.prod(g["u"].shape[1:])) for g in grids)
-    prec = hydro.HYDRO_FP64 if args.precision == "fp64" else hydro.HYDRO_MIXED
-    stream = torch.cuda.Stream()
-    b = hydro.Batch(grids, precision=prec, recon=RECON_CODES[args.recon],
-                    solver=SOLVER_CODES[args.solver])
-    b._check(b._L.hydro_batch_set_stream(b.h, hydro.ctypes.c_void_p(stream.cuda_stream)),
-             "set_stream")
-    bs, order, tune_ms = b.autotune(use_cache=True)
-    for _ in range(args.warmup):
-        b.step(args.cfl, nsteps=1)
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        b.step(args.cfl, nsteps=1)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    ms_max = max_over_ranks(ms, ws)
-    value = replicas_value(ncells, args.steps, ws, ms_max)
-    # end to end: every step uploads every grid's state from pinned host memory,
-    # steps and downloads the states; steps alternate between two batches on two
-    # streams (the asynchronous API), each synced while the other's work is
-    # queued, so one batch's copies overlap the other's step
-    e2e = None
-    if not args.no_e2e:
-        hosts = [torch.from_numpy(g["u"]).pin_memory() for g in grids]
-        outs = [[torch.empty_like(x).pin_memory() for x in hosts] for _ in range(2)]
-        stream2 = torch.cuda.Stream()
-        b2 = hydro.Batch(grids, precision=prec, recon=RECON_CODES[args.recon],
-                         solver=SOLVER_CODES[args.solver])
-        b2.set_stream(stream2)
-        b2.autotune(use_cache=True)
-        pipe = [b, b2]
-
-        def e2e_step(k):
-            bk = pipe[k % 2]
-            for i, x in enumerate(hosts):
-                bk.set_state_async(i, x)
-            bk.step_async(args.cfl, nsteps=1)
-            for i, x in enumerate(outs[k % 2]):
-                bk.get_state_async(i, x)
-
-        e2e_step(0)
-        e2e_step(1)
-        b.sync()
-        b2.sync()
-        ke = max(2, min(args.steps, 6))
-        if ws > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        eb = torch.cuda.Event()
-        e0.record(stream)
-        stream2.wait_event(e0)
-        for k in range(ke):
-            e2e_step(k)
-            if k >= 1:
-                pipe[(k - 1) % 2].sync()
-        eb.record(stream2)
-        stream.wait_event(eb)
-        e1.record(stream)
-        pipe[(ke - 1) % 2].sync()
-        torch.cuda.synchronize()
-        te = max_over_ranks(e0.elapsed_time(e1), ws)
-        e2e = {"value": replicas_value(ncells, ke, ws, te), "unit": UNIT,
-               "h2d_bytes_per_step": int(sum(x.numel() * 8 for x in hosts)),
-               "d2h_bytes_per_step": int(sum(x.numel() * 8 for x in outs[0])), "steps": ke,
-               "pipeline": "2 batches on 2 streams: one batch's copies overlap the other's step"}
-        b2.close()
+    _, _, local = dist_env()
+    rec, _ = measure_batch(w["grids"], w["desc"], args.precision, args.steps, args.warmup,
+                           args.cfl, ws, local, e2e=not args.no_e2e,
+                           keep_states=args.compare_l1 and args.precision == "mixed")
     l1 = None
     if args.compare_l1 and args.precision == "mixed":
+        from paper_1410_4194_gb300 import hydro
         res = {}
         for name, pr in (("mixed", hydro.HYDRO_MIXED), ("fp64", hydro.HYDRO_FP64)):
-            bb = hydro.Batch(grids, precision=pr)
+            bb = hydro.Batch(w["grids"], precision=pr)
             bb.step(args.cfl, nsteps=args.warmup + args.steps)
-            res[name] = [bb.get_state(i) for i in range(len(grids))]
+            res[name] = [bb.get_state(i) for i in range(len(w["grids"]))]
             bb.close()
         d = sum(np.abs(a - c).reshape(5, -1).sum(axis=1) for a, c in zip(res["mixed"], res["fp64"]))
         s_ = sum(np.abs(c).reshape(5, -1).sum(axis=1) for c in res["fp64"])
@@ -635,48 +835,18 @@ def run_batch(args, w, ws, rank, local):
         l1 = {"steps": args.warmup + args.steps, "fields": ["rho", "mx", "my", "mz", "E"],
               "l1_rel": list(d / np.array([s_[0], mom, mom, mom, s_[4]])),
               "reference": "HYDRO_FP64 batch from the same initial states"}
-    b.close()
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
         return
-    # kernels of one step of the graph (3D grids): primitives + dt, update, and
-    # per axis the slope pass (none for PCM or in mixed precision, whose PPMC
-    # kernel forms its own slopes), reconstruction and the two Riemann sets
-    slope_pass = 0 if (args.recon == "pcm" or args.precision == "mixed") else 1
-    launches_per_step = 3 + 3 * (3 + slope_pass)
-    # step-level roofline (the graph's kernels are not timed one by one):
-    # FP64 flops of a cell update times the cell-update rate
-    if args.precision == "fp64":
-        pu = ALGORITHMIC_FLOPS["batched"]
-        per_cell = (pu["prims"] + 3 * (pu["slopes"] + pu["ppmc"] + pu["riemann1"]
-                                       + pu["riemann2"]) + pu["update"])
-        src = "algorithmic FP64 flops per cell update (oracle/count_ops.py, Sedov sample)"
-    else:
-        per_cell = mixed_bytes_per_cell_update(3)
-        src = "algorithmic HBM bytes of the mixed-precision kernels per cell update"
-    achieved = per_cell * value / ws
+    cfg = dict(rec["config"])
+    cfg["parallelism"] = "replicas" if ws > 1 else "single"
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-        "config": {"workload": w["desc"], "cells": ncells, "grids": len(grids),
-                   "precision": args.precision, "schedule": {"block": bs, "order": order},
-                   "parallelism": "replicas" if ws > 1 else "single",
-                   "l2": "inputs larger than L2 (states %.2f GB)" % (ncells * 40 / 1e9)},
-        "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-        "hbm": hbm_report(value / ws),
-        "roofline": ({"bound": "alu", "achieved": achieved, "peak": FP64_FLOPS_PEAK,
-                      "unit": "FP64 FLOP/s", "frac": achieved / FP64_FLOPS_PEAK, "traffic": None,
-                      "kernel": "whole step (graph)", "flops_per_cell_update": per_cell,
-                      "flops_source": src, "peak_source": PEAK_SOURCE}
-                     if args.precision == "fp64" else
-                     {"bound": "hbm", "achieved": achieved / 1e9, "peak": hbm_peak_gbs()[0],
-                      "unit": "GB/s", "frac": achieved / 1e9 / hbm_peak_gbs()[0], "traffic": None,
-                      "kernel": "whole step (graph)", "bytes_per_cell_update": per_cell,
-                      "bytes_source": src,
-                      "peak_source": "%s HBM copy bandwidth" % hbm_peak_gbs()[1]}),
+        "metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": rec["dtype"], "data": "synthetic",
+        "config": cfg, "e2e": rec["e2e"], "gpu_launches": rec["gpu_launches"],
+        "clocks": rec["clocks"], "hbm": rec["hbm"], "roofline": rec["roofline"],
         "cpu_baseline": None,
     }
     if l1 is not None:
@@ -688,13 +858,14 @@ def run_batch(args, w, ws, rank, local):
         dist.destroy_process_group()
 
 
-def compare_l1(w, args, g, hydro, stream):
+def compare_l1(w, args, hydro):
     """Run the mixed and the FP64 path from the workload's initial state for
     warmup + steps steps and report the relative L1 difference per field (the
     momenta against their group's scale)."""
     import torch
     _, nz, ny, nx = w["u"].shape
     n = args.warmup + args.steps
+    stream = torch.cuda.current_stream()
     res = {}
     for name, prec in (("mixed", hydro.HYDRO_MIXED), ("fp64", hydro.HYDRO_FP64)):
         h = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], precision=prec, stream=stream)
@@ -707,12 +878,8 @@ def compare_l1(w, args, g, hydro, stream):
         h.get_state(out)
         h.close()
         res[name] = out
-    d = (res["mixed"] - res["fp64"]).abs().reshape(5, -1).sum(dim=1)
-    s = res["fp64"].abs().reshape(5, -1).sum(dim=1)
-    mom = s[1:4].max()
-    den = torch.stack([s[0], mom, mom, mom, s[4]])
-    l1 = (d / den).tolist()
-    return {"steps": n, "fields": ["rho", "mx", "my", "mz", "E"], "l1_rel": l1,
+    return {"steps": n, "fields": ["rho", "mx", "my", "mz", "E"],
+            "l1_rel": l1_rel(res["mixed"], res["fp64"]),
             "reference": "HYDRO_FP64 GPU path from the same initial state"}
 
 
@@ -834,6 +1001,9 @@ def workload_shape(name):
     if name.startswith("noh"):
         n = int(name[3:] or 200)
         return n, n, n
+    if name.startswith("turbulence") and name != "turbulence":
+        n = int(name[10:])
+        return n, n, n
     return {"sod512": (512, 1, 1), "shock_cloud": (512, 256, 256),
             "turbulence": (512, 512, 512)}[name]
 
@@ -846,6 +1016,10 @@ def workload_desc(name):
         n = int(name[3:] or 200)
         return ("3D Noh strong shock, %d^3 octant, reflecting inner and analytic outer faces, "
                 "gamma 5/3, p0 1e-6, CFL 0.3" % n)
+    if name.startswith("turbulence") and name != "turbulence":
+        n = int(name[10:])
+        return ("3D supersonic turbulence, %d^3 periodic, rms Mach 5, shells 1..%d, CFL 0.3"
+                % (n, max(1, 16 * n // 512)))
     return WORKLOAD_DESC.get(name, name)
 
 

@@ -386,6 +386,16 @@ int hydro_check_conversions(unsigned long long* mismatches, void* stream);
  * memory.  Returns HYDRO_OK, HYDRO_EINVAL (mismatches NULL) or HYDRO_ECUDA. */
 int hydro_check_scaling(unsigned long long* mismatches, void* stream);
 
+/* The paper has no counterpart to this entry point.  Measured FP64 throughput
+ * of the current device, the ceiling of the FP64 path (bound by its FP64 pipe):
+ * a kernel of independent fused multiply-add chains on every SM (152 x 8
+ * blocks of 256 threads, 8 chains of 4096 FMAs a thread), timed with CUDA
+ * events on `stream`, the fastest of three launches after a warm-up.
+ * flops_per_s: host double receiving 2 flops per FMA over that time.  Waits
+ * for the stream; allocates nothing.  Returns HYDRO_OK, HYDRO_EINVAL
+ * (flops_per_s NULL) or HYDRO_ECUDA. */
+int hydro_probe_fp64_rate(double* flops_per_s, void* stream);
+
 /* Host-only self-check of the integer division the kernels' index arithmetic
  * uses (a multiply-high and a shift by constants formed per grid, in place of
  * an integer division; valid for numerators below 2^31, which the size rules

@@ -3,7 +3,9 @@
 // (bit for bit in the normal range, zeros and infinities; subnormals flushed
 // to a signed zero; NaN to NaN); hydro_check_scaling(): its integer halving,
 // doubling and sign tests against the FP64 arithmetic, and the float-float to
-// double conversion of hydro_ffsum.cuh against the FP64 add.
+// double conversion of hydro_ffsum.cuh against the FP64 add;
+// hydro_probe_fp64_rate(): the device's measured FP64 FMA throughput, the
+// denominator of the FP64 kernels' roofline.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -152,7 +154,61 @@ __global__ void __launch_bounds__(kThreads) k_check_scaling(unsigned long long* 
   }
 }
 
+// FP64 FMA throughput: every thread runs kChains independent chains
+// x <- x * b + c of kRateIters fused multiply-adds each (b, c from the host, so
+// nothing folds); the sum is stored only if it equals a value it cannot take,
+// which keeps the chains live without writing memory
+constexpr int kChains = 8;
+constexpr int kRateIters = 4096;
+constexpr unsigned kRateBlocks = 152 * 8;
+__device__ double g_rate_sink;
+
+__global__ void __launch_bounds__(kThreads) k_fp64_rate(double b, double c, double never) {
+  double x[kChains];
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) x[k] = (double)(threadIdx.x + k);
+  for (int i = 0; i < kRateIters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) x[k] = fma(x[k], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) s += x[k];
+  if (s == never) g_rate_sink = s;
+}
+
 }  // namespace
+
+extern "C" int hydro_probe_fp64_rate(double* flops_per_s, void* stream) {
+  if (!flops_per_s) return HYDRO_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess) return HYDRO_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return HYDRO_ECUDA;
+  }
+  int rc = HYDRO_OK;
+  float best_ms = -1.0f;
+  // a warm-up launch, then the fastest of three timed ones
+  for (int rep = 0; rep < 4 && rc == HYDRO_OK; ++rep) {
+    if (cudaEventRecord(e0, st) != cudaSuccess) rc = HYDRO_ECUDA;
+    k_fp64_rate<<<kRateBlocks, kThreads, 0, st>>>(0.999999, 1e-7, -1.0);
+    if (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, st) != cudaSuccess ||
+        cudaEventSynchronize(e1) != cudaSuccess)
+      rc = HYDRO_ECUDA;
+    float ms = 0.0f;
+    if (rc == HYDRO_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = HYDRO_ECUDA;
+    if (rc == HYDRO_OK && rep > 0 && (best_ms < 0.0f || ms < best_ms)) best_ms = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != HYDRO_OK) return rc;
+  if (!(best_ms > 0.0f)) return HYDRO_ECUDA;
+  const double fmas = (double)kRateBlocks * kThreads * kChains * kRateIters;
+  *flops_per_s = 2.0 * fmas / (best_ms * 1e-3);
+  return HYDRO_OK;
+}
 
 extern "C" int hydro_check_scaling(unsigned long long* mismatches, void* stream) {
   if (!mismatches) return HYDRO_EINVAL;

@@ -37,7 +37,7 @@ EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_time", "hydro_get_time",
            "hydro_batch_step", "hydro_batch_step_async", "hydro_batch_sync",
            "hydro_batch_set_state_async", "hydro_batch_get_state_async", "hydro_batch_autotune", "hydro_batch_last_error",
            "hydro_batch_cuda_error_string", "hydro_batch_free", "hydro_check_conversions",
-           "hydro_check_fastdiv", "hydro_check_scaling",
+           "hydro_check_fastdiv", "hydro_check_scaling", "hydro_probe_fp64_rate",
            "hydro_set_reconstruction", "hydro_batch_set_reconstruction",
            "hydro_set_riemann_solver", "hydro_batch_set_riemann_solver")
 STAGES = ("prims", "set_dt", "slopes", "ppmc", "riemann1", "riemann2", "update")
@@ -109,6 +109,7 @@ def load():
     L.hydro_batch_free.argtypes = [vp]
     L.hydro_check_conversions.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), vp]
     L.hydro_check_scaling.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), vp]
+    L.hydro_probe_fp64_rate.argtypes = [dp, vp]
     L.hydro_check_fastdiv.argtypes = []
     L.hydro_check_fastdiv.restype = ctypes.c_longlong
     L.hydro_set_reconstruction.argtypes = [vp, ctypes.c_int]
@@ -431,6 +432,17 @@ def check_conversions():
     if rc != 0:
         raise HydroError(rc, "check_conversions")
     return int(out[0]), int(out[1])
+
+
+def probe_fp64_rate():
+    """Measured FP64 throughput of the current device in flop/s (2 per fused
+    multiply-add), from a kernel of independent FMA chains on every SM."""
+    L = load()
+    out = ctypes.c_double(0.0)
+    rc = L.hydro_probe_fp64_rate(ctypes.byref(out), _torch_stream_ptr())
+    if rc != 0:
+        raise HydroError(rc, "probe_fp64_rate")
+    return float(out.value)
 
 
 def check_scaling():

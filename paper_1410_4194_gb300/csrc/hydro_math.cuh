@@ -1216,6 +1216,7 @@ struct RSide {
   T inv_A;  // 1/A_k = (gamma+1) rho_k / 2
   T cf;     // 2 a_k/(gamma-1)
   T cd;     // a_k/gamma = p_k/(rho_k a_k)
+  T cdp;    // a_k/(gamma p_k): f' on a rarefaction is cdp (p/p_k)^(z-1)
 };
 
 // pressure function f_k, its derivative, and x = (p/p_k)^z on a rarefaction
@@ -1290,6 +1291,68 @@ __device__ __forceinline__ void make_side(const T W[5], T inv_d, const GasT<T>& 
   s.B = g.gm1_gp1 * s.p;
   s.cf = S ? T(2) * s.a * g.inv_gm1 : s.a * g.fan_d;  // fan_d = 2 inv_gm1 exactly
   s.cd = s.a * g.inv_g;
+  s.cdp = S ? T(0) : s.cd * s.inv_p;
+}
+
+// Pressure function of one side without a branch between its two forms, for
+// gamma with z = (gamma-1)/(2 gamma) = 1/K (fast FP64 path, used for K = 5).  On
+// GB300 the FP64 pipe runs at 1/64 of the float rate and a warp whose lanes
+// take both the rarefaction and the shock form issues both: on turbulent data
+// nine warps in ten hold both kinds of sides.  Here both forms are one
+// reciprocal-root iteration t = sigma^(-1/m) with lane-selected operands:
+//   rarefaction (p <= p_k): sigma = p/p_k, m = K: x = (p/p_k)^(1/K) = sigma t^(K-1),
+//     f = cf (x - 1), f' = cdp t^(K-1)  (= x a_k/(gamma p), as x/r = t^(K-1));
+//   shock: sigma = (p + B_k)/A_k, m = 2: q = sqrt(A_k/(p + B_k)) = t,
+//     f = (p - p_k) q, f' = q (1 - (p - p_k)/(2 (p + B_k))), 1/(p + B_k) = t^2/A_k;
+// with the seed t from the float log2/exp2 (relative error ~2^-22) and two
+// Newton steps t <- t + (t/m)(1 - sigma t^m), which leave t within an ulp or
+// two.  A side whose ratio p/p_k lies within 2^-20 of 1 (equal pressures up to
+// rounding: uniform regions, where the two-shock start value can land an ulp
+// on either side of p_k) takes the rarefaction form's short series on either
+// branch: the shock and rarefaction forms of f agree there to within
+// (gamma+1)|3 gamma - 5| e^3 sqrt(p_k/rho)/(96 gamma^(5/2)), e = p/p_k - 1
+// (third-order contact; zero for gamma = 5/3), below the rounding of f_L + f_R
+// + u_R - u_L, and f' to O(e^2), which only scales the Newton step.  A sigma
+// outside [1e-30, 1e30] (beyond the float seed's range) takes side_f.
+// FD: also f'.  x = 0 on a shock side (the sampling of a shock side does not
+// use it).
+template <int K, bool FD>
+__device__ __forceinline__ void side_eval(double p, const RSide<double>& s,
+                                          const GasT<double>& g, double& f, double& fd,
+                                          double& x) {
+  const bool rare = !lt<false>(s.p, p);  // p <= p_k
+  const double r = p * s.inv_p;
+  const long long rb = __double_as_longlong(r);
+  if (rb > 0x3feffffe00000000LL && rb < 0x3ff0000100000000LL) {
+    // (1 + e)^(1/K) and (1 + e)^(1/K - 1) to second order, e = r - 1 exact
+    // (Sterbenz); the third-order terms are below 1e-18
+    const double e = r - 1.0;
+    x = fma(e, fma(e, -(K - 1) / (2.0 * K * K), 1.0 / K), 1.0);
+    f = s.cf * (x - 1.0);
+    if (FD) fd = s.cdp * fma(e, fma(e, (K - 1) * (2.0 * K - 1) / (2.0 * K * K), -(K - 1.0) / K), 1.0);
+    return;
+  }
+  const double sig = rare ? r : (p + s.B) * s.inv_A;
+  if (!(lt<false>(1e-30, sig) && lt<false>(sig, 1e30))) {
+    side_f<false>(p, nr_rcp(p), s, g, f, fd, x);
+    return;
+  }
+  const double inv_m = rare ? 1.0 / K : 0.5;
+  const float nm = rare ? -1.0f / K : -0.5f;
+  double t = f2d(exp2f(__log2f(d2f(sig)) * nm));
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double t2 = t * t, t4 = t2 * t2;
+    const double tK = (K == 5) ? t4 * t : t4 * t2 * t;
+    const double e = fma(-sig, rare ? tK : t2, 1.0);
+    t = fma(t * inv_m, e, t);
+  }
+  const double t2 = t * t, t4 = t2 * t2;
+  const double tK1 = (K == 5) ? t4 : t4 * t2;  // t^(K-1)
+  x = rare ? r * tK1 : 0.0;
+  const double dp = p - s.p;
+  f = (rare ? s.cf : dp) * (rare ? x - 1.0 : t);
+  if (FD) fd = (rare ? s.cdp : t) * (rare ? tK1 : fma(-half<false>(dp), t2 * s.inv_A, 1.0));
 }
 
 // sampled state on a rarefaction side at x/t = 0 past the head: star state
@@ -1343,10 +1406,11 @@ __device__ __forceinline__ void sample_shock(const RSide<T>& k, T pm, T um, T sg
 }
 
 // Exact Riemann flux from primitive states in sweep order (inv_d = 1/rho of
-// each side, unused when strict); returns the status flags.
-template <bool S = false, typename T>
-__device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv_dL, T inv_dR,
-                                             const GasT<T>& g, T F[5]) {
+// each side, unused when strict); returns the status flags.  K = 5 or 7: the
+// fast FP64 form for z = 1/K (side_eval); K = 0: any gamma, strict or float.
+template <bool S, typename T, int K>
+__device__ __forceinline__ int riemann_exact_k(const T WL[5], const T WR[5], T inv_dL, T inv_dR,
+                                               const GasT<T>& g, T F[5]) {
   RSide<T> L, R;
   make_side<S>(WL, inv_dL, g, L);
   make_side<S>(WR, inv_dR, g, R);
@@ -1370,9 +1434,14 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
   T prev_step = T(0);  // float path: the previous Newton step
   bool same = false;   // the last step left p unchanged (bit for bit)
   for (int it = 0; it < kNewtonMax; ++it) {
-    const T ip = S ? T(0) : nr_rcp(p);
-    side_f<S>(p, ip, L, g, fL, dfL, xL);
-    side_f<S>(p, ip, R, g, fR, dfR, xR);
+    if constexpr (K != 0) {
+      side_eval<K, true>(p, L, g, fL, dfL, xL);
+      side_eval<K, true>(p, R, g, fR, dfR, xR);
+    } else {
+      const T ip = S ? T(0) : nr_rcp(p);
+      side_f<S>(p, ip, L, g, fL, dfL, xL);
+      side_f<S>(p, ip, R, g, fR, dfR, xR);
+    }
     const T F = fL + fR + R.u - L.u;
     T pn = p - (S ? F / (dfL + dfR) : nr_div(F, dfL + dfR));
     if (lt<S>(pn, T(kPFloor))) pn = T(kPFloor);
@@ -1405,8 +1474,14 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
   // f_L, f_R and x at the final p (already in hand when the last step left p
   // unchanged, the usual case for smooth data)
   if (!same) {
-    side_f_only<S>(p, L, g, fL, xL);
-    side_f_only<S>(p, R, g, fR, xR);
+    if constexpr (K != 0) {
+      T unused;
+      side_eval<K, false>(p, L, g, fL, unused, xL);
+      side_eval<K, false>(p, R, g, fR, unused, xR);
+    } else {
+      side_f_only<S>(p, L, g, fL, xL);
+      side_f_only<S>(p, R, g, fR, xR);
+    }
   }
   const T pm = p;
   const T um = half<S>(L.u + R.u + fR - fL);
@@ -1444,6 +1519,21 @@ __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv
   F[3] = mf * w;
   F[4] = (E + ps) * u;
   return flags;
+}
+
+// The fast FP64 path takes the branch-free pressure functions for gamma = 5/3
+// (K = 5, every three-dimensional workload here).  Other gamma keep the
+// correctly rounded k-th root of side_f: for K = 7 the branch-free form's t^6
+// and t^7 add two roundings (the fast/strict difference after 10 steps grew
+// from 2e-15 to 1.1e-14 of a variable's scale), and a second copy of the solver
+// in every Riemann kernel cost 0.2-0.3% on Sedov 256^3 (code size).
+template <bool S = false, typename T>
+__device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv_dL, T inv_dR,
+                                             const GasT<T>& g, T F[5]) {
+  if constexpr (!S && sizeof(T) == 8) {
+    if (g.k == 5) return riemann_exact_k<false, T, 5>(WL, WR, inv_dL, inv_dR, g, F);
+  }
+  return riemann_exact_k<S, T, 0>(WL, WR, inv_dL, inv_dR, g, F);
 }
 
 }  // namespace hydro

@@ -332,6 +332,13 @@ void fill_desc(GridDesc& d, double gamma) {
   d.gf = make_gas<float>(gamma);
   for (int s = kStageSlopes; s <= kStageRiemann2; ++s)
     for (int a = 0; a < 3; ++a) d.box[s - kStageSlopes][a] = stage_box(d.G, s, a);
+  for (int a = 0; a < 3; ++a) {
+    Box b = d.box[kStagePpmc - kStageSlopes][a];
+    b.n[a] = (b.n[a] + kPpmcSeg - 1) / kPpmcSeg;
+    b.div0 = make_fastdiv((unsigned)b.n[0]);
+    b.div01 = make_fastdiv((unsigned)b.n[0] * (unsigned)b.n[1]);
+    d.seg[a] = b;
+  }
 }
 
 bool build_launch_tables(const GridDesc* desc, const int* order, int n, int bs, int* tab,
@@ -345,6 +352,12 @@ bool build_launch_tables(const GridDesc* desc, const int* order, int n, int bs, 
         units = (long long)g.G.N[0] * g.G.N[1] * g.G.N[2];
       } else if (k == 1) {
         units = g.G.nreal;
+      } else if (k >= ppmc_seg_kind(1)) {
+        // kPpmcSegThreads a block whatever bs is: one compiled kernel, so the
+        // rounding of its fused multiply-adds does not depend on the schedule
+        const int axis = k - ppmc_seg_kind(1) + 1;
+        const long long segs = g.G.n[axis] > 1 ? box_count(g.seg[axis]) : 0;
+        units = (segs + kPpmcSegThreads - 1) / kPpmcSegThreads * bs;
       } else {
         const int stage = kStageSlopes + (k - 2) / 3, axis = (k - 2) % 3;
         units = g.G.n[axis] > 1 ? box_count(g.box[stage - kStageSlopes][axis]) : 0;

@@ -110,6 +110,8 @@ struct GridDesc {
   GasT<double> gd;  // gamma-derived constants, formed on the host
   GasT<float> gf;
   Box box[4][3];    // [stage - kStageSlopes][axis]: units of the per-axis stages
+  Box seg[3];       // mixed PPMC along y and z: the PPMC box with segments of
+                    // kPpmcSeg cells along the sweep axis as units (seg[0] unused)
 };
 
 // A batched launch covers the blocks of all grids: grid order[i] owns blocks
@@ -146,8 +148,13 @@ inline long long padded_cells(const int n[3]) {
 Box stage_box_of(const Geom& G, int stage, int axis);
 
 // Launch kinds of a (batched) step: 0 primitives, 1 update, then the four
-// per-axis stages x three axes.
-constexpr int kLaunchKinds = 2 + 4 * 3;
+// per-axis stages x three axes, then the mixed PPMC by segments along y and z.
+constexpr int kLaunchKinds = 2 + 4 * 3 + 2;
+inline int ppmc_seg_kind(int axis) { return 2 + 4 * 3 + (axis - 1); }
+// cells a thread of the segmented mixed PPMC kernels reconstructs along the
+// sweep axis (y or z)
+constexpr int kPpmcSeg = 4;
+constexpr int kPpmcSegThreads = 128;  // threads a block of those kernels, for any schedule
 inline int launch_kind(int stage, int axis) { return 2 + (stage - kStageSlopes) * 3 + axis; }
 // Fill a descriptor's stage boxes and gas constants from its geometry and gamma.
 void fill_desc(GridDesc& d, double gamma);
@@ -190,6 +197,9 @@ cudaError_t batch_stage_mixed(const BatchLaunch& L, int stage, int axis, int bs,
 cudaError_t batch_prims_mixed(const BatchLaunch& L, int bs, unsigned blocks, cudaStream_t st,
                               bool noh);
 cudaError_t batch_update_mixed(const BatchLaunch& L, int bs, unsigned blocks, cudaStream_t st);
+// the mixed PPMC along y (axis 1) or z (axis 2) by segments (launch kind
+// ppmc_seg_kind(axis), kPpmcSegThreads a block)
+cudaError_t batch_ppmc_mixed_seg(const BatchLaunch& L, int axis, unsigned blocks, cudaStream_t st);
 cudaError_t fp64_riemann_soa(int n, const double* UL, const double* UR, double gamma, double* F,
                              int* flags, cudaStream_t st);
 cudaError_t fp64_ppmc_soa(int n, const double* w, double dtdx, double gamma, double* WsL,

@@ -138,9 +138,12 @@ def test_batch_other_methods_match_single_grids_and_oracle(recon, solver):
 def test_block_size_leaves_results_unchanged(precision):
     """A single grid's launches with 128 or 256 threads a block: the same
     arithmetic per cell, the dt a maximum over cells.  FP64 is bitwise the
-    same; in mixed precision the per-block pick of the cell whose signal speed
-    is evaluated in FP64 can only differ where float estimates tie, which these
-    states do not have (bitwise here too)."""
+    same.  In mixed precision each block evaluates in FP64 the signal speed of
+    the cell with its largest float estimate, so dt is the FP64 maximum except
+    where two cells' float estimates tie while their FP64 values differ: then
+    within 10 * 2^-24 relative, and which tied cell a block picks depends on
+    the block size (the blast's mirror-image cells can tie); the states then
+    differ only by the effect of that dt difference."""
     w = W.sedov(40)
     out = {}
     for bs in (128, 256):
@@ -153,8 +156,16 @@ def test_block_size_leaves_results_unchanged(precision):
             out[bs] = (dts, g.get_state())
         finally:
             g.close()
-    assert out[128][0] == out[256][0]
-    assert np.array_equal(out[128][1], out[256][1])
+    if precision == hydro.HYDRO_FP64:
+        assert out[128][0] == out[256][0]
+        assert np.array_equal(out[128][1], out[256][1])
+    else:
+        d128, d256 = np.array(out[128][0]), np.array(out[256][0])
+        assert np.all(np.abs(d128 - d256) <= 10 * 2.0 ** -24 * d256), (d128, d256)
+        m = np.abs(out[256][1]).reshape(5, -1).max(axis=1)
+        scale = np.array([m[0], m[1:4].max(), m[1:4].max(), m[1:4].max(), m[4]])
+        diff = np.abs(out[128][1] - out[256][1]).reshape(5, -1).max(axis=1) / scale
+        assert np.all(diff <= 1e-6), diff
     g = hydro.Grid(16, 16, 16, 0.1, 1.4, [0] * 6)
     try:
         assert g.block_size() == 128  # the default

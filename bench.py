@@ -120,24 +120,24 @@ _FP64_SRC = ["hydro_fp64_fast.cu", "hydro_internal.h", "hydro_kernels.cuh", "hyd
 _MIXED_SRC = ["hydro_ffsum.cuh", "hydro_internal.h", "hydro_kernels.cuh", "hydro_math.cuh",
               "hydro_mixed.cu"]
 NCU_TRAFFIC = {
-    ("fp64", "riemann2"): {"bytes_per_unit": 204.65, "digest": "91e3d6724020d16e", "bs": 128,
+    ("fp64", "riemann2"): {"bytes_per_unit": 204.77, "digest": "b7950d09f77fb953", "bs": 128,
                            "sources": _FP64_SRC},
-    ("fp64", "ppmc"): {"bytes_per_unit": 185.99, "digest": "91e3d6724020d16e", "bs": 128,
+    ("fp64", "ppmc"): {"bytes_per_unit": 188.23, "digest": "b7950d09f77fb953", "bs": 128,
                        "sources": _FP64_SRC},
-    ("fp64", "riemann1"): {"bytes_per_unit": 118.38, "digest": "91e3d6724020d16e", "bs": 128,
+    ("fp64", "riemann1"): {"bytes_per_unit": 119.71, "digest": "b7950d09f77fb953", "bs": 128,
                            "sources": _FP64_SRC},
-    ("fp64", "slopes"): {"bytes_per_unit": 99.54, "digest": "91e3d6724020d16e", "bs": 128,
+    ("fp64", "slopes"): {"bytes_per_unit": 100.93, "digest": "b7950d09f77fb953", "bs": 128,
                          "sources": _FP64_SRC},
-    ("mixed", "riemann2"): {"bytes_per_unit": 99.76, "digest": "66b22e580e1154c8", "bs": 128,
+    ("mixed", "riemann2"): {"bytes_per_unit": 99.71, "digest": "19b7ab523887e7f2", "bs": 128,
                             "sources": _MIXED_SRC},
-    ("mixed", "update"): {"bytes_per_unit": 137.86, "digest": "66b22e580e1154c8", "bs": 128,
+    ("mixed", "update"): {"bytes_per_unit": 137.86, "digest": "19b7ab523887e7f2", "bs": 128,
                           "sources": _MIXED_SRC},
-    # the x sweep (one thread a cell, 62.5 B) and the y, z sweeps (segments, 64.6 B)
-    ("mixed", "ppmc"): {"bytes_per_unit": 63.9, "digest": "66b22e580e1154c8", "bs": 128,
+    # the x sweep (one thread a cell, 62.6 B) and the y, z sweeps (segments, 64.5 B)
+    ("mixed", "ppmc"): {"bytes_per_unit": 63.9, "digest": "19b7ab523887e7f2", "bs": 128,
                         "sources": _MIXED_SRC},
-    ("mixed", "riemann1"): {"bytes_per_unit": 54.93, "digest": "66b22e580e1154c8", "bs": 128,
+    ("mixed", "riemann1"): {"bytes_per_unit": 54.93, "digest": "19b7ab523887e7f2", "bs": 128,
                             "sources": _MIXED_SRC},
-    ("mixed", "prims"): {"bytes_per_unit": 58.88, "digest": "66b22e580e1154c8", "bs": 128,
+    ("mixed", "prims"): {"bytes_per_unit": 58.91, "digest": "19b7ab523887e7f2", "bs": 128,
                          "sources": _MIXED_SRC},
 }
 

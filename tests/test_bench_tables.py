@@ -43,3 +43,23 @@ def test_ncu_traffic_table_is_consistent():
     for key, info in bench.NCU_TRAFFIC.items():
         assert 0.75 < info["bytes_per_unit"] / bench.ALGORITHMIC_BYTES[key[0]][key[1]] < 1.05, key
         assert len(bench.source_digest(info["sources"])) == 16
+
+
+def test_l1_helper_and_scaled_turbulence_recipe():
+    """bench.l1_rel: the relative L1 difference per field, the momenta against
+    their group's largest L1 norm; the small turbulence boxes keep the 512^3
+    recipe's 32 cells across the shortest wavelength (shells scaled with n)."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    ref = np.ones((5, 2, 2, 2))
+    ref[1:4] = 0.0
+    ref[2] = 2.0  # the momenta's common scale: sum |m_y| = 16
+    a = ref.copy()
+    a[0, 0, 0, 0] += 0.5   # rho: 0.5 / 8
+    a[3, 1, 1, 1] += 1.0   # m_z: 1 / 16
+    l1 = bench.l1_rel(a, ref)
+    assert l1 == pytest.approx([0.5 / 8, 0.0, 0.0, 1.0 / 16, 0.0])
+    assert bench.workload_shape("turbulence128") == (128, 128, 128)
+    assert "shells 1..4" in bench.workload_desc("turbulence128")

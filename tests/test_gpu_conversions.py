@@ -24,3 +24,18 @@ def test_integer_scaling_matches_the_fp64_multiply():
     assert doubling == 0, "2x mismatches: %d" % doubling
     assert signs == 0, "product sign mismatches: %d" % signs
     assert ffsums == 0, "float-float sum mismatches: %d" % ffsums
+
+
+def test_fp64_rate_probe_is_the_fp64_pipe():
+    """The FP64 throughput probe (the denominator the benchmark reports beside
+    the unit-count peak) measures between half and 1.05 times GB300's two FP64
+    FMA a clock an SM at the maximum clock (152 SMs x 2070 MHz x 2 x 2 flops):
+    a kernel whose chains the compiler folded, or a float pipe measured by
+    mistake, would fall outside."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for -m gpu tests")
+    from paper_1410_4194_gb300 import hydro
+    rate = hydro.probe_fp64_rate()
+    nominal = 152 * 2070e6 * 2 * 2
+    assert 0.5 * nominal < rate < 1.05 * nominal, rate

@@ -620,20 +620,24 @@ HYDRO_BATCH_WRAPPER(kb_ppmp, ppmp_body, 1)
 HYDRO_BATCH_WRAPPER(kb_plmc, plmc_body, 1)
 HYDRO_BATCH_WRAPPER(kb_plmp, plmp_body, 1)
 HYDRO_BATCH_WRAPPER(kb_pcm, pcm_body, 1)
-HYDRO_BATCH_WRAPPER(kb_riemann2, riemann2_body, 3)
-// the first Riemann set runs with 1024 resident threads an SM (64 registers):
-// 1.8% faster on Sedov 256^3 than with 768 (80 registers); the second set gains
-// nothing from it
-#define HYDRO_BATCH_WRAPPER_1024(NAME, BODY, STAGE_IDX)                                        \
+// The Riemann sets with their own register budgets, THR resident threads an SM
+// (with 128-thread blocks; 256-thread blocks round down to a multiple of 256),
+// by measurement on Sedov 256^3 and Mach-5 turbulence 256^3: the first set at
+// 1024 (64 registers), 1.8% faster than at 768 (80 registers); the second at
+// 896 (72 registers), 0.4-0.6% faster than at 768 and 1% faster than at 640
+// (96 registers); the reconstruction and slope kernels gain nothing from 640
+// or 896
+#define HYDRO_BATCH_WRAPPER_T(NAME, BODY, STAGE_IDX, THR)                                      \
   template <int D, bool S, int BS>                                                             \
-  __global__ void __launch_bounds__(BS, 1024 / BS) NAME(BatchLaunch L) {                      \
+  __global__ void __launch_bounds__(BS, THR / BS) NAME(BatchLaunch L) {                       \
     const BatchItem it = batch_item(L);                                                        \
     const Box& box = it.d->box[STAGE_IDX][D];                                                  \
     if (it.t < (long long)box.n[0] * box.n[1] * box.n[2])                                      \
       BODY<D, S>(it.d->G, it.d->B, box, it.d->gd, it.t);                                       \
   }
-HYDRO_BATCH_WRAPPER_1024(kb_riemann1, riemann1_body, 2)
-#undef HYDRO_BATCH_WRAPPER_1024
+HYDRO_BATCH_WRAPPER_T(kb_riemann1, riemann1_body, 2, 1024)
+HYDRO_BATCH_WRAPPER_T(kb_riemann2, riemann2_body, 3, 896)
+#undef HYDRO_BATCH_WRAPPER_T
 HYDRO_BATCH_WRAPPER(kb_riemann1_roe, riemann1_roe_body, 2)
 HYDRO_BATCH_WRAPPER(kb_riemann2_roe, riemann2_roe_body, 3)
 #undef HYDRO_BATCH_WRAPPER

@@ -193,6 +193,13 @@ __device__ __forceinline__ double join_bits(unsigned lo, unsigned hi) {
   asm("mov.b64 %0, {%1, %2};" : "=d"(x) : "r"(lo), "r"(hi));
   return x;
 }
+// x with its sign flipped where smask is 0x80000000 (0 leaves x): a negation
+// chosen per lane, on the integer pipe
+__device__ __forceinline__ double flip_sign(double x, unsigned smask) {
+  unsigned lo, hi;
+  split_bits(x, lo, hi);
+  return join_bits(lo, hi ^ smask);
+}
 
 // Sign tests of a product x*y from the factors' sign bits and zero tests, on
 // the integer pipe: an FP64 multiply formed only for its sign costs a full slot
@@ -618,6 +625,72 @@ __device__ __forceinline__ void limited_slope(const T wm[5], const T wc[5], cons
 }
 
 // ---------------------------------------------------------------------------
+// The characteristic corrections of App. A.3 in the fast FP64 path.  The
+// contact term E (left face, lambda^0 < 0) excludes the contact term D (right
+// face, lambda^0 > 0), and the acoustic term B (left face, lambda^p < 0)
+// excludes C (right face, lambda^m > 0).  Each pair is computed once with
+// operands chosen per lane: the face's traced reference state and wave speed,
+// and the negations that tell the two formulas apart, applied to sign bits on
+// the integer pipe.  A warp whose cells take different members of a pair (on
+// supersonic turbulent data, most warps) then issues the FP64 work once
+// instead of once for each branch.  Every member keeps its printed operation
+// order (E = T^m_L - T^0_L, the halvings exact), so the results are those of
+// the branches taken one by one, bit for bit up to the sign of a zero.
+// lm, l0, lp: lambda^m, lambda^0, lambda^p of the cell; tLm, tRp: its
+// reference-state integrals; sL, sR: the corrections, zero on entry.
+__device__ __forceinline__ void ppmc_corrections_fast(double rho, double a, double inv_a,
+                                                      double inv_a2, double inv_rho, double dtdx,
+                                                      double lm, double l0, double lp,
+                                                      const double dw[5], const double w6[5],
+                                                      const double tLm[5], const double tRp[5],
+                                                      double sL[5], double sR[5]) {
+  const double c23 = 2.0 / 3.0;
+  const bool cE = neg<false>(l0), cD = pos<false>(l0);
+  if (cE || cD) {
+    // E: T^m_L - (alpha^0/2)(dw + w6 (1 + (2/3) alpha^0)), into s_L;
+    // D: T^p_R - (beta^0/2)(dw - w6 (1 - (2/3) beta^0)), into s_R
+    const unsigned sm = cE ? 0u : 0x80000000u;
+    const double c = dtdx * l0;
+    const double k = fma(flip_sign(c23, sm), c, 1.0);
+    const double hc = half_bits(c);
+    double X[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      if (q == 1) continue;
+      X[q] = fma(-hc, fma(flip_sign(w6[q], sm), k, dw[q]), cE ? tLm[q] : tRp[q]);
+    }
+    const double x0 = fma(-X[4], inv_a2, X[0]);
+    sL[0] = cE ? x0 : 0.0;
+    sR[0] = cE ? 0.0 : x0;
+    sL[2] = cE ? X[2] : 0.0;
+    sR[2] = cE ? 0.0 : X[2];
+    sL[3] = cE ? X[3] : 0.0;
+    sR[3] = cE ? 0.0 : X[3];
+  }
+  const bool cB = neg<false>(lp), cC = pos<false>(lm);
+  if (cB || cC) {
+    // B: T^m_L - T^p_L (alpha^p), into s_L; C: T^p_R - T^m_R (beta^m), into s_R
+    const unsigned sm = cB ? 0u : 0x80000000u;
+    const double c = dtdx * (cB ? lp : lm);
+    const double k = fma(flip_sign(c23, sm), c, 1.0);
+    const double hc = half_bits(c);
+    const double X1 = fma(-hc, fma(flip_sign(w6[1], sm), k, dw[1]), cB ? tLm[1] : tRp[1]);
+    const double X4 = fma(-hc, fma(flip_sign(w6[4], sm), k, dw[4]), cB ? tLm[4] : tRp[4]);
+    const double rX1 = flip_sign(rho, sm) * X1;  // rho B1, or -(rho C1)
+    const double s0 = half_bits(fma(X4, inv_a2, rX1 * inv_a));
+    const double s1 = half_bits(fma(flip_sign(X4, sm), inv_a * inv_rho, X1));
+    const double s4 = half_bits(fma(rX1, a, X4));
+    const double t0 = (cB ? sL[0] : sR[0]) + s0;
+    sL[0] = cB ? t0 : sL[0];
+    sR[0] = cB ? sR[0] : t0;
+    sL[1] = cB ? s1 : 0.0;
+    sR[1] = cB ? 0.0 : s1;
+    sL[4] = cB ? s4 : 0.0;
+    sR[4] = cB ? 0.0 : s4;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // App. A.3: PPMC.  w_m, w_c, w_p: primitive averages of cells i-1, i, i+1;
 // s_m, s_c, s_p: their limited slopes; a, inv_a, inv_rho of cell i.  Outputs the
 // traced states at the left (WsL) and right (WsR) face of cell i, pressure
@@ -668,49 +741,56 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
   }
   T sL[5] = {T(0), T(0), T(0), T(0), T(0)};
   T sR[5] = {T(0), T(0), T(0), T(0), T(0)};
-  if (neg<S>(l0)) {  // contact and advected velocities reach the left face: E
-    const T a0 = dtdx * l0;
-    T E[5];
+  if constexpr (!S && sizeof(T) == 8) {
+    ppmc_corrections_fast(rho, a, inv_a, inv_a2, inv_rho, dtdx, lm, l0, lp, dw, w6, tLm, tRp,
+                          sL, sR);
+  } else {
+    if (neg<S>(l0)) {  // contact and advected velocities reach the left face: E
+      const T a0 = dtdx * l0;
+      T E[5];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) E[q] = tLm[q] - half<S>(a0) * (dw[q] + w6[q] * (T(1) + c23 * a0));
-    sL[0] = sL[0] + (E[0] - (S ? E[4] / (a * a) : E[4] * inv_a2));
-    sL[2] = sL[2] + E[2];
-    sL[3] = sL[3] + E[3];
-  }
-  if (neg<S>(lp)) {  // right acoustic wave reaches the left face: B
-    const T ap = dtdx * lp;
-    const T B1 = tLm[1] - half<S>(ap) * (dw[1] + w6[1] * (T(1) + c23 * ap));
-    const T B4 = tLm[4] - half<S>(ap) * (dw[4] + w6[4] * (T(1) + c23 * ap));
-    if constexpr (S) {
-      sL[0] = sL[0] + T(0.5) * (rho * B1 / a + B4 / (a * a));
-      sL[1] = sL[1] + T(0.5) * (B1 + B4 / (a * rho));
-    } else {
-      sL[0] = sL[0] + T(0.5) * (rho * B1 * inv_a + B4 * inv_a2);
-      sL[1] = sL[1] + T(0.5) * (B1 + B4 * (inv_a * inv_rho));
+      for (int q = 0; q < 5; ++q)
+        E[q] = tLm[q] - half<S>(a0) * (dw[q] + w6[q] * (T(1) + c23 * a0));
+      sL[0] = sL[0] + (E[0] - (S ? E[4] / (a * a) : E[4] * inv_a2));
+      sL[2] = sL[2] + E[2];
+      sL[3] = sL[3] + E[3];
     }
-    sL[4] = sL[4] + T(0.5) * (rho * B1 * a + B4);
-  }
-  if (pos<S>(lm)) {  // left acoustic wave reaches the right face: C
-    const T bm = dtdx * lm;
-    const T C1 = tRp[1] - half<S>(bm) * (dw[1] - w6[1] * (T(1) - c23 * bm));
-    const T C4 = tRp[4] - half<S>(bm) * (dw[4] - w6[4] * (T(1) - c23 * bm));
-    if constexpr (S) {
-      sR[0] = sR[0] + T(0.5) * (-(rho * C1) / a + C4 / (a * a));
-      sR[1] = sR[1] + T(0.5) * (C1 - C4 / (a * rho));
-    } else {
-      sR[0] = sR[0] + T(0.5) * (-(rho * C1) * inv_a + C4 * inv_a2);
-      sR[1] = sR[1] + T(0.5) * (C1 - C4 * (inv_a * inv_rho));
+    if (neg<S>(lp)) {  // right acoustic wave reaches the left face: B
+      const T ap = dtdx * lp;
+      const T B1 = tLm[1] - half<S>(ap) * (dw[1] + w6[1] * (T(1) + c23 * ap));
+      const T B4 = tLm[4] - half<S>(ap) * (dw[4] + w6[4] * (T(1) + c23 * ap));
+      if constexpr (S) {
+        sL[0] = sL[0] + T(0.5) * (rho * B1 / a + B4 / (a * a));
+        sL[1] = sL[1] + T(0.5) * (B1 + B4 / (a * rho));
+      } else {
+        sL[0] = sL[0] + T(0.5) * (rho * B1 * inv_a + B4 * inv_a2);
+        sL[1] = sL[1] + T(0.5) * (B1 + B4 * (inv_a * inv_rho));
+      }
+      sL[4] = sL[4] + T(0.5) * (rho * B1 * a + B4);
     }
-    sR[4] = sR[4] + T(0.5) * (-(rho * C1 * a) + C4);
-  }
-  if (pos<S>(l0)) {  // contact and advected velocities reach the right face: D
-    const T b0 = dtdx * l0;
-    T D[5];
+    if (pos<S>(lm)) {  // left acoustic wave reaches the right face: C
+      const T bm = dtdx * lm;
+      const T C1 = tRp[1] - half<S>(bm) * (dw[1] - w6[1] * (T(1) - c23 * bm));
+      const T C4 = tRp[4] - half<S>(bm) * (dw[4] - w6[4] * (T(1) - c23 * bm));
+      if constexpr (S) {
+        sR[0] = sR[0] + T(0.5) * (-(rho * C1) / a + C4 / (a * a));
+        sR[1] = sR[1] + T(0.5) * (C1 - C4 / (a * rho));
+      } else {
+        sR[0] = sR[0] + T(0.5) * (-(rho * C1) * inv_a + C4 * inv_a2);
+        sR[1] = sR[1] + T(0.5) * (C1 - C4 * (inv_a * inv_rho));
+      }
+      sR[4] = sR[4] + T(0.5) * (-(rho * C1 * a) + C4);
+    }
+    if (pos<S>(l0)) {  // contact and advected velocities reach the right face: D
+      const T b0 = dtdx * l0;
+      T D[5];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) D[q] = tRp[q] - half<S>(b0) * (dw[q] - w6[q] * (T(1) - c23 * b0));
-    sR[0] = sR[0] + (D[0] - (S ? D[4] / (a * a) : D[4] * inv_a2));
-    sR[2] = sR[2] + D[2];
-    sR[3] = sR[3] + D[3];
+      for (int q = 0; q < 5; ++q)
+        D[q] = tRp[q] - half<S>(b0) * (dw[q] - w6[q] * (T(1) - c23 * b0));
+      sR[0] = sR[0] + (D[0] - (S ? D[4] / (a * a) : D[4] * inv_a2));
+      sR[2] = sR[2] + D[2];
+      sR[3] = sR[3] + D[3];
+    }
   }
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
@@ -1417,6 +1497,61 @@ __device__ __forceinline__ void sample_shock(const RSide<T>& k, T pm, T um, T sg
   }
 }
 
+// The sampling at x/t = 0 in the fast FP64 path: the side the contact leaves
+// behind (left for u* >= 0, right otherwise) is sampled by one code path with
+// its operands chosen per lane, the side's state and the signs that mirror
+// the right-side formulas into the left-side ones (applied to sign bits on the
+// integer pipe).  On data where the contact moves either way within a warp
+// (supersonic turbulence) the warp then issues each sampling formula once
+// instead of once for each side.  Every test and formula is the side's own,
+// operation for operation: the head test u_R + a_R <= 0 is -u_R - a_R >= 0,
+// the tail test u* + a_R x >= 0 is -u* - a_R x <= 0, and so on.
+template <typename T>
+__device__ __forceinline__ void sample_fast(const RSide<T>& L, const RSide<T>& R, T pm, T um,
+                                            T xL, T xR, const GasT<T>& g, T& d, T& u, T& ps) {
+  const bool left = nonneg<false>(um);
+  const unsigned sm = left ? 0u : 0x80000000u;
+  const T kd = left ? L.d : R.d, ku = left ? L.u : R.u, kp = left ? L.p : R.p;
+  const T ka = left ? L.a : R.a, kip = left ? L.inv_p : R.inv_p;
+  const T x = left ? xL : xR;
+  if (!lt<false>(kp, pm)) {  // rarefaction
+    if (nonneg<false>(flip_sign(ku, sm) - ka)) {  // x/t = 0 ahead of the head: data state
+      d = kd; u = ku; ps = kp;
+      return;
+    }
+    const T tail = fma(-ka, x, flip_sign(um, sm));  // u* - a* (left), -(u* + a*) (right)
+    if (left ? neg<false>(tail) : nonpos<false>(tail)) {  // star state (see sample_raref)
+      if (g.k == 5) {
+        d = kd * (x * x * x);
+      } else if (g.k == 7) {
+        const T x2 = x * x;
+        d = kd * (x2 * x2 * x);
+      } else {
+        d = nr_div(kd * (pm * kip), x * x);
+      }
+      u = um;
+      ps = pm;
+    } else {  // inside the fan
+      const T a = g.two_gp1 * fma(flip_sign(g.half_gm1, sm), ku, ka);
+      T pd, pp;
+      fan_powers(nr_div(a, ka), g, pd, pp);
+      d = kd * pd;
+      ps = kp * pp;
+      u = flip_sign(a, sm);
+    }
+  } else {  // shock
+    const T r = pm * kip;
+    const T sk = fma(-flip_sign(ka, sm), nr_sqrt(g.sh_a * r + g.sh_b), ku);
+    if (nonneg<false>(flip_sign(sk, sm))) {  // the shock has not crossed x/t = 0
+      d = kd; u = ku; ps = kp;
+    } else {
+      d = nr_div(kd * (r + g.gm1_gp1), r * g.gm1_gp1 + T(1));
+      u = um;
+      ps = pm;
+    }
+  }
+}
+
 // Exact Riemann flux from primitive states in sweep order (inv_d = 1/rho of
 // each side, unused when strict); returns the status flags.  K = 5 or 7: the
 // fast FP64 form for z = 1/K (side_eval); K = 0: any gamma, strict or float.
@@ -1499,7 +1634,9 @@ __device__ __forceinline__ int riemann_exact_k(const T WL[5], const T WR[5], T i
   const T um = half<S>(L.u + R.u + fR - fL);
 
   T d, u, ps;
-  if (nonneg<S>(um)) {
+  if constexpr (!S && sizeof(T) == 8) {
+    sample_fast(L, R, pm, um, xL, xR, g, d, u, ps);
+  } else if (nonneg<S>(um)) {
     if (!lt<S>(L.p, pm)) {  // left rarefaction
       if (nonneg<S>(L.u - L.a)) {
         d = L.d; u = L.u; ps = L.p;

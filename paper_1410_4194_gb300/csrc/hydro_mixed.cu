@@ -7,9 +7,9 @@
 // the increments of the face state so that its pressure recovery has no
 // cancellation of total and kinetic energy (see half_step_side).
 // Float64, where the step's stability needs it:
-//   * primitives of the FP64 state: the internal energy E - rho v^2/2 (the
-//     cancellation of total and kinetic energy at high Mach), the pressure
-//     floor and the CFL time-step reduction;
+//   * primitives of the FP64 state: the internal energy, as rho E - |m|^2/2
+//     (the cancellation of total and kinetic energy at high Mach), the
+//     pressure floor and the CFL time-step reduction;
 //   * the conserved update (Eq. conserved_update), accumulated from the float
 //     CTU fluxes into the FP64 state.
 // Intermediates (primitives, face states, fluxes) are float, in float4
@@ -132,15 +132,19 @@ __device__ __forceinline__ void store_face(const Face5& A, long long c, const fl
 
 // What a cell keeps for the FP64 signal speed of the CFL condition.
 struct DtCand {
-  double m[3], p, r;  // momentum, pressure, 1/rho
-  float s;            // float estimate of max_d |v_d| + a; -1 for cells outside dt
+  double m[3], d, re;  // momentum, density, rho times the internal energy
+  float s;             // float estimate of max_d |v_d| + a; -1 for cells outside dt
 };
 
-// primitives in FP64 (ghosts by index remap, as in the FP64 path), stored as
-// float.  The FP64 work of a cell is 1/rho and the internal energy
-// E - |m|^2 (1/rho) / 2 (the cancellation of total and kinetic energy at high
-// Mach needs it); the velocities and the sound speed, which are stored as
-// float, are formed in float from the rounded operands (a few float ulps).
+// primitives from the FP64 state (ghosts by index remap, as in the FP64 path),
+// stored as float.  The cancellation of total and kinetic energy at high Mach
+// is taken in FP64: rho e = rho E - |m|^2/2, whose only rounding is that of
+// its fused multiply-add (|m|^2/2 exact).  The division of rho e by rho that
+// remains is well conditioned, so the pressure is (rho e)(gamma-1)/rho with
+// the float reciprocal of the rounded density (five FP64 instructions a cell,
+// where forming e = E - |m|^2 (1/rho)/2 needed an FP64 reciprocal first); the
+// velocities and the sound speed are formed in float from rounded operands.
+// Every stored value is within a few float ulps of its FP64 value.
 template <bool NOH>
 __device__ __forceinline__ void prims_mixed_body(const Geom& G, const BufsF& B, const BcDesc& bc,
                                                  const GasD& g, const GasF& gf, int want_dt,
@@ -158,15 +162,12 @@ __device__ __forceinline__ void prims_mixed_body(const Geom& G, const BufsF& B, 
     mf[d] = d2f(U[1 + d]);
     if (neg & (1 << d)) mf[d] = -mf[d];
   }
-  // 1/rho: float reciprocal of the rounded density refined by one Newton
-  // step r <- r + r (1 - rho r) in FP64 (relative error below 2^-44)
   const float df = d2f(U[0]);
   const float rf = __frcp_rn(df);
-  double r = f2d(rf);
-  r = fma(r, fma(-U[0], r, 1.0), r);
-  // FP64 internal energy E - |m|^2 / (2 rho) and the pressure floor
+  // FP64 rho e = rho E - |m|^2/2 (m2/2 exact), then the pressure and its floor
   const double m2 = fma(U[1], U[1], fma(U[2], U[2], U[3] * U[3]));
-  const double p = vmax<false>(g.gm1 * fma(-half_bits(m2), r, U[4]), kPFloor);  // m2/2 exact
+  const double re = fma(U[0], U[4], -half_bits(m2));
+  const double p = vmax<false>(re * f2d(gf.gm1 * rf), kPFloor);
   const float pf = d2f(p);
   const float af = sqrtf(gf.gamma * pf * rf);
   float vf[3];
@@ -183,25 +184,31 @@ __device__ __forceinline__ void prims_mixed_body(const Geom& G, const BufsF& B, 
     cand.s = m + af;
 #pragma unroll
     for (int d = 0; d < 3; ++d) cand.m[d] = U[1 + d];
-    cand.p = p;
-    cand.r = r;
+    cand.d = U[0];
+    cand.re = re;
   }
 }
 
-// FP64 signal speed max_d |v_d| + a of a cell, v = m (1/rho) and
-// a = sqrt(gamma p / rho) from a float reciprocal square root of x = a^2
-// refined by one Newton step, a = x y (1 + (1 - x y^2)/2) (relative error
-// ~1e-13).  Rounding is monotonic, so max_d |v_d| + a equals the largest of
-// the |v_d| + a.
+// FP64 signal speed max_d |v_d| + a of a cell: 1/rho from the float
+// reciprocal refined by two Newton steps (to FP64 precision), the floored
+// pressure (gamma-1)(rho e)(1/rho), v = m (1/rho), and a = sqrt(gamma p / rho)
+// from a float reciprocal square root of x = a^2 refined by one Newton step,
+// a = x y (1 + (1 - x y^2)/2) (relative error ~1e-13).  Rounding is
+// monotonic, so max_d |v_d| + a equals the largest of the |v_d| + a.  One
+// cell a block takes this path.
 __device__ __forceinline__ double signal_speed_fp64(const Geom& G, const GasD& g, const DtCand& c) {
-  const double x = g.gamma * c.p * c.r;
+  double r = f2d(__frcp_rn(d2f(c.d)));
+  r = fma(r, fma(-c.d, r, 1.0), r);
+  r = fma(r, fma(-c.d, r, 1.0), r);
+  const double p = vmax<false>(g.gm1 * (c.re * r), kPFloor);
+  const double x = g.gamma * p * r;
   const double y = f2d(rsqrtf(d2f(x)));
   const double xy = x * y;
   const double a = fma(0.5 * xy, fma(-xy, y, 1.0), xy);
   double vmaxabs = 0.0;
 #pragma unroll
   for (int d = 0; d < 3; ++d)
-    if (G.n[d] > 1) vmaxabs = max_nonneg(vmaxabs, fabs(c.m[d] * c.r));
+    if (G.n[d] > 1) vmaxabs = max_nonneg(vmaxabs, fabs(c.m[d] * r));
   return vmaxabs + a;
 }
 

@@ -319,9 +319,10 @@ __device__ __forceinline__ void riemann1_body(const Geom& G, const Bufs& B, cons
   } else {
     load_rot<D>(B.UL[D], G.ps, f, WL);
     load_rot<D>(B.UR[D], G.ps, f, WR);
-    idL = nr_rcp(WL[0]);
-    idR = nr_rcp(WR[0]);
+    idL = idR = 0.0;
     if constexpr (ROE) {
+      idL = nr_rcp(WL[0]);
+      idR = nr_rcp(WR[0]);
       prim2cons(WL, g, UL);
       prim2cons(WR, g, UR);
     }
@@ -329,8 +330,12 @@ __device__ __forceinline__ void riemann1_body(const Geom& G, const Bufs& B, cons
   if constexpr (ROE) {
     riemann_roe<S>(UL, UR, WL, WR, idL, idR, 0.0, g, F);
     B.eta[D][f] = h_eta<S>(WL, WR, idL, idR, g);
-  } else {
+  } else if constexpr (S) {
     fl = riemann_exact<S>(WL, WR, idL, idR, g, F);
+  } else {
+    // the face states are primitives: the solver needs 1/rho only for the
+    // sound speeds, which it forms without it
+    fl = riemann_exact<S, double, false>(WL, WR, idL, idR, g, F);
   }
   store_rot<D>(B.F1[D], G.ps, f, F);
   if (fl) atomicOr(rec_flags(B.rec), fl);
@@ -620,24 +625,26 @@ HYDRO_BATCH_WRAPPER(kb_ppmp, ppmp_body, 1)
 HYDRO_BATCH_WRAPPER(kb_plmc, plmc_body, 1)
 HYDRO_BATCH_WRAPPER(kb_plmp, plmp_body, 1)
 HYDRO_BATCH_WRAPPER(kb_pcm, pcm_body, 1)
-// The Riemann sets with their own register budgets, THR resident threads an SM
-// (with 128-thread blocks; 256-thread blocks round down to a multiple of 256),
-// by measurement on Sedov 256^3 and Mach-5 turbulence 256^3: the first set at
-// 1024 (64 registers), 1.8% faster than at 768 (80 registers); the second at
-// 896 (72 registers), 0.4-0.6% faster than at 768 and 1% faster than at 640
-// (96 registers); the reconstruction and slope kernels gain nothing from 640
-// or 896
-#define HYDRO_BATCH_WRAPPER_T(NAME, BODY, STAGE_IDX, THR)                                      \
+// The Riemann sets with their own register budgets, by measurement on Sedov
+// 256^3 and Mach-5 turbulence 256^3: the first set at 64 registers (1024
+// resident threads an SM), 1.8% faster than at 80 (768 threads); the second
+// at 72 (896 threads with 128-thread blocks, 768 with 256), 0.4-0.6% faster
+// than at 80 and 1% faster than at 96 (640 threads); the reconstruction and
+// slope kernels gain nothing from 640 or 896 threads.  The budget is a
+// register count, the same for both block sizes, so that both compile to the
+// same code and a grid's results do not depend on its block size (bit for
+// bit; a bound in resident threads would give 256-thread blocks 80 registers).
+#define HYDRO_BATCH_WRAPPER_R(NAME, BODY, STAGE_IDX, REGS)                                     \
   template <int D, bool S, int BS>                                                             \
-  __global__ void __launch_bounds__(BS, THR / BS) NAME(BatchLaunch L) {                       \
+  __global__ void __maxnreg__(REGS) NAME(BatchLaunch L) {                                      \
     const BatchItem it = batch_item(L);                                                        \
     const Box& box = it.d->box[STAGE_IDX][D];                                                  \
     if (it.t < (long long)box.n[0] * box.n[1] * box.n[2])                                      \
       BODY<D, S>(it.d->G, it.d->B, box, it.d->gd, it.t);                                       \
   }
-HYDRO_BATCH_WRAPPER_T(kb_riemann1, riemann1_body, 2, 1024)
-HYDRO_BATCH_WRAPPER_T(kb_riemann2, riemann2_body, 3, 896)
-#undef HYDRO_BATCH_WRAPPER_T
+HYDRO_BATCH_WRAPPER_R(kb_riemann1, riemann1_body, 2, 64)
+HYDRO_BATCH_WRAPPER_R(kb_riemann2, riemann2_body, 3, 72)
+#undef HYDRO_BATCH_WRAPPER_R
 HYDRO_BATCH_WRAPPER(kb_riemann1_roe, riemann1_roe_body, 2)
 HYDRO_BATCH_WRAPPER(kb_riemann2_roe, riemann2_roe_body, 3)
 #undef HYDRO_BATCH_WRAPPER

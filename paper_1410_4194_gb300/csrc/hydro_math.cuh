@@ -200,6 +200,26 @@ __device__ __forceinline__ double flip_sign(double x, unsigned smask) {
   split_bits(x, lo, hi);
   return join_bits(lo, hi ^ smask);
 }
+// |x| and, for the limiters, the sign of c given to a non-negative m (c < 0:
+// -m, else m) by sign-bit moves on the integer pipe.  An FP64 absolute value
+// or negation that the compiler cannot fold into an arithmetic instruction's
+// operand would otherwise be issued on the FP64 pipe as an add.  With S
+// (strict), and for float, the library operations.
+template <bool S, typename T>
+__device__ __forceinline__ T vabs(T x) {
+  if constexpr (S || sizeof(T) == 4) {
+    return xabs(x);
+  } else {
+    unsigned lo, hi;
+    split_bits(x, lo, hi);
+    return join_bits(lo, hi & 0x7fffffffu);
+  }
+}
+template <bool S, typename T>
+__device__ __forceinline__ T sign_of(T c, T m) {
+  if constexpr (S || sizeof(T) == 4) return neg<S>(c) ? -m : m;
+  else return flip_sign(m, neg<S>(c) ? 0x80000000u : 0u);
+}
 
 // Sign tests of a product x*y from the factors' sign bits and zero tests, on
 // the integer pipe: an FP64 multiply formed only for its sign costs a full slot
@@ -602,6 +622,14 @@ __device__ __forceinline__ void limited_slope(const T wm[5], const T wc[5], cons
     keep[q] = prod_pos<S>(xl[q], xr[q]);
     any = any || keep[q];
   }
+  if constexpr (!S && sizeof(T) == 8) {
+    // no characteristic slope kept: the back-projection of zeros is +0
+    if (!any) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) dw[q] = T(0);
+      return;
+    }
+  }
   T xi[5] = {T(0), T(0), T(0), T(0), T(0)};
   // the centred difference is projected only where the limiter keeps a slope
   // (in FP64; in strict mode and in float always, as printed)
@@ -612,8 +640,9 @@ __device__ __forceinline__ void limited_slope(const T wm[5], const T wc[5], cons
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       if (keep[q]) {
-        const T m = vmin<S>(vmin<S>(xabs(xc[q]), twice<S>(xabs(xl[q]))), twice<S>(xabs(xr[q])));
-        xi[q] = neg<S>(xc[q]) ? -m : m;
+        const T m = vmin<S>(vmin<S>(vabs<S>(xc[q]), twice<S>(vabs<S>(xl[q]))),
+                            twice<S>(vabs<S>(xr[q])));
+        xi[q] = sign_of<S>(xc[q], m);
       }
     }
   }
@@ -634,16 +663,21 @@ __device__ __forceinline__ void limited_slope(const T wm[5], const T wc[5], cons
 // the integer pipe.  A warp whose cells take different members of a pair (on
 // supersonic turbulent data, most warps) then issues the FP64 work once
 // instead of once for each branch.  Every member keeps its printed operation
-// order (E = T^m_L - T^0_L, the halvings exact), so the results are those of
-// the branches taken one by one, bit for bit up to the sign of a zero.
-// lm, l0, lp: lambda^m, lambda^0, lambda^p of the cell; tLm, tRp: its
-// reference-state integrals; sL, sR: the corrections, zero on entry.
+// order (E = T^m_L - T^0_L, the halvings exact).  The corrections are added
+// to the reference states in place, contact term first, each where it applies
+// (a face state no correction reaches takes no addition of zero), so a face
+// that both a contact and an acoustic term reach sums them one after the
+// other rather than first with each other.
+// lm, l0, lp: lambda^m, lambda^0, lambda^p of the cell; the reference-state
+// integrals are T^m_L = hAm gM and T^p_R = hBp gP; WL, WR: the reference
+// states at the left and right face, corrected on return.
 __device__ __forceinline__ void ppmc_corrections_fast(double rho, double a, double inv_a,
                                                       double inv_a2, double inv_rho, double dtdx,
                                                       double lm, double l0, double lp,
                                                       const double dw[5], const double w6[5],
-                                                      const double tLm[5], const double tRp[5],
-                                                      double sL[5], double sR[5]) {
+                                                      double hAm, double hBp, const double gM[5],
+                                                      const double gP[5], double WL[5],
+                                                      double WR[5]) {
   const double c23 = 2.0 / 3.0;
   const bool cE = neg<false>(l0), cD = pos<false>(l0);
   if (cE || cD) {
@@ -657,15 +691,17 @@ __device__ __forceinline__ void ppmc_corrections_fast(double rho, double a, doub
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       if (q == 1) continue;
-      X[q] = fma(-hc, fma(flip_sign(w6[q], sm), k, dw[q]), cE ? tLm[q] : tRp[q]);
+      const double t = (cE ? hAm : hBp) * (cE ? gM[q] : gP[q]);  // T^m_L or T^p_R
+      X[q] = fma(-hc, fma(flip_sign(w6[q], sm), k, dw[q]), t);
     }
-    const double x0 = fma(-X[4], inv_a2, X[0]);
-    sL[0] = cE ? x0 : 0.0;
-    sR[0] = cE ? 0.0 : x0;
-    sL[2] = cE ? X[2] : 0.0;
-    sR[2] = cE ? 0.0 : X[2];
-    sL[3] = cE ? X[3] : 0.0;
-    sR[3] = cE ? 0.0 : X[3];
+    X[0] = fma(-X[4], inv_a2, X[0]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q == 1) continue;
+      const double v = (cE ? WL[q] : WR[q]) + X[q];
+      WL[q] = cE ? v : WL[q];
+      WR[q] = cE ? WR[q] : v;
+    }
   }
   const bool cB = neg<false>(lp), cC = pos<false>(lm);
   if (cB || cC) {
@@ -674,19 +710,21 @@ __device__ __forceinline__ void ppmc_corrections_fast(double rho, double a, doub
     const double c = dtdx * (cB ? lp : lm);
     const double k = fma(flip_sign(c23, sm), c, 1.0);
     const double hc = half_bits(c);
-    const double X1 = fma(-hc, fma(flip_sign(w6[1], sm), k, dw[1]), cB ? tLm[1] : tRp[1]);
-    const double X4 = fma(-hc, fma(flip_sign(w6[4], sm), k, dw[4]), cB ? tLm[4] : tRp[4]);
+    const double h = cB ? hAm : hBp;
+    const double X1 = fma(-hc, fma(flip_sign(w6[1], sm), k, dw[1]), h * (cB ? gM[1] : gP[1]));
+    const double X4 = fma(-hc, fma(flip_sign(w6[4], sm), k, dw[4]), h * (cB ? gM[4] : gP[4]));
     const double rX1 = flip_sign(rho, sm) * X1;  // rho B1, or -(rho C1)
-    const double s0 = half_bits(fma(X4, inv_a2, rX1 * inv_a));
-    const double s1 = half_bits(fma(flip_sign(X4, sm), inv_a * inv_rho, X1));
-    const double s4 = half_bits(fma(rX1, a, X4));
-    const double t0 = (cB ? sL[0] : sR[0]) + s0;
-    sL[0] = cB ? t0 : sL[0];
-    sR[0] = cB ? sR[0] : t0;
-    sL[1] = cB ? s1 : 0.0;
-    sR[1] = cB ? 0.0 : s1;
-    sL[4] = cB ? s4 : 0.0;
-    sR[4] = cB ? 0.0 : s4;
+    double sc[5];
+    sc[0] = half_bits(fma(X4, inv_a2, rX1 * inv_a));
+    sc[1] = half_bits(fma(flip_sign(X4, sm), inv_a * inv_rho, X1));
+    sc[4] = half_bits(fma(rX1, a, X4));
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      if (q == 2 || q == 3) continue;
+      const double v = (cB ? WL[q] : WR[q]) + sc[q];
+      WL[q] = cB ? v : WL[q];
+      WR[q] = cB ? WR[q] : v;
+    }
   }
 }
 
@@ -716,8 +754,16 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
       L = wi;
       R = wi;
     }
-    if (diffs_prod_neg<S>(R, L, L, T(3) * wi - T(2) * R)) L = T(3) * wi - T(2) * R;
-    if (diffs_prod_neg<S>(R, L, T(3) * wi - T(2) * L, R)) R = T(3) * wi - T(2) * L;
+    if constexpr (!S && sizeof(T) == 8) {
+      // 3 w_i - 2 W as one FMA on the exact doubling (a single rounding)
+      const T sl = fma(T(3), wi, -twice_bits(R));
+      if (diffs_prod_neg<S>(R, L, L, sl)) L = sl;
+      const T sr = fma(T(3), wi, -twice_bits(L));
+      if (diffs_prod_neg<S>(R, L, sr, R)) R = sr;
+    } else {
+      if (diffs_prod_neg<S>(R, L, L, T(3) * wi - T(2) * R)) L = T(3) * wi - T(2) * R;
+      if (diffs_prod_neg<S>(R, L, T(3) * wi - T(2) * L, R)) R = T(3) * wi - T(2) * L;
+    }
     L = vmin<S>(vmax<S>(wi, w_m[q]), vmax<S>(vmin<S>(wi, w_m[q]), L));
     R = vmin<S>(vmax<S>(wi, w_p[q]), vmax<S>(vmin<S>(wi, w_p[q]), R));
     WsL[q] = L;
@@ -732,19 +778,34 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
   const T c23 = T(2.0 / 3.0);
   const T inv_a2 = inv_a * inv_a;
   // integral of the parabola over the domain of dependence of the fastest
-  // left-going (m) and right-going (p) waves: the reference states
-  T tLm[5], tRp[5];
+  // left-going (m) and right-going (p) waves, T^m_L = (alpha^m/2) gM and
+  // T^p_R = (beta^p/2) gP: the reference states W_L - T^m_L, W_R - T^p_R
+  T gM[5], gP[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    tLm[q] = half<S>(am) * (dw[q] + w6[q] * (T(1) + c23 * am));
-    tRp[q] = half<S>(bp) * (dw[q] - w6[q] * (T(1) - c23 * bp));
+    gM[q] = dw[q] + w6[q] * (T(1) + c23 * am);
+    gP[q] = dw[q] - w6[q] * (T(1) - c23 * bp);
   }
-  T sL[5] = {T(0), T(0), T(0), T(0), T(0)};
-  T sR[5] = {T(0), T(0), T(0), T(0), T(0)};
   if constexpr (!S && sizeof(T) == 8) {
-    ppmc_corrections_fast(rho, a, inv_a, inv_a2, inv_rho, dtdx, lm, l0, lp, dw, w6, tLm, tRp,
-                          sL, sR);
+    // fast FP64: each reference state as one FMA (the product T^m_L is
+    // formed only where a correction needs it)
+    const T hAm = half<S>(am), hBp = half<S>(bp);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      WsL[q] = fma(-hAm, gM[q], WsL[q]);
+      WsR[q] = fma(-hBp, gP[q], WsR[q]);
+    }
+    ppmc_corrections_fast(rho, a, inv_a, inv_a2, inv_rho, dtdx, lm, l0, lp, dw, w6, hAm, hBp, gM,
+                          gP, WsL, WsR);
   } else {
+    T tLm[5], tRp[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      tLm[q] = half<S>(am) * gM[q];
+      tRp[q] = half<S>(bp) * gP[q];
+    }
+    T sL[5] = {T(0), T(0), T(0), T(0), T(0)};
+    T sR[5] = {T(0), T(0), T(0), T(0), T(0)};
     if (neg<S>(l0)) {  // contact and advected velocities reach the left face: E
       const T a0 = dtdx * l0;
       T E[5];
@@ -791,11 +852,11 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
       sR[2] = sR[2] + D[2];
       sR[3] = sR[3] + D[3];
     }
-  }
 #pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    WsL[q] = (WsL[q] - tLm[q]) + sL[q];
-    WsR[q] = (WsR[q] - tRp[q]) + sR[q];
+    for (int q = 0; q < 5; ++q) {
+      WsL[q] = (WsL[q] - tLm[q]) + sL[q];
+      WsR[q] = (WsR[q] - tRp[q]) + sR[q];
+    }
   }
   WsL[4] = vmax<S>(WsL[4], T(kPFloor));
   WsR[4] = vmax<S>(WsR[4], T(kPFloor));
@@ -818,8 +879,8 @@ __device__ __forceinline__ void prim_slope(const T wm[5], const T wc[5], const T
       const T dL = wc[q] - wm[q];
       const T dR = wp[q] - wc[q];
       const T dC = half<S>(wp[q] - wm[q]);
-      const T m = vmin<S>(vmin<S>(xabs(dC), twice<S>(xabs(dL))), twice<S>(xabs(dR)));
-      s = neg<S>(dC) ? -m : m;
+      const T m = vmin<S>(vmin<S>(vabs<S>(dC), twice<S>(vabs<S>(dL))), twice<S>(vabs<S>(dR)));
+      s = sign_of<S>(dC, m);
     }
     dw[q] = s;
   }
@@ -948,7 +1009,7 @@ __device__ __forceinline__ T flatten_tilde(const T p[5], T um, T up) {
   } else {
     if (lt<S>(T(3) * xabs(num), vmin<S>(p[3], p[1])) || pos<S>(up - um)) return T(0);
     const T den = p[4] - p[0];
-    if (bits_equal(xabs(den), T(0))) return pos<S>(num) ? T(1) : T(0);
+    if (bits_equal(vabs<S>(den), T(0))) return pos<S>(num) ? T(1) : T(0);
     const T St = nr_div(num, den);
     return vmax<S>(T(0), vmin<S>(T(1), T(10) * (St - T(0.75))));
   }
@@ -998,7 +1059,7 @@ __device__ __forceinline__ void ppmp_states(const T w[7][5], const T sm[5], cons
         eta = tmax(T(0), tmin(T(20) * eta_t - T(1), T(1)));
       }
     } else {
-      const T dr = xabs(wip[0] - wim[0]), mr = vmin<S>(wip[0], wim[0]);
+      const T dr = vabs<S>(wip[0] - wim[0]), mr = vmin<S>(wip[0], wim[0]);
       const T dp = xabs(wip[4] - wim[4]), mp = vmin<S>(wip[4], wim[4]);
       const T e2m = wi[0] - T(2) * wim[0] + w[1][0];
       const T e2p = w[5][0] - T(2) * wip[0] + wi[0];
@@ -1042,8 +1103,15 @@ __device__ __forceinline__ void ppmp_states(const T w[7][5], const T sm[5], cons
       L = wi[q];
       R = wi[q];
     }
-    if (diffs_prod_neg<S>(R, L, L, T(3) * wi[q] - T(2) * R)) L = T(3) * wi[q] - T(2) * R;
-    if (diffs_prod_neg<S>(R, L, T(3) * wi[q] - T(2) * L, R)) R = T(3) * wi[q] - T(2) * L;
+    if constexpr (!S && sizeof(T) == 8) {  // one FMA on the exact doubling, as in PPMC
+      const T sl = fma(T(3), wi[q], -twice_bits(R));
+      if (diffs_prod_neg<S>(R, L, L, sl)) L = sl;
+      const T sr = fma(T(3), wi[q], -twice_bits(L));
+      if (diffs_prod_neg<S>(R, L, sr, R)) R = sr;
+    } else {
+      if (diffs_prod_neg<S>(R, L, L, T(3) * wi[q] - T(2) * R)) L = T(3) * wi[q] - T(2) * R;
+      if (diffs_prod_neg<S>(R, L, T(3) * wi[q] - T(2) * L, R)) R = T(3) * wi[q] - T(2) * L;
+    }
     WL[q] = L;
     WR[q] = R;
     dw[q] = R - L;
@@ -1239,8 +1307,8 @@ __device__ __forceinline__ void riemann_roe(const T UL[5], const T UR[5], const 
     xi3 = dU[0] * (T(1) - Na * gp * V2) + (dU[1] * u + dU[2] * v + dU[3] * w - dU[4]) * (gp * ia2);
   const T xi4 = dU[0] * Na * (T(0.5) * gp * V2 - u * a) - dU[1] * Na * (gp * u - a) -
                 dU[2] * Na * gp * v - dU[3] * Na * gp * w + dU[4] * Na * gp;
-  const T alm = vmax<S>(xabs(lm), etaH), al0 = vmax<S>(xabs(l0), etaH),
-          alp = vmax<S>(xabs(lp), etaH);
+  const T alm = vmax<S>(vabs<S>(lm), etaH), al0 = vmax<S>(vabs<S>(l0), etaH),
+          alp = vmax<S>(vabs<S>(lp), etaH);
   const T C0 = xi0 * alm, C1 = xi1 * al0, C2 = xi2 * al0, C3 = xi3 * al0, C4 = xi4 * alp;
   T s[5];
   s[0] = C0 + C3 + C4;
@@ -1283,7 +1351,8 @@ __device__ __forceinline__ T h_eta(const T WL[5], const T WR[5], T inv_dL, T inv
     aL = nr_sqrt(g.gamma * WL[4] * inv_dL);
     aR = nr_sqrt(g.gamma * WR[4] * inv_dR);
   }
-  return half<S>(vmax<S>(xabs((WR[1] + aR) - (WL[1] + aL)), xabs((WR[1] - aR) - (WL[1] - aL))));
+  return half<S>(vmax<S>(vabs<S>((WR[1] + aR) - (WL[1] + aL)),
+                         vabs<S>((WR[1] - aR) - (WL[1] - aL))));
 }
 
 // ---------------------------------------------------------------------------
@@ -1352,7 +1421,10 @@ __device__ __forceinline__ void side_f_only(T p, const RSide<T>& s, const GasT<T
   }
 }
 
-template <bool S, typename T>
+// INV: inv_d = 1/rho is given; without it (fast FP64) the sound speed is
+// a = x / sqrt(x rho) with x = gamma p, as a product with a reciprocal square
+// root (nine FP64 issue slots against eleven for 1/rho and then sqrt(x/rho))
+template <bool S, typename T, bool INV = true>
 __device__ __forceinline__ void make_side(const T W[5], T inv_d, const GasT<T>& g, RSide<T>& s) {
   s.d = W[0];
   s.u = W[1];
@@ -1363,7 +1435,12 @@ __device__ __forceinline__ void make_side(const T W[5], T inv_d, const GasT<T>& 
     s.A = T(2) / (g.gp1 * s.d);
     s.inv_A = T(0);
   } else {
-    s.a = nr_sqrt(g.gamma * s.p * inv_d);
+    if constexpr (INV || sizeof(T) == 4) {
+      s.a = nr_sqrt(g.gamma * s.p * inv_d);
+    } else {
+      const T x = g.gamma * s.p;
+      s.a = x * nr_rsqrt(x * s.d);
+    }
     s.inv_p = nr_rcp(s.p);
     s.A = g.two_gp1 * inv_d;
     s.inv_A = g.half_gp1 * s.d;
@@ -1555,12 +1632,12 @@ __device__ __forceinline__ void sample_fast(const RSide<T>& L, const RSide<T>& R
 // Exact Riemann flux from primitive states in sweep order (inv_d = 1/rho of
 // each side, unused when strict); returns the status flags.  K = 5 or 7: the
 // fast FP64 form for z = 1/K (side_eval); K = 0: any gamma, strict or float.
-template <bool S, typename T, int K>
+template <bool S, typename T, int K, bool INV = true>
 __device__ __forceinline__ int riemann_exact_k(const T WL[5], const T WR[5], T inv_dL, T inv_dR,
                                                const GasT<T>& g, T F[5]) {
   RSide<T> L, R;
-  make_side<S>(WL, inv_dL, g, L);
-  make_side<S>(WR, inv_dR, g, R);
+  make_side<S, T, INV>(WL, inv_dL, g, L);
+  make_side<S, T, INV>(WR, inv_dR, g, R);
   // primitive-variable estimate, then the two-shock estimate as Newton start
   T pt = half<S>(L.p + R.p) +
          half<S>(half<S>(half<S>(L.u - R.u))) * (L.d + R.d) * (L.a + R.a);  // (1/8) du, exact
@@ -1598,7 +1675,7 @@ __device__ __forceinline__ int riemann_exact_k(const T WL[5], const T WR[5], T i
       done = T(2) * xabs(pn - p) / xabs(pn + p) < T(kNewtonTol);
     else
       // 2|d| < tol |s| as |d| < (tol/2) |s|: both sides halved exactly
-      done = lt<S>(xabs(pn - p), T(0.5 * kNewtonTol) * xabs(pn + p));
+      done = lt<S>(vabs<S>(pn - p), T(0.5 * kNewtonTol) * xabs(pn + p));
     if constexpr (sizeof(T) == 4) {
       // In float the residual f_L + f_R + u_R - u_L carries the rounding error of
       // its terms; near the root the Newton steps that noise produces can stay
@@ -1676,13 +1753,14 @@ __device__ __forceinline__ int riemann_exact_k(const T WL[5], const T WR[5], T i
 // and t^7 add two roundings (the fast/strict difference after 10 steps grew
 // from 2e-15 to 1.1e-14 of a variable's scale), and a second copy of the solver
 // in every Riemann kernel cost 0.2-0.3% on Sedov 256^3 (code size).
-template <bool S = false, typename T>
+// INV = false: inv_dL, inv_dR are not given (fast FP64 only; see make_side).
+template <bool S = false, typename T, bool INV = true>
 __device__ __forceinline__ int riemann_exact(const T WL[5], const T WR[5], T inv_dL, T inv_dR,
                                              const GasT<T>& g, T F[5]) {
   if constexpr (!S && sizeof(T) == 8) {
-    if (g.k == 5) return riemann_exact_k<false, T, 5>(WL, WR, inv_dL, inv_dR, g, F);
+    if (g.k == 5) return riemann_exact_k<false, T, 5, INV>(WL, WR, inv_dL, inv_dR, g, F);
   }
-  return riemann_exact_k<S, T, 0>(WL, WR, inv_dL, inv_dR, g, F);
+  return riemann_exact_k<S, T, 0, INV>(WL, WR, inv_dL, inv_dR, g, F);
 }
 
 }  // namespace hydro

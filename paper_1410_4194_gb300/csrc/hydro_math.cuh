@@ -1638,6 +1638,12 @@ __device__ __forceinline__ int riemann_exact_k(const T WL[5], const T WR[5], T i
   RSide<T> L, R;
   make_side<S, T, INV>(WL, inv_dL, g, L);
   make_side<S, T, INV>(WR, inv_dR, g, R);
+  if constexpr (K == 5) {
+    // gamma = 5/3: B_k = p_k (gamma-1)/(gamma+1) = p_k/4 exactly, by moving
+    // the exponent (p_k is at least the 1e-20 floor, a normal number)
+    L.B = half_bits(half_bits(L.p));
+    R.B = half_bits(half_bits(R.p));
+  }
   // primitive-variable estimate, then the two-shock estimate as Newton start
   T pt = half<S>(L.p + R.p) +
          half<S>(half<S>(half<S>(L.u - R.u))) * (L.d + R.d) * (L.a + R.a);  // (1/8) du, exact
@@ -1737,13 +1743,20 @@ __device__ __forceinline__ int riemann_exact_k(const T WL[5], const T WR[5], T i
   const bool left = nonneg<S>(u);
   const T v = left ? WL[2] : WR[2];
   const T w = left ? WL[3] : WR[3];
-  const T E = (S ? ps / g.gm1 : ps * g.inv_gm1) + half<S>(d) * (u * u + v * v + w * w);
+  T Ep;  // E + p
+  if constexpr (!S && sizeof(T) == 8) {
+    // E + p = p gamma/(gamma-1) + rho V^2/2, gamma/(gamma-1) = fan_p/2 exactly
+    Ep = fma(ps, half<S>(g.fan_p), half<S>(d) * (u * u + v * v + w * w));
+  } else {
+    const T E = (S ? ps / g.gm1 : ps * g.inv_gm1) + half<S>(d) * (u * u + v * v + w * w);
+    Ep = E + ps;
+  }
   const T mf = d * u;
   F[0] = mf;
   F[1] = mf * u + ps;
   F[2] = mf * v;
   F[3] = mf * w;
-  F[4] = (E + ps) * u;
+  F[4] = Ep * u;
   return flags;
 }
 

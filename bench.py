@@ -76,14 +76,14 @@ ALGORITHMIC_FLOPS = {
 
 # The FP64 part of the mixed-precision stages, flops per unit, from the kernels'
 # own FP64 arithmetic (everything else in them is float; a fused multiply-add
-# counts 2): the primitive stage forms 1/rho by one Newton step (2 FMA),
-# |m|^2 (1 multiply + 2 FMA) and p = (gamma-1) (E - |m|^2/rho/2) (1 multiply
-# + 1 FMA; the halving is integer arithmetic), 12 flops a padded cell; the
-# update converts the float-float flux sum to a double in integer arithmetic
-# and applies it with 1 FMA a variable, 10 flops a cell; the Riemann stages,
-# the reconstruction and the transverse half-step are float.
+# counts 2): the primitive stage forms |m|^2 (1 multiply + 2 FMA), rho E -
+# |m|^2/2 (1 FMA; the halving is integer arithmetic) and its product with
+# (gamma-1)/rho taken in float (1 multiply), 8 flops a padded cell; the update
+# converts the float-float flux sum to a double in integer arithmetic and
+# applies it with 1 FMA a variable, 10 flops a cell; the Riemann stages, the
+# reconstruction and the transverse half-step are float.
 def mixed_fp64_flops(active_axes):
-    return {"riemann2": 0, "riemann1": 0, "ppmc": 0, "update": 10, "prims": 12}
+    return {"riemann2": 0, "riemann1": 0, "ppmc": 0, "update": 10, "prims": 8}
 
 # Algorithmic HBM bytes per unit of each stage's kernel (every plane read and
 # written once; stencil neighbours come from cache): FP64 intermediates are
@@ -120,24 +120,24 @@ _FP64_SRC = ["hydro_fp64_fast.cu", "hydro_internal.h", "hydro_kernels.cuh", "hyd
 _MIXED_SRC = ["hydro_ffsum.cuh", "hydro_internal.h", "hydro_kernels.cuh", "hydro_math.cuh",
               "hydro_mixed.cu"]
 NCU_TRAFFIC = {
-    ("fp64", "riemann2"): {"bytes_per_unit": 204.77, "digest": "b7950d09f77fb953", "bs": 128,
+    ("fp64", "riemann2"): {"bytes_per_unit": 207.1, "digest": "171e5803e22b43be", "bs": 128,
                            "sources": _FP64_SRC},
-    ("fp64", "ppmc"): {"bytes_per_unit": 188.23, "digest": "b7950d09f77fb953", "bs": 128,
+    ("fp64", "ppmc"): {"bytes_per_unit": 184.5, "digest": "171e5803e22b43be", "bs": 128,
                        "sources": _FP64_SRC},
-    ("fp64", "riemann1"): {"bytes_per_unit": 119.71, "digest": "b7950d09f77fb953", "bs": 128,
+    ("fp64", "riemann1"): {"bytes_per_unit": 121.3, "digest": "171e5803e22b43be", "bs": 128,
                            "sources": _FP64_SRC},
-    ("fp64", "slopes"): {"bytes_per_unit": 100.93, "digest": "b7950d09f77fb953", "bs": 128,
+    ("fp64", "slopes"): {"bytes_per_unit": 99.6, "digest": "171e5803e22b43be", "bs": 128,
                          "sources": _FP64_SRC},
-    ("mixed", "riemann2"): {"bytes_per_unit": 99.71, "digest": "19b7ab523887e7f2", "bs": 128,
+    ("mixed", "riemann2"): {"bytes_per_unit": 99.7, "digest": "1b593b26c2ac44c4", "bs": 128,
                             "sources": _MIXED_SRC},
-    ("mixed", "update"): {"bytes_per_unit": 137.86, "digest": "19b7ab523887e7f2", "bs": 128,
+    ("mixed", "update"): {"bytes_per_unit": 137.9, "digest": "1b593b26c2ac44c4", "bs": 128,
                           "sources": _MIXED_SRC},
     # the x sweep (one thread a cell, 62.6 B) and the y, z sweeps (segments, 64.5 B)
-    ("mixed", "ppmc"): {"bytes_per_unit": 63.9, "digest": "19b7ab523887e7f2", "bs": 128,
+    ("mixed", "ppmc"): {"bytes_per_unit": 63.9, "digest": "1b593b26c2ac44c4", "bs": 128,
                         "sources": _MIXED_SRC},
-    ("mixed", "riemann1"): {"bytes_per_unit": 54.93, "digest": "19b7ab523887e7f2", "bs": 128,
+    ("mixed", "riemann1"): {"bytes_per_unit": 54.9, "digest": "1b593b26c2ac44c4", "bs": 128,
                             "sources": _MIXED_SRC},
-    ("mixed", "prims"): {"bytes_per_unit": 58.91, "digest": "19b7ab523887e7f2", "bs": 128,
+    ("mixed", "prims"): {"bytes_per_unit": 59.3, "digest": "1b593b26c2ac44c4", "bs": 128,
                          "sources": _MIXED_SRC},
 }
 

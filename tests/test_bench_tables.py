@@ -21,12 +21,12 @@ def test_flop_table_matches_counting_oracle(name):
 
 
 def test_mixed_tables_by_construction():
-    """Mixed precision: FP64 only in the primitives (12 flops) and the update
+    """Mixed precision: FP64 only in the primitives (8 flops) and the update
     (10); the step's algorithmic HBM bytes per cell update add up the stages'."""
     sys.path.insert(0, ROOT)
     import bench
     f3 = bench.mixed_fp64_flops(3)
-    assert f3["riemann2"] == 0 and f3["update"] == 10 and f3["prims"] == 12
+    assert f3["riemann2"] == 0 and f3["update"] == 10 and f3["prims"] == 8
     b = bench.ALGORITHMIC_BYTES["mixed"]
     assert bench.mixed_bytes_per_cell_update(3) == (b["prims"] + b["update"]
                                                     + 3 * (b["ppmc"] + b["riemann1"]

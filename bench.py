@@ -43,6 +43,9 @@ if ROOT not in sys.path:
 
 METRIC = "cell-updates/s on 1 GB300 (CTU+PPM+exact RS), FP64 vs mixed/batched at matched L1"
 UNIT = "cell-updates/s"
+# independent grids (or batches) the end-to-end measurement rotates over: one
+# is uploaded, one steps and one is downloaded at a time
+E2E_PIPELINE = 3
 
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 2070 MHz x 2 FP64 FMA
 # per clock per SM x 2 flops per FMA (NVIDIA's nominal 1.25 TFLOP/s).
@@ -477,47 +480,54 @@ def measure_single(w, precision, steps, warmup, cfl, ws, local, recon="ppmc", so
 
     # ---- end to end through the public API with host buffers ----------------
     # Every step uploads its input state from pinned host memory, steps, and
-    # downloads the resulting state.  Steps alternate between two grids on two
-    # streams (the asynchronous API), so one grid's copies overlap the other's
-    # step, as a pipeline of independent problems would run.
+    # downloads the resulting state.  Steps rotate over E2E_PIPELINE grids on as
+    # many streams (the asynchronous API), so that the host-to-device copy of
+    # one grid, the step of another and the device-to-host copy of a third run
+    # at once, as a pipeline of independent problems would run.
     rec["e2e"] = None
     if e2e:
         import torch.distributed as dist
-        out_host = [torch.empty_like(u_host).pin_memory() for _ in range(2)]
-        stream2 = torch.cuda.Stream()
-        g2 = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], precision=prec,
-                        stream=stream2, recon=RECON_CODES[recon], solver=SOLVER_CODES[solver])
-        for face, prim in (w.get("inflow") or {}).items():
-            g2.set_inflow(face, prim)
-        pipe = [g, g2]
+        npipe = E2E_PIPELINE
+        out_host = [torch.empty_like(u_host).pin_memory() for _ in range(npipe)]
+        pipe, streams = [g], [stream]
+        for _ in range(npipe - 1):
+            sk = torch.cuda.Stream()
+            gk = hydro.Grid(nx, ny, nz, w["dx"], w["gamma"], w["bc"], precision=prec,
+                            stream=sk, recon=RECON_CODES[recon], solver=SOLVER_CODES[solver])
+            for face, prim in (w.get("inflow") or {}).items():
+                gk.set_inflow(face, prim)
+            pipe.append(gk)
+            streams.append(sk)
 
         def e2e_step(k):
-            gk = pipe[k % 2]
+            gk = pipe[k % npipe]
             gk.set_state_async(u_host)
             gk.step_async(cfl)
-            gk.get_state_async(out_host[k % 2])
+            gk.get_state_async(out_host[k % npipe])
 
-        e2e_step(0)
-        e2e_step(1)
-        g.sync()
-        g2.sync()
-        ke = max(2, min(steps, 10))
+        for k in range(npipe):
+            e2e_step(k)
+        for gk in pipe:
+            gk.sync()
+        ke = max(npipe, min(steps, 12))
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        eb = torch.cuda.Event()
         e0.record(stream)
-        stream2.wait_event(e0)
+        for sk in streams[1:]:
+            sk.wait_event(e0)
         for k in range(ke):
             e2e_step(k)
-        eb.record(stream2)
-        stream.wait_event(eb)
+        for sk in streams[1:]:
+            eb = torch.cuda.Event()
+            eb.record(sk)
+            stream.wait_event(eb)
         e1.record(stream)
-        g.sync()
-        g2.sync()
+        for gk in pipe:
+            gk.sync()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         te = max_over_ranks(e0.elapsed_time(e1), ws)
@@ -525,9 +535,10 @@ def measure_single(w, precision, steps, warmup, cfl, ws, local, recon="ppmc", so
                       "h2d_bytes_per_step": int(u_host.numel() * 8),
                       "d2h_bytes_per_step": int(out_host[0].numel() * 8), "steps": ke,
                       "host_wall_s": wall,
-                      "pipeline": "2 grids on 2 streams: one grid's copies overlap the "
-                                  "other's step"}
-        g2.close()
+                      "pipeline": "%d grids on %d streams: one grid's upload, another's step "
+                                  "and a third's download overlap" % (npipe, npipe)}
+        for gk in pipe[1:]:
+            gk.close()
     active = sum(1 for n in (nx, ny, nz) if n > 1)
     rec["roofline"] = single_roofline(stages, precision, w["key"], recon, solver, active,
                                       g.block_size(), fp64_live, clocks.get("sm_mhz"))
@@ -577,56 +588,65 @@ def measure_batch(grids, desc, precision, steps, warmup, cfl, ws, local, e2e=Tru
     value = replicas_value(ncells, steps, ws, ms)
     states = [b.get_state(i) for i in range(len(grids))] if keep_states else None
     # end to end: every step uploads every grid's state from pinned host memory,
-    # steps and downloads the states; steps alternate between two batches on two
-    # streams (the asynchronous API), each synced while the other's work is
-    # queued, so one batch's copies overlap the other's step
+    # steps and downloads the states; steps rotate over E2E_PIPELINE batches on
+    # as many streams (the asynchronous API), each synced once the next two
+    # batches' work is queued, so that one batch's upload, another's step and a
+    # third's download overlap
     e2e_rec = None
     if e2e:
+        npipe = E2E_PIPELINE
         hosts = [torch.from_numpy(g["u"]).pin_memory() for g in grids]
-        outs = [[torch.empty_like(x).pin_memory() for x in hosts] for _ in range(2)]
-        stream2 = torch.cuda.Stream()
-        b2 = hydro.Batch(grids, precision=prec)
-        b2.set_stream(stream2)
-        b2.autotune(use_cache=True)
-        pipe = [b, b2]
+        outs = [[torch.empty_like(x).pin_memory() for x in hosts] for _ in range(npipe)]
+        pipe, streams = [b], [stream]
+        for _ in range(npipe - 1):
+            sk = torch.cuda.Stream()
+            bk = hydro.Batch(grids, precision=prec)
+            bk.set_stream(sk)
+            bk.autotune(use_cache=True)
+            pipe.append(bk)
+            streams.append(sk)
 
         def e2e_step(k):
-            bk = pipe[k % 2]
+            bk = pipe[k % npipe]
             for i, x in enumerate(hosts):
                 bk.set_state_async(i, x)
             bk.step_async(cfl, nsteps=1)
-            for i, x in enumerate(outs[k % 2]):
+            for i, x in enumerate(outs[k % npipe]):
                 bk.get_state_async(i, x)
 
-        e2e_step(0)
-        e2e_step(1)
-        b.sync()
-        b2.sync()
-        ke = max(2, min(steps, 6))
+        for k in range(npipe):
+            e2e_step(k)
+        for bk in pipe:
+            bk.sync()
+        ke = max(npipe, min(steps, 6))
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        eb = torch.cuda.Event()
         e0.record(stream)
-        stream2.wait_event(e0)
+        for sk in streams[1:]:
+            sk.wait_event(e0)
         for k in range(ke):
             e2e_step(k)
-            if k >= 1:
-                pipe[(k - 1) % 2].sync()
-        eb.record(stream2)
-        stream.wait_event(eb)
+            if k >= npipe - 1:
+                pipe[(k - npipe + 1) % npipe].sync()
+        for sk in streams[1:]:
+            eb = torch.cuda.Event()
+            eb.record(sk)
+            stream.wait_event(eb)
         e1.record(stream)
-        pipe[(ke - 1) % 2].sync()
+        for j in range(max(0, ke - npipe + 1), ke):
+            pipe[j % npipe].sync()
         torch.cuda.synchronize()
         te = max_over_ranks(e0.elapsed_time(e1), ws)
         e2e_rec = {"value": replicas_value(ncells, ke, ws, te), "unit": UNIT,
                    "h2d_bytes_per_step": int(sum(x.numel() * 8 for x in hosts)),
                    "d2h_bytes_per_step": int(sum(x.numel() * 8 for x in outs[0])), "steps": ke,
-                   "pipeline": "2 batches on 2 streams: one batch's copies overlap the "
-                               "other's step"}
-        b2.close()
+                   "pipeline": "%d batches on %d streams: one batch's upload, another's step "
+                               "and a third's download overlap" % (npipe, npipe)}
+        for bk in pipe[1:]:
+            bk.close()
     b.close()
     # kernels of one step of the graph (3D grids): primitives + dt, update, and
     # per axis the slope pass (none in mixed precision, whose PPMC kernel forms

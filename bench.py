@@ -144,6 +144,23 @@ NCU_TRAFFIC = {
                          "sources": _MIXED_SRC},
 }
 
+# FP64 pipe lane-slots (warp FP64 instructions x 32) per unit of the FP64
+# kernels from one-launch ncu captures with the FP64 instruction counters
+# (Sedov 160^3 and Mach-5 turbulence 128^3, the same recipes as the benchmark
+# workloads at a capturable size; the counts are per unit of work and depend on
+# the data, not the size).  With the live launch time they give the fraction of
+# the FP64 pipe's issue capacity (2 lanes a clock an SM) a kernel uses: what
+# bounds the FP64 path, beside the algorithmic-flop fraction (an FMA counts 2
+# flops; divisions and roots take several slots a flop).  Null once the sources
+# change.
+NCU_FP64_SLOTS = {
+    ("sedov", "riemann2"): 191.2, ("sedov", "riemann1"): 115.1, ("sedov", "ppmc"): 88.0,
+    ("sedov", "slopes"): 23.0,
+    ("turbulence", "riemann2"): 283.3, ("turbulence", "riemann1"): 206.3,
+    ("turbulence", "ppmc"): 124.5, ("turbulence", "slopes"): 42.0,
+}
+NCU_FP64_SLOTS_DIGEST = "171e5803e22b43be"
+
 
 def workload(name):
     from paper_1410_4194_gb300 import workloads as W
@@ -403,6 +420,19 @@ def single_roofline(stages, precision, wkey, recon, solver, active, block_size, 
              "units_per_launch": units_per_launch, "avg_launch_ms": avg_ms,
              "flops_source": "algorithmic FP64 flops per unit (oracle/count_ops.py, %s)" % tkey,
              "peak_source": PEAK_SOURCE, "bytes_per_unit_algorithmic": bytes_per_unit}
+        wbase = tkey.split("/")[0]
+        slots = NCU_FP64_SLOTS.get((wbase, dom))
+        if (precision == "fp64" and slots and active == 3 and recon == "ppmc"
+                and solver == "exact" and block_size == 128
+                and NCU_FP64_SLOTS_DIGEST == source_digest(_FP64_SRC)):
+            clk = (sm_mhz or 2070.0) * 1e6
+            r["fp64_lane_slots_per_unit"] = slots
+            r["fp64_issue_frac"] = slots * units_per_launch / (avg_ms / 1e3) / (2 * 152 * clk)
+            r["fp64_issue_source"] = (
+                "ncu FP64-pipe lane-slots per unit (smsp__inst_executed_pipe_fp64 x 32, "
+                "%s recipe at 160^3 / 128^3) x units / live launch time, against "
+                "2 lanes a clock x 152 SMs at the %s SM clock"
+                % (wbase, "median sampled" if sm_mhz else "maximum"))
         if fp64_live:
             r["peak_measured"] = fp64_live
             r["frac_of_measured"] = achieved / fp64_live

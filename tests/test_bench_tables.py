@@ -63,3 +63,14 @@ def test_l1_helper_and_scaled_turbulence_recipe():
     assert l1 == pytest.approx([0.5 / 8, 0.0, 0.0, 1.0 / 16, 0.0])
     assert bench.workload_shape("turbulence128") == (128, 128, 128)
     assert "shells 1..4" in bench.workload_desc("turbulence128")
+
+
+def test_fp64_slot_table_matches_the_traffic_capture():
+    """The FP64 lane-slot counts and the DRAM bytes per unit come from the same
+    ncu captures of the same kernel sources."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.NCU_FP64_SLOTS_DIGEST == bench.NCU_TRAFFIC[("fp64", "riemann2")]["digest"]
+    for (wl, stage), v in bench.NCU_FP64_SLOTS.items():
+        assert wl in ("sedov", "turbulence") and stage in bench.ALGORITHMIC_FLOPS["sedov"]
+        assert 0 < v < 400

@@ -1422,8 +1422,10 @@ __device__ __forceinline__ void side_f_only(T p, const RSide<T>& s, const GasT<T
 }
 
 // INV: inv_d = 1/rho is given; without it (fast FP64) the sound speed is
-// a = x / sqrt(x rho) with x = gamma p, as a product with a reciprocal square
-// root (nine FP64 issue slots against eleven for 1/rho and then sqrt(x/rho))
+// a = x / sqrt(x rho) with x = gamma p, as a product with the reciprocal square
+// root y = 1/sqrt(x rho) (nine FP64 issue slots against eleven for 1/rho and
+// then sqrt(x/rho)), and the rarefaction derivative's factor a/(gamma p) is y
+// itself
 template <bool S, typename T, bool INV = true>
 __device__ __forceinline__ void make_side(const T W[5], T inv_d, const GasT<T>& g, RSide<T>& s) {
   s.d = W[0];
@@ -1435,20 +1437,23 @@ __device__ __forceinline__ void make_side(const T W[5], T inv_d, const GasT<T>& 
     s.A = T(2) / (g.gp1 * s.d);
     s.inv_A = T(0);
   } else {
+    s.inv_p = nr_rcp(s.p);
     if constexpr (INV || sizeof(T) == 4) {
       s.a = nr_sqrt(g.gamma * s.p * inv_d);
+      s.cdp = s.a * g.inv_g * s.inv_p;
     } else {
       const T x = g.gamma * s.p;
-      s.a = x * nr_rsqrt(x * s.d);
+      const T y = nr_rsqrt(x * s.d);
+      s.a = x * y;
+      s.cdp = y;
     }
-    s.inv_p = nr_rcp(s.p);
     s.A = g.two_gp1 * inv_d;
     s.inv_A = g.half_gp1 * s.d;
   }
   s.B = g.gm1_gp1 * s.p;
   s.cf = S ? T(2) * s.a * g.inv_gm1 : s.a * g.fan_d;  // fan_d = 2 inv_gm1 exactly
   s.cd = s.a * g.inv_g;
-  s.cdp = S ? T(0) : s.cd * s.inv_p;
+  if constexpr (S) s.cdp = T(0);
 }
 
 // Pressure function of one side without a branch between its two forms, for

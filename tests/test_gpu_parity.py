@@ -294,6 +294,22 @@ def test_full_size_sedov_one_step_all_cells(mode):
     assert err.max() <= TOL, err.max()
 
 
+@pytest.mark.parametrize("recon,solver", [("ppmp", "exact"), ("plmc", "exact"), ("pcm", "exact"),
+                                          ("ppmc", "roe"), ("plmp", "roe")])
+def test_full_size_sedov_other_methods_all_cells(recon, solver):
+    """The other reconstructions and the Roe solver at the benchmark's full size
+    and launch configuration (Sedov 256^3, the fast FP64 mode their benchmark
+    lines time): one step compared cell by cell with the oracle."""
+    w = W.sedov(256)
+    r = hydro.HYDRO_RECON_PPMC if recon == "ppmc" else RECONS[recon]
+    sv = hydro.HYDRO_RIEMANN_ROE if solver == "roe" else hydro.HYDRO_RIEMANN_EXACT
+    ug, uo, tg, to = run_both(w, 1, precision=hydro.HYDRO_FP64, recon=r, solver=sv)
+    assert tg == pytest.approx(to, rel=1e-12)
+    floor = FLOOR[hydro.HYDRO_FP64]
+    err = rel_err(ug, uo, floor)
+    assert err.max() <= TOL, (recon, solver, err.max())
+
+
 def test_conservation_and_symmetry_on_gpu():
     w = W.sedov(64)
     ug, tg, ng = hydro.run(w["u"], w["dx"], w["gamma"], w["bc"], nsteps=20, cfl=0.3)

@@ -136,10 +136,19 @@ __device__ __forceinline__ bool lt(T a, T b) {
   if constexpr (S || sizeof(T) == 4) return a < b;
   else return ord(a) < ord(b);
 }
+// float: the min/max instructions (one instruction against a compare and a
+// select; they differ from the compare-and-select only for NaN operands and in
+// which zero of +0/-0 they return)
 template <bool S, typename T>
-__device__ __forceinline__ T vmin(T a, T b) { return lt<S>(b, a) ? b : a; }
+__device__ __forceinline__ T vmin(T a, T b) {
+  if constexpr (sizeof(T) == 4) return fminf(a, b);
+  else return lt<S>(b, a) ? b : a;
+}
 template <bool S, typename T>
-__device__ __forceinline__ T vmax(T a, T b) { return lt<S>(a, b) ? b : a; }
+__device__ __forceinline__ T vmax(T a, T b) {
+  if constexpr (sizeof(T) == 4) return fmaxf(a, b);
+  else return lt<S>(a, b) ? b : a;
+}
 // larger of two non-negative doubles (a NaN counts as absent, as in the
 // IEEE "(a < b) ? b : a" with the NaN second), on the integer pipe: the bit
 // patterns of non-negative doubles order like the values, and a NaN's exceeds

@@ -11,7 +11,12 @@ Closed forms that fix it:
     traced to the upwind face equals the exact average of that quadratic over
     the contact's domain of dependence (pins w6, the 2/3 factors and the
     contact correction);
-  * mirror data give mirrored face states.
+  * mirror data give mirrored face states;
+  * a small-amplitude acoustic simple wave carried by a supersonic flow: the
+    state traced to the downwind face equals the background plus the wave's
+    eigenvector times the exact average of its profile over that wave's domain
+    of dependence (pins the acoustic corrections B and C: their signs, the
+    factors 1/2, rho/a and a rho, and which wave speed bounds each integral).
 """
 import numpy as np
 import pytest
@@ -147,3 +152,106 @@ def test_extremum_is_flattened_and_bounded():
     hi = np.maximum(w[:, 1:4, :].max(axis=1), w[:, 2, :])
     assert np.all(WsL >= lo - 1e-14) and np.all(WsL <= hi + 1e-14)
     assert np.all(WsR >= lo - 1e-14) and np.all(WsR <= hi + 1e-14)
+
+
+def _ppmc_lib(L, w, dtdx, gamma):
+    """oracle.ppmc through a given oracle library (a planted-mistake copy)."""
+    import ctypes
+    w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1, 5, 5)
+    n = w.shape[0]
+    WsL = np.zeros((n, 5)); WsR = np.zeros((n, 5))
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.oracle_ppmc.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp, dp]
+    L.oracle_ppmc.restype = ctypes.c_int
+    L.oracle_ppmc(n, w.ctypes.data_as(dp), float(dtdx), float(gamma), WsL.ctypes.data_as(dp),
+                  WsR.ctypes.data_as(dp))
+    return WsL, WsR
+
+
+def _acoustic_wave_errors(family, ppmc_fn):
+    """Largest deviation of the traced acoustic-wave perturbation from its exact
+    first-order value, relative to the perturbation's size (see the test)."""
+    rho0, p0 = 1.3, 0.9
+    a0 = np.sqrt(GAMMA * p0 / rho0)
+    eps = 1e-6
+    h = 0.02
+    qc = [0.4, 0.9, 1.3]  # q(x) = 0.4 + 0.9 x + 1.3 x^2, monotone on the stencils
+    if family == "left":
+        U, lam, r = 2.0 * a0, 2.0 * a0 - a0, np.array([1.0, -a0 / rho0, 0.0, 0.0, a0 * a0])
+    else:
+        U, lam, r = -2.0 * a0, -2.0 * a0 + a0, np.array([1.0, a0 / rho0, 0.0, 0.0, a0 * a0])
+    w0 = np.array([rho0, U, 0.15, -0.05, p0])
+    profiles = [[w0[q] + eps * r[q] * qc[0], eps * r[q] * qc[1], eps * r[q] * qc[2]]
+                for q in range(5)]
+    x0s = np.linspace(0.05, 0.25, 5)
+    w = stencils_from_profiles(profiles, x0s, h)
+    F = lambda x: sum(c * x ** (k + 1) / (k + 1) for k, c in enumerate(qc))
+    worst = 0.0
+    for cfl in (0.1, 0.3):
+        dt = cfl * h / (abs(U) + a0)
+        WsL, WsR = ppmc_fn(w, dt / h, GAMMA)
+        for i, x0 in enumerate(x0s):
+            if family == "left":
+                b = x0 + 0.5 * h
+                aa = b - lam * dt
+                got = WsR[i]
+            else:
+                aa = x0 - 0.5 * h
+                b = aa - lam * dt
+                got = WsL[i]
+            avg = (F(b) - F(aa)) / (b - aa)
+            pert = (got - w0) / eps
+            worst = max(worst, float(np.abs(pert - r * avg).max() / (np.abs(r).max() * abs(avg))))
+    return worst
+
+
+@pytest.mark.parametrize("family", ["left", "right"])
+def test_supersonic_acoustic_wave_traces_to_exact_average(family):
+    """A linear acoustic simple wave, w = w0 + eps r_k q(x) with q quadratic and
+    r_k the wave's right eigenvector in primitive variables (left-going family:
+    (1, -a/rho, 0, 0, a^2); right-going: (1, a/rho, 0, 0, a^2)), on a uniform
+    flow moving supersonically so that the wave reaches the downwind face only
+    through the correction terms: the left-going wave in a flow u = 2a to the
+    right face (the C term, lambda^m = u - a > 0), the right-going wave in u =
+    -2a to the left face (the B term, lambda^p = u + a < 0).  To first order in
+    eps the traced state is w0 + eps r_k <q>, <q> the exact average of q over
+    [x_f - lambda dt, x_f] (right face) or [x_f, x_f - lambda dt] (left face);
+    the O(eps^2) remainder bounds the tolerance (1e-5 of the perturbation)."""
+    assert _acoustic_wave_errors(family, lambda w, dtdx, g: oracle.ppmc(w, dtdx, g)) <= 1e-5
+
+
+_PPMC = "void ppmc_cell(const R (*w)[5], R dtdx, const Gas& g, R WsL[5], R WsR[5]) {"
+_ACOUSTIC_MUTANTS = {
+    # the left-going wave's correction with the wrong sign of its velocity term
+    "C_sign": [(_PPMC, "sR[0] = sR[0] + R(0.5) * (-(d * C[1]) / a + C[4] / a2);",
+                "sR[0] = sR[0] + R(0.5) * ((d * C[1]) / a + C[4] / a2);")],
+    # the right-going wave's velocity correction without its factor 1/2
+    "B_half": [(_PPMC, "sL[1] = sL[1] + R(0.5) * (B[1] + B[4] / (a * d));",
+                "sL[1] = sL[1] + (B[1] + B[4] / (a * d));")],
+    # B bounded by the contact's speed instead of the right-going wave's
+    "B_wave": [(_PPMC, "B[q] = TL_m[q] - TL_p[q];", "B[q] = TL_m[q] - TL_0[q];")],
+    # C bounded by the contact's speed instead of the left-going wave's
+    "C_wave": [(_PPMC, "C[q] = TR_p[q] - TR_m[q];", "C[q] = TR_p[q] - TR_0[q];")],
+    # the pressure part of the C term's density correction dropped
+    "C_pressure": [(_PPMC, "sR[0] = sR[0] + R(0.5) * (-(d * C[1]) / a + C[4] / a2);",
+                    "sR[0] = sR[0] + R(0.5) * (-(d * C[1]) / a);")],
+}
+
+
+def test_acoustic_pin_catches_planted_mistakes():
+    """Each plausible slip in the acoustic corrections, planted in a copy of the
+    oracle source, fails the supersonic acoustic-wave pin (on the face its term
+    reaches): a sign of the velocity term, a dropped factor 1/2, the wrong wave
+    speed bounding the integral, a dropped pressure term."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from tests.helpers import build_oracle_mutant
+    with ThreadPoolExecutor(max_workers=len(_ACOUSTIC_MUTANTS)) as ex:
+        libs = dict(zip(_ACOUSTIC_MUTANTS, ex.map(lambda kv: build_oracle_mutant(*kv),
+                                                    _ACOUSTIC_MUTANTS.items())))
+    for tag, L in libs.items():
+        errs = {fam: _acoustic_wave_errors(fam, lambda w, dtdx, g: _ppmc_lib(L, w, dtdx, g))
+                for fam in ("left", "right")}
+        assert max(errs.values()) > 1e-3, "planted mistake %r passes the acoustic pin: %s" % (
+            tag, errs)
+        print("%s: %s" % (tag, errs))

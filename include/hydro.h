@@ -386,6 +386,23 @@ int hydro_check_conversions(unsigned long long* mismatches, void* stream);
  * memory.  Returns HYDRO_OK, HYDRO_EINVAL (mismatches NULL) or HYDRO_ECUDA. */
 int hydro_check_scaling(unsigned long long* mismatches, void* stream);
 
+/* Self-check of the kernels' FP64 operations refined from hardware seeds by
+ * Newton-type iterations (the fast FP64 path replaces IEEE division and square
+ * root, about ten FP64 issue slots each on GB300, by three to eight): the
+ * reciprocal, the quotient and the square root against CUDA's correctly rounded
+ * __drcp_rn, __ddiv_rn and __dsqrt_rn; the reciprocal square root, and the
+ * reciprocal roots sigma^(-1/5) and sigma^(-1/2) of the exact solver's pressure
+ * function (sigma in [1e-30, 1e30]), against the nearest double to the exact
+ * value (a correction with the residual 1 - sigma t^m in double-double
+ * arithmetic).  2^26 counter-hashed positive normal operands each (binades
+ * -500..500 for the reciprocal, square root and reciprocal square root,
+ * -200..200 for the quotient's operands).  max_ulp: host array of six largest
+ * distances in ulps (reciprocal, quotient, square root, reciprocal square root,
+ * fifth root, square-root form).  Runs on `stream` and waits for it; allocates
+ * 48 bytes of device memory.  Returns HYDRO_OK, HYDRO_EINVAL (max_ulp NULL) or
+ * HYDRO_ECUDA. */
+int hydro_check_newton(unsigned long long* max_ulp, void* stream);
+
 /* The paper has no counterpart to this entry point.  Measured FP64 throughput
  * of the current device, the ceiling of the FP64 path (bound by its FP64 pipe):
  * a kernel of independent fused multiply-add chains on every SM (152 x 8

@@ -426,8 +426,12 @@ __device__ __forceinline__ void riemann2_body(const Geom& G, const Bufs& B, cons
       etaH = max_nn<S>(etaH, e[cr + st]);
     }
     riemann_roe<S>(UL, UR, WL, WR, idL, idR, etaH, g, Fx);
-  } else {
+  } else if constexpr (S) {
     fl = riemann_exact<S>(WL, WR, idL, idR, g, Fx);
+  } else {
+    // the sound speeds from reciprocal square roots of gamma p rho, as in the
+    // first set (one FP64 issue slot a side fewer than sqrt(gamma p / rho))
+    fl = riemann_exact<S, double, false>(WL, WR, idL, idR, g, Fx);
   }
   // CTU flux of this face replaces its (now consumed) left state
   store_rot<D>(B.UL[D], ps, f, Fx);

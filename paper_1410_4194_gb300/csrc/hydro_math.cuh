@@ -392,12 +392,22 @@ __device__ __forceinline__ float d2f(double x) {
 // Seeds: rcp.approx.ftz.f64 (reciprocal, relative error near 2^-23, issued on
 // the SFU) and the float reciprocal square root of the operand scaled by an
 // even power of two into [1, 4) (so that every positive normal double has a
-// seed).  Iterations (each squares the relative error e):
-//   reciprocal   r <- r + r (1 - b r), twice;
-//   quotient     r once, q = a r, then q <- q + r (a - b q) (Markstein's
-//                correction with the residual formed exactly by fma);
-//   square root  s = x y, then s <- s + (y/2)(x - s^2), twice;
-//   rsqrt        y <- y + (y/2)(1 - x y^2), twice.
+// seed).  Iterations:
+//   reciprocal   one third-order step r <- r (1 + e + e^2), e = 1 - b r: the
+//                series of 1/(1 - e) = 1/(b r) cut after e^2, leaving the
+//                seed's error cubed (~2^-69);
+//   quotient     a Newton step for r (r <- r + r e, error squared), q = a r,
+//                then q <- q + r (a - b q) (Markstein's correction with the
+//                residual formed exactly by fma);
+//   square root  s = x y, then s <- s + (y/2)(x - s^2), twice (each step
+//                multiplies the error by the seed's);
+//   rsqrt        one third-order step y <- y (1 + e/2 + 3 e^2/8), e = 1 - x y^2:
+//                the binomial series of (1 - e)^(-1/2) = 1/(y sqrt(x)) cut
+//                after e^2 (error (5/2) times the seed's cubed, ~2^-64).
+// A third-order step costs three (reciprocal) or five (rsqrt) FP64 issue slots
+// against four and six for two Newton steps: either way what is left is the
+// final rounding and, for rsqrt, the rounding of x y inside the residual (an
+// absolute ~2^-53 in e).
 // Results are within an ulp or two of the correctly rounded value for
 // positive normal operands (the only ones the solver passes); zero, infinite
 // and NaN operands are not handled.  The float overloads (mixed precision) are
@@ -419,9 +429,9 @@ __device__ __forceinline__ double rsqrt_seed(double x) {
   return __hiloint2double(__double2hiint(ym) - (k << 20), __double2loint(ym));
 }
 __device__ __forceinline__ double nr_rcp(double b) {
-  double r = rcp_seed(b);
-  r = fma(r, fma(-b, r, 1.0), r);
-  return fma(r, fma(-b, r, 1.0), r);
+  const double r = rcp_seed(b);
+  const double e = fma(-b, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 __device__ __forceinline__ double nr_div(double a, double b) {
   double r = rcp_seed(b);
@@ -437,9 +447,9 @@ __device__ __forceinline__ double nr_sqrt(double x) {
   return fma(hy, fma(-s, s, x), s);
 }
 __device__ __forceinline__ double nr_rsqrt(double x) {
-  double y = rsqrt_seed(x);
-  y = fma(half_bits(y), fma(-x * y, y, 1.0), y);
-  return fma(half_bits(y), fma(-x * y, y, 1.0), y);
+  const double y = rsqrt_seed(x);
+  const double e = fma(-x * y, y, 1.0);
+  return fma(y * e, fma(e, 0.375, 0.5), y);
 }
 __device__ __forceinline__ float nr_rcp(float b) {
   float r;
@@ -1466,6 +1476,29 @@ __device__ __forceinline__ void make_side(const T W[5], T inv_d, const GasT<T>& 
   if constexpr (S) s.cdp = T(0);
 }
 
+// t = sigma^(-1/m) for sigma in [1e-30, 1e30], with m = K where rare, else 2
+// (the two forms of side_eval, chosen per lane).  The seed comes from the float
+// log2 and exp2, with relative error delta ~2^-22 near sigma = 1 and up to
+// ~2^-19 at the ends of the range (the float exponent log2(sigma)/m keeps fewer
+// fraction bits there).  One third-order step follows:
+//   t <- t (1 + e/m + (m+1) e^2/(2 m^2)),  e = 1 - sigma t^m,
+// the binomial series of (1 - e)^(-1/m) = (exact root)/t cut after e^2.  It
+// leaves a relative error of (m+1)(2m+1)/6 delta^3 (below 2^-54 for m = 5 at
+// the range's ends) beside the rounding of e (~2^-53 absolute from the
+// products forming t^m).  Two Newton steps t <- t + (t/m) e reach the same
+// accuracy with five more FP64 issue slots.
+template <int K>
+__device__ __forceinline__ double rroot_seeded(double sig, bool rare) {
+  const float nm = rare ? -1.0f / K : -0.5f;
+  const double t = f2d(exp2f(__log2f(d2f(sig)) * nm));
+  const double c1 = rare ? 1.0 / K : 0.5;
+  const double c2 = rare ? (K + 1) / (2.0 * K * K) : 0.375;
+  const double t2 = t * t, t4 = t2 * t2;
+  const double tK = (K == 5) ? t4 * t : t4 * t2 * t;
+  const double e = fma(-sig, rare ? tK : t2, 1.0);
+  return fma(t * e, fma(e, c2, c1), t);
+}
+
 // Pressure function of one side without a branch between its two forms, for
 // gamma with z = (gamma-1)/(2 gamma) = 1/K (fast FP64 path, used for K = 5).  On
 // GB300 the FP64 pipe runs at 1/64 of the float rate and a warp whose lanes
@@ -1476,9 +1509,8 @@ __device__ __forceinline__ void make_side(const T W[5], T inv_d, const GasT<T>& 
 //     f = cf (x - 1), f' = cdp t^(K-1)  (= x a_k/(gamma p), as x/r = t^(K-1));
 //   shock: sigma = (p + B_k)/A_k, m = 2: q = sqrt(A_k/(p + B_k)) = t,
 //     f = (p - p_k) q, f' = q (1 - (p - p_k)/(2 (p + B_k))), 1/(p + B_k) = t^2/A_k;
-// with the seed t from the float log2/exp2 (relative error ~2^-22) and two
-// Newton steps t <- t + (t/m)(1 - sigma t^m), which leave t within an ulp or
-// two.  A side whose ratio p/p_k lies within 2^-20 of 1 (equal pressures up to
+// t from rroot_seeded (a float seed and one third-order step), within an ulp
+// or so.  A side whose ratio p/p_k lies within 2^-20 of 1 (equal pressures up to
 // rounding: uniform regions, where the two-shock start value can land an ulp
 // on either side of p_k) takes the rarefaction form's short series on either
 // branch: the shock and rarefaction forms of f agree there to within
@@ -1509,16 +1541,7 @@ __device__ __forceinline__ void side_eval(double p, const RSide<double>& s,
     side_f<false>(p, nr_rcp(p), s, g, f, fd, x);
     return;
   }
-  const double inv_m = rare ? 1.0 / K : 0.5;
-  const float nm = rare ? -1.0f / K : -0.5f;
-  double t = f2d(exp2f(__log2f(d2f(sig)) * nm));
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const double t2 = t * t, t4 = t2 * t2;
-    const double tK = (K == 5) ? t4 * t : t4 * t2 * t;
-    const double e = fma(-sig, rare ? tK : t2, 1.0);
-    t = fma(t * inv_m, e, t);
-  }
+  const double t = rroot_seeded<K>(sig, rare);
   const double t2 = t * t, t4 = t2 * t2;
   const double tK1 = (K == 5) ? t4 : t4 * t2;  // t^(K-1)
   x = rare ? r * tK1 : 0.0;

@@ -4,6 +4,9 @@
 // to a signed zero; NaN to NaN); hydro_check_scaling(): its integer halving,
 // doubling and sign tests against the FP64 arithmetic, and the float-float to
 // double conversion of hydro_ffsum.cuh against the FP64 add;
+// hydro_check_newton(): its Newton-refined FP64 reciprocal, quotient, square
+// root, reciprocal square root and the pressure function's reciprocal roots,
+// in ulps from CUDA's correctly rounded operations or from the exact root;
 // hydro_probe_fp64_rate(): the device's measured FP64 FMA throughput, the
 // denominator of the FP64 kernels' roofline.
 #include <cuda_runtime.h>
@@ -154,6 +157,73 @@ __global__ void __launch_bounds__(kThreads) k_check_scaling(unsigned long long* 
   }
 }
 
+// distance in ulps between two positive finite doubles
+__device__ __forceinline__ unsigned long long ulps(double a, double b) {
+  const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return (unsigned long long)(x > y ? x - y : y - x);
+}
+
+// the nearest double to sigma^(-1/m), from t within a few ulps of it: the
+// residual 1 - sigma t^m in double-double arithmetic (products split by fma,
+// 1 - s exact by Sterbenz as s lies within a factor 2 of 1), then
+// t (1 - res)^(-1/m) = t (1 + res/m + O(res^2)) rounded once; res ~ 2^-52, so
+// the dropped terms are ~2^-105 of t
+__device__ __forceinline__ double root_reference(double t, double sig, int m) {
+  double hi = t, lo = 0.0;
+  for (int i = 1; i < m; ++i) {
+    const double p = hi * t;
+    lo = fma(hi, t, -p) + lo * t;
+    hi = p;
+  }
+  const double s = sig * hi;
+  const double sl = fma(sig, hi, -s) + sig * lo;
+  const double res = (1.0 - s) - sl;
+  return fma(t, res / m, t);
+}
+
+// a positive normal double with the exponent drawn from [-emax, emax] and a
+// random fraction; one case in eight with the fraction all zeros (a power of
+// two) and one in eight all ones (just below one)
+__device__ __forceinline__ double newton_sample(unsigned long long i, unsigned emax) {
+  const unsigned long long r = mix64(i);
+  const unsigned long long e = 1023ull - emax + (mix64(i ^ 0x2545f491ull) % (2ull * emax + 1));
+  unsigned long long f = r & 0xfffffffffffffull;
+  if ((r >> 61) == 0) f = 0;
+  if ((r >> 61) == 1) f = 0xfffffffffffffull;
+  return __longlong_as_double((long long)((e << 52) | f));
+}
+
+constexpr unsigned long long kNewtonSamples = 1ull << 26;
+
+// largest ulp distances: 0 nr_rcp against __drcp_rn, 1 nr_div against
+// __ddiv_rn, 2 nr_sqrt against __dsqrt_rn, 3 nr_rsqrt against the nearest
+// double to x^(-1/2), 4 and 5 rroot_seeded<5> (rarefaction form m = 5, shock
+// form m = 2) against the nearest double to sigma^(-1/m), sigma in
+// [1e-30, 1e30] (the range the pressure function hands it)
+__global__ void __launch_bounds__(kThreads) k_check_newton(unsigned long long* worst) {
+  unsigned long long w[6] = {0, 0, 0, 0, 0, 0};
+  const unsigned long long stride = (unsigned long long)gridDim.x * kThreads;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * kThreads + threadIdx.x;
+       i < kNewtonSamples; i += stride) {
+    const double b = newton_sample(8 * i, 500), x = newton_sample(8 * i + 1, 500);
+    const double a = newton_sample(8 * i + 2, 200), c = newton_sample(8 * i + 3, 200);
+    // sigma over the binades -99..99, kept strictly inside (1e-30, 1e30)
+    const double sig = fmin(fmax(newton_sample(8 * i + 4, 99), nextafter(1e-30, 1.0)),
+                            nextafter(1e30, 1.0));
+    const double y = hydro::nr_rsqrt(x);
+    const double t5 = hydro::rroot_seeded<5>(sig, true);
+    const double t2 = hydro::rroot_seeded<5>(sig, false);
+    const unsigned long long d[6] = {
+        ulps(hydro::nr_rcp(b), __drcp_rn(b)), ulps(hydro::nr_div(a, c), __ddiv_rn(a, c)),
+        ulps(hydro::nr_sqrt(x), __dsqrt_rn(x)), ulps(y, root_reference(y, x, 2)),
+        ulps(t5, root_reference(t5, sig, 5)), ulps(t2, root_reference(t2, sig, 2))};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = d[k] > w[k] ? d[k] : w[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) atomicMax(worst + k, w[k]);
+}
+
 // FP64 FMA throughput: every thread runs kChains independent chains
 // x <- x * b + c of kRateIters fused multiply-adds each (b, c from the host, so
 // nothing folds); the sum is stored only if it equals a value it cannot take,
@@ -223,6 +293,26 @@ extern "C" int hydro_check_scaling(unsigned long long* mismatches, void* stream)
   }
   if (rc == HYDRO_OK &&
       (cudaMemcpyAsync(mismatches, d, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    rc = HYDRO_ECUDA;
+  cudaFree(d);
+  return rc;
+}
+
+extern "C" int hydro_check_newton(unsigned long long* max_ulp, void* stream) {
+  if (!max_ulp) return HYDRO_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, 6 * sizeof(unsigned long long)) != cudaSuccess) return HYDRO_ECUDA;
+  int rc = HYDRO_OK;
+  if (cudaMemsetAsync(d, 0, 6 * sizeof(unsigned long long), st) != cudaSuccess) rc = HYDRO_ECUDA;
+  if (rc == HYDRO_OK) {
+    k_check_newton<<<kBlocks, kThreads, 0, st>>>(d);
+    if (cudaGetLastError() != cudaSuccess) rc = HYDRO_ECUDA;
+  }
+  if (rc == HYDRO_OK &&
+      (cudaMemcpyAsync(max_ulp, d, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                        st) != cudaSuccess ||
        cudaStreamSynchronize(st) != cudaSuccess))
     rc = HYDRO_ECUDA;

@@ -37,7 +37,8 @@ EXPORTS = ("hydro_init", "hydro_set_inflow", "hydro_set_time", "hydro_get_time",
            "hydro_batch_step", "hydro_batch_step_async", "hydro_batch_sync",
            "hydro_batch_set_state_async", "hydro_batch_get_state_async", "hydro_batch_autotune", "hydro_batch_last_error",
            "hydro_batch_cuda_error_string", "hydro_batch_free", "hydro_check_conversions",
-           "hydro_check_fastdiv", "hydro_check_scaling", "hydro_probe_fp64_rate",
+           "hydro_check_fastdiv", "hydro_check_newton", "hydro_check_scaling",
+           "hydro_probe_fp64_rate",
            "hydro_set_reconstruction", "hydro_batch_set_reconstruction",
            "hydro_set_riemann_solver", "hydro_batch_set_riemann_solver")
 STAGES = ("prims", "set_dt", "slopes", "ppmc", "riemann1", "riemann2", "update")
@@ -109,6 +110,7 @@ def load():
     L.hydro_batch_free.argtypes = [vp]
     L.hydro_check_conversions.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), vp]
     L.hydro_check_scaling.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), vp]
+    L.hydro_check_newton.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), vp]
     L.hydro_probe_fp64_rate.argtypes = [dp, vp]
     L.hydro_check_fastdiv.argtypes = []
     L.hydro_check_fastdiv.restype = ctypes.c_longlong
@@ -454,6 +456,18 @@ def check_scaling():
     if rc != 0:
         raise HydroError(rc, "check_scaling")
     return int(out[0]), int(out[1]), int(out[2]), int(out[3])
+
+
+def check_newton():
+    """Largest ulp distances (reciprocal, quotient, square root, reciprocal
+    square root, fifth root, square-root form) of the kernels' Newton-refined
+    FP64 operations from correctly rounded references."""
+    L = load()
+    out = (ctypes.c_ulonglong * 6)()
+    rc = L.hydro_check_newton(out, _torch_stream_ptr())
+    if rc != 0:
+        raise HydroError(rc, "check_newton")
+    return tuple(int(v) for v in out)
 
 
 def check_fastdiv():

@@ -105,9 +105,20 @@ __device__ __forceinline__ double prims_body(const Geom& G, const Bufs& B, const
     // dx / max(|v_d| + a) exactly, because rounding and the quotient are
     // monotone; so the cells contribute a maximum and one division follows
     if (want_dt && real) {
+      if constexpr (S) {
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
-        if (G.n[d] > 1) local = max_nn<S>(local, fabs(W[1 + d]) + a);
+        for (int d = 0; d < 3; ++d)
+          if (G.n[d] > 1) local = tmax(local, fabs(W[1 + d]) + a);
+      } else {
+        // max_d (|v_d| + a) as (max_d |v_d|) + a, the same double (adding a
+        // is monotone under rounding): the maximum on the integer pipe, one
+        // FP64 add; a NaN counts as absent, as in the maxima
+        double vm = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          if (G.n[d] > 1) vm = max_nonneg(vm, vabs<false>(W[1 + d]));
+        local = max_nonneg(local, vm + a);
+      }
     }
   }
   return local;

@@ -599,8 +599,14 @@ __device__ __forceinline__ void prim2cons(const T W[5], const GasT<T>& g, T U[5]
   U[1] = d * W[1];
   U[2] = d * W[2];
   U[3] = d * W[3];
-  const T e = S ? W[4] / g.gm1 : W[4] * g.inv_gm1;
-  U[4] = e + half<S>(d) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  if constexpr (S) {
+    U[4] = W[4] / g.gm1 + half<S>(d) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  } else {
+    // rho V^2/2 as (m . v)/2 with the momenta just formed, the halving on the
+    // integer pipe and p/(gamma-1) folded into the last multiply-add: one FP64
+    // issue slot fewer than rho/2 (v . v) + p/(gamma-1)
+    U[4] = fma(W[4], g.inv_gm1, half<S>(U[1] * W[1] + U[2] * W[2] + U[3] * W[3]));
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1384,7 +1390,6 @@ struct RSide {
   T A, B;   // A_k = 2/((gamma+1) rho_k), B_k = (gamma-1)/(gamma+1) p_k
   T inv_A;  // 1/A_k = (gamma+1) rho_k / 2
   T cf;     // 2 a_k/(gamma-1)
-  T cd;     // a_k/gamma = p_k/(rho_k a_k)
   T cdp;    // a_k/(gamma p_k): f' on a rarefaction is cdp (p/p_k)^(z-1)
 };
 
@@ -1402,7 +1407,7 @@ __device__ __forceinline__ void side_f(T p, T inv_p, const RSide<T>& s, const Ga
     } else {
       x = pow_z(p * s.inv_p, g);
       f = s.cf * (x - T(1));
-      fd = x * s.cd * inv_p;
+      fd = x * (s.a * g.inv_g) * inv_p;  // a_k/gamma = p_k/(rho_k a_k)
     }
   } else {
     x = T(0);
@@ -1472,7 +1477,6 @@ __device__ __forceinline__ void make_side(const T W[5], T inv_d, const GasT<T>& 
   }
   s.B = g.gm1_gp1 * s.p;
   s.cf = S ? T(2) * s.a * g.inv_gm1 : s.a * g.fan_d;  // fan_d = 2 inv_gm1 exactly
-  s.cd = s.a * g.inv_g;
   if constexpr (S) s.cdp = T(0);
 }
 

@@ -189,27 +189,26 @@ __device__ __forceinline__ void prims_mixed_body(const Geom& G, const BufsF& B, 
   }
 }
 
-// FP64 signal speed max_d |v_d| + a of a cell: 1/rho from the float
-// reciprocal refined by two Newton steps (to FP64 precision), the floored
-// pressure (gamma-1)(rho e)(1/rho), v = m (1/rho), and a = sqrt(gamma p / rho)
-// from a float reciprocal square root of x = a^2 refined by one Newton step,
-// a = x y (1 + (1 - x y^2)/2) (relative error ~1e-13).  Rounding is
-// monotonic, so max_d |v_d| + a equals the largest of the |v_d| + a.  One
-// cell a block takes this path.
+// FP64 signal speed max_d |v_d| + a of a cell: 1/rho (nr_rcp, to FP64
+// precision), the floored pressure (gamma-1)(rho e)(1/rho), and a =
+// sqrt(gamma p / rho) from a float reciprocal square root of x = a^2 refined
+// by one Newton step, a = x y (1 + (1 - x y^2)/2) (relative error ~1e-13);
+// max_d |v_d| as (max_d |m_d|)(1/rho) (multiplying by 1/rho > 0 is monotone,
+// so the largest product is the product of the largest), the maximum on the
+// integer pipe.  One lane a block takes this path, and each of its FP64
+// instructions holds the FP64 pipe as long as a full warp's: eleven of them.
 __device__ __forceinline__ double signal_speed_fp64(const Geom& G, const GasD& g, const DtCand& c) {
-  double r = f2d(__frcp_rn(d2f(c.d)));
-  r = fma(r, fma(-c.d, r, 1.0), r);
-  r = fma(r, fma(-c.d, r, 1.0), r);
+  const double r = nr_rcp(c.d);
   const double p = vmax<false>(g.gm1 * (c.re * r), kPFloor);
   const double x = g.gamma * p * r;
   const double y = f2d(rsqrtf(d2f(x)));
   const double xy = x * y;
-  const double a = fma(0.5 * xy, fma(-xy, y, 1.0), xy);
-  double vmaxabs = 0.0;
+  const double a = fma(half_bits(xy), fma(-xy, y, 1.0), xy);
+  double mmax = 0.0;
 #pragma unroll
   for (int d = 0; d < 3; ++d)
-    if (G.n[d] > 1) vmaxabs = max_nonneg(vmaxabs, fabs(c.m[d] * r));
-  return vmaxabs + a;
+    if (G.n[d] > 1) mmax = max_nonneg(mmax, vabs<false>(c.m[d]));
+  return mmax * r + a;
 }
 
 // The CFL reduction: each block evaluates the FP64 signal speed of one cell,

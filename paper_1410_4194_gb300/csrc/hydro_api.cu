@@ -198,9 +198,11 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt, bool to_end = false,
     for (int s = kStageSlopes; s <= kStageRiemann1; ++s) {
       // no slope pass for PCM; the mixed PPMC kernel forms its own slopes
       if (s == kStageSlopes && (h->recon == HYDRO_RECON_PCM || P == HYDRO_MIXED)) continue;
-      if (s == kStagePpmc && P == HYDRO_MIXED && d > 0) {  // by segments along y and z
-        const int k = ppmc_seg_kind(d);
-        STAGE(h, s, d, batch_ppmc_mixed_seg(one_grid(h, k), d, h->blocks[k], st));
+      if (s == kStagePpmc && d > 0 && (P == HYDRO_MIXED || h->recon == HYDRO_RECON_PPMC)) {
+        const int k = ppmc_seg_kind(d);  // PPMC by segments along y and z
+        STAGE(h, s, d,
+              P == HYDRO_MIXED ? batch_ppmc_mixed_seg(one_grid(h, k), d, h->blocks[k], st)
+                               : batch_ppmc_fp64_seg(one_grid(h, k), d, h->blocks[k], st));
         continue;
       }
       const int k = launch_kind(s, d);

@@ -131,9 +131,12 @@ int enqueue_step(hydro_batch_t h, double cfl, int step) {
       // no slope pass for PCM; the mixed PPMC kernel forms its own slopes
       if (s == kStageSlopes && (h->recon == HYDRO_RECON_PCM || h->precision == HYDRO_MIXED))
         continue;
-      if (s == kStagePpmc && h->precision == HYDRO_MIXED && d > 0) {  // by segments along y, z
+      if (s == kStagePpmc && d > 0 &&
+          (h->precision == HYDRO_MIXED || h->recon == HYDRO_RECON_PPMC)) {  // by segments along y, z
         const int k = ppmc_seg_kind(d);
-        BCK(h, batch_ppmc_mixed_seg(launch_of(h, k), d, h->blocks[k], st));
+        BCK(h, h->precision == HYDRO_MIXED
+                   ? batch_ppmc_mixed_seg(launch_of(h, k), d, h->blocks[k], st)
+                   : batch_ppmc_fp64_seg(launch_of(h, k), d, h->blocks[k], st));
         continue;
       }
       BCK(h, batch_stage(launch_of(h, kind), h->precision, h->recon, h->solver, s, d, bs,

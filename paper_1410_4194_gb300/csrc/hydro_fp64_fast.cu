@@ -12,4 +12,13 @@ cudaError_t batch_stage_fp64(const BatchLaunch& L, int recon, int solver, int st
   return launch_batch_stage<false>(L, recon, solver, stage, axis, bs, blocks, st);
 }
 
+cudaError_t batch_ppmc_fp64_seg(const BatchLaunch& L, int axis, unsigned blocks, cudaStream_t st) {
+  if (blocks == 0) return cudaSuccess;
+  if (axis == 1)
+    kb_ppmc_seg<1><<<blocks, kPpmcSegThreads, 0, st>>>(L);
+  else
+    kb_ppmc_seg<2><<<blocks, kPpmcSegThreads, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
 }  // namespace hydro

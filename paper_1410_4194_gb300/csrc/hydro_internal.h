@@ -200,6 +200,8 @@ cudaError_t batch_update_mixed(const BatchLaunch& L, int bs, unsigned blocks, cu
 // the mixed PPMC along y (axis 1) or z (axis 2) by segments (launch kind
 // ppmc_seg_kind(axis), kPpmcSegThreads a block)
 cudaError_t batch_ppmc_mixed_seg(const BatchLaunch& L, int axis, unsigned blocks, cudaStream_t st);
+// the fast FP64 PPMC along y or z by segments (the same launch kind and blocks)
+cudaError_t batch_ppmc_fp64_seg(const BatchLaunch& L, int axis, unsigned blocks, cudaStream_t st);
 cudaError_t fp64_riemann_soa(int n, const double* UL, const double* UR, double gamma, double* F,
                              int* flags, cudaStream_t st);
 cudaError_t fp64_ppmc_soa(int n, const double* w, double dtdx, double gamma, double* WsL,

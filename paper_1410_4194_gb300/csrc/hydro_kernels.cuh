@@ -159,6 +159,112 @@ __device__ __forceinline__ void ppmc_body(const Geom& G, const Bufs& B, const Bo
   }
 }
 
+// PPMC along x (fast FP64) with the face values shared through the warp.
+// Lane l takes cell 31 k + l of the box (k: the warp's chunk; x runs fastest),
+// forms the parabola's value at its cell's left face and takes its right
+// face's value from lane l + 1, which holds the next cell of the row; the last
+// cell of a row forms its own.  A warp so forms 32 face values for 31 cells
+// instead of 62 (lane 31 only supplies one), the same doubles (ppmc_face).
+// 31 cells a warp need 32/31 of a one-thread-a-cell launch: a warp takes the
+// chunks k, k + W, k + 2W, ... (W warps in the grid's launch).
+template <int BS>
+__device__ __forceinline__ void ppmc_x_shared_body(const Geom& G, const Bufs& B, const Box& box,
+                                                   long long t) {
+  const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
+  const long long nchunk = (count + 30) / 31;
+  const long long nwarp = (count + BS - 1) / BS * (BS / 32);
+  const int lane = threadIdx.x & 31;
+  const long long ps = G.ps, s = G.s[0];
+  const double dtdx = B.rec[2];
+  for (long long k = t >> 5; k < nchunk; k += nwarp) {  // the same trips for the whole warp
+    const long long cell = 31 * k + lane;
+    const bool have = cell < count;
+    int c3[3] = {0, 0, 0};
+    long long c = 0;
+    double wm[5], wc[5], sc[5], Lf[5];
+    if (have) {
+      box_coords(box, cell, c3);
+      c = pidx(G, c3);
+      load_prim<0>(B.W, ps, c - s, wm);
+      load_prim<0>(B.W, ps, c, wc);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        sc[q] = B.S[q * ps + c];
+        Lf[q] = ppmc_face<false>(wm[q], wc[q], B.S[q * ps + c - s], sc[q]);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) Lf[q] = 0.0;
+    }
+    double Rf[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Rf[q] = __shfl_down_sync(0xffffffffu, Lf[q], 1);
+    if (have && lane < 31) {
+      double wp[5];
+      load_prim<0>(B.W, ps, c + s, wp);
+      if (c3[0] == box.lo[0] + box.n[0] - 1) {  // the row's last cell: its own right face
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Rf[q] = ppmc_face<false>(wc[q], wp[q], sc[q], B.S[q * ps + c + s]);
+      }
+      const double a = B.W[5 * ps + c], inv_a = B.W[6 * ps + c], inv_rho = B.W[7 * ps + c];
+      double WsL[5], WsR[5];
+      ppmc_states_faces<false>(wm, wc, wp, Lf, Rf, a, inv_a, inv_rho, dtdx, WsL, WsR);
+      store_rot<0>(B.UR[0], ps, c, WsL);
+      store_rot<0>(B.UL[0], ps, c + s, WsR);
+    }
+  }
+}
+
+// PPMC along y or z (fast FP64) for a segment of up to kPpmcSeg consecutive
+// cells of a column: a cell's right face value is the next cell's left one
+// (ppmc_face), so a segment of K cells forms K + 1 face values instead of 2K,
+// and the averages and slopes slide through registers (K + 2 cells loaded
+// instead of 3K).  The cells of a warp are 32 x-adjacent columns, so every load
+// and store stays a coalesced row.
+template <int D>
+__device__ __forceinline__ void ppmc_seg_body(const Geom& G, const Bufs& B, const Box& seg,
+                                              const Box& box, long long t) {
+  int c3[3];
+  box_coords(seg, t, c3);
+  const int k0 = box.lo[D] + (c3[D] - seg.lo[D]) * kPpmcSeg;  // first cell along D
+  const int kn = min(kPpmcSeg, box.lo[D] + box.n[D] - k0);     // cells in this segment
+  c3[D] = k0;
+  const long long ps = G.ps, s = G.s[D];
+  const long long c0 = pidx(G, c3);
+  const double dtdx = B.rec[2];
+  double wm[5], wc[5], sc[5], Lf[5];
+  load_prim<D>(B.W, ps, c0 - s, wm);
+  load_prim<D>(B.W, ps, c0, wc);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    sc[q] = B.S[q * ps + c0];
+    Lf[q] = ppmc_face<false>(wm[q], wc[q], B.S[q * ps + c0 - s], sc[q]);
+  }
+#pragma unroll 1
+  for (int k = 0; k < kn; ++k) {
+    const long long c = c0 + k * s;
+    double wp[5], sp[5], Rf[5];
+    load_prim<D>(B.W, ps, c + s, wp);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      sp[q] = B.S[q * ps + c + s];
+      Rf[q] = ppmc_face<false>(wc[q], wp[q], sc[q], sp[q]);
+    }
+    const double a = B.W[5 * ps + c], inv_a = B.W[6 * ps + c], inv_rho = B.W[7 * ps + c];
+    double WsL[5], WsR[5];
+    ppmc_states_faces<false>(wm, wc, wp, Lf, Rf, a, inv_a, inv_rho, dtdx, WsL, WsR);
+    store_rot<D>(B.UR[D], ps, c, WsL);
+    store_rot<D>(B.UL[D], ps, c + s, WsR);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      wm[q] = wc[q];
+      wc[q] = wp[q];
+      sc[q] = sp[q];
+      Lf[q] = Rf[q];
+    }
+  }
+}
+
 template <int D, bool S>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_ppmc(Geom G, Bufs B, Box box, Gas g) {
   const long long count = (long long)box.n[0] * box.n[1] * box.n[2];
@@ -646,6 +752,27 @@ HYDRO_BATCH_WRAPPER(kb_pcm, pcm_body, 1)
     if (it.t < (long long)box.n[0] * box.n[1] * box.n[2])                                      \
       BODY<D, S>(it.d->G, it.d->B, box, it.d->gd, it.t);                                       \
   }
+// PPMC (fast FP64) along x with the face values shared through the warp (one
+// launch of the x PPMC stage's blocks; see ppmc_x_shared_body) and along y, z
+// by segments (units: the segments of seg[D], kPpmcSegThreads a block for any
+// schedule).  Both at 128 registers (512 resident threads an SM): at the
+// one-cell kernel's 80 their windows and face values spill, which cost more
+// than the extra warps gave (measured, one GB300: Sedov 256^3 PPMC 7.31 ->
+// 7.21 ms a step, turbulence 256^3 10.64 -> 10.47).
+constexpr int kPpmcSharedThreadsPerSM = 512;
+template <int BS>
+__global__ void __launch_bounds__(BS, kPpmcSharedThreadsPerSM / BS) kb_ppmc_xs(BatchLaunch L) {
+  const BatchItem it = batch_item(L);
+  ppmc_x_shared_body<BS>(it.d->G, it.d->B, it.d->box[1][0], it.t);
+}
+template <int D>
+__global__ void __launch_bounds__(kPpmcSegThreads, kPpmcSharedThreadsPerSM / kPpmcSegThreads)
+    kb_ppmc_seg(BatchLaunch L) {
+  const BatchItem it = batch_item(L);
+  const Box& seg = it.d->seg[D];
+  if (it.t < (long long)seg.n[0] * seg.n[1] * seg.n[2])
+    ppmc_seg_body<D>(it.d->G, it.d->B, seg, it.d->box[1][D], it.t);
+}
 HYDRO_BATCH_WRAPPER_R(kb_riemann1, riemann1_body, 2, 64)
 HYDRO_BATCH_WRAPPER_R(kb_riemann2, riemann2_body, 3, 72)
 #undef HYDRO_BATCH_WRAPPER_R
@@ -755,7 +882,16 @@ cudaError_t launch_batch_stage(const BatchLaunch& L, int recon, int solver, int 
         case HYDRO_RECON_PLMC: HYDRO_BATCH_AXIS(kb_plmc) break;
         case HYDRO_RECON_PLMP: HYDRO_BATCH_AXIS(kb_plmp) break;
         case HYDRO_RECON_PCM: HYDRO_BATCH_AXIS(kb_pcm) break;
-        default: HYDRO_BATCH_AXIS(kb_ppmc) break;
+        default:
+          if (!S && axis == 0) {  // face values shared through the warp
+            if (bs == 128)
+              kb_ppmc_xs<128><<<blocks, 128, 0, st>>>(L);
+            else
+              kb_ppmc_xs<256><<<blocks, 256, 0, st>>>(L);
+          } else {
+            HYDRO_BATCH_AXIS(kb_ppmc)
+          }
+          break;
       }
       break;
     case kStageRiemann1:

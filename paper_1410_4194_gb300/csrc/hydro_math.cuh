@@ -755,27 +755,31 @@ __device__ __forceinline__ void ppmc_corrections_fast(double rho, double a, doub
 }
 
 // ---------------------------------------------------------------------------
-// App. A.3: PPMC.  w_m, w_c, w_p: primitive averages of cells i-1, i, i+1;
-// s_m, s_c, s_p: their limited slopes; a, inv_a, inv_rho of cell i.  Outputs the
-// traced states at the left (WsL) and right (WsR) face of cell i, pressure
-// floored.
+// App. A.3: PPMC.  The parabola's value at the face between cells j and j+1
+// (Eq. parabolic_interpolation) from their averages and limited slopes; the
+// same expression, and so the same double, for the right face of cell j and
+// the left face of cell j+1, which lets neighbouring cells share it.
 template <bool S = false, typename T>
-__device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], const T w_p[5],
-                                            const T s_m[5], const T s_c[5], const T s_p[5], T a,
-                                            T inv_a, T inv_rho, T dtdx, T WsL[5], T WsR[5]) {
-  const T c16 = T(1.0 / 6.0);
+__device__ __forceinline__ T ppmc_face(T w_left, T w_right, T s_left, T s_right) {
+  if constexpr (S)
+    return T(0.5) * (w_right + w_left) - (s_right - s_left) / T(6);
+  else
+    return half<S>(w_right + w_left) - (s_right - s_left) * T(1.0 / 6.0);
+}
+
+// PPMC of cell i from its face values: w_m, w_c, w_p: primitive averages of
+// cells i-1, i, i+1; L, R: the parabola's values at its left and right faces
+// (ppmc_face); a, inv_a, inv_rho of cell i.  Outputs the traced states at the
+// left (WsL) and right (WsR) face of cell i, pressure floored.
+template <bool S = false, typename T>
+__device__ __forceinline__ void ppmc_states_faces(const T w_m[5], const T w_c[5], const T w_p[5],
+                                                  const T Lf[5], const T Rf[5], T a, T inv_a,
+                                                  T inv_rho, T dtdx, T WsL[5], T WsR[5]) {
   T dw[5], w6[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     const T wi = w_c[q];
-    T L, R;
-    if constexpr (S) {
-      L = T(0.5) * (wi + w_m[q]) - (s_c[q] - s_m[q]) / T(6);
-      R = T(0.5) * (w_p[q] + wi) - (s_p[q] - s_c[q]) / T(6);
-    } else {
-      L = half<S>(wi + w_m[q]) - (s_c[q] - s_m[q]) * c16;
-      R = half<S>(w_p[q] + wi) - (s_p[q] - s_c[q]) * c16;
-    }
+    T L = Lf[q], R = Rf[q];
     if (diffs_prod_nonpos<S>(R, wi, wi, L)) {
       L = wi;
       R = wi;
@@ -886,6 +890,21 @@ __device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], cons
   }
   WsL[4] = vmax<S>(WsL[4], T(kPFloor));
   WsR[4] = vmax<S>(WsR[4], T(kPFloor));
+}
+
+// PPMC of cell i from the averages and limited slopes of cells i-1, i, i+1
+// (s_m, s_c, s_p), both face values formed here.
+template <bool S = false, typename T>
+__device__ __forceinline__ void ppmc_states(const T w_m[5], const T w_c[5], const T w_p[5],
+                                            const T s_m[5], const T s_c[5], const T s_p[5], T a,
+                                            T inv_a, T inv_rho, T dtdx, T WsL[5], T WsR[5]) {
+  T Lf[5], Rf[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    Lf[q] = ppmc_face<S>(w_m[q], w_c[q], s_m[q], s_c[q]);
+    Rf[q] = ppmc_face<S>(w_c[q], w_p[q], s_c[q], s_p[q]);
+  }
+  ppmc_states_faces<S>(w_m, w_c, w_p, Lf, Rf, a, inv_a, inv_rho, dtdx, WsL, WsR);
 }
 
 // ---------------------------------------------------------------------------

@@ -35,13 +35,18 @@ def test_mixed_tables_by_construction():
 
 
 def test_ncu_traffic_table_is_consistent():
-    """Each captured per-unit DRAM traffic sits just below the stage's
-    algorithmic bytes (nothing re-read; part of the last writes still in L2
-    when a kernel ends), and names the sources its digest covers."""
+    """Each captured per-unit DRAM traffic sits near the stage's algorithmic
+    bytes (below them where part of the last writes is still in L2 when a
+    kernel ends), and names the sources its digest covers.  Above by at most
+    5%, except the FP64 PPMC, whose y and z sweeps by four-cell segments read
+    the halo rows of the neighbouring segments again (200.9 B a cell against
+    184; the three sweeps average 195.3, 6% above) in a kernel bound by its
+    FP64 pipe with DRAM 14% busy."""
     sys.path.insert(0, ROOT)
     import bench
     for key, info in bench.NCU_TRAFFIC.items():
-        assert 0.75 < info["bytes_per_unit"] / bench.ALGORITHMIC_BYTES[key[0]][key[1]] < 1.05, key
+        hi = 1.10 if key == ("fp64", "ppmc") else 1.05
+        assert 0.75 < info["bytes_per_unit"] / bench.ALGORITHMIC_BYTES[key[0]][key[1]] < hi, key
         assert len(bench.source_digest(info["sources"])) == 16
 
 

@@ -123,26 +123,28 @@ _FP64_SRC = ["hydro_fp64_fast.cu", "hydro_internal.h", "hydro_kernels.cuh", "hyd
 _MIXED_SRC = ["hydro_ffsum.cuh", "hydro_internal.h", "hydro_kernels.cuh", "hydro_math.cuh",
               "hydro_mixed.cu"]
 NCU_TRAFFIC = {
-    ("fp64", "riemann2"): {"bytes_per_unit": 207.8, "digest": "31d6d9364824b074", "bs": 128,
+    # the x sweep (one face a thread, 207.7 B) and the y, z sweeps (segments of
+    # four faces, 213.3 B)
+    ("fp64", "riemann2"): {"bytes_per_unit": 211.4, "digest": "d32566f3c692a888", "bs": 128,
                            "sources": _FP64_SRC},
     # the x sweep (face values shared through the warp, 184.0 B) and the y, z
-    # sweeps (segments, 200.9 B)
-    ("fp64", "ppmc"): {"bytes_per_unit": 195.3, "digest": "31d6d9364824b074", "bs": 128,
+    # sweeps (segments, 200.7 B)
+    ("fp64", "ppmc"): {"bytes_per_unit": 195.1, "digest": "d32566f3c692a888", "bs": 128,
                        "sources": _FP64_SRC},
-    ("fp64", "riemann1"): {"bytes_per_unit": 120.3, "digest": "31d6d9364824b074", "bs": 128,
+    ("fp64", "riemann1"): {"bytes_per_unit": 120.4, "digest": "d32566f3c692a888", "bs": 128,
                            "sources": _FP64_SRC},
-    ("fp64", "slopes"): {"bytes_per_unit": 99.6, "digest": "31d6d9364824b074", "bs": 128,
+    ("fp64", "slopes"): {"bytes_per_unit": 99.5, "digest": "d32566f3c692a888", "bs": 128,
                          "sources": _FP64_SRC},
-    ("mixed", "riemann2"): {"bytes_per_unit": 99.7, "digest": "643700885125384f", "bs": 128,
+    ("mixed", "riemann2"): {"bytes_per_unit": 99.7, "digest": "ee5a686edf4a7f81", "bs": 128,
                             "sources": _MIXED_SRC},
-    ("mixed", "update"): {"bytes_per_unit": 138.0, "digest": "643700885125384f", "bs": 128,
+    ("mixed", "update"): {"bytes_per_unit": 137.9, "digest": "ee5a686edf4a7f81", "bs": 128,
                           "sources": _MIXED_SRC},
     # the x sweep (one thread a cell, 62.6 B) and the y, z sweeps (segments, 64.4 B)
-    ("mixed", "ppmc"): {"bytes_per_unit": 63.8, "digest": "643700885125384f", "bs": 128,
+    ("mixed", "ppmc"): {"bytes_per_unit": 63.8, "digest": "ee5a686edf4a7f81", "bs": 128,
                         "sources": _MIXED_SRC},
-    ("mixed", "riemann1"): {"bytes_per_unit": 55.2, "digest": "643700885125384f", "bs": 128,
+    ("mixed", "riemann1"): {"bytes_per_unit": 55.1, "digest": "ee5a686edf4a7f81", "bs": 128,
                             "sources": _MIXED_SRC},
-    ("mixed", "prims"): {"bytes_per_unit": 59.3, "digest": "643700885125384f", "bs": 128,
+    ("mixed", "prims"): {"bytes_per_unit": 59.3, "digest": "ee5a686edf4a7f81", "bs": 128,
                          "sources": _MIXED_SRC},
 }
 
@@ -156,12 +158,12 @@ NCU_TRAFFIC = {
 # flops; divisions and roots take several slots a flop).  Null once the sources
 # change.
 NCU_FP64_SLOTS = {
-    ("sedov", "riemann2"): 181.1, ("sedov", "riemann1"): 105.1, ("sedov", "ppmc"): 75.4,
+    ("sedov", "riemann2"): 177.8, ("sedov", "riemann1"): 105.1, ("sedov", "ppmc"): 75.4,
     ("sedov", "slopes"): 23.0,
-    ("turbulence", "riemann2"): 253.2, ("turbulence", "riemann1"): 176.1,
+    ("turbulence", "riemann2"): 250.9, ("turbulence", "riemann1"): 176.1,
     ("turbulence", "ppmc"): 113.4, ("turbulence", "slopes"): 42.0,
 }
-NCU_FP64_SLOTS_DIGEST = "31d6d9364824b074"
+NCU_FP64_SLOTS_DIGEST = "d32566f3c692a888"
 
 
 def workload(name):
@@ -397,9 +399,15 @@ def single_roofline(stages, precision, wkey, recon, solver, active, block_size, 
     elif precision == "strict":
         kname = "k_%s (strict)" % dom
     elif dom == "ppmc":
-        kname = "kb_" + recon
+        # fast FP64 PPMC: face values shared through the warp along x, by
+        # segments along y and z
+        kname = "kb_ppmc_xs (x) / kb_ppmc_seg (y, z)" if recon == "ppmc" else "kb_" + recon
     elif dom in ("riemann1", "riemann2") and solver == "roe":
         kname = "kb_%s_roe" % dom
+    elif dom == "riemann2" and active > 1:
+        # the fast FP64 exact second set: one face a thread along x, by
+        # segments along y and z
+        kname = "kb_riemann2 (x) / kb_riemann2_seg (y, z)"
     else:
         kname = "kb_" + dom
     # captured traffic applies to the kernels captured (PPMC + exact solver, 3D

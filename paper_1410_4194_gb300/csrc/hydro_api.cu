@@ -212,6 +212,11 @@ int enqueue_step(hydro_t h, double cfl, double fixed_dt, bool to_end = false,
   }
   for (int d = 0; d < 3; ++d) {
     if (!active(G, d)) continue;
+    if (d > 0 && P == HYDRO_FP64 && h->solver == HYDRO_RIEMANN_EXACT) {  // by segments
+      const int k = riemann2_seg_kind(d);
+      STAGE(h, kStageRiemann2, d, batch_riemann2_fp64_seg(one_grid(h, k), d, h->blocks[k], st));
+      continue;
+    }
     const int k = launch_kind(kStageRiemann2, d);
     STAGE(h, kStageRiemann2, d,
           batch_stage(one_grid(h, k), P, h->recon, h->solver, kStageRiemann2, d, h->bs,

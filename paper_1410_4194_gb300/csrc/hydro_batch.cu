@@ -145,6 +145,11 @@ int enqueue_step(hydro_batch_t h, double cfl, int step) {
   }
   for (int d = 0; d < 3; ++d) {
     if (!h->axis_used[d]) continue;
+    if (d > 0 && h->precision == HYDRO_FP64 && h->solver == HYDRO_RIEMANN_EXACT) {  // by segments
+      const int kind = riemann2_seg_kind(d);
+      BCK(h, batch_riemann2_fp64_seg(launch_of(h, kind), d, h->blocks[kind], st));
+      continue;
+    }
     const int kind = launch_kind(kStageRiemann2, d);
     BCK(h, batch_stage(launch_of(h, kind), h->precision, h->recon, h->solver, kStageRiemann2, d,
                        bs, h->blocks[kind], st));

@@ -344,11 +344,13 @@ void fill_desc(GridDesc& d, double gamma) {
   for (int s = kStageSlopes; s <= kStageRiemann2; ++s)
     for (int a = 0; a < 3; ++a) d.box[s - kStageSlopes][a] = stage_box(d.G, s, a);
   for (int a = 0; a < 3; ++a) {
-    Box b = d.box[kStagePpmc - kStageSlopes][a];
-    b.n[a] = (b.n[a] + kPpmcSeg - 1) / kPpmcSeg;
-    b.div0 = make_fastdiv((unsigned)b.n[0]);
-    b.div01 = make_fastdiv((unsigned)b.n[0] * (unsigned)b.n[1]);
-    d.seg[a] = b;
+    for (int which = 0; which < 2; ++which) {
+      Box b = d.box[(which ? kStageRiemann2 : kStagePpmc) - kStageSlopes][a];
+      b.n[a] = (b.n[a] + kPpmcSeg - 1) / kPpmcSeg;
+      b.div0 = make_fastdiv((unsigned)b.n[0]);
+      b.div01 = make_fastdiv((unsigned)b.n[0] * (unsigned)b.n[1]);
+      (which ? d.seg2 : d.seg)[a] = b;
+    }
   }
 }
 
@@ -366,8 +368,9 @@ bool build_launch_tables(const GridDesc* desc, const int* order, int n, int bs, 
       } else if (k >= ppmc_seg_kind(1)) {
         // kPpmcSegThreads a block whatever bs is: one compiled kernel, so the
         // rounding of its fused multiply-adds does not depend on the schedule
-        const int axis = k - ppmc_seg_kind(1) + 1;
-        const long long segs = g.G.n[axis] > 1 ? box_count(g.seg[axis]) : 0;
+        const bool r2 = k >= riemann2_seg_kind(1);
+        const int axis = k - (r2 ? riemann2_seg_kind(1) : ppmc_seg_kind(1)) + 1;
+        const long long segs = g.G.n[axis] > 1 ? box_count((r2 ? g.seg2 : g.seg)[axis]) : 0;
         units = (segs + kPpmcSegThreads - 1) / kPpmcSegThreads * bs;
       } else {
         const int stage = kStageSlopes + (k - 2) / 3, axis = (k - 2) % 3;

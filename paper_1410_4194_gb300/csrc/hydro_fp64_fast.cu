@@ -21,4 +21,14 @@ cudaError_t batch_ppmc_fp64_seg(const BatchLaunch& L, int axis, unsigned blocks,
   return cudaGetLastError();
 }
 
+cudaError_t batch_riemann2_fp64_seg(const BatchLaunch& L, int axis, unsigned blocks,
+                                    cudaStream_t st) {
+  if (blocks == 0) return cudaSuccess;
+  if (axis == 1)
+    kb_riemann2_seg<1><<<blocks, kPpmcSegThreads, 0, st>>>(L);
+  else
+    kb_riemann2_seg<2><<<blocks, kPpmcSegThreads, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
 }  // namespace hydro

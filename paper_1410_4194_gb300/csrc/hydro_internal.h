@@ -110,8 +110,10 @@ struct GridDesc {
   GasT<double> gd;  // gamma-derived constants, formed on the host
   GasT<float> gf;
   Box box[4][3];    // [stage - kStageSlopes][axis]: units of the per-axis stages
-  Box seg[3];       // mixed PPMC along y and z: the PPMC box with segments of
-                    // kPpmcSeg cells along the sweep axis as units (seg[0] unused)
+  Box seg[3];       // PPMC along y and z: the PPMC box with segments of kPpmcSeg
+                    // cells along the sweep axis as units (seg[0] unused)
+  Box seg2[3];      // the fast FP64 second Riemann set along y and z: its face box
+                    // with segments of kPpmcSeg faces along the sweep axis as units
 };
 
 // A batched launch covers the blocks of all grids: grid order[i] owns blocks
@@ -148,9 +150,11 @@ inline long long padded_cells(const int n[3]) {
 Box stage_box_of(const Geom& G, int stage, int axis);
 
 // Launch kinds of a (batched) step: 0 primitives, 1 update, then the four
-// per-axis stages x three axes, then the mixed PPMC by segments along y and z.
-constexpr int kLaunchKinds = 2 + 4 * 3 + 2;
+// per-axis stages x three axes, then PPMC by segments along y and z, then the
+// fast FP64 second Riemann set by segments along y and z.
+constexpr int kLaunchKinds = 2 + 4 * 3 + 2 + 2;
 inline int ppmc_seg_kind(int axis) { return 2 + 4 * 3 + (axis - 1); }
+inline int riemann2_seg_kind(int axis) { return 2 + 4 * 3 + 2 + (axis - 1); }
 // cells a thread of the segmented mixed PPMC kernels reconstructs along the
 // sweep axis (y or z)
 constexpr int kPpmcSeg = 4;
@@ -202,6 +206,10 @@ cudaError_t batch_update_mixed(const BatchLaunch& L, int bs, unsigned blocks, cu
 cudaError_t batch_ppmc_mixed_seg(const BatchLaunch& L, int axis, unsigned blocks, cudaStream_t st);
 // the fast FP64 PPMC along y or z by segments (the same launch kind and blocks)
 cudaError_t batch_ppmc_fp64_seg(const BatchLaunch& L, int axis, unsigned blocks, cudaStream_t st);
+// the fast FP64 second Riemann set (exact solver) along y or z by segments
+// (launch kind riemann2_seg_kind(axis), kPpmcSegThreads a block)
+cudaError_t batch_riemann2_fp64_seg(const BatchLaunch& L, int axis, unsigned blocks,
+                                    cudaStream_t st);
 cudaError_t fp64_riemann_soa(int n, const double* UL, const double* UR, double gamma, double* F,
                              int* flags, cudaStream_t st);
 cudaError_t fp64_ppmc_soa(int n, const double* w, double dtdx, double gamma, double* WsL,

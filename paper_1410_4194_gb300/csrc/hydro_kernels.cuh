@@ -543,6 +543,90 @@ __device__ __forceinline__ void riemann2_body(const Geom& G, const Bufs& B, cons
   store_rot<D>(B.UL[D], ps, f, Fx);
   if (fl) atomicOr(rec_flags(B.rec), fl);
 }
+// The transverse half-step and second set of exact solves (fast FP64) along y
+// or z for a segment of up to kPpmcSeg consecutive faces of a column.  The
+// cell between faces f and f + s supplies the right state of face f and the
+// left state of face f + s, and both take its transverse flux differences:
+// formed once here and added to both states in the order of riemann2_body
+// (the same doubles), where one face a thread forms each cell's differences
+// twice.  The next face's left state is formed before the current face's solve,
+// so five doubles are carried across it.  The cells of a warp are 32
+// x-adjacent columns, so every load and store stays a coalesced row.
+template <int D>
+__device__ __forceinline__ void riemann2_seg_body(const Geom& G, const Bufs& B, const Box& seg,
+                                                  const Box& box, const Gas& g, long long t) {
+  int c3[3];
+  box_coords(seg, t, c3);
+  const int k0 = box.lo[D] + (c3[D] - seg.lo[D]) * kPpmcSeg;  // first face along D
+  const int kn = min(kPpmcSeg, box.lo[D] + box.n[D] - k0);     // faces in this segment
+  c3[D] = k0;
+  const long long ps = G.ps, s = G.s[D];
+  const long long f0 = pidx(G, c3);
+  const double h = B.rec[3];
+  constexpr int T1 = Perm<D>::t1, T2 = Perm<D>::t2;
+  const bool act1 = G.n[T1] > 1, act2 = G.n[T2] > 1;
+  const double* Fa = B.F1[T1];
+  const double* Fb = B.F1[T2];
+  const long long sa = G.s[T1], sb = G.s[T2];
+  double UhL[5];
+  {
+    double Ws[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Ws[q] = B.UL[D][q * ps + f0];
+    prim2cons(Ws, g, UhL);
+    const long long cl = f0 - s;
+    if (act1) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) UhL[q] = UhL[q] + h * (Fa[q * ps + cl] - Fa[q * ps + cl + sa]);
+    }
+    if (act2) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) UhL[q] = UhL[q] + h * (Fb[q * ps + cl] - Fb[q * ps + cl + sb]);
+    }
+  }
+#pragma unroll 1
+  for (int k = 0; k < kn; ++k) {
+    const long long f = f0 + k * s;  // the cell f lies between faces f and f + s
+    const bool next = k + 1 < kn;
+    double UhR[5], UhN[5], Ws[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Ws[q] = B.UR[D][q * ps + f];
+    prim2cons(Ws, g, UhR);
+    if (next) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) Ws[q] = B.UL[D][q * ps + f + s];
+      prim2cons(Ws, g, UhN);
+    }
+    if (act1) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const double dq = Fa[q * ps + f] - Fa[q * ps + f + sa];
+        UhR[q] = UhR[q] + h * dq;
+        if (next) UhN[q] = UhN[q] + h * dq;
+      }
+    }
+    if (act2) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const double dq = Fb[q * ps + f] - Fb[q * ps + f + sb];
+        UhR[q] = UhR[q] + h * dq;
+        if (next) UhN[q] = UhN[q] + h * dq;
+      }
+    }
+    double UL[5], UR[5], WL[5], WR[5], Fx[5], idL, idR;
+    UL[0] = UhL[0]; UL[1] = UhL[1 + D]; UL[2] = UhL[1 + T1]; UL[3] = UhL[1 + T2]; UL[4] = UhL[4];
+    UR[0] = UhR[0]; UR[1] = UhR[1 + D]; UR[2] = UhR[1 + T1]; UR[3] = UhR[1 + T2]; UR[4] = UhR[4];
+    cons2prim<false>(UL, g, WL, idL);
+    cons2prim<false>(UR, g, WR, idR);
+    const int fl = riemann_exact<false, double, false>(WL, WR, idL, idR, g, Fx);
+    // CTU flux of this face replaces its (now consumed) left state
+    store_rot<D>(B.UL[D], ps, f, Fx);
+    if (fl) atomicOr(rec_flags(B.rec), fl);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) UhL[q] = UhN[q];
+  }
+}
+
 template <int D, bool S>
 __device__ __forceinline__ void riemann2_roe_body(const Geom& G, const Bufs& B, const Box& box,
     const Gas& g, long long t) {
@@ -772,6 +856,16 @@ __global__ void __launch_bounds__(kPpmcSegThreads, kPpmcSharedThreadsPerSM / kPp
   const Box& seg = it.d->seg[D];
   if (it.t < (long long)seg.n[0] * seg.n[1] * seg.n[2])
     ppmc_seg_body<D>(it.d->G, it.d->B, seg, it.d->box[1][D], it.t);
+}
+// the fast FP64 second Riemann set along y, z by segments (units: the segments
+// of seg2[D], kPpmcSegThreads a block for any schedule)
+constexpr int kRiemann2SegRegs = 96;
+template <int D>
+__global__ void __maxnreg__(kRiemann2SegRegs) kb_riemann2_seg(BatchLaunch L) {
+  const BatchItem it = batch_item(L);
+  const Box& seg = it.d->seg2[D];
+  if (it.t < (long long)seg.n[0] * seg.n[1] * seg.n[2])
+    riemann2_seg_body<D>(it.d->G, it.d->B, seg, it.d->box[3][D], it.d->gd, it.t);
 }
 HYDRO_BATCH_WRAPPER_R(kb_riemann1, riemann1_body, 2, 64)
 HYDRO_BATCH_WRAPPER_R(kb_riemann2, riemann2_body, 3, 72)

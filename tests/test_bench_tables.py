@@ -38,14 +38,15 @@ def test_ncu_traffic_table_is_consistent():
     """Each captured per-unit DRAM traffic sits near the stage's algorithmic
     bytes (below them where part of the last writes is still in L2 when a
     kernel ends), and names the sources its digest covers.  Above by at most
-    5%, except the FP64 PPMC, whose y and z sweeps by four-cell segments read
-    the halo rows of the neighbouring segments again (200.9 B a cell against
-    184; the three sweeps average 195.3, 6% above) in a kernel bound by its
-    FP64 pipe with DRAM 14% busy."""
+    5%, except the FP64 PPMC and second Riemann set, whose y and z sweeps by
+    four-cell segments read the halo rows of the neighbouring segments again
+    (PPMC 200.7 B a cell against 184, the three sweeps averaging 195.1; the
+    second set 213.3 B a face against 200, averaging 211.4) in kernels bound by
+    their FP64 pipe with DRAM 8-16% busy."""
     sys.path.insert(0, ROOT)
     import bench
     for key, info in bench.NCU_TRAFFIC.items():
-        hi = 1.10 if key == ("fp64", "ppmc") else 1.05
+        hi = 1.10 if key in (("fp64", "ppmc"), ("fp64", "riemann2")) else 1.05
         assert 0.75 < info["bytes_per_unit"] / bench.ALGORITHMIC_BYTES[key[0]][key[1]] < hi, key
         assert len(bench.source_digest(info["sources"])) == 16
 

@@ -255,3 +255,106 @@ def test_acoustic_pin_catches_planted_mistakes():
         assert max(errs.values()) > 1e-3, "planted mistake %r passes the acoustic pin: %s" % (
             tag, errs)
         print("%s: %s" % (tag, errs))
+
+
+# ---------------------------------------------------------------------------
+# Planted mistakes in the rest of PPMC (the slopes, the parabola, the traced
+# integrals, the contact correction, monotonicity): each fails one of the pins
+# above, re-run through a copy of the oracle with the mistake.
+
+def _smooth_pin_violations(ppmc_fn):
+    """Each pin's largest error over its tolerance (1: at the tolerance): the
+    cubic face values, the advected quadratic, the flattened extremum and the
+    neighbour bounds (test_cubic_face_values_dt0,
+    test_advected_quadratic_traces_to_exact_upwind_average,
+    test_extremum_is_flattened_and_bounded)."""
+    out = {}
+    profiles = [[1.0, 0.30, 0.05, 0.01], [0.20, 0.40, -0.03, 0.02], [-0.1, 0.25, 0.02, -0.01],
+                [0.05, -0.2, 0.01, 0.005], [1.0, 0.60, 0.04, 0.02]]
+    h = 0.01
+    x0s = np.linspace(-0.3, 0.3, 13)
+    WsL, WsR = ppmc_fn(stencils_from_profiles(profiles, x0s, h), 0.0, GAMMA)
+    err = 0.0
+    for i, x0 in enumerate(x0s):
+        for q in range(5):
+            err = max(err, abs(WsL[i, q] - poly(profiles[q], x0 - 0.5 * h)),
+                      abs(WsR[i, q] - poly(profiles[q], x0 + 0.5 * h)))
+    out["cubic"] = err / 1e-12
+    err = 0.0
+    h = 0.02
+    rho = [2.0, 0.8, 0.9, 0.0]
+    F = lambda x: sum(c * x ** (k + 1) / (k + 1) for k, c in enumerate(rho))
+    for U in (0.3, -0.3):
+        profiles = [rho, [U, 0, 0, 0], [0.1, 0, 0, 0], [-0.2, 0, 0, 0], [1.0, 0, 0, 0]]
+        x0s = np.linspace(-0.2, 0.2, 9)
+        w = stencils_from_profiles(profiles, x0s, h)
+        for cfl in (0.1, 0.25, 0.4):
+            dt = cfl * h / (abs(U) + np.sqrt(GAMMA * 1.0 / 2.5))
+            WsL, WsR = ppmc_fn(w, dt / h, GAMMA)
+            for i, x0 in enumerate(x0s):
+                if U > 0:
+                    b = x0 + 0.5 * h
+                    a = b - U * dt
+                    got = WsR[i, 0]
+                else:
+                    a = x0 - 0.5 * h
+                    b = a - U * dt
+                    got = WsL[i, 0]
+                err = max(err, abs(got - (F(b) - F(a)) / (b - a)))
+    out["quadratic"] = err / 1e-12
+    w = np.zeros((1, 5, 5))
+    w[0, :, 0] = [1.0, 1.5, 2.0, 1.5, 1.0]
+    w[0, :, 4] = 1.0
+    WsL, WsR = ppmc_fn(w, 0.0, GAMMA)
+    out["extremum"] = max(abs(WsL[0, 0] - 2.0), abs(WsR[0, 0] - 2.0)) / 1e-15
+    return out
+
+
+_P = "void ppmc_cell("
+_MUTANTS_SMOOTH = {
+    # w6 as printed, 6 w_i - 3 (W_L - W_R): the parabola's mean is then not w_i
+    "w6_printed": [(_P, "w6[q] = R(6.0) * wi[q] - R(3.0) * (L + Rr);",
+                    "w6[q] = R(6.0) * wi[q] - R(3.0) * (L - Rr);")],
+    # the parabolic interpolation with a third of the slope difference
+    "face_third": [(_P, "R L = R(0.5) * (wi[q] + wim[q]) - (dwc[q] - dwm[q]) / R(6.0);",
+                    "R L = R(0.5) * (wi[q] + wim[q]) - (dwc[q] - dwm[q]) / R(3.0);")],
+    # the contact's traced integral with the sign of its 2/3 term flipped
+    "two_thirds_sign": [(_P, "TL_0[q] = R(0.5) * a0 * (dw[q] + w6[q] * (R(1.0) + two3 * a0));",
+                         "TL_0[q] = R(0.5) * a0 * (dw[q] + w6[q] * (R(1.0) - two3 * a0));")],
+    # the contact correction of the density left out
+    "contact_density": [(_P, "sL[0] = sL[0] + (E[0] - E[4] / a2);",
+                         "sL[0] = sL[0] + (-E[4] / a2);")],
+    # an extremum not flattened
+    "no_flattening": [(_P, "{ L = wi[q]; Rr = wi[q]; }", "{ }")],
+    # the left face bounded by the right neighbour
+    "bound_side": [(_P, "L = mn(mx(wi[q], wim[q]), mx(mn(wi[q], wim[q]), L));",
+                    "L = mn(mx(wi[q], wip[q]), mx(mn(wi[q], wip[q]), L));")],
+    # the characteristic projection's first component as printed (R7 reading)
+    "xi0_printed": [("void project(", "x[0] = R(0.5) * (-(d * dv[1]) / a + dv[4] / (a * a));",
+                     "x[0] = R(-0.5) * (d * dv[1] / a + dv[4] / (a * a));")],
+    # the MC limiter without its factor 2 (a minmod of three differences)
+    "mc_factor": [("void plmc_slope(",
+                   "const R lim = mn(mn(fabs(xC[q]), R(2.0) * fabs(xL[q])), R(2.0) * fabs(xR[q]));",
+                   "const R lim = mn(mn(fabs(xC[q]), fabs(xL[q])), fabs(xR[q]));")],
+}
+
+
+def test_ppmc_pins_catch_planted_mistakes():
+    """Each plausible slip in the slopes, the parabola, the traced integrals,
+    the contact correction or the monotonicity step, planted in a copy of the
+    oracle source, fails at least one PPMC pin by far more than its tolerance;
+    the oracle as it is passes them all."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from tests.helpers import build_oracle_mutant
+    with ThreadPoolExecutor(max_workers=len(_MUTANTS_SMOOTH)) as ex:
+        libs = dict(zip(_MUTANTS_SMOOTH, ex.map(lambda kv: build_oracle_mutant(*kv),
+                                                  _MUTANTS_SMOOTH.items())))
+    for tag, L in libs.items():
+        with np.errstate(all="ignore"):
+            v = _smooth_pin_violations(lambda w, dtdx, g: _ppmc_lib(L, w, dtdx, g))
+        assert max(v.values()) > 10.0 or not np.all(np.isfinite(list(v.values()))), (
+            "planted mistake %r passes the PPMC pins: %s" % (tag, v))
+        print("%s: %s" % (tag, {k: "%.3g" % x for k, x in v.items()}))
+    base = _smooth_pin_violations(oracle.ppmc)
+    assert max(base.values()) <= 1.0, base

@@ -536,3 +536,120 @@ def test_transverse_pin_catches_planted_mistakes():
         assert caught, "planted mistake %r passes the transverse pin: %s" % (tag, errs)
         print("%s: %s" % (tag, errs))
 
+
+
+# ---------------------------------------------------------------------------
+# Planted mistakes in the conserved update and the ghost rules: each fails the
+# smooth-advection order pin or the ghost-rule pin, re-run through a copy of
+# the oracle with the mistake.
+
+def _advection_order(L):
+    """The smooth-advection pin through the oracle library L: the mean density
+    errors after one period at 32, 64, 128 cells and the observed order."""
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    errs = []
+    for n in (32, 64, 128):
+        x = (np.arange(n) + 0.5) / n
+        rho = 1.0 + 0.2 * np.sin(2 * np.pi * x)
+        u0 = np.ascontiguousarray(W.prim_to_cons(rho.reshape(1, 1, n), 1.0, 0.0, 0.0, 1.0, 1.4))
+        h = L.oracle_init(n, 1, 1, 1.0 / n, 1.4, (ctypes.c_int * 6)(*([P] * 6)))
+        assert h
+        try:
+            L.oracle_set_state(h, u0.ctypes.data_as(dp))
+            t, steps = 0.0, 0
+            while t < 1.0 and steps < 2000:
+                dt = min(L.oracle_compute_dt(h, 0.4), 1.0 - t)
+                if not dt > 0.0:
+                    break
+                L.oracle_step_dt(h, dt)
+                t += dt
+                steps += 1
+            out = np.zeros_like(u0)
+            L.oracle_get_state(h, out.ctypes.data_as(dp))
+        finally:
+            L.oracle_free(h)
+        errs.append(float(np.abs(out[0, 0, 0] - rho).mean()))
+    with np.errstate(all="ignore"):
+        order = float(np.log2(errs[1] / errs[2]))
+    return errs, order
+
+
+def _ghost_rule_errors(L):
+    """The reflective, periodic and outflow ghost rules of test_ghost_fill_rules
+    through the oracle library L: the number of ghost values that differ from
+    the rule."""
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.oracle_fill_ghosts.argtypes = [ctypes.c_void_p, dp]
+    nx, ny, nz = 6, 5, 4
+    rng = np.random.Generator(np.random.PCG64(2))
+    u0 = np.zeros((5, nz, ny, nx))
+    u0[0] = 1.0 + rng.random((nz, ny, nx))
+    u0[1:4] = rng.normal(size=(3, nz, ny, nx))
+    u0[4] = 5.0 + rng.random((nz, ny, nx))
+    h = L.oracle_init(nx, ny, nz, 0.1, 1.4, (ctypes.c_int * 6)(P, P, R_, O, O, O))
+    assert h
+    G = 4
+    up = np.zeros((5, nz + 2 * G, ny + 2 * G, nx + 2 * G))
+    try:
+        L.oracle_set_state(h, np.ascontiguousarray(u0).ctypes.data_as(dp))
+        L.oracle_fill_ghosts(h, up.ctypes.data_as(dp))
+    finally:
+        L.oracle_free(h)
+    bad = 0
+    for d in range(1, G + 1):
+        bad += int(np.sum(up[:, G:G + nz, G:G + ny, G - d] != u0[:, :, :, nx - d]))
+        bad += int(np.sum(up[:, G:G + nz, G:G + ny, G + nx - 1 + d] != u0[:, :, :, d - 1]))
+        exp = u0[:, :, d - 1, :].copy()
+        exp[2] = -exp[2]
+        bad += int(np.sum(up[:, G:G + nz, G - d, G:G + nx] != exp))
+        bad += int(np.sum(up[:, G:G + nz, G + ny - 1 + d, G:G + nx] != u0[:, :, ny - 1, :]))
+    return bad
+
+
+_UPD = "un = un + dtdx * (F2[d][q * nc + c] - F2[d][q * nc + c + sd]);"
+_FG = "void fill_ghosts(Grid<R>& G) {"
+_UPDATE_GHOST_MUTANTS = {
+    # the flux difference with the wrong sign (still conservative)
+    "update_sign": [(_CTU, _UPD, "un = un - dtdx * (F2[d][q * nc + c] - F2[d][q * nc + c + sd]);")],
+    # half the step
+    "update_half": [(_CTU, _UPD, "un = un + R(0.5) * dtdx * (F2[d][q * nc + c] - F2[d][q * nc + c + sd]);")],
+    # the fluxes of the faces one cell to the left (still conservative)
+    "update_shift": [(_CTU, _UPD, "un = un + dtdx * (F2[d][q * nc + c - sd] - F2[d][q * nc + c]);")],
+    # the reflective rule without the negated normal momentum
+    "reflect_momentum": [(_FG, "if (type == BC_REFLECT && q == 1 + d) val_ = -val_;", "")],
+    # the periodic rule one cell off
+    "periodic_offset": [(_FG, "case BC_PERIODIC: src = side == 0 ? G.gh[d] + G.n[d] - gd : G.gh[d] + gd - 1; break;",
+                         "case BC_PERIODIC: src = side == 0 ? G.gh[d] + G.n[d] - gd - 1 : G.gh[d] + gd; break;")],
+    # the outflow rule copying the second real cell from the face
+    "outflow_inner": [(_FG, "case BC_OUTFLOW: src = side == 0 ? G.gh[d] : G.gh[d] + G.n[d] - 1; break;",
+                       "case BC_OUTFLOW: src = side == 0 ? G.gh[d] + 1 : G.gh[d] + G.n[d] - 2; break;")],
+}
+
+
+def test_update_and_ghost_pins_catch_planted_mistakes():
+    """Each plausible slip in the conserved update (Eq. conserved_update) or
+    the ghost rules (Sec. 3.1), planted in a copy of the oracle source, fails
+    the smooth-advection pin (observed order above 1.8, error at 128 cells
+    below 1e-3) or the ghost-rule pin; the oracle as it is passes both."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from tests.helpers import build_oracle_mutant
+    with ThreadPoolExecutor(max_workers=len(_UPDATE_GHOST_MUTANTS)) as ex:
+        libs = dict(zip(_UPDATE_GHOST_MUTANTS, ex.map(lambda kv: build_oracle_mutant(*kv),
+                                                        _UPDATE_GHOST_MUTANTS.items())))
+
+    def passes(L):
+        _bind_run(L)
+        errs, order = _advection_order(L)
+        ghosts = _ghost_rule_errors(L)
+        ok = bool(order > 1.8 and errs[2] < 1e-3 and ghosts == 0)
+        return ok, {"errs": errs, "order": order, "ghost_mismatches": ghosts}
+
+    for tag, L in libs.items():
+        ok, info = passes(L)
+        assert not ok, "planted mistake %r passes the update and ghost pins: %s" % (tag, info)
+        print("%s: %s" % (tag, info))
+    ok, info = passes(oracle.lib())
+    assert ok, info

@@ -179,3 +179,116 @@ def test_roe_steps_conserve_and_keep_symmetries(recon):
     sc = np.abs(u).max()
     np.testing.assert_allclose(run(mirror_x(w["u"])), mirror_x(u), rtol=0, atol=1e-12 * sc)
     np.testing.assert_allclose(run(rotate_xyz(w["u"])), rotate_xyz(u), rtol=0, atol=1e-12 * sc)
+
+
+# ---------------------------------------------------------------------------
+# Planted mistakes in the Roe solver, the HLLE fallback and the H-correction
+# quantity: each fails one of the pins above, re-run through a copy of the
+# oracle with the mistake.
+
+def _roe_lib(L):
+    """oracle.riemann_roe through a given oracle library (a planted-mistake copy)."""
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.oracle_riemann_roe.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_double, dp]
+    L.oracle_riemann_roe.restype = ctypes.c_int
+
+    def roe(UL, UR, gamma, etaH=None):
+        UL = np.ascontiguousarray(UL, dtype=np.float64).reshape(-1, 5)
+        UR = np.ascontiguousarray(UR, dtype=np.float64).reshape(-1, 5)
+        F = np.zeros((UL.shape[0], 5))
+        e = None if etaH is None else np.ascontiguousarray(etaH, dtype=np.float64).reshape(-1)
+        L.oracle_riemann_roe(UL.shape[0], UL.ctypes.data_as(dp), UR.ctypes.data_as(dp),
+                             None if e is None else e.ctypes.data_as(dp), float(gamma),
+                             F.ctypes.data_as(dp))
+        return F
+
+    return roe
+
+
+def _roe_pin_violations(roe):
+    """Each pin's largest error over its tolerance (1: at the tolerance): the
+    isolated shocks and contacts, the large-H local Lax-Friedrichs flux and the
+    123 interface's HLLE flux."""
+    out = {}
+    g = 1.4
+    err = 0.0
+    for mach, s in ((1.5, 0.4), (3.0, -0.3), (2.0, 0.05)):
+        WL, WR = shock_pair(mach, s, g)
+        F = roe(cons1(WL, g), cons1(WR, g), g)
+        expect = flux1(WL, g) if s > 0 else flux1(WR, g)
+        err = max(err, np.max(np.abs(F - expect) / (1.0 + np.abs(expect))))
+    out["shock"] = err / 1e-12
+    err = 0.0
+    for u in (0.4, -0.25):
+        gc = 5.0 / 3.0
+        WL = np.array([[2.0, u, 0.3, -0.1, 1.0]])
+        WR = np.array([[0.5, u, -0.2, 0.4, 1.0]])
+        F = roe(cons1(WL, gc), cons1(WR, gc), gc)
+        expect = flux1(WL, gc) if u > 0 else flux1(WR, gc)
+        err = max(err, np.max(np.abs(F - expect) / (1.0 + np.abs(expect))))
+    out["contact"] = err / 1e-12
+    WL, WR = W.random_states(100, seed=9, gamma=g, rho_range=(0.5, 2.0), p_range=(0.5, 2.0),
+                             vmax=0.5)
+    aL = np.sqrt(g * WL[:, 4] / WL[:, 0])
+    aR = np.sqrt(g * WR[:, 4] / WR[:, 0])
+    UL, UR = cons1(WL, g), cons1(WR, g)
+    eta = 50.0 * np.ones(len(UL))
+    F = roe(UL, UR, g, eta)
+    expect = 0.5 * (flux1(WL, g) + flux1(WR, g)) - 0.5 * eta[:, None] * (UR - UL)
+    sub = np.abs(0.5 * (WL[:, 1] + WR[:, 1])) < 0.5 * np.minimum(aL, aR)
+    out["llf"] = np.max(np.abs(F[sub] - expect[sub]) / (1.0 + np.abs(expect[sub]))) / 1e-11
+    WL = np.array([[1.0, -2.0, 0.0, 0.0, 0.4]])
+    WR = np.array([[1.0, 2.0, 0.0, 0.0, 0.4]])
+    b = 2.0 + np.sqrt(g * 0.4)
+    F = roe(cons1(WL, g), cons1(WR, g), g)
+    out["hlle_123"] = np.max(np.abs(F - [[0.0, 4.4 - 2.0 * b, 0.0, 0.0, 0.0]])) / 1e-13
+    return out
+
+
+_ROE_H = "int riemann_roe_cons("
+_HLLE_H = "void roe_hlle_flux("
+_ROE_MUTANTS = {
+    # the Roe velocity as the plain average instead of the sqrt(rho)-weighted one
+    "plain_average": [(_ROE_H, "const R u = (sL * WL[1] + sR * WR[1]) / (sL + sR);",
+                       "const R u = R(0.5) * (WL[1] + WR[1]);")],
+    # the enthalpy average with the weights swapped
+    "enthalpy_weights": [(_ROE_H, "const R H = (sL * HL + sR * HR) / (sL + sR);",
+                          "const R H = (sR * HL + sL * HR) / (sL + sR);")],
+    # the u - a wave strength with the sign of its u a term flipped
+    "xi0_sign": [(_ROE_H, "dU[0] * Na * (R(0.5) * gp * V2 + u * a)",
+                  "dU[0] * Na * (R(0.5) * gp * V2 - u * a)")],
+    # the energy component of the u + a eigenvector with H - u a
+    "eigvec_energy": [(_ROE_H, "C4 * (H + u * a);", "C4 * (H - u * a);")],
+    # the H correction not applied to the u + a family
+    "h_corr_missing": [(_ROE_H, "alp = mx(fabs(lp), etaH);", "alp = fabs(lp);")],
+    # the HLLE bounds taken without the data states' wave speeds
+    "hlle_bounds": [(_HLLE_H, "const R bm = mn(mn(lm, WL[1] - aL), R(0.0));",
+                     "const R bm = mn(lm, R(0.0));"),
+                    (_HLLE_H, "const R bp = mx(mx(lp, WR[1] + aR), R(0.0));",
+                     "const R bp = mx(lp, R(0.0));")],
+    # the fallback test on the intermediate state dropped
+    "no_fallback": [(_ROE_H, "if (fail) roe_hlle_flux(UL, UR, WL, WR, FL, FR, lm, lp, g, F);", "")],
+}
+
+
+def test_roe_pins_catch_planted_mistakes():
+    """Each plausible slip in the Roe averages, the wave strengths, an
+    eigenvector, the H correction, the HLLE bounds or the fallback test,
+    planted in a copy of the oracle source, fails one of the pins (isolated
+    shock and contact, large-H Lax-Friedrichs flux, the 123 interface) by far
+    more than its tolerance; the oracle as it is passes them all."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from tests.helpers import build_oracle_mutant
+    with ThreadPoolExecutor(max_workers=len(_ROE_MUTANTS)) as ex:
+        libs = dict(zip(_ROE_MUTANTS, ex.map(lambda kv: build_oracle_mutant(*kv),
+                                               _ROE_MUTANTS.items())))
+    for tag, L in libs.items():
+        with np.errstate(all="ignore"):
+            v = _roe_pin_violations(_roe_lib(L))
+        assert max(v.values()) > 10.0 or not np.all(np.isfinite(list(v.values()))), (
+            "planted mistake %r passes the Roe pins: %s" % (tag, v))
+        print("%s: %s" % (tag, {k: "%.3g" % x for k, x in v.items()}))
+    base = _roe_pin_violations(oracle.riemann_roe)
+    assert max(base.values()) <= 1.0, base

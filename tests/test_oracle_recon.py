@@ -264,3 +264,166 @@ def test_ppmp_supersonic_acoustic_wave_corrections(side):
                      p0 + eps * p0 * xm)[3:4]
     got = UsL if side == "left" else UsR
     np.testing.assert_allclose(got, cons(expect), rtol=1e-11, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Planted mistakes in PLMP, PLMC and PPMP: each fails one of the pins above,
+# re-run through a copy of the oracle with the mistake.
+
+def _reconstruct_lib(L):
+    """oracle.reconstruct through a given oracle library (a planted-mistake copy)."""
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.oracle_reconstruct.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, dp, dp]
+    L.oracle_reconstruct.restype = ctypes.c_int
+
+    def rec(recon, w, dtdx, dx, gamma):
+        w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1, 7, 5)
+        UsL = np.zeros((w.shape[0], 5)); UsR = np.zeros((w.shape[0], 5))
+        L.oracle_reconstruct(w.shape[0], int(recon), w.ctypes.data_as(dp), float(dtdx),
+                             float(dx), float(gamma), UsL.ctypes.data_as(dp),
+                             UsR.ctypes.data_as(dp))
+        return UsL, UsR
+
+    return rec
+
+
+def _sod_contact_cells_lib(L, recon, nx=100):
+    """_contact_cells through the oracle library L."""
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.oracle_init.restype = ctypes.c_void_p
+    L.oracle_init.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [ctypes.POINTER(ctypes.c_int)]
+    L.oracle_free.argtypes = [ctypes.c_void_p]
+    L.oracle_set_state.argtypes = [ctypes.c_void_p, dp]
+    L.oracle_get_state.argtypes = [ctypes.c_void_p, dp]
+    L.oracle_set_recon.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.oracle_compute_dt.restype = ctypes.c_double
+    L.oracle_compute_dt.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    L.oracle_step_dt.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    w = W.sod(nx, left=(1.0, 0.0, 1.0), right=(0.1, 0.0, 0.1))
+    u0 = np.ascontiguousarray(w["u"])
+    h = L.oracle_init(nx, 1, 1, w["dx"], w["gamma"], (ctypes.c_int * 6)(*w["bc"]))
+    assert h
+    try:
+        L.oracle_set_recon(h, int(recon))
+        L.oracle_set_state(h, u0.ctypes.data_as(dp))
+        t, steps = 0.0, 0
+        while t < 0.2 and steps < 2000:
+            dt = min(L.oracle_compute_dt(h, 0.3), 0.2 - t)
+            if not dt > 0.0:
+                return 99
+            L.oracle_step_dt(h, dt)
+            t += dt
+            steps += 1
+        u = np.zeros_like(u0)
+        L.oracle_get_state(h, u.ctypes.data_as(dp))
+    finally:
+        L.oracle_free(h)
+    x = (np.arange(nx) + 0.5) / nx
+    rho_e, _, _ = exact_riemann_profile(x, 0.2, 0.5, (1, 0, 1), (0.1, 0, 0.1), 1.4)
+    rl = rho_e[(x > 0.6) & (x < 0.66)].mean()
+    rr = rho_e[(x > 0.75) & (x < 0.8)].mean()
+    lo, hi = rr + 0.05 * (rl - rr), rr + 0.95 * (rl - rr)
+    rho = u[0, 0, 0]
+    return int(np.sum((x > 0.62) & (x < 0.8) & (rho > lo) & (rho < hi)))
+
+
+def _recon_pin_violations(rec, contact_cells):
+    """Each pin's largest error over its tolerance (1: at the tolerance): linear
+    data (PPMP, PLMC, PLMP), PPMP's cubic, the advected quadratic (PPMP), the
+    advected linear density (PLMC, PLMP) and PPMP's Sod contact width."""
+    out = {}
+    x = np.arange(7) - 3.0
+    st = stencil(1.0 + 0.002 * x, 0.3 + 0.01 * x, 0.1 - 0.02 * x, 0.05 * x, 1.0 + 0.01 * x)
+    wl = cons(stencil(1.0 - 0.001, 0.3 - 0.005, 0.1 + 0.01, -0.025, 1.0 - 0.005)[3:4])
+    wr = cons(stencil(1.0 + 0.001, 0.3 + 0.005, 0.1 - 0.01, 0.025, 1.0 + 0.005)[3:4])
+    err = 0.0
+    for recon in (oracle.RECON_PPMP, oracle.RECON_PLMC, oracle.RECON_PLMP):
+        UsL, UsR = rec(recon, st[None], 0.0, 1.0, G)
+        err = max(err, np.max(np.abs(UsL - wl) / (np.abs(wl) + 1e-2)),
+                  np.max(np.abs(UsR - wr) / (np.abs(wr) + 1e-2)))
+    out["linear"] = err / 1e-13
+    dx = 0.1
+    cubics = [np.poly1d([0.002, 0.001, 0.004, 1.0]), np.poly1d([0.05, -0.02, 0.3, 0.2]),
+              np.poly1d([-0.03, 0.01, 0.2, -0.1]), np.poly1d([0.02, 0.03, -0.1, 0.3]),
+              np.poly1d([0.001, -0.002, 0.02, 1.0])]
+    stc = np.stack([cell_averages(c, -3.5 * dx, dx) for c in cubics], axis=1)
+    UsL, UsR = rec(oracle.RECON_PPMP, stc[None], 0.0, dx, G)
+    cl = cons(np.array([[c(-0.5 * dx) for c in cubics]]))
+    cr = cons(np.array([[c(0.5 * dx) for c in cubics]]))
+    out["ppmp_cubic"] = max(np.max(np.abs(UsL / cl - 1)), np.max(np.abs(UsR / cr - 1))) / 1e-12
+    dxq, u, p = 1.0, 0.4, 1.0
+    q = np.poly1d([0.001, 0.004, 1.0])
+    rho = cell_averages(q, -3.5 * dxq, dxq)
+    UsL, UsR = rec(oracle.RECON_PPMP, stencil(rho, u, 0.0, 0.0, p)[None], 0.3, dxq, G)
+    a = np.sqrt(G * p / rho[3])
+    Q = np.polyint(q)
+    sR, sL = u * 0.3, (a - u) * 0.3
+    rhoR = (Q(0.5) - Q(0.5 - sR)) / sR
+    rhoL = (Q(-0.5 + sL) - Q(-0.5)) / sL
+    out["ppmp_quadratic"] = max(abs(UsR[0, 0] / rhoR - 1), abs(UsL[0, 0] / rhoL - 1)) / 1e-13
+    s = 0.002
+    stl = stencil(1.0 + s * x, u, 0.0, 0.0, p)
+    a1 = np.sqrt(G * p)
+    err = 0.0
+    UsL, UsR = rec(oracle.RECON_PLMC, stl[None], 0.3, 1.0, G)
+    err = max(err, abs(UsR[0, 0] - (1.0 + s * (0.5 - 0.5 * u * 0.3))),
+              abs(UsL[0, 0] - (1.0 + s * (-0.5 + 0.5 * (a1 - u) * 0.3))))
+    UsL, UsR = rec(oracle.RECON_PLMP, stl[None], 0.3, 1.0, G)
+    err = max(err, abs(UsR[0, 0] - (1.0 + s * (0.5 - 0.5 * u * 0.3))),
+              abs(UsL[0, 0] - (1.0 + s * (-0.5 - 0.5 * u * 0.3))))
+    out["plm_linear_advection"] = err / 1e-14
+    out["ppmp_sod_contact"] = contact_cells / 2.0
+    return out
+
+
+_PLMP = "void plmp_cell("
+_PLMC = "void plmc_cell("
+_PPMP = "void ppmp_cell("
+_RECON_MUTANTS = {
+    # PLMP's half-step flux evolution with the wrong sign
+    "plmp_evolution_sign": [(_PLMP, "UsL[q] = UL[q] + h * (FL[q] - FR[q]);",
+                             "UsL[q] = UL[q] - h * (FL[q] - FR[q]);")],
+    # PLMP's left boundary value a whole slope from the average
+    "plmp_full_slope": [(_PLMP, "WL[q] = w[1][q] - R(0.5) * dw[q];", "WL[q] = w[1][q] - dw[q];")],
+    # PLMC's contact correction with the acoustic speed difference
+    "plmc_contact_speed": [(_PLMC, "sR[0] = sR[0] + (lp - l0) * (dw[0] - dw[4] / a2);",
+                            "sR[0] = sR[0] + (lp - lm) * (dw[0] - dw[4] / a2);")],
+    # PLMC's trace of the right face with the wrong sign
+    "plmc_trace_sign": [(_PLMC, "WsR[q] = (WR[q] - R(0.5) * bp * dw[q]) + h * sR[q];",
+                         "WsR[q] = (WR[q] + R(0.5) * bp * dw[q]) + h * sR[q];")],
+    # PPMP's interpolation with a third of the slope difference
+    "ppmp_face_third": [(_PPMP, "WL[q] = R(0.5) * (wi[q] + wim[q]) - (dwc[q] - dwm[q]) / R(6.0);",
+                         "WL[q] = R(0.5) * (wi[q] + wim[q]) - (dwc[q] - dwm[q]) / R(3.0);")],
+    # PPMP's contact test as printed (same concavity; reading N1)
+    "ppmp_contact_printed": [(_PPMP, "d2m * d2p < R(0.0)) {", "d2m * d2p > R(0.0)) {")],
+    # the primitive MC limiter without its factor 2
+    "mc_prim_factor": [("void plm_prim_slope(",
+                        "dw[q] = sgn(dC) * mn(mn(fabs(dC), R(2.0) * fabs(dL)), R(2.0) * fabs(dR));",
+                        "dw[q] = sgn(dC) * mn(mn(fabs(dC), fabs(dL)), fabs(dR));")],
+}
+
+
+def test_recon_pins_catch_planted_mistakes():
+    """Each plausible slip in PLMP, PLMC or PPMP (a sign, a factor, the wrong
+    wave speed, the printed contact test, the limiter's factor 2), planted in a
+    copy of the oracle source, fails one of the pins (linear data, PPMP's cubic,
+    the advected quadratic and linear profiles, PPMP's two-zone Sod contact) by
+    far more than its tolerance; the oracle as it is passes them all."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from tests.helpers import build_oracle_mutant
+    with ThreadPoolExecutor(max_workers=len(_RECON_MUTANTS)) as ex:
+        libs = dict(zip(_RECON_MUTANTS, ex.map(lambda kv: build_oracle_mutant(*kv),
+                                                 _RECON_MUTANTS.items())))
+    for tag, L in libs.items():
+        with np.errstate(all="ignore"):
+            v = _recon_pin_violations(_reconstruct_lib(L),
+                                      _sod_contact_cells_lib(L, oracle.RECON_PPMP))
+        assert max(v.values()) > 1.4 or not np.all(np.isfinite(list(v.values()))), (
+            "planted mistake %r passes the reconstruction pins: %s" % (tag, v))
+        print("%s: %s" % (tag, {k: "%.3g" % x for k, x in v.items()}))
+    base = _recon_pin_violations(oracle.reconstruct, _contact_cells(oracle.RECON_PPMP))
+    assert max(base.values()) <= 1.0, base

@@ -376,7 +376,32 @@ def _recon_pin_violations(rec, contact_cells):
               abs(UsL[0, 0] - (1.0 + s * (-0.5 - 0.5 * u * 0.3))))
     out["plm_linear_advection"] = err / 1e-14
     out["ppmp_sod_contact"] = contact_cells / 2.0
+    out["ppmp_acoustic"] = max(_ppmp_acoustic_error(rec, side) for side in ("left", "right"))
     return out
+
+
+def _ppmp_acoustic_error(rec, side):
+    """test_ppmp_supersonic_acoustic_wave_corrections through the
+    reconstruction rec: the largest error over its tolerance (rtol 1e-11,
+    atol 1e-12)."""
+    rho0, p0 = 1.0, 1.0
+    a0 = np.sqrt(G * p0 / rho0)
+    C = rho0 * a0
+    eps = 1e-6
+    x = np.arange(7) - 3.0
+    dtdx = 0.1
+    if side == "left":
+        u0, sgn, lam = -2.0 * a0, +1.0, -2.0 * a0 + a0
+    else:
+        u0, sgn, lam = 2.0 * a0, -1.0, 2.0 * a0 - a0
+    dp = eps * p0 * x
+    st = stencil(rho0 + dp / a0 ** 2, u0 + sgn * dp / C, 0.0, 0.0, p0 + dp)
+    UsL, UsR = rec(oracle.RECON_PPMP, st[None], dtdx, 1.0, G)
+    xm = (-0.5 if side == "left" else 0.5) - 0.5 * lam * dtdx
+    expect = cons(stencil(rho0 + eps * p0 * xm / a0 ** 2, u0 + sgn * eps * p0 * xm / C, 0.0, 0.0,
+                          p0 + eps * p0 * xm)[3:4])
+    got = UsL if side == "left" else UsR
+    return float(np.max(np.abs(got - expect) / (1e-12 + 1e-11 * np.abs(expect))))
 
 
 _PLMP = "void plmp_cell("
@@ -399,6 +424,11 @@ _RECON_MUTANTS = {
                          "WL[q] = R(0.5) * (wi[q] + wim[q]) - (dwc[q] - dwm[q]) / R(3.0);")],
     # PPMP's contact test as printed (same concavity; reading N1)
     "ppmp_contact_printed": [(_PPMP, "d2m * d2p < R(0.0)) {", "d2m * d2p > R(0.0)) {")],
+    # PPMP's chi^p_L as printed (reading N4)
+    "chi_p_printed": [(_PPMP, "((WLm[1] - WLp[1]) + (WLm[4] - WLp[4]) / CL)",
+                       "((WLm[1] - WLp[1]) - (WLm[4] + WLp[4]) / CL)")],
+    # PPMP's right-face velocity correction with the wrong sign
+    "chi_m_velocity": [(_PPMP, "WsR[1] = WRp[1] - CR * chiRm;", "WsR[1] = WRp[1] + CR * chiRm;")],
     # the primitive MC limiter without its factor 2
     "mc_prim_factor": [("void plm_prim_slope(",
                         "dw[q] = sgn(dC) * mn(mn(fabs(dC), R(2.0) * fabs(dL)), R(2.0) * fabs(dR));",
@@ -408,10 +438,11 @@ _RECON_MUTANTS = {
 
 def test_recon_pins_catch_planted_mistakes():
     """Each plausible slip in PLMP, PLMC or PPMP (a sign, a factor, the wrong
-    wave speed, the printed contact test, the limiter's factor 2), planted in a
-    copy of the oracle source, fails one of the pins (linear data, PPMP's cubic,
-    the advected quadratic and linear profiles, PPMP's two-zone Sod contact) by
-    far more than its tolerance; the oracle as it is passes them all."""
+    wave speed, the printed contact test and chi^p_L, the limiter's factor 2),
+    planted in a copy of the oracle source, fails one of the pins (linear data,
+    PPMP's cubic, the advected quadratic and linear profiles, PPMP's two-zone
+    Sod contact, PPMP's supersonic acoustic corrections); the oracle as it is
+    passes them all."""
     from concurrent.futures import ThreadPoolExecutor
 
     from tests.helpers import build_oracle_mutant

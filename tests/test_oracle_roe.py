@@ -292,3 +292,61 @@ def test_roe_pins_catch_planted_mistakes():
         print("%s: %s" % (tag, {k: "%.3g" % x for k, x in v.items()}))
     base = _roe_pin_violations(oracle.riemann_roe)
     assert max(base.values()) <= 1.0, base
+
+
+def _roe_steps_lib(L, u0, dx, gamma, nsteps, cfl, recon):
+    """oracle.run with the Roe solver through the oracle library L."""
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.oracle_init.restype = ctypes.c_void_p
+    L.oracle_init.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [ctypes.POINTER(ctypes.c_int)]
+    L.oracle_free.argtypes = [ctypes.c_void_p]
+    L.oracle_set_state.argtypes = [ctypes.c_void_p, dp]
+    L.oracle_get_state.argtypes = [ctypes.c_void_p, dp]
+    L.oracle_set_recon.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.oracle_set_solver.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.oracle_compute_dt.restype = ctypes.c_double
+    L.oracle_compute_dt.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    L.oracle_step_dt.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    u0 = np.ascontiguousarray(u0)
+    _, nz, ny, nx = u0.shape
+    h = L.oracle_init(nx, ny, nz, dx, gamma, (ctypes.c_int * 6)(*([P] * 6)))
+    assert h
+    try:
+        L.oracle_set_recon(h, int(recon))
+        L.oracle_set_solver(h, int(oracle.SOLVER_ROE))
+        L.oracle_set_state(h, u0.ctypes.data_as(dp))
+        for _ in range(nsteps):
+            L.oracle_step_dt(h, L.oracle_compute_dt(h, cfl))
+        u = np.zeros_like(u0)
+        L.oracle_get_state(h, u.ctypes.data_as(dp))
+    finally:
+        L.oracle_free(h)
+    return u
+
+
+def test_h_correction_reading_is_needed_for_mirror_symmetry():
+    """Reading N10 (App. C): the H-correction quantity takes the largest jump of
+    both acoustic speeds, max(|d(u + a)|, |d(u - a)|)/2.  A copy of the oracle
+    with the printed single term |d(u + a)|/2 breaks the mirror symmetry of Roe
+    steps on the Sedov blast (a mirrored flow gets different dissipation), which
+    the oracle as it is keeps to rounding."""
+    from tests.helpers import build_oracle_mutant
+    L = build_oracle_mutant("eta_printed", [(
+        "R h_eta(",
+        "return R(0.5) * mx(fabs((WR[1] + aR) - (WL[1] + aL)), fabs((WR[1] - aR) - (WL[1] - aL)));",
+        "return R(0.5) * fabs((WR[1] + aR) - (WL[1] + aL));")])
+    w = W.sedov(16)
+
+    def mirror_error(run):
+        u = run(w["u"])
+        return np.max(np.abs(run(mirror_x(w["u"])) - mirror_x(u))) / (1e-12 * np.abs(u).max())
+
+    bad = mirror_error(lambda x: _roe_steps_lib(L, x, w["dx"], w["gamma"], 4, 0.3,
+                                                oracle.RECON_PPMC))
+    good = mirror_error(lambda x: oracle.run(x, w["dx"], w["gamma"], [P] * 6, nsteps=4, cfl=0.3,
+                                             recon=oracle.RECON_PPMC,
+                                             solver=oracle.SOLVER_ROE)[0])
+    assert good <= 1.0, good
+    assert bad > 10.0, bad
+    print("mirror error over tolerance: printed eta %.3g, reading %.3g" % (bad, good))

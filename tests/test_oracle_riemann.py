@@ -384,6 +384,9 @@ _RIEMANN_MUTANTS = {
                  "AL = R(2.0) / (R(g.gm1) * dL), AR = R(2.0) / (R(g.gm1) * dR)")],
     # the left fan's sound speed with the sign of the velocity term flipped
     "fan_sign": [(_H_RP, "(aL + R(g.half_gm1) * uL)", "(aL - R(g.half_gm1) * uL)")],
+    # the right fan's sound speed as printed, a_R + (gamma-1) u_R / 2 (reading R18)
+    "right_fan_printed": [(_H_RP, "const R a = R(g.two_gp1) * (aR - R(g.half_gm1) * uR);",
+                           "const R a = aR + R(g.half_gm1) * uR;")],
     # the left shock speed with the two coefficients of the square root swapped
     "shock_speed": [(_H_RP, "sqrt(R(g.sh_a) * pm / pL + R(g.sh_b))",
                      "sqrt(R(g.sh_b) * pm / pL + R(g.sh_a))")],

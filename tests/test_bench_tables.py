@@ -80,3 +80,32 @@ def test_fp64_slot_table_matches_the_traffic_capture():
     for (wl, stage), v in bench.NCU_FP64_SLOTS.items():
         assert wl in ("sedov", "turbulence") and stage in bench.ALGORITHMIC_FLOPS["sedov"]
         assert 0 < v < 400
+
+
+def test_single_roofline_of_a_synthetic_fp64_step():
+    """The FP64 roofline from a per-stage split: the dominant stage (the second
+    Riemann set, its x and y, z kernels named), its algorithmic flops per launch
+    over its average launch time against the unit-count peak, the captured
+    traffic scaled to the launch's units while the sources match the capture,
+    and the FP64 issue fraction from the captured lane-slots (Sedov 256^3
+    shapes: 257 x 256 x 256 faces a launch, three launches)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    faces = 257 * 256 * 256
+    stages = {"prims": (2.4, 3, 3 * 264 ** 3), "riemann2": (16.2, 3, 3 * faces),
+              "riemann1": (9.9, 3, 3 * 257 * 258 * 258)}
+    r = bench.single_roofline(stages, "fp64", "sedov", "ppmc", "exact", 3, 128, None, 2070.0)
+    assert r["kernel"] == "kb_riemann2 (x) / kb_riemann2_seg (y, z)"
+    assert r["units_per_launch"] == faces and abs(r["avg_launch_ms"] - 5.4) < 1e-12
+    flops = bench.ALGORITHMIC_FLOPS["sedov"]["riemann2"] * faces / 5.4e-3
+    assert abs(r["achieved"] / flops - 1) < 1e-12
+    assert abs(r["frac"] - flops / bench.FP64_FLOPS_PEAK) < 1e-12
+    info = bench.NCU_TRAFFIC[("fp64", "riemann2")]
+    assert abs(r["traffic"] - info["bytes_per_unit"] * faces) < 1e-3
+    slots = bench.NCU_FP64_SLOTS[("sedov", "riemann2")]
+    assert abs(r["fp64_issue_frac"] - slots * faces / 5.4e-3 / (2 * 152 * 2070e6)) < 1e-12
+    # a 1D grid names the one-face kernel; the Roe solver its own kernel
+    r1 = bench.single_roofline(stages, "fp64", "sedov", "ppmc", "exact", 1, 128, None, 2070.0)
+    assert r1["kernel"] == "kb_riemann2"
+    rr = bench.single_roofline(stages, "fp64", "sedov", "ppmc", "roe", 3, 128, None, 2070.0)
+    assert rr["kernel"] == "kb_riemann2_roe" and rr["traffic"] is None
